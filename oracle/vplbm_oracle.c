@@ -1,0 +1,598 @@
+/*
+ * Plain FP64 CPU oracle of the volume-penalization lattice Boltzmann method
+ * (VP-LBM, D2Q9, multiple relaxation time) with a rigid disk.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * statement of what the GPU path computes.  It is used by the test-suite,
+ * by the package's smoke check and by the CPU-baseline leg of the benchmark;
+ * no product code path may call it.  It shares no code, header, table or
+ * constant with the CUDA implementation.
+ *
+ * Every step follows the paper in its own order (Algorithm 1, Sec. 2.3):
+ *   1. streaming of the post-collision populations (Eq. 18) with the
+ *      boundary rules of Sec. 3.1 / 3.2;
+ *   2. macroscopic moments (Eq. 19) with the penalized velocity of
+ *      Eqs. (20)-(22);
+ *   3. MRT collision with a source term (Eqs. 8, 17), moments by the
+ *      matrix M of Eq. (15), equilibria of Eq. (14), forcing of Eq. (12);
+ *   4. force and torque on the body, then the rigid-body update of
+ *      Eqs. (23)-(24) by fourth-order Runge-Kutta (Algorithm 1, step 3).
+ * Matrix-vector products are written as plain loops over the 9x9 matrices;
+ * M^-1 is obtained by Gauss-Jordan elimination, not from a closed form.
+ *
+ * Readings taken where the paper is silent or ambiguous (all restated in
+ * the design notes of the repository):
+ *   - Eq. (22) is evaluated in the algebraically identical form
+ *     a = -chi (j/rho + g/2 - u_s) / (eta + chi/2), u = j/rho + g/2 + a/2,
+ *     which stays finite for eta -> 0.
+ *   - The forcing term of Eq. (12) is used without its (1 - 1/(2 tau))
+ *     prefactor, because Eqs. (8)/(17) already apply (I - S/2) in moment
+ *     space; it is added with a plus sign as the body acceleration
+ *     a = -chi/eta (u - u_s) (the minus of Eq. 1 folded into a).
+ *   - chi(x) = 1 iff (i - x_G)^2 + (j - y_G)^2 <= R^2, evaluated in FP64
+ *     exactly as written (the file is compiled with -ffp-contract=off).
+ *   - The force that drives the body is the momentum exchanged through the
+ *     links between the solid region R(n) = {chi = 1 at step n} and the
+ *     rest of the lattice during the streaming into step n, i.e. Eqs.
+ *     (25)-(27) with u_Gamma = 0, summed here node by node over R(n):
+ *       F_h(n) = sum_{x in R(n)} [ j(x, n) - j~(x, n-1) ],
+ *       T_h(n) = sum_{x in R(n)} (x - x_G) x [ j(x, n) - j~(x, n-1) ],
+ *     j = sum_a c_a f_a after streaming, j~ = sum_a c_a f~_a of the node's
+ *     own post-collision populations.  The reaction of the penalization
+ *     force, sum_solid rho chi (u - u_s)/eta, and its torque are reduced
+ *     as well and recorded beside it.
+ *   - Walls are half-way bounce-back; a velocity wall adds
+ *     6 w_a rho0 (c_a . u_w); a zero-gradient edge copies the population of
+ *     the edge column itself.  When the source node of a pull lies outside
+ *     in y, the south/north rule wins over the west/east rule.
+ *
+ * Storage: f[(a*ny + j)*nx + i], node (i, j) at x = i, y = j.
+ * The state after n steps is the post-collision population field of step
+ * n - 1 (for n = 0: the equilibrium given at initialisation).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 9
+
+/* ---- lattice constants, restated from Sec. 2.2 ---------------------- */
+
+static int C[Q][2];      /* Eq. (10) */
+static double W[Q];      /* Eq. (13) */
+static int OPP[Q];       /* index of -c_a */
+/* Eq. (15): rows rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy */
+static const double M[Q][Q] = {
+    { 1,  1,  1,  1,  1,  1,  1,  1,  1},
+    {-4, -1, -1, -1, -1,  2,  2,  2,  2},
+    { 4, -2, -2, -2, -2,  1,  1,  1,  1},
+    { 0,  1,  0, -1,  0,  1, -1, -1,  1},
+    { 0, -2,  0,  2,  0,  1, -1, -1,  1},
+    { 0,  0,  1,  0, -1,  1,  1, -1, -1},
+    { 0,  0, -2,  0,  2,  1,  1, -1, -1},
+    { 0,  1, -1,  1, -1,  0,  0,  0,  0},
+    { 0,  0,  0,  0,  0,  1, -1,  1, -1}};
+static double MINV[Q][Q];
+static int constants_ready = 0;
+
+static void setup_constants(void)
+{
+    if (constants_ready) return;
+    const double pi = 3.14159265358979323846;
+    /* Eq. (10): c_0 = 0; c_1..4 at angles (a-1) pi/2; c_5..8 at (2a-9) pi/4,
+     * length sqrt(2); rounded to the integer lattice vectors. */
+    C[0][0] = 0; C[0][1] = 0;
+    for (int a = 1; a <= 4; ++a) {
+        double ang = (a - 1) * pi / 2.0;
+        C[a][0] = (int)lround(cos(ang));
+        C[a][1] = (int)lround(sin(ang));
+    }
+    for (int a = 5; a <= 8; ++a) {
+        double ang = (2 * a - 9) * pi / 4.0;
+        C[a][0] = (int)lround(sqrt(2.0) * cos(ang));
+        C[a][1] = (int)lround(sqrt(2.0) * sin(ang));
+    }
+    /* Eq. (13) */
+    W[0] = 4.0 / 9.0;
+    for (int a = 1; a <= 4; ++a) W[a] = 1.0 / 9.0;
+    for (int a = 5; a <= 8; ++a) W[a] = 1.0 / 36.0;
+    for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < Q; ++b)
+            if (C[b][0] == -C[a][0] && C[b][1] == -C[a][1]) OPP[a] = b;
+    /* M^-1 by Gauss-Jordan elimination with partial pivoting. */
+    double A[Q][2 * Q];
+    for (int r = 0; r < Q; ++r)
+        for (int c = 0; c < 2 * Q; ++c)
+            A[r][c] = (c < Q) ? M[r][c] : (c - Q == r ? 1.0 : 0.0);
+    for (int col = 0; col < Q; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < Q; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (piv != col)
+            for (int c = 0; c < 2 * Q; ++c) {
+                double t = A[col][c]; A[col][c] = A[piv][c]; A[piv][c] = t;
+            }
+        double p = A[col][col];
+        for (int c = 0; c < 2 * Q; ++c) A[col][c] /= p;
+        for (int r = 0; r < Q; ++r) {
+            if (r == col) continue;
+            double fct = A[r][col];
+            if (fct == 0.0) continue;
+            for (int c = 0; c < 2 * Q; ++c) A[r][c] -= fct * A[col][c];
+        }
+    }
+    for (int r = 0; r < Q; ++r)
+        for (int c = 0; c < Q; ++c) MINV[r][c] = A[r][Q + c];
+    constants_ready = 1;
+}
+
+/* ---- public descriptors (ctypes mirrors them) ------------------------ */
+
+enum { ORC_PERIODIC = 0, ORC_NOSLIP = 1, ORC_VELOCITY = 2, ORC_ZEROGRAD = 3 };
+enum { ORC_WEST = 0, ORC_EAST = 1, ORC_SOUTH = 2, ORC_NORTH = 3 };
+enum { ORC_FIXED = 0, ORC_IMPOSED = 1, ORC_FREE = 2 };
+
+typedef struct {
+    int nx, ny;
+    double s[Q];          /* diagonal of S, Eq. (16) */
+    double eta;           /* penalization factor, Eq. (2) */
+    double rho0;          /* reference density of the walls */
+    double gx, gy;        /* uniform body acceleration of the fluid */
+    int bc_kind[4];       /* west, east, south, north */
+    double bc_u[4][2];    /* uniform wall velocity per edge */
+    const double *bc_ux[4]; /* optional per-node wall velocity, edge length */
+    const double *bc_uy[4];
+} orc_lattice;
+
+typedef struct {
+    int present;
+    double radius;
+    double x, y, theta, vx, vy, omega;   /* initial pose and velocity */
+    int motion;                          /* ORC_FIXED / ORC_IMPOSED / ORC_FREE */
+    int axis;                            /* imposed coordinate: 0 x, 1 y, 2 theta */
+    double amp, freq, phase;             /* q(t) = q_c + amp sin(2 pi freq t + phase) */
+    double mass, inertia;
+    double damp[3], stiff[3], q0[3], f_ext[3];  /* Eqs. (23)-(24), per x, y, theta */
+    unsigned dof_mask;                   /* bit0 x, bit1 y, bit2 theta */
+    double u_ref, d_ref;                 /* C_D, C_L normalisation (Sec. 3.1) */
+} orc_body;
+
+/* One record per step n: force and torque of that step, pose used by it. */
+typedef struct {
+    double t, fx, fy, torque, cd, cl, x, y, theta, vx, vy, omega;
+    double fpen_x, fpen_y, tpen, n_solid;
+} orc_record;
+
+typedef struct {
+    orc_lattice lat;
+    orc_body body;
+    double *prof_ux[4], *prof_uy[4];
+    double *ft;            /* post-collision populations (the state) */
+    double *fn;            /* scratch for the next state */
+    long long step;
+    double q[3], v[3];     /* pose (x, y, theta) and velocity */
+    double q_center;       /* centre of the imposed sinusoid */
+    orc_record *hist;
+    long long hist_cap;
+} orc_sim;
+
+/* ---- small building blocks ------------------------------------------ */
+
+static double edge_u(const orc_sim *s, int side, int comp, int k)
+{
+    const double *p = comp == 0 ? s->prof_ux[side] : s->prof_uy[side];
+    if (p) return p[k];
+    return s->lat.bc_u[side][comp];
+}
+
+/* chi of Eq. (2) for the disk at the current pose (reading R1). */
+static int chi_at(const orc_sim *s, int i, int j)
+{
+    if (!s->body.present) return 0;
+    double dx = (double)i - s->q[0];
+    double dy = (double)j - s->q[1];
+    double d2 = dx * dx + dy * dy;
+    double r2 = s->body.radius * s->body.radius;
+    return d2 <= r2;
+}
+
+/* Equilibrium of Eq. (11). */
+static void equilibrium(double rho, double ux, double uy, double feq[Q])
+{
+    const double cs2 = 1.0 / 3.0;
+    for (int a = 0; a < Q; ++a) {
+        double cu = C[a][0] * ux + C[a][1] * uy;
+        /* uu : (cc - cs^2 I) */
+        double uucc = ux * ux * (C[a][0] * C[a][0] - cs2)
+                    + 2.0 * ux * uy * (C[a][0] * C[a][1])
+                    + uy * uy * (C[a][1] * C[a][1] - cs2);
+        feq[a] = W[a] * rho * (1.0 + cu / cs2 + uucc / (2.0 * cs2 * cs2));
+    }
+}
+
+/* Moment equilibria of Eq. (14). */
+static void moment_equilibrium(double rho, double ux, double uy, double meq[Q])
+{
+    double u2 = ux * ux + uy * uy;
+    meq[0] = rho;
+    meq[1] = rho * (-2.0 + 3.0 * u2);
+    meq[2] = rho * (1.0 - 3.0 * u2);
+    meq[3] = rho * ux;
+    meq[4] = -rho * ux;
+    meq[5] = rho * uy;
+    meq[6] = -rho * uy;
+    meq[7] = rho * (ux * ux - uy * uy);
+    meq[8] = rho * ux * uy;
+}
+
+/* Forcing term of Eq. (12) for the force density G = rho F, without the
+ * (1 - 1/(2 tau)) prefactor (it is replaced by (I - S/2) of Eq. 17). */
+static void guo_forcing(double ux, double uy, double Gx, double Gy, double F[Q])
+{
+    const double cs2 = 1.0 / 3.0;
+    for (int a = 0; a < Q; ++a) {
+        double cu = C[a][0] * ux + C[a][1] * uy;
+        double vx = (C[a][0] - ux) / cs2 + cu * C[a][0] / (cs2 * cs2);
+        double vy = (C[a][1] - uy) / cs2 + cu * C[a][1] / (cs2 * cs2);
+        F[a] = W[a] * (vx * Gx + vy * Gy);
+    }
+}
+
+/* Velocity of Eq. (22) in the eta-stable form; returns the penalization
+ * acceleration a and the velocity u. */
+static void penalized_velocity(double rho, double jx, double jy, int chi,
+                               double usx, double usy, double eta,
+                               double gx, double gy,
+                               double *ux, double *uy, double *ax, double *ay)
+{
+    double vx = jx / rho + 0.5 * gx;
+    double vy = jy / rho + 0.5 * gy;
+    double c = (double)chi;
+    *ax = -c * (vx - usx) / (eta + 0.5 * c);
+    *ay = -c * (vy - usy) / (eta + 0.5 * c);
+    *ux = vx + 0.5 * *ax;
+    *uy = vy + 0.5 * *ay;
+}
+
+/* MRT collision with source, Eq. (17): m* = m - S (m - m_eq) + (I - S/2) M F. */
+static void collide(const double f[Q], const double s[Q], double rho,
+                    double ux, double uy, double Gx, double Gy, double ft[Q])
+{
+    double m[Q], meq[Q], F[Q], MF[Q], ms[Q];
+    for (int r = 0; r < Q; ++r) {
+        m[r] = 0.0;
+        for (int a = 0; a < Q; ++a) m[r] += M[r][a] * f[a];
+    }
+    moment_equilibrium(rho, ux, uy, meq);
+    guo_forcing(ux, uy, Gx, Gy, F);
+    for (int r = 0; r < Q; ++r) {
+        MF[r] = 0.0;
+        for (int a = 0; a < Q; ++a) MF[r] += M[r][a] * F[a];
+    }
+    for (int r = 0; r < Q; ++r)
+        ms[r] = m[r] - s[r] * (m[r] - meq[r]) + (1.0 - 0.5 * s[r]) * MF[r];
+    for (int a = 0; a < Q; ++a) {
+        ft[a] = 0.0;
+        for (int r = 0; r < Q; ++r) ft[a] += MINV[a][r] * ms[r];
+    }
+}
+
+/* ---- streaming with boundary rules (Eq. 18) ------------------------- */
+
+static double pulled(const orc_sim *s, int a, int i, int j)
+{
+    const int nx = s->lat.nx, ny = s->lat.ny;
+    const double *ft = s->ft;
+#define FT(b, ii, jj) ft[((size_t)(b) * ny + (jj)) * nx + (ii)]
+    int si = i - C[a][0];
+    int sj = j - C[a][1];
+    if (sj < 0 || sj >= ny) {
+        int side = sj < 0 ? ORC_SOUTH : ORC_NORTH;
+        int kind = s->lat.bc_kind[side];
+        if (kind == ORC_PERIODIC) {
+            sj = (sj + ny) % ny;
+        } else {
+            /* half-way bounce-back at y = -1/2 or y = ny - 1/2 */
+            double val = FT(OPP[a], i, j);
+            if (kind == ORC_VELOCITY) {
+                double cu = C[a][0] * edge_u(s, side, 0, i) + C[a][1] * edge_u(s, side, 1, i);
+                val += 6.0 * W[a] * s->lat.rho0 * cu;
+            }
+            return val;
+        }
+    }
+    if (si < 0 || si >= nx) {
+        int side = si < 0 ? ORC_WEST : ORC_EAST;
+        int kind = s->lat.bc_kind[side];
+        if (kind == ORC_PERIODIC) {
+            si = (si + nx) % nx;
+        } else if (kind == ORC_ZEROGRAD) {
+            return FT(a, i, sj);
+        } else {
+            double val = FT(OPP[a], i, j);
+            if (kind == ORC_VELOCITY) {
+                double cu = C[a][0] * edge_u(s, side, 0, j) + C[a][1] * edge_u(s, side, 1, j);
+                val += 6.0 * W[a] * s->lat.rho0 * cu;
+            }
+            return val;
+        }
+    }
+    return FT(a, si, sj);
+#undef FT
+}
+
+/* Macroscopic state of node (i, j) at the current step: the pulled
+ * populations f, rho, j, chi, u_s, velocity u and penalization a. */
+typedef struct {
+    double f[Q];
+    double rho, jx, jy, ux, uy, ax, ay, usx, usy, dx, dy;
+    int chi;
+} node_state;
+
+static void node_macro(const orc_sim *s, int i, int j, node_state *ns)
+{
+    ns->rho = 0.0; ns->jx = 0.0; ns->jy = 0.0;
+    for (int a = 0; a < Q; ++a) {
+        ns->f[a] = pulled(s, a, i, j);
+        ns->rho += ns->f[a];                 /* Eq. (19) */
+        ns->jx += C[a][0] * ns->f[a];
+        ns->jy += C[a][1] * ns->f[a];
+    }
+    ns->chi = chi_at(s, i, j);
+    ns->dx = (double)i - s->q[0];
+    ns->dy = (double)j - s->q[1];
+    /* rigid-body velocity at the node */
+    ns->usx = s->v[0] - s->v[2] * ns->dy;
+    ns->usy = s->v[1] + s->v[2] * ns->dx;
+    penalized_velocity(ns->rho, ns->jx, ns->jy, ns->chi, ns->usx, ns->usy,
+                       s->lat.eta, s->lat.gx, s->lat.gy,
+                       &ns->ux, &ns->uy, &ns->ax, &ns->ay);
+}
+
+/* ---- rigid body (Eqs. 23-24, Algorithm 1 step 3) -------------------- */
+
+static void body_rhs(const orc_body *b, const double F[3], const double q[3],
+                     const double v[3], double acc[3])
+{
+    for (int d = 0; d < 3; ++d) {
+        double m = d < 2 ? b->mass : b->inertia;
+        acc[d] = (F[d] + b->f_ext[d] - b->damp[d] * v[d] - b->stiff[d] * (q[d] - b->q0[d])) / m;
+    }
+}
+
+/* Advance pose and velocity by one time step (h = 1) with the hydrodynamic
+ * force and torque F held over the step. */
+static void body_advance(const orc_body *b, long long step, double q_center,
+                         const double F[3], double q[3], double v[3])
+{
+    const double pi = 3.14159265358979323846;
+    if (b->motion == ORC_FIXED) return;
+    if (b->motion == ORC_IMPOSED) {
+        double t1 = (double)(step + 1);
+        double ph = 2.0 * pi * b->freq * t1 + b->phase;
+        q[b->axis] = q_center + b->amp * sin(ph);
+        v[b->axis] = 2.0 * pi * b->freq * b->amp * cos(ph);
+        return;
+    }
+    /* classic fourth-order Runge-Kutta on (q, v) for the free DOFs */
+    const double h = 1.0;
+    double k1q[3], k1v[3], k2q[3], k2v[3], k3q[3], k3v[3], k4q[3], k4v[3];
+    double qt[3], vt[3];
+    for (int d = 0; d < 3; ++d) k1q[d] = v[d];
+    body_rhs(b, F, q, v, k1v);
+    for (int d = 0; d < 3; ++d) { qt[d] = q[d] + 0.5 * h * k1q[d]; vt[d] = v[d] + 0.5 * h * k1v[d]; }
+    for (int d = 0; d < 3; ++d) k2q[d] = vt[d];
+    body_rhs(b, F, qt, vt, k2v);
+    for (int d = 0; d < 3; ++d) { qt[d] = q[d] + 0.5 * h * k2q[d]; vt[d] = v[d] + 0.5 * h * k2v[d]; }
+    for (int d = 0; d < 3; ++d) k3q[d] = vt[d];
+    body_rhs(b, F, qt, vt, k3v);
+    for (int d = 0; d < 3; ++d) { qt[d] = q[d] + h * k3q[d]; vt[d] = v[d] + h * k3v[d]; }
+    for (int d = 0; d < 3; ++d) k4q[d] = vt[d];
+    body_rhs(b, F, qt, vt, k4v);
+    for (int d = 0; d < 3; ++d) {
+        if (!((b->dof_mask >> d) & 1u)) continue;
+        q[d] = q[d] + h / 6.0 * (k1q[d] + 2.0 * k2q[d] + 2.0 * k3q[d] + k4q[d]);
+        v[d] = v[d] + h / 6.0 * (k1v[d] + 2.0 * k2v[d] + 2.0 * k3v[d] + k4v[d]);
+    }
+}
+
+/* ---- public API ------------------------------------------------------ */
+
+void orc_free(orc_sim *s);
+
+orc_sim *orc_create(const orc_lattice *lat, const orc_body *body, long long hist_cap)
+{
+    setup_constants();
+    if (lat->nx < 2 || lat->ny < 2) return NULL;
+    orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
+    if (!s) return NULL;
+    s->lat = *lat;
+    if (body) s->body = *body; else s->body.present = 0;
+    for (int side = 0; side < 4; ++side) {
+        int len = side < 2 ? lat->ny : lat->nx;
+        s->lat.bc_ux[side] = NULL; s->lat.bc_uy[side] = NULL;
+        if (lat->bc_ux[side]) {
+            s->prof_ux[side] = (double *)malloc(sizeof(double) * len);
+            memcpy(s->prof_ux[side], lat->bc_ux[side], sizeof(double) * len);
+        }
+        if (lat->bc_uy[side]) {
+            s->prof_uy[side] = (double *)malloc(sizeof(double) * len);
+            memcpy(s->prof_uy[side], lat->bc_uy[side], sizeof(double) * len);
+        }
+    }
+    size_t n = (size_t)Q * lat->nx * lat->ny;
+    s->ft = (double *)calloc(n, sizeof(double));
+    s->fn = (double *)calloc(n, sizeof(double));
+    s->hist_cap = hist_cap > 0 ? hist_cap : 1;
+    s->hist = (orc_record *)calloc((size_t)s->hist_cap, sizeof(orc_record));
+    if (!s->ft || !s->fn || !s->hist) { orc_free(s); return NULL; }
+    s->q[0] = s->body.x; s->q[1] = s->body.y; s->q[2] = s->body.theta;
+    s->v[0] = s->body.vx; s->v[1] = s->body.vy; s->v[2] = s->body.omega;
+    if (s->body.present && s->body.motion == ORC_IMPOSED)
+        s->q_center = s->q[s->body.axis] - s->body.amp * sin(s->body.phase);
+    s->step = 0;
+    return s;
+}
+
+void orc_free(orc_sim *s)
+{
+    if (!s) return;
+    for (int side = 0; side < 4; ++side) { free(s->prof_ux[side]); free(s->prof_uy[side]); }
+    free(s->ft); free(s->fn); free(s->hist); free(s);
+}
+
+/* State = equilibrium (Eq. 11) of the given fields (NULL: rho0, 0). */
+void orc_init_equilibrium(orc_sim *s, const double *rho, const double *ux, const double *uy)
+{
+    const int nx = s->lat.nx, ny = s->lat.ny;
+    double feq[Q];
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t k = (size_t)j * nx + i;
+            equilibrium(rho ? rho[k] : s->lat.rho0, ux ? ux[k] : 0.0, uy ? uy[k] : 0.0, feq);
+            for (int a = 0; a < Q; ++a) s->ft[((size_t)a * ny + j) * nx + i] = feq[a];
+        }
+}
+
+void orc_set_populations(orc_sim *s, const double *f)
+{
+    memcpy(s->ft, f, sizeof(double) * (size_t)Q * s->lat.nx * s->lat.ny);
+}
+
+void orc_get_populations(const orc_sim *s, double *f)
+{
+    memcpy(f, s->ft, sizeof(double) * (size_t)Q * s->lat.nx * s->lat.ny);
+}
+
+/* rho(n), u(n) of Eqs. (19)-(22) at the current step. */
+void orc_get_fields(const orc_sim *s, double *rho, double *ux, double *uy)
+{
+    const int nx = s->lat.nx, ny = s->lat.ny;
+    node_state ns;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            node_macro(s, i, j, &ns);
+            size_t k = (size_t)j * nx + i;
+            if (rho) rho[k] = ns.rho;
+            if (ux) ux[k] = ns.ux;
+            if (uy) uy[k] = ns.uy;
+        }
+}
+
+/* One time step of Algorithm 1. */
+static void one_step(orc_sim *s)
+{
+    const int nx = s->lat.nx, ny = s->lat.ny;
+    node_state ns;
+    double ft[Q];
+    double fpen[3] = {0, 0, 0}, fh[3] = {0, 0, 0};
+    double nsolid = 0.0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            node_macro(s, i, j, &ns);
+            double Gx = ns.rho * (s->lat.gx + ns.ax);
+            double Gy = ns.rho * (s->lat.gy + ns.ay);
+            collide(ns.f, s->lat.s, ns.rho, ns.ux, ns.uy, Gx, Gy, ft);
+            for (int a = 0; a < Q; ++a) s->fn[((size_t)a * ny + j) * nx + i] = ft[a];
+            if (ns.chi) {
+                /* reaction of the penalization force on the body */
+                double px = -ns.rho * ns.ax, py = -ns.rho * ns.ay;
+                fpen[0] += px;
+                fpen[1] += py;
+                fpen[2] += ns.dx * py - ns.dy * px;
+                /* momentum brought into the node by the streaming (Eq. 25) */
+                double ox = 0.0, oy = 0.0;
+                for (int a = 0; a < Q; ++a) {
+                    double own = s->ft[((size_t)a * ny + j) * nx + i];
+                    ox += C[a][0] * own;
+                    oy += C[a][1] * own;
+                }
+                double ex = ns.jx - ox, ey = ns.jy - oy;
+                fh[0] += ex;
+                fh[1] += ey;
+                fh[2] += ns.dx * ey - ns.dy * ex;   /* Eq. (27) */
+                nsolid += 1.0;
+            }
+        }
+    double *t = s->ft; s->ft = s->fn; s->fn = t;
+
+    orc_record *r = &s->hist[s->step % s->hist_cap];
+    r->t = (double)s->step;
+    r->fx = fh[0]; r->fy = fh[1]; r->torque = fh[2];
+    double qref = 0.5 * s->lat.rho0 * s->body.d_ref * s->body.u_ref * s->body.u_ref;
+    r->cd = qref > 0 ? fh[0] / qref : 0.0;
+    r->cl = qref > 0 ? fh[1] / qref : 0.0;
+    r->x = s->q[0]; r->y = s->q[1]; r->theta = s->q[2];
+    r->vx = s->v[0]; r->vy = s->v[1]; r->omega = s->v[2];
+    r->fpen_x = fpen[0]; r->fpen_y = fpen[1]; r->tpen = fpen[2];
+    r->n_solid = nsolid;
+
+    if (s->body.present) body_advance(&s->body, s->step, s->q_center, fh, s->q, s->v);
+    s->step += 1;
+}
+
+void orc_step(orc_sim *s, long long n)
+{
+    for (long long k = 0; k < n; ++k) one_step(s);
+}
+
+long long orc_get_step(const orc_sim *s) { return s->step; }
+
+/* Copies records first .. first+count-1 (must still be in the ring). */
+int orc_get_history(const orc_sim *s, long long first, long long count, orc_record *dst)
+{
+    if (first < 0 || count < 0 || first + count > s->step) return -1;
+    if (first < s->step - s->hist_cap) return -1;
+    for (long long k = 0; k < count; ++k) dst[k] = s->hist[(first + k) % s->hist_cap];
+    return 0;
+}
+
+void orc_get_body(const orc_sim *s, double q[3], double v[3])
+{
+    for (int d = 0; d < 3; ++d) { q[d] = s->q[d]; v[d] = s->v[d]; }
+}
+
+/* ---- single-node entry points used by the pinning tests ------------- */
+
+void orc_constants(int c[Q][2], double w[Q], double m[Q][Q], double minv[Q][Q])
+{
+    setup_constants();
+    memcpy(c, C, sizeof(C)); memcpy(w, W, sizeof(W));
+    memcpy(m, M, sizeof(M)); memcpy(minv, MINV, sizeof(MINV));
+}
+
+void orc_equilibrium(double rho, double ux, double uy, double feq[Q])
+{
+    setup_constants();
+    equilibrium(rho, ux, uy, feq);
+}
+
+void orc_moment_equilibrium(double rho, double ux, double uy, double meq[Q])
+{
+    moment_equilibrium(rho, ux, uy, meq);
+}
+
+void orc_guo_forcing(double ux, double uy, double Gx, double Gy, double F[Q])
+{
+    setup_constants();
+    guo_forcing(ux, uy, Gx, Gy, F);
+}
+
+void orc_collide(const double f[Q], const double s[Q], double rho, double ux,
+                 double uy, double Gx, double Gy, double ft[Q])
+{
+    setup_constants();
+    collide(f, s, rho, ux, uy, Gx, Gy, ft);
+}
+
+void orc_penalized_velocity(double rho, double jx, double jy, int chi, double usx,
+                            double usy, double eta, double gx, double gy, double out[4])
+{
+    penalized_velocity(rho, jx, jy, chi, usx, usy, eta, gx, gy, &out[0], &out[1], &out[2], &out[3]);
+}
+
+void orc_body_advance(const orc_body *b, long long step, double q_center,
+                      const double F[3], double q[3], double v[3])
+{
+    body_advance(b, step, q_center, F, q, v);
+}

@@ -1,0 +1,367 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these checks re-types an oracle formula: each one compares the
+oracle with a different statement of the same fact (a second formula of the
+paper, a textbook moment identity, a conservation law, a closed-form
+solution, an exact fixed point).  A dropped term, a wrong sign or a
+transposed index in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+RNG = np.random.default_rng(1234)
+CS2 = 1.0 / 3.0
+
+
+def test_lattice_vectors_match_moment_rows():
+    # Eq. (10) evaluated from its trigonometric form must give the velocity
+    # set whose x/y components are the j_x and j_y rows of M (Eq. 15).
+    c, w, M, Minv = oracle.constants()
+    assert np.array_equal(c[:, 0], M[3].astype(int))
+    assert np.array_equal(c[:, 1], M[5].astype(int))
+    assert np.array_equal(c[1:5], [[1, 0], [0, 1], [-1, 0], [0, -1]])
+    assert np.array_equal(c[5:], [[1, 1], [-1, 1], [-1, -1], [1, -1]])
+
+
+def test_weights_isotropy():
+    # Eq. (13) with c_s^2 = 1/3: sum w = 1, sum w c = 0, sum w c c = c_s^2 I,
+    # and the fourth-order isotropy sum w c_x^2 c_y^2 = c_s^4.
+    c, w, _, _ = oracle.constants()
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.allclose(w @ c, 0.0, atol=1e-16)
+    cc = np.einsum("a,ai,aj->ij", w, c, c)
+    assert np.allclose(cc, CS2 * np.eye(2), atol=1e-15)
+    assert abs(np.sum(w * c[:, 0] ** 2 * c[:, 1] ** 2) - CS2 ** 2) < 1e-15
+
+
+def test_moment_matrix_inverse_and_orthogonality():
+    _, _, M, Minv = oracle.constants()
+    assert np.allclose(M @ Minv, np.eye(9), atol=1e-15)
+    assert np.allclose(Minv @ M, np.eye(9), atol=1e-15)
+    G = M @ M.T
+    assert np.allclose(G, np.diag([9, 36, 36, 6, 12, 6, 12, 4, 4]), atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_equilibrium_moments(seed):
+    # Two independent statements of the paper: M f_eq (Eqs. 11, 15) equals
+    # the moment equilibria of Eq. (14).
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + rng.uniform(-0.1, 0.1)
+    ux, uy = rng.uniform(-0.1, 0.1, size=2)
+    _, _, M, _ = oracle.constants()
+    feq = oracle.equilibrium(rho, ux, uy)
+    meq = oracle.moment_equilibrium(rho, ux, uy)
+    assert np.allclose(M @ feq, meq, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_forcing_moments(seed):
+    # Guo's forcing (Eq. 12, without the prefactor): zeroth moment 0, first
+    # moment G, second moment u G + G u.
+    rng = np.random.default_rng(seed)
+    ux, uy, gx, gy = rng.uniform(-0.1, 0.1, size=4)
+    c, _, _, _ = oracle.constants()
+    F = oracle.guo_forcing(ux, uy, gx, gy)
+    assert abs(F.sum()) < 1e-16
+    assert np.allclose(c.T @ F, [gx, gy], atol=1e-16)
+    second = np.einsum("a,ai,aj->ij", F, c, c)
+    u = np.array([ux, uy])
+    g = np.array([gx, gy])
+    assert np.allclose(second, np.outer(u, g) + np.outer(g, u), atol=1e-16)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_equilibrium_is_fixed_point(seed):
+    rng = np.random.default_rng(seed)
+    s = rng.uniform(0.5, 1.95, size=9)
+    rho = 1.0 + rng.uniform(-0.1, 0.1)
+    ux, uy = rng.uniform(-0.1, 0.1, size=2)
+    feq = oracle.equilibrium(rho, ux, uy)
+    out = oracle.collide(feq, s, rho, ux, uy, 0.0, 0.0)
+    assert np.allclose(out, feq, rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_collision_conserves_mass_and_adds_force(seed):
+    # With rho = sum f and u = (sum c f + G/2)/rho (Eq. 19), the collision
+    # must keep mass and add exactly G to the momentum, for any S.
+    rng = np.random.default_rng(seed)
+    c, _, _, _ = oracle.constants()
+    f = oracle.equilibrium(1.02, 0.03, -0.02) * (1 + 0.05 * rng.uniform(-1, 1, 9))
+    s = rng.uniform(0.5, 1.95, size=9)
+    gx, gy = rng.uniform(-1e-3, 1e-3, size=2)
+    rho = f.sum()
+    j = c.T @ f
+    ux, uy = (j + 0.5 * np.array([gx, gy])) / rho
+    out = oracle.collide(f, s, rho, ux, uy, gx, gy)
+    assert abs(out.sum() - rho) < 1e-15
+    assert np.allclose(c.T @ out - j, [gx, gy], atol=1e-16)
+
+
+@pytest.mark.parametrize("eta", [1e-3, 1e-6, 0.3])
+def test_penalized_velocity_matches_eq22(eta):
+    # The eta-stable evaluation equals Eq. (22) as printed; in the solid the
+    # velocity tends to u_s as eta -> 0, in the fluid it is j/rho.
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        rho = 1.0 + rng.uniform(-0.05, 0.05)
+        jx, jy, usx, usy = rng.uniform(-0.1, 0.1, size=4)
+        for chi in (0, 1):
+            ux, uy, ax, ay = oracle.penalized_velocity(rho, jx, jy, chi, usx, usy, eta)
+            k = chi / eta
+            lit_x = (jx + 0.5 * k * rho * usx) / (rho + 0.5 * k * rho)
+            lit_y = (jy + 0.5 * k * rho * usy) / (rho + 0.5 * k * rho)
+            assert abs(ux - lit_x) < 1e-13 and abs(uy - lit_y) < 1e-13
+            # a = -chi/eta (u - u_s) (penalization term of Eq. 1)
+            assert abs(ax + k * (ux - usx)) < 1e-9 * max(1.0, k * 1e-3)
+            if chi == 0:
+                assert ux == jx / rho and ax == 0.0
+            elif eta <= 1e-6:
+                assert abs(ux - usx) < 1e-5 and abs(uy - usy) < 1e-5
+
+
+def _momentum(f):
+    c, _, _, _ = oracle.constants()
+    return np.array([np.sum(c[:, 0][:, None, None] * f), np.sum(c[:, 1][:, None, None] * f)])
+
+
+def test_uniform_penalization_closed_form():
+    # A disk covering the whole periodic box, held with velocity V: the
+    # momentum obeys j_{n+1} = j_n + rho a_n with a_n from Eq. (22), i.e.
+    # (j_n/rho - V) = r^n (j_0/rho - V), r = (eta - 1/2)/(eta + 1/2).
+    eta = 0.3
+    V = np.array([0.02, -0.01])
+    body = {"radius": 1e4, "x": 3.0, "y": 2.0, "vx": V[0], "vy": V[1], "motion": "fixed"}
+    p = wl.periodic_box(6, 5, tau=0.7, eta=eta, body=body)
+    sim = oracle.OracleSim(p)
+    u0 = np.array([0.05, 0.03])
+    sim.init_equilibrium(np.ones((5, 6)), np.full((5, 6), u0[0]), np.full((5, 6), u0[1]))
+    r = (eta - 0.5) / (eta + 0.5)
+    for n in range(1, 8):
+        sim.step(1)
+        j = _momentum(sim.populations()) / 30.0
+        assert np.allclose(j - V, r ** n * (u0 - V), atol=1e-15)
+
+
+def test_galilean_uniform_flow_with_comoving_body():
+    # Uniform flow U, a (very heavy) free disk moving at U: nothing changes.
+    U = (0.04, 0.015)
+    body = {"radius": 5.3, "x": 15.2, "y": 11.7, "vx": U[0], "vy": U[1],
+            "motion": "free", "mass": 1e30, "inertia": 1e30, "dof_mask": 7}
+    p = wl.periodic_box(32, 24, tau=0.6, eta=1e-3, body=body)
+    sim = oracle.OracleSim(p)
+    sim.init_equilibrium(np.ones((24, 32)), np.full((24, 32), U[0]), np.full((24, 32), U[1]))
+    f0 = sim.populations()
+    sim.step(40)
+    assert np.max(np.abs(sim.populations() - f0)) < 1e-15
+    q, v = sim.body_state()
+    assert abs(q[0] - (15.2 + 40 * U[0])) < 1e-12 and abs(q[1] - (11.7 + 40 * U[1])) < 1e-12
+
+
+def _chi(nx, ny, q, radius):
+    X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    return (X - q[0]) ** 2 + (Y - q[1]) ** 2 <= radius * radius
+
+
+def _mem_link_sum(S, chi, q):
+    """Eqs. (25)-(27) with u_Gamma = 0, link by link, periodic lattice."""
+    c, _, _, _ = oracle.constants()
+    ny, nx = chi.shape
+    F = np.zeros(2)
+    T = 0.0
+    for j in range(ny):
+        for i in range(nx):
+            if not chi[j, i]:
+                continue
+            for a in range(1, 9):
+                cx, cy = c[a]
+                fi, fj = (i - cx) % nx, (j - cy) % ny      # x_f = x_s - e_a
+                if not chi[fj, fi]:
+                    opp = [k for k in range(9) if c[k][0] == -cx and c[k][1] == -cy][0]
+                    # e_a f~_a(x_f) - e_abar f~_abar(x_s)
+                    link = np.array([cx, cy]) * (S[a, fj, fi] + S[opp, j, i])
+                    F += link
+                    T += (i - q[0]) * link[1] - (j - q[1]) * link[0]
+    return F, T
+
+
+def test_body_force_is_momentum_exchange_and_momentum_balances():
+    # Periodic box with a free disk: the force driving the body equals the
+    # momentum-exchange sum over solid/fluid links (Eqs. 25-27, u_Gamma = 0);
+    # the fluid gains exactly -F_pen per step (the sum of G); the body gains
+    # exactly F_h (RK4 with a constant force is exact); mass is conserved.
+    body = {"radius": 4.5, "x": 14.3, "y": 12.6, "vx": 0.01, "vy": -0.005,
+            "motion": "free", "mass": 90.0, "inertia": 900.0, "dof_mask": 3}
+    p = wl.periodic_box(30, 26, tau=0.65, eta=1e-3, body=body)
+    sim = oracle.OracleSim(p)
+    f0 = wl.random_populations(30, 26, seed=3, amp=0.02, u_amp=0.03)
+    sim.set_populations(f0)
+    mass0 = f0.sum()
+    S = sim.populations()
+    prev_j = _momentum(S)
+    prev_q, prev_v = sim.body_state()
+    for n in range(25):
+        F_mem, T_mem = _mem_link_sum(S, _chi(30, 26, prev_q, 4.5), prev_q)
+        sim.step(1)
+        S = sim.populations()
+        assert abs(S.sum() - mass0) < 1e-14 * mass0
+        rec = sim.history(n, 1)[0]
+        assert np.allclose([rec[1], rec[2]], F_mem, atol=1e-15)
+        assert abs(rec[3] - T_mem) < 1e-13
+        j = _momentum(S)
+        assert np.allclose(j - prev_j, [-rec[12], -rec[13]], atol=1e-14)
+        q, v = sim.body_state()
+        assert np.allclose(body["mass"] * (v[:2] - prev_v[:2]), [rec[1], rec[2]], atol=1e-13)
+        prev_j, prev_q, prev_v = j, q, v
+
+
+def test_angular_momentum_balance_rotating_disk():
+    # Disk free to rotate only, fluid at rest far away: the fluid's angular
+    # momentum about x_G changes by -T_pen per step, and the body's by T_h.
+    body = {"radius": 5.0, "x": 23.4, "y": 24.2, "omega": 0.004, "motion": "free",
+            "mass": 1.0, "inertia": 2000.0, "dof_mask": 4}
+    p = wl.periodic_box(48, 48, tau=0.7, eta=1e-3, body=body)
+    sim = oracle.OracleSim(p)
+    sim.init_equilibrium()
+    c, _, _, _ = oracle.constants()
+    X, Y = np.meshgrid(np.arange(48.0), np.arange(48.0))
+
+    def ang(f):
+        jx = np.tensordot(c[:, 0], f, axes=1)
+        jy = np.tensordot(c[:, 1], f, axes=1)
+        return np.sum((X - body["x"]) * jy - (Y - body["y"]) * jx)
+
+    L_prev = ang(sim.populations())
+    w_prev = sim.body_state()[1][2]
+    for n in range(12):
+        sim.step(1)
+        rec = sim.history(n, 1)[0]
+        L = ang(sim.populations())
+        assert abs((L - L_prev) + rec[14]) < 1e-13
+        w = sim.body_state()[1][2]
+        assert abs(body["inertia"] * (w - w_prev) - rec[3]) < 1e-13
+        L_prev, w_prev = L, w
+
+
+def test_light_free_body_stays_bounded():
+    # Explicit coupling with the momentum-exchange force keeps a free disk of
+    # density ratio 1.4 stable (the populations stay positive).
+    body = {"radius": 4.5, "x": 14.3, "y": 12.6, "vx": 0.01, "vy": -0.005,
+            "motion": "free", "mass": 90.0, "inertia": 900.0, "dof_mask": 7}
+    p = wl.periodic_box(30, 26, tau=0.65, eta=1e-3, body=body)
+    sim = oracle.OracleSim(p)
+    sim.init_equilibrium()
+    sim.step(400)
+    assert sim.populations().min() > 0.0
+
+
+def _taylor_green_nu(n_grid, tau=0.8, U=0.01, t0=10, t1=110):
+    p = wl.periodic_box(n_grid, n_grid, tau=tau)
+    k = 2 * math.pi / n_grid
+    X, Y = np.meshgrid(np.arange(n_grid, dtype=float), np.arange(n_grid, dtype=float))
+    ux = -U * np.cos(k * X) * np.sin(k * Y)
+    uy = U * np.sin(k * X) * np.cos(k * Y)
+    rho = 1.0 - 3.0 * U * U / 4.0 * (np.cos(2 * k * X) + np.cos(2 * k * Y))
+    sim = oracle.OracleSim(p)
+    sim.init_equilibrium(rho, ux, uy)
+    mode = -np.cos(k * X) * np.sin(k * Y)
+
+    def amp():
+        _, fx, _ = sim.fields()
+        return np.sum(fx * mode) / np.sum(mode * mode)
+
+    sim.step(t0)
+    a0 = amp()
+    sim.step(t1 - t0)
+    a1 = amp()
+    return -math.log(a1 / a0) / (2 * k * k * (t1 - t0))
+
+
+def test_taylor_green_viscosity_second_order():
+    # Decay rate of the Taylor-Green vortex gives nu = c_s^2 (tau - 1/2)
+    # (Eq. 6) with an error that falls at second order in the resolution.
+    tau = 0.8
+    nu = (tau - 0.5) / 3.0
+    e32 = abs(_taylor_green_nu(32, tau) / nu - 1)
+    e64 = abs(_taylor_green_nu(64, tau) / nu - 1)
+    assert e64 < 2e-3
+    assert e32 / e64 > 3.0
+
+
+def test_poiseuille_bounce_back_exact():
+    # Body-force-driven channel with half-way bounce-back walls: with
+    # (1/s_nu - 1/2)(1/s_q - 1/2) = 3/16 the steady profile is the exact
+    # parabola u(y) = g/(2 nu) (y + 1/2)(H - 1/2 - y), H = ny.
+    tau = 0.8
+    nu = (tau - 0.5) / 3.0
+    sq = 1.0 / (0.5 + (3.0 / 16.0) / (tau - 0.5))
+    rates = [1 / tau, 1.1, 1.25, 1 / tau, sq, 1 / tau, sq, 1 / tau, 1 / tau]
+    ny, g = 12, 1e-6
+    p = wl.periodic_box(3, ny, rates=rates, g_fluid=(g, 0.0))
+    p["bc"]["south"] = {"kind": "noslip", "u": (0.0, 0.0)}
+    p["bc"]["north"] = {"kind": "noslip", "u": (0.0, 0.0)}
+    sim = oracle.OracleSim(p)
+    sim.init_equilibrium()
+    sim.step(12000)
+    _, ux, uy = sim.fields()
+    y = np.arange(ny, dtype=float)
+    exact = g / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    assert np.max(np.abs(ux[:, 1] - exact)) < 1e-9 * np.max(exact)
+    assert np.max(np.abs(uy)) < 1e-15
+
+
+def test_rk4_free_fall_is_exact():
+    body = {"radius": 1.0, "x": 0, "y": 0, "motion": "free", "mass": 3.0, "inertia": 5.0,
+            "f_ext": (0.2, -0.5, 0.1), "dof_mask": 7}
+    q = np.array([1.0, 2.0, 0.3])
+    v = np.array([0.1, -0.2, 0.05])
+    F = np.array([0.4, 0.1, -0.2])
+    q1, v1 = oracle.body_advance(body, 0, 0.0, F, q, v)
+    acc = (F + np.array(body["f_ext"])) / np.array([3.0, 3.0, 5.0])
+    assert np.allclose(v1, v + acc, atol=1e-15)
+    assert np.allclose(q1, q + v + 0.5 * acc, atol=1e-15)
+
+
+def test_rk4_spring_local_error_fifth_order():
+    # Undamped spring, one RK4 step of size h = 1: in the dimensionless step
+    # w h the local error is O((w h)^5) against the exact solution (initial
+    # velocity scaled with w so that both solution terms keep their size),
+    # with the leading coefficient v0/w * (w h)^5 / 120 of the RK4 series.
+    errs = []
+    for wn in (0.1, 0.05):
+        m = 2.0
+        k = m * wn * wn
+        body = {"radius": 1, "x": 0, "y": 0, "motion": "free", "mass": m, "inertia": 1.0,
+                "stiff": (0.0, k, 0.0), "q0": (0.0, 1.0, 0.0), "dof_mask": 2}
+        q = np.array([0.0, 1.3, 0.0])
+        v = np.array([0.0, 0.2 * wn, 0.0])
+        F = np.zeros(3)
+        q1, v1 = oracle.body_advance(body, 0, 0.0, F, q, v)
+        exact = 1.0 + 0.3 * math.cos(wn) + v[1] / wn * math.sin(wn)
+        err = q1[1] - exact
+        lead = -0.2 * wn ** 5 / 120.0
+        assert abs(err - lead) < 0.2 * abs(lead)
+        errs.append(abs(err))
+        assert q1[0] == q[0] and q1[2] == q[2]
+    assert errs[0] / errs[1] > 2 ** 5 * 0.8
+
+
+def test_imposed_motion_closed_form():
+    body = {"radius": 3.0, "x": 10.0, "y": 12.0, "motion": "imposed", "axis": 1,
+            "amp": 2.0, "freq": 0.01, "phase": 0.4}
+    p = wl.periodic_box(24, 24, body=body)
+    sim = oracle.OracleSim(p)
+    sim.init_equilibrium()
+    sim.step(7)
+    q, v = sim.body_state()
+    yc = 12.0 - 2.0 * math.sin(0.4)
+    assert abs(q[1] - (yc + 2.0 * math.sin(2 * math.pi * 0.01 * 7 + 0.4))) < 1e-14
+    assert abs(v[1] - 2 * math.pi * 0.01 * 2.0 * math.cos(2 * math.pi * 0.01 * 7 + 0.4)) < 1e-15
+    h = sim.history()
+    assert abs(h[0, 7] - 12.0) < 1e-14  # the record holds the pose used by step 0

@@ -1,0 +1,260 @@
+"""Seeded synthetic workloads shared by the tests, the benchmark and the oracle.
+
+This module only *describes problems*: lattice sizes, relaxation rates,
+boundary kinds and wall velocities, body geometry and motion parameters, and
+seeded random initial data.  It holds no step of the time-stepping method;
+the oracle and the CUDA path each turn these plain dicts into their own
+structures.  Parameter derivations (viscosity from the Reynolds number, the
+relaxation time from Eq. 6, gravity from the Happel settling relation of
+Eqs. 33-35, the spring stiffness from the reduced velocity) are input
+preparation, done here once so that both sides receive identical numbers.
+
+A problem dict has the keys
+    nx, ny            lattice size (nodes), node (i, j) at x = i, y = j
+    s                 9 relaxation rates, diagonal of S (Eq. 16)
+    eta               penalization factor (Eq. 2)
+    rho0              reference density (1.0)
+    g_fluid           uniform body acceleration of the fluid (gx, gy)
+    bc                {west|east|south|north: {kind, u, ux_profile, uy_profile}}
+                      kind in periodic / noslip / velocity / zerograd
+    body              None or {radius, x, y, theta, vx, vy, omega, motion,
+                      axis, amp, freq, phase, mass, inertia, damp, stiff, q0,
+                      f_ext, dof_mask, u_ref, d_ref}
+    init              {"rho": scalar, "u": (ux, uy)} uniform initial state
+    steps             number of time steps of the full workload
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+Q = 9
+RHO0 = 1.0
+
+
+def tau_from_nu(nu: float) -> float:
+    """Relaxation time for a lattice viscosity (Eq. 6, c_s^2 = 1/3, dt = 1)."""
+    return 3.0 * nu + 0.5
+
+
+def paper_rates(tau: float) -> list:
+    """Relaxation rates chosen in Sec. 3 (Eq. 28)."""
+    st = 1.0 / tau
+    return [st, 1.1, 1.25, st, 1.8, st, 1.8, st, st]
+
+
+def _bc(kind, u=(0.0, 0.0), ux_profile=None, uy_profile=None):
+    d = {"kind": kind, "u": (float(u[0]), float(u[1]))}
+    if ux_profile is not None:
+        d["ux_profile"] = np.asarray(ux_profile, dtype=np.float64)
+    if uy_profile is not None:
+        d["uy_profile"] = np.asarray(uy_profile, dtype=np.float64)
+    return d
+
+
+def parabolic_profile(ny: int, u_max: float) -> np.ndarray:
+    """Poiseuille inlet profile vanishing at the half-way walls y=-1/2, ny-1/2."""
+    j = np.arange(ny, dtype=np.float64)
+    return 4.0 * u_max * (j + 0.5) * (ny - 0.5 - j) / (ny * ny)
+
+
+def disk_mass(radius: float, density_ratio: float) -> tuple:
+    """Mass and moment of inertia per unit depth of a uniform disk."""
+    m = density_ratio * RHO0 * math.pi * radius * radius
+    return m, 0.5 * m * radius * radius
+
+
+# ---- the five workloads ----------------------------------------------------
+
+def channel_fixed_disk(nx=256, ny=128, diameter=20.0, center=(64.0, 64.0),
+                       u_max=0.05, re=100.0, eta=1e-3, steps=2000) -> dict:
+    """Plain FP64 workload: parabolic channel flow past a fixed disk."""
+    nu = u_max * diameter / re
+    tau = tau_from_nu(nu)
+    return {
+        "name": f"channel_fixed_disk_{nx}x{ny}",
+        "nx": nx, "ny": ny, "s": paper_rates(tau), "eta": eta, "rho0": RHO0,
+        "g_fluid": (0.0, 0.0),
+        "bc": {"west": _bc("velocity", ux_profile=parabolic_profile(ny, u_max)),
+               "east": _bc("zerograd"), "south": _bc("noslip"), "north": _bc("noslip")},
+        "body": {"radius": diameter / 2, "x": center[0], "y": center[1],
+                 "motion": "fixed", "u_ref": u_max, "d_ref": diameter},
+        "init": {"rho": RHO0, "u": (0.0, 0.0)},
+        "steps": steps,
+    }
+
+
+# Strouhal number used to place the imposed-oscillation frequency at
+# 0.8 x the shedding frequency of the fixed disk (a stated estimate).
+STROUHAL = 0.2
+
+
+def oscillating_disk(nx=2048, ny=1024, diameter=40.0, x_c=400.0, u0=0.04,
+                     re=100.0, eta=1e-3, amp_over_d=0.2, f_over_st=0.8,
+                     steps=100_000) -> dict:
+    """Imposed transverse oscillation y_c(t) = y0 + A sin(2 pi f t)."""
+    nu = u0 * diameter / re
+    tau = tau_from_nu(nu)
+    f_st = STROUHAL * u0 / diameter
+    return {
+        "name": f"oscillating_disk_{nx}x{ny}",
+        "nx": nx, "ny": ny, "s": paper_rates(tau), "eta": eta, "rho0": RHO0,
+        "g_fluid": (0.0, 0.0),
+        "bc": {"west": _bc("velocity", u=(u0, 0.0)), "east": _bc("zerograd"),
+               "south": _bc("noslip"), "north": _bc("noslip")},
+        "body": {"radius": diameter / 2, "x": x_c, "y": ny / 2.0,
+                 "motion": "imposed", "axis": 1, "amp": amp_over_d * diameter,
+                 "freq": f_over_st * f_st, "phase": 0.0,
+                 "u_ref": u0, "d_ref": diameter},
+        "init": {"rho": RHO0, "u": (u0, 0.0)},
+        "steps": steps,
+    }
+
+
+def happel_kappa(h_tilde: float) -> float:
+    """Confinement factor of Eq. (34)."""
+    h = h_tilde
+    return 1.0 / (math.log(h) - 0.9157 + 1.7244 * h**-2 - 1.7302 * h**-4
+                  + 2.4056 * h**-6 - 4.5913 * h**-8)
+
+
+def sedimenting_disk(nx=1024, ny=4096, diameter=32.0, density_ratio=1.5,
+                     re_terminal=5.0, tau=0.8, eta=1e-3, offset=1.0,
+                     steps=200_000) -> dict:
+    """Free disk settling in a closed box (translation + rotation)."""
+    nu = (tau - 0.5) / 3.0
+    mu = RHO0 * nu
+    v_s = re_terminal * nu / diameter
+    kappa = happel_kappa(nx / diameter)
+    # Eqs. (33)/(35) with the gravity factor restored
+    g = 16.0 * kappa * mu * v_s / (diameter**2 * (density_ratio - 1.0) * RHO0)
+    radius = diameter / 2
+    m, inertia = disk_mass(radius, density_ratio)
+    x0 = (nx - 1) / 2.0 + offset
+    y0 = ny - 3.0 * diameter
+    # weight and buoyancy of Eq. (31), gravity along -y
+    fy = -m * (1.0 - 1.0 / density_ratio) * g
+    return {
+        "name": f"sedimenting_disk_{nx}x{ny}",
+        "nx": nx, "ny": ny, "s": paper_rates(tau), "eta": eta, "rho0": RHO0,
+        "g_fluid": (0.0, 0.0),
+        "bc": {s: _bc("noslip") for s in ("west", "east", "south", "north")},
+        "body": {"radius": radius, "x": x0, "y": y0, "motion": "free",
+                 "mass": m, "inertia": inertia, "f_ext": (0.0, fy, 0.0),
+                 "dof_mask": 7, "u_ref": v_s, "d_ref": diameter},
+        "init": {"rho": RHO0, "u": (0.0, 0.0)},
+        "steps": steps, "gravity": g,
+    }
+
+
+def viv_disk(ny=256, u_star=5.0, mass_ratio=10.0, u0=0.04, re=100.0,
+             eta=1e-3, steps=50_000) -> dict:
+    """Spring-mounted disk free in y (zero damping), Eq. (37)."""
+    nx = 2 * ny
+    diameter = ny / 8.0
+    radius = diameter / 2
+    nu = u0 * diameter / re
+    tau = tau_from_nu(nu)
+    m, inertia = disk_mass(radius, mass_ratio)
+    f_n = u0 / (u_star * diameter)
+    k = m * (2.0 * math.pi * f_n) ** 2
+    y0 = ny / 2.0
+    return {
+        "name": f"viv_disk_{nx}x{ny}_U{u_star:.3f}",
+        "nx": nx, "ny": ny, "s": paper_rates(tau), "eta": eta, "rho0": RHO0,
+        "g_fluid": (0.0, 0.0),
+        "bc": {"west": _bc("velocity", u=(u0, 0.0)), "east": _bc("zerograd"),
+               "south": _bc("noslip"), "north": _bc("noslip")},
+        "body": {"radius": radius, "x": 0.2 * nx, "y": y0, "motion": "free",
+                 "mass": m, "inertia": inertia, "stiff": (0.0, k, 0.0),
+                 "q0": (0.0, y0, 0.0), "dof_mask": 2, "u_ref": u0, "d_ref": diameter},
+        "init": {"rho": RHO0, "u": (u0, 0.0)},
+        "steps": steps,
+    }
+
+
+def viv_sweep(n=64, steps=50_000) -> list:
+    """64 spring-mounted disks on uneven grids, reduced velocity in [3, 12]."""
+    rng = np.random.default_rng(0)
+    sizes = [256 + 16 * int(round(48 * i / (n - 1))) for i in range(n)]
+    u_stars = np.linspace(3.0, 12.0, n)
+    perm = rng.permutation(n)
+    return [viv_disk(ny=sizes[i], u_star=float(u_stars[perm[i]]), steps=steps)
+            for i in range(n)]
+
+
+def adjoint_disk(nx=1024, ny=512, diameter=32.0, u0=0.04, re=100.0, eta=1e-3,
+                 amp_over_d=0.2, steps=20_000) -> dict:
+    """Imposed oscillation used for the gradient workload."""
+    p = oscillating_disk(nx=nx, ny=ny, diameter=diameter, x_c=0.2 * nx, u0=u0,
+                         re=re, eta=eta, amp_over_d=amp_over_d, steps=steps)
+    p["name"] = f"adjoint_disk_{nx}x{ny}"
+    return p
+
+
+# ---- small cases for parity and pinning tests ------------------------------
+
+def periodic_box(nx, ny, tau=0.8, eta=1e-3, body=None, g_fluid=(0.0, 0.0),
+                 rates=None) -> dict:
+    return {
+        "name": f"periodic_{nx}x{ny}", "nx": nx, "ny": ny,
+        "s": rates if rates is not None else paper_rates(tau), "eta": eta,
+        "rho0": RHO0, "g_fluid": g_fluid,
+        "bc": {s: _bc("periodic") for s in ("west", "east", "south", "north")},
+        "body": body, "init": {"rho": RHO0, "u": (0.0, 0.0)}, "steps": 0,
+    }
+
+
+def random_rates(seed: int) -> list:
+    rng = np.random.default_rng(seed)
+    return list(rng.uniform(0.6, 1.9, size=Q))
+
+
+def random_populations(nx: int, ny: int, seed: int, amp: float = 0.05,
+                       u_amp: float = 0.05) -> np.ndarray:
+    """Near-equilibrium random populations, layout [9][ny][nx]."""
+    rng = np.random.default_rng(seed)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    c = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1],
+                  [1, 1], [-1, 1], [-1, -1], [1, -1]], dtype=np.float64)
+    ux = rng.uniform(-u_amp, u_amp, size=(ny, nx))
+    uy = rng.uniform(-u_amp, u_amp, size=(ny, nx))
+    rho = 1.0 + rng.uniform(-0.02, 0.02, size=(ny, nx))
+    f = np.empty((Q, ny, nx))
+    for a in range(Q):
+        cu = c[a, 0] * ux + c[a, 1] * uy
+        f[a] = w[a] * rho * (1.0 + 3.0 * cu)
+    f *= 1.0 + amp * rng.uniform(-1.0, 1.0, size=f.shape)
+    return f
+
+
+def random_wall_profile(n: int, seed: int, amp: float = 0.05) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-amp, amp, size=n)
+
+
+def mixed_bc_box(nx, ny, seed=0, west="velocity", east="zerograd",
+                 south="noslip", north="velocity", tau=0.7, eta=1e-3,
+                 body=None, rates=None) -> dict:
+    """Small box exercising every boundary rule with random wall velocities."""
+    def side(kind, n, k):
+        if kind == "velocity":
+            return _bc("velocity", ux_profile=random_wall_profile(n, seed + 10 * k),
+                       uy_profile=random_wall_profile(n, seed + 10 * k + 1, 0.02))
+        return _bc(kind)
+    return {
+        "name": f"mixed_{nx}x{ny}", "nx": nx, "ny": ny,
+        "s": rates if rates is not None else paper_rates(tau), "eta": eta,
+        "rho0": RHO0, "g_fluid": (0.0, 0.0),
+        "bc": {"west": side(west, ny, 1), "east": side(east, ny, 2),
+               "south": side(south, nx, 3), "north": side(north, nx, 4)},
+        "body": body, "init": {"rho": RHO0, "u": (0.0, 0.0)}, "steps": 0,
+    }
+
+
+def scaled(problem: dict, **changes) -> dict:
+    """Copy of a problem with top-level keys replaced."""
+    p = dict(problem)
+    p.update(changes)
+    return p
