@@ -1,0 +1,373 @@
+"""Benchmark of the VP-LBM hot path: MLUPS and fraction of the HBM roofline.
+
+One bench step is one time step (Algorithm 1: stream, collide with
+penalization, force/torque reduction, body update) over the whole lattice of
+the imposed-oscillation workload (2048 x 1024 D2Q9, disk D = 40, FP32
+deviation storage).  The device-timed value has the populations resident in
+HBM; the e2e value goes through the C ABI with host buffers (initial fields
+uploaded from pinned memory, force history and final fields read back).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own replica (the single-lattice
+path has no exchange step): value = node updates of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+METRIC = "D2Q9 VP-MRT MLUPS & % HBM roofline; FP32/batched/adjoint vs FP64 plain, same GPU"
+UNIT = "MLUPS"
+BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36}   # 9 loads + 9 stores of one population
+KERNEL_NAME = {"f64": "vp_mrt_step<0>", "f32": "vp_mrt_step<1>", "f16": "vp_mrt_step<2>"}
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "vp_mrt_step_f32_oscillating_2048x1024.md")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1905_05110_gb300", "csrc", "step_kernels.cu")
+
+
+def workload(name: str) -> dict:
+    if name == "oscillating_2048x1024":
+        return wl.oscillating_disk()
+    if name == "sedimenting_1024x4096":
+        return wl.sedimenting_disk()
+    if name == "channel_256x128":
+        return wl.channel_fixed_disk()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    with open(KERNEL_SOURCE, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def profiled_traffic(nodes: int):
+    """DRAM bytes per launch from the committed ncu summary, if still valid."""
+    try:
+        text = open(PROFILE_TRAFFIC).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.e+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:]))
+                except ValueError:
+                    continue
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in loaded:
+            for name, flag in zip(names, r[3][1:5]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(loaded),
+                "power_w_max": max(r[2] for r in rows)}
+
+
+def time_device(sim, steps, stream, torch):
+    """CUDA-event time of `steps` time steps on the simulation's stream."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def cpu_baseline(problem: dict, budget_s: float = 12.0):
+    """The FP64 oracle, single-threaded, on time steps of the same lattice."""
+    import oracle
+    sim = oracle.OracleSim(problem, hist_cap=64)
+    u = problem["init"]["u"]
+    shape = (problem["ny"], problem["nx"])
+    sim.init_equilibrium(np.ones(shape), np.full(shape, u[0]), np.full(shape, u[1]))
+    t0 = time.perf_counter()
+    sim.step(1)
+    one = time.perf_counter() - t0
+    extra = max(0, min(20, int(budget_s / max(one, 1e-3)) - 1))
+    t0 = time.perf_counter()
+    sim.step(extra)
+    dt = time.perf_counter() - t0
+    steps = extra if extra > 0 else 1
+    if extra == 0:
+        dt = one
+    nodes = problem["nx"] * problem["ny"]
+    return {"value": nodes * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} FP64 time steps of the full {problem['nx']}x{problem['ny']} lattice "
+                      f"(after 1 untimed), plain C, one thread"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    p = workload(args.workload)
+    import oracle
+    nodes = p["nx"] * p["ny"]
+    per_step_est = nodes * 0.5e-6
+    sample = p
+    if (args.steps + args.warmup) * per_step_est > 150:
+        # bounded sample: a strip of the same lattice (same physics per node)
+        ny = max(16, int(p["ny"] * 150 / ((args.steps + args.warmup) * per_step_est)))
+        sample = dict(p, ny=ny, body=dict(p["body"], y=ny / 2.0))
+    sim = oracle.OracleSim(sample, hist_cap=max(16, args.steps + args.warmup))
+    u = sample["init"]["u"]
+    shape = (sample["ny"], sample["nx"])
+    sim.init_equilibrium(np.ones(shape), np.full(shape, u[0]), np.full(shape, u[1]))
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = sample["nx"] * sample["ny"] * args.steps / dt / 1e6
+    desc = (f"{args.steps} FP64 oracle time steps of a {sample['nx']}x{sample['ny']} lattice "
+            f"({'full workload' if sample is p else 'strip of the workload'}), one thread")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": p["name"], "nx": p["nx"], "ny": p["ny"]},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1905_05110_gb300 as vp
+    from paper_1905_05110_gb300 import build as vbuild
+
+    if rank == 0 or not os.path.exists(vbuild.LIB):
+        vbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    p = workload(args.workload)
+    nodes = p["nx"] * p["ny"]
+    prec = args.precision
+
+    sim = vp.Simulation(p, precision=prec, history_capacity=max(1024, args.steps + args.warmup + 64),
+                        stream=stream)
+    sim.init_from_problem()
+    if not args.no_autotune:
+        sim.autotune(20)
+    bx, by = sim.launch()
+    sim.step(args.warmup)
+    sim.sync()
+
+    launches0 = sim.launches
+    with ClockSampler(local_rank) as clocks:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        dt = time_device(sim, args.steps, stream, torch)
+        torch.cuda.synchronize()
+    launches = sim.launches - launches0
+    sim.sync()
+    if world > 1:
+        t = torch.tensor([dt], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dt = float(t.item())
+    value = world * nodes * args.steps / dt / 1e6
+    clock = clocks.summary()
+
+    # roofline of the fused step kernel (the only kernel in the timed region)
+    peak, peak_kind = measured_peak()
+    per_launch = dt / args.steps
+    achieved = BYTES_PER_NODE[prec] * nodes / per_launch / 1e9
+    traffic = profiled_traffic(nodes) if prec == "f32" and args.workload == "oscillating_2048x1024" else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                "kernel": KERNEL_NAME[prec], "algorithmic_bytes_per_launch": BYTES_PER_NODE[prec] * nodes}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(sim, p, args.steps, torch)
+
+    # the other precisions on the same GPU, for the FP32 / FP16 vs FP64 comparison
+    compare = {}
+    if not args.no_compare and rank == 0:
+        for other in ("f64", "f16"):
+            if other == prec:
+                continue
+            s2 = vp.Simulation(p, precision=other, history_capacity=4096, stream=stream)
+            s2.init_from_problem()
+            if not args.no_autotune:
+                s2.autotune(8)
+            s2.step(50)
+            s2.sync()
+            k = max(200, min(args.steps, 2000 if other == "f64" else args.steps))
+            t2 = time_device(s2, k, stream, torch)
+            s2.sync()
+            compare[other] = {"mlups": nodes * k / t2 / 1e6, "steps": k,
+                              "gbs_algorithmic": BYTES_PER_NODE[other] * nodes * k / t2 / 1e9,
+                              "launch": list(s2.launch())}
+            s2.close()
+        if "f64" in compare:
+            compare["speedup_vs_f64"] = (nodes * args.steps / dt / 1e6) / compare["f64"]["mlups"]
+
+    base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        base = cpu_baseline(p)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec != "f64" else "f64",
+                "data": "synthetic",
+                "config": {"workload": p["name"], "nx": p["nx"], "ny": p["ny"],
+                           "storage": {"f32": "f32 deviation", "f16": "f16 deviation", "f64": "f64"}[prec],
+                           "launch": [bx, by], "parallelism": f"replicas x{world}",
+                           "l2": "not flushed: populations 151 MB read+write per step > 129 MB L2"},
+                "roofline": roofline, "cpu_baseline": base, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clock, "compare": compare}
+        print(json.dumps(line), flush=True)
+    sim.close()
+
+
+def run_e2e(sim, p, steps, torch):
+    """Same metric through the public API with host buffers, copies timed."""
+    import paper_1905_05110_gb300 as vp
+    ny, nx = p["ny"], p["nx"]
+    u = p["init"]["u"]
+    pinned = [torch.empty((ny, nx), dtype=torch.float64, pin_memory=True) for _ in range(6)]
+    pinned[0].fill_(p["init"]["rho"])
+    pinned[1].fill_(u[0])
+    pinned[2].fill_(u[1])
+    hist = (vp.Record * steps)()
+    arrs = [t.numpy() for t in pinned]
+
+    def once():
+        vp.vplbm_init_equilibrium(sim.ctx, arrs[0], arrs[1], arrs[2])
+        vp.vplbm_step(sim.ctx, steps)
+        lib = vp.load_library()
+        st = lib.vplbm_get_history(sim.ctx, 0, steps, hist)
+        if st != 0:
+            raise vp.VplbmError(st, vp.vplbm_last_error())
+        vp.vplbm_get_fields(sim.ctx, arrs[3], arrs[4], arrs[5])
+
+    once()   # warm-up of the same path
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    once()
+    dt = time.perf_counter() - t0
+    h2d = 3 * nx * ny * 8
+    d2h = 3 * nx * ny * 8 + steps * 128
+    return {"value": nx * ny * steps / dt / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "what": "init from pinned host fields + steps + history and fields to pinned host"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40000)
+    ap.add_argument("--warmup", type=int, default=1000)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="oscillating_2048x1024")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f16", "f64"])
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * vplbm.h - C ABI of the GB300 volume-penalization lattice Boltzmann library.
+ *
+ * The library advances a D2Q9 multiple-relaxation-time lattice Boltzmann
+ * fluid in which a rigid disk is represented by a characteristic function
+ * chi and enters the fluid as a penalization force (Liberge & Beghein,
+ * "Fluid Structure Interaction modelling using Lattice Boltzmann and Volume
+ * Penalization method", Sec. 2).  One time step is Algorithm 1 of Sec. 2.3:
+ * collide and stream (Eqs. 17-18), macroscopic moments with the penalized
+ * velocity (Eqs. 19-22), the force and torque on the body (Eqs. 25-27), the
+ * rigid-body update (Eqs. 23-24, fourth-order Runge-Kutta).
+ *
+ * Conventions shared by every entry point:
+ *  - Lattice units: dx = dt = 1, c_s^2 = 1/3.  Node (i, j), 0 <= i < nx,
+ *    0 <= j < ny, sits at x = i, y = j.  Walls are half-way: x = -1/2,
+ *    x = nx - 1/2, y = -1/2, y = ny - 1/2.
+ *  - Host arrays of a field are row-major [ny][nx] (i fastest); population
+ *    arrays are [9][ny][nx] with the velocity order of Eq. (10):
+ *    c0 = (0,0), c1..c4 = (1,0),(0,1),(-1,0),(0,-1),
+ *    c5..c8 = (1,1),(-1,1),(-1,-1),(1,-1).
+ *  - The state after n steps is the post-collision population field of
+ *    step n - 1 (for n = 0 the field set by vplbm_init_equilibrium or
+ *    vplbm_set_populations).  Populations cross the ABI as full f in FP64,
+ *    whatever the storage precision.
+ *  - Every pointer argument is a HOST pointer unless its name ends in _dev.
+ *    Host inputs are copied before the call returns; the caller keeps
+ *    ownership of everything it passes.
+ *  - Work is queued on the stream given at creation.  Calls that return
+ *    data to the host synchronize that stream.  Errors detected on the
+ *    device (non-finite density) are latched and returned by the next
+ *    vplbm_sync or host read.
+ *  - No call aborts or throws: every failure returns a status, and
+ *    vplbm_last_error() gives a message (per calling thread).
+ */
+#ifndef VPLBM_H
+#define VPLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VPLBM_OK = 0,
+    VPLBM_EINVAL = 1,        /* invalid argument or descriptor */
+    VPLBM_ENOMEM = 2,        /* device or host allocation failed */
+    VPLBM_ECUDA = 3,         /* a CUDA runtime call failed */
+    VPLBM_ENONFINITE = 4,    /* a density became non-positive or non-finite */
+    VPLBM_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    VPLBM_EUNSUPPORTED = 6,  /* valid request this build does not provide */
+    VPLBM_ERANGE = 7,        /* history record no longer (or not yet) stored */
+    VPLBM_EIO = 8            /* file read or write failed */
+} vplbm_status;
+
+/* Storage precision of the populations.  Arithmetic is FP64 for VPLBM_F64
+ * and FP32 otherwise; force/torque sums and the body update are always FP64.
+ * The _DEV variants store f_a - w_a rho0 (deviation from rest). */
+typedef enum { VPLBM_F64 = 0, VPLBM_F32_DEV = 1, VPLBM_F16_DEV = 2 } vplbm_precision;
+
+/* Boundary kinds of one lattice edge (Sec. 3.1 / 3.2):
+ *  PERIODIC  wrap around (must be set on both opposite edges);
+ *  NOSLIP    half-way bounce-back, f_a(x) = f~_abar(x);
+ *  VELOCITY  half-way bounce-back of a moving wall,
+ *            f_a(x) = f~_abar(x) + 6 w_a rho0 (c_a . u_w);
+ *  ZEROGRAD  west/east only: f_a(x) = f~_a(i, j - c_ay) from the edge column.
+ * When the source node of a pull lies outside in y, the south/north rule
+ * applies, otherwise the west/east rule. */
+typedef enum {
+    VPLBM_BC_PERIODIC = 0, VPLBM_BC_NOSLIP = 1, VPLBM_BC_VELOCITY = 2, VPLBM_BC_ZEROGRAD = 3
+} vplbm_bc_kind;
+
+enum { VPLBM_WEST = 0, VPLBM_EAST = 1, VPLBM_SOUTH = 2, VPLBM_NORTH = 3 };
+
+typedef struct {
+    int kind;                 /* vplbm_bc_kind */
+    double ux, uy;            /* uniform wall velocity (VELOCITY) */
+    const double *ux_profile; /* optional per-node wall velocity along the */
+    const double *uy_profile; /* edge (ny values west/east, nx south/north) */
+} vplbm_bc;
+
+/* Lattice and fluid.  s: diagonal of S (Eq. 16) in the moment order of
+ * Eq. (15), each in (0, 2); eta > 0: penalization factor (Eq. 2);
+ * rho0 > 0: reference density; (gx, gy): uniform body acceleration of the
+ * fluid, added to the penalization force in the forcing term. */
+typedef struct {
+    int nx, ny;               /* >= 3 each */
+    double s[9];
+    double eta;
+    double rho0;
+    double gx, gy;
+    vplbm_bc bc[4];           /* indexed by VPLBM_WEST .. VPLBM_NORTH */
+    int precision;            /* vplbm_precision */
+} vplbm_lattice_desc;
+
+typedef enum {
+    VPLBM_MOTION_FIXED = 0,   /* pose and velocity held at their initial values */
+    VPLBM_MOTION_IMPOSED = 1, /* q_axis(t) = q_c + amp sin(2 pi freq t + phase) */
+    VPLBM_MOTION_FREE = 2     /* Eqs. (23)-(24) for the DOFs in dof_mask, RK4 */
+} vplbm_motion;
+
+/* Rigid disk.  chi(x) = 1 iff (i - x_G)^2 + (j - y_G)^2 <= radius^2 (FP64,
+ * no fused multiply-add).  The rigid velocity at a node is
+ * u_s = (vx - omega (y - y_G), vy + omega (x - x_G)).
+ * Imposed motion: q_c is chosen so that q_axis(0) equals the initial pose.
+ * Free motion: m q'' + damp q' + stiff (q - q0) = F_h + f_ext per DOF
+ * (x, y with mass, theta with inertia); F_h is held over the step. */
+typedef struct {
+    double radius;
+    double x, y, theta, vx, vy, omega;
+    int motion;               /* vplbm_motion */
+    int axis;                 /* imposed coordinate: 0 x, 1 y, 2 theta */
+    double amp, freq, phase;
+    double mass, inertia;
+    double damp[3], stiff[3], q0[3], f_ext[3];
+    unsigned dof_mask;        /* bit0 x, bit1 y, bit2 theta */
+    double u_ref, d_ref;      /* C_D = F_x / (rho0 d_ref u_ref^2 / 2), C_L alike */
+} vplbm_body_desc;
+
+/* One record per time step n.  (fx, fy, torque) is the momentum exchanged
+ * through the links between the solid nodes and the rest of the lattice
+ * during the streaming into step n (Eqs. 25-27 with u_Gamma = 0), the force
+ * that drives a free body; (fpen_x, fpen_y, tpen) is the reaction of the
+ * penalization force, sum over solid nodes of rho chi (u - u_s) / eta, and
+ * its torque about x_G.  Pose and velocity are those used by step n. */
+typedef struct {
+    double t, fx, fy, torque, cd, cl, x, y, theta, vx, vy, omega;
+    double fpen_x, fpen_y, tpen, n_solid;
+} vplbm_record;
+
+typedef struct vplbm_ctx vplbm_ctx;
+
+/* Device memory a context needs, for callers that allocate it themselves. */
+typedef struct {
+    size_t populations;   /* bytes of EACH of the two population buffers */
+    size_t body_state;    /* bytes of the body-state pair */
+    size_t partials;      /* bytes of the per-block reduction scratch */
+    size_t history;       /* bytes of the history ring */
+    size_t profiles;      /* bytes of the wall-velocity profiles */
+    size_t control;       /* bytes of the ticket / error words */
+} vplbm_buffer_sizes;
+
+typedef struct {
+    void *populations_dev[2];
+    void *body_state_dev;
+    void *partials_dev;
+    void *history_dev;
+    void *profiles_dev;
+    void *control_dev;
+} vplbm_buffers;
+
+/* Size of each device buffer for this lattice, body and history capacity.
+ * Every buffer must be 256-byte aligned. */
+vplbm_status vplbm_buffer_sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body,
+                                    long long history_capacity, vplbm_buffer_sizes *out);
+
+/* Create a simulation.  body may be NULL (no solid).  history_capacity
+ * (>= 1) records are kept in a ring.  cuda_stream is a cudaStream_t (NULL:
+ * the legacy default stream).  The library allocates its device memory.
+ * The populations are left at rest (rho0, u = 0). */
+vplbm_status vplbm_create(const vplbm_lattice_desc *lat, const vplbm_body_desc *body,
+                          long long history_capacity, void *cuda_stream, vplbm_ctx **out);
+
+/* Same, on device buffers owned by the caller (sizes from
+ * vplbm_buffer_sizes_for); the caller keeps them alive until destroy. */
+vplbm_status vplbm_create_with_buffers(const vplbm_lattice_desc *lat, const vplbm_body_desc *body,
+                                       long long history_capacity, void *cuda_stream,
+                                       const vplbm_buffers *buffers, vplbm_ctx **out);
+
+void vplbm_destroy(vplbm_ctx *ctx);
+
+/* State := equilibrium (Eq. 11) of the host fields rho, ux, uy ([ny][nx]);
+ * a NULL field means rho0 (for rho) or 0 (for a velocity).  Resets the
+ * step counter, the history and the body to its initial pose. */
+vplbm_status vplbm_init_equilibrium(vplbm_ctx *ctx, const double *rho, const double *ux,
+                                    const double *uy);
+
+/* State := the host populations f[9][ny][nx] (full f; rounded to the
+ * storage precision).  Resets step counter, history and body like init. */
+vplbm_status vplbm_set_populations(vplbm_ctx *ctx, const double *f);
+
+/* Queue nsteps >= 0 time steps on the context's stream (asynchronous). */
+vplbm_status vplbm_step(vplbm_ctx *ctx, long long nsteps);
+
+/* Wait for queued work; returns a latched device error if any. */
+vplbm_status vplbm_sync(vplbm_ctx *ctx);
+
+/* Current state, full f in FP64 [9][ny][nx] (host). */
+vplbm_status vplbm_get_populations(vplbm_ctx *ctx, double *f);
+
+/* rho, u_x, u_y of the current step (Eqs. 19-22, with chi of the current
+ * pose), host arrays [ny][nx]; any pointer may be NULL. */
+vplbm_status vplbm_get_fields(vplbm_ctx *ctx, double *rho, double *ux, double *uy);
+
+/* Same into device arrays (asynchronous, on the context's stream). */
+vplbm_status vplbm_get_fields_dev(vplbm_ctx *ctx, double *rho_dev, double *ux_dev, double *uy_dev);
+
+/* Records first .. first + count - 1; VPLBM_ERANGE if any of them is not
+ * yet written or already overwritten in the ring. */
+vplbm_status vplbm_get_history(vplbm_ctx *ctx, long long first, long long count, vplbm_record *dst);
+
+/* Pose (x, y, theta), velocity (vx, vy, omega) and step counter. */
+vplbm_status vplbm_get_body(vplbm_ctx *ctx, double q[3], double v[3], long long *step);
+
+/* Launch shape of the step kernel: block_x * block_y threads per block,
+ * block_x a multiple of 32, block_x * block_y in {128, 256, 512}. */
+vplbm_status vplbm_set_launch(vplbm_ctx *ctx, int block_x, int block_y);
+vplbm_status vplbm_get_launch(vplbm_ctx *ctx, int *block_x, int *block_y);
+
+/* Time every candidate launch shape on the current state (the state is
+ * saved and restored around the trials) and keep the fastest. */
+vplbm_status vplbm_autotune(vplbm_ctx *ctx, int steps_per_trial);
+
+/* Number of step-kernel launches made by vplbm_step since creation. */
+vplbm_status vplbm_get_launch_count(vplbm_ctx *ctx, long long *launches);
+
+/* Write / read a checkpoint: populations (storage precision), body state,
+ * step counter and history ring.  vplbm_load requires a context created
+ * with the same lattice size, precision and history capacity. */
+vplbm_status vplbm_save(vplbm_ctx *ctx, const char *path);
+vplbm_status vplbm_load(vplbm_ctx *ctx, const char *path);
+
+/* Message of the last failed call on this thread (never NULL). */
+const char *vplbm_last_error(void);
+
+/* Library version string. */
+const char *vplbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VPLBM_H */

@@ -1,0 +1,451 @@
+"""GB300-native volume-penalization lattice Boltzmann (VP-LBM) for rigid-body FSI.
+
+Thin Python binding of the C ABI declared in ``include/vplbm.h``.  Every
+function named ``vplbm_*`` here marshals its arguments and calls the entry
+point of the same name in ``libvplbm.so``; all of the time stepping runs in
+the library's CUDA kernels.  PyTorch is used only for device memory (the
+``Simulation`` class allocates the library's buffers as torch tensors) and for
+the CUDA stream handle.
+
+If the library has not been built, or no CUDA device is present, the calls
+raise: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "VplbmError", "load_library", "lattice_desc", "body_desc", "Simulation",
+    "vplbm_create", "vplbm_create_with_buffers", "vplbm_buffer_sizes_for", "vplbm_destroy",
+    "vplbm_init_equilibrium", "vplbm_set_populations", "vplbm_step", "vplbm_sync",
+    "vplbm_get_populations", "vplbm_get_fields", "vplbm_get_fields_dev", "vplbm_get_history",
+    "vplbm_get_body", "vplbm_set_launch", "vplbm_get_launch", "vplbm_autotune",
+    "vplbm_get_launch_count", "vplbm_save", "vplbm_load", "vplbm_last_error", "vplbm_version",
+    "EXPORTED_SYMBOLS", "RECORD_FIELDS",
+]
+
+Q = 9
+STATUS = {0: "VPLBM_OK", 1: "VPLBM_EINVAL", 2: "VPLBM_ENOMEM", 3: "VPLBM_ECUDA",
+          4: "VPLBM_ENONFINITE", 5: "VPLBM_ETIMEOUT", 6: "VPLBM_EUNSUPPORTED",
+          7: "VPLBM_ERANGE", 8: "VPLBM_EIO"}
+PRECISIONS = {"f64": 0, "f32": 1, "f16": 2}
+BC_KINDS = {"periodic": 0, "noslip": 1, "velocity": 2, "zerograd": 3}
+MOTIONS = {"fixed": 0, "imposed": 1, "free": 2}
+SIDES = ("west", "east", "south", "north")
+RECORD_FIELDS = ("t", "fx", "fy", "torque", "cd", "cl", "x", "y", "theta",
+                 "vx", "vy", "omega", "fpen_x", "fpen_y", "tpen", "n_solid")
+
+
+class VplbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+# ---- C structs (mirrors of include/vplbm.h) ----------------------------------
+
+class BC(C.Structure):
+    _fields_ = [("kind", C.c_int), ("ux", C.c_double), ("uy", C.c_double),
+                ("ux_profile", C.POINTER(C.c_double)), ("uy_profile", C.POINTER(C.c_double))]
+
+
+class LatticeDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("s", C.c_double * 9), ("eta", C.c_double),
+                ("rho0", C.c_double), ("gx", C.c_double), ("gy", C.c_double),
+                ("bc", BC * 4), ("precision", C.c_int)]
+
+
+class BodyDesc(C.Structure):
+    _fields_ = [("radius", C.c_double), ("x", C.c_double), ("y", C.c_double),
+                ("theta", C.c_double), ("vx", C.c_double), ("vy", C.c_double),
+                ("omega", C.c_double), ("motion", C.c_int), ("axis", C.c_int),
+                ("amp", C.c_double), ("freq", C.c_double), ("phase", C.c_double),
+                ("mass", C.c_double), ("inertia", C.c_double),
+                ("damp", C.c_double * 3), ("stiff", C.c_double * 3),
+                ("q0", C.c_double * 3), ("f_ext", C.c_double * 3),
+                ("dof_mask", C.c_uint), ("u_ref", C.c_double), ("d_ref", C.c_double)]
+
+
+class Record(C.Structure):
+    _fields_ = [(n, C.c_double) for n in RECORD_FIELDS]
+
+
+class BufferSizes(C.Structure):
+    _fields_ = [(n, C.c_size_t) for n in
+                ("populations", "body_state", "partials", "history", "profiles", "control")]
+
+
+class Buffers(C.Structure):
+    _fields_ = [("populations_dev", C.c_void_p * 2), ("body_state_dev", C.c_void_p),
+                ("partials_dev", C.c_void_p), ("history_dev", C.c_void_p),
+                ("profiles_dev", C.c_void_p), ("control_dev", C.c_void_p)]
+
+
+_D = C.POINTER(C.c_double)
+_CTX = C.c_void_p
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "vplbm_buffer_sizes_for": (C.c_int, [C.POINTER(LatticeDesc), C.POINTER(BodyDesc), C.c_longlong,
+                                         C.POINTER(BufferSizes)]),
+    "vplbm_create": (C.c_int, [C.POINTER(LatticeDesc), C.POINTER(BodyDesc), C.c_longlong, C.c_void_p,
+                               C.POINTER(_CTX)]),
+    "vplbm_create_with_buffers": (C.c_int, [C.POINTER(LatticeDesc), C.POINTER(BodyDesc), C.c_longlong,
+                                            C.c_void_p, C.POINTER(Buffers), C.POINTER(_CTX)]),
+    "vplbm_destroy": (None, [_CTX]),
+    "vplbm_init_equilibrium": (C.c_int, [_CTX, _D, _D, _D]),
+    "vplbm_set_populations": (C.c_int, [_CTX, _D]),
+    "vplbm_step": (C.c_int, [_CTX, C.c_longlong]),
+    "vplbm_sync": (C.c_int, [_CTX]),
+    "vplbm_get_populations": (C.c_int, [_CTX, _D]),
+    "vplbm_get_fields": (C.c_int, [_CTX, _D, _D, _D]),
+    "vplbm_get_fields_dev": (C.c_int, [_CTX, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vplbm_get_history": (C.c_int, [_CTX, C.c_longlong, C.c_longlong, C.POINTER(Record)]),
+    "vplbm_get_body": (C.c_int, [_CTX, _D, _D, C.POINTER(C.c_longlong)]),
+    "vplbm_set_launch": (C.c_int, [_CTX, C.c_int, C.c_int]),
+    "vplbm_get_launch": (C.c_int, [_CTX, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "vplbm_autotune": (C.c_int, [_CTX, C.c_int]),
+    "vplbm_get_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_longlong)]),
+    "vplbm_save": (C.c_int, [_CTX, C.c_char_p]),
+    "vplbm_load": (C.c_int, [_CTX, C.c_char_p]),
+    "vplbm_last_error": (C.c_char_p, []),
+    "vplbm_version": (C.c_char_p, []),
+}
+EXPORTED_SYMBOLS = tuple(_SIGS)
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = False):
+    """Load libvplbm.so (optionally building it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"{path} is not built; run __graft_entry__.build() or "
+                              "python -m paper_1905_05110_gb300.build")
+        _build.build()
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise VplbmError(status, load_library().vplbm_last_error().decode())
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _f64(a, shape=None):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        arr = arr.reshape(shape)
+    return arr
+
+
+# ---- descriptors from problem dicts -------------------------------------------
+
+def lattice_desc(problem: dict, precision: str = "f64", keep: list | None = None) -> LatticeDesc:
+    """C lattice descriptor from a problem dict; ``keep`` receives array refs."""
+    keep = keep if keep is not None else []
+    d = LatticeDesc()
+    d.nx, d.ny = int(problem["nx"]), int(problem["ny"])
+    for k in range(9):
+        d.s[k] = float(problem["s"][k])
+    d.eta = float(problem.get("eta", 1e-3))
+    d.rho0 = float(problem.get("rho0", 1.0))
+    g = problem.get("g_fluid", (0.0, 0.0))
+    d.gx, d.gy = float(g[0]), float(g[1])
+    for k, side in enumerate(SIDES):
+        bc = problem["bc"][side]
+        d.bc[k].kind = BC_KINDS[bc["kind"]]
+        u = bc.get("u", (0.0, 0.0))
+        d.bc[k].ux, d.bc[k].uy = float(u[0]), float(u[1])
+        for key, field in (("ux_profile", "ux_profile"), ("uy_profile", "uy_profile")):
+            prof = bc.get(key)
+            if prof is None:
+                setattr(d.bc[k], field, None)
+            else:
+                arr = _f64(prof)
+                keep.append(arr)
+                setattr(d.bc[k], field, _dptr(arr))
+    d.precision = PRECISIONS[precision]
+    return d
+
+
+def body_desc(body: dict | None) -> BodyDesc | None:
+    if not body:
+        return None
+    b = BodyDesc()
+    b.radius = float(body["radius"])
+    b.x, b.y = float(body["x"]), float(body["y"])
+    b.theta = float(body.get("theta", 0.0))
+    b.vx, b.vy = float(body.get("vx", 0.0)), float(body.get("vy", 0.0))
+    b.omega = float(body.get("omega", 0.0))
+    b.motion = MOTIONS[body.get("motion", "fixed")]
+    b.axis = int(body.get("axis", 1))
+    b.amp, b.freq = float(body.get("amp", 0.0)), float(body.get("freq", 0.0))
+    b.phase = float(body.get("phase", 0.0))
+    b.mass, b.inertia = float(body.get("mass", 1.0)), float(body.get("inertia", 1.0))
+    for key in ("damp", "stiff", "q0", "f_ext"):
+        vals = body.get(key, (0.0, 0.0, 0.0))
+        arr = getattr(b, key)
+        for k in range(3):
+            arr[k] = float(vals[k])
+    b.dof_mask = int(body.get("dof_mask", 0))
+    b.u_ref, b.d_ref = float(body.get("u_ref", 0.0)), float(body.get("d_ref", 0.0))
+    return b
+
+
+def _byref(x):
+    return None if x is None else C.byref(x)
+
+
+# ---- same-name wrappers of the C entry points -----------------------------------
+
+def vplbm_version() -> str:
+    return load_library().vplbm_version().decode()
+
+
+def vplbm_last_error() -> str:
+    return load_library().vplbm_last_error().decode()
+
+
+def vplbm_buffer_sizes_for(lat: LatticeDesc, body: BodyDesc | None, history_capacity: int) -> BufferSizes:
+    out = BufferSizes()
+    _check(load_library().vplbm_buffer_sizes_for(C.byref(lat), _byref(body), int(history_capacity),
+                                                 C.byref(out)))
+    return out
+
+
+def vplbm_create(lat: LatticeDesc, body: BodyDesc | None, history_capacity: int, stream: int = 0):
+    ctx = _CTX()
+    _check(load_library().vplbm_create(C.byref(lat), _byref(body), int(history_capacity),
+                                       C.c_void_p(stream), C.byref(ctx)))
+    return ctx
+
+
+def vplbm_create_with_buffers(lat: LatticeDesc, body: BodyDesc | None, history_capacity: int,
+                              stream: int, buffers: Buffers):
+    ctx = _CTX()
+    _check(load_library().vplbm_create_with_buffers(C.byref(lat), _byref(body), int(history_capacity),
+                                                    C.c_void_p(stream), C.byref(buffers), C.byref(ctx)))
+    return ctx
+
+
+def vplbm_destroy(ctx):
+    load_library().vplbm_destroy(ctx)
+
+
+def vplbm_init_equilibrium(ctx, rho=None, ux=None, uy=None):
+    _check(load_library().vplbm_init_equilibrium(ctx, _dptr(rho), _dptr(ux), _dptr(uy)))
+
+
+def vplbm_set_populations(ctx, f: np.ndarray):
+    _check(load_library().vplbm_set_populations(ctx, _dptr(f)))
+
+
+def vplbm_step(ctx, nsteps: int):
+    _check(load_library().vplbm_step(ctx, int(nsteps)))
+
+
+def vplbm_sync(ctx):
+    _check(load_library().vplbm_sync(ctx))
+
+
+def vplbm_get_populations(ctx, out: np.ndarray):
+    _check(load_library().vplbm_get_populations(ctx, _dptr(out)))
+
+
+def vplbm_get_fields(ctx, rho, ux, uy):
+    _check(load_library().vplbm_get_fields(ctx, _dptr(rho), _dptr(ux), _dptr(uy)))
+
+
+def vplbm_get_fields_dev(ctx, rho_ptr: int, ux_ptr: int, uy_ptr: int):
+    _check(load_library().vplbm_get_fields_dev(ctx, C.c_void_p(rho_ptr), C.c_void_p(ux_ptr),
+                                               C.c_void_p(uy_ptr)))
+
+
+def vplbm_get_history(ctx, first: int, count: int):
+    buf = (Record * max(int(count), 1))()
+    _check(load_library().vplbm_get_history(ctx, int(first), int(count), buf))
+    return buf
+
+
+def vplbm_get_body(ctx):
+    q = np.zeros(3)
+    v = np.zeros(3)
+    step = C.c_longlong()
+    _check(load_library().vplbm_get_body(ctx, _dptr(q), _dptr(v), C.byref(step)))
+    return q, v, int(step.value)
+
+
+def vplbm_set_launch(ctx, bx: int, by: int):
+    _check(load_library().vplbm_set_launch(ctx, int(bx), int(by)))
+
+
+def vplbm_get_launch(ctx):
+    bx, by = C.c_int(), C.c_int()
+    _check(load_library().vplbm_get_launch(ctx, C.byref(bx), C.byref(by)))
+    return bx.value, by.value
+
+
+def vplbm_autotune(ctx, steps_per_trial: int = 20):
+    _check(load_library().vplbm_autotune(ctx, int(steps_per_trial)))
+
+
+def vplbm_get_launch_count(ctx) -> int:
+    n = C.c_longlong()
+    _check(load_library().vplbm_get_launch_count(ctx, C.byref(n)))
+    return int(n.value)
+
+
+def vplbm_save(ctx, path: str):
+    _check(load_library().vplbm_save(ctx, os.fsencode(path)))
+
+
+def vplbm_load(ctx, path: str):
+    _check(load_library().vplbm_load(ctx, os.fsencode(path)))
+
+
+# ---- convenience object ------------------------------------------------------------
+
+class Simulation:
+    """One VP-LBM simulation on the current CUDA device.
+
+    Device buffers are torch tensors handed to ``vplbm_create_with_buffers``;
+    work runs on ``stream`` (default: torch's current stream).
+    """
+
+    def __init__(self, problem: dict, precision: str = "f32", history_capacity: int = 1 << 16,
+                 stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Simulation needs a CUDA device; there is no CPU fallback")
+        self.torch = torch
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.problem = problem
+        self.precision = precision
+        self.nx, self.ny = int(problem["nx"]), int(problem["ny"])
+        self._keep: list = []
+        self._lat = lattice_desc(problem, precision, self._keep)
+        self._body = body_desc(problem.get("body"))
+        self.history_capacity = int(history_capacity)
+        sizes = vplbm_buffer_sizes_for(self._lat, self._body, self.history_capacity)
+        self._tensors = {}
+
+        def alloc(name, nbytes):
+            # one extra 256-byte slot so the data pointer can be aligned
+            t = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=self.device)
+            self._tensors[name] = t
+            ptr = t.data_ptr()
+            return ptr + (-ptr) % 256
+
+        bufs = Buffers()
+        bufs.populations_dev[0] = alloc("f0", sizes.populations)
+        bufs.populations_dev[1] = alloc("f1", sizes.populations)
+        bufs.body_state_dev = alloc("bs", sizes.body_state)
+        bufs.partials_dev = alloc("partials", sizes.partials)
+        bufs.history_dev = alloc("hist", sizes.history)
+        bufs.profiles_dev = alloc("prof", sizes.profiles)
+        bufs.control_dev = alloc("ctrl", sizes.control)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = vplbm_create_with_buffers(self._lat, self._body, self.history_capacity,
+                                             self.stream.cuda_stream, bufs)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            vplbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # state -------------------------------------------------------------------------
+    def init_equilibrium(self, rho=None, ux=None, uy=None):
+        shape = (self.ny, self.nx)
+        arrs = [None if a is None else _f64(np.broadcast_to(a, shape)) for a in (rho, ux, uy)]
+        vplbm_init_equilibrium(self.ctx, *arrs)
+
+    def init_from_problem(self):
+        """Equilibrium of the problem's uniform initial state."""
+        init = self.problem.get("init", {})
+        u = init.get("u", (0.0, 0.0))
+        self.init_equilibrium(init.get("rho", None), u[0], u[1])
+
+    def set_populations(self, f):
+        vplbm_set_populations(self.ctx, _f64(f, (Q, self.ny, self.nx)))
+
+    def step(self, n: int = 1):
+        vplbm_step(self.ctx, n)
+
+    def sync(self):
+        vplbm_sync(self.ctx)
+
+    def populations(self) -> np.ndarray:
+        out = np.empty((Q, self.ny, self.nx))
+        vplbm_get_populations(self.ctx, out)
+        return out
+
+    def fields(self):
+        rho = np.empty((self.ny, self.nx))
+        ux = np.empty_like(rho)
+        uy = np.empty_like(rho)
+        vplbm_get_fields(self.ctx, rho, ux, uy)
+        return rho, ux, uy
+
+    def history(self, first: int = 0, count: int | None = None) -> np.ndarray:
+        if count is None:
+            count = self.nstep - first
+        buf = vplbm_get_history(self.ctx, first, count)
+        arr = np.frombuffer(buf, dtype=np.float64, count=count * len(RECORD_FIELDS))
+        return arr.reshape(count, len(RECORD_FIELDS)).copy()
+
+    def body_state(self):
+        q, v, _ = vplbm_get_body(self.ctx)
+        return q, v
+
+    @property
+    def nstep(self) -> int:
+        return vplbm_get_body(self.ctx)[2]
+
+    def set_launch(self, bx, by):
+        vplbm_set_launch(self.ctx, bx, by)
+
+    def launch(self):
+        return vplbm_get_launch(self.ctx)
+
+    def autotune(self, steps_per_trial: int = 20):
+        vplbm_autotune(self.ctx, steps_per_trial)
+        return self.launch()
+
+    @property
+    def launches(self) -> int:
+        return vplbm_get_launch_count(self.ctx)
+
+    def save(self, path):
+        vplbm_save(self.ctx, path)
+
+    def load(self, path):
+        vplbm_load(self.ctx, path)

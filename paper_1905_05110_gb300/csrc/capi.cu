@@ -1,0 +1,801 @@
+// Host runtime behind the C ABI of include/vplbm.h: descriptor checks,
+// device memory, CUDA-graph replay of the time loop, host transfers,
+// launch-shape autotuning and checkpoints.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vplbm_internal.cuh"
+
+using namespace vplbm;
+
+namespace {
+
+thread_local std::string g_error = "no error";
+
+vplbm_status fail(vplbm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(VPLBM_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));         \
+    } while (0)
+
+constexpr size_t ALIGN = 256;
+constexpr int GRAPH_STEPS = 32;   // steps per captured graph (even)
+constexpr char CKPT_MAGIC[8] = {'V', 'P', 'L', 'B', 'M', 'C', 'K', '1'};
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+size_t elem_size(int precision)
+{
+    return precision == VPLBM_F64 ? 8 : (precision == VPLBM_F32_DEV ? 4 : 2);
+}
+
+double w_host(int a) { return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+// IEEE half <-> double on the host (round to nearest even).
+double half_to_double(uint16_t h)
+{
+    const int s = (h >> 15) & 1, e = (h >> 10) & 31, m = h & 1023;
+    double v;
+    if (e == 0) v = ldexp((double)m, -24);
+    else if (e == 31) v = m ? NAN : INFINITY;
+    else v = ldexp((double)(m | 1024), e - 25);
+    return s ? -v : v;
+}
+
+uint16_t double_to_half(double x)
+{
+    // via float, then float -> half with round-to-nearest-even
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    const uint32_t sign = (u >> 16) & 0x8000u;
+    u &= 0x7fffffffu;
+    if (u >= 0x7f800000u) return (uint16_t)(sign | (u > 0x7f800000u ? 0x7e00u : 0x7c00u));
+    if (u >= 0x477ff000u) return (uint16_t)(sign | 0x7c00u);   // overflow to inf
+    if (u < 0x38800000u) {                                       // subnormal half
+        if (u < 0x33000000u) return (uint16_t)sign;
+        const int e = (int)(u >> 23);
+        uint32_t m = (u & 0x7fffffu) | 0x800000u;
+        const int shift = 126 - e;                                // 14..24
+        uint32_t hm = m >> shift;
+        const uint32_t rem = m & ((1u << shift) - 1u), half = 1u << (shift - 1);
+        if (rem > half || (rem == half && (hm & 1u))) ++hm;
+        return (uint16_t)(sign | hm);
+    }
+    uint32_t hb = ((u >> 13) - (112u << 10));
+    const uint32_t rem = u & 0x1fffu;
+    if (rem > 0x1000u || (rem == 0x1000u && (hb & 1u))) ++hb;
+    return (uint16_t)(sign | hb);
+}
+
+}  // namespace
+
+struct vplbm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;        // caller's stream
+    cudaStream_t capture = nullptr;       // private stream used only to capture graphs
+    int precision = 0;
+    int nx = 0, ny = 0;
+    long long ps = 0;                     // plane stride (elements)
+    size_t pop_bytes = 0;
+    StepParams base{};
+    vplbm_body_desc body_desc{};
+    bool has_body = false;
+    void *f[2] = {nullptr, nullptr};
+    BodyState *bs = nullptr;              // [2]
+    double *partials = nullptr;
+    long long max_parts = 0;
+    Control *ctrl = nullptr;
+    vplbm_record *hist = nullptr;
+    long long hist_cap = 0;
+    double *prof = nullptr;
+    void *owned = nullptr;                // single allocation when the library owns memory
+    long long nstep = 0;
+    int bx = 128, by = 2;
+    cudaGraphExec_t graph = nullptr;
+    int graph_bx = 0, graph_by = 0;
+    long long launches = 0;
+};
+
+namespace {
+
+vplbm_status check_lattice(const vplbm_lattice_desc *lat)
+{
+    if (!lat) return fail(VPLBM_EINVAL, "lattice descriptor is NULL");
+    if (lat->nx < 3 || lat->ny < 3) return fail(VPLBM_EINVAL, "nx and ny must be >= 3 (got %d x %d)", lat->nx, lat->ny);
+    if ((long long)lat->nx * lat->ny > (1LL << 31)) return fail(VPLBM_EINVAL, "lattice too large");
+    if (lat->nx > (1 << 22) || lat->ny > 65535) return fail(VPLBM_EINVAL, "nx must be <= 2^22 and ny <= 65535");
+    for (int k = 0; k < 9; ++k)
+        if (!(lat->s[k] > 0.0 && lat->s[k] < 2.0)) return fail(VPLBM_EINVAL, "relaxation rate s[%d]=%g outside (0,2)", k, lat->s[k]);
+    if (!(lat->eta > 0.0) || !isfinite(lat->eta)) return fail(VPLBM_EINVAL, "eta must be > 0");
+    if (!(lat->rho0 > 0.0) || !isfinite(lat->rho0)) return fail(VPLBM_EINVAL, "rho0 must be > 0");
+    if (!isfinite(lat->gx) || !isfinite(lat->gy)) return fail(VPLBM_EINVAL, "fluid acceleration not finite");
+    if (lat->precision < VPLBM_F64 || lat->precision > VPLBM_F16_DEV) return fail(VPLBM_EINVAL, "unknown precision %d", lat->precision);
+    for (int s = 0; s < 4; ++s) {
+        const int k = lat->bc[s].kind;
+        if (k < VPLBM_BC_PERIODIC || k > VPLBM_BC_ZEROGRAD) return fail(VPLBM_EINVAL, "edge %d: unknown boundary kind %d", s, k);
+        if (k == VPLBM_BC_ZEROGRAD && s >= VPLBM_SOUTH) return fail(VPLBM_EUNSUPPORTED, "zero-gradient is supported on west/east edges only");
+    }
+    if ((lat->bc[VPLBM_WEST].kind == VPLBM_BC_PERIODIC) != (lat->bc[VPLBM_EAST].kind == VPLBM_BC_PERIODIC))
+        return fail(VPLBM_EINVAL, "west and east must both be periodic or neither");
+    if ((lat->bc[VPLBM_SOUTH].kind == VPLBM_BC_PERIODIC) != (lat->bc[VPLBM_NORTH].kind == VPLBM_BC_PERIODIC))
+        return fail(VPLBM_EINVAL, "south and north must both be periodic or neither");
+    return VPLBM_OK;
+}
+
+vplbm_status check_body(const vplbm_body_desc *b)
+{
+    if (!b) return VPLBM_OK;
+    if (!(b->radius >= 0.0) || b->radius > 1e6) return fail(VPLBM_EINVAL, "radius must be in [0, 1e6]");
+    const double vals[6] = {b->x, b->y, b->theta, b->vx, b->vy, b->omega};
+    for (double v : vals)
+        if (!isfinite(v) || fabs(v) > 1e7) return fail(VPLBM_EINVAL, "body pose/velocity must be finite and < 1e7");
+    if (b->motion < VPLBM_MOTION_FIXED || b->motion > VPLBM_MOTION_FREE) return fail(VPLBM_EINVAL, "unknown motion %d", b->motion);
+    if (b->motion == VPLBM_MOTION_IMPOSED && (b->axis < 0 || b->axis > 2)) return fail(VPLBM_EINVAL, "imposed axis must be 0, 1 or 2");
+    if (b->motion == VPLBM_MOTION_FREE) {
+        if (!(b->mass > 0.0) || !(b->inertia > 0.0)) return fail(VPLBM_EINVAL, "free motion needs mass > 0 and inertia > 0");
+        if (b->dof_mask & ~7u) return fail(VPLBM_EINVAL, "dof_mask has bits beyond x|y|theta");
+    }
+    return VPLBM_OK;
+}
+
+void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long long cap, vplbm_buffer_sizes *s,
+               long long *ps_out, long long *parts_out)
+{
+    const long long n = (long long)lat->nx * lat->ny;
+    const long long ps = (long long)round_up((size_t)n, 128);
+    long long parts = 1;
+    for (int k = 0; k < N_SHAPES; ++k) {
+        const long long m = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr,
+                                                 SHAPES[k][0], SHAPES[k][1]);
+        if (m > parts) parts = m;
+    }
+    s->populations = round_up((size_t)(9 * ps) * elem_size(lat->precision), ALIGN);
+    s->body_state = round_up(2 * sizeof(BodyState), ALIGN);
+    s->partials = round_up((size_t)parts * NPART * sizeof(double), ALIGN);
+    s->history = round_up((size_t)cap * sizeof(vplbm_record), ALIGN);
+    s->profiles = round_up((size_t)8 * (lat->nx > lat->ny ? lat->nx : lat->ny) * sizeof(double), ALIGN);
+    s->control = sizeof(Control);
+    if (ps_out) *ps_out = ps;
+    if (parts_out) *parts_out = parts;
+}
+
+BodyState initial_state(const vplbm_ctx *c)
+{
+    BodyState s{};
+    if (c->has_body) {
+        const vplbm_body_desc &b = c->body_desc;
+        s.q[0] = b.x; s.q[1] = b.y; s.q[2] = b.theta;
+        s.v[0] = b.vx; s.v[1] = b.vy; s.v[2] = b.omega;
+    }
+    s.step = 0;
+    return s;
+}
+
+StepParams params_for(const vplbm_ctx *c, long long step)
+{
+    StepParams p = c->base;
+    const int par = (int)(step & 1);
+    p.fin = c->f[par];
+    p.fout = c->f[par ^ 1];
+    p.bs_in = c->bs + par;
+    p.bs_out = c->bs + (par ^ 1);
+    return p;
+}
+
+// Reset step counter, body state and control word (after a new state).
+vplbm_status reset_run(vplbm_ctx *c)
+{
+    BodyState s[2] = {initial_state(c), initial_state(c)};
+    CUDA_TRY(cudaMemcpyAsync(c->bs, s, sizeof s, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->ctrl, 0, sizeof(Control), c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->nstep = 0;
+    return VPLBM_OK;
+}
+
+vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body_desc *body,
+                   long long cap, void *stream)
+{
+    c->stream = (cudaStream_t)stream;
+    CUDA_TRY(cudaGetDevice(&c->device));
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking));
+    c->precision = lat->precision;
+    c->nx = lat->nx;
+    c->ny = lat->ny;
+    c->hist_cap = cap;
+    c->has_body = body != nullptr;
+    if (body) c->body_desc = *body;
+
+    StepParams &p = c->base;
+    p.nx = lat->nx;
+    p.ny = lat->ny;
+    p.ps = c->ps;
+    for (int k = 0; k < 9; ++k) p.s[k] = lat->s[k];
+    p.eta = lat->eta;
+    p.rho0 = lat->rho0;
+    p.gx = lat->gx;
+    p.gy = lat->gy;
+    // wall velocity profiles: [side][comp][maxlen]
+    const int maxlen = lat->nx > lat->ny ? lat->nx : lat->ny;
+    std::vector<double> prof((size_t)8 * maxlen, 0.0);
+    for (int s = 0; s < 4; ++s) {
+        p.bc[s] = lat->bc[s].kind;
+        p.wall_u0[s][0] = lat->bc[s].ux;
+        p.wall_u0[s][1] = lat->bc[s].uy;
+        const int len = s < 2 ? lat->ny : lat->nx;
+        const double *src[2] = {lat->bc[s].ux_profile, lat->bc[s].uy_profile};
+        for (int comp = 0; comp < 2; ++comp) {
+            p.wall_prof[s][comp] = nullptr;
+            if (src[comp] && lat->bc[s].kind == VPLBM_BC_VELOCITY) {
+                for (int k = 0; k < len; ++k) {
+                    if (!isfinite(src[comp][k])) return fail(VPLBM_EINVAL, "edge %d: wall velocity not finite", s);
+                    prof[(size_t)(s * 2 + comp) * maxlen + k] = src[comp][k];
+                }
+                p.wall_prof[s][comp] = c->prof + (size_t)(s * 2 + comp) * maxlen;
+            }
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->prof, prof.data(), prof.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+
+    DevBody &b = p.body;
+    memset(&b, 0, sizeof b);
+    b.present = body ? 1 : 0;
+    if (body) {
+        b.motion = body->motion;
+        b.axis = body->axis;
+        b.dof_mask = body->dof_mask;
+        b.radius = body->radius;
+        b.r2 = body->radius * body->radius;
+        b.amp = body->amp;
+        b.freq = body->freq;
+        b.phase = body->phase;
+        const double q0[3] = {body->x, body->y, body->theta};
+        b.q_center = body->motion == VPLBM_MOTION_IMPOSED ? q0[body->axis] - body->amp * sin(body->phase) : 0.0;
+        b.mass = body->mass;
+        b.inertia = body->inertia;
+        for (int d = 0; d < 3; ++d) {
+            b.damp[d] = body->damp[d];
+            b.stiff[d] = body->stiff[d];
+            b.q0[d] = body->q0[d];
+            b.f_ext[d] = body->f_ext[d];
+        }
+        b.qref = 0.5 * lat->rho0 * body->d_ref * body->u_ref * body->u_ref;
+    }
+    p.partials = c->partials;
+    p.max_parts = c->max_parts;
+    p.ticket = &c->ctrl->ticket;
+    p.err = &c->ctrl->err;
+    p.hist = c->hist;
+    p.hist_cap = cap;
+
+    // populations at rest
+    StepParams q = params_for(c, 0);
+    q.fout = c->f[0];
+    CUDA_TRY(launch_init_equilibrium(c->precision, q, nullptr, nullptr, nullptr, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->hist, 0, (size_t)cap * sizeof(vplbm_record), c->stream));
+    return reset_run(c);
+}
+
+vplbm_status create_impl(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long long cap,
+                         void *stream, const vplbm_buffers *user, vplbm_ctx **out)
+{
+    if (!out) return fail(VPLBM_EINVAL, "out pointer is NULL");
+    *out = nullptr;
+    vplbm_status st = check_lattice(lat);
+    if (st != VPLBM_OK) return st;
+    st = check_body(body);
+    if (st != VPLBM_OK) return st;
+    if (cap < 1) return fail(VPLBM_EINVAL, "history capacity must be >= 1");
+    vplbm_buffer_sizes sz;
+    long long ps = 0, parts = 0;
+    sizes_for(lat, body, cap, &sz, &ps, &parts);
+
+    vplbm_ctx *c = new (std::nothrow) vplbm_ctx();
+    if (!c) return fail(VPLBM_ENOMEM, "host allocation failed");
+    c->ps = ps;
+    c->pop_bytes = sz.populations;
+    c->max_parts = parts;
+    if (user) {
+        const void *ptrs[7] = {user->populations_dev[0], user->populations_dev[1], user->body_state_dev,
+                               user->partials_dev, user->history_dev, user->profiles_dev, user->control_dev};
+        for (const void *q : ptrs)
+            if (!q || ((uintptr_t)q % ALIGN)) {
+                delete c;
+                return fail(VPLBM_EINVAL, "caller buffers must be non-NULL and 256-byte aligned");
+            }
+        c->f[0] = user->populations_dev[0];
+        c->f[1] = user->populations_dev[1];
+        c->bs = (BodyState *)user->body_state_dev;
+        c->partials = (double *)user->partials_dev;
+        c->hist = (vplbm_record *)user->history_dev;
+        c->prof = (double *)user->profiles_dev;
+        c->ctrl = (Control *)user->control_dev;
+    } else {
+        const size_t total = 2 * sz.populations + sz.body_state + sz.partials + sz.history + sz.profiles + sz.control;
+        cudaError_t e = cudaMalloc(&c->owned, total);
+        if (e != cudaSuccess) {
+            delete c;
+            (void)cudaGetLastError();
+            return fail(VPLBM_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", total, cudaGetErrorString(e));
+        }
+        char *base = (char *)c->owned;
+        c->f[0] = base; base += sz.populations;
+        c->f[1] = base; base += sz.populations;
+        c->bs = (BodyState *)base; base += sz.body_state;
+        c->partials = (double *)base; base += sz.partials;
+        c->hist = (vplbm_record *)base; base += sz.history;
+        c->prof = (double *)base; base += sz.profiles;
+        c->ctrl = (Control *)base;
+    }
+    st = setup(c, lat, body, cap, stream);
+    if (st != VPLBM_OK) {
+        vplbm_destroy(c);
+        return st;
+    }
+    *out = c;
+    return VPLBM_OK;
+}
+
+vplbm_status ensure_graph(vplbm_ctx *c)
+{
+    if (c->graph && c->graph_bx == c->bx && c->graph_by == c->by) return VPLBM_OK;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    CUDA_TRY(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < GRAPH_STEPS && err == cudaSuccess; ++k)
+        err = launch_step(c->precision, params_for(c, k), c->bx, c->by, c->capture);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->capture, &g);
+    if (err != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(VPLBM_ECUDA, "graph capture failed: %s", cudaGetErrorString(err != cudaSuccess ? err : e2));
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return fail(VPLBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e3));
+    c->graph_bx = c->bx;
+    c->graph_by = c->by;
+    return VPLBM_OK;
+}
+
+vplbm_status step_impl(vplbm_ctx *c, long long n)
+{
+    while (n > 0) {
+        if ((c->nstep & 1) == 0 && n >= GRAPH_STEPS) {
+            vplbm_status st = ensure_graph(c);
+            if (st != VPLBM_OK) return st;
+            CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+            c->nstep += GRAPH_STEPS;
+            c->launches += GRAPH_STEPS;
+            n -= GRAPH_STEPS;
+        } else {
+            CUDA_TRY(launch_step(c->precision, params_for(c, c->nstep), c->bx, c->by, c->stream));
+            c->nstep += 1;
+            c->launches += 1;
+            n -= 1;
+        }
+    }
+    return VPLBM_OK;
+}
+
+vplbm_status read_error(vplbm_ctx *c)
+{
+    Control ctl;
+    CUDA_TRY(cudaMemcpyAsync(&ctl, c->ctrl, sizeof ctl, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (ctl.err & ERR_NONFINITE) return fail(VPLBM_ENONFINITE, "a density became non-positive or non-finite");
+    if (ctl.err & ERR_INTERNAL) return fail(VPLBM_ECUDA, "internal reduction capacity exceeded");
+    return VPLBM_OK;
+}
+
+// Host copy of the stored populations <-> full f in FP64.
+void stored_to_full(const vplbm_ctx *c, const void *raw, double *f)
+{
+    const long long n = (long long)c->nx * c->ny;
+    const double rho0 = c->base.rho0;
+    for (int a = 0; a < 9; ++a) {
+        const double base = c->precision == VPLBM_F64 ? 0.0 : w_host(a) * rho0;
+        for (long long k = 0; k < n; ++k) {
+            const long long idx = a * c->ps + k;
+            double v;
+            if (c->precision == VPLBM_F64) v = ((const double *)raw)[idx];
+            else if (c->precision == VPLBM_F32_DEV) v = (double)((const float *)raw)[idx];
+            else v = half_to_double(((const uint16_t *)raw)[idx]);
+            f[a * n + k] = v + base;
+        }
+    }
+}
+
+void full_to_stored(const vplbm_ctx *c, const double *f, void *raw)
+{
+    const long long n = (long long)c->nx * c->ny;
+    const double rho0 = c->base.rho0;
+    for (int a = 0; a < 9; ++a) {
+        const double base = c->precision == VPLBM_F64 ? 0.0 : w_host(a) * rho0;
+        for (long long k = 0; k < n; ++k) {
+            const long long idx = a * c->ps + k;
+            const double v = f[a * n + k] - base;
+            if (c->precision == VPLBM_F64) ((double *)raw)[idx] = v;
+            else if (c->precision == VPLBM_F32_DEV) ((float *)raw)[idx] = (float)v;
+            else ((uint16_t *)raw)[idx] = double_to_half(v);
+        }
+    }
+}
+
+struct CkptHeader {
+    char magic[8];
+    int nx, ny, precision, pad;
+    long long ps, nstep, hist_cap, launches;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char *vplbm_last_error(void) { return g_error.c_str(); }
+
+const char *vplbm_version(void) { return "vplbm 0.1.0 (sm_103a)"; }
+
+vplbm_status vplbm_buffer_sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body,
+                                    long long history_capacity, vplbm_buffer_sizes *out)
+{
+    if (!out) return fail(VPLBM_EINVAL, "out pointer is NULL");
+    vplbm_status st = check_lattice(lat);
+    if (st != VPLBM_OK) return st;
+    st = check_body(body);
+    if (st != VPLBM_OK) return st;
+    if (history_capacity < 1) return fail(VPLBM_EINVAL, "history capacity must be >= 1");
+    sizes_for(lat, body, history_capacity, out, nullptr, nullptr);
+    return VPLBM_OK;
+}
+
+vplbm_status vplbm_create(const vplbm_lattice_desc *lat, const vplbm_body_desc *body,
+                          long long history_capacity, void *cuda_stream, vplbm_ctx **out)
+{
+    try {
+        return create_impl(lat, body, history_capacity, cuda_stream, nullptr, out);
+    } catch (...) {
+        return fail(VPLBM_ENOMEM, "host allocation failed");
+    }
+}
+
+vplbm_status vplbm_create_with_buffers(const vplbm_lattice_desc *lat, const vplbm_body_desc *body,
+                                       long long history_capacity, void *cuda_stream,
+                                       const vplbm_buffers *buffers, vplbm_ctx **out)
+{
+    if (!buffers) return fail(VPLBM_EINVAL, "buffers is NULL");
+    try {
+        return create_impl(lat, body, history_capacity, cuda_stream, buffers, out);
+    } catch (...) {
+        return fail(VPLBM_ENOMEM, "host allocation failed");
+    }
+}
+
+void vplbm_destroy(vplbm_ctx *c)
+{
+    if (!c) return;
+    if (c->stream || c->owned) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->capture) cudaStreamDestroy(c->capture);
+    if (c->owned) cudaFree(c->owned);
+    delete c;
+}
+
+vplbm_status vplbm_init_equilibrium(vplbm_ctx *c, const double *rho, const double *ux, const double *uy)
+{
+    if (!c) return fail(VPLBM_EINVAL, "context is NULL");
+    const size_t n = (size_t)c->nx * c->ny;
+    double *tmp = nullptr;
+    const int nf = (rho ? 1 : 0) + (ux ? 1 : 0) + (uy ? 1 : 0);
+    if (nf) CUDA_TRY(cudaMallocAsync((void **)&tmp, nf * n * sizeof(double), c->stream));
+    double *d[3] = {nullptr, nullptr, nullptr};
+    const double *h[3] = {rho, ux, uy};
+    int k = 0;
+    for (int m = 0; m < 3; ++m)
+        if (h[m]) {
+            d[m] = tmp + k++ * n;
+            CUDA_TRY(cudaMemcpyAsync(d[m], h[m], n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        }
+    StepParams p = params_for(c, 0);
+    p.fout = c->f[0];
+    CUDA_TRY(launch_init_equilibrium(c->precision, p, d[0], d[1], d[2], c->stream));
+    if (tmp) CUDA_TRY(cudaFreeAsync(tmp, c->stream));
+    return reset_run(c);
+}
+
+vplbm_status vplbm_set_populations(vplbm_ctx *c, const double *f)
+{
+    if (!c || !f) return fail(VPLBM_EINVAL, "NULL argument");
+    try {
+        std::vector<char> raw(c->pop_bytes, 0);
+        full_to_stored(c, f, raw.data());
+        CUDA_TRY(cudaMemcpyAsync(c->f[0], raw.data(), c->pop_bytes, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    } catch (const std::bad_alloc &) {
+        return fail(VPLBM_ENOMEM, "host allocation failed");
+    }
+    return reset_run(c);
+}
+
+vplbm_status vplbm_step(vplbm_ctx *c, long long nsteps)
+{
+    if (!c) return fail(VPLBM_EINVAL, "context is NULL");
+    if (nsteps < 0) return fail(VPLBM_EINVAL, "nsteps must be >= 0");
+    return step_impl(c, nsteps);
+}
+
+vplbm_status vplbm_sync(vplbm_ctx *c)
+{
+    if (!c) return fail(VPLBM_EINVAL, "context is NULL");
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return read_error(c);
+}
+
+vplbm_status vplbm_get_populations(vplbm_ctx *c, double *f)
+{
+    if (!c || !f) return fail(VPLBM_EINVAL, "NULL argument");
+    try {
+        std::vector<char> raw(c->pop_bytes);
+        CUDA_TRY(cudaMemcpyAsync(raw.data(), c->f[c->nstep & 1], c->pop_bytes, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        stored_to_full(c, raw.data(), f);
+    } catch (const std::bad_alloc &) {
+        return fail(VPLBM_ENOMEM, "host allocation failed");
+    }
+    return read_error(c);
+}
+
+vplbm_status vplbm_get_fields_dev(vplbm_ctx *c, double *rho_dev, double *ux_dev, double *uy_dev)
+{
+    if (!c) return fail(VPLBM_EINVAL, "context is NULL");
+    CUDA_TRY(launch_fields(c->precision, params_for(c, c->nstep), rho_dev, ux_dev, uy_dev, c->stream));
+    return VPLBM_OK;
+}
+
+vplbm_status vplbm_get_fields(vplbm_ctx *c, double *rho, double *ux, double *uy)
+{
+    if (!c) return fail(VPLBM_EINVAL, "context is NULL");
+    const size_t n = (size_t)c->nx * c->ny;
+    double *tmp = nullptr;
+    CUDA_TRY(cudaMallocAsync((void **)&tmp, 3 * n * sizeof(double), c->stream));
+    vplbm_status st = vplbm_get_fields_dev(c, tmp, tmp + n, tmp + 2 * n);
+    if (st != VPLBM_OK) {
+        cudaFreeAsync(tmp, c->stream);
+        return st;
+    }
+    double *h[3] = {rho, ux, uy};
+    for (int m = 0; m < 3; ++m)
+        if (h[m]) CUDA_TRY(cudaMemcpyAsync(h[m], tmp + m * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaFreeAsync(tmp, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return read_error(c);
+}
+
+vplbm_status vplbm_get_history(vplbm_ctx *c, long long first, long long count, vplbm_record *dst)
+{
+    if (!c || (!dst && count > 0)) return fail(VPLBM_EINVAL, "NULL argument");
+    if (first < 0 || count < 0) return fail(VPLBM_EINVAL, "negative range");
+    if (first + count > c->nstep || first < c->nstep - c->hist_cap)
+        return fail(VPLBM_ERANGE, "records [%lld, %lld) not available (step %lld, capacity %lld)", first,
+                    first + count, c->nstep, c->hist_cap);
+    long long done = 0;
+    while (done < count) {
+        const long long slot = (first + done) % c->hist_cap;
+        long long len = c->hist_cap - slot;
+        if (len > count - done) len = count - done;
+        CUDA_TRY(cudaMemcpyAsync(dst + done, c->hist + slot, (size_t)len * sizeof(vplbm_record),
+                                 cudaMemcpyDeviceToHost, c->stream));
+        done += len;
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return read_error(c);
+}
+
+vplbm_status vplbm_get_body(vplbm_ctx *c, double q[3], double v[3], long long *step)
+{
+    if (!c) return fail(VPLBM_EINVAL, "context is NULL");
+    BodyState s;
+    CUDA_TRY(cudaMemcpyAsync(&s, c->bs + (c->nstep & 1), sizeof s, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int d = 0; d < 3; ++d) {
+        if (q) q[d] = s.q[d];
+        if (v) v[d] = s.v[d];
+    }
+    if (step) *step = s.step;
+    return read_error(c);
+}
+
+vplbm_status vplbm_set_launch(vplbm_ctx *c, int bx, int by)
+{
+    if (!c) return fail(VPLBM_EINVAL, "context is NULL");
+    const int t = bx * by;
+    if (bx < 32 || bx % 32 || by < 1 || (t != 128 && t != 256 && t != 512))
+        return fail(VPLBM_EINVAL, "launch shape %dx%d not allowed", bx, by);
+    if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, bx, by) > c->max_parts)
+        return fail(VPLBM_EINVAL, "launch shape %dx%d needs more reduction scratch than allocated", bx, by);
+    c->bx = bx;
+    c->by = by;
+    return VPLBM_OK;
+}
+
+vplbm_status vplbm_get_launch(vplbm_ctx *c, int *bx, int *by)
+{
+    if (!c) return fail(VPLBM_EINVAL, "context is NULL");
+    if (bx) *bx = c->bx;
+    if (by) *by = c->by;
+    return VPLBM_OK;
+}
+
+vplbm_status vplbm_get_launch_count(vplbm_ctx *c, long long *launches)
+{
+    if (!c || !launches) return fail(VPLBM_EINVAL, "NULL argument");
+    *launches = c->launches;
+    return VPLBM_OK;
+}
+
+vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
+{
+    if (!c) return fail(VPLBM_EINVAL, "context is NULL");
+    if (steps_per_trial < 2) steps_per_trial = 2;
+    steps_per_trial += steps_per_trial & 1;
+    // save the run state
+    void *save_f = nullptr, *save_h = nullptr;
+    BodyState save_bs[2];
+    const size_t hbytes = (size_t)c->hist_cap * sizeof(vplbm_record);
+    CUDA_TRY(cudaMalloc(&save_f, c->pop_bytes));
+    if (cudaMalloc(&save_h, hbytes) != cudaSuccess) {
+        cudaFree(save_f);
+        return fail(VPLBM_ENOMEM, "autotune scratch allocation failed");
+    }
+    const long long nstep0 = c->nstep;
+    const int bx0 = c->bx, by0 = c->by;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    vplbm_status st = VPLBM_OK;
+    float best = 1e30f;
+    int best_k = -1;
+    auto restore = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(c->f[nstep0 & 1], save_f, c->pop_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->hist, save_h, hbytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->bs, save_bs, sizeof save_bs, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        c->nstep = nstep0;
+        return e;
+    };
+    do {
+        if (cudaMemcpyAsync(save_f, c->f[nstep0 & 1], c->pop_bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+            cudaMemcpyAsync(save_h, c->hist, hbytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+            cudaMemcpyAsync(save_bs, c->bs, sizeof save_bs, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess ||
+            cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            st = fail(VPLBM_ECUDA, "autotune setup failed");
+            break;
+        }
+        for (int k = 0; k < N_SHAPES; ++k) {
+            if (vplbm_set_launch(c, SHAPES[k][0], SHAPES[k][1]) != VPLBM_OK) continue;
+            for (int rep = 0; rep < 2; ++rep) {   // first pass warms up
+                if (restore() != cudaSuccess) { st = fail(VPLBM_ECUDA, "autotune restore failed"); break; }
+                cudaEventRecord(e0, c->stream);
+                for (int s = 0; s < steps_per_trial && st == VPLBM_OK; ++s) {
+                    if (launch_step(c->precision, params_for(c, c->nstep), c->bx, c->by, c->stream) != cudaSuccess)
+                        st = fail(VPLBM_ECUDA, "autotune launch failed");
+                    c->nstep++;
+                }
+                cudaEventRecord(e1, c->stream);
+                if (st != VPLBM_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                    if (st == VPLBM_OK) st = fail(VPLBM_ECUDA, "autotune timing failed");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 1 && ms < best) { best = ms; best_k = k; }
+            }
+            if (st != VPLBM_OK) break;
+        }
+    } while (0);
+    if (restore() != cudaSuccess && st == VPLBM_OK) st = fail(VPLBM_ECUDA, "autotune restore failed");
+    // the trials may have latched errors on a state that was restored
+    cudaMemsetAsync(&c->ctrl->err, 0, sizeof(int), c->stream);
+    cudaStreamSynchronize(c->stream);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(save_f);
+    cudaFree(save_h);
+    if (best_k >= 0) {
+        c->bx = SHAPES[best_k][0];
+        c->by = SHAPES[best_k][1];
+    } else {
+        c->bx = bx0;
+        c->by = by0;
+    }
+    return st;
+}
+
+vplbm_status vplbm_save(vplbm_ctx *c, const char *path)
+{
+    if (!c || !path) return fail(VPLBM_EINVAL, "NULL argument");
+    try {
+        std::vector<char> raw(c->pop_bytes);
+        std::vector<vplbm_record> hist((size_t)c->hist_cap);
+        BodyState bs;
+        CUDA_TRY(cudaMemcpyAsync(raw.data(), c->f[c->nstep & 1], c->pop_bytes, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(hist.data(), c->hist, hist.size() * sizeof(vplbm_record), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(&bs, c->bs + (c->nstep & 1), sizeof bs, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        CkptHeader h{};
+        memcpy(h.magic, CKPT_MAGIC, 8);
+        h.nx = c->nx; h.ny = c->ny; h.precision = c->precision;
+        h.ps = c->ps; h.nstep = c->nstep; h.hist_cap = c->hist_cap; h.launches = c->launches;
+        FILE *fp = fopen(path, "wb");
+        if (!fp) return fail(VPLBM_EIO, "cannot open %s for writing", path);
+        bool ok = fwrite(&h, sizeof h, 1, fp) == 1 && fwrite(&bs, sizeof bs, 1, fp) == 1 &&
+                  fwrite(raw.data(), 1, raw.size(), fp) == raw.size() &&
+                  fwrite(hist.data(), sizeof(vplbm_record), hist.size(), fp) == hist.size();
+        ok = (fclose(fp) == 0) && ok;
+        if (!ok) return fail(VPLBM_EIO, "write to %s failed", path);
+    } catch (const std::bad_alloc &) {
+        return fail(VPLBM_ENOMEM, "host allocation failed");
+    }
+    return read_error(c);
+}
+
+vplbm_status vplbm_load(vplbm_ctx *c, const char *path)
+{
+    if (!c || !path) return fail(VPLBM_EINVAL, "NULL argument");
+    try {
+        FILE *fp = fopen(path, "rb");
+        if (!fp) return fail(VPLBM_EIO, "cannot open %s", path);
+        CkptHeader h;
+        BodyState bs;
+        bool ok = fread(&h, sizeof h, 1, fp) == 1 && fread(&bs, sizeof bs, 1, fp) == 1;
+        if (!ok || memcmp(h.magic, CKPT_MAGIC, 8) != 0) {
+            fclose(fp);
+            return fail(VPLBM_EIO, "%s is not a checkpoint", path);
+        }
+        if (h.nx != c->nx || h.ny != c->ny || h.precision != c->precision || h.ps != c->ps || h.hist_cap != c->hist_cap) {
+            fclose(fp);
+            return fail(VPLBM_EINVAL, "checkpoint %s does not match this context", path);
+        }
+        std::vector<char> raw(c->pop_bytes);
+        std::vector<vplbm_record> hist((size_t)c->hist_cap);
+        ok = fread(raw.data(), 1, raw.size(), fp) == raw.size() &&
+             fread(hist.data(), sizeof(vplbm_record), hist.size(), fp) == hist.size();
+        fclose(fp);
+        if (!ok) return fail(VPLBM_EIO, "%s is truncated", path);
+        const int par = (int)(h.nstep & 1);
+        CUDA_TRY(cudaMemcpyAsync(c->f[par], raw.data(), raw.size(), cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->hist, hist.data(), hist.size() * sizeof(vplbm_record), cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->bs + par, &bs, sizeof bs, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaMemsetAsync(c->ctrl, 0, sizeof(Control), c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        c->nstep = h.nstep;
+    } catch (const std::bad_alloc &) {
+        return fail(VPLBM_ENOMEM, "host allocation failed");
+    }
+    return VPLBM_OK;
+}
+
+}  // extern "C"

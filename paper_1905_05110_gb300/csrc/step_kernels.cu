@@ -1,0 +1,564 @@
+// Fused VP-MRT D2Q9 step for sm_103a, and the small kernels around it.
+//
+// One launch is one time step of Algorithm 1 (Sec. 2.3) for every node:
+//   pull-stream the post-collision populations of the previous step
+//   (Eq. 18) with the boundary rules of Sec. 3.1/3.2 -> rho, j (Eq. 19)
+//   -> chi and u_s from the body pose, in registers (Eq. 2) -> penalized
+//   velocity (Eq. 22) -> MRT collision with forcing in moment space
+//   (Eqs. 14-17) -> store.  Blocks whose tile meets the disk's bounding box
+//   also reduce, in FP64, the penalization reaction and the momentum
+//   exchanged through solid/fluid links (Eqs. 25-27); the last of them sums
+//   the block partials in a fixed order and one thread advances the body
+//   (Eqs. 23-24, RK4), writes the history record and the next pose.
+//
+// Storage is structure-of-arrays f[a][j][i] with a padded plane stride;
+// consecutive threads own consecutive i, so every one of the 9 loads and 9
+// stores of a warp is a contiguous 128-byte (FP32) run.  chi is never
+// stored.  The collision uses the closed forms of M, M^-1 and M F
+// (the rows of Eq. 15 are orthogonal: M^-1 = M^T diag(1/9, 1/36, 1/36,
+// 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)).
+#include <math.h>
+
+#include "vplbm_internal.cuh"
+
+namespace vplbm {
+
+const int SHAPES[N_SHAPES][2] = {{128, 2}, {256, 1}, {64, 4}, {32, 8}, {128, 1}, {256, 2}, {64, 2}};
+
+namespace {
+
+// ---- precision traits -------------------------------------------------
+
+template <int P> struct Prec;
+template <> struct Prec<VPLBM_F64> { using S = double; using T = double; static constexpr bool DEV = false; };
+template <> struct Prec<VPLBM_F32_DEV> { using S = float; using T = float; static constexpr bool DEV = true; };
+template <> struct Prec<VPLBM_F16_DEV> { using S = __half; using T = float; static constexpr bool DEV = true; };
+
+__device__ __forceinline__ double ldv(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ldv(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ldv(const __half *p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ void stv(double *p, double x) { *p = x; }
+__device__ __forceinline__ void stv(float *p, float x) { *p = x; }
+__device__ __forceinline__ void stv(__half *p, float x) { *p = __float2half_rn(x); }
+
+// D2Q9 velocity set in the order of Eq. (10), weights of Eq. (13).
+__host__ __device__ constexpr int cx_of(int a) { return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0); }
+__host__ __device__ constexpr int cy_of(int a) { return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0); }
+__host__ __device__ constexpr int opp_of(int a) { return a == 0 ? 0 : (a <= 4 ? ((a + 1) % 4) + 1 : ((a - 5 + 2) % 4) + 5); }
+__host__ __device__ constexpr double w_of(int a) { return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 && opp_of(4) == 2, "opp axis");
+static_assert(opp_of(5) == 7 && opp_of(6) == 8 && opp_of(7) == 5 && opp_of(8) == 6, "opp diag");
+
+__device__ __forceinline__ double wall_u(const StepParams &p, int side, int comp, int k)
+{
+    const double *prof = p.wall_prof[side][comp];
+    return prof ? prof[k] : p.wall_u0[side][comp];
+}
+
+// Pull of population a into edge node (i, j), with the boundary rules.
+template <int P>
+__device__ typename Prec<P>::T pull_edge(const StepParams &p, const typename Prec<P>::S *fin, int a, int i, int j)
+{
+    using T = typename Prec<P>::T;
+    const int nx = p.nx, ny = p.ny;
+    const long long ps = p.ps;
+    int si = i - cx_of(a);
+    int sj = j - cy_of(a);
+    if (sj < 0 || sj >= ny) {
+        const int side = sj < 0 ? VPLBM_SOUTH : VPLBM_NORTH;
+        const int kind = p.bc[side];
+        if (kind == VPLBM_BC_PERIODIC) {
+            sj = sj < 0 ? sj + ny : sj - ny;
+        } else {
+            T val = ldv(fin + opp_of(a) * ps + (long long)j * nx + i);
+            if (kind == VPLBM_BC_VELOCITY) {
+                double cu = cx_of(a) * wall_u(p, side, 0, i) + cy_of(a) * wall_u(p, side, 1, i);
+                val += (T)(6.0 * w_of(a) * p.rho0 * cu);
+            }
+            return val;
+        }
+    }
+    if (si < 0 || si >= nx) {
+        const int side = si < 0 ? VPLBM_WEST : VPLBM_EAST;
+        const int kind = p.bc[side];
+        if (kind == VPLBM_BC_PERIODIC) {
+            si = si < 0 ? si + nx : si - nx;
+        } else if (kind == VPLBM_BC_ZEROGRAD) {
+            return ldv(fin + a * ps + (long long)sj * nx + i);
+        } else {
+            T val = ldv(fin + opp_of(a) * ps + (long long)j * nx + i);
+            if (kind == VPLBM_BC_VELOCITY) {
+                double cu = cx_of(a) * wall_u(p, side, 0, j) + cy_of(a) * wall_u(p, side, 1, j);
+                val += (T)(6.0 * w_of(a) * p.rho0 * cu);
+            }
+            return val;
+        }
+    }
+    return ldv(fin + a * ps + (long long)sj * nx + si);
+}
+
+// Pull-stream all 9 populations of node (i, j).
+template <int P>
+__device__ __forceinline__ void pull_all(const StepParams &p, const typename Prec<P>::S *__restrict__ fin,
+                                         int i, int j, typename Prec<P>::T f[NQ])
+{
+    const int nx = p.nx;
+    const long long ps = p.ps;
+    if (i > 0 && i < nx - 1 && j > 0 && j < p.ny - 1) {
+        const long long b = (long long)j * nx + i;
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) f[a] = ldv(fin + a * ps + b - cx_of(a) - (long long)cy_of(a) * nx);
+    } else {
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) f[a] = pull_edge<P>(p, fin, a, i, j);
+    }
+}
+
+// Exact chi predicate of Eq. (2) in FP64 without contraction.
+__device__ __forceinline__ bool chi_exact(int i, int j, double xg, double yg, double r2)
+{
+    double dx = __dsub_rn((double)i, xg);
+    double dy = __dsub_rn((double)j, yg);
+    double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    return d2 <= r2;
+}
+
+// Per-block values derived from the pose (computed once by thread 0).
+struct BlockPose {
+    double q[3], v[3];
+    long long step;
+    int tx0, tx1, ty0, ty1;   // tiles that may hold solid nodes
+    int xi, yi;               // floor(x_G), floor(y_G) (clamped)
+    float xf, yf;             // x_G - xi, y_G - yi
+    float vxf, vyf, omf;
+};
+
+__device__ void block_pose(const StepParams &p, int bx, int by, BlockPose &bp)
+{
+    const BodyState bs = *p.bs_in;
+    for (int d = 0; d < 3; ++d) { bp.q[d] = bs.q[d]; bp.v[d] = bs.v[d]; }
+    bp.step = bs.step;
+    bp.tx0 = bp.tx1 = bp.ty0 = bp.ty1 = 0;
+    bp.xi = bp.yi = 0;
+    bp.xf = bp.yf = 0.f;
+    bp.vxf = (float)bs.v[0]; bp.vyf = (float)bs.v[1]; bp.omf = (float)bs.v[2];
+    if (!p.body.present) return;
+    if (!isfinite(bs.q[0]) || !isfinite(bs.q[1])) return;   // reported by the tail's record
+    const double R = p.body.radius;
+    // node range that may satisfy the chi predicate, one node of margin
+    double ilo = fmax(floor(bs.q[0] - R) - 1.0, 0.0), ihi = fmin(ceil(bs.q[0] + R) + 1.0, (double)(p.nx - 1));
+    double jlo = fmax(floor(bs.q[1] - R) - 1.0, 0.0), jhi = fmin(ceil(bs.q[1] + R) + 1.0, (double)(p.ny - 1));
+    if (!(ilo <= ihi) || !(jlo <= jhi)) return;   // disk outside the lattice (or NaN pose)
+    bp.tx0 = (int)ilo / bx; bp.tx1 = (int)ihi / bx;
+    bp.ty0 = (int)jlo / by; bp.ty1 = (int)jhi / by;
+    double fx = floor(bs.q[0]), fy = floor(bs.q[1]);
+    bp.xi = (int)fx; bp.yi = (int)fy;
+    bp.xf = (float)(bs.q[0] - fx); bp.yf = (float)(bs.q[1] - fy);
+}
+
+// ---- rigid body (Eqs. 23-24 and Algorithm 1 step 3) --------------------
+
+__device__ void body_acc(const DevBody &b, const double F[3], const double q[3], const double v[3], double acc[3])
+{
+    for (int d = 0; d < 3; ++d) {
+        const double m = d < 2 ? b.mass : b.inertia;
+        acc[d] = (F[d] + b.f_ext[d] - b.damp[d] * v[d] - b.stiff[d] * (q[d] - b.q0[d])) / m;
+    }
+}
+
+__device__ void body_advance(const DevBody &b, long long step, const double F[3], double q[3], double v[3])
+{
+    if (!b.present || b.motion == VPLBM_MOTION_FIXED) return;
+    if (b.motion == VPLBM_MOTION_IMPOSED) {
+        const double two_pi = 6.283185307179586;
+        const double ph = two_pi * b.freq * (double)(step + 1) + b.phase;
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        q[b.axis] = b.q_center + b.amp * sn;
+        v[b.axis] = two_pi * b.freq * b.amp * cs;
+        return;
+    }
+    // classic RK4, h = 1, force held over the step
+    double k1v[3], k2v[3], k3v[3], k4v[3], k2q[3], k3q[3], k4q[3], qt[3], vt[3];
+    body_acc(b, F, q, v, k1v);
+    for (int d = 0; d < 3; ++d) { qt[d] = q[d] + 0.5 * v[d]; vt[d] = v[d] + 0.5 * k1v[d]; }
+    for (int d = 0; d < 3; ++d) k2q[d] = vt[d];
+    body_acc(b, F, qt, vt, k2v);
+    for (int d = 0; d < 3; ++d) { qt[d] = q[d] + 0.5 * k2q[d]; vt[d] = v[d] + 0.5 * k2v[d]; }
+    for (int d = 0; d < 3; ++d) k3q[d] = vt[d];
+    body_acc(b, F, qt, vt, k3v);
+    for (int d = 0; d < 3; ++d) { qt[d] = q[d] + k3q[d]; vt[d] = v[d] + k3v[d]; }
+    for (int d = 0; d < 3; ++d) k4q[d] = vt[d];
+    body_acc(b, F, qt, vt, k4v);
+    for (int d = 0; d < 3; ++d) {
+        if (!((b.dof_mask >> d) & 1u)) continue;
+        const double nq = q[d] + (v[d] + 2.0 * k2q[d] + 2.0 * k3q[d] + k4q[d]) / 6.0;
+        const double nv = v[d] + (k1v[d] + 2.0 * k2v[d] + 2.0 * k3v[d] + k4v[d]) / 6.0;
+        q[d] = nq;
+        v[d] = nv;
+    }
+}
+
+// Last participating block: fixed-order sum of the partials, history
+// record, body update, next pose.  Runs on warp 0.
+__device__ void step_tail(const StepParams &p, const BlockPose &bp, int nparts)
+{
+    const int lane = threadIdx.x & 31;
+    double acc[NPART - 1];
+#pragma unroll
+    for (int k = 0; k < NPART - 1; ++k) acc[k] = 0.0;
+    for (int s = lane; s < nparts; s += 32) {
+        const double *src = p.partials + (size_t)s * NPART;
+#pragma unroll
+        for (int k = 0; k < NPART - 1; ++k) acc[k] += __ldcg(src + k);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < NPART - 1; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
+    if (lane != 0) return;
+
+    const double Fh[3] = {acc[3], acc[4], acc[5]};
+    vplbm_record r;
+    r.t = (double)bp.step;
+    r.fx = Fh[0]; r.fy = Fh[1]; r.torque = Fh[2];
+    r.cd = p.body.qref > 0 ? Fh[0] / p.body.qref : 0.0;
+    r.cl = p.body.qref > 0 ? Fh[1] / p.body.qref : 0.0;
+    r.x = bp.q[0]; r.y = bp.q[1]; r.theta = bp.q[2];
+    r.vx = bp.v[0]; r.vy = bp.v[1]; r.omega = bp.v[2];
+    r.fpen_x = acc[0]; r.fpen_y = acc[1]; r.tpen = acc[2];
+    r.n_solid = acc[6];
+    p.hist[bp.step % p.hist_cap] = r;
+
+    BodyState nb;
+    for (int d = 0; d < 3; ++d) { nb.q[d] = bp.q[d]; nb.v[d] = bp.v[d]; }
+    body_advance(p.body, bp.step, Fh, nb.q, nb.v);
+    nb.step = bp.step + 1;
+    nb.pad = 0;
+    *p.bs_out = nb;
+    *p.ticket = 0u;   // ready for the next launch (stream order)
+}
+
+// ---- the fused step ----------------------------------------------------
+
+template <int P>
+__global__ void __launch_bounds__(512) vp_mrt_step(const StepParams p)
+{
+    using S = typename Prec<P>::S;
+    using T = typename Prec<P>::T;
+    constexpr bool DEV = Prec<P>::DEV;
+
+    __shared__ BlockPose bp;
+    __shared__ double red[16][NPART];
+    __shared__ int s_last;
+
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid == 0) block_pose(p, blockDim.x, blockDim.y, bp);
+    __syncthreads();
+
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool inside = i < p.nx && j < p.ny;
+    const bool part_block = (int)blockIdx.x >= bp.tx0 && (int)blockIdx.x <= bp.tx1 &&
+                            (int)blockIdx.y >= bp.ty0 && (int)blockIdx.y <= bp.ty1;
+
+    const S *__restrict__ fin = static_cast<const S *>(p.fin);
+    S *__restrict__ fout = static_cast<S *>(p.fout);
+
+    double part[NPART - 1];
+#pragma unroll
+    for (int k = 0; k < NPART - 1; ++k) part[k] = 0.0;
+    bool chi = false;
+
+    if (inside) {
+        T f[NQ];
+        pull_all<P>(p, fin, i, j, f);
+
+        const T rs = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+        const T rho = DEV ? (T)p.rho0 + rs : rs;
+        const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+        const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+
+        // chi and u_s (Eq. 2, Alg. 1 step 4), only where the disk can be
+        T dxl = 0, dyl = 0;
+        if (part_block && p.body.present) {
+            if constexpr (DEV) {
+                const float dxf = (float)(i - bp.xi) - bp.xf;
+                const float dyf = (float)(j - bp.yi) - bp.yf;
+                const float d2 = dxf * dxf + dyf * dyf;
+                const float r2 = (float)p.body.r2;
+                const float band = 1e-5f * r2 + 1e-5f;
+                if (fabsf(d2 - r2) <= band) chi = chi_exact(i, j, bp.q[0], bp.q[1], p.body.r2);
+                else chi = d2 <= r2;
+                dxl = dxf; dyl = dyf;
+            } else {
+                chi = chi_exact(i, j, bp.q[0], bp.q[1], p.body.r2);
+                dxl = (double)i - bp.q[0];
+                dyl = (double)j - bp.q[1];
+            }
+        }
+
+        // penalized velocity, Eq. (22) in the eta-stable form
+        const T inv_rho = (T)1 / rho;
+        const T gx = (T)p.gx, gy = (T)p.gy;
+        const T vx = jx * inv_rho + (T)0.5 * gx;
+        const T vy = jy * inv_rho + (T)0.5 * gy;
+        T ax = 0, ay = 0;
+        if (chi) {
+            T usx, usy;
+            if constexpr (DEV) { usx = bp.vxf - bp.omf * dyl; usy = bp.vyf + bp.omf * dxl; }
+            else { usx = bp.v[0] - bp.v[2] * dyl; usy = bp.v[1] + bp.v[2] * dxl; }
+            const T k = (T)(1.0 / (p.eta + 0.5));
+            ax = -(vx - usx) * k;
+            ay = -(vy - usy) * k;
+        }
+        const T ux = vx + (T)0.5 * ax;
+        const T uy = vy + (T)0.5 * ay;
+        const T Gx = rho * (gx + ax);
+        const T Gy = rho * (gy + ay);
+
+        // moments (rows of Eq. 15); equilibria (Eq. 14); M F closed form
+        const T sa = (f[1] + f[2]) + (f[3] + f[4]);
+        const T sd = (f[5] + f[6]) + (f[7] + f[8]);
+        const T e = (T)-4 * f[0] - sa + (T)2 * sd;
+        const T ep = (T)4 * f[0] - (T)2 * sa + sd;
+        const T qx = (T)2 * (f[3] - f[1]) + (f[5] - f[6]) + (f[8] - f[7]);
+        const T qy = (T)2 * (f[4] - f[2]) + (f[5] + f[6]) - (f[7] + f[8]);
+        const T pxx = (f[1] + f[3]) - (f[2] + f[4]);
+        const T pxy = (f[5] + f[7]) - (f[6] + f[8]);
+
+        const T u2r = rho * (ux * ux + uy * uy);
+        const T uG = ux * Gx + uy * Gy;
+        const T s1 = (T)p.s[1], s2 = (T)p.s[2], s4 = (T)p.s[4], s6 = (T)p.s[6], s7 = (T)p.s[7], s8 = (T)p.s[8];
+
+        const T e_s = e - s1 * (e - ((T)-2 * rs + (T)3 * u2r)) + ((T)1 - (T)0.5 * s1) * ((T)6 * uG);
+        const T ep_s = ep - s2 * (ep - (rs - (T)3 * u2r)) - ((T)1 - (T)0.5 * s2) * ((T)6 * uG);
+        const T jx_s = jx + Gx;
+        const T jy_s = jy + Gy;
+        const T qx_s = qx - s4 * (qx + rho * ux) - ((T)1 - (T)0.5 * s4) * Gx;
+        const T qy_s = qy - s6 * (qy + rho * uy) - ((T)1 - (T)0.5 * s6) * Gy;
+        const T pxx_s = pxx - s7 * (pxx - rho * (ux * ux - uy * uy)) + ((T)1 - (T)0.5 * s7) * ((T)2 * (ux * Gx - uy * Gy));
+        const T pxy_s = pxy - s8 * (pxy - rho * ux * uy) + ((T)1 - (T)0.5 * s8) * (ux * Gy + uy * Gx);
+
+        // back to populations, M^-1 = M^T diag(1/|row|^2)
+        const T r9 = rs * (T)(1.0 / 9.0);
+        const T A = r9 - e_s * (T)(1.0 / 36.0) - ep_s * (T)(1.0 / 18.0);
+        const T B = r9 + e_s * (T)(1.0 / 18.0) + ep_s * (T)(1.0 / 36.0);
+        const T X1 = (jx_s - qx_s) * (T)(1.0 / 6.0);
+        const T Y1 = (jy_s - qy_s) * (T)(1.0 / 6.0);
+        const T X2 = jx_s * (T)(1.0 / 6.0) + qx_s * (T)(1.0 / 12.0);
+        const T Y2 = jy_s * (T)(1.0 / 6.0) + qy_s * (T)(1.0 / 12.0);
+        const T Pq = pxx_s * (T)0.25;
+        const T Rq = pxy_s * (T)0.25;
+
+        const long long b = (long long)j * p.nx + i;
+        const long long ps = p.ps;
+        stv(fout + b, r9 - e_s * (T)(1.0 / 9.0) + ep_s * (T)(1.0 / 9.0));
+        stv(fout + ps + b, A + X1 + Pq);
+        stv(fout + 2 * ps + b, A + Y1 - Pq);
+        stv(fout + 3 * ps + b, A - X1 + Pq);
+        stv(fout + 4 * ps + b, A - Y1 - Pq);
+        stv(fout + 5 * ps + b, B + X2 + Y2 + Rq);
+        stv(fout + 6 * ps + b, B - X2 + Y2 - Rq);
+        stv(fout + 7 * ps + b, B - X2 - Y2 + Rq);
+        stv(fout + 8 * ps + b, B + X2 - Y2 - Rq);
+
+        if (!(rho > (T)0) || !(rho < (T)1e30)) *p.err = ERR_NONFINITE;
+
+        if (chi) {
+            // FP64 contributions of a solid node
+            const double rd = (double)rho;
+            const double dxd = (double)i - bp.q[0], dyd = (double)j - bp.q[1];
+            const double px = -rd * (double)ax, py = -rd * (double)ay;
+            double jxd = 0, jyd = 0, oxd = 0, oyd = 0;
+#pragma unroll
+            for (int a = 1; a < NQ; ++a) {
+                const double fa = (double)f[a];
+                const double own = (double)ldv(fin + a * ps + b);
+                jxd += cx_of(a) * fa;
+                jyd += cy_of(a) * fa;
+                oxd += cx_of(a) * own;
+                oyd += cy_of(a) * own;
+            }
+            const double ex = jxd - oxd, ey = jyd - oyd;
+            part[0] = px;
+            part[1] = py;
+            part[2] = dxd * py - dyd * px;
+            part[3] = ex;
+            part[4] = ey;
+            part[5] = dxd * ey - dyd * ex;
+            part[6] = 1.0;
+        }
+    }
+
+    if (!part_block) return;   // uniform over the block
+
+    // ---- block reduction of the 7 FP64 sums (fixed order) -------------
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (blockDim.x * blockDim.y) >> 5;
+    if (__any_sync(0xffffffffu, chi)) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < NPART - 1; ++k) part[k] += __shfl_down_sync(0xffffffffu, part[k], off);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NPART - 1; ++k) red[warp][k] = part[k];
+    __syncthreads();
+    const int ntx = bp.tx1 - bp.tx0 + 1;
+    const int nparts = ntx * (bp.ty1 - bp.ty0 + 1);
+    if (nparts > p.max_parts) {          // cannot happen for a finite pose; never overrun
+        if (tid == 0) *p.err |= ERR_INTERNAL;
+        return;
+    }
+    if (warp == 0) {
+        double v[NPART - 1];
+#pragma unroll
+        for (int k = 0; k < NPART - 1; ++k) v[k] = lane < nwarps ? red[lane][k] : 0.0;
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < NPART - 1; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+        if (lane == 0) {
+            const int slot = ((int)blockIdx.y - bp.ty0) * ntx + ((int)blockIdx.x - bp.tx0);
+            double *dst = p.partials + (size_t)slot * NPART;
+#pragma unroll
+            for (int k = 0; k < NPART - 1; ++k) __stcg(dst + k, v[k]);
+            __threadfence();
+            const unsigned t = atomicAdd(p.ticket, 1u);
+            s_last = (t == (unsigned)(nparts - 1));
+        }
+    }
+    __syncthreads();
+    if (s_last && warp == 0) {
+        __threadfence();
+        step_tail(p, bp, nparts);
+    }
+}
+
+// ---- equilibrium initialisation (Eq. 11) -------------------------------
+
+template <int P>
+__global__ void init_equilibrium_kernel(const StepParams p, const double *rho_f, const double *ux_f, const double *uy_f)
+{
+    using S = typename Prec<P>::S;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx || j >= p.ny) return;
+    const long long k = (long long)j * p.nx + i;
+    const double rho = rho_f ? rho_f[k] : p.rho0;
+    const double ux = ux_f ? ux_f[k] : 0.0;
+    const double uy = uy_f ? uy_f[k] : 0.0;
+    const double u2 = ux * ux + uy * uy;
+    S *fout = static_cast<S *>(p.fout);
+#pragma unroll
+    for (int a = 0; a < NQ; ++a) {
+        const double cu = cx_of(a) * ux + cy_of(a) * uy;
+        const double poly = 3.0 * cu + 4.5 * cu * cu - 1.5 * u2;
+        double val;
+        if (Prec<P>::DEV) val = w_of(a) * ((rho - p.rho0) + rho * poly);
+        else val = w_of(a) * rho * (1.0 + poly);
+        stv(fout + a * p.ps + k, (typename Prec<P>::T)val);
+    }
+}
+
+// ---- macroscopic fields of the current step (Eqs. 19-22) ---------------
+
+template <int P>
+__global__ void fields_kernel(const StepParams p, double *rho_o, double *ux_o, double *uy_o)
+{
+    using S = typename Prec<P>::S;
+    using T = typename Prec<P>::T;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx || j >= p.ny) return;
+    const S *fin = static_cast<const S *>(p.fin);
+    T f[NQ];
+    pull_all<P>(p, fin, i, j, f);
+    double rs = 0, jx = 0, jy = 0;
+#pragma unroll
+    for (int a = 0; a < NQ; ++a) {
+        rs += (double)f[a];
+        jx += cx_of(a) * (double)f[a];
+        jy += cy_of(a) * (double)f[a];
+    }
+    const double rho = Prec<P>::DEV ? p.rho0 + rs : rs;
+    const BodyState bs = *p.bs_in;
+    bool chi = p.body.present && chi_exact(i, j, bs.q[0], bs.q[1], p.body.r2);
+    double vx = jx / rho + 0.5 * p.gx, vy = jy / rho + 0.5 * p.gy;
+    double ax = 0, ay = 0;
+    if (chi) {
+        const double dx = (double)i - bs.q[0], dy = (double)j - bs.q[1];
+        const double usx = bs.v[0] - bs.v[2] * dy, usy = bs.v[1] + bs.v[2] * dx;
+        ax = -(vx - usx) / (p.eta + 0.5);
+        ay = -(vy - usy) / (p.eta + 0.5);
+    }
+    const long long k = (long long)j * p.nx + i;
+    if (rho_o) rho_o[k] = rho;
+    if (ux_o) ux_o[k] = vx + 0.5 * ax;
+    if (uy_o) uy_o[k] = vy + 0.5 * ay;
+}
+
+template <int P>
+cudaError_t launch_step_t(const StepParams &p, int bx, int by, cudaStream_t stream)
+{
+    dim3 block(bx, by);
+    dim3 grid((p.nx + bx - 1) / bx, (p.ny + by - 1) / by);
+    vp_mrt_step<P><<<grid, block, 0, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+long long max_reduction_blocks(int nx, int ny, double radius, int present, int bx, int by)
+{
+    if (!present) return 1;
+    const long long span = (long long)ceil(2.0 * radius) + 5;
+    long long tx = span / bx + 2, ty = span / by + 2;
+    const long long gx = (nx + bx - 1) / bx, gy = (ny + by - 1) / by;
+    if (tx > gx) tx = gx;
+    if (ty > gy) ty = gy;
+    return tx * ty;
+}
+
+cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream)
+{
+    switch (precision) {
+    case VPLBM_F64: return launch_step_t<VPLBM_F64>(p, bx, by, stream);
+    case VPLBM_F32_DEV: return launch_step_t<VPLBM_F32_DEV>(p, bx, by, stream);
+    case VPLBM_F16_DEV: return launch_step_t<VPLBM_F16_DEV>(p, bx, by, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_init_equilibrium(int precision, const StepParams &p, const double *rho_dev,
+                                    const double *ux_dev, const double *uy_dev, cudaStream_t stream)
+{
+    dim3 block(128);
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    switch (precision) {
+    case VPLBM_F64: init_equilibrium_kernel<VPLBM_F64><<<grid, block, 0, stream>>>(p, rho_dev, ux_dev, uy_dev); break;
+    case VPLBM_F32_DEV: init_equilibrium_kernel<VPLBM_F32_DEV><<<grid, block, 0, stream>>>(p, rho_dev, ux_dev, uy_dev); break;
+    case VPLBM_F16_DEV: init_equilibrium_kernel<VPLBM_F16_DEV><<<grid, block, 0, stream>>>(p, rho_dev, ux_dev, uy_dev); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields(int precision, const StepParams &p, double *rho_dev, double *ux_dev,
+                          double *uy_dev, cudaStream_t stream)
+{
+    dim3 block(128);
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    switch (precision) {
+    case VPLBM_F64: fields_kernel<VPLBM_F64><<<grid, block, 0, stream>>>(p, rho_dev, ux_dev, uy_dev); break;
+    case VPLBM_F32_DEV: fields_kernel<VPLBM_F32_DEV><<<grid, block, 0, stream>>>(p, rho_dev, ux_dev, uy_dev); break;
+    case VPLBM_F16_DEV: fields_kernel<VPLBM_F16_DEV><<<grid, block, 0, stream>>>(p, rho_dev, ux_dev, uy_dev); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace vplbm

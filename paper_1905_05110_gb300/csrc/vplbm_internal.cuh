@@ -1,0 +1,91 @@
+// Internal declarations shared by the kernel and runtime translation units.
+// Not part of the public ABI (include/vplbm.h is).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vplbm.h"
+
+namespace vplbm {
+
+constexpr int NQ = 9;
+
+// Pose and velocity of the body at the start of a step, plus the step
+// counter.  Two copies alternate: a step reads one and its tail writes the
+// other, so late blocks of the same launch never see a half-updated pose.
+struct BodyState {
+    double q[3];       // x_G, y_G, theta
+    double v[3];       // vx, vy, omega
+    long long step;    // time step this state belongs to
+    long long pad;
+};
+static_assert(sizeof(BodyState) == 64, "BodyState layout");
+
+// Body constants over a run (copied into every launch's parameters).
+struct DevBody {
+    int present;
+    int motion;
+    int axis;
+    unsigned dof_mask;
+    double radius, r2;
+    double amp, freq, phase, q_center;
+    double mass, inertia;
+    double damp[3], stiff[3], q0[3], f_ext[3];
+    double qref;       // rho0 d_ref u_ref^2 / 2 (0: no C_D / C_L)
+};
+
+// Number of doubles per block partial: fpen_x, fpen_y, tpen, fh_x, fh_y,
+// th, n_solid, (pad).
+constexpr int NPART = 8;
+
+struct StepParams {
+    int nx, ny;
+    long long ps;                 // plane stride (elements) of a population buffer
+    double s[NQ];
+    double eta, rho0, gx, gy;
+    int bc[4];
+    double wall_u0[4][2];
+    const double *wall_prof[4][2];
+    DevBody body;
+    const void *fin;
+    void *fout;
+    const BodyState *bs_in;
+    BodyState *bs_out;
+    double *partials;
+    long long max_parts;          // capacity of partials, in blocks
+    unsigned *ticket;
+    int *err;
+    vplbm_record *hist;
+    long long hist_cap;
+};
+
+// Error bits latched in the control word.
+constexpr int ERR_NONFINITE = 1;
+constexpr int ERR_INTERNAL = 2;
+
+// Control block: ticket counter and error word.
+struct Control {
+    unsigned ticket;
+    int err;
+    unsigned pad[62];
+};
+static_assert(sizeof(Control) == 256, "Control layout");
+
+// Launchers (step_kernels.cu).  All are asynchronous on `stream`.
+cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream);
+cudaError_t launch_init_equilibrium(int precision, const StepParams &p, const double *rho_dev,
+                                    const double *ux_dev, const double *uy_dev, cudaStream_t stream);
+cudaError_t launch_fields(int precision, const StepParams &p, double *rho_dev, double *ux_dev,
+                          double *uy_dev, cudaStream_t stream);
+
+// Largest number of blocks that can take part in the force reduction for
+// a disk of this radius under launch shape (bx, by) on an nx x ny lattice.
+long long max_reduction_blocks(int nx, int ny, double radius, int present, int bx, int by);
+
+// Launch shapes the runtime may pick from.
+constexpr int N_SHAPES = 7;
+extern const int SHAPES[N_SHAPES][2];
+
+}  // namespace vplbm

@@ -1,0 +1,292 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (max |gpu - oracle| / max |oracle| per field; populations are
+compared as deviations from rest, f - w rho0):
+  - FP64 storage and arithmetic: 1e-12 on populations and fields, forces to
+    1e-10 of their scale (sums of a few hundred terms in another order).
+  - FP32 deviation storage: one step from a common state 2e-6 (a handful of
+    FP32 roundings of an O(u) deviation); runs of hundreds of steps 1e-4.
+  - FP16 deviation storage: one step 2e-3 (11-bit mantissa of the stored
+    deviation); runs 5e-2.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from helpers import REC, dev_err, make_pair, moving_bodies, rel_err
+
+pytestmark = pytest.mark.gpu
+
+BC_SETS = [
+    ("periodic", "periodic", "periodic", "periodic"),
+    ("velocity", "zerograd", "noslip", "velocity"),
+    ("noslip", "noslip", "periodic", "periodic"),
+    ("velocity", "velocity", "noslip", "noslip"),
+    ("zerograd", "zerograd", "velocity", "noslip"),
+    ("periodic", "periodic", "velocity", "velocity"),
+]
+
+ONE_STEP_TOL = {"f64": 1e-13, "f32": 2e-6, "f16": 2e-3}
+RUN_TOL = {"f64": 1e-12, "f32": 1e-4, "f16": 5e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library(gpu_library):
+    return gpu_library
+
+
+def _box(nx, ny, bcs, seed, body=None, tau=0.7):
+    w, e, s, n = bcs
+    return wl.mixed_bc_box(nx, ny, seed=seed, west=w, east=e, south=s, north=n, tau=tau, body=body,
+                           rates=wl.random_rates(seed))
+
+
+@pytest.mark.parametrize("bcs", BC_SETS)
+@pytest.mark.parametrize("size", [(67, 45), (5, 4), (130, 3)])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16"])
+def test_steps_from_random_state_every_boundary(bcs, size, precision):
+    nx, ny = size
+    p = _box(nx, ny, bcs, seed=nx + ny)
+    f0 = wl.random_populations(nx, ny, seed=11, amp=0.03, u_amp=0.05)
+    if precision != "f64":   # both sides start from the stored (rounded) state
+        gpu, _ = make_pair(p, precision, init=None, f0=f0)
+        f0 = gpu.populations()
+    gpu, orc = make_pair(p, precision, f0=f0)
+    for n in (1, 2):
+        gpu.step(1)
+        orc.step(1)
+        tol = ONE_STEP_TOL[precision] * (3 if n == 2 else 1)
+        assert dev_err(gpu.populations(), orc.populations()) < tol
+        gr, gx, gy = gpu.fields()
+        orr, ox, oy = orc.fields()
+        assert rel_err(gr - 1, orr - 1) < 10 * tol
+        assert rel_err(gx, ox) < 10 * tol and rel_err(gy, oy) < 10 * tol
+
+
+@pytest.mark.parametrize("motion", ["fixed", "imposed", "free"])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_body_runs_match_oracle(motion, precision):
+    nx, ny = 97, 70
+    body = moving_bodies(nx, ny)[motion]
+    p = _box(nx, ny, ("velocity", "zerograd", "noslip", "noslip"), seed=5, body=body, tau=0.62)
+    p["bc"]["west"] = {"kind": "velocity", "u": (0.05, 0.0)}
+    gpu, orc = make_pair(p, precision)
+    steps = 150
+    gpu.step(steps)
+    orc.step(steps)
+    tol = RUN_TOL[precision]
+    assert dev_err(gpu.populations(), orc.populations()) < tol
+    gr, gx, gy = gpu.fields()
+    orr, ox, oy = orc.fields()
+    assert rel_err(gx, ox) < tol and rel_err(gy, oy) < tol
+    hg, ho = gpu.history(), orc.history()
+    assert np.array_equal(hg[:, REC["t"]], np.arange(steps))
+    assert np.array_equal(hg[:, REC["n_solid"]], ho[:, REC["n_solid"]])
+    ftol = 1e-10 if precision == "f64" else 1e-3
+    for key in ("fx", "fy", "torque", "fpen_x", "fpen_y", "tpen"):
+        assert rel_err(hg[:, REC[key]], ho[:, REC[key]]) < ftol, key
+    ptol = 1e-12 if precision == "f64" else 1e-6
+    for key in ("x", "y", "theta", "vx", "vy", "omega"):
+        assert np.max(np.abs(hg[:, REC[key]] - ho[:, REC[key]])) <= ptol * max(1.0, np.max(np.abs(ho[:, REC[key]]))), key
+
+
+def test_channel_fixed_disk_fp64_full_run():
+    # 256 x 128 parabolic channel past a fixed disk, 2000 steps, FP64.
+    p = wl.channel_fixed_disk()
+    gpu, orc = make_pair(p, "f64")
+    gpu.step(p["steps"])
+    orc.step(p["steps"])
+    assert dev_err(gpu.populations(), orc.populations()) < 1e-12
+    gr, gx, gy = gpu.fields()
+    orr, ox, oy = orc.fields()
+    assert rel_err(gr - 1, orr - 1) < 1e-12
+    assert rel_err(gx, ox) < 1e-12 and rel_err(gy, oy) < 1e-12
+    hg, ho = gpu.history(), orc.history()
+    assert np.max(np.abs(hg[:, REC["cd"]] - ho[:, REC["cd"]])) < 1e-10
+    assert np.max(np.abs(hg[:, REC["cl"]] - ho[:, REC["cl"]])) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_channel_fixed_disk_reduced_precision(precision):
+    p = wl.channel_fixed_disk(steps=600)
+    gpu, orc = make_pair(p, precision)
+    gpu.step(p["steps"])
+    orc.step(p["steps"])
+    gr, gx, gy = gpu.fields()
+    orr, ox, oy = orc.fields()
+    tol = RUN_TOL[precision]
+    assert rel_err(gx, ox) < tol and rel_err(gy, oy) < tol
+    hg, ho = gpu.history(), orc.history()
+    assert np.max(np.abs(hg[-100:, REC["cd"]] - ho[-100:, REC["cd"]])) < 50 * tol
+
+
+FULL = {
+    "oscillating_2048x1024": lambda: wl.oscillating_disk(),
+    "sedimenting_1024x4096": lambda: wl.sedimenting_disk(),
+    "adjoint_1024x512": lambda: wl.adjoint_disk(),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FULL))
+def test_full_size_one_step_every_launch_shape(name):
+    # Full workload size: after a few GPU steps, one more step from the same
+    # state on the GPU (each launch shape) and in the oracle, all nodes.
+    import paper_1905_05110_gb300 as vp
+    p = FULL[name]()
+    gpu = vp.Simulation(p, precision="f32", history_capacity=64)
+    gpu.init_from_problem()
+    gpu.step(6)
+    f0 = gpu.populations()
+    q0, v0 = gpu.body_state()
+    body = dict(p["body"])
+    body.update(x=q0[0], y=q0[1], theta=q0[2], vx=v0[0], vy=v0[1], omega=v0[2])
+    if body["motion"] == "imposed":
+        body["motion"] = "fixed"   # one step: compare the state update, pose from history
+    p1 = dict(p, body=body)
+    orc = oracle.OracleSim(p1, hist_cap=4)
+    orc.set_populations(f0)
+    orc.step(1)
+    ref = orc.populations()
+    ref_h = orc.history(0, 1)[0]
+    for bx, by in vp_shapes():
+        g = vp.Simulation(p1, precision="f32", history_capacity=4)
+        g.set_launch(bx, by)
+        g.set_populations(f0)
+        g.step(1)
+        assert dev_err(g.populations(), ref) < ONE_STEP_TOL["f32"], (bx, by)
+        h = g.history(0, 1)[0]
+        assert h[REC["n_solid"]] == ref_h[REC["n_solid"]]
+        assert rel_err(h[[REC["fx"], REC["fy"]]], ref_h[[REC["fx"], REC["fy"]]]) < 1e-3
+        g.close()
+    del orc
+
+
+def vp_shapes():
+    return [(128, 2), (256, 1), (64, 4), (32, 8), (128, 1), (256, 2), (64, 2)]
+
+
+def test_fp64_full_size_two_steps():
+    p = wl.oscillating_disk()
+    gpu, orc = make_pair(p, "f64", hist_cap=8)
+    gpu.step(2)
+    orc.step(2)
+    assert dev_err(gpu.populations(), orc.populations()) < 1e-13
+    hg, ho = gpu.history(), orc.history()
+    assert rel_err(hg[:, REC["fy"]], ho[:, REC["fy"]]) < 1e-10
+    assert np.max(np.abs(hg[:, REC["y"]] - ho[:, REC["y"]])) < 1e-12
+
+
+def test_deterministic_and_graph_equals_direct_launches():
+    p = wl.oscillating_disk(nx=300, ny=160, diameter=24, x_c=80)
+    import paper_1905_05110_gb300 as vp
+    runs = []
+    for mode in ("graph", "graph", "direct"):
+        g = vp.Simulation(p, precision="f32", history_capacity=256)
+        g.init_from_problem()
+        if mode == "graph":
+            g.step(96)
+        else:
+            for _ in range(96):
+                g.step(1)
+        runs.append((g.populations(), g.history()))
+        g.close()
+    for f, h in runs[1:]:
+        assert np.array_equal(f, runs[0][0])
+        assert np.array_equal(h, runs[0][1])
+
+
+def test_launch_shapes_give_identical_fields_for_fixed_body():
+    import paper_1905_05110_gb300 as vp
+    p = wl.channel_fixed_disk(nx=200, ny=90, center=(50.3, 44.6), diameter=18)
+    ref = None
+    for bx, by in vp_shapes():
+        g = vp.Simulation(p, precision="f32", history_capacity=64)
+        g.set_launch(bx, by)
+        g.init_from_problem()
+        g.step(40)
+        f = g.populations()
+        if ref is None:
+            ref = f
+        assert np.array_equal(f, ref), (bx, by)
+        g.close()
+
+
+def test_checkpoint_resume_is_bitwise(tmp_path):
+    import paper_1905_05110_gb300 as vp
+    p = wl.sedimenting_disk(nx=128, ny=256, diameter=16)
+    a = vp.Simulation(p, precision="f32", history_capacity=128)
+    a.init_from_problem()
+    a.step(41)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    a.step(40)
+    b = vp.Simulation(p, precision="f32", history_capacity=128)
+    b.load(path)
+    assert b.nstep == 41
+    b.step(40)
+    assert np.array_equal(a.populations(), b.populations())
+    assert np.array_equal(a.history(), b.history())
+
+
+def test_history_ring_and_ranges():
+    import paper_1905_05110_gb300 as vp
+    p = wl.channel_fixed_disk(nx=64, ny=40, center=(20, 20), diameter=8)
+    big = vp.Simulation(p, precision="f32", history_capacity=64)
+    small = vp.Simulation(p, precision="f32", history_capacity=10)
+    for g in (big, small):
+        g.init_from_problem()
+        g.step(25)
+    with pytest.raises(vp.VplbmError) as ei:
+        small.history(0, 5)
+    assert ei.value.status == 7
+    with pytest.raises(vp.VplbmError):
+        big.history(20, 10)
+    assert np.array_equal(small.history(15, 10), big.history(15, 10))
+
+
+def test_nonfinite_state_is_reported_not_trapped():
+    import paper_1905_05110_gb300 as vp
+    p = wl.channel_fixed_disk(nx=64, ny=40, center=(20, 20), diameter=8)
+    g = vp.Simulation(p, precision="f32", history_capacity=16)
+    f = wl.random_populations(64, 40, seed=2)
+    f[3, 10, 30] = np.nan
+    g.set_populations(f)
+    g.step(2)
+    with pytest.raises(vp.VplbmError) as ei:
+        g.sync()
+    assert ei.value.status == 4
+    # the context stays usable
+    g.init_from_problem()
+    g.step(3)
+    g.sync()
+
+
+def test_fields_dev_matches_host_fields():
+    import torch
+    import paper_1905_05110_gb300 as vp
+    p = wl.oscillating_disk(nx=160, ny=96, diameter=16, x_c=40)
+    g = vp.Simulation(p, precision="f32", history_capacity=16)
+    g.init_from_problem()
+    g.step(7)
+    rho, ux, uy = g.fields()
+    out = torch.empty((3, 96, 160), dtype=torch.float64, device="cuda")
+    vp.vplbm_get_fields_dev(g.ctx, out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr())
+    g.sync()
+    o = out.cpu().numpy()
+    assert np.array_equal(o[0], rho) and np.array_equal(o[1], ux) and np.array_equal(o[2], uy)
+
+
+def test_autotune_restores_state():
+    import paper_1905_05110_gb300 as vp
+    p = wl.oscillating_disk(nx=512, ny=256, diameter=20, x_c=100)
+    g = vp.Simulation(p, precision="f32", history_capacity=64)
+    g.init_from_problem()
+    g.step(10)
+    f = g.populations()
+    h = g.history()
+    shape = g.autotune(4)
+    assert shape in [tuple(s) for s in vp_shapes()]
+    assert g.nstep == 10
+    assert np.array_equal(g.populations(), f)
+    assert np.array_equal(g.history(), h)
