@@ -203,7 +203,7 @@ vplbm_status vplbm_get_history(vplbm_ctx *ctx, long long first, long long count,
 vplbm_status vplbm_get_body(vplbm_ctx *ctx, double q[3], double v[3], long long *step);
 
 /* Launch shape of the step kernel: block_x * block_y threads per block,
- * block_x a multiple of 32, block_x * block_y in {128, 256, 512}. */
+ * block_x a multiple of 32, block_x * block_y in {128, 256}. */
 vplbm_status vplbm_set_launch(vplbm_ctx *ctx, int block_x, int block_y);
 vplbm_status vplbm_get_launch(vplbm_ctx *ctx, int *block_x, int *block_y);
 

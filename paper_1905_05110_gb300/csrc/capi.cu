@@ -187,6 +187,7 @@ BodyState initial_state(const vplbm_ctx *c)
         s.v[0] = b.vx; s.v[1] = b.vy; s.v[2] = b.omega;
     }
     s.step = 0;
+    derive_pose(s, c->has_body ? 1 : 0, c->has_body ? c->body_desc.radius : 0.0, c->nx, c->ny);
     return s;
 }
 
@@ -231,6 +232,7 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     p.ps = c->ps;
     for (int k = 0; k < 9; ++k) p.s[k] = lat->s[k];
     p.eta = lat->eta;
+    p.pen_k = 1.0 / (lat->eta + 0.5);
     p.rho0 = lat->rho0;
     p.gx = lat->gx;
     p.gy = lat->gy;
@@ -633,7 +635,7 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int bx, int by)
 {
     if (!c) return fail(VPLBM_EINVAL, "context is NULL");
     const int t = bx * by;
-    if (bx < 32 || bx % 32 || by < 1 || (t != 128 && t != 256 && t != 512))
+    if (bx < 32 || bx % 32 || by < 1 || (t != 128 && t != 256))
         return fail(VPLBM_EINVAL, "launch shape %dx%d not allowed", bx, by);
     if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, bx, by) > c->max_parts)
         return fail(VPLBM_EINVAL, "launch shape %dx%d needs more reduction scratch than allocated", bx, by);

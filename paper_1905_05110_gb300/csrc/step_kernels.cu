@@ -23,7 +23,7 @@
 
 namespace vplbm {
 
-const int SHAPES[N_SHAPES][2] = {{128, 2}, {256, 1}, {64, 4}, {32, 8}, {128, 1}, {256, 2}, {64, 2}};
+const int SHAPES[N_SHAPES][2] = {{128, 2}, {256, 1}, {64, 4}, {32, 8}, {128, 1}, {64, 2}, {32, 4}};
 
 namespace {
 
@@ -124,39 +124,6 @@ __device__ __forceinline__ bool chi_exact(int i, int j, double xg, double yg, do
     return d2 <= r2;
 }
 
-// Per-block values derived from the pose (computed once by thread 0).
-struct BlockPose {
-    double q[3], v[3];
-    long long step;
-    int tx0, tx1, ty0, ty1;   // tiles that may hold solid nodes
-    int xi, yi;               // floor(x_G), floor(y_G) (clamped)
-    float xf, yf;             // x_G - xi, y_G - yi
-    float vxf, vyf, omf;
-};
-
-__device__ void block_pose(const StepParams &p, int bx, int by, BlockPose &bp)
-{
-    const BodyState bs = *p.bs_in;
-    for (int d = 0; d < 3; ++d) { bp.q[d] = bs.q[d]; bp.v[d] = bs.v[d]; }
-    bp.step = bs.step;
-    bp.tx0 = bp.tx1 = bp.ty0 = bp.ty1 = 0;
-    bp.xi = bp.yi = 0;
-    bp.xf = bp.yf = 0.f;
-    bp.vxf = (float)bs.v[0]; bp.vyf = (float)bs.v[1]; bp.omf = (float)bs.v[2];
-    if (!p.body.present) return;
-    if (!isfinite(bs.q[0]) || !isfinite(bs.q[1])) return;   // reported by the tail's record
-    const double R = p.body.radius;
-    // node range that may satisfy the chi predicate, one node of margin
-    double ilo = fmax(floor(bs.q[0] - R) - 1.0, 0.0), ihi = fmin(ceil(bs.q[0] + R) + 1.0, (double)(p.nx - 1));
-    double jlo = fmax(floor(bs.q[1] - R) - 1.0, 0.0), jhi = fmin(ceil(bs.q[1] + R) + 1.0, (double)(p.ny - 1));
-    if (!(ilo <= ihi) || !(jlo <= jhi)) return;   // disk outside the lattice (or NaN pose)
-    bp.tx0 = (int)ilo / bx; bp.tx1 = (int)ihi / bx;
-    bp.ty0 = (int)jlo / by; bp.ty1 = (int)jhi / by;
-    double fx = floor(bs.q[0]), fy = floor(bs.q[1]);
-    bp.xi = (int)fx; bp.yi = (int)fy;
-    bp.xf = (float)(bs.q[0] - fx); bp.yf = (float)(bs.q[1] - fy);
-}
-
 // ---- rigid body (Eqs. 23-24 and Algorithm 1 step 3) --------------------
 
 __device__ void body_acc(const DevBody &b, const double F[3], const double q[3], const double v[3], double acc[3])
@@ -202,7 +169,7 @@ __device__ void body_advance(const DevBody &b, long long step, const double F[3]
 
 // Last participating block: fixed-order sum of the partials, history
 // record, body update, next pose.  Runs on warp 0.
-__device__ void step_tail(const StepParams &p, const BlockPose &bp, int nparts)
+__device__ __noinline__ void step_tail(const StepParams &p, int nparts)
 {
     const int lane = threadIdx.x & 31;
     double acc[NPART - 1];
@@ -219,62 +186,95 @@ __device__ void step_tail(const StepParams &p, const BlockPose &bp, int nparts)
         for (int k = 0; k < NPART - 1; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
     if (lane != 0) return;
 
+    const BodyState cur = *p.bs_in;
     const double Fh[3] = {acc[3], acc[4], acc[5]};
     vplbm_record r;
-    r.t = (double)bp.step;
+    r.t = (double)cur.step;
     r.fx = Fh[0]; r.fy = Fh[1]; r.torque = Fh[2];
     r.cd = p.body.qref > 0 ? Fh[0] / p.body.qref : 0.0;
     r.cl = p.body.qref > 0 ? Fh[1] / p.body.qref : 0.0;
-    r.x = bp.q[0]; r.y = bp.q[1]; r.theta = bp.q[2];
-    r.vx = bp.v[0]; r.vy = bp.v[1]; r.omega = bp.v[2];
+    r.x = cur.q[0]; r.y = cur.q[1]; r.theta = cur.q[2];
+    r.vx = cur.v[0]; r.vy = cur.v[1]; r.omega = cur.v[2];
     r.fpen_x = acc[0]; r.fpen_y = acc[1]; r.tpen = acc[2];
     r.n_solid = acc[6];
-    p.hist[bp.step % p.hist_cap] = r;
+    p.hist[cur.step % p.hist_cap] = r;
 
-    BodyState nb;
-    for (int d = 0; d < 3; ++d) { nb.q[d] = bp.q[d]; nb.v[d] = bp.v[d]; }
-    body_advance(p.body, bp.step, Fh, nb.q, nb.v);
-    nb.step = bp.step + 1;
-    nb.pad = 0;
+    BodyState nb = cur;
+    body_advance(p.body, cur.step, Fh, nb.q, nb.v);
+    nb.step = cur.step + 1;
+    derive_pose(nb, p.body.present, p.body.radius, p.nx, p.ny);
     *p.bs_out = nb;
     *p.ticket = 0u;   // ready for the next launch (stream order)
+}
+
+// Contributions of one solid node to the 7 FP64 sums: penalization
+// reaction (force, torque) and momentum exchanged through its links during
+// the streaming into this step (force, torque), plus the node count.
+template <int P>
+__device__ __forceinline__ void solid_node_sums(const StepParams &p, const typename Prec<P>::S *fin, int i, int j,
+                                                double rho, double ax, double ay, double part[NPART - 1])
+{
+    using T = typename Prec<P>::T;
+    const BodyState *bs = p.bs_in;
+    T f[NQ];
+    pull_all<P>(p, fin, i, j, f);   // reloaded (cache hits) so f is not live across the stores
+    const long long b = (long long)j * p.nx + i;
+    const double dxd = (double)i - bs->q[0], dyd = (double)j - bs->q[1];
+    const double px = -rho * ax, py = -rho * ay;
+    double jxd = 0, jyd = 0, oxd = 0, oyd = 0;
+#pragma unroll
+    for (int a = 1; a < NQ; ++a) {
+        const double fa = (double)f[a];
+        const double own = (double)ldv(fin + a * p.ps + b);
+        jxd += cx_of(a) * fa;
+        jyd += cy_of(a) * fa;
+        oxd += cx_of(a) * own;
+        oyd += cy_of(a) * own;
+    }
+    const double ex = jxd - oxd, ey = jyd - oyd;
+    part[0] = px;
+    part[1] = py;
+    part[2] = dxd * py - dyd * px;
+    part[3] = ex;
+    part[4] = ey;
+    part[5] = dxd * ey - dyd * ex;
+    part[6] = 1.0;
 }
 
 // ---- the fused step ----------------------------------------------------
 
 template <int P>
-__global__ void __launch_bounds__(512) vp_mrt_step(const StepParams p)
+__global__ void __launch_bounds__(256, 4) vp_mrt_step(const StepParams p)
 {
     using S = typename Prec<P>::S;
     using T = typename Prec<P>::T;
     constexpr bool DEV = Prec<P>::DEV;
 
-    __shared__ BlockPose bp;
-    __shared__ double red[16][NPART];
+    __shared__ double red[8][NPART];
     __shared__ int s_last;
-
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    if (tid == 0) block_pose(p, blockDim.x, blockDim.y, bp);
-    __syncthreads();
 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const bool inside = i < p.nx && j < p.ny;
-    const bool part_block = (int)blockIdx.x >= bp.tx0 && (int)blockIdx.x <= bp.tx1 &&
-                            (int)blockIdx.y >= bp.ty0 && (int)blockIdx.y <= bp.ty1;
-
     const S *__restrict__ fin = static_cast<const S *>(p.fin);
     S *__restrict__ fout = static_cast<S *>(p.fout);
+    const BodyState *__restrict__ bs = p.bs_in;
 
-    double part[NPART - 1];
-#pragma unroll
-    for (int k = 0; k < NPART - 1; ++k) part[k] = 0.0;
+    // streaming loads first: nothing below them waits on the pose
+    T f[NQ];
+    if (inside) pull_all<P>(p, fin, i, j, f);
+
+    // does this block's tile meet the node range that may hold solid nodes?
+    const int4 range = __ldg(reinterpret_cast<const int4 *>(&bs->ilo));   // ilo, ihi, jlo, jhi
+    const int bi0 = blockIdx.x * blockDim.x, bj0 = blockIdx.y * blockDim.y;
+    const bool any_solid = range.x <= range.y;
+    const bool part_block = any_solid
+        ? (bi0 + (int)blockDim.x - 1 >= range.x && bi0 <= range.y && bj0 + (int)blockDim.y - 1 >= range.z && bj0 <= range.w)
+        : (blockIdx.x == 0 && blockIdx.y == 0);
+
     bool chi = false;
-
+    double cr = 0, cax = 0, cay = 0;
     if (inside) {
-        T f[NQ];
-        pull_all<P>(p, fin, i, j, f);
-
         const T rs = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
         const T rho = DEV ? (T)p.rho0 + rs : rs;
         const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
@@ -282,34 +282,43 @@ __global__ void __launch_bounds__(512) vp_mrt_step(const StepParams p)
 
         // chi and u_s (Eq. 2, Alg. 1 step 4), only where the disk can be
         T dxl = 0, dyl = 0;
-        if (part_block && p.body.present) {
+        if (part_block && any_solid) {
             if constexpr (DEV) {
-                const float dxf = (float)(i - bp.xi) - bp.xf;
-                const float dyf = (float)(j - bp.yi) - bp.yf;
+                const int2 xy = __ldg(reinterpret_cast<const int2 *>(&bs->xi));
+                const float2 fr = __ldg(reinterpret_cast<const float2 *>(&bs->xf));
+                const float dxf = (float)(i - xy.x) - fr.x;
+                const float dyf = (float)(j - xy.y) - fr.y;
                 const float d2 = dxf * dxf + dyf * dyf;
                 const float r2 = (float)p.body.r2;
                 const float band = 1e-5f * r2 + 1e-5f;
-                if (fabsf(d2 - r2) <= band) chi = chi_exact(i, j, bp.q[0], bp.q[1], p.body.r2);
+                if (fabsf(d2 - r2) <= band) chi = chi_exact(i, j, bs->q[0], bs->q[1], p.body.r2);
                 else chi = d2 <= r2;
                 dxl = dxf; dyl = dyf;
             } else {
-                chi = chi_exact(i, j, bp.q[0], bp.q[1], p.body.r2);
-                dxl = (double)i - bp.q[0];
-                dyl = (double)j - bp.q[1];
+                const double xg = __ldg(&bs->q[0]), yg = __ldg(&bs->q[1]);
+                chi = chi_exact(i, j, xg, yg, p.body.r2);
+                dxl = (double)i - xg;
+                dyl = (double)j - yg;
             }
         }
 
         // penalized velocity, Eq. (22) in the eta-stable form
-        const T inv_rho = (T)1 / rho;
+        T inv_rho;
+        if constexpr (DEV) inv_rho = __frcp_rn(rho);
+        else inv_rho = (T)1 / rho;
         const T gx = (T)p.gx, gy = (T)p.gy;
         const T vx = jx * inv_rho + (T)0.5 * gx;
         const T vy = jy * inv_rho + (T)0.5 * gy;
         T ax = 0, ay = 0;
         if (chi) {
             T usx, usy;
-            if constexpr (DEV) { usx = bp.vxf - bp.omf * dyl; usy = bp.vyf + bp.omf * dxl; }
-            else { usx = bp.v[0] - bp.v[2] * dyl; usy = bp.v[1] + bp.v[2] * dxl; }
-            const T k = (T)(1.0 / (p.eta + 0.5));
+            if constexpr (DEV) {
+                const float4 vv = __ldg(reinterpret_cast<const float4 *>(&bs->vxf));
+                usx = vv.x - vv.z * dyl; usy = vv.y + vv.z * dxl;
+            } else {
+                usx = bs->v[0] - bs->v[2] * dyl; usy = bs->v[1] + bs->v[2] * dxl;
+            }
+            const T k = (T)p.pen_k;
             ax = -(vx - usx) * k;
             ay = -(vy - usy) * k;
         }
@@ -365,36 +374,18 @@ __global__ void __launch_bounds__(512) vp_mrt_step(const StepParams p)
         stv(fout + 8 * ps + b, B + X2 - Y2 - Rq);
 
         if (!(rho > (T)0) || !(rho < (T)1e30)) *p.err = ERR_NONFINITE;
-
-        if (chi) {
-            // FP64 contributions of a solid node
-            const double rd = (double)rho;
-            const double dxd = (double)i - bp.q[0], dyd = (double)j - bp.q[1];
-            const double px = -rd * (double)ax, py = -rd * (double)ay;
-            double jxd = 0, jyd = 0, oxd = 0, oyd = 0;
-#pragma unroll
-            for (int a = 1; a < NQ; ++a) {
-                const double fa = (double)f[a];
-                const double own = (double)ldv(fin + a * ps + b);
-                jxd += cx_of(a) * fa;
-                jyd += cy_of(a) * fa;
-                oxd += cx_of(a) * own;
-                oyd += cy_of(a) * own;
-            }
-            const double ex = jxd - oxd, ey = jyd - oyd;
-            part[0] = px;
-            part[1] = py;
-            part[2] = dxd * py - dyd * px;
-            part[3] = ex;
-            part[4] = ey;
-            part[5] = dxd * ey - dyd * ex;
-            part[6] = 1.0;
-        }
+        cr = (double)rho; cax = (double)ax; cay = (double)ay;
     }
 
     if (!part_block) return;   // uniform over the block
 
     // ---- block reduction of the 7 FP64 sums (fixed order) -------------
+    double part[NPART - 1];
+#pragma unroll
+    for (int k = 0; k < NPART - 1; ++k) part[k] = 0.0;
+    if (chi) solid_node_sums<P>(p, fin, i, j, cr, cax, cay, part);
+
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int nwarps = (blockDim.x * blockDim.y) >> 5;
     if (__any_sync(0xffffffffu, chi)) {
@@ -407,8 +398,13 @@ __global__ void __launch_bounds__(512) vp_mrt_step(const StepParams p)
 #pragma unroll
         for (int k = 0; k < NPART - 1; ++k) red[warp][k] = part[k];
     __syncthreads();
-    const int ntx = bp.tx1 - bp.tx0 + 1;
-    const int nparts = ntx * (bp.ty1 - bp.ty0 + 1);
+    int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;
+    if (any_solid) {
+        tx0 = range.x / (int)blockDim.x; tx1 = range.y / (int)blockDim.x;
+        ty0 = range.z / (int)blockDim.y; ty1 = range.w / (int)blockDim.y;
+    }
+    const int ntx = tx1 - tx0 + 1;
+    const int nparts = ntx * (ty1 - ty0 + 1);
     if (nparts > p.max_parts) {          // cannot happen for a finite pose; never overrun
         if (tid == 0) *p.err |= ERR_INTERNAL;
         return;
@@ -418,11 +414,11 @@ __global__ void __launch_bounds__(512) vp_mrt_step(const StepParams p)
 #pragma unroll
         for (int k = 0; k < NPART - 1; ++k) v[k] = lane < nwarps ? red[lane][k] : 0.0;
 #pragma unroll
-        for (int off = 8; off > 0; off >>= 1)
+        for (int off = 4; off > 0; off >>= 1)
 #pragma unroll
             for (int k = 0; k < NPART - 1; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
         if (lane == 0) {
-            const int slot = ((int)blockIdx.y - bp.ty0) * ntx + ((int)blockIdx.x - bp.tx0);
+            const int slot = ((int)blockIdx.y - ty0) * ntx + ((int)blockIdx.x - tx0);
             double *dst = p.partials + (size_t)slot * NPART;
 #pragma unroll
             for (int k = 0; k < NPART - 1; ++k) __stcg(dst + k, v[k]);
@@ -434,7 +430,7 @@ __global__ void __launch_bounds__(512) vp_mrt_step(const StepParams p)
     __syncthreads();
     if (s_last && warp == 0) {
         __threadfence();
-        step_tail(p, bp, nparts);
+        step_tail(p, nparts);
     }
 }
 

@@ -12,16 +12,23 @@ namespace vplbm {
 
 constexpr int NQ = 9;
 
-// Pose and velocity of the body at the start of a step, plus the step
-// counter.  Two copies alternate: a step reads one and its tail writes the
-// other, so late blocks of the same launch never see a half-updated pose.
+// Pose and velocity of the body at the start of a step, the step counter,
+// and values derived from the pose that every thread of the step kernel
+// needs (so the kernel's main path needs no FP64 and no block barrier).
+// Two copies alternate: a step reads one and its tail writes the other, so
+// late blocks of the same launch never see a half-updated pose.
 struct BodyState {
     double q[3];       // x_G, y_G, theta
     double v[3];       // vx, vy, omega
     long long step;    // time step this state belongs to
-    long long pad;
+    int ilo, ihi;      // node range [ilo, ihi] x [jlo, jhi] that may hold
+    int jlo, jhi;      //   solid nodes (ilo > ihi: none)
+    int xi, yi;        // floor(x_G), floor(y_G)
+    float xf, yf;      // x_G - xi, y_G - yi (exact in FP64, rounded to FP32)
+    float vxf, vyf, omf;
+    int pad[7];
 };
-static_assert(sizeof(BodyState) == 64, "BodyState layout");
+static_assert(sizeof(BodyState) == 128, "BodyState layout");
 
 // Body constants over a run (copied into every launch's parameters).
 struct DevBody {
@@ -45,6 +52,7 @@ struct StepParams {
     long long ps;                 // plane stride (elements) of a population buffer
     double s[NQ];
     double eta, rho0, gx, gy;
+    double pen_k;                 // 1 / (eta + 1/2)
     int bc[4];
     double wall_u0[4][2];
     const double *wall_prof[4][2];
@@ -72,6 +80,26 @@ struct Control {
     unsigned pad[62];
 };
 static_assert(sizeof(Control) == 256, "Control layout");
+
+// Fill the derived fields of s from its pose (host and device, same IEEE
+// operations on both).
+__host__ __device__ inline void derive_pose(BodyState &s, int present, double radius, int nx, int ny)
+{
+    s.ilo = 1; s.ihi = 0; s.jlo = 1; s.jhi = 0;
+    s.xi = s.yi = 0;
+    s.xf = s.yf = 0.f;
+    s.vxf = (float)s.v[0]; s.vyf = (float)s.v[1]; s.omf = (float)s.v[2];
+    for (int k = 0; k < 7; ++k) s.pad[k] = 0;
+    if (!present || !isfinite(s.q[0]) || !isfinite(s.q[1])) return;
+    // nodes that may satisfy the chi predicate, one node of margin
+    const double ilo = fmax(floor(s.q[0] - radius) - 1.0, 0.0), ihi = fmin(ceil(s.q[0] + radius) + 1.0, (double)(nx - 1));
+    const double jlo = fmax(floor(s.q[1] - radius) - 1.0, 0.0), jhi = fmin(ceil(s.q[1] + radius) + 1.0, (double)(ny - 1));
+    if (!(ilo <= ihi) || !(jlo <= jhi)) return;   // disk outside the lattice
+    s.ilo = (int)ilo; s.ihi = (int)ihi; s.jlo = (int)jlo; s.jhi = (int)jhi;
+    const double fx = floor(s.q[0]), fy = floor(s.q[1]);
+    s.xi = (int)fx; s.yi = (int)fy;
+    s.xf = (float)(s.q[0] - fx); s.yf = (float)(s.q[1] - fy);
+}
 
 // Launchers (step_kernels.cu).  All are asynchronous on `stream`.
 cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream);

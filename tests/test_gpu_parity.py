@@ -97,11 +97,16 @@ def test_channel_fixed_disk_fp64_full_run():
     gpu, orc = make_pair(p, "f64")
     gpu.step(p["steps"])
     orc.step(p["steps"])
-    assert dev_err(gpu.populations(), orc.populations()) < 1e-12
     gr, gx, gy = gpu.fields()
     orr, ox, oy = orc.fields()
-    assert rel_err(gr - 1, orr - 1) < 1e-12
-    assert rel_err(gx, ox) < 1e-12 and rel_err(gy, oy) < 1e-12
+    errs = {"f": rel_err(gpu.populations(), orc.populations()), "rho": rel_err(gr, orr),
+            "ux": rel_err(gx, ox), "uy": rel_err(gy, oy), "rho-1": rel_err(gr - 1, orr - 1)}
+    print("fp64 channel 2000 steps:", errs)
+    # fields and populations 1e-12 of their scale; the density deviation
+    # (10^3 smaller than rho) 1e-10 of its own scale
+    assert errs["f"] < 1e-12 and errs["rho"] < 1e-12
+    assert errs["ux"] < 1e-12 and errs["uy"] < 1e-12
+    assert errs["rho-1"] < 1e-10
     hg, ho = gpu.history(), orc.history()
     assert np.max(np.abs(hg[:, REC["cd"]] - ho[:, REC["cd"]])) < 1e-10
     assert np.max(np.abs(hg[:, REC["cl"]] - ho[:, REC["cl"]])) < 1e-10
