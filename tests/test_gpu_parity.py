@@ -168,7 +168,7 @@ def test_full_size_one_step_every_launch_shape(name):
 
 
 def vp_shapes():
-    return [(128, 2), (256, 1), (64, 4), (32, 8), (128, 1), (256, 2), (64, 2)]
+    return [(128, 2), (256, 1), (64, 4), (32, 8), (128, 1), (64, 2), (32, 4)]
 
 
 def test_fp64_full_size_two_steps():
