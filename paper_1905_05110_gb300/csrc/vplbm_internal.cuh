@@ -4,6 +4,7 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "vplbm.h"
@@ -18,17 +19,23 @@ constexpr int NQ = 9;
 // Two copies alternate: a step reads one and its tail writes the other, so
 // late blocks of the same launch never see a half-updated pose.
 struct BodyState {
-    double q[3];       // x_G, y_G, theta
-    double v[3];       // vx, vy, omega
-    long long step;    // time step this state belongs to
-    int ilo, ihi;      // node range [ilo, ihi] x [jlo, jhi] that may hold
-    int jlo, jhi;      //   solid nodes (ilo > ihi: none)
-    int xi, yi;        // floor(x_G), floor(y_G)
-    float xf, yf;      // x_G - xi, y_G - yi (exact in FP64, rounded to FP32)
-    float vxf, vyf, omf;
-    int pad[7];
+    double q[3];       // x_G, y_G, theta                      (offset 0)
+    double v[3];       // vx, vy, omega                        (24)
+    long long step;    // time step this state belongs to      (48)
+    long long pad0;    //                                      (56)
+    int ilo, ihi;      // node range [ilo, ihi] x [jlo, jhi]   (64, read as one int4)
+    int jlo, jhi;      //   that may hold solid nodes (ilo > ihi: none)
+    int xi, yi;        // floor(x_G), floor(y_G)               (80, int2)
+    float xf, yf;      // x_G - xi, y_G - yi, rounded to FP32   (88, float2)
+    float vxf, vyf, omf, pad1;   // velocities in FP32          (96, float4)
+    int pad[4];        //                                      (112)
 };
 static_assert(sizeof(BodyState) == 128, "BodyState layout");
+// the step kernel reads these groups with vector loads
+static_assert(offsetof(BodyState, ilo) % 16 == 0, "int4 load of the solid range");
+static_assert(offsetof(BodyState, xi) % 8 == 0, "int2 load of floor(x_G)");
+static_assert(offsetof(BodyState, xf) % 8 == 0, "float2 load of the fractions");
+static_assert(offsetof(BodyState, vxf) % 16 == 0, "float4 load of the velocities");
 
 // Body constants over a run (copied into every launch's parameters).
 struct DevBody {
@@ -89,7 +96,9 @@ __host__ __device__ inline void derive_pose(BodyState &s, int present, double ra
     s.xi = s.yi = 0;
     s.xf = s.yf = 0.f;
     s.vxf = (float)s.v[0]; s.vyf = (float)s.v[1]; s.omf = (float)s.v[2];
-    for (int k = 0; k < 7; ++k) s.pad[k] = 0;
+    s.pad0 = 0;
+    s.pad1 = 0.f;
+    for (int k = 0; k < 4; ++k) s.pad[k] = 0;
     if (!present || !isfinite(s.q[0]) || !isfinite(s.q[1])) return;
     // nodes that may satisfy the chi predicate, one node of margin
     const double ilo = fmax(floor(s.q[0] - radius) - 1.0, 0.0), ihi = fmin(ceil(s.q[0] + radius) + 1.0, (double)(nx - 1));
