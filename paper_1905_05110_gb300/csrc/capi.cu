@@ -236,6 +236,11 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     p.rho0 = lat->rho0;
     p.gx = lat->gx;
     p.gy = lat->gy;
+    for (int k = 0; k < 9; ++k) p.sf[k] = (float)lat->s[k];
+    p.rho0f = (float)lat->rho0;
+    p.gxf = (float)lat->gx;
+    p.gyf = (float)lat->gy;
+    p.pen_kf = (float)p.pen_k;
     // wall velocity profiles: [side][comp][maxlen]
     const int maxlen = lat->nx > lat->ny ? lat->nx : lat->ny;
     std::vector<double> prof((size_t)8 * maxlen, 0.0);
@@ -267,6 +272,7 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
         b.dof_mask = body->dof_mask;
         b.radius = body->radius;
         b.r2 = body->radius * body->radius;
+        p.r2f = (float)b.r2;
         b.amp = body->amp;
         b.freq = body->freq;
         b.phase = body->phase;

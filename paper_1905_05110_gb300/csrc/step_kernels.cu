@@ -50,6 +50,12 @@ __host__ __device__ constexpr double w_of(int a) { return a == 0 ? 4.0 / 9.0 : (
 static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 && opp_of(4) == 2, "opp axis");
 static_assert(opp_of(5) == 7 && opp_of(6) == 8 && opp_of(7) == 5 && opp_of(8) == 6, "opp diag");
 
+// A parameter in the kernel's arithmetic type: the FP64 value for the FP64
+// kernel, the host-rounded FP32 copy otherwise (no conversion on the device).
+template <typename T> __device__ __forceinline__ T par(double d, float f);
+template <> __device__ __forceinline__ double par<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float par<float>(double, float f) { return f; }
+
 __device__ __forceinline__ double wall_u(const StepParams &p, int side, int comp, int k)
 {
     const double *prof = p.wall_prof[side][comp];
@@ -273,10 +279,10 @@ __global__ void __launch_bounds__(256, 4) vp_mrt_step(const StepParams p)
         : (blockIdx.x == 0 && blockIdx.y == 0);
 
     bool chi = false;
-    double cr = 0, cax = 0, cay = 0;
+    T cr = 0, cax = 0, cay = 0;   // kept for the solid-node sums (converted there)
     if (inside) {
         const T rs = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-        const T rho = DEV ? (T)p.rho0 + rs : rs;
+        const T rho = DEV ? par<T>(p.rho0, p.rho0f) + rs : rs;
         const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
         const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
 
@@ -289,7 +295,7 @@ __global__ void __launch_bounds__(256, 4) vp_mrt_step(const StepParams p)
                 const float dxf = (float)(i - xy.x) - fr.x;
                 const float dyf = (float)(j - xy.y) - fr.y;
                 const float d2 = dxf * dxf + dyf * dyf;
-                const float r2 = (float)p.body.r2;
+                const float r2 = p.r2f;
                 const float band = 1e-5f * r2 + 1e-5f;
                 if (fabsf(d2 - r2) <= band) chi = chi_exact(i, j, bs->q[0], bs->q[1], p.body.r2);
                 else chi = d2 <= r2;
@@ -306,7 +312,7 @@ __global__ void __launch_bounds__(256, 4) vp_mrt_step(const StepParams p)
         T inv_rho;
         if constexpr (DEV) inv_rho = __frcp_rn(rho);
         else inv_rho = (T)1 / rho;
-        const T gx = (T)p.gx, gy = (T)p.gy;
+        const T gx = par<T>(p.gx, p.gxf), gy = par<T>(p.gy, p.gyf);
         const T vx = jx * inv_rho + (T)0.5 * gx;
         const T vy = jy * inv_rho + (T)0.5 * gy;
         T ax = 0, ay = 0;
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(256, 4) vp_mrt_step(const StepParams p)
             } else {
                 usx = bs->v[0] - bs->v[2] * dyl; usy = bs->v[1] + bs->v[2] * dxl;
             }
-            const T k = (T)p.pen_k;
+            const T k = par<T>(p.pen_k, p.pen_kf);
             ax = -(vx - usx) * k;
             ay = -(vy - usy) * k;
         }
@@ -339,7 +345,8 @@ __global__ void __launch_bounds__(256, 4) vp_mrt_step(const StepParams p)
 
         const T u2r = rho * (ux * ux + uy * uy);
         const T uG = ux * Gx + uy * Gy;
-        const T s1 = (T)p.s[1], s2 = (T)p.s[2], s4 = (T)p.s[4], s6 = (T)p.s[6], s7 = (T)p.s[7], s8 = (T)p.s[8];
+        const T s1 = par<T>(p.s[1], p.sf[1]), s2 = par<T>(p.s[2], p.sf[2]), s4 = par<T>(p.s[4], p.sf[4]);
+        const T s6 = par<T>(p.s[6], p.sf[6]), s7 = par<T>(p.s[7], p.sf[7]), s8 = par<T>(p.s[8], p.sf[8]);
 
         const T e_s = e - s1 * (e - ((T)-2 * rs + (T)3 * u2r)) + ((T)1 - (T)0.5 * s1) * ((T)6 * uG);
         const T ep_s = ep - s2 * (ep - (rs - (T)3 * u2r)) - ((T)1 - (T)0.5 * s2) * ((T)6 * uG);
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(256, 4) vp_mrt_step(const StepParams p)
         stv(fout + 8 * ps + b, B + X2 - Y2 - Rq);
 
         if (!(rho > (T)0) || !(rho < (T)1e30)) *p.err = ERR_NONFINITE;
-        cr = (double)rho; cax = (double)ax; cay = (double)ay;
+        cr = rho; cax = ax; cay = ay;
     }
 
     if (!part_block) return;   // uniform over the block
@@ -383,7 +390,7 @@ __global__ void __launch_bounds__(256, 4) vp_mrt_step(const StepParams p)
     double part[NPART - 1];
 #pragma unroll
     for (int k = 0; k < NPART - 1; ++k) part[k] = 0.0;
-    if (chi) solid_node_sums<P>(p, fin, i, j, cr, cax, cay, part);
+    if (chi) solid_node_sums<P>(p, fin, i, j, (double)cr, (double)cax, (double)cay, part);
 
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;

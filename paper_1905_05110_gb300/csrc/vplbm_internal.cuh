@@ -60,6 +60,10 @@ struct StepParams {
     double s[NQ];
     double eta, rho0, gx, gy;
     double pen_k;                 // 1 / (eta + 1/2)
+    // FP32 copies for the FP32/FP16 kernels (a double->float conversion
+    // runs on the FP64 pipe, which is narrow on GB300)
+    float sf[NQ];
+    float rho0f, gxf, gyf, pen_kf, r2f;
     int bc[4];
     double wall_u0[4][2];
     const double *wall_prof[4][2];
