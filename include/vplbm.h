@@ -220,6 +220,55 @@ vplbm_status vplbm_get_launch_count(vplbm_ctx *ctx, long long *launches);
 vplbm_status vplbm_save(vplbm_ctx *ctx, const char *path);
 vplbm_status vplbm_load(vplbm_ctx *ctx, const char *path);
 
+/* ---- allocation-free stepping --------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * must not allocate device memory while they run: a host application whose
+ * device memory belongs to another framework's caching allocator (an extra
+ * cudaMalloc would fail or fragment that pool), or a control loop with a
+ * fixed memory budget that forbids allocation after start-up, since
+ * cudaMalloc and cudaFree can synchronize the device and take unbounded time.
+ *
+ * vplbm_step_noalloc queues nsteps time steps -- the same fused step kernel
+ * as vplbm_step -- on buffers the caller owns, and allocates nothing: the
+ * kernel's scratch (block force partials, tail ticket, error word, internal
+ * pose records) is one static device array of about 260 KB that every GPU
+ * loading this library holds until the process exits.  Its device address is
+ * looked up on the first call on each device (with that device current), so
+ * make that first call before any stream capture.  All calls share the
+ * array: calls whose work overlaps on the GPU (other streams, other threads)
+ * race on it and must be serialized by the caller.
+ *
+ *  populations_dev[0]  device buffer holding the state in storage layout:
+ *                      9 planes, plane stride = nx*ny rounded up to a
+ *                      multiple of 128 elements, element (a, j, i) at
+ *                      a*stride + j*nx + i; FP64 full f for VPLBM_F64,
+ *                      FP32 / FP16 of f_a - w_a rho0 for the _DEV kinds.
+ *  populations_dev[1]  second buffer of the same size; after the call the
+ *                      state is in populations_dev[nsteps & 1].
+ *  state_dev           device vplbm_body_state, read at the start, written at
+ *                      the end (pose and velocity after the steps, step
+ *                      counter advanced by nsteps, error != 0 if a density
+ *                      became non-positive or non-finite).
+ *  history_dev         NULL, or a device ring of history_capacity records;
+ *                      the record of step n goes to slot n % capacity.
+ * Walls take uniform velocities only (bc[].ux_profile/uy_profile must be
+ * NULL: VPLBM_EUNSUPPORTED).  A disk too large for the fixed scratch (radius
+ * above about 450 lattice units) is rejected with VPLBM_ERANGE before any
+ * device work.  Asynchronous on cuda_stream; read state_dev after
+ * synchronizing. */
+typedef struct {
+    double q[3];      /* x_G, y_G, theta */
+    double v[3];      /* vx, vy, omega */
+    long long step;   /* step counter: time of q and v */
+    int error;        /* output: non-zero if the call saw a non-finite density */
+    int pad;
+} vplbm_body_state;
+
+vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const vplbm_body_desc *body,
+                                void *const populations_dev[2], vplbm_body_state *state_dev,
+                                vplbm_record *history_dev, long long history_capacity,
+                                long long nsteps, void *cuda_stream);
+
 /* Message of the last failed call on this thread (never NULL). */
 const char *vplbm_last_error(void);
 

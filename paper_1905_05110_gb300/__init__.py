@@ -26,6 +26,7 @@ __all__ = [
     "vplbm_get_populations", "vplbm_get_fields", "vplbm_get_fields_dev", "vplbm_get_history",
     "vplbm_get_body", "vplbm_set_launch", "vplbm_get_launch", "vplbm_autotune",
     "vplbm_get_launch_count", "vplbm_save", "vplbm_load", "vplbm_last_error", "vplbm_version",
+    "vplbm_step_noalloc", "BodyState",
     "EXPORTED_SYMBOLS", "RECORD_FIELDS",
 ]
 
@@ -86,6 +87,11 @@ class Buffers(C.Structure):
                 ("profiles_dev", C.c_void_p), ("control_dev", C.c_void_p)]
 
 
+class BodyState(C.Structure):
+    _fields_ = [("q", C.c_double * 3), ("v", C.c_double * 3), ("step", C.c_longlong),
+                ("error", C.c_int), ("pad", C.c_int)]
+
+
 _D = C.POINTER(C.c_double)
 _CTX = C.c_void_p
 
@@ -113,6 +119,8 @@ _SIGS = {
     "vplbm_get_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_longlong)]),
     "vplbm_save": (C.c_int, [_CTX, C.c_char_p]),
     "vplbm_load": (C.c_int, [_CTX, C.c_char_p]),
+    "vplbm_step_noalloc": (C.c_int, [C.POINTER(LatticeDesc), C.POINTER(BodyDesc), C.c_void_p * 2,
+                                     C.c_void_p, C.c_void_p, C.c_longlong, C.c_longlong, C.c_void_p]),
     "vplbm_last_error": (C.c_char_p, []),
     "vplbm_version": (C.c_char_p, []),
 }
@@ -316,6 +324,15 @@ def vplbm_get_launch_count(ctx) -> int:
     n = C.c_longlong()
     _check(load_library().vplbm_get_launch_count(ctx, C.byref(n)))
     return int(n.value)
+
+
+def vplbm_step_noalloc(lat: LatticeDesc, body: BodyDesc | None, populations_ptrs, state_ptr: int,
+                       history_ptr: int | None, history_capacity: int, nsteps: int, stream: int = 0):
+    """Allocation-free steps on caller-owned device buffers (see include/vplbm.h)."""
+    pops = (C.c_void_p * 2)(int(populations_ptrs[0]), int(populations_ptrs[1]))
+    _check(load_library().vplbm_step_noalloc(C.byref(lat), _byref(body), pops, C.c_void_p(state_ptr),
+                                             C.c_void_p(history_ptr or 0), int(history_capacity),
+                                             int(nsteps), C.c_void_p(stream)))
 
 
 def vplbm_save(ctx, path: str):

@@ -88,6 +88,11 @@ uint16_t double_to_half(double x)
 
 }  // namespace
 
+namespace vplbm {
+// Error reporting for the other translation units of the library.
+vplbm_status report_error(vplbm_status st, const char *msg) { return fail(st, "%s", msg); }
+}  // namespace vplbm
+
 struct vplbm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;        // caller's stream
