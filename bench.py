@@ -36,10 +36,15 @@ import workloads as wl  # noqa: E402
 METRIC = "D2Q9 VP-MRT MLUPS & % HBM roofline; FP32/batched/adjoint vs FP64 plain, same GPU"
 UNIT = "MLUPS"
 BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36}   # 9 loads + 9 stores of one population
-KERNEL_NAME = {"f64": "vp_mrt_step<0>", "f32": "vp_mrt_step<1>", "f16": "vp_mrt_step<2>"}
+PREC_ID = {"f64": 0, "f32": 1, "f16": 2}
 FALLBACK_HBM_GBS = 6800.0
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "vp_mrt_step_f32_oscillating_2048x1024.md")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_1905_05110_gb300", "csrc", "step_kernels.cu")
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+CSRC = os.path.join(ROOT, "paper_1905_05110_gb300", "csrc")
+
+
+def kernel_name(prec: str, launch) -> str:
+    base = "vp_mrt_step_tma" if tuple(launch) == (0, 0) else "vp_mrt_step"
+    return f"{base}<{PREC_ID[prec]}>"
 
 
 def workload(name: str) -> dict:
@@ -67,14 +72,22 @@ def measured_peak():
 
 
 def kernel_source_hash() -> str:
-    with open(KERNEL_SOURCE, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """Hash of every CUDA source of the library (any change invalidates counters)."""
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(CSRC, name), "rb") as fh:
+                h.update(name.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
-def profiled_traffic(nodes: int):
+def profiled_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if still valid."""
+    stem = kernel.replace("<", "_").replace(">", "")
+    path = os.path.join(PROFILE_DIR, f"{stem}_{workload}.md")
     try:
-        text = open(PROFILE_TRAFFIC).read()
+        text = open(path).read()
     except OSError:
         return None
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
@@ -256,10 +269,12 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peak()
     per_launch = dt / args.steps
     achieved = BYTES_PER_NODE[prec] * nodes / per_launch / 1e9
-    traffic = profiled_traffic(nodes) if prec == "f32" and args.workload == "oscillating_2048x1024" else None
+    kname = kernel_name(prec, (bx, by))
+    traffic = profiled_traffic(kname, args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                "kernel": KERNEL_NAME[prec], "algorithmic_bytes_per_launch": BYTES_PER_NODE[prec] * nodes}
+                "kernel": kname, "algorithmic_bytes_per_launch": BYTES_PER_NODE[prec] * nodes,
+                "kernel_source_sha256_16": kernel_source_hash()}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None

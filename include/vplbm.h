@@ -203,13 +203,24 @@ vplbm_status vplbm_get_history(vplbm_ctx *ctx, long long first, long long count,
 vplbm_status vplbm_get_body(vplbm_ctx *ctx, double q[3], double v[3], long long *step);
 
 /* Launch shape of the step kernel: block_x * block_y threads per block,
- * block_x a multiple of 32, block_x * block_y in {128, 256}. */
+ * block_x a multiple of 32, block_x * block_y in {128, 256}; or (0, 0) for
+ * the TMA-staged persistent kernel (FP32/FP16 storage, nx * element size a
+ * multiple of 16 bytes, nx >= 136 (FP32) / 144 (FP16), ny >= 6), which a new
+ * context selects whenever the lattice allows it. */
 vplbm_status vplbm_set_launch(vplbm_ctx *ctx, int block_x, int block_y);
 vplbm_status vplbm_get_launch(vplbm_ctx *ctx, int *block_x, int *block_y);
 
 /* Time every candidate launch shape on the current state (the state is
  * saved and restored around the trials) and keep the fastest. */
 vplbm_status vplbm_autotune(vplbm_ctx *ctx, int steps_per_trial);
+
+/* Test hook for the bounded waits of the TMA-staged kernel: when enabled,
+ * the first shared-memory stage of every block waits for 16 bytes more than
+ * its tensor copies deliver, so the wait gives up after about one second,
+ * the block leaves once its copies have landed, and the next vplbm_sync
+ * returns VPLBM_ETIMEOUT; the context stays usable.  Disable to resume.
+ * VPLBM_EUNSUPPORTED unless the TMA-staged kernel is selected. */
+vplbm_status vplbm_inject_wait_timeout(vplbm_ctx *ctx, int enable);
 
 /* Number of step-kernel launches made by vplbm_step since creation. */
 vplbm_status vplbm_get_launch_count(vplbm_ctx *ctx, long long *launches);

@@ -26,7 +26,7 @@ __all__ = [
     "vplbm_get_populations", "vplbm_get_fields", "vplbm_get_fields_dev", "vplbm_get_history",
     "vplbm_get_body", "vplbm_set_launch", "vplbm_get_launch", "vplbm_autotune",
     "vplbm_get_launch_count", "vplbm_save", "vplbm_load", "vplbm_last_error", "vplbm_version",
-    "vplbm_step_noalloc", "BodyState",
+    "vplbm_step_noalloc", "BodyState", "vplbm_inject_wait_timeout",
     "EXPORTED_SYMBOLS", "RECORD_FIELDS",
 ]
 
@@ -117,6 +117,7 @@ _SIGS = {
     "vplbm_get_launch": (C.c_int, [_CTX, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "vplbm_autotune": (C.c_int, [_CTX, C.c_int]),
     "vplbm_get_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_longlong)]),
+    "vplbm_inject_wait_timeout": (C.c_int, [_CTX, C.c_int]),
     "vplbm_save": (C.c_int, [_CTX, C.c_char_p]),
     "vplbm_load": (C.c_int, [_CTX, C.c_char_p]),
     "vplbm_step_noalloc": (C.c_int, [C.POINTER(LatticeDesc), C.POINTER(BodyDesc), C.c_void_p * 2,
@@ -318,6 +319,10 @@ def vplbm_get_launch(ctx):
 
 def vplbm_autotune(ctx, steps_per_trial: int = 20):
     _check(load_library().vplbm_autotune(ctx, int(steps_per_trial)))
+
+
+def vplbm_inject_wait_timeout(ctx, enable: bool):
+    _check(load_library().vplbm_inject_wait_timeout(ctx, int(bool(enable))))
 
 
 def vplbm_get_launch_count(ctx) -> int:

@@ -116,8 +116,13 @@ struct vplbm_ctx {
     long long nstep = 0;
     int bx = 128, by = 2;
     cudaGraphExec_t graph = nullptr;
-    int graph_bx = 0, graph_by = 0;
+    int graph_bx = -1, graph_by = -1;
     long long launches = 0;
+    // TMA-staged kernel (FP32/FP16 storage): tensor maps of the two
+    // population buffers as sources, persistent grid size
+    bool tma_ok = false;
+    CUtensorMap tmap[2];
+    int tma_grid = 0;
 };
 
 namespace {
@@ -167,7 +172,8 @@ void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long 
 {
     const long long n = (long long)lat->nx * lat->ny;
     const long long ps = (long long)round_up((size_t)n, 128);
-    long long parts = 1;
+    long long parts = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr,
+                                           TMA_TILE_W, TMA_TILE_H);
     for (int k = 0; k < N_SHAPES; ++k) {
         const long long m = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr,
                                                  SHAPES[k][0], SHAPES[k][1]);
@@ -205,6 +211,58 @@ StepParams params_for(const vplbm_ctx *c, long long step)
     p.bs_in = c->bs + par;
     p.bs_out = c->bs + (par ^ 1);
     return p;
+}
+
+// One time step with the context's kernel choice (bx == 0: TMA-staged).
+cudaError_t launch_one(const vplbm_ctx *c, long long step, cudaStream_t stream)
+{
+    const StepParams p = params_for(c, step);
+    if (c->bx == 0) return launch_step_tma(c->precision, p, c->tmap[step & 1], c->tma_grid, stream);
+    return launch_step(c->precision, p, c->bx, c->by, stream);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor maps and grid of the TMA-staged kernel, when the lattice allows
+// it (row pitch a multiple of 16 bytes, lattice at least one box wide).
+void setup_tma(vplbm_ctx *c)
+{
+    c->tma_ok = false;
+    if (c->precision != VPLBM_F32_DEV && c->precision != VPLBM_F16_DEV) return;
+    const int es = (int)elem_size(c->precision);
+    const int halo = tma_halo(c->precision);
+    const int boxw = TMA_TILE_W + 2 * halo;
+    if ((c->nx * es) % 16 != 0 || c->nx < boxw || c->ny < TMA_BOX_H + 2) return;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        (void)cudaGetLastError();
+        return;
+    }
+    EncodeTiledFn encode = (EncodeTiledFn)fn;
+    const cuuint64_t dims[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)c->nx * es, (cuuint64_t)c->ps * es};
+    const cuuint32_t box[3] = {(cuuint32_t)boxw, (cuuint32_t)TMA_BOX_H, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt =
+        c->precision == VPLBM_F32_DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    for (int b = 0; b < 2; ++b) {
+        CUresult r = encode(&c->tmap[b], dt, 3, c->f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return;
+    }
+    int per_sm = 0, nsm = 0;
+    if (tma_prepare(c->precision, &per_sm) != cudaSuccess || per_sm < 1 ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    c->tma_grid = per_sm * nsm;
+    c->tma_ok = true;
 }
 
 // Reset step counter, body state and control word (after a new state).
@@ -300,6 +358,11 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     p.hist = c->hist;
     p.hist_cap = cap;
 
+    setup_tma(c);
+    if (c->tma_ok) {
+        c->bx = 0;
+        c->by = 0;
+    }
     // populations at rest
     StepParams q = params_for(c, 0);
     q.fout = c->f[0];
@@ -378,7 +441,7 @@ vplbm_status ensure_graph(vplbm_ctx *c)
     CUDA_TRY(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = cudaSuccess;
     for (int k = 0; k < GRAPH_STEPS && err == cudaSuccess; ++k)
-        err = launch_step(c->precision, params_for(c, k), c->bx, c->by, c->capture);
+        err = launch_one(c, k, c->capture);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c->capture, &g);
     if (err != cudaSuccess || e2 != cudaSuccess) {
@@ -404,7 +467,7 @@ vplbm_status step_impl(vplbm_ctx *c, long long n)
             c->launches += GRAPH_STEPS;
             n -= GRAPH_STEPS;
         } else {
-            CUDA_TRY(launch_step(c->precision, params_for(c, c->nstep), c->bx, c->by, c->stream));
+            CUDA_TRY(launch_one(c, c->nstep, c->stream));
             c->nstep += 1;
             c->launches += 1;
             n -= 1;
@@ -420,6 +483,7 @@ vplbm_status read_error(vplbm_ctx *c)
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (ctl.err & ERR_NONFINITE) return fail(VPLBM_ENONFINITE, "a density became non-positive or non-finite");
     if (ctl.err & ERR_INTERNAL) return fail(VPLBM_ECUDA, "internal reduction capacity exceeded");
+    if (ctl.err & ERR_TIMEOUT) return fail(VPLBM_ETIMEOUT, "a bounded wait for a tensor copy gave up");
     return VPLBM_OK;
 }
 
@@ -645,6 +709,12 @@ vplbm_status vplbm_get_body(vplbm_ctx *c, double q[3], double v[3], long long *s
 vplbm_status vplbm_set_launch(vplbm_ctx *c, int bx, int by)
 {
     if (!c) return fail(VPLBM_EINVAL, "context is NULL");
+    if (bx == 0 && by == 0) {
+        if (!c->tma_ok) return fail(VPLBM_EUNSUPPORTED, "the TMA-staged kernel needs FP32/FP16 storage and nx*elem a multiple of 16 bytes");
+        c->bx = 0;
+        c->by = 0;
+        return VPLBM_OK;
+    }
     const int t = bx * by;
     if (bx < 32 || bx % 32 || by < 1 || (t != 128 && t != 256))
         return fail(VPLBM_EINVAL, "launch shape %dx%d not allowed", bx, by);
@@ -660,6 +730,15 @@ vplbm_status vplbm_get_launch(vplbm_ctx *c, int *bx, int *by)
     if (!c) return fail(VPLBM_EINVAL, "context is NULL");
     if (bx) *bx = c->bx;
     if (by) *by = c->by;
+    return VPLBM_OK;
+}
+
+vplbm_status vplbm_inject_wait_timeout(vplbm_ctx *c, int enable)
+{
+    if (!c) return fail(VPLBM_EINVAL, "context is NULL");
+    if (enable && !(c->tma_ok && c->bx == 0)) return fail(VPLBM_EUNSUPPORTED, "the TMA-staged kernel is not selected");
+    c->base.tx_extra = enable ? 16u : 0u;
+    c->graph_bx = -1;   // recapture graphs with the new parameters
     return VPLBM_OK;
 }
 
@@ -689,7 +768,7 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     vplbm_status st = VPLBM_OK;
     float best = 1e30f;
-    int best_k = -1;
+    int best_k = -2;
     auto restore = [&]() -> cudaError_t {
         cudaError_t e = cudaMemcpyAsync(c->f[nstep0 & 1], save_f, c->pop_bytes, cudaMemcpyDeviceToDevice, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c->hist, save_h, hbytes, cudaMemcpyDeviceToDevice, c->stream);
@@ -707,13 +786,14 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
             st = fail(VPLBM_ECUDA, "autotune setup failed");
             break;
         }
-        for (int k = 0; k < N_SHAPES; ++k) {
-            if (vplbm_set_launch(c, SHAPES[k][0], SHAPES[k][1]) != VPLBM_OK) continue;
+        for (int k = -1; k < N_SHAPES; ++k) {
+            const int cbx = k < 0 ? 0 : SHAPES[k][0], cby = k < 0 ? 0 : SHAPES[k][1];
+            if (vplbm_set_launch(c, cbx, cby) != VPLBM_OK) continue;
             for (int rep = 0; rep < 2; ++rep) {   // first pass warms up
                 if (restore() != cudaSuccess) { st = fail(VPLBM_ECUDA, "autotune restore failed"); break; }
                 cudaEventRecord(e0, c->stream);
                 for (int s = 0; s < steps_per_trial && st == VPLBM_OK; ++s) {
-                    if (launch_step(c->precision, params_for(c, c->nstep), c->bx, c->by, c->stream) != cudaSuccess)
+                    if (launch_one(c, c->nstep, c->stream) != cudaSuccess)
                         st = fail(VPLBM_ECUDA, "autotune launch failed");
                     c->nstep++;
                 }
@@ -740,6 +820,9 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
     if (best_k >= 0) {
         c->bx = SHAPES[best_k][0];
         c->by = SHAPES[best_k][1];
+    } else if (best_k == -1 && best < 1e29f) {
+        c->bx = 0;
+        c->by = 0;
     } else {
         c->bx = bx0;
         c->by = by0;

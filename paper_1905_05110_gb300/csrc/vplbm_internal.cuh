@@ -2,6 +2,7 @@
 // Not part of the public ABI (include/vplbm.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
@@ -78,11 +79,13 @@ struct StepParams {
     int *err;
     vplbm_record *hist;
     long long hist_cap;
+    unsigned tx_extra;            // test hook: bytes the first TMA stage waits for in vain
 };
 
 // Error bits latched in the control word.
 constexpr int ERR_NONFINITE = 1;
 constexpr int ERR_INTERNAL = 2;
+constexpr int ERR_TIMEOUT = 4;
 
 // Control block: ticket counter and error word.
 struct Control {
@@ -120,6 +123,15 @@ cudaError_t launch_init_equilibrium(int precision, const StepParams &p, const do
                                     const double *ux_dev, const double *uy_dev, cudaStream_t stream);
 cudaError_t launch_fields(int precision, const StepParams &p, double *rho_dev, double *ux_dev,
                           double *uy_dev, cudaStream_t stream);
+
+// TMA-staged step (step_tma.cu), FP32/FP16 storage.  The tensor map
+// describes the source population buffer as (x: nx, y: ny, plane: 9).
+int tma_smem_bytes(int precision);
+int tma_halo(int precision);
+cudaError_t tma_prepare(int precision, int *blocks_per_sm);
+cudaError_t launch_step_tma(int precision, const StepParams &p, const CUtensorMap &map, int grid,
+                            cudaStream_t stream);
+constexpr int TMA_TILE_W = 128, TMA_TILE_H = 4, TMA_BOX_H = 4;
 
 // Largest number of blocks that can take part in the force reduction for
 // a disk of this radius under launch shape (bx, by) on an nx x ny lattice.

@@ -1,0 +1,422 @@
+// Device code shared by the step kernels: precision traits, the pull with
+// boundary rules, the per-node VP-MRT update (Eqs. 14-22), the solid-node
+// sums (Eqs. 25-27), the rigid-body update (Eqs. 23-24) and the tail.
+// Internal to the library; every function is inlined into its kernel.
+#pragma once
+
+#include <math.h>
+
+#include "vplbm_internal.cuh"
+
+namespace vplbm {
+namespace {
+
+// ---- precision traits -------------------------------------------------
+
+template <int P> struct Prec;
+template <> struct Prec<VPLBM_F64> { using S = double; using T = double; static constexpr bool DEV = false; };
+template <> struct Prec<VPLBM_F32_DEV> { using S = float; using T = float; static constexpr bool DEV = true; };
+template <> struct Prec<VPLBM_F16_DEV> { using S = __half; using T = float; static constexpr bool DEV = true; };
+
+__device__ __forceinline__ double ldv(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ldv(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ldv(const __half *p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ void stv(double *p, double x) { *p = x; }
+__device__ __forceinline__ void stv(float *p, float x) { *p = x; }
+__device__ __forceinline__ void stv(__half *p, float x) { *p = __float2half_rn(x); }
+
+// D2Q9 velocity set in the order of Eq. (10), weights of Eq. (13).
+__host__ __device__ constexpr int cx_of(int a) { return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0); }
+__host__ __device__ constexpr int cy_of(int a) { return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0); }
+__host__ __device__ constexpr int opp_of(int a) { return a == 0 ? 0 : (a <= 4 ? ((a + 1) % 4) + 1 : ((a - 5 + 2) % 4) + 5); }
+__host__ __device__ constexpr double w_of(int a) { return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 && opp_of(4) == 2, "opp axis");
+static_assert(opp_of(5) == 7 && opp_of(6) == 8 && opp_of(7) == 5 && opp_of(8) == 6, "opp diag");
+
+// A parameter in the kernel's arithmetic type: the FP64 value for the FP64
+// kernel, the host-rounded FP32 copy otherwise (no conversion on the device).
+template <typename T> __device__ __forceinline__ T par(double d, float f);
+template <> __device__ __forceinline__ double par<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float par<float>(double, float f) { return f; }
+
+__device__ __forceinline__ double wall_u(const StepParams &p, int side, int comp, int k)
+{
+    const double *prof = p.wall_prof[side][comp];
+    return prof ? prof[k] : p.wall_u0[side][comp];
+}
+
+// Pull of population a into edge node (i, j), with the boundary rules.
+template <int P>
+__device__ typename Prec<P>::T pull_edge(const StepParams &p, const typename Prec<P>::S *fin, int a, int i, int j)
+{
+    using T = typename Prec<P>::T;
+    const int nx = p.nx, ny = p.ny;
+    const long long ps = p.ps;
+    int si = i - cx_of(a);
+    int sj = j - cy_of(a);
+    if (sj < 0 || sj >= ny) {
+        const int side = sj < 0 ? VPLBM_SOUTH : VPLBM_NORTH;
+        const int kind = p.bc[side];
+        if (kind == VPLBM_BC_PERIODIC) {
+            sj = sj < 0 ? sj + ny : sj - ny;
+        } else {
+            T val = ldv(fin + opp_of(a) * ps + (long long)j * nx + i);
+            if (kind == VPLBM_BC_VELOCITY) {
+                double cu = cx_of(a) * wall_u(p, side, 0, i) + cy_of(a) * wall_u(p, side, 1, i);
+                val += (T)(6.0 * w_of(a) * p.rho0 * cu);
+            }
+            return val;
+        }
+    }
+    if (si < 0 || si >= nx) {
+        const int side = si < 0 ? VPLBM_WEST : VPLBM_EAST;
+        const int kind = p.bc[side];
+        if (kind == VPLBM_BC_PERIODIC) {
+            si = si < 0 ? si + nx : si - nx;
+        } else if (kind == VPLBM_BC_ZEROGRAD) {
+            return ldv(fin + a * ps + (long long)sj * nx + i);
+        } else {
+            T val = ldv(fin + opp_of(a) * ps + (long long)j * nx + i);
+            if (kind == VPLBM_BC_VELOCITY) {
+                double cu = cx_of(a) * wall_u(p, side, 0, j) + cy_of(a) * wall_u(p, side, 1, j);
+                val += (T)(6.0 * w_of(a) * p.rho0 * cu);
+            }
+            return val;
+        }
+    }
+    return ldv(fin + a * ps + (long long)sj * nx + si);
+}
+
+// Pull-stream all 9 populations of node (i, j).
+template <int P>
+__device__ __forceinline__ void pull_all(const StepParams &p, const typename Prec<P>::S *__restrict__ fin,
+                                         int i, int j, typename Prec<P>::T f[NQ])
+{
+    const int nx = p.nx;
+    const long long ps = p.ps;
+    if (i > 0 && i < nx - 1 && j > 0 && j < p.ny - 1) {
+        const long long b = (long long)j * nx + i;
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) f[a] = ldv(fin + a * ps + b - cx_of(a) - (long long)cy_of(a) * nx);
+    } else {
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) f[a] = pull_edge<P>(p, fin, a, i, j);
+    }
+}
+
+// Exact chi predicate of Eq. (2) in FP64 without contraction.
+__device__ __forceinline__ bool chi_exact(int i, int j, double xg, double yg, double r2)
+{
+    double dx = __dsub_rn((double)i, xg);
+    double dy = __dsub_rn((double)j, yg);
+    double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    return d2 <= r2;
+}
+
+// ---- rigid body (Eqs. 23-24 and Algorithm 1 step 3) --------------------
+
+__device__ void body_acc(const DevBody &b, const double F[3], const double q[3], const double v[3], double acc[3])
+{
+    for (int d = 0; d < 3; ++d) {
+        const double m = d < 2 ? b.mass : b.inertia;
+        acc[d] = (F[d] + b.f_ext[d] - b.damp[d] * v[d] - b.stiff[d] * (q[d] - b.q0[d])) / m;
+    }
+}
+
+__device__ void body_advance(const DevBody &b, long long step, const double F[3], double q[3], double v[3])
+{
+    if (!b.present || b.motion == VPLBM_MOTION_FIXED) return;
+    if (b.motion == VPLBM_MOTION_IMPOSED) {
+        const double two_pi = 6.283185307179586;
+        const double ph = two_pi * b.freq * (double)(step + 1) + b.phase;
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        q[b.axis] = b.q_center + b.amp * sn;
+        v[b.axis] = two_pi * b.freq * b.amp * cs;
+        return;
+    }
+    // classic RK4, h = 1, force held over the step
+    double k1v[3], k2v[3], k3v[3], k4v[3], k2q[3], k3q[3], k4q[3], qt[3], vt[3];
+    body_acc(b, F, q, v, k1v);
+    for (int d = 0; d < 3; ++d) { qt[d] = q[d] + 0.5 * v[d]; vt[d] = v[d] + 0.5 * k1v[d]; }
+    for (int d = 0; d < 3; ++d) k2q[d] = vt[d];
+    body_acc(b, F, qt, vt, k2v);
+    for (int d = 0; d < 3; ++d) { qt[d] = q[d] + 0.5 * k2q[d]; vt[d] = v[d] + 0.5 * k2v[d]; }
+    for (int d = 0; d < 3; ++d) k3q[d] = vt[d];
+    body_acc(b, F, qt, vt, k3v);
+    for (int d = 0; d < 3; ++d) { qt[d] = q[d] + k3q[d]; vt[d] = v[d] + k3v[d]; }
+    for (int d = 0; d < 3; ++d) k4q[d] = vt[d];
+    body_acc(b, F, qt, vt, k4v);
+    for (int d = 0; d < 3; ++d) {
+        if (!((b.dof_mask >> d) & 1u)) continue;
+        const double nq = q[d] + (v[d] + 2.0 * k2q[d] + 2.0 * k3q[d] + k4q[d]) / 6.0;
+        const double nv = v[d] + (k1v[d] + 2.0 * k2v[d] + 2.0 * k3v[d] + k4v[d]) / 6.0;
+        q[d] = nq;
+        v[d] = nv;
+    }
+}
+
+// Last participating block: fixed-order sum of the partials, history
+// record, body update, next pose.  Runs on warp 0.
+__device__ __noinline__ void step_tail(const StepParams &p, int nparts)
+{
+    const int lane = threadIdx.x & 31;
+    double acc[NPART - 1];
+#pragma unroll
+    for (int k = 0; k < NPART - 1; ++k) acc[k] = 0.0;
+    for (int s = lane; s < nparts; s += 32) {
+        const double *src = p.partials + (size_t)s * NPART;
+#pragma unroll
+        for (int k = 0; k < NPART - 1; ++k) acc[k] += __ldcg(src + k);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < NPART - 1; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
+    if (lane != 0) return;
+
+    const BodyState cur = *p.bs_in;
+    const double Fh[3] = {acc[3], acc[4], acc[5]};
+    vplbm_record r;
+    r.t = (double)cur.step;
+    r.fx = Fh[0]; r.fy = Fh[1]; r.torque = Fh[2];
+    r.cd = p.body.qref > 0 ? Fh[0] / p.body.qref : 0.0;
+    r.cl = p.body.qref > 0 ? Fh[1] / p.body.qref : 0.0;
+    r.x = cur.q[0]; r.y = cur.q[1]; r.theta = cur.q[2];
+    r.vx = cur.v[0]; r.vy = cur.v[1]; r.omega = cur.v[2];
+    r.fpen_x = acc[0]; r.fpen_y = acc[1]; r.tpen = acc[2];
+    r.n_solid = acc[6];
+    p.hist[cur.step % p.hist_cap] = r;
+
+    BodyState nb = cur;
+    body_advance(p.body, cur.step, Fh, nb.q, nb.v);
+    nb.step = cur.step + 1;
+    derive_pose(nb, p.body.present, p.body.radius, p.nx, p.ny);
+    *p.bs_out = nb;
+    *p.ticket = 0u;   // ready for the next launch (stream order)
+}
+
+// Contributions of one solid node to the 7 FP64 sums: penalization
+// reaction (force, torque) and momentum exchanged through its links during
+// the streaming into this step (force, torque), plus the node count.
+template <int P>
+__device__ __forceinline__ void solid_node_sums(const StepParams &p, const typename Prec<P>::S *fin, int i, int j,
+                                                double rho, double ax, double ay, double part[NPART - 1])
+{
+    using T = typename Prec<P>::T;
+    const BodyState *bs = p.bs_in;
+    T f[NQ];
+    pull_all<P>(p, fin, i, j, f);   // reloaded (cache hits) so f is not live across the stores
+    const long long b = (long long)j * p.nx + i;
+    const double dxd = (double)i - bs->q[0], dyd = (double)j - bs->q[1];
+    const double px = -rho * ax, py = -rho * ay;
+    double jxd = 0, jyd = 0, oxd = 0, oyd = 0;
+#pragma unroll
+    for (int a = 1; a < NQ; ++a) {
+        const double fa = (double)f[a];
+        const double own = (double)ldv(fin + a * p.ps + b);
+        jxd += cx_of(a) * fa;
+        jyd += cy_of(a) * fa;
+        oxd += cx_of(a) * own;
+        oyd += cy_of(a) * own;
+    }
+    const double ex = jxd - oxd, ey = jyd - oyd;
+    part[0] = px;
+    part[1] = py;
+    part[2] = dxd * py - dyd * px;
+    part[3] = ex;
+    part[4] = ey;
+    part[5] = dxd * ey - dyd * ex;
+    part[6] = 1.0;
+}
+
+
+// The VP-MRT update of one interior-or-edge node from its pulled
+// populations f: moments, chi and u_s, penalized velocity (Eq. 22),
+// collision with forcing (Eq. 17) and the store of f~.  Returns chi and
+// keeps rho, a for the solid-node sums.
+template <int P>
+__device__ __forceinline__ bool node_update(const StepParams &p, const BodyState *__restrict__ bs, bool near_body,
+                                            int i, int j, const typename Prec<P>::T f[NQ],
+                                            typename Prec<P>::S *__restrict__ fout, typename Prec<P>::T &cr,
+                                            typename Prec<P>::T &cax, typename Prec<P>::T &cay)
+{
+    using T = typename Prec<P>::T;
+    constexpr bool DEV = Prec<P>::DEV;
+    bool chi = false;
+    const T rs = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const T rho = DEV ? par<T>(p.rho0, p.rho0f) + rs : rs;
+    const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+
+    // chi and u_s (Eq. 2, Alg. 1 step 4), only where the disk can be
+    T dxl = 0, dyl = 0;
+    if (near_body) {
+        if constexpr (DEV) {
+            const int2 xy = __ldg(reinterpret_cast<const int2 *>(&bs->xi));
+            const float2 fr = __ldg(reinterpret_cast<const float2 *>(&bs->xf));
+            const float dxf = (float)(i - xy.x) - fr.x;
+            const float dyf = (float)(j - xy.y) - fr.y;
+            const float d2 = dxf * dxf + dyf * dyf;
+            const float r2 = p.r2f;
+            const float band = 1e-5f * r2 + 1e-5f;
+            if (fabsf(d2 - r2) <= band) chi = chi_exact(i, j, bs->q[0], bs->q[1], p.body.r2);
+            else chi = d2 <= r2;
+            dxl = dxf; dyl = dyf;
+        } else {
+            const double xg = __ldg(&bs->q[0]), yg = __ldg(&bs->q[1]);
+            chi = chi_exact(i, j, xg, yg, p.body.r2);
+            dxl = (double)i - xg;
+            dyl = (double)j - yg;
+        }
+    }
+
+    // penalized velocity, Eq. (22) in the eta-stable form
+    T inv_rho;
+    if constexpr (DEV) inv_rho = __frcp_rn(rho);
+    else inv_rho = (T)1 / rho;
+    const T gx = par<T>(p.gx, p.gxf), gy = par<T>(p.gy, p.gyf);
+    const T vx = jx * inv_rho + (T)0.5 * gx;
+    const T vy = jy * inv_rho + (T)0.5 * gy;
+    T ax = 0, ay = 0;
+    if (chi) {
+        T usx, usy;
+        if constexpr (DEV) {
+            const float4 vv = __ldg(reinterpret_cast<const float4 *>(&bs->vxf));
+            usx = vv.x - vv.z * dyl; usy = vv.y + vv.z * dxl;
+        } else {
+            usx = bs->v[0] - bs->v[2] * dyl; usy = bs->v[1] + bs->v[2] * dxl;
+        }
+        const T k = par<T>(p.pen_k, p.pen_kf);
+        ax = -(vx - usx) * k;
+        ay = -(vy - usy) * k;
+    }
+    const T ux = vx + (T)0.5 * ax;
+    const T uy = vy + (T)0.5 * ay;
+    const T Gx = rho * (gx + ax);
+    const T Gy = rho * (gy + ay);
+
+    // moments (rows of Eq. 15); equilibria (Eq. 14); M F closed form
+    const T sa = (f[1] + f[2]) + (f[3] + f[4]);
+    const T sd = (f[5] + f[6]) + (f[7] + f[8]);
+    const T e = (T)-4 * f[0] - sa + (T)2 * sd;
+    const T ep = (T)4 * f[0] - (T)2 * sa + sd;
+    const T qx = (T)2 * (f[3] - f[1]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const T qy = (T)2 * (f[4] - f[2]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const T pxx = (f[1] + f[3]) - (f[2] + f[4]);
+    const T pxy = (f[5] + f[7]) - (f[6] + f[8]);
+
+    const T u2r = rho * (ux * ux + uy * uy);
+    const T uG = ux * Gx + uy * Gy;
+    const T s1 = par<T>(p.s[1], p.sf[1]), s2 = par<T>(p.s[2], p.sf[2]), s4 = par<T>(p.s[4], p.sf[4]);
+    const T s6 = par<T>(p.s[6], p.sf[6]), s7 = par<T>(p.s[7], p.sf[7]), s8 = par<T>(p.s[8], p.sf[8]);
+
+    const T e_s = e - s1 * (e - ((T)-2 * rs + (T)3 * u2r)) + ((T)1 - (T)0.5 * s1) * ((T)6 * uG);
+    const T ep_s = ep - s2 * (ep - (rs - (T)3 * u2r)) - ((T)1 - (T)0.5 * s2) * ((T)6 * uG);
+    const T jx_s = jx + Gx;
+    const T jy_s = jy + Gy;
+    const T qx_s = qx - s4 * (qx + rho * ux) - ((T)1 - (T)0.5 * s4) * Gx;
+    const T qy_s = qy - s6 * (qy + rho * uy) - ((T)1 - (T)0.5 * s6) * Gy;
+    const T pxx_s = pxx - s7 * (pxx - rho * (ux * ux - uy * uy)) + ((T)1 - (T)0.5 * s7) * ((T)2 * (ux * Gx - uy * Gy));
+    const T pxy_s = pxy - s8 * (pxy - rho * ux * uy) + ((T)1 - (T)0.5 * s8) * (ux * Gy + uy * Gx);
+
+    // back to populations, M^-1 = M^T diag(1/|row|^2)
+    const T r9 = rs * (T)(1.0 / 9.0);
+    const T A = r9 - e_s * (T)(1.0 / 36.0) - ep_s * (T)(1.0 / 18.0);
+    const T B = r9 + e_s * (T)(1.0 / 18.0) + ep_s * (T)(1.0 / 36.0);
+    const T X1 = (jx_s - qx_s) * (T)(1.0 / 6.0);
+    const T Y1 = (jy_s - qy_s) * (T)(1.0 / 6.0);
+    const T X2 = jx_s * (T)(1.0 / 6.0) + qx_s * (T)(1.0 / 12.0);
+    const T Y2 = jy_s * (T)(1.0 / 6.0) + qy_s * (T)(1.0 / 12.0);
+    const T Pq = pxx_s * (T)0.25;
+    const T Rq = pxy_s * (T)0.25;
+
+    const long long b = (long long)j * p.nx + i;
+    const long long ps = p.ps;
+    stv(fout + b, r9 - e_s * (T)(1.0 / 9.0) + ep_s * (T)(1.0 / 9.0));
+    stv(fout + ps + b, A + X1 + Pq);
+    stv(fout + 2 * ps + b, A + Y1 - Pq);
+    stv(fout + 3 * ps + b, A - X1 + Pq);
+    stv(fout + 4 * ps + b, A - Y1 - Pq);
+    stv(fout + 5 * ps + b, B + X2 + Y2 + Rq);
+    stv(fout + 6 * ps + b, B - X2 + Y2 - Rq);
+    stv(fout + 7 * ps + b, B - X2 - Y2 + Rq);
+    stv(fout + 8 * ps + b, B + X2 - Y2 - Rq);
+
+    if (!(rho > (T)0) || !(rho < (T)1e30)) *p.err = ERR_NONFINITE;
+    cr = rho; cax = ax; cay = ay;
+    return chi;
+}
+
+// Does the tile [i0, i0+w) x [j0, j0+h) meet the node range that may hold
+// solid nodes?  With no solid node anywhere, tile (0, 0) stands in so that
+// one block still runs the tail.
+__device__ __forceinline__ bool tile_near_body(const int4 range, int i0, int j0, int w, int h, bool first_tile)
+{
+    if (range.x > range.y) return first_tile;
+    return i0 + w - 1 >= range.x && i0 <= range.y && j0 + h - 1 >= range.z && j0 <= range.w;
+}
+
+// Block-wide fixed-order reduction of the 7 FP64 sums of one tile, its
+// partial slot, the ticket, and the tail in the last tile.  Every thread
+// of the block calls it (it contains block barriers); tile (tx, ty) is the
+// tile's index in the w x h tiling.
+__device__ __forceinline__ void tile_reduce(const StepParams &p, const int4 range, int tx, int ty, int w, int h,
+                                            bool any_chi_thread, double part[NPART - 1], double (*red)[NPART],
+                                            int *s_last)
+{
+    const int nthreads = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = nthreads >> 5;
+    if (__any_sync(0xffffffffu, any_chi_thread)) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < NPART - 1; ++k) part[k] += __shfl_down_sync(0xffffffffu, part[k], off);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NPART - 1; ++k) red[warp][k] = part[k];
+    __syncthreads();
+    int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;
+    if (range.x <= range.y) {
+        tx0 = range.x / w; tx1 = range.y / w;
+        ty0 = range.z / h; ty1 = range.w / h;
+    }
+    const int ntx = tx1 - tx0 + 1;
+    const int nparts = ntx * (ty1 - ty0 + 1);
+    if (nparts > p.max_parts) {          // cannot happen for a finite pose; never overrun
+        if (tid == 0) *p.err |= ERR_INTERNAL;
+        __syncthreads();
+        return;
+    }
+    if (warp == 0) {
+        double v[NPART - 1];
+#pragma unroll
+        for (int k = 0; k < NPART - 1; ++k) v[k] = lane < nwarps ? red[lane][k] : 0.0;
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < NPART - 1; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+        if (lane == 0) {
+            const int slot = (ty - ty0) * ntx + (tx - tx0);
+            double *dst = p.partials + (size_t)slot * NPART;
+#pragma unroll
+            for (int k = 0; k < NPART - 1; ++k) __stcg(dst + k, v[k]);
+            __threadfence();
+            const unsigned t = atomicAdd(p.ticket, 1u);
+            *s_last = (t == (unsigned)(nparts - 1));
+        }
+    }
+    __syncthreads();
+    if (*s_last && warp == 0) {
+        __threadfence();
+        step_tail(p, nparts);
+    }
+    __syncthreads();   // red and s_last are reused by the next tile
+}
+
+}  // namespace
+}  // namespace vplbm
