@@ -43,7 +43,7 @@ CSRC = os.path.join(ROOT, "paper_1905_05110_gb300", "csrc")
 
 
 def kernel_name(prec: str, launch) -> str:
-    base = "vp_mrt_step_tma" if tuple(launch) == (0, 0) else "vp_mrt_step"
+    base = {"tma": "vp_mrt_step_tma", "pair": "vp_mrt_step_pair", "scalar": "vp_mrt_step"}[launch[0]]
     return f"{base}<{PREC_ID[prec]}>"
 
 
@@ -245,7 +245,7 @@ def run_ours(args, rank, world, local_rank):
     sim.init_from_problem()
     if not args.no_autotune:
         sim.autotune(20)
-    bx, by = sim.launch()
+    launch = sim.launch()
     sim.step(args.warmup)
     sim.sync()
 
@@ -269,7 +269,7 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peak()
     per_launch = dt / args.steps
     achieved = BYTES_PER_NODE[prec] * nodes / per_launch / 1e9
-    kname = kernel_name(prec, (bx, by))
+    kname = kernel_name(prec, launch)
     traffic = profiled_traffic(kname, args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
@@ -314,7 +314,7 @@ def run_ours(args, rank, world, local_rank):
                 "data": "synthetic",
                 "config": {"workload": p["name"], "nx": p["nx"], "ny": p["ny"],
                            "storage": {"f32": "f32 deviation", "f16": "f16 deviation", "f64": "f64"}[prec],
-                           "launch": [bx, by], "parallelism": f"replicas x{world}",
+                           "launch": list(launch), "parallelism": f"replicas x{world}",
                            "l2": "not flushed: populations 151 MB read+write per step > 129 MB L2"},
                 "roofline": roofline, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clock, "compare": compare}

@@ -202,16 +202,28 @@ vplbm_status vplbm_get_history(vplbm_ctx *ctx, long long first, long long count,
 /* Pose (x, y, theta), velocity (vx, vy, omega) and step counter. */
 vplbm_status vplbm_get_body(vplbm_ctx *ctx, double q[3], double v[3], long long *step);
 
-/* Launch shape of the step kernel: block_x * block_y threads per block,
- * block_x a multiple of 32, block_x * block_y in {128, 256}; or (0, 0) for
- * the TMA-staged persistent kernel (FP32/FP16 storage, nx * element size a
- * multiple of 16 bytes, nx >= 136 (FP32) / 144 (FP16), ny >= 6), which a new
- * context selects whenever the lattice allows it. */
-vplbm_status vplbm_set_launch(vplbm_ctx *ctx, int block_x, int block_y);
-vplbm_status vplbm_get_launch(vplbm_ctx *ctx, int *block_x, int *block_y);
+/* Step kernels.  All compute the same method; they differ in data movement:
+ *  VPLBM_KERNEL_SCALAR  one node per thread (every precision);
+ *  VPLBM_KERNEL_PAIR    two x-adjacent nodes per thread with packed FP32x2
+ *                       arithmetic (FP32/FP16 storage, even nx); the default
+ *                       where the lattice allows it;
+ *  VPLBM_KERNEL_TMA     persistent blocks fed by tensor-memory-accelerator
+ *                       copies into a shared-memory ring (FP32/FP16 storage,
+ *                       nx * element size a multiple of 16 bytes,
+ *                       nx >= 136 (FP32) / 144 (FP16), ny >= 6).
+ * Nodes on the lattice edges and near the body always take the scalar
+ * arithmetic.  The results of different kernels agree to the rounding of
+ * the storage precision. */
+typedef enum { VPLBM_KERNEL_SCALAR = 0, VPLBM_KERNEL_PAIR = 1, VPLBM_KERNEL_TMA = 2 } vplbm_kernel;
 
-/* Time every candidate launch shape on the current state (the state is
- * saved and restored around the trials) and keep the fastest. */
+/* Kernel and block shape: block_x * block_y threads, block_x a multiple of
+ * 32, block_x * block_y in {128, 256} (ignored for VPLBM_KERNEL_TMA).
+ * VPLBM_EUNSUPPORTED if the kernel cannot run this lattice. */
+vplbm_status vplbm_set_launch(vplbm_ctx *ctx, int kernel, int block_x, int block_y);
+vplbm_status vplbm_get_launch(vplbm_ctx *ctx, int *kernel, int *block_x, int *block_y);
+
+/* Time every candidate kernel and block shape on the current state (the
+ * state is saved and restored around the trials) and keep the fastest. */
 vplbm_status vplbm_autotune(vplbm_ctx *ctx, int steps_per_trial);
 
 /* Test hook for the bounded waits of the TMA-staged kernel: when enabled,

@@ -113,8 +113,8 @@ _SIGS = {
     "vplbm_get_fields_dev": (C.c_int, [_CTX, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vplbm_get_history": (C.c_int, [_CTX, C.c_longlong, C.c_longlong, C.POINTER(Record)]),
     "vplbm_get_body": (C.c_int, [_CTX, _D, _D, C.POINTER(C.c_longlong)]),
-    "vplbm_set_launch": (C.c_int, [_CTX, C.c_int, C.c_int]),
-    "vplbm_get_launch": (C.c_int, [_CTX, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "vplbm_set_launch": (C.c_int, [_CTX, C.c_int, C.c_int, C.c_int]),
+    "vplbm_get_launch": (C.c_int, [_CTX, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "vplbm_autotune": (C.c_int, [_CTX, C.c_int]),
     "vplbm_get_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_longlong)]),
     "vplbm_inject_wait_timeout": (C.c_int, [_CTX, C.c_int]),
@@ -307,14 +307,18 @@ def vplbm_get_body(ctx):
     return q, v, int(step.value)
 
 
-def vplbm_set_launch(ctx, bx: int, by: int):
-    _check(load_library().vplbm_set_launch(ctx, int(bx), int(by)))
+KERNELS = {"scalar": 0, "pair": 1, "tma": 2}
+KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
+
+
+def vplbm_set_launch(ctx, kernel: int, bx: int, by: int):
+    _check(load_library().vplbm_set_launch(ctx, int(kernel), int(bx), int(by)))
 
 
 def vplbm_get_launch(ctx):
-    bx, by = C.c_int(), C.c_int()
-    _check(load_library().vplbm_get_launch(ctx, C.byref(bx), C.byref(by)))
-    return bx.value, by.value
+    k, bx, by = C.c_int(), C.c_int(), C.c_int()
+    _check(load_library().vplbm_get_launch(ctx, C.byref(k), C.byref(bx), C.byref(by)))
+    return k.value, bx.value, by.value
 
 
 def vplbm_autotune(ctx, steps_per_trial: int = 20):
@@ -452,11 +456,15 @@ class Simulation:
     def nstep(self) -> int:
         return vplbm_get_body(self.ctx)[2]
 
-    def set_launch(self, bx, by):
-        vplbm_set_launch(self.ctx, bx, by)
+    def set_launch(self, kernel, bx=0, by=0):
+        """kernel: "scalar", "pair" or "tma" (or its number)."""
+        k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        vplbm_set_launch(self.ctx, k, bx, by)
 
     def launch(self):
-        return vplbm_get_launch(self.ctx)
+        """(kernel name, block_x, block_y) of the step kernel."""
+        k, bx, by = vplbm_get_launch(self.ctx)
+        return KERNEL_NAMES[k], bx, by
 
     def autotune(self, steps_per_trial: int = 20):
         vplbm_autotune(self.ctx, steps_per_trial)

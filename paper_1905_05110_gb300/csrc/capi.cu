@@ -114,9 +114,10 @@ struct vplbm_ctx {
     double *prof = nullptr;
     void *owned = nullptr;                // single allocation when the library owns memory
     long long nstep = 0;
+    int kernel = KERNEL_SCALAR;           // KERNEL_SCALAR / KERNEL_PAIR / KERNEL_TMA
     int bx = 128, by = 2;
     cudaGraphExec_t graph = nullptr;
-    int graph_bx = -1, graph_by = -1;
+    int graph_kernel = -1, graph_bx = -1, graph_by = -1;
     long long launches = 0;
     // TMA-staged kernel (FP32/FP16 storage): tensor maps of the two
     // population buffers as sources, persistent grid size
@@ -174,11 +175,12 @@ void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long 
     const long long ps = (long long)round_up((size_t)n, 128);
     long long parts = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr,
                                            TMA_TILE_W, TMA_TILE_H);
-    for (int k = 0; k < N_SHAPES; ++k) {
-        const long long m = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr,
-                                                 SHAPES[k][0], SHAPES[k][1]);
-        if (m > parts) parts = m;
-    }
+    for (int k = 0; k < N_SHAPES; ++k)
+        for (int wmul = 1; wmul <= 2; ++wmul) {   // scalar and paired tilings
+            const long long m = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr,
+                                                     wmul * SHAPES[k][0], SHAPES[k][1]);
+            if (m > parts) parts = m;
+        }
     s->populations = round_up((size_t)(9 * ps) * elem_size(lat->precision), ALIGN);
     s->body_state = round_up(2 * sizeof(BodyState), ALIGN);
     s->partials = round_up((size_t)parts * NPART * sizeof(double), ALIGN);
@@ -213,12 +215,26 @@ StepParams params_for(const vplbm_ctx *c, long long step)
     return p;
 }
 
-// One time step with the context's kernel choice (bx == 0: TMA-staged).
+// One time step with the context's kernel choice.
 cudaError_t launch_one(const vplbm_ctx *c, long long step, cudaStream_t stream)
 {
     const StepParams p = params_for(c, step);
-    if (c->bx == 0) return launch_step_tma(c->precision, p, c->tmap[step & 1], c->tma_grid, stream);
+    if (c->kernel == KERNEL_TMA) return launch_step_tma(c->precision, p, c->tmap[step & 1], c->tma_grid, stream);
+    if (c->kernel == KERNEL_PAIR) return launch_step_pair(c->precision, p, c->bx, c->by, stream);
     return launch_step(c->precision, p, c->bx, c->by, stream);
+}
+
+bool pair_ok(const vplbm_ctx *c)
+{
+    return (c->precision == VPLBM_F32_DEV || c->precision == VPLBM_F16_DEV) && c->nx % 2 == 0;
+}
+
+// Reduction tile of a launch choice (the pair kernel's block covers 2*bx).
+void tile_of(int kernel, int bx, int by, int *w, int *h)
+{
+    if (kernel == KERNEL_TMA) { *w = TMA_TILE_W; *h = TMA_TILE_H; }
+    else if (kernel == KERNEL_PAIR) { *w = 2 * bx; *h = by; }
+    else { *w = bx; *h = by; }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -304,6 +320,20 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     p.gxf = (float)lat->gx;
     p.gyf = (float)lat->gy;
     p.pen_kf = (float)p.pen_k;
+    {
+        PairConsts &k = p.pc;
+        const double *sv = lat->s;
+        k.hgx = (float)(0.5 * lat->gx);
+        k.hgy = (float)(0.5 * lat->gy);
+        k.om1 = (float)(1.0 - sv[1]); k.om2 = (float)(1.0 - sv[2]); k.om4 = (float)(1.0 - sv[4]);
+        k.om6 = (float)(1.0 - sv[6]); k.om7 = (float)(1.0 - sv[7]); k.om8 = (float)(1.0 - sv[8]);
+        k.h1x6 = (float)(6.0 * (1.0 - 0.5 * sv[1]));
+        k.mh2x6 = (float)(-6.0 * (1.0 - 0.5 * sv[2]));
+        k.mh4 = (float)(-(1.0 - 0.5 * sv[4]));
+        k.mh6 = (float)(-(1.0 - 0.5 * sv[6]));
+        k.h7x2 = (float)(2.0 * (1.0 - 0.5 * sv[7]));
+        k.h8 = (float)(1.0 - 0.5 * sv[8]);
+    }
     // wall velocity profiles: [side][comp][maxlen]
     const int maxlen = lat->nx > lat->ny ? lat->nx : lat->ny;
     std::vector<double> prof((size_t)8 * maxlen, 0.0);
@@ -359,9 +389,10 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     p.hist_cap = cap;
 
     setup_tma(c);
-    if (c->tma_ok) {
-        c->bx = 0;
-        c->by = 0;
+    if (pair_ok(c)) {   // default: paired FP32x2 kernel where the lattice allows it
+        c->kernel = KERNEL_PAIR;
+        c->bx = 64;
+        c->by = 4;
     }
     // populations at rest
     StepParams q = params_for(c, 0);
@@ -433,7 +464,7 @@ vplbm_status create_impl(const vplbm_lattice_desc *lat, const vplbm_body_desc *b
 
 vplbm_status ensure_graph(vplbm_ctx *c)
 {
-    if (c->graph && c->graph_bx == c->bx && c->graph_by == c->by) return VPLBM_OK;
+    if (c->graph && c->graph_kernel == c->kernel && c->graph_bx == c->bx && c->graph_by == c->by) return VPLBM_OK;
     if (c->graph) {
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
@@ -451,6 +482,7 @@ vplbm_status ensure_graph(vplbm_ctx *c)
     cudaError_t e3 = cudaGraphInstantiate(&c->graph, g, 0);
     cudaGraphDestroy(g);
     if (e3 != cudaSuccess) return fail(VPLBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e3));
+    c->graph_kernel = c->kernel;
     c->graph_bx = c->bx;
     c->graph_by = c->by;
     return VPLBM_OK;
@@ -706,28 +738,37 @@ vplbm_status vplbm_get_body(vplbm_ctx *c, double q[3], double v[3], long long *s
     return read_error(c);
 }
 
-vplbm_status vplbm_set_launch(vplbm_ctx *c, int bx, int by)
+vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
 {
     if (!c) return fail(VPLBM_EINVAL, "context is NULL");
-    if (bx == 0 && by == 0) {
-        if (!c->tma_ok) return fail(VPLBM_EUNSUPPORTED, "the TMA-staged kernel needs FP32/FP16 storage and nx*elem a multiple of 16 bytes");
-        c->bx = 0;
-        c->by = 0;
+    if (kernel == KERNEL_TMA) {
+        if (!c->tma_ok)
+            return fail(VPLBM_EUNSUPPORTED, "the TMA-staged kernel needs FP32/FP16 storage, nx*elem a multiple of 16 bytes and nx >= 136/144");
+        c->kernel = KERNEL_TMA;
+        c->bx = TMA_TILE_W;
+        c->by = 2;
         return VPLBM_OK;
     }
+    if (kernel != KERNEL_SCALAR && kernel != KERNEL_PAIR) return fail(VPLBM_EINVAL, "unknown kernel %d", kernel);
+    if (kernel == KERNEL_PAIR && !pair_ok(c))
+        return fail(VPLBM_EUNSUPPORTED, "the paired kernel needs FP32/FP16 storage and an even nx");
     const int t = bx * by;
     if (bx < 32 || bx % 32 || by < 1 || (t != 128 && t != 256))
         return fail(VPLBM_EINVAL, "launch shape %dx%d not allowed", bx, by);
-    if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, bx, by) > c->max_parts)
+    int w, h;
+    tile_of(kernel, bx, by, &w, &h);
+    if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, w, h) > c->max_parts)
         return fail(VPLBM_EINVAL, "launch shape %dx%d needs more reduction scratch than allocated", bx, by);
+    c->kernel = kernel;
     c->bx = bx;
     c->by = by;
     return VPLBM_OK;
 }
 
-vplbm_status vplbm_get_launch(vplbm_ctx *c, int *bx, int *by)
+vplbm_status vplbm_get_launch(vplbm_ctx *c, int *kernel, int *bx, int *by)
 {
     if (!c) return fail(VPLBM_EINVAL, "context is NULL");
+    if (kernel) *kernel = c->kernel;
     if (bx) *bx = c->bx;
     if (by) *by = c->by;
     return VPLBM_OK;
@@ -736,9 +777,9 @@ vplbm_status vplbm_get_launch(vplbm_ctx *c, int *bx, int *by)
 vplbm_status vplbm_inject_wait_timeout(vplbm_ctx *c, int enable)
 {
     if (!c) return fail(VPLBM_EINVAL, "context is NULL");
-    if (enable && !(c->tma_ok && c->bx == 0)) return fail(VPLBM_EUNSUPPORTED, "the TMA-staged kernel is not selected");
+    if (enable && c->kernel != KERNEL_TMA) return fail(VPLBM_EUNSUPPORTED, "the TMA-staged kernel is not selected");
     c->base.tx_extra = enable ? 16u : 0u;
-    c->graph_bx = -1;   // recapture graphs with the new parameters
+    c->graph_kernel = -1;   // recapture graphs with the new parameters
     return VPLBM_OK;
 }
 
@@ -764,11 +805,11 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
         return fail(VPLBM_ENOMEM, "autotune scratch allocation failed");
     }
     const long long nstep0 = c->nstep;
-    const int bx0 = c->bx, by0 = c->by;
+    const int k0 = c->kernel, bx0 = c->bx, by0 = c->by;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     vplbm_status st = VPLBM_OK;
     float best = 1e30f;
-    int best_k = -2;
+    int best_kernel = -1, best_bx = 0, best_by = 0;
     auto restore = [&]() -> cudaError_t {
         cudaError_t e = cudaMemcpyAsync(c->f[nstep0 & 1], save_f, c->pop_bytes, cudaMemcpyDeviceToDevice, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c->hist, save_h, hbytes, cudaMemcpyDeviceToDevice, c->stream);
@@ -786,9 +827,13 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
             st = fail(VPLBM_ECUDA, "autotune setup failed");
             break;
         }
-        for (int k = -1; k < N_SHAPES; ++k) {
-            const int cbx = k < 0 ? 0 : SHAPES[k][0], cby = k < 0 ? 0 : SHAPES[k][1];
-            if (vplbm_set_launch(c, cbx, cby) != VPLBM_OK) continue;
+        // candidates: the TMA-staged kernel, then every shape of the paired
+        // and of the scalar kernel
+        for (int cand = -1; cand < 2 * N_SHAPES; ++cand) {
+            const int ck = cand < 0 ? KERNEL_TMA : (cand < N_SHAPES ? KERNEL_PAIR : KERNEL_SCALAR);
+            const int cbx = cand < 0 ? 0 : SHAPES[cand % N_SHAPES][0];
+            const int cby = cand < 0 ? 0 : SHAPES[cand % N_SHAPES][1];
+            if (vplbm_set_launch(c, ck, cbx, cby) != VPLBM_OK) continue;
             for (int rep = 0; rep < 2; ++rep) {   // first pass warms up
                 if (restore() != cudaSuccess) { st = fail(VPLBM_ECUDA, "autotune restore failed"); break; }
                 cudaEventRecord(e0, c->stream);
@@ -804,7 +849,7 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
                 }
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
-                if (rep == 1 && ms < best) { best = ms; best_k = k; }
+                if (rep == 1 && ms < best) { best = ms; best_kernel = c->kernel; best_bx = c->bx; best_by = c->by; }
             }
             if (st != VPLBM_OK) break;
         }
@@ -817,13 +862,12 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
     if (e1) cudaEventDestroy(e1);
     cudaFree(save_f);
     cudaFree(save_h);
-    if (best_k >= 0) {
-        c->bx = SHAPES[best_k][0];
-        c->by = SHAPES[best_k][1];
-    } else if (best_k == -1 && best < 1e29f) {
-        c->bx = 0;
-        c->by = 0;
+    if (best_kernel >= 0) {
+        c->kernel = best_kernel;
+        c->bx = best_bx;
+        c->by = best_by;
     } else {
+        c->kernel = k0;
         c->bx = bx0;
         c->by = by0;
     }

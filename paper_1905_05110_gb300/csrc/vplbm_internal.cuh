@@ -55,6 +55,15 @@ struct DevBody {
 // th, n_solid, (pad).
 constexpr int NPART = 8;
 
+// Host-folded constants of the paired FP32x2 kernel (uniform over a run):
+// 1 - s_k, the (1 - s_k/2) factors of Eq. (17) with the signs and integer
+// factors of the closed-form M F folded in, and g/2.
+struct PairConsts {
+    float hgx, hgy;
+    float om1, om2, om4, om6, om7, om8;
+    float h1x6, mh2x6, mh4, mh6, h7x2, h8;
+};
+
 struct StepParams {
     int nx, ny;
     long long ps;                 // plane stride (elements) of a population buffer
@@ -65,6 +74,7 @@ struct StepParams {
     // runs on the FP64 pipe, which is narrow on GB300)
     float sf[NQ];
     float rho0f, gxf, gyf, pen_kf, r2f;
+    PairConsts pc;
     int bc[4];
     double wall_u0[4][2];
     const double *wall_prof[4][2];
@@ -116,6 +126,12 @@ __host__ __device__ inline void derive_pose(BodyState &s, int present, double ra
     s.xi = (int)fx; s.yi = (int)fy;
     s.xf = (float)(s.q[0] - fx); s.yf = (float)(s.q[1] - fy);
 }
+
+// Step kernels a context can launch.
+enum { KERNEL_SCALAR = 0, KERNEL_PAIR = 1, KERNEL_TMA = 2 };
+
+// Paired FP32x2 step (step_pair.cu): block (bx, by) covers 2*bx x by nodes.
+cudaError_t launch_step_pair(int precision, const StepParams &p, int bx, int by, cudaStream_t stream);
 
 // Launchers (step_kernels.cu).  All are asynchronous on `stream`.
 cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream);

@@ -154,12 +154,12 @@ def test_full_size_one_step_every_launch_shape(name):
     orc.step(1)
     ref = orc.populations()
     ref_h = orc.history(0, 1)[0]
-    for bx, by in vp_shapes():
+    for kern, bx, by in vp_shapes():
         g = vp.Simulation(p1, precision="f32", history_capacity=4)
-        g.set_launch(bx, by)
+        g.set_launch(kern, bx, by)
         g.set_populations(f0)
         g.step(1)
-        assert dev_err(g.populations(), ref) < ONE_STEP_TOL["f32"], (bx, by)
+        assert dev_err(g.populations(), ref) < ONE_STEP_TOL["f32"], (kern, bx, by)
         h = g.history(0, 1)[0]
         assert h[REC["n_solid"]] == ref_h[REC["n_solid"]]
         assert rel_err(h[[REC["fx"], REC["fy"]]], ref_h[[REC["fx"], REC["fy"]]]) < 1e-3
@@ -167,9 +167,13 @@ def test_full_size_one_step_every_launch_shape(name):
     del orc
 
 
+SCALAR_SHAPES = [(128, 2), (256, 1), (64, 4), (32, 8), (128, 1), (64, 2), (32, 4)]
+
+
 def vp_shapes():
-    # (0, 0) selects the TMA-staged persistent kernel
-    return [(0, 0), (128, 2), (256, 1), (64, 4), (32, 8), (128, 1), (64, 2), (32, 4)]
+    """Every kernel and block shape the runtime can launch."""
+    return ([("tma", 0, 0)] + [("pair", bx, by) for bx, by in SCALAR_SHAPES]
+            + [("scalar", bx, by) for bx, by in SCALAR_SHAPES])
 
 
 def test_fp64_full_size_two_steps():
@@ -206,9 +210,9 @@ def test_launch_shapes_give_identical_fields_for_fixed_body():
     import paper_1905_05110_gb300 as vp
     p = wl.channel_fixed_disk(nx=200, ny=90, center=(50.3, 44.6), diameter=18)
     ref = None
-    for bx, by in vp_shapes()[1:]:
+    for bx, by in SCALAR_SHAPES:
         g = vp.Simulation(p, precision="f32", history_capacity=64)
-        g.set_launch(bx, by)
+        g.set_launch("scalar", bx, by)
         g.init_from_problem()
         g.step(40)
         f = g.populations()
@@ -292,7 +296,7 @@ def test_autotune_restores_state():
     f = g.populations()
     h = g.history()
     shape = g.autotune(4)
-    assert shape in [tuple(s) for s in vp_shapes()]
+    assert shape in [tuple(s) for s in vp_shapes()] or shape[0] == "tma"
     assert g.nstep == 10
     assert np.array_equal(g.populations(), f)
     assert np.array_equal(g.history(), h)
@@ -311,7 +315,7 @@ def test_tma_kernel_steps_from_random_state(bcs, precision):
     g, _ = make_pair(p, precision, init=None, f0=f0)
     f0 = g.populations()
     gpu, orc = make_pair(p, precision, f0=f0)
-    assert gpu.launch() == (0, 0)
+    gpu.set_launch("tma")
     for n in (1, 2):
         gpu.step(1)
         orc.step(1)
@@ -327,14 +331,14 @@ def test_tma_kernel_matches_plain_kernel_over_a_run(precision):
     import paper_1905_05110_gb300 as vp
     p = wl.oscillating_disk(nx=392, ny=203, diameter=30, x_c=100)
     runs = {}
-    for shape in ((0, 0), (128, 2)):
+    for shape in (("tma", 0, 0), ("scalar", 128, 2)):
         g = vp.Simulation(p, precision=precision, history_capacity=256)
         g.set_launch(*shape)
         g.init_from_problem()
         g.step(150)
-        runs[shape] = (g.populations(), g.history())
+        runs[shape[0]] = (g.populations(), g.history())
         g.close()
-    (fa, ha), (fb, hb) = runs[(0, 0)], runs[(128, 2)]
+    (fa, ha), (fb, hb) = runs["tma"], runs["scalar"]
     assert dev_err(fa, fb) < (1e-5 if precision == "f32" else 1e-2)
     assert np.array_equal(ha[:, REC["n_solid"]], hb[:, REC["n_solid"]])
     assert rel_err(ha[:, REC["cl"]], hb[:, REC["cl"]]) < (1e-3 if precision == "f32" else 5e-2)
@@ -345,7 +349,7 @@ def test_tma_bounded_wait_reports_timeout_and_context_survives():
     p = wl.oscillating_disk(nx=256, ny=64, diameter=12, x_c=60)
     g = vp.Simulation(p, precision="f32", history_capacity=64)
     g.init_from_problem()
-    assert g.launch() == (0, 0)
+    g.set_launch("tma")
     vp.vplbm_inject_wait_timeout(g.ctx, True)
     g.step(1)
     with pytest.raises(vp.VplbmError) as ei:
@@ -356,6 +360,29 @@ def test_tma_bounded_wait_reports_timeout_and_context_survives():
     g.step(40)
     g.sync()
     ref = vp.Simulation(p, precision="f32", history_capacity=64)
+    ref.set_launch("tma")
     ref.init_from_problem()
     ref.step(40)
     assert np.array_equal(g.populations(), ref.populations())
+
+
+@pytest.mark.parametrize("bcs", BC_SETS)
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+@pytest.mark.parametrize("size", [(98, 45), (66, 3), (6, 5)])
+def test_pair_kernel_steps_from_random_state(bcs, precision, size):
+    # the paired FP32x2 kernel, ragged against its 2*bx x by blocks, with the
+    # warp-edge lanes and every boundary set
+    nx, ny = size
+    body = moving_bodies(nx, ny)["free"] if min(nx, ny) > 20 else None
+    p = _box(nx, ny, bcs, seed=nx * ny, body=body)
+    f0 = wl.random_populations(nx, ny, seed=13, amp=0.03, u_amp=0.05)
+    g, _ = make_pair(p, precision, init=None, f0=f0)
+    f0 = g.populations()
+    for bx, by in ((32, 4), (64, 4), (128, 1)):
+        gpu, orc = make_pair(p, precision, f0=f0)
+        gpu.set_launch("pair", bx, by)
+        for n in (1, 2):
+            gpu.step(1)
+            orc.step(1)
+            tol = ONE_STEP_TOL[precision] * (3 if n == 2 else 1)
+            assert dev_err(gpu.populations(), orc.populations()) < tol, (bx, by, n)

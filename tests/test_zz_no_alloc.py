@@ -45,6 +45,7 @@ def test_noalloc_two_calls_match_regular_step(gpu_library, precision):
     n1, n2 = 40, 23
     cap = 128
     ref = vp.Simulation(p, precision=precision, history_capacity=cap)
+    ref.set_launch("scalar", 128, 2)   # the kernel and shape the no-alloc path runs
     ref.init_from_problem()
 
     lat = vp.lattice_desc(p, precision)
