@@ -203,18 +203,24 @@ vplbm_status vplbm_get_history(vplbm_ctx *ctx, long long first, long long count,
 vplbm_status vplbm_get_body(vplbm_ctx *ctx, double q[3], double v[3], long long *step);
 
 /* Step kernels.  All compute the same method; they differ in data movement:
- *  VPLBM_KERNEL_SCALAR  one node per thread (every precision);
+ *  VPLBM_KERNEL_SCALAR  one node per thread (every precision; the default
+ *                       for FP64 storage);
  *  VPLBM_KERNEL_PAIR    two x-adjacent nodes per thread with packed FP32x2
- *                       arithmetic (FP32/FP16 storage, even nx); the default
- *                       where the lattice allows it;
+ *                       arithmetic (FP32/FP16 storage, even nx);
  *  VPLBM_KERNEL_TMA     persistent blocks fed by tensor-memory-accelerator
  *                       copies into a shared-memory ring (FP32/FP16 storage,
  *                       nx * element size a multiple of 16 bytes,
- *                       nx >= 136 (FP32) / 144 (FP16), ny >= 6).
+ *                       nx >= 136 (FP32) / 144 (FP16), ny >= 6);
+ *  VPLBM_KERNEL_ASYNC   four nodes per thread down a column, their
+ *                       populations copied to shared memory two nodes ahead
+ *                       of the collision (FP32/FP16 storage); the default
+ *                       for FP32/FP16 storage.
  * Nodes on the lattice edges and near the body always take the scalar
  * arithmetic.  The results of different kernels agree to the rounding of
  * the storage precision. */
-typedef enum { VPLBM_KERNEL_SCALAR = 0, VPLBM_KERNEL_PAIR = 1, VPLBM_KERNEL_TMA = 2 } vplbm_kernel;
+typedef enum {
+    VPLBM_KERNEL_SCALAR = 0, VPLBM_KERNEL_PAIR = 1, VPLBM_KERNEL_TMA = 2, VPLBM_KERNEL_ASYNC = 3
+} vplbm_kernel;
 
 /* Kernel and block shape: block_x * block_y threads, block_x a multiple of
  * 32, block_x * block_y in {128, 256} (ignored for VPLBM_KERNEL_TMA).

@@ -168,6 +168,8 @@ vplbm_status check_body(const vplbm_body_desc *b)
     return VPLBM_OK;
 }
 
+void tile_of(int kernel, int bx, int by, int *w, int *h);
+
 void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long long cap, vplbm_buffer_sizes *s,
                long long *ps_out, long long *parts_out)
 {
@@ -176,9 +178,10 @@ void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long 
     long long parts = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr,
                                            TMA_TILE_W, TMA_TILE_H);
     for (int k = 0; k < N_SHAPES; ++k)
-        for (int wmul = 1; wmul <= 2; ++wmul) {   // scalar and paired tilings
-            const long long m = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr,
-                                                     wmul * SHAPES[k][0], SHAPES[k][1]);
+        for (int kern = KERNEL_SCALAR; kern <= KERNEL_ASYNC; ++kern) {   // every kernel's tiling
+            int w, h;
+            tile_of(kern, SHAPES[k][0], SHAPES[k][1], &w, &h);
+            const long long m = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr, w, h);
             if (m > parts) parts = m;
         }
     s->populations = round_up((size_t)(9 * ps) * elem_size(lat->precision), ALIGN);
@@ -221,6 +224,7 @@ cudaError_t launch_one(const vplbm_ctx *c, long long step, cudaStream_t stream)
     const StepParams p = params_for(c, step);
     if (c->kernel == KERNEL_TMA) return launch_step_tma(c->precision, p, c->tmap[step & 1], c->tma_grid, stream);
     if (c->kernel == KERNEL_PAIR) return launch_step_pair(c->precision, p, c->bx, c->by, stream);
+    if (c->kernel == KERNEL_ASYNC) return launch_step_async(c->precision, p, c->bx, c->by, stream);
     return launch_step(c->precision, p, c->bx, c->by, stream);
 }
 
@@ -234,6 +238,7 @@ void tile_of(int kernel, int bx, int by, int *w, int *h)
 {
     if (kernel == KERNEL_TMA) { *w = TMA_TILE_W; *h = TMA_TILE_H; }
     else if (kernel == KERNEL_PAIR) { *w = 2 * bx; *h = by; }
+    else if (kernel == KERNEL_ASYNC) { *w = bx; *h = by * async_rows_per_thread(); }
     else { *w = bx; *h = by; }
 }
 
@@ -389,10 +394,10 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     p.hist_cap = cap;
 
     setup_tma(c);
-    if (pair_ok(c)) {   // default: paired FP32x2 kernel where the lattice allows it
-        c->kernel = KERNEL_PAIR;
-        c->bx = 64;
-        c->by = 4;
+    if (c->precision != VPLBM_F64) {   // default: the software-pipelined kernel
+        c->kernel = KERNEL_ASYNC;
+        c->bx = 128;
+        c->by = 2;
     }
     // populations at rest
     StepParams q = params_for(c, 0);
@@ -749,9 +754,12 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
         c->by = 2;
         return VPLBM_OK;
     }
-    if (kernel != KERNEL_SCALAR && kernel != KERNEL_PAIR) return fail(VPLBM_EINVAL, "unknown kernel %d", kernel);
+    if (kernel != KERNEL_SCALAR && kernel != KERNEL_PAIR && kernel != KERNEL_ASYNC)
+        return fail(VPLBM_EINVAL, "unknown kernel %d", kernel);
     if (kernel == KERNEL_PAIR && !pair_ok(c))
         return fail(VPLBM_EUNSUPPORTED, "the paired kernel needs FP32/FP16 storage and an even nx");
+    if (kernel == KERNEL_ASYNC && c->precision == VPLBM_F64)
+        return fail(VPLBM_EUNSUPPORTED, "the pipelined kernel needs FP32/FP16 storage");
     const int t = bx * by;
     if (bx < 32 || bx % 32 || by < 1 || (t != 128 && t != 256))
         return fail(VPLBM_EINVAL, "launch shape %dx%d not allowed", bx, by);
@@ -829,8 +837,9 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
         }
         // candidates: the TMA-staged kernel, then every shape of the paired
         // and of the scalar kernel
-        for (int cand = -1; cand < 2 * N_SHAPES; ++cand) {
-            const int ck = cand < 0 ? KERNEL_TMA : (cand < N_SHAPES ? KERNEL_PAIR : KERNEL_SCALAR);
+        for (int cand = -1; cand < 3 * N_SHAPES; ++cand) {
+            const int ck = cand < 0 ? KERNEL_TMA
+                         : (cand < N_SHAPES ? KERNEL_ASYNC : (cand < 2 * N_SHAPES ? KERNEL_PAIR : KERNEL_SCALAR));
             const int cbx = cand < 0 ? 0 : SHAPES[cand % N_SHAPES][0];
             const int cby = cand < 0 ? 0 : SHAPES[cand % N_SHAPES][1];
             if (vplbm_set_launch(c, ck, cbx, cby) != VPLBM_OK) continue;

@@ -128,7 +128,12 @@ __host__ __device__ inline void derive_pose(BodyState &s, int present, double ra
 }
 
 // Step kernels a context can launch.
-enum { KERNEL_SCALAR = 0, KERNEL_PAIR = 1, KERNEL_TMA = 2 };
+enum { KERNEL_SCALAR = 0, KERNEL_PAIR = 1, KERNEL_TMA = 2, KERNEL_ASYNC = 3 };
+
+// Software-pipelined step (step_async.cu): block (bx, by) covers
+// bx x (by * async_rows_per_thread()) nodes.
+int async_rows_per_thread();
+cudaError_t launch_step_async(int precision, const StepParams &p, int bx, int by, cudaStream_t stream);
 
 // Paired FP32x2 step (step_pair.cu): block (bx, by) covers 2*bx x by nodes.
 cudaError_t launch_step_pair(int precision, const StepParams &p, int bx, int by, cudaStream_t stream);
