@@ -213,13 +213,18 @@ vplbm_status vplbm_get_body(vplbm_ctx *ctx, double q[3], double v[3], long long 
  *                       nx >= 136 (FP32) / 144 (FP16), ny >= 6);
  *  VPLBM_KERNEL_ASYNC   four nodes per thread down a column, their
  *                       populations copied to shared memory two nodes ahead
- *                       of the collision (FP32/FP16 storage); the default
- *                       for FP32/FP16 storage.
+ *                       of the collision (FP32/FP16 storage);
+ *  VPLBM_KERNEL_PIPE    a warp walks four rows of a 64-column strip, two
+ *                       nodes per lane, the rows it pulls copied to shared
+ *                       memory two rows ahead, packed FP32x2 collision
+ *                       (FP32/FP16 storage, even nx; block_x 128 or 256,
+ *                       block_y 1); the default where the lattice allows it.
  * Nodes on the lattice edges and near the body always take the scalar
  * arithmetic.  The results of different kernels agree to the rounding of
  * the storage precision. */
 typedef enum {
-    VPLBM_KERNEL_SCALAR = 0, VPLBM_KERNEL_PAIR = 1, VPLBM_KERNEL_TMA = 2, VPLBM_KERNEL_ASYNC = 3
+    VPLBM_KERNEL_SCALAR = 0, VPLBM_KERNEL_PAIR = 1, VPLBM_KERNEL_TMA = 2, VPLBM_KERNEL_ASYNC = 3,
+    VPLBM_KERNEL_PIPE = 4
 } vplbm_kernel;
 
 /* Kernel and block shape: block_x * block_y threads, block_x a multiple of

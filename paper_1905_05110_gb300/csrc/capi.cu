@@ -178,7 +178,7 @@ void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long 
     long long parts = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr,
                                            TMA_TILE_W, TMA_TILE_H);
     for (int k = 0; k < N_SHAPES; ++k)
-        for (int kern = KERNEL_SCALAR; kern <= KERNEL_ASYNC; ++kern) {   // every kernel's tiling
+        for (int kern = KERNEL_SCALAR; kern <= KERNEL_PIPE; ++kern) {   // every kernel's tiling
             int w, h;
             tile_of(kern, SHAPES[k][0], SHAPES[k][1], &w, &h);
             const long long m = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr, w, h);
@@ -225,6 +225,7 @@ cudaError_t launch_one(const vplbm_ctx *c, long long step, cudaStream_t stream)
     if (c->kernel == KERNEL_TMA) return launch_step_tma(c->precision, p, c->tmap[step & 1], c->tma_grid, stream);
     if (c->kernel == KERNEL_PAIR) return launch_step_pair(c->precision, p, c->bx, c->by, stream);
     if (c->kernel == KERNEL_ASYNC) return launch_step_async(c->precision, p, c->bx, c->by, stream);
+    if (c->kernel == KERNEL_PIPE) return launch_step_pipe(c->precision, p, c->bx, stream);
     return launch_step(c->precision, p, c->bx, c->by, stream);
 }
 
@@ -239,6 +240,7 @@ void tile_of(int kernel, int bx, int by, int *w, int *h)
     if (kernel == KERNEL_TMA) { *w = TMA_TILE_W; *h = TMA_TILE_H; }
     else if (kernel == KERNEL_PAIR) { *w = 2 * bx; *h = by; }
     else if (kernel == KERNEL_ASYNC) { *w = bx; *h = by * async_rows_per_thread(); }
+    else if (kernel == KERNEL_PIPE) { *w = 64; *h = (bx / 32) * pipe_rows_per_warp(); }
     else { *w = bx; *h = by; }
 }
 
@@ -394,7 +396,9 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     p.hist_cap = cap;
 
     setup_tma(c);
-    if (c->precision != VPLBM_F64) {   // default: the software-pipelined kernel
+    if (pair_ok(c) && vplbm_set_launch(c, KERNEL_PIPE, 256, 1) == VPLBM_OK) {
+        // default: the warp-pipelined paired kernel
+    } else if (c->precision != VPLBM_F64) {
         c->kernel = KERNEL_ASYNC;
         c->bx = 128;
         c->by = 2;
@@ -754,6 +758,20 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
         c->by = 2;
         return VPLBM_OK;
     }
+    if (kernel == KERNEL_PIPE) {
+        if (!pair_ok(c)) return fail(VPLBM_EUNSUPPORTED, "the warp-pipelined kernel needs FP32/FP16 storage and an even nx");
+        if (bx != 128 && bx != 256) return fail(VPLBM_EINVAL, "the warp-pipelined kernel takes 128 or 256 threads");
+        int w, h;
+        tile_of(kernel, bx, 1, &w, &h);
+        if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, w, h) > c->max_parts)
+            return fail(VPLBM_EINVAL, "launch shape needs more reduction scratch than allocated");
+        cudaError_t e = pipe_prepare(c->precision, bx);
+        if (e != cudaSuccess) return fail(VPLBM_ECUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(e));
+        c->kernel = kernel;
+        c->bx = bx;
+        c->by = 1;
+        return VPLBM_OK;
+    }
     if (kernel != KERNEL_SCALAR && kernel != KERNEL_PAIR && kernel != KERNEL_ASYNC)
         return fail(VPLBM_EINVAL, "unknown kernel %d", kernel);
     if (kernel == KERNEL_PAIR && !pair_ok(c))
@@ -837,11 +855,11 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
         }
         // candidates: the TMA-staged kernel, then every shape of the paired
         // and of the scalar kernel
-        for (int cand = -1; cand < 3 * N_SHAPES; ++cand) {
-            const int ck = cand < 0 ? KERNEL_TMA
+        for (int cand = -3; cand < 3 * N_SHAPES; ++cand) {
+            const int ck = cand == -3 ? KERNEL_TMA : cand < 0 ? KERNEL_PIPE
                          : (cand < N_SHAPES ? KERNEL_ASYNC : (cand < 2 * N_SHAPES ? KERNEL_PAIR : KERNEL_SCALAR));
-            const int cbx = cand < 0 ? 0 : SHAPES[cand % N_SHAPES][0];
-            const int cby = cand < 0 ? 0 : SHAPES[cand % N_SHAPES][1];
+            const int cbx = cand == -3 ? 0 : cand == -2 ? 256 : cand == -1 ? 128 : SHAPES[cand % N_SHAPES][0];
+            const int cby = cand < 0 ? 1 : SHAPES[cand % N_SHAPES][1];
             if (vplbm_set_launch(c, ck, cbx, cby) != VPLBM_OK) continue;
             for (int rep = 0; rep < 2; ++rep) {   // first pass warms up
                 if (restore() != cudaSuccess) { st = fail(VPLBM_ECUDA, "autotune restore failed"); break; }

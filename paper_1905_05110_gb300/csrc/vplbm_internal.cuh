@@ -128,7 +128,13 @@ __host__ __device__ inline void derive_pose(BodyState &s, int present, double ra
 }
 
 // Step kernels a context can launch.
-enum { KERNEL_SCALAR = 0, KERNEL_PAIR = 1, KERNEL_TMA = 2, KERNEL_ASYNC = 3 };
+enum { KERNEL_SCALAR = 0, KERNEL_PAIR = 1, KERNEL_TMA = 2, KERNEL_ASYNC = 3, KERNEL_PIPE = 4 };
+
+// Warp-pipelined paired step (step_pipe.cu): block (bx, 1), bx in {128, 256},
+// covers 64 x (bx / 32 * pipe_rows_per_warp()) nodes.
+int pipe_rows_per_warp();
+cudaError_t pipe_prepare(int precision, int bx);
+cudaError_t launch_step_pipe(int precision, const StepParams &p, int bx, cudaStream_t stream);
 
 // Software-pipelined step (step_async.cu): block (bx, by) covers
 // bx x (by * async_rows_per_thread()) nodes.
