@@ -218,13 +218,19 @@ vplbm_status vplbm_get_body(vplbm_ctx *ctx, double q[3], double v[3], long long 
  *                       nodes per lane, the rows it pulls copied to shared
  *                       memory two rows ahead, packed FP32x2 collision
  *                       (FP32/FP16 storage, even nx; block_x 128 or 256,
- *                       block_y 1); the default where the lattice allows it.
+ *                       block_y 1);
+ *  VPLBM_KERNEL_STREAM  persistent blocks walk runs of 2*block_x x block_y
+ *                       tiles, two nodes per thread, the next tile's
+ *                       populations prefetched into registers while the
+ *                       current one collides on the packed FP32x2 pipe
+ *                       (FP32/FP16 storage, even nx); the default where the
+ *                       lattice allows it.
  * Nodes on the lattice edges and near the body always take the scalar
  * arithmetic.  The results of different kernels agree to the rounding of
  * the storage precision. */
 typedef enum {
     VPLBM_KERNEL_SCALAR = 0, VPLBM_KERNEL_PAIR = 1, VPLBM_KERNEL_TMA = 2, VPLBM_KERNEL_ASYNC = 3,
-    VPLBM_KERNEL_PIPE = 4
+    VPLBM_KERNEL_PIPE = 4, VPLBM_KERNEL_STREAM = 5
 } vplbm_kernel;
 
 /* Kernel and block shape: block_x * block_y threads, block_x a multiple of
@@ -253,6 +259,37 @@ vplbm_status vplbm_get_launch_count(vplbm_ctx *ctx, long long *launches);
  * with the same lattice size, precision and history capacity. */
 vplbm_status vplbm_save(vplbm_ctx *ctx, const char *path);
 vplbm_status vplbm_load(vplbm_ctx *ctx, const char *path);
+
+/* ---- batched sweep ---------------------------------------------------------
+ * Many independent simulations of uneven lattice sizes (a parameter sweep:
+ * stiffness, reduced velocity, ... as in the vortex-induced-vibration study
+ * of Sec. 3.3) advanced together: one kernel launch per time step covers the
+ * tiles of every member (warp-pipelined paired kernel), K steps at a time
+ * as CUDA graphs, each member keeping its own body, force reduction, tail
+ * and history.  Members are ordinary contexts (vplbm_batch_member): every
+ * per-simulation call (init, fields, history, body, checkpoints) works on
+ * them; vplbm_step on a single member would take it out of step with the
+ * others, which vplbm_batch_step then rejects with VPLBM_EINVAL.
+ * All members: same precision, FP32 or FP16 deviation storage, even nx. */
+typedef struct vplbm_batch vplbm_batch;
+
+/* lats[0..n-1] describe the members; bodies is NULL (no body anywhere) or an
+ * array of n pointers (NULL entries: that member has no body). */
+vplbm_status vplbm_batch_create(const vplbm_lattice_desc *lats, const vplbm_body_desc *const *bodies, int n,
+                                long long history_capacity, void *cuda_stream, vplbm_batch **out);
+void vplbm_batch_destroy(vplbm_batch *batch);   /* destroys the members too */
+vplbm_status vplbm_batch_member(vplbm_batch *batch, int k, vplbm_ctx **member);
+/* nsteps time steps of every member (asynchronous on the batch's stream). */
+vplbm_status vplbm_batch_step(vplbm_batch *batch, long long nsteps);
+/* Wait; returns the first member's latched device error, if any. */
+vplbm_status vplbm_batch_sync(vplbm_batch *batch);
+/* Threads per block of the batched kernel (128 or 256) and the number of
+ * batched step launches made so far. */
+vplbm_status vplbm_batch_set_launch(vplbm_batch *batch, int block_x);
+vplbm_status vplbm_batch_get_launch(vplbm_batch *batch, int *block_x, long long *launches);
+/* Time each block width over 2 x steps_per_trial steps and keep the fastest;
+ * the trial steps advance the members (they are real steps). */
+vplbm_status vplbm_batch_autotune(vplbm_batch *batch, int steps_per_trial);
 
 /* ---- allocation-free stepping --------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that

@@ -26,7 +26,9 @@ __all__ = [
     "vplbm_get_populations", "vplbm_get_fields", "vplbm_get_fields_dev", "vplbm_get_history",
     "vplbm_get_body", "vplbm_set_launch", "vplbm_get_launch", "vplbm_autotune",
     "vplbm_get_launch_count", "vplbm_save", "vplbm_load", "vplbm_last_error", "vplbm_version",
-    "vplbm_step_noalloc", "BodyState", "vplbm_inject_wait_timeout",
+    "vplbm_step_noalloc", "BodyState", "vplbm_inject_wait_timeout", "Batch",
+    "vplbm_batch_create", "vplbm_batch_destroy", "vplbm_batch_member", "vplbm_batch_step",
+    "vplbm_batch_sync", "vplbm_batch_set_launch", "vplbm_batch_get_launch", "vplbm_batch_autotune",
     "EXPORTED_SYMBOLS", "RECORD_FIELDS",
 ]
 
@@ -122,6 +124,15 @@ _SIGS = {
     "vplbm_load": (C.c_int, [_CTX, C.c_char_p]),
     "vplbm_step_noalloc": (C.c_int, [C.POINTER(LatticeDesc), C.POINTER(BodyDesc), C.c_void_p * 2,
                                      C.c_void_p, C.c_void_p, C.c_longlong, C.c_longlong, C.c_void_p]),
+    "vplbm_batch_create": (C.c_int, [C.POINTER(LatticeDesc), C.c_void_p, C.c_int, C.c_longlong, C.c_void_p,
+                                     C.POINTER(C.c_void_p)]),
+    "vplbm_batch_destroy": (None, [C.c_void_p]),
+    "vplbm_batch_member": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(_CTX)]),
+    "vplbm_batch_step": (C.c_int, [C.c_void_p, C.c_longlong]),
+    "vplbm_batch_sync": (C.c_int, [C.c_void_p]),
+    "vplbm_batch_set_launch": (C.c_int, [C.c_void_p, C.c_int]),
+    "vplbm_batch_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
+    "vplbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int]),
     "vplbm_last_error": (C.c_char_p, []),
     "vplbm_version": (C.c_char_p, []),
 }
@@ -307,7 +318,7 @@ def vplbm_get_body(ctx):
     return q, v, int(step.value)
 
 
-KERNELS = {"scalar": 0, "pair": 1, "tma": 2, "async": 3, "pipe": 4}
+KERNELS = {"scalar": 0, "pair": 1, "tma": 2, "async": 3, "pipe": 4, "stream": 5}
 KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
 
 
@@ -342,6 +353,50 @@ def vplbm_step_noalloc(lat: LatticeDesc, body: BodyDesc | None, populations_ptrs
     _check(load_library().vplbm_step_noalloc(C.byref(lat), _byref(body), pops, C.c_void_p(state_ptr),
                                              C.c_void_p(history_ptr or 0), int(history_capacity),
                                              int(nsteps), C.c_void_p(stream)))
+
+
+def vplbm_batch_create(lats, bodies, history_capacity: int, stream: int = 0):
+    """lats: list of LatticeDesc; bodies: list of BodyDesc or None per member."""
+    n = len(lats)
+    lat_arr = (LatticeDesc * n)(*lats)
+    body_ptrs = (C.POINTER(BodyDesc) * n)(*[C.pointer(b) if b is not None else C.POINTER(BodyDesc)()
+                                            for b in bodies])
+    out = C.c_void_p()
+    _check(load_library().vplbm_batch_create(lat_arr, C.cast(body_ptrs, C.c_void_p), n, int(history_capacity),
+                                             C.c_void_p(stream), C.byref(out)))
+    return out
+
+
+def vplbm_batch_destroy(batch):
+    load_library().vplbm_batch_destroy(batch)
+
+
+def vplbm_batch_member(batch, k: int):
+    ctx = _CTX()
+    _check(load_library().vplbm_batch_member(batch, int(k), C.byref(ctx)))
+    return ctx
+
+
+def vplbm_batch_step(batch, nsteps: int):
+    _check(load_library().vplbm_batch_step(batch, int(nsteps)))
+
+
+def vplbm_batch_sync(batch):
+    _check(load_library().vplbm_batch_sync(batch))
+
+
+def vplbm_batch_set_launch(batch, block_x: int):
+    _check(load_library().vplbm_batch_set_launch(batch, int(block_x)))
+
+
+def vplbm_batch_get_launch(batch):
+    bx, n = C.c_int(), C.c_longlong()
+    _check(load_library().vplbm_batch_get_launch(batch, C.byref(bx), C.byref(n)))
+    return bx.value, int(n.value)
+
+
+def vplbm_batch_autotune(batch, steps_per_trial: int = 8):
+    _check(load_library().vplbm_batch_autotune(batch, int(steps_per_trial)))
 
 
 def vplbm_save(ctx, path: str):
@@ -479,3 +534,69 @@ class Simulation:
 
     def load(self, path):
         vplbm_load(self.ctx, path)
+
+
+class _Member:
+    """A batch member: the per-simulation calls on a context the batch owns."""
+
+    def __init__(self, ctx, problem):
+        self.ctx = ctx
+        self.problem = problem
+        self.nx, self.ny = int(problem["nx"]), int(problem["ny"])
+
+    init_equilibrium = Simulation.init_equilibrium
+    init_from_problem = Simulation.init_from_problem
+    set_populations = Simulation.set_populations
+    populations = Simulation.populations
+    fields = Simulation.fields
+    history = Simulation.history
+    body_state = Simulation.body_state
+    nstep = Simulation.nstep
+
+
+class Batch:
+    """Many simulations of uneven sizes stepped together (one launch per step)."""
+
+    def __init__(self, problems, precision: str = "f32", history_capacity: int = 1 << 12, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Batch needs a CUDA device; there is no CPU fallback")
+        self.problems = list(problems)
+        self._keep: list = []
+        lats = [lattice_desc(p, precision, self._keep) for p in self.problems]
+        bodies = [body_desc(p.get("body")) for p in self.problems]
+        self._bodies = bodies
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = vplbm_batch_create(lats, bodies, history_capacity, self.stream.cuda_stream)
+        self.members = [_Member(vplbm_batch_member(self.handle, k), p) for k, p in enumerate(self.problems)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            vplbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_from_problems(self):
+        for m in self.members:
+            m.init_from_problem()
+
+    def step(self, n: int = 1):
+        vplbm_batch_step(self.handle, n)
+
+    def sync(self):
+        vplbm_batch_sync(self.handle)
+
+    def set_launch(self, block_x: int):
+        vplbm_batch_set_launch(self.handle, block_x)
+
+    def launch(self):
+        return vplbm_batch_get_launch(self.handle)
+
+    def autotune(self, steps_per_trial: int = 8):
+        vplbm_batch_autotune(self.handle, steps_per_trial)
+        return self.launch()[0]

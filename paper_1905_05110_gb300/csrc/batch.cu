@@ -1,0 +1,303 @@
+// Batched sweep: many simulations of uneven lattice sizes stepped together,
+// one launch per time step covering every member's tiles (captured as CUDA
+// graphs of 32 steps), each member with its own body, reduction and tail.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "vplbm_ctx.cuh"
+
+using namespace vplbm;
+
+namespace {
+
+constexpr int BATCH_GRAPH_STEPS = 32;
+
+vplbm_status berr(vplbm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return report_error(st, buf);
+}
+
+}  // namespace
+
+struct vplbm_batch {
+    int n = 0;
+    std::vector<vplbm_ctx *> members;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;
+    int precision = 0;
+    int bx = 256;                     // threads per block of the batched kernel
+    StepParams *params_dev = nullptr; // [2][n]: parameters of each member per step parity
+    int *tile_start_dev = nullptr;    // [n + 1]
+    int total_tiles = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_bx = -1;
+    long long launches = 0;
+};
+
+namespace {
+
+// Tile prefix of the members for block width bx (tiles of 64 x bx/32*rows).
+vplbm_status build_tiles(vplbm_batch *b)
+{
+    std::vector<int> start(b->n + 1, 0);
+    const int tile_h = (b->bx / 32) * pipe_rows_per_warp();
+    long long total = 0;
+    for (int k = 0; k < b->n; ++k) {
+        const vplbm_ctx *c = b->members[k];
+        start[k] = (int)total;
+        total += (long long)((c->nx + 63) / 64) * ((c->ny + tile_h - 1) / tile_h);
+    }
+    if (total > (1LL << 30)) return berr(VPLBM_EINVAL, "batch too large (%lld tiles)", total);
+    start[b->n] = (int)total;
+    b->total_tiles = (int)total;
+    cudaError_t e = cudaMemcpyAsync(b->tile_start_dev, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return berr(VPLBM_ECUDA, "tile table upload failed: %s", cudaGetErrorString(e));
+    return VPLBM_OK;
+}
+
+vplbm_status upload_params(vplbm_batch *b)
+{
+    std::vector<StepParams> ps(2 * (size_t)b->n);
+    for (int par = 0; par < 2; ++par)
+        for (int k = 0; k < b->n; ++k) ps[(size_t)par * b->n + k] = ctx_params(b->members[k], par);
+    cudaError_t e = cudaMemcpyAsync(b->params_dev, ps.data(), ps.size() * sizeof(StepParams), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return berr(VPLBM_ECUDA, "parameter upload failed: %s", cudaGetErrorString(e));
+    return VPLBM_OK;
+}
+
+cudaError_t launch_batch_step(const vplbm_batch *b, long long step, cudaStream_t stream)
+{
+    BatchLaunch bl;
+    bl.params = b->params_dev + (size_t)(step & 1) * b->n;
+    bl.tile_start = b->tile_start_dev;
+    bl.n = b->n;
+    return launch_step_pipe_batch(b->precision, bl, b->total_tiles, b->bx, stream);
+}
+
+// All members must stand at the same step (they advance together).
+vplbm_status common_step(const vplbm_batch *b, long long *step)
+{
+    const long long s = b->members[0]->nstep;
+    for (int k = 1; k < b->n; ++k)
+        if (b->members[k]->nstep != s)
+            return berr(VPLBM_EINVAL, "batch members are at different steps (%lld vs %lld)", s, b->members[k]->nstep);
+    *step = s;
+    return VPLBM_OK;
+}
+
+vplbm_status ensure_batch_graph(vplbm_batch *b)
+{
+    if (b->graph && b->graph_bx == b->bx) return VPLBM_OK;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return berr(VPLBM_ECUDA, "capture begin failed: %s", cudaGetErrorString(e));
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < BATCH_GRAPH_STEPS && err == cudaSuccess; ++k) err = launch_batch_step(b, k, b->capture);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->capture, &g);
+    if (err != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return berr(VPLBM_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(err != cudaSuccess ? err : e));
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return berr(VPLBM_ECUDA, "batch graph instantiate failed: %s", cudaGetErrorString(e));
+    b->graph_bx = b->bx;
+    return VPLBM_OK;
+}
+
+vplbm_status batch_step_impl(vplbm_batch *b, long long n)
+{
+    long long step;
+    vplbm_status st = common_step(b, &step);
+    if (st != VPLBM_OK) return st;
+    long long done = 0;
+    while (done < n) {
+        long long adv;
+        if (((step + done) & 1) == 0 && n - done >= BATCH_GRAPH_STEPS) {
+            st = ensure_batch_graph(b);
+            if (st != VPLBM_OK) break;
+            cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+            if (e != cudaSuccess) { st = berr(VPLBM_ECUDA, "batch graph launch failed: %s", cudaGetErrorString(e)); break; }
+            adv = BATCH_GRAPH_STEPS;
+        } else {
+            cudaError_t e = launch_batch_step(b, step + done, b->stream);
+            if (e != cudaSuccess) { st = berr(VPLBM_ECUDA, "batch launch failed: %s", cudaGetErrorString(e)); break; }
+            adv = 1;
+        }
+        done += adv;
+        b->launches += adv;
+    }
+    for (int k = 0; k < b->n; ++k) b->members[k]->nstep = step + done;
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+void vplbm_batch_destroy(vplbm_batch *b)
+{
+    if (!b) return;
+    if (b->stream || b->params_dev) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    if (b->params_dev) cudaFree(b->params_dev);
+    if (b->tile_start_dev) cudaFree(b->tile_start_dev);
+    for (vplbm_ctx *c : b->members) vplbm_destroy(c);
+    delete b;
+}
+
+vplbm_status vplbm_batch_create(const vplbm_lattice_desc *lats, const vplbm_body_desc *const *bodies, int n,
+                                long long history_capacity, void *cuda_stream, vplbm_batch **out)
+{
+    if (!out || !lats || n < 1) return berr(VPLBM_EINVAL, "need n >= 1 lattice descriptors and an out pointer");
+    *out = nullptr;
+    const int prec = lats[0].precision;
+    for (int k = 0; k < n; ++k) {
+        if (lats[k].precision != prec) return berr(VPLBM_EINVAL, "member %d: all members need the same precision", k);
+        if (prec != VPLBM_F32_DEV && prec != VPLBM_F16_DEV)
+            return berr(VPLBM_EUNSUPPORTED, "the batched step runs FP32/FP16 deviation storage");
+        if (lats[k].nx % 2) return berr(VPLBM_EUNSUPPORTED, "member %d: the batched step needs an even nx", k);
+    }
+    vplbm_batch *b = new (std::nothrow) vplbm_batch();
+    if (!b) return berr(VPLBM_ENOMEM, "host allocation failed");
+    b->n = n;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->precision = prec;
+    vplbm_status st = VPLBM_OK;
+    try {
+        b->members.assign(n, nullptr);
+    } catch (...) {
+        delete b;
+        return berr(VPLBM_ENOMEM, "host allocation failed");
+    }
+    for (int k = 0; k < n && st == VPLBM_OK; ++k)
+        st = vplbm_create(&lats[k], bodies ? bodies[k] : nullptr, history_capacity, cuda_stream, &b->members[k]);
+    cudaError_t e = cudaSuccess;
+    if (st == VPLBM_OK) {
+        e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaMalloc(&b->params_dev, 2 * (size_t)n * sizeof(StepParams));
+        if (e == cudaSuccess) e = cudaMalloc(&b->tile_start_dev, (size_t)(n + 1) * sizeof(int));
+        if (e == cudaSuccess) e = pipe_batch_prepare(prec, b->bx);
+        if (e != cudaSuccess) st = berr(VPLBM_ECUDA, "batch setup failed: %s", cudaGetErrorString(e));
+    }
+    if (st == VPLBM_OK) st = upload_params(b);
+    if (st == VPLBM_OK) st = build_tiles(b);
+    if (st != VPLBM_OK) {
+        vplbm_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return VPLBM_OK;
+}
+
+vplbm_status vplbm_batch_member(vplbm_batch *b, int k, vplbm_ctx **member)
+{
+    if (!b || !member || k < 0 || k >= b->n) return berr(VPLBM_EINVAL, "no member %d", k);
+    *member = b->members[k];
+    return VPLBM_OK;
+}
+
+vplbm_status vplbm_batch_step(vplbm_batch *b, long long nsteps)
+{
+    if (!b) return berr(VPLBM_EINVAL, "batch is NULL");
+    if (nsteps < 0) return berr(VPLBM_EINVAL, "nsteps must be >= 0");
+    return batch_step_impl(b, nsteps);
+}
+
+vplbm_status vplbm_batch_sync(vplbm_batch *b)
+{
+    if (!b) return berr(VPLBM_EINVAL, "batch is NULL");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return berr(VPLBM_ECUDA, "stream synchronize failed: %s", cudaGetErrorString(e));
+    for (int k = 0; k < b->n; ++k) {
+        vplbm_status st = ctx_read_error(b->members[k]);
+        if (st != VPLBM_OK) return st;
+    }
+    return VPLBM_OK;
+}
+
+vplbm_status vplbm_batch_set_launch(vplbm_batch *b, int block_x)
+{
+    if (!b) return berr(VPLBM_EINVAL, "batch is NULL");
+    if (block_x != 128 && block_x != 256) return berr(VPLBM_EINVAL, "block_x must be 128 or 256");
+    for (int k = 0; k < b->n; ++k) {
+        const vplbm_ctx *c = b->members[k];
+        const int tile_h = (block_x / 32) * pipe_rows_per_warp();
+        if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, 64, tile_h) >
+            c->max_parts)
+            return berr(VPLBM_EINVAL, "member %d: launch shape needs more reduction scratch than allocated", k);
+    }
+    cudaError_t e = pipe_batch_prepare(b->precision, block_x);
+    if (e != cudaSuccess) return berr(VPLBM_ECUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(e));
+    const int old = b->bx;
+    b->bx = block_x;
+    vplbm_status st = build_tiles(b);
+    if (st != VPLBM_OK) {
+        b->bx = old;
+        build_tiles(b);
+    }
+    return st;
+}
+
+vplbm_status vplbm_batch_get_launch(vplbm_batch *b, int *block_x, long long *launches)
+{
+    if (!b) return berr(VPLBM_EINVAL, "batch is NULL");
+    if (block_x) *block_x = b->bx;
+    if (launches) *launches = b->launches;
+    return VPLBM_OK;
+}
+
+vplbm_status vplbm_batch_autotune(vplbm_batch *b, int steps_per_trial)
+{
+    if (!b) return berr(VPLBM_EINVAL, "batch is NULL");
+    if (steps_per_trial < 2) steps_per_trial = 2;
+    steps_per_trial += steps_per_trial & 1;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return berr(VPLBM_ECUDA, "event creation failed");
+    float best = 1e30f;
+    int best_bx = b->bx;
+    vplbm_status st = VPLBM_OK;
+    const int cands[2] = {256, 128};
+    for (int bx : cands) {
+        st = vplbm_batch_set_launch(b, bx);
+        if (st != VPLBM_OK) break;
+        for (int rep = 0; rep < 2 && st == VPLBM_OK; ++rep) {
+            cudaEventRecord(e0, b->stream);
+            st = batch_step_impl(b, steps_per_trial);
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = berr(VPLBM_ECUDA, "autotune timing failed");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1 && ms < best) {
+                best = ms;
+                best_bx = bx;
+            }
+        }
+        if (st != VPLBM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    vplbm_status st2 = vplbm_batch_set_launch(b, best_bx);
+    return st != VPLBM_OK ? st : st2;
+}
+
+}  // extern "C"

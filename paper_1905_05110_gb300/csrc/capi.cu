@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "vplbm_internal.cuh"
+#include "vplbm_ctx.cuh"
 
 using namespace vplbm;
 
@@ -93,38 +93,6 @@ namespace vplbm {
 vplbm_status report_error(vplbm_status st, const char *msg) { return fail(st, "%s", msg); }
 }  // namespace vplbm
 
-struct vplbm_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;        // caller's stream
-    cudaStream_t capture = nullptr;       // private stream used only to capture graphs
-    int precision = 0;
-    int nx = 0, ny = 0;
-    long long ps = 0;                     // plane stride (elements)
-    size_t pop_bytes = 0;
-    StepParams base{};
-    vplbm_body_desc body_desc{};
-    bool has_body = false;
-    void *f[2] = {nullptr, nullptr};
-    BodyState *bs = nullptr;              // [2]
-    double *partials = nullptr;
-    long long max_parts = 0;
-    Control *ctrl = nullptr;
-    vplbm_record *hist = nullptr;
-    long long hist_cap = 0;
-    double *prof = nullptr;
-    void *owned = nullptr;                // single allocation when the library owns memory
-    long long nstep = 0;
-    int kernel = KERNEL_SCALAR;           // KERNEL_SCALAR / KERNEL_PAIR / KERNEL_TMA
-    int bx = 128, by = 2;
-    cudaGraphExec_t graph = nullptr;
-    int graph_kernel = -1, graph_bx = -1, graph_by = -1;
-    long long launches = 0;
-    // TMA-staged kernel (FP32/FP16 storage): tensor maps of the two
-    // population buffers as sources, persistent grid size
-    bool tma_ok = false;
-    CUtensorMap tmap[2];
-    int tma_grid = 0;
-};
 
 namespace {
 
@@ -178,7 +146,7 @@ void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long 
     long long parts = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr,
                                            TMA_TILE_W, TMA_TILE_H);
     for (int k = 0; k < N_SHAPES; ++k)
-        for (int kern = KERNEL_SCALAR; kern <= KERNEL_PIPE; ++kern) {   // every kernel's tiling
+        for (int kern = KERNEL_SCALAR; kern <= KERNEL_STREAM; ++kern) {   // every kernel's tiling
             int w, h;
             tile_of(kern, SHAPES[k][0], SHAPES[k][1], &w, &h);
             const long long m = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr, w, h);
@@ -226,6 +194,7 @@ cudaError_t launch_one(const vplbm_ctx *c, long long step, cudaStream_t stream)
     if (c->kernel == KERNEL_PAIR) return launch_step_pair(c->precision, p, c->bx, c->by, stream);
     if (c->kernel == KERNEL_ASYNC) return launch_step_async(c->precision, p, c->bx, c->by, stream);
     if (c->kernel == KERNEL_PIPE) return launch_step_pipe(c->precision, p, c->bx, stream);
+    if (c->kernel == KERNEL_STREAM) return launch_step_stream(c->precision, p, c->bx, c->by, c->stream_grid, stream);
     return launch_step(c->precision, p, c->bx, c->by, stream);
 }
 
@@ -241,6 +210,7 @@ void tile_of(int kernel, int bx, int by, int *w, int *h)
     else if (kernel == KERNEL_PAIR) { *w = 2 * bx; *h = by; }
     else if (kernel == KERNEL_ASYNC) { *w = bx; *h = by * async_rows_per_thread(); }
     else if (kernel == KERNEL_PIPE) { *w = 64; *h = (bx / 32) * pipe_rows_per_warp(); }
+    else if (kernel == KERNEL_STREAM) { *w = 2 * bx; *h = by; }
     else { *w = bx; *h = by; }
 }
 
@@ -396,8 +366,8 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     p.hist_cap = cap;
 
     setup_tma(c);
-    if (pair_ok(c) && vplbm_set_launch(c, KERNEL_PIPE, 256, 1) == VPLBM_OK) {
-        // default: the warp-pipelined paired kernel
+    if (pair_ok(c) && vplbm_set_launch(c, KERNEL_STREAM, 64, 4) == VPLBM_OK) {
+        // default: the streaming paired kernel
     } else if (c->precision != VPLBM_F64) {
         c->kernel = KERNEL_ASYNC;
         c->bx = 128;
@@ -569,6 +539,12 @@ struct CkptHeader {
 };
 
 }  // namespace
+
+namespace vplbm {
+StepParams ctx_params(const vplbm_ctx *c, long long step) { return params_for(c, step); }
+cudaError_t ctx_launch(const vplbm_ctx *c, long long step, cudaStream_t stream) { return launch_one(c, step, stream); }
+vplbm_status ctx_read_error(vplbm_ctx *c) { return read_error(c); }
+}  // namespace vplbm
 
 // ---------------------------------------------------------------- C ABI
 
@@ -772,8 +748,10 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
         c->by = 1;
         return VPLBM_OK;
     }
-    if (kernel != KERNEL_SCALAR && kernel != KERNEL_PAIR && kernel != KERNEL_ASYNC)
+    if (kernel != KERNEL_SCALAR && kernel != KERNEL_PAIR && kernel != KERNEL_ASYNC && kernel != KERNEL_STREAM)
         return fail(VPLBM_EINVAL, "unknown kernel %d", kernel);
+    if (kernel == KERNEL_STREAM && !pair_ok(c))
+        return fail(VPLBM_EUNSUPPORTED, "the streaming kernel needs FP32/FP16 storage and an even nx");
     if (kernel == KERNEL_PAIR && !pair_ok(c))
         return fail(VPLBM_EUNSUPPORTED, "the paired kernel needs FP32/FP16 storage and an even nx");
     if (kernel == KERNEL_ASYNC && c->precision == VPLBM_F64)
@@ -785,6 +763,13 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
     tile_of(kernel, bx, by, &w, &h);
     if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, w, h) > c->max_parts)
         return fail(VPLBM_EINVAL, "launch shape %dx%d needs more reduction scratch than allocated", bx, by);
+    if (kernel == KERNEL_STREAM) {
+        int per_sm = 0, nsm = 0;
+        cudaError_t e = stream_prepare(c->precision, bx, by, &per_sm);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+        if (e != cudaSuccess || per_sm < 1) return fail(VPLBM_ECUDA, "occupancy query failed");
+        c->stream_grid = per_sm * nsm;
+    }
     c->kernel = kernel;
     c->bx = bx;
     c->by = by;
@@ -855,9 +840,10 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
         }
         // candidates: the TMA-staged kernel, then every shape of the paired
         // and of the scalar kernel
-        for (int cand = -3; cand < 3 * N_SHAPES; ++cand) {
+        for (int cand = -3; cand < 4 * N_SHAPES; ++cand) {
             const int ck = cand == -3 ? KERNEL_TMA : cand < 0 ? KERNEL_PIPE
-                         : (cand < N_SHAPES ? KERNEL_ASYNC : (cand < 2 * N_SHAPES ? KERNEL_PAIR : KERNEL_SCALAR));
+                         : cand < N_SHAPES ? KERNEL_STREAM
+                         : (cand < 2 * N_SHAPES ? KERNEL_ASYNC : (cand < 3 * N_SHAPES ? KERNEL_PAIR : KERNEL_SCALAR));
             const int cbx = cand == -3 ? 0 : cand == -2 ? 256 : cand == -1 ? 128 : SHAPES[cand % N_SHAPES][0];
             const int cby = cand < 0 ? 1 : SHAPES[cand % N_SHAPES][1];
             if (vplbm_set_launch(c, ck, cbx, cby) != VPLBM_OK) continue;

@@ -46,30 +46,30 @@ __device__ __forceinline__ float2 lds2(const __half *row, int pos) { return __ha
 __device__ __forceinline__ float lds1(const float *row, int pos) { return row[pos]; }
 __device__ __forceinline__ float lds1(const __half *row, int pos) { return __half2float(row[pos]); }
 
+// One tile (64 x nwarps*PNK nodes) of the step; tile_x / tile_y index the
+// tile in the lattice, p may live in shared memory (batched launch).
 template <int P>
-__global__ void __launch_bounds__(256, 3) vp_mrt_step_pipe(const StepParams p)
+__device__ __forceinline__ void pipe_tile(const StepParams &p, int tile_x, int tile_y, unsigned char *smem,
+                                          double (*red)[NPART], int *s_last)
 {
     using S = typename Prec<P>::S;
     using T = typename Prec<P>::T;
     using C = Pipe<P>;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[8][NPART];
-    __shared__ int s_last;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int tile_h = nwarps * PNK;
     const int nx = p.nx, ny = p.ny;
     const long long ps = p.ps;
-    const int i0 = blockIdx.x * 64;
+    const int i0 = tile_x * 64;
     const int i = i0 + 2 * lane;
-    const int jw = blockIdx.y * tile_h + warp * PNK;
+    const int jw = tile_y * tile_h + warp * PNK;
     const S *__restrict__ fin = static_cast<const S *>(p.fin);
     S *__restrict__ fout = static_cast<S *>(p.fout);
     const BodyState *__restrict__ bs = p.bs_in;
 
     const int4 range = __ldg(reinterpret_cast<const int4 *>(&bs->ilo));   // ilo, ihi, jlo, jhi
-    const bool part_block = tile_near_body(range, i0, blockIdx.y * tile_h, 64, tile_h, blockIdx.x == 0 && blockIdx.y == 0);
+    const bool part_block = tile_near_body(range, i0, tile_y * tile_h, 64, tile_h, tile_x == 0 && tile_y == 0);
 
     if (!part_block) {   // uniform over the block
         unsigned char *wbuf = smem + warp * C::WARP_BYTES;
@@ -152,7 +152,47 @@ __global__ void __launch_bounds__(256, 3) vp_mrt_step_pipe(const StepParams p)
             }
         }
     }
-    tile_reduce(p, range, blockIdx.x, blockIdx.y, 64, tile_h, any_chi, part, red, &s_last);
+    tile_reduce(p, range, tile_x, tile_y, 64, tile_h, any_chi, part, red, s_last);
+}
+
+
+template <int P>
+__global__ void __launch_bounds__(256, 3) vp_mrt_step_pipe(const StepParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[8][NPART];
+    __shared__ int s_last;
+    pipe_tile<P>(p, blockIdx.x, blockIdx.y, smem, red, &s_last);
+}
+
+// Every member of a batch in one launch: block b runs tile b of the
+// concatenated tile lists; its member is found in the tile prefix and its
+// step parameters are staged in shared memory.
+template <int P>
+__global__ void __launch_bounds__(256, 3) vp_mrt_step_pipe_batch(const BatchLaunch bl)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[8][NPART];
+    __shared__ int s_last;
+    __shared__ __align__(16) StepParams sp;
+    __shared__ int s_member, s_local;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = bl.n - 1;   // last member whose first tile is <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bl.tile_start[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        s_member = lo;
+        s_local = (int)blockIdx.x - bl.tile_start[lo];
+    }
+    __syncthreads();
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(bl.params + s_member);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&sp);
+    for (int k = threadIdx.x; k < (int)(sizeof(StepParams) / 4); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    const int ntx = (sp.nx + 63) / 64;
+    pipe_tile<P>(sp, s_local % ntx, s_local / ntx, smem, red, &s_last);
 }
 
 }  // namespace
@@ -165,6 +205,26 @@ cudaError_t pipe_prepare(int precision, int bx)
     const void *fn = precision == VPLBM_F32_DEV ? (const void *)vp_mrt_step_pipe<VPLBM_F32_DEV>
                                                 : (const void *)vp_mrt_step_pipe<VPLBM_F16_DEV>;
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t pipe_batch_prepare(int precision, int bx)
+{
+    const int smem = (bx / 32) * (precision == VPLBM_F32_DEV ? Pipe<VPLBM_F32_DEV>::WARP_BYTES : Pipe<VPLBM_F16_DEV>::WARP_BYTES);
+    const void *fn = precision == VPLBM_F32_DEV ? (const void *)vp_mrt_step_pipe_batch<VPLBM_F32_DEV>
+                                                : (const void *)vp_mrt_step_pipe_batch<VPLBM_F16_DEV>;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_step_pipe_batch(int precision, const BatchLaunch &bl, int total_tiles, int bx, cudaStream_t stream)
+{
+    const int nwarps = bx / 32;
+    if (precision == VPLBM_F32_DEV)
+        vp_mrt_step_pipe_batch<VPLBM_F32_DEV><<<total_tiles, bx, nwarps * Pipe<VPLBM_F32_DEV>::WARP_BYTES, stream>>>(bl);
+    else if (precision == VPLBM_F16_DEV)
+        vp_mrt_step_pipe_batch<VPLBM_F16_DEV><<<total_tiles, bx, nwarps * Pipe<VPLBM_F16_DEV>::WARP_BYTES, stream>>>(bl);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step_pipe(int precision, const StepParams &p, int bx, cudaStream_t stream)

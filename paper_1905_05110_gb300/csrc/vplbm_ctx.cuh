@@ -1,0 +1,50 @@
+// The simulation context behind vplbm_ctx (internal to the library).
+#pragma once
+
+#include "vplbm_internal.cuh"
+
+using vplbm::BodyState;
+using vplbm::Control;
+using vplbm::StepParams;
+
+struct vplbm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;        // caller's stream
+    cudaStream_t capture = nullptr;       // private stream used only to capture graphs
+    int precision = 0;
+    int nx = 0, ny = 0;
+    long long ps = 0;                     // plane stride (elements)
+    size_t pop_bytes = 0;
+    StepParams base{};
+    vplbm_body_desc body_desc{};
+    bool has_body = false;
+    void *f[2] = {nullptr, nullptr};
+    BodyState *bs = nullptr;              // [2]
+    double *partials = nullptr;
+    long long max_parts = 0;
+    Control *ctrl = nullptr;
+    vplbm_record *hist = nullptr;
+    long long hist_cap = 0;
+    double *prof = nullptr;
+    void *owned = nullptr;                // single allocation when the library owns memory
+    long long nstep = 0;
+    int kernel = vplbm::KERNEL_SCALAR;           // KERNEL_SCALAR / KERNEL_PAIR / KERNEL_TMA
+    int bx = 128, by = 2;
+    cudaGraphExec_t graph = nullptr;
+    int graph_kernel = -1, graph_bx = -1, graph_by = -1;
+    long long launches = 0;
+    // TMA-staged kernel (FP32/FP16 storage): tensor maps of the two
+    // population buffers as sources, persistent grid size
+    bool tma_ok = false;
+    CUtensorMap tmap[2];
+    int tma_grid = 0;
+    int stream_grid = 0;                  // persistent grid of the streaming kernel
+};
+
+namespace vplbm {
+// Shared runtime helpers (capi.cu).
+StepParams ctx_params(const vplbm_ctx *c, long long step);        // parameters of step `step`
+cudaError_t ctx_launch(const vplbm_ctx *c, long long step, cudaStream_t stream);
+vplbm_status ctx_read_error(vplbm_ctx *c);                          // latched device errors (syncs)
+vplbm_status report_error(vplbm_status st, const char *msg);
+}  // namespace vplbm

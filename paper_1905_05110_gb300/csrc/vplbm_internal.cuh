@@ -128,13 +128,27 @@ __host__ __device__ inline void derive_pose(BodyState &s, int present, double ra
 }
 
 // Step kernels a context can launch.
-enum { KERNEL_SCALAR = 0, KERNEL_PAIR = 1, KERNEL_TMA = 2, KERNEL_ASYNC = 3, KERNEL_PIPE = 4 };
+enum { KERNEL_SCALAR = 0, KERNEL_PAIR = 1, KERNEL_TMA = 2, KERNEL_ASYNC = 3, KERNEL_PIPE = 4, KERNEL_STREAM = 5 };
+
+// Streaming paired step (step_stream.cu): persistent grid, block (bx, by)
+// walks items of 2*bx x by nodes with the next item prefetched.
+cudaError_t stream_prepare(int precision, int bx, int by, int *blocks_per_sm);
+cudaError_t launch_step_stream(int precision, const StepParams &p, int bx, int by, int grid, cudaStream_t stream);
 
 // Warp-pipelined paired step (step_pipe.cu): block (bx, 1), bx in {128, 256},
 // covers 64 x (bx / 32 * pipe_rows_per_warp()) nodes.
 int pipe_rows_per_warp();
 cudaError_t pipe_prepare(int precision, int bx);
 cudaError_t launch_step_pipe(int precision, const StepParams &p, int bx, cudaStream_t stream);
+
+// Batched launch of the warp-pipelined step over many lattices.
+struct BatchLaunch {
+    const StepParams *params;   // one per member (device), for this step's parity
+    const int *tile_start;      // n + 1 prefix sums of the members' tile counts (device)
+    int n;
+};
+cudaError_t pipe_batch_prepare(int precision, int bx);
+cudaError_t launch_step_pipe_batch(int precision, const BatchLaunch &bl, int total_tiles, int bx, cudaStream_t stream);
 
 // Software-pipelined step (step_async.cu): block (bx, by) covers
 // bx x (by * async_rows_per_thread()) nodes.

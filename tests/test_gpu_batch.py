@@ -1,0 +1,85 @@
+"""Batched sweep: members stepped in one launch per step match the same
+simulations stepped alone, and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from helpers import REC, dev_err, make_pair, moving_bodies, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library(gpu_library):
+    return gpu_library
+
+
+def _members():
+    out = []
+    for (nx, ny), motion in (((130, 66), "fixed"), ((256, 96), "imposed"), ((194, 70), "free")):
+        body = moving_bodies(nx, ny)[motion]
+        p = wl.mixed_bc_box(nx, ny, seed=nx, west="velocity", east="zerograd", south="noslip",
+                            north="noslip", tau=0.6, body=body)
+        p["bc"]["west"] = {"kind": "velocity", "u": (0.04, 0.0)}
+        p["init"] = {"rho": 1.0, "u": (0.04, 0.0)}
+        out.append(p)
+    return out
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_batch_members_match_standalone_runs(precision):
+    import paper_1905_05110_gb300 as vp
+    probs = _members()
+    batch = vp.Batch(probs, precision=precision, history_capacity=256)
+    batch.set_launch(256)
+    batch.init_from_problems()
+    batch.step(70)   # two graphs of 32 and 6 single launches
+    batch.sync()
+    for k, p in enumerate(probs):
+        alone = vp.Simulation(p, precision=precision, history_capacity=256)
+        alone.set_launch("pipe", 256, 1)   # the same tile code as the batched kernel
+        alone.init_from_problem()
+        alone.step(70)
+        m = batch.members[k]
+        assert m.nstep == 70
+        assert dev_err(m.populations(), alone.populations()) < 1e-6
+        hm, ha = m.history(), alone.history()
+        assert np.array_equal(hm[:, REC["n_solid"]], ha[:, REC["n_solid"]])
+        assert rel_err(hm[:, REC["fy"]], ha[:, REC["fy"]]) < 1e-4
+        alone.close()
+    assert batch.launch()[1] == 70
+    batch.close()
+
+
+def test_batch_member_matches_oracle():
+    import paper_1905_05110_gb300 as vp
+    probs = _members()
+    batch = vp.Batch(probs, precision="f32", history_capacity=64)
+    batch.init_from_problems()
+    batch.step(25)
+    for k, p in enumerate(probs):
+        orc = oracle.OracleSim(p, hist_cap=64)
+        shape = (p["ny"], p["nx"])
+        orc.init_equilibrium(np.ones(shape), np.full(shape, 0.04), np.zeros(shape))
+        orc.step(25)
+        assert dev_err(batch.members[k].populations(), orc.populations()) < 1e-4
+        hb, ho = batch.members[k].history(), orc.history()
+        assert np.array_equal(hb[:, REC["n_solid"]], ho[:, REC["n_solid"]])
+    batch.close()
+
+
+def test_batch_rejects_members_out_of_step_and_autotunes():
+    import paper_1905_05110_gb300 as vp
+    probs = _members()
+    batch = vp.Batch(probs, precision="f32", history_capacity=64)
+    batch.init_from_problems()
+    vp.vplbm_step(batch.members[1].ctx, 1)
+    with pytest.raises(vp.VplbmError) as ei:
+        batch.step(1)
+    assert ei.value.status == 1
+    batch.init_from_problems()
+    bx = batch.autotune(4)
+    assert bx in (128, 256)
+    batch.sync()
+    batch.close()

@@ -173,6 +173,7 @@ SCALAR_SHAPES = [(128, 2), (256, 1), (64, 4), (32, 8), (128, 1), (64, 2), (32, 4
 def vp_shapes():
     """Every kernel and block shape the runtime can launch."""
     return ([("tma", 0, 0), ("pipe", 256, 1), ("pipe", 128, 1)]
+            + [("stream", bx, by) for bx, by in SCALAR_SHAPES]
             + [("async", bx, by) for bx, by in SCALAR_SHAPES]
             + [("pair", bx, by) for bx, by in SCALAR_SHAPES]
             + [("scalar", bx, by) for bx, by in SCALAR_SHAPES])
@@ -431,3 +432,25 @@ def test_pipe_kernel_steps_from_random_state(bcs, precision, size):
             orc.step(1)
             tol = ONE_STEP_TOL[precision] * (3 if n == 2 else 1)
             assert dev_err(gpu.populations(), orc.populations()) < tol, (bx, n)
+
+
+@pytest.mark.parametrize("bcs", BC_SETS)
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+@pytest.mark.parametrize("size", [(130, 45), (66, 3), (6, 37), (262, 70)])
+def test_stream_kernel_steps_from_random_state(bcs, precision, size):
+    # the streaming paired kernel: persistent item runs crossing strips,
+    # warp-edge lanes, every boundary set, a body in the larger boxes
+    nx, ny = size
+    body = moving_bodies(nx, ny)["free"] if min(nx, ny) > 20 else None
+    p = _box(nx, ny, bcs, seed=nx * ny + 3, body=body)
+    f0 = wl.random_populations(nx, ny, seed=16, amp=0.03, u_amp=0.05)
+    g, _ = make_pair(p, precision, init=None, f0=f0)
+    f0 = g.populations()
+    for bx, by in ((64, 4), (32, 8), (128, 1)):
+        gpu, orc = make_pair(p, precision, f0=f0)
+        gpu.set_launch("stream", bx, by)
+        for n in (1, 2):
+            gpu.step(1)
+            orc.step(1)
+            tol = ONE_STEP_TOL[precision] * (3 if n == 2 else 1)
+            assert dev_err(gpu.populations(), orc.populations()) < tol, (bx, by, n)
