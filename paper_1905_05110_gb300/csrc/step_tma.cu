@@ -22,8 +22,8 @@ namespace {
 
 constexpr int TW = 128;        // chunk width = blockDim.x
 constexpr int TY = 2;          // blockDim.y
-constexpr int CR = 4;          // chunk rows (each thread: rows ty and ty + 2)
-constexpr int NSTAGE = 4;      // shared-memory ring depth
+constexpr int CR = TMA_TILE_H; // chunk rows (one node per thread)
+constexpr int NSTAGE = 3;      // shared-memory ring depth
 constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;
 
 template <int P> struct Tma {
@@ -36,8 +36,8 @@ template <int P> struct Tma {
     static constexpr unsigned TX_BYTES = NQ * CR * BOXW * ES;   // delivered per stage
     static constexpr int SMEM = NSTAGE * STAGE_BYTES + 128;      // + alignment slack
 };
-static_assert(Tma<VPLBM_F32_DEV>::PLANE_BYTES == CR * Tma<VPLBM_F32_DEV>::BOXW * 4, "dense F32 planes");
-static_assert(Tma<VPLBM_F16_DEV>::PLANE_BYTES == CR * Tma<VPLBM_F16_DEV>::BOXW * 2, "dense F16 planes");
+// each plane's box lands at a 128-byte aligned offset of the stage
+static_assert(Tma<VPLBM_F32_DEV>::PLANE_BYTES % 128 == 0 && Tma<VPLBM_F16_DEV>::PLANE_BYTES % 128 == 0, "plane alignment");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr)
 {
@@ -95,7 +95,7 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 }
 
 template <int P>
-__global__ void __launch_bounds__(256, 2) vp_mrt_step_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap)
+__global__ void __launch_bounds__(256, 4) vp_mrt_step_tma(const StepParams p, const __grid_constant__ CUtensorMap tmap)
 {
     using S = typename Prec<P>::S;
     using T = typename Prec<P>::T;

@@ -172,7 +172,7 @@ int tma_halo(int precision);
 cudaError_t tma_prepare(int precision, int *blocks_per_sm);
 cudaError_t launch_step_tma(int precision, const StepParams &p, const CUtensorMap &map, int grid,
                             cudaStream_t stream);
-constexpr int TMA_TILE_W = 128, TMA_TILE_H = 4, TMA_BOX_H = 4;
+constexpr int TMA_TILE_W = 128, TMA_TILE_H = 2, TMA_BOX_H = 2;
 
 // Largest number of blocks that can take part in the force reduction for
 // a disk of this radius under launch shape (bx, by) on an nx x ny lattice.
