@@ -71,6 +71,10 @@ class Record(C.Structure):
     _fields_ = [(n, C.c_double) for n in RECORD_FIELDS]
 
 
+class AdjointDesc(C.Structure):
+    _fields_ = [("nsteps", C.c_longlong), ("w0", C.c_longlong), ("w_cd", C.c_double), ("w_cl", C.c_double)]
+
+
 _D = C.POINTER(C.c_double)
 
 
@@ -102,6 +106,8 @@ def lib():
                                                  + [C.c_double] * 5 + [_D])
             L.orc_body_advance.argtypes = [C.POINTER(Body), C.c_longlong, C.c_double,
                                            _D, _D, _D]
+            L.orc_adjoint.restype = C.c_int
+            L.orc_adjoint.argtypes = [C.c_void_p, C.POINTER(AdjointDesc), _D, _D]
             _lib = L
     return _lib
 
@@ -241,6 +247,20 @@ class OracleSim:
         for k in range(count):
             out[k] = [getattr(buf[k], n) for n in RECORD_FIELDS]
         return out
+
+    def adjoint(self, nsteps: int, w0: int, w_cd: float = 1.0, w_cl: float = 0.0):
+        """Forward nsteps from the current state, then the discrete adjoint.
+
+        Returns (grad, (J1, J2)); grad = [dJ/du_in(j) for the west wall's u_x
+        profile (ny values)] + [dJ/deta, dJ/ds_nu, dJ/ds_e] for
+        J = w_cd * mean C_D + w_cl * RMS C_L over steps [w0, nsteps).
+        """
+        d = AdjointDesc(int(nsteps), int(w0), float(w_cd), float(w_cl))
+        grad = np.zeros(self.ny + 3)
+        js = np.zeros(2)
+        if lib().orc_adjoint(self._h, C.byref(d), _dptr(grad), _dptr(js)) != 0:
+            raise ValueError("oracle adjoint: free body or history ring too short")
+        return grad, (float(js[0]), float(js[1]))
 
     def body_state(self):
         q = np.zeros(3)

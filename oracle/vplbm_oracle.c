@@ -596,3 +596,226 @@ void orc_body_advance(const orc_body *b, long long step, double q_center,
 {
     body_advance(b, step, q_center, F, q, v);
 }
+
+/* ---- discrete adjoint of Algorithm 1 (body on a prescribed path) -------
+ *
+ * The state S_n is the post-collision population field entering step n;
+ * one step is S_{n+1} = C(Pull(S_n)) node by node, and the force of step n
+ * is F_h(n) = sum_{x in R(n)} [ sum_a c_a Pull(S_n)_a(x) - sum_a c_a S_n(a, x) ].
+ * The objective (the second half-window [w0, N) of the run) is
+ *   J = w_cd * J1 + w_cl * J2,  J1 = mean C_D(n),  J2 = sqrt(mean C_L(n)^2).
+ * The reverse sweep carries L_n = dJ/dS_n:
+ *   mu(x)  = (dC/df at f = Pull(S_n)(x))^T L_{n+1}(x) + [x in R(n)] dJ/dF_h(n) . c
+ *   L_n    = Pull^T mu - [x in R(n)] dJ/dF_h(n) . c
+ * and collects dJ/dtheta = sum_n L_{n+1}^T dC/dtheta + mu^T dPull/dtheta for
+ * theta = the west wall's u_x profile, eta, s_nu (= s_7 = s_8), s_e (= s_1).
+ * The collision is differentiated in reverse through its own steps (moments
+ * by M, equilibria, Guo forcing, penalized velocity); Pull^T is the scatter
+ * of each pulled value back onto the population it came from.  The body
+ * pose only depends on time, so chi and u_s are fixed per step.
+ */
+
+typedef struct {
+    long long nsteps;   /* N */
+    long long w0;       /* objective window [w0, N) */
+    double w_cd, w_cl;  /* weights of J1 and J2 */
+} orc_adjoint_desc;
+
+/* Source of the pull of population a into node (i, j): population b at
+ * (si, sj); *wall = side of a velocity wall whose term 6 w_a rho0 c_a.u_w
+ * is added (-1: none). */
+static void pull_source(const orc_sim *s, int a, int i, int j, int *b, int *si_out, int *sj_out, int *wall)
+{
+    const int nx = s->lat.nx, ny = s->lat.ny;
+    int si = i - C[a][0], sj = j - C[a][1];
+    *wall = -1;
+    if (sj < 0 || sj >= ny) {
+        int side = sj < 0 ? ORC_SOUTH : ORC_NORTH;
+        if (s->lat.bc_kind[side] == ORC_PERIODIC) {
+            sj = (sj + ny) % ny;
+        } else {
+            *b = OPP[a]; *si_out = i; *sj_out = j;
+            if (s->lat.bc_kind[side] == ORC_VELOCITY) *wall = side;
+            return;
+        }
+    }
+    if (si < 0 || si >= nx) {
+        int side = si < 0 ? ORC_WEST : ORC_EAST;
+        int kind = s->lat.bc_kind[side];
+        if (kind == ORC_PERIODIC) {
+            si = (si + nx) % nx;
+        } else if (kind == ORC_ZEROGRAD) {
+            *b = a; *si_out = i; *sj_out = sj;
+            return;
+        } else {
+            *b = OPP[a]; *si_out = i; *sj_out = j;
+            if (kind == ORC_VELOCITY) *wall = side;
+            return;
+        }
+    }
+    *b = a; *si_out = si; *sj_out = sj;
+}
+
+/* Reverse of the node update f -> f~ = C(f): given xi = dJ/df~, returns
+ * mu = (dC/df)^T xi, and adds xi^T dC/d(eta) to *d_eta and xi^T dC/ds_r to
+ * d_s[r]. */
+static void collide_adjoint(const double f[Q], const double s[Q], int chi, double usx, double usy, double eta,
+                            double gx, double gy, const double xi[Q], double mu[Q], double *d_eta, double d_s[Q])
+{
+    /* forward intermediates */
+    double rho = 0, jx = 0, jy = 0;
+    for (int a = 0; a < Q; ++a) { rho += f[a]; jx += C[a][0] * f[a]; jy += C[a][1] * f[a]; }
+    const double c = (double)chi;
+    const double k = 1.0 / (eta + 0.5 * c);
+    const double vx = jx / rho + 0.5 * gx, vy = jy / rho + 0.5 * gy;
+    const double ax = -c * k * (vx - usx), ay = -c * k * (vy - usy);
+    const double ux = vx + 0.5 * ax, uy = vy + 0.5 * ay;
+    const double Gx = rho * (gx + ax), Gy = rho * (gy + ay);
+    double m[Q], meq[Q], F[Q], MF[Q];
+    for (int r = 0; r < Q; ++r) { m[r] = 0; for (int a = 0; a < Q; ++a) m[r] += M[r][a] * f[a]; }
+    moment_equilibrium(rho, ux, uy, meq);
+    guo_forcing(ux, uy, Gx, Gy, F);
+    for (int r = 0; r < Q; ++r) { MF[r] = 0; for (int a = 0; a < Q; ++a) MF[r] += M[r][a] * F[a]; }
+
+    /* f~ = M^-1 m*  ->  lam_ms = M^-T xi */
+    double lam_ms[Q], lam_m[Q], lam_meq[Q], lam_MF[Q], lam_F[Q];
+    for (int r = 0; r < Q; ++r) { lam_ms[r] = 0; for (int a = 0; a < Q; ++a) lam_ms[r] += MINV[a][r] * xi[a]; }
+    /* m*_r = m_r - s_r (m_r - meq_r) + (1 - s_r/2) MF_r */
+    for (int r = 0; r < Q; ++r) {
+        lam_m[r] = (1.0 - s[r]) * lam_ms[r];
+        lam_meq[r] = s[r] * lam_ms[r];
+        lam_MF[r] = (1.0 - 0.5 * s[r]) * lam_ms[r];
+        d_s[r] += lam_ms[r] * (-(m[r] - meq[r]) - 0.5 * MF[r]);
+    }
+    for (int a = 0; a < Q; ++a) { lam_F[a] = 0; for (int r = 0; r < Q; ++r) lam_F[a] += M[r][a] * lam_MF[r]; }
+    double lam_rho = 0, lam_ux = 0, lam_uy = 0, lam_Gx = 0, lam_Gy = 0;
+    /* meq(rho, u), Eq. (14) */
+    {
+        const double u2 = ux * ux + uy * uy;
+        const double br[Q] = {1.0, -2.0 + 3.0 * u2, 1.0 - 3.0 * u2, ux, -ux, uy, -uy, ux * ux - uy * uy, ux * uy};
+        const double dux[Q] = {0, 6 * ux, -6 * ux, 1, -1, 0, 0, 2 * ux, uy};
+        const double duy[Q] = {0, 6 * uy, -6 * uy, 0, 0, 1, -1, -2 * uy, ux};
+        for (int r = 0; r < Q; ++r) {
+            lam_rho += lam_meq[r] * br[r];
+            lam_ux += lam_meq[r] * rho * dux[r];
+            lam_uy += lam_meq[r] * rho * duy[r];
+        }
+    }
+    /* F(u, G), Eq. (12) without the prefactor: F_a = W_a [3 (c - u) + 9 (c.u) c] . G */
+    for (int a = 0; a < Q; ++a) {
+        const double cx = C[a][0], cy = C[a][1];
+        const double cu = cx * ux + cy * uy;
+        lam_Gx += lam_F[a] * W[a] * (3.0 * (cx - ux) + 9.0 * cu * cx);
+        lam_Gy += lam_F[a] * W[a] * (3.0 * (cy - uy) + 9.0 * cu * cy);
+        lam_ux += lam_F[a] * W[a] * ((-3.0 + 9.0 * cx * cx) * Gx + 9.0 * cx * cy * Gy);
+        lam_uy += lam_F[a] * W[a] * (9.0 * cy * cx * Gx + (-3.0 + 9.0 * cy * cy) * Gy);
+    }
+    /* G = rho (g + a) */
+    lam_rho += lam_Gx * (gx + ax) + lam_Gy * (gy + ay);
+    double lam_ax = rho * lam_Gx, lam_ay = rho * lam_Gy;
+    /* u = v + a/2 */
+    double lam_vx = lam_ux, lam_vy = lam_uy;
+    lam_ax += 0.5 * lam_ux;
+    lam_ay += 0.5 * lam_uy;
+    /* a = -chi k (v - u_s), k = 1/(eta + chi/2) */
+    lam_vx += -c * k * lam_ax;
+    lam_vy += -c * k * lam_ay;
+    *d_eta += (lam_ax * (c * k * k * (vx - usx)) + lam_ay * (c * k * k * (vy - usy)));
+    /* v = j / rho + g/2 */
+    const double lam_jx = lam_vx / rho, lam_jy = lam_vy / rho;
+    lam_rho += -(lam_vx * jx + lam_vy * jy) / (rho * rho);
+    /* m = M f (direct path), rho = sum f, j = sum c f */
+    for (int a = 0; a < Q; ++a) {
+        double acc = 0;
+        for (int r = 0; r < Q; ++r) acc += M[r][a] * lam_m[r];
+        mu[a] = acc + lam_rho + C[a][0] * lam_jx + C[a][1] * lam_jy;
+    }
+}
+
+/* Runs the forward from the current state for d->nsteps steps (the state
+ * advances), then the reverse sweep.  grad (ny + 3 entries): dJ/du_in(j)
+ * for the west wall's u_x profile, dJ/deta, dJ/ds_nu, dJ/ds_e.  out_j: J1,
+ * J2.  Returns 0, or -1 if the body is free or the history ring is short. */
+int orc_adjoint(orc_sim *s, const orc_adjoint_desc *d, double *grad, double out_j[2])
+{
+    const int nx = s->lat.nx, ny = s->lat.ny;
+    const long long N = d->nsteps;
+    if (s->body.present && s->body.motion == ORC_FREE) return -1;
+    if (N < 1 || d->w0 < 0 || d->w0 >= N || s->hist_cap < s->step + N) return -1;
+    const size_t nf = (size_t)Q * nx * ny;
+    const long long step0 = s->step;
+    double *states = (double *)malloc(sizeof(double) * nf * (size_t)N);
+    double *lam = (double *)calloc(nf, sizeof(double));
+    double *nlam = (double *)calloc(nf, sizeof(double));
+    double *mu = (double *)calloc(nf, sizeof(double));
+    if (!states || !lam || !nlam || !mu) { free(states); free(lam); free(nlam); free(mu); return -1; }
+    for (long long n = 0; n < N; ++n) {
+        memcpy(states + nf * (size_t)n, s->ft, sizeof(double) * nf);
+        one_step(s);
+    }
+    /* objectives from the recorded forces */
+    const double qref = 0.5 * s->lat.rho0 * s->body.d_ref * s->body.u_ref * s->body.u_ref;
+    const double nh = (double)(N - d->w0);
+    double sum_cd = 0, sum_cl2 = 0;
+    for (long long n = d->w0; n < N; ++n) {
+        const orc_record *r = &s->hist[(step0 + n) % s->hist_cap];
+        sum_cd += r->fx / qref;
+        sum_cl2 += (r->fy / qref) * (r->fy / qref);
+    }
+    const double J1 = sum_cd / nh, J2 = sqrt(sum_cl2 / nh);
+    out_j[0] = J1; out_j[1] = J2;
+
+    for (int k = 0; k < ny + 3; ++k) grad[k] = 0.0;
+    double d_eta = 0, d_s[Q] = {0};
+    double *saved_ft = s->ft;
+    double saved_q[3], saved_v[3];
+    for (int dd = 0; dd < 3; ++dd) { saved_q[dd] = s->q[dd]; saved_v[dd] = s->v[dd]; }
+    node_state ns;
+    for (long long n = N - 1; n >= 0; --n) {
+        const orc_record *r = &s->hist[(step0 + n) % s->hist_cap];
+        s->ft = states + nf * (size_t)n;
+        s->q[0] = r->x; s->q[1] = r->y; s->q[2] = r->theta;
+        s->v[0] = r->vx; s->v[1] = r->vy; s->v[2] = r->omega;
+        double wx = 0, wy = 0;   /* dJ/dF_h(n) */
+        if (n >= d->w0) {
+            wx = d->w_cd / (qref * nh);
+            wy = (J2 > 0) ? d->w_cl * (r->fy / qref) / (J2 * qref * nh) : 0.0;
+        }
+        /* mu at every node */
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                node_macro(s, i, j, &ns);
+                double xi[Q], m_loc[Q];
+                for (int a = 0; a < Q; ++a) xi[a] = lam[((size_t)a * ny + j) * nx + i];
+                collide_adjoint(ns.f, s->lat.s, ns.chi, ns.usx, ns.usy, s->lat.eta, s->lat.gx, s->lat.gy, xi, m_loc,
+                                &d_eta, d_s);
+                if (ns.chi)
+                    for (int a = 0; a < Q; ++a) m_loc[a] += wx * C[a][0] + wy * C[a][1];
+                for (int a = 0; a < Q; ++a) mu[((size_t)a * ny + j) * nx + i] = m_loc[a];
+            }
+        /* L_n = Pull^T mu - own term */
+        memset(nlam, 0, sizeof(double) * nf);
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                for (int a = 0; a < Q; ++a) {
+                    int b, si, sj, wall;
+                    pull_source(s, a, i, j, &b, &si, &sj, &wall);
+                    const double g = mu[((size_t)a * ny + j) * nx + i];
+                    nlam[((size_t)b * ny + sj) * nx + si] += g;
+                    if (wall == ORC_WEST && s->prof_ux[ORC_WEST])
+                        grad[j] += g * 6.0 * W[a] * s->lat.rho0 * C[a][0];
+                }
+                if (chi_at(s, i, j))
+                    for (int a = 0; a < Q; ++a) nlam[((size_t)a * ny + j) * nx + i] -= wx * C[a][0] + wy * C[a][1];
+            }
+        double *t = lam; lam = nlam; nlam = t;
+    }
+    grad[ny] = d_eta;
+    grad[ny + 1] = d_s[7] + d_s[8];
+    grad[ny + 2] = d_s[1];
+    /* leave the simulation after its forward run */
+    s->ft = saved_ft;
+    for (int dd = 0; dd < 3; ++dd) { s->q[dd] = saved_q[dd]; s->v[dd] = saved_v[dd]; }
+    free(states); free(lam); free(nlam); free(mu);
+    return 0;
+}

@@ -258,3 +258,37 @@ def scaled(problem: dict, **changes) -> dict:
     p = dict(problem)
     p.update(changes)
     return p
+
+
+def adjoint_channel(nx=24, ny=14, u_in=0.03, tau=0.6, eta=0.05, s_e=1.1, radius=3.0, steps=30) -> dict:
+    """Small channel with a parabolic inlet profile and an oscillating disk,
+    for gradient checks (the parameters are the inlet profile, eta, s_nu and
+    s_e)."""
+    rates = paper_rates(tau)
+    rates[1] = s_e
+    return {
+        "name": f"adjoint_channel_{nx}x{ny}", "nx": nx, "ny": ny, "s": rates, "eta": eta, "rho0": RHO0,
+        "g_fluid": (0.0, 0.0),
+        "bc": {"west": _bc("velocity", ux_profile=parabolic_profile(ny, u_in)), "east": _bc("zerograd"),
+               "south": _bc("noslip"), "north": _bc("noslip")},
+        "body": {"radius": radius, "x": nx / 3.0, "y": ny / 2.0 + 0.3, "motion": "imposed", "axis": 1,
+                 "amp": 1.0, "freq": 0.02, "phase": 0.0, "u_ref": u_in, "d_ref": 2 * radius},
+        "init": {"rho": RHO0, "u": (u_in, 0.0)},
+        "steps": steps,
+    }
+
+
+def with_params(problem: dict, u_in_profile=None, eta=None, s_nu=None, s_e=None) -> dict:
+    """Copy of a problem with the adjoint's parameters replaced."""
+    p = dict(problem)
+    p["s"] = list(problem["s"])
+    p["bc"] = {k: dict(v) for k, v in problem["bc"].items()}
+    if u_in_profile is not None:
+        p["bc"]["west"]["ux_profile"] = np.asarray(u_in_profile, dtype=np.float64)
+    if eta is not None:
+        p["eta"] = float(eta)
+    if s_nu is not None:
+        p["s"][7] = p["s"][8] = float(s_nu)
+    if s_e is not None:
+        p["s"][1] = float(s_e)
+    return p
