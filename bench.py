@@ -45,7 +45,7 @@ CSRC = os.path.join(ROOT, "paper_1905_05110_gb300", "csrc")
 def kernel_name(prec: str, launch) -> str:
     base = {"tma": "vp_mrt_step_tma", "pair": "vp_mrt_step_pair", "scalar": "vp_mrt_step",
             "async": "vp_mrt_step_async", "pipe": "vp_mrt_step_pipe",
-            "stream": "vp_mrt_step_stream"}[launch[0]]
+            "stream": "vp_mrt_step_stream", "scalar48": "vp_mrt_step", "scalar40": "vp_mrt_step"}[launch[0]]
     return f"{base}<{PREC_ID[prec]}>"
 
 

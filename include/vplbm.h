@@ -203,8 +203,10 @@ vplbm_status vplbm_get_history(vplbm_ctx *ctx, long long first, long long count,
 vplbm_status vplbm_get_body(vplbm_ctx *ctx, double q[3], double v[3], long long *step);
 
 /* Step kernels.  All compute the same method; they differ in data movement:
- *  VPLBM_KERNEL_SCALAR  one node per thread (every precision; the default
- *                       for FP64 storage);
+ *  VPLBM_KERNEL_SCALAR  one node per thread (every precision), register
+ *                       budget for 4 blocks of 256 threads per SM;
+ *  VPLBM_KERNEL_SCALAR_48 / _40  the same with the budget of 5 / 6 blocks
+ *                       (48 / 40 registers); _48 is the default;
  *  VPLBM_KERNEL_PAIR    two x-adjacent nodes per thread with packed FP32x2
  *                       arithmetic (FP32/FP16 storage, even nx);
  *  VPLBM_KERNEL_TMA     persistent blocks fed by tensor-memory-accelerator
@@ -223,14 +225,13 @@ vplbm_status vplbm_get_body(vplbm_ctx *ctx, double q[3], double v[3], long long 
  *                       tiles, two nodes per thread, the next tile's
  *                       populations prefetched into registers while the
  *                       current one collides on the packed FP32x2 pipe
- *                       (FP32/FP16 storage, even nx); the default where the
- *                       lattice allows it.
+ *                       (FP32/FP16 storage, even nx).
  * Nodes on the lattice edges and near the body always take the scalar
  * arithmetic.  The results of different kernels agree to the rounding of
  * the storage precision. */
 typedef enum {
     VPLBM_KERNEL_SCALAR = 0, VPLBM_KERNEL_PAIR = 1, VPLBM_KERNEL_TMA = 2, VPLBM_KERNEL_ASYNC = 3,
-    VPLBM_KERNEL_PIPE = 4, VPLBM_KERNEL_STREAM = 5
+    VPLBM_KERNEL_PIPE = 4, VPLBM_KERNEL_STREAM = 5, VPLBM_KERNEL_SCALAR_48 = 6, VPLBM_KERNEL_SCALAR_40 = 7
 } vplbm_kernel;
 
 /* Kernel and block shape: block_x * block_y threads, block_x a multiple of

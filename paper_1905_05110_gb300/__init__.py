@@ -318,7 +318,7 @@ def vplbm_get_body(ctx):
     return q, v, int(step.value)
 
 
-KERNELS = {"scalar": 0, "pair": 1, "tma": 2, "async": 3, "pipe": 4, "stream": 5}
+KERNELS = {"scalar": 0, "pair": 1, "tma": 2, "async": 3, "pipe": 4, "stream": 5, "scalar48": 6, "scalar40": 7}
 KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
 
 

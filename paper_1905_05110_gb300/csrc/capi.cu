@@ -100,7 +100,7 @@ vplbm_status check_lattice(const vplbm_lattice_desc *lat)
 {
     if (!lat) return fail(VPLBM_EINVAL, "lattice descriptor is NULL");
     if (lat->nx < 3 || lat->ny < 3) return fail(VPLBM_EINVAL, "nx and ny must be >= 3 (got %d x %d)", lat->nx, lat->ny);
-    if ((long long)lat->nx * lat->ny > (1LL << 31)) return fail(VPLBM_EINVAL, "lattice too large");
+    if ((long long)lat->nx * lat->ny >= (1LL << 31)) return fail(VPLBM_EINVAL, "lattice too large");
     if (lat->nx > (1 << 22) || lat->ny > 65535) return fail(VPLBM_EINVAL, "nx must be <= 2^22 and ny <= 65535");
     for (int k = 0; k < 9; ++k)
         if (!(lat->s[k] > 0.0 && lat->s[k] < 2.0)) return fail(VPLBM_EINVAL, "relaxation rate s[%d]=%g outside (0,2)", k, lat->s[k]);
@@ -146,7 +146,7 @@ void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long 
     long long parts = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr,
                                            TMA_TILE_W, TMA_TILE_H);
     for (int k = 0; k < N_SHAPES; ++k)
-        for (int kern = KERNEL_SCALAR; kern <= KERNEL_STREAM; ++kern) {   // every kernel's tiling
+        for (int kern = KERNEL_SCALAR; kern <= KERNEL_SCALAR_40; ++kern) {   // every kernel's tiling
             int w, h;
             tile_of(kern, SHAPES[k][0], SHAPES[k][1], &w, &h);
             const long long m = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr, w, h);
@@ -183,6 +183,7 @@ StepParams params_for(const vplbm_ctx *c, long long step)
     p.fout = c->f[par ^ 1];
     p.bs_in = c->bs + par;
     p.bs_out = c->bs + (par ^ 1);
+    set_planes(p, (int)elem_size(c->precision));
     return p;
 }
 
@@ -195,7 +196,8 @@ cudaError_t launch_one(const vplbm_ctx *c, long long step, cudaStream_t stream)
     if (c->kernel == KERNEL_ASYNC) return launch_step_async(c->precision, p, c->bx, c->by, stream);
     if (c->kernel == KERNEL_PIPE) return launch_step_pipe(c->precision, p, c->bx, stream);
     if (c->kernel == KERNEL_STREAM) return launch_step_stream(c->precision, p, c->bx, c->by, c->stream_grid, stream);
-    return launch_step(c->precision, p, c->bx, c->by, stream);
+    const int minb = c->kernel == KERNEL_SCALAR_40 ? 6 : c->kernel == KERNEL_SCALAR_48 ? 5 : 4;
+    return launch_step(c->precision, p, c->bx, c->by, stream, minb);
 }
 
 bool pair_ok(const vplbm_ctx *c)
@@ -211,7 +213,7 @@ void tile_of(int kernel, int bx, int by, int *w, int *h)
     else if (kernel == KERNEL_ASYNC) { *w = bx; *h = by * async_rows_per_thread(); }
     else if (kernel == KERNEL_PIPE) { *w = 64; *h = (bx / 32) * pipe_rows_per_warp(); }
     else if (kernel == KERNEL_STREAM) { *w = 2 * bx; *h = by; }
-    else { *w = bx; *h = by; }
+    else { *w = bx; *h = by; }   // the scalar kernels
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -366,13 +368,10 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     p.hist_cap = cap;
 
     setup_tma(c);
-    if (pair_ok(c) && vplbm_set_launch(c, KERNEL_STREAM, 64, 4) == VPLBM_OK) {
-        // default: the streaming paired kernel
-    } else if (c->precision != VPLBM_F64) {
-        c->kernel = KERNEL_ASYNC;
-        c->bx = 128;
-        c->by = 2;
-    }
+    // default: the scalar kernel sized for 5 blocks of 256 threads per SM
+    c->kernel = KERNEL_SCALAR_48;
+    c->bx = 256;
+    c->by = 1;
     // populations at rest
     StepParams q = params_for(c, 0);
     q.fout = c->f[0];
@@ -748,7 +747,7 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
         c->by = 1;
         return VPLBM_OK;
     }
-    if (kernel != KERNEL_SCALAR && kernel != KERNEL_PAIR && kernel != KERNEL_ASYNC && kernel != KERNEL_STREAM)
+    if (kernel < KERNEL_SCALAR || kernel > KERNEL_SCALAR_40 || kernel == KERNEL_TMA || kernel == KERNEL_PIPE)
         return fail(VPLBM_EINVAL, "unknown kernel %d", kernel);
     if (kernel == KERNEL_STREAM && !pair_ok(c))
         return fail(VPLBM_EUNSUPPORTED, "the streaming kernel needs FP32/FP16 storage and an even nx");
@@ -840,10 +839,10 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
         }
         // candidates: the TMA-staged kernel, then every shape of the paired
         // and of the scalar kernel
-        for (int cand = -3; cand < 4 * N_SHAPES; ++cand) {
-            const int ck = cand == -3 ? KERNEL_TMA : cand < 0 ? KERNEL_PIPE
-                         : cand < N_SHAPES ? KERNEL_STREAM
-                         : (cand < 2 * N_SHAPES ? KERNEL_ASYNC : (cand < 3 * N_SHAPES ? KERNEL_PAIR : KERNEL_SCALAR));
+        static const int kinds[6] = {KERNEL_SCALAR_48, KERNEL_SCALAR_40, KERNEL_SCALAR, KERNEL_PAIR, KERNEL_ASYNC,
+                                     KERNEL_STREAM};
+        for (int cand = -3; cand < 6 * N_SHAPES; ++cand) {
+            const int ck = cand == -3 ? KERNEL_TMA : cand < 0 ? KERNEL_PIPE : kinds[cand / N_SHAPES];
             const int cbx = cand == -3 ? 0 : cand == -2 ? 256 : cand == -1 ? 128 : SHAPES[cand % N_SHAPES][0];
             const int cby = cand < 0 ? 1 : SHAPES[cand % N_SHAPES][1];
             if (vplbm_set_launch(c, ck, cbx, cby) != VPLBM_OK) continue;

@@ -205,6 +205,7 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const 
         p.fout = populations_dev[par ^ 1];
         p.bs_in = &scratch->bs[par];
         p.bs_out = &scratch->bs[par ^ 1];
+        set_planes(p, lat->precision == VPLBM_F64 ? 8 : (lat->precision == VPLBM_F32_DEV ? 4 : 2));
         e = launch_step(lat->precision, p, NOALLOC_BX, NOALLOC_BY, stream);
     }
     if (e == cudaSuccess) {

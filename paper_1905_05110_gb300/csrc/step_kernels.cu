@@ -33,8 +33,10 @@ namespace {
 
 // ---- the fused step ----------------------------------------------------
 
-template <int P>
-__global__ void __launch_bounds__(256, 4) vp_mrt_step(const StepParams p)
+// MINB: blocks of 256 threads per SM the register budget is sized for
+// (4: 64 registers, 5: 48, 6: 40).
+template <int P, int MINB>
+__global__ void __launch_bounds__(256, MINB) vp_mrt_step(const StepParams p)
 {
     using S = typename Prec<P>::S;
     using T = typename Prec<P>::T;
@@ -42,20 +44,23 @@ __global__ void __launch_bounds__(256, 4) vp_mrt_step(const StepParams p)
     __shared__ double red[8][NPART];
     __shared__ int s_last;
 
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const bool inside = i < p.nx && j < p.ny;
+    const int bi0 = blockIdx.x * blockDim.x, bj0 = blockIdx.y * blockDim.y;
+    const int i = bi0 + threadIdx.x;
+    const int j = bj0 + threadIdx.y;
     const S *__restrict__ fin = static_cast<const S *>(p.fin);
     S *__restrict__ fout = static_cast<S *>(p.fout);
     const BodyState *__restrict__ bs = p.bs_in;
+    // no node of the block on a lattice edge (uniform over the block)
+    const bool block_interior = bi0 > 0 && bj0 > 0 && bi0 + (int)blockDim.x < p.nx && bj0 + (int)blockDim.y < p.ny;
+    const bool inside = block_interior || (i < p.nx && j < p.ny);
 
     // streaming loads first: nothing below them waits on the pose
     T f[NQ];
-    if (inside) pull_all<P>(p, fin, i, j, f);
+    if (block_interior) pull_all<P, true>(p, fin, i, j, f);
+    else if (inside) pull_all<P>(p, fin, i, j, f);
 
     const int4 range = __ldg(reinterpret_cast<const int4 *>(&bs->ilo));   // ilo, ihi, jlo, jhi
-    const bool part_block = tile_near_body(range, blockIdx.x * blockDim.x, blockIdx.y * blockDim.y, blockDim.x,
-                                           blockDim.y, blockIdx.x == 0 && blockIdx.y == 0);
+    const bool part_block = tile_near_body(range, bi0, bj0, blockDim.x, blockDim.y, blockIdx.x == 0 && blockIdx.y == 0);
     bool chi = false;
     T cr = 0, cax = 0, cay = 0;   // kept for the solid-node sums (converted there)
     if (inside)
@@ -133,11 +138,13 @@ __global__ void fields_kernel(const StepParams p, double *rho_o, double *ux_o, d
 }
 
 template <int P>
-cudaError_t launch_step_t(const StepParams &p, int bx, int by, cudaStream_t stream)
+cudaError_t launch_step_t(const StepParams &p, int bx, int by, int minb, cudaStream_t stream)
 {
     dim3 block(bx, by);
     dim3 grid((p.nx + bx - 1) / bx, (p.ny + by - 1) / by);
-    vp_mrt_step<P><<<grid, block, 0, stream>>>(p);
+    if (minb == 6) vp_mrt_step<P, 6><<<grid, block, 0, stream>>>(p);
+    else if (minb == 5) vp_mrt_step<P, 5><<<grid, block, 0, stream>>>(p);
+    else vp_mrt_step<P, 4><<<grid, block, 0, stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -154,12 +161,12 @@ long long max_reduction_blocks(int nx, int ny, double radius, int present, int b
     return tx * ty;
 }
 
-cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream)
+cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb)
 {
     switch (precision) {
-    case VPLBM_F64: return launch_step_t<VPLBM_F64>(p, bx, by, stream);
-    case VPLBM_F32_DEV: return launch_step_t<VPLBM_F32_DEV>(p, bx, by, stream);
-    case VPLBM_F16_DEV: return launch_step_t<VPLBM_F16_DEV>(p, bx, by, stream);
+    case VPLBM_F64: return launch_step_t<VPLBM_F64>(p, bx, by, minb, stream);
+    case VPLBM_F32_DEV: return launch_step_t<VPLBM_F32_DEV>(p, bx, by, minb, stream);
+    case VPLBM_F16_DEV: return launch_step_t<VPLBM_F16_DEV>(p, bx, by, minb, stream);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -81,6 +81,11 @@ struct StepParams {
     DevBody body;
     const void *fin;
     void *fout;
+    // per-plane pointers (set_planes): src_plane[a] = &fin[a][-c_ay][-c_ax],
+    // so the pull of an interior node b = j*nx + i reads src_plane[a][b];
+    // dst_plane[a] = &fout[a][0][0]
+    const void *src_plane[NQ];
+    void *dst_plane[NQ];
     const BodyState *bs_in;
     BodyState *bs_out;
     double *partials;
@@ -105,6 +110,19 @@ struct Control {
 };
 static_assert(sizeof(Control) == 256, "Control layout");
 
+// Per-plane pointers of the step's source and destination buffers; call
+// whenever fin / fout change.  es: bytes per stored population.
+inline void set_planes(StepParams &p, int es)
+{
+    static const int cx[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    static const int cy[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    for (int a = 0; a < NQ; ++a) {
+        const long long off = (long long)a * p.ps - cx[a] - (long long)cy[a] * p.nx;
+        p.src_plane[a] = static_cast<const char *>(p.fin) + off * es;
+        p.dst_plane[a] = static_cast<char *>(p.fout) + (long long)a * p.ps * es;
+    }
+}
+
 // Fill the derived fields of s from its pose (host and device, same IEEE
 // operations on both).
 __host__ __device__ inline void derive_pose(BodyState &s, int present, double radius, int nx, int ny)
@@ -128,7 +146,8 @@ __host__ __device__ inline void derive_pose(BodyState &s, int present, double ra
 }
 
 // Step kernels a context can launch.
-enum { KERNEL_SCALAR = 0, KERNEL_PAIR = 1, KERNEL_TMA = 2, KERNEL_ASYNC = 3, KERNEL_PIPE = 4, KERNEL_STREAM = 5 };
+enum { KERNEL_SCALAR = 0, KERNEL_PAIR = 1, KERNEL_TMA = 2, KERNEL_ASYNC = 3, KERNEL_PIPE = 4, KERNEL_STREAM = 5,
+       KERNEL_SCALAR_48 = 6, KERNEL_SCALAR_40 = 7 };
 
 // Streaming paired step (step_stream.cu): persistent grid, block (bx, by)
 // walks items of 2*bx x by nodes with the next item prefetched.
@@ -159,7 +178,7 @@ cudaError_t launch_step_async(int precision, const StepParams &p, int bx, int by
 cudaError_t launch_step_pair(int precision, const StepParams &p, int bx, int by, cudaStream_t stream);
 
 // Launchers (step_kernels.cu).  All are asynchronous on `stream`.
-cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream);
+cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb = 4);
 cudaError_t launch_init_equilibrium(int precision, const StepParams &p, const double *rho_dev,
                                     const double *ux_dev, const double *uy_dev, cudaStream_t stream);
 cudaError_t launch_fields(int precision, const StepParams &p, double *rho_dev, double *ux_dev,

@@ -88,17 +88,17 @@ __device__ typename Prec<P>::T pull_edge(const StepParams &p, const typename Pre
     return ldv(fin + a * ps + (long long)sj * nx + si);
 }
 
-// Pull-stream all 9 populations of node (i, j).
-template <int P>
+// Pull-stream all 9 populations of node (i, j); INTERIOR: the caller knows
+// the node is not on a lattice edge.
+template <int P, bool INTERIOR = false>
 __device__ __forceinline__ void pull_all(const StepParams &p, const typename Prec<P>::S *__restrict__ fin,
                                          int i, int j, typename Prec<P>::T f[NQ])
 {
-    const int nx = p.nx;
-    const long long ps = p.ps;
-    if (i > 0 && i < nx - 1 && j > 0 && j < p.ny - 1) {
-        const long long b = (long long)j * nx + i;
+    using S = typename Prec<P>::S;
+    if (INTERIOR || (i > 0 && i < p.nx - 1 && j > 0 && j < p.ny - 1)) {
+        const int b = j * p.nx + i;
 #pragma unroll
-        for (int a = 0; a < NQ; ++a) f[a] = ldv(fin + a * ps + b - cx_of(a) - (long long)cy_of(a) * nx);
+        for (int a = 0; a < NQ; ++a) f[a] = ldv(static_cast<const S *>(p.src_plane[a]) + b);
     } else {
 #pragma unroll
         for (int a = 0; a < NQ; ++a) f[a] = pull_edge<P>(p, fin, a, i, j);
@@ -332,17 +332,19 @@ __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState
     const T Pq = pxx_s * (T)0.25;
     const T Rq = pxy_s * (T)0.25;
 
-    const long long b = (long long)j * p.nx + i;
-    const long long ps = p.ps;
-    stv(fout + b, r9 - e_s * (T)(1.0 / 9.0) + ep_s * (T)(1.0 / 9.0));
-    stv(fout + ps + b, A + X1 + Pq);
-    stv(fout + 2 * ps + b, A + Y1 - Pq);
-    stv(fout + 3 * ps + b, A - X1 + Pq);
-    stv(fout + 4 * ps + b, A - Y1 - Pq);
-    stv(fout + 5 * ps + b, B + X2 + Y2 + Rq);
-    stv(fout + 6 * ps + b, B - X2 + Y2 - Rq);
-    stv(fout + 7 * ps + b, B - X2 - Y2 + Rq);
-    stv(fout + 8 * ps + b, B + X2 - Y2 - Rq);
+    using S = typename Prec<P>::S;
+    const int b = j * p.nx + i;
+    S *const *dp = reinterpret_cast<S *const *>(p.dst_plane);
+    stv(dp[0] + b, r9 - e_s * (T)(1.0 / 9.0) + ep_s * (T)(1.0 / 9.0));
+    stv(dp[1] + b, A + X1 + Pq);
+    stv(dp[2] + b, A + Y1 - Pq);
+    stv(dp[3] + b, A - X1 + Pq);
+    stv(dp[4] + b, A - Y1 - Pq);
+    stv(dp[5] + b, B + X2 + Y2 + Rq);
+    stv(dp[6] + b, B - X2 + Y2 - Rq);
+    stv(dp[7] + b, B - X2 - Y2 + Rq);
+    stv(dp[8] + b, B + X2 - Y2 - Rq);
+    (void)fout;
 
     if (!(rho > (T)0) || !(rho < (T)1e30)) *p.err = ERR_NONFINITE;
     cr = rho; cax = ax; cay = ay;

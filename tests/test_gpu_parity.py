@@ -176,7 +176,9 @@ def vp_shapes():
             + [("stream", bx, by) for bx, by in SCALAR_SHAPES]
             + [("async", bx, by) for bx, by in SCALAR_SHAPES]
             + [("pair", bx, by) for bx, by in SCALAR_SHAPES]
-            + [("scalar", bx, by) for bx, by in SCALAR_SHAPES])
+            + [("scalar", bx, by) for bx, by in SCALAR_SHAPES]
+            + [("scalar48", bx, by) for bx, by in SCALAR_SHAPES]
+            + [("scalar40", bx, by) for bx, by in SCALAR_SHAPES])
 
 
 def test_fp64_full_size_two_steps():
