@@ -261,6 +261,31 @@ vplbm_status vplbm_get_launch_count(vplbm_ctx *ctx, long long *launches);
 vplbm_status vplbm_save(vplbm_ctx *ctx, const char *path);
 vplbm_status vplbm_load(vplbm_ctx *ctx, const char *path);
 
+/* ---- discrete adjoint --------------------------------------------------------
+ * Gradients of J = w_cd * mean C_D + w_cl * RMS C_L, both over the steps
+ * [window_start, nsteps) of a run of nsteps steps from the current state,
+ * with respect to the inlet u_x profile of the west wall (a VELOCITY wall
+ * with a ux_profile), eta (Eq. 2), s_nu (= s_7 = s_8, Eq. 16) and s_e (= s_1).
+ * C_D, C_L use the momentum-exchange force of each step (Eqs. 25-27).  The
+ * body must move on a prescribed path (fixed or imposed; chi is the binary
+ * mask of each step).  The run is the exact discrete reverse of the
+ * forward steps: forward with a checkpoint every checkpoint_interval steps
+ * (0: ceil(sqrt(nsteps))), then, segment by segment from the end, the
+ * segment's states are recomputed and the adjoint stepped back through it.
+ * The context ends at the state after the forward run (advanced by nsteps).
+ * FP64 storage: FP64 adjoint; FP32 deviation storage: FP32 adjoint with
+ * FP64 parameter sums.  history_capacity must be >= nsteps.
+ * grad (host, ny + 3 values): dJ/du_in(j) for j < ny, then dJ/deta,
+ * dJ/ds_nu, dJ/ds_e.  j_out (host, 2 values, may be NULL): J1, J2. */
+typedef struct {
+    long long nsteps;
+    long long window_start;
+    double w_cd, w_cl;
+    long long checkpoint_interval;
+} vplbm_adjoint_desc;
+
+vplbm_status vplbm_adjoint(vplbm_ctx *ctx, const vplbm_adjoint_desc *desc, double *grad, double *j_out);
+
 /* ---- batched sweep ---------------------------------------------------------
  * Many independent simulations of uneven lattice sizes (a parameter sweep:
  * stiffness, reduced velocity, ... as in the vortex-induced-vibration study

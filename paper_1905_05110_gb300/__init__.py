@@ -89,6 +89,11 @@ class Buffers(C.Structure):
                 ("profiles_dev", C.c_void_p), ("control_dev", C.c_void_p)]
 
 
+class AdjointDesc(C.Structure):
+    _fields_ = [("nsteps", C.c_longlong), ("window_start", C.c_longlong), ("w_cd", C.c_double),
+                ("w_cl", C.c_double), ("checkpoint_interval", C.c_longlong)]
+
+
 class BodyState(C.Structure):
     _fields_ = [("q", C.c_double * 3), ("v", C.c_double * 3), ("step", C.c_longlong),
                 ("error", C.c_int), ("pad", C.c_int)]
@@ -133,6 +138,7 @@ _SIGS = {
     "vplbm_batch_set_launch": (C.c_int, [C.c_void_p, C.c_int]),
     "vplbm_batch_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     "vplbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int]),
+    "vplbm_adjoint": (C.c_int, [_CTX, C.c_void_p, _D, _D]),
     "vplbm_last_error": (C.c_char_p, []),
     "vplbm_version": (C.c_char_p, []),
 }
@@ -399,6 +405,16 @@ def vplbm_batch_autotune(batch, steps_per_trial: int = 8):
     _check(load_library().vplbm_batch_autotune(batch, int(steps_per_trial)))
 
 
+def vplbm_adjoint(ctx, ny: int, nsteps: int, window_start: int, w_cd: float = 1.0, w_cl: float = 0.0,
+                  checkpoint_interval: int = 0):
+    """Discrete-adjoint gradient; returns (grad[ny + 3], (J1, J2))."""
+    d = AdjointDesc(int(nsteps), int(window_start), float(w_cd), float(w_cl), int(checkpoint_interval))
+    grad = np.zeros(int(ny) + 3)
+    js = np.zeros(2)
+    _check(load_library().vplbm_adjoint(ctx, C.cast(C.pointer(d), C.c_void_p), _dptr(grad), _dptr(js)))
+    return grad, (float(js[0]), float(js[1]))
+
+
 def vplbm_save(ctx, path: str):
     _check(load_library().vplbm_save(ctx, os.fsencode(path)))
 
@@ -528,6 +544,11 @@ class Simulation:
     @property
     def launches(self) -> int:
         return vplbm_get_launch_count(self.ctx)
+
+    def adjoint(self, nsteps: int, window_start: int, w_cd: float = 1.0, w_cl: float = 0.0,
+                checkpoint_interval: int = 0):
+        """Gradient of w_cd mean C_D + w_cl RMS C_L over [window_start, nsteps)."""
+        return vplbm_adjoint(self.ctx, self.ny, nsteps, window_start, w_cd, w_cl, checkpoint_interval)
 
     def save(self, path):
         vplbm_save(self.ctx, path)

@@ -1,0 +1,82 @@
+"""GPU discrete adjoint against the FP64 oracle adjoint (itself pinned by
+central finite differences in the CPU suite)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from helpers import dev_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library(gpu_library):
+    return gpu_library
+
+
+def _init_both(p, precision, hist=512):
+    import paper_1905_05110_gb300 as vp
+    g = vp.Simulation(p, precision=precision, history_capacity=hist)
+    g.init_from_problem()
+    o = oracle.OracleSim(p, hist_cap=hist)
+    sh = (p["ny"], p["nx"])
+    u = p["init"]["u"]
+    o.init_equilibrium(np.ones(sh), np.full(sh, u[0]), np.full(sh, u[1]))
+    return g, o
+
+
+def _cases():
+    base = wl.adjoint_channel()
+    yield "channel", base
+    for south, north in (("periodic", "periodic"), ("noslip", "velocity")):
+        p = wl.mixed_bc_box(26, 15, seed=4, west="velocity", east="zerograd", south=south, north=north, tau=0.62,
+                            body=dict(base["body"], x=9.0, y=7.4))
+        p["bc"]["west"] = dict(base["bc"]["west"])
+        p["bc"]["west"]["ux_profile"] = wl.parabolic_profile(15, 0.03)
+        p["init"] = {"rho": 1.0, "u": (0.03, 0.0)}
+        p["eta"] = 0.05
+        yield f"box_{south}_{north}", p
+
+
+@pytest.mark.parametrize("ckpt", [0, 7, 1])
+@pytest.mark.parametrize("weights", [(1.0, 0.0), (0.0, 1.0)])
+@pytest.mark.parametrize("case", ["channel", "box_periodic_periodic", "box_noslip_velocity"])
+def test_fp64_adjoint_matches_oracle(case, weights, ckpt):
+    p = dict(_cases())[case]
+    N, w0 = 30, 15
+    g, o = _init_both(p, "f64")
+    gg, gj = g.adjoint(N, w0, *weights, checkpoint_interval=ckpt)
+    og, oj = o.adjoint(N, w0, *weights)
+    assert np.allclose(gj, oj, rtol=1e-11)
+    scale_u = np.max(np.abs(og[:-3]))
+    assert np.max(np.abs(gg[:-3] - og[:-3])) < 1e-9 * scale_u
+    for k in (-3, -2, -1):
+        assert abs(gg[k] - og[k]) < 1e-9 * abs(og[k]), k
+    # the context ends at the state after the forward run
+    assert g.nstep == N
+    assert dev_err(g.populations(), o.populations()) < 1e-12
+
+
+@pytest.mark.parametrize("weights", [(1.0, 0.0), (0.0, 1.0)])
+def test_fp32_adjoint_close_to_oracle(weights):
+    p = wl.adjoint_channel()
+    N, w0 = 30, 15
+    g, o = _init_both(p, "f32")
+    gg, gj = g.adjoint(N, w0, *weights)
+    og, oj = o.adjoint(N, w0, *weights)
+    assert np.allclose(gj, oj, rtol=1e-4)
+    scale_u = np.max(np.abs(og[:-3]))
+    assert np.max(np.abs(gg[:-3] - og[:-3])) < 1e-3 * scale_u
+    for k in (-3, -2, -1):
+        assert abs(gg[k] - og[k]) < 1e-3 * abs(og[k]), k
+
+
+def test_adjoint_rejects_free_bodies():
+    import paper_1905_05110_gb300 as vp
+    p = wl.sedimenting_disk(nx=64, ny=128, diameter=8)
+    g = vp.Simulation(p, precision="f64", history_capacity=64)
+    g.init_from_problem()
+    with pytest.raises(vp.VplbmError) as ei:
+        g.adjoint(10, 5)
+    assert ei.value.status == 6
