@@ -305,6 +305,10 @@ def run_ours(args, rank, world, local_rank):
         if "f64" in compare:
             compare["speedup_vs_f64"] = (nodes * args.steps / dt / 1e6) / compare["f64"]["mlups"]
 
+    if not args.no_compare and rank == 0:
+        compare["batched"] = run_batched(args, torch, stream)
+        compare["adjoint"] = run_adjoint(args, torch, compare.get("f64"))
+
     base = None
     if rank == 0 and not args.no_cpu_baseline:
         base = cpu_baseline(p)
@@ -322,6 +326,87 @@ def run_ours(args, rank, world, local_rank):
                 "gpu_launches": launches, "clocks": clock, "compare": compare}
         print(json.dumps(line), flush=True)
     sim.close()
+
+
+def run_batched(args, torch, stream):
+    """The 64-member spring-mounted sweep (uneven lattices) in one launch per
+    step, against the same members on the FP64 plain path, with the C_D / C_L
+    difference of one member over a run stated."""
+    import paper_1905_05110_gb300 as vp
+    probs = wl.viv_sweep()
+    nodes = sum(p["nx"] * p["ny"] for p in probs)
+    b = vp.Batch(probs, precision="f32", history_capacity=4096, stream=stream)
+    b.init_from_problems()
+    bx = b.autotune(4)
+    b.init_from_problems()
+    b.step(64)
+    b.sync()
+    k = max(64, min(512, args.steps // 50))
+    t = time_device(b, k, stream, torch)
+    b.sync()
+    mlups = nodes * k / t / 1e6
+    # FP64 plain path: every member on its own, a few steps each
+    t64 = 0.0
+    k64 = 8
+    for p in probs:
+        s64 = vp.Simulation(p, precision="f64", history_capacity=64, stream=stream)
+        s64.init_from_problem()
+        s64.step(2)
+        s64.sync()
+        t64 += time_device(s64, k64, stream, torch)
+        s64.close()
+    mlups64 = nodes * k64 / t64 / 1e6
+    # accuracy: member 0 over 3000 steps, FP32 batched vs FP64
+    acc_steps = 3000
+    m = b.members[0]
+    b.init_from_problems()
+    b.step(acc_steps)
+    h32 = m.history(0, acc_steps)
+    s64 = vp.Simulation(probs[0], precision="f64", history_capacity=acc_steps, stream=stream)
+    s64.init_from_problem()
+    s64.step(acc_steps)
+    h64 = s64.history(0, acc_steps)
+    s64.close()
+    half = acc_steps // 2
+    cd32, cd64 = h32[half:, 4].mean(), h64[half:, 4].mean()
+    b.close()
+    return {"members": len(probs), "nodes": nodes, "mlups": mlups, "steps": k, "block_x": bx,
+            "gbs_algorithmic": 72 * nodes * k / t / 1e9,
+            "f64_plain_sequential_mlups": mlups64, "speedup_vs_f64_plain": mlups / mlups64,
+            "accuracy_member0_3000_steps": {
+                "lattice": f"{probs[0]['nx']}x{probs[0]['ny']}",
+                "max_abs_dcl": float(np.max(np.abs(h32[:, 5] - h64[:, 5]))),
+                "max_abs_dcd": float(np.max(np.abs(h32[:, 4] - h64[:, 4]))),
+                "mean_cd_rel_diff_2nd_half": float(abs(cd32 - cd64) / abs(cd64))}}
+
+
+def run_adjoint(args, torch, f64_compare):
+    """Gradient of mean C_D + RMS C_L over the second half of 1024 x 512 runs
+    w.r.t. the 512-entry inlet profile, eta, s_nu, s_e (515 values), by the
+    FP32 discrete adjoint with checkpoints every 141 steps."""
+    import paper_1905_05110_gb300 as vp
+    p = wl.adjoint_disk()
+    nsteps = min(p["steps"], max(2000, args.steps // 2))
+    ck = p["checkpoint_interval"] if nsteps == p["steps"] else max(1, int(round(nsteps ** 0.5)))
+    nodes = p["nx"] * p["ny"]
+    sim = vp.Simulation(p, precision="f32", history_capacity=nsteps + 8)
+    sim.init_from_problem()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    grad, js = sim.adjoint(nsteps, nsteps // 2, 1.0, 1.0, checkpoint_interval=ck)
+    dt = time.perf_counter() - t0
+    sim.init_from_problem()
+    t_fwd = time_device(sim, nsteps, torch.cuda.current_stream(), torch)
+    sim.close()
+    nparams = p["ny"] + 3
+    out = {"lattice": f"{p['nx']}x{p['ny']}", "steps": nsteps, "checkpoint_interval": ck, "params": nparams,
+           "seconds": dt, "forward_f32_seconds": t_fwd, "J": js,
+           "speedup_vs_fd_f32_forward": 2 * nparams * t_fwd / dt,
+           "grad_norm": float(np.linalg.norm(grad))}
+    if f64_compare:
+        t_fd64 = 2 * nparams * nodes * nsteps / (f64_compare["mlups"] * 1e6)
+        out["speedup_vs_fd_f64_plain"] = t_fd64 / dt
+    return out
 
 
 def run_e2e(sim, p, steps, torch):

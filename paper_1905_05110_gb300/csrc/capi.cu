@@ -299,20 +299,8 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     p.gxf = (float)lat->gx;
     p.gyf = (float)lat->gy;
     p.pen_kf = (float)p.pen_k;
-    {
-        PairConsts &k = p.pc;
-        const double *sv = lat->s;
-        k.hgx = (float)(0.5 * lat->gx);
-        k.hgy = (float)(0.5 * lat->gy);
-        k.om1 = (float)(1.0 - sv[1]); k.om2 = (float)(1.0 - sv[2]); k.om4 = (float)(1.0 - sv[4]);
-        k.om6 = (float)(1.0 - sv[6]); k.om7 = (float)(1.0 - sv[7]); k.om8 = (float)(1.0 - sv[8]);
-        k.h1x6 = (float)(6.0 * (1.0 - 0.5 * sv[1]));
-        k.mh2x6 = (float)(-6.0 * (1.0 - 0.5 * sv[2]));
-        k.mh4 = (float)(-(1.0 - 0.5 * sv[4]));
-        k.mh6 = (float)(-(1.0 - 0.5 * sv[6]));
-        k.h7x2 = (float)(2.0 * (1.0 - 0.5 * sv[7]));
-        k.h8 = (float)(1.0 - 0.5 * sv[8]);
-    }
+    fold_consts(p.pc, lat->s, lat->gx, lat->gy);
+    fold_consts(p.pcd, lat->s, lat->gx, lat->gy);
     // wall velocity profiles: [side][comp][maxlen]
     const int maxlen = lat->nx > lat->ny ? lat->nx : lat->ny;
     std::vector<double> prof((size_t)8 * maxlen, 0.0);

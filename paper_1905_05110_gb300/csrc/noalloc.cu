@@ -160,6 +160,8 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const 
     p.gxf = (float)lat->gx;
     p.gyf = (float)lat->gy;
     p.pen_kf = (float)p.pen_k;
+    fold_consts(p.pc, lat->s, lat->gx, lat->gy);
+    fold_consts(p.pcd, lat->s, lat->gx, lat->gy);
     for (int s = 0; s < 4; ++s) {
         p.bc[s] = lat->bc[s].kind;
         p.wall_u0[s][0] = lat->bc[s].ux;

@@ -58,11 +58,27 @@ constexpr int NPART = 8;
 // Host-folded constants of the paired FP32x2 kernel (uniform over a run):
 // 1 - s_k, the (1 - s_k/2) factors of Eq. (17) with the signs and integer
 // factors of the closed-form M F folded in, and g/2.
-struct PairConsts {
-    float hgx, hgy;
-    float om1, om2, om4, om6, om7, om8;
-    float h1x6, mh2x6, mh4, mh6, h7x2, h8;
+template <typename R> struct FoldedConsts {
+    R hgx, hgy;
+    R om1, om2, om4, om6, om7, om8;
+    R h1x6, mh2x6, mh4, mh6, h7x2, h8;
 };
+using PairConsts = FoldedConsts<float>;
+
+// Fill the folded factors from the relaxation rates and fluid acceleration.
+template <typename R> inline void fold_consts(FoldedConsts<R> &k, const double *sv, double gx, double gy)
+{
+    k.hgx = (R)(0.5 * gx);
+    k.hgy = (R)(0.5 * gy);
+    k.om1 = (R)(1.0 - sv[1]); k.om2 = (R)(1.0 - sv[2]); k.om4 = (R)(1.0 - sv[4]);
+    k.om6 = (R)(1.0 - sv[6]); k.om7 = (R)(1.0 - sv[7]); k.om8 = (R)(1.0 - sv[8]);
+    k.h1x6 = (R)(6.0 * (1.0 - 0.5 * sv[1]));
+    k.mh2x6 = (R)(-6.0 * (1.0 - 0.5 * sv[2]));
+    k.mh4 = (R)(-(1.0 - 0.5 * sv[4]));
+    k.mh6 = (R)(-(1.0 - 0.5 * sv[6]));
+    k.h7x2 = (R)(2.0 * (1.0 - 0.5 * sv[7]));
+    k.h8 = (R)(1.0 - 0.5 * sv[8]);
+}
 
 struct StepParams {
     int nx, ny;
@@ -74,7 +90,8 @@ struct StepParams {
     // runs on the FP64 pipe, which is narrow on GB300)
     float sf[NQ];
     float rho0f, gxf, gyf, pen_kf, r2f;
-    PairConsts pc;
+    PairConsts pc;                // FP32 folded factors
+    FoldedConsts<double> pcd;     // FP64 folded factors
     int bc[4];
     double wall_u0[4][2];
     const double *wall_prof[4][2];

@@ -40,6 +40,11 @@ template <typename T> __device__ __forceinline__ T par(double d, float f);
 template <> __device__ __forceinline__ double par<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float par<float>(double, float f) { return f; }
 
+// Host-folded relaxation factors in the arithmetic type of the kernel.
+template <typename T> __device__ __forceinline__ const auto &folded(const StepParams &p);
+template <> __device__ __forceinline__ const auto &folded<float>(const StepParams &p) { return p.pc; }
+template <> __device__ __forceinline__ const auto &folded<double>(const StepParams &p) { return p.pcd; }
+
 __device__ __forceinline__ double wall_u(const StepParams &p, int side, int comp, int k)
 {
     const double *prof = p.wall_prof[side][comp];
@@ -245,10 +250,14 @@ __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState
     using T = typename Prec<P>::T;
     constexpr bool DEV = Prec<P>::DEV;
     bool chi = false;
-    const T rs = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    // sums shared by the moments (rows of Eq. 15)
+    const T d13 = f[1] - f[3], d24 = f[2] - f[4], b13 = f[1] + f[3], b24 = f[2] + f[4];
+    const T d56 = f[5] - f[6], d87 = f[8] - f[7], a56 = f[5] + f[6], a78 = f[7] + f[8];
+    const T sx = d56 + d87, ty = a56 - a78, sa = b13 + b24, sd = a56 + a78;
+    const T rs = (f[0] + sa) + sd;
     const T rho = DEV ? par<T>(p.rho0, p.rho0f) + rs : rs;
-    const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const T jx = d13 + sx;
+    const T jy = d24 + ty;
 
     // chi and u_s (Eq. 2, Alg. 1 step 4), only where the disk can be
     T dxl = 0, dyl = 0;
@@ -297,29 +306,27 @@ __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState
     const T Gx = rho * (gx + ax);
     const T Gy = rho * (gy + ay);
 
-    // moments (rows of Eq. 15); equilibria (Eq. 14); M F closed form
-    const T sa = (f[1] + f[2]) + (f[3] + f[4]);
-    const T sd = (f[5] + f[6]) + (f[7] + f[8]);
-    const T e = (T)-4 * f[0] - sa + (T)2 * sd;
-    const T ep = (T)4 * f[0] - (T)2 * sa + sd;
-    const T qx = (T)2 * (f[3] - f[1]) + (f[5] - f[6]) + (f[8] - f[7]);
-    const T qy = (T)2 * (f[4] - f[2]) + (f[5] + f[6]) - (f[7] + f[8]);
-    const T pxx = (f[1] + f[3]) - (f[2] + f[4]);
+    // moments (rows of Eq. 15); equilibria (Eq. 14); M F closed form;
+    // Eq. (17) with the host-folded factors 1 - s_k and (1 - s_k/2)
+    const T e = fma((T)-4, f[0], fma((T)2, sd, -sa));
+    const T ep = fma((T)4, f[0], fma((T)-2, sa, sd));
+    const T qx = fma((T)-2, d13, sx);
+    const T qy = fma((T)-2, d24, ty);
+    const T pxx = b13 - b24;
     const T pxy = (f[5] + f[7]) - (f[6] + f[8]);
 
-    const T u2r = rho * (ux * ux + uy * uy);
-    const T uG = ux * Gx + uy * Gy;
-    const T s1 = par<T>(p.s[1], p.sf[1]), s2 = par<T>(p.s[2], p.sf[2]), s4 = par<T>(p.s[4], p.sf[4]);
-    const T s6 = par<T>(p.s[6], p.sf[6]), s7 = par<T>(p.s[7], p.sf[7]), s8 = par<T>(p.s[8], p.sf[8]);
-
-    const T e_s = e - s1 * (e - ((T)-2 * rs + (T)3 * u2r)) + ((T)1 - (T)0.5 * s1) * ((T)6 * uG);
-    const T ep_s = ep - s2 * (ep - (rs - (T)3 * u2r)) - ((T)1 - (T)0.5 * s2) * ((T)6 * uG);
+    const auto &k = folded<T>(p);
+    const T ux2 = ux * ux, uy2 = uy * uy;
+    const T u2r = rho * (ux2 + uy2);
+    const T uG = fma(ux, Gx, uy * Gy);
+    const T e_s = fma((T)k.om1, e, fma(par<T>(p.s[1], p.sf[1]), fma((T)3, u2r, (T)-2 * rs), (T)k.h1x6 * uG));
+    const T ep_s = fma((T)k.om2, ep, fma(par<T>(p.s[2], p.sf[2]), fma((T)-3, u2r, rs), (T)k.mh2x6 * uG));
     const T jx_s = jx + Gx;
     const T jy_s = jy + Gy;
-    const T qx_s = qx - s4 * (qx + rho * ux) - ((T)1 - (T)0.5 * s4) * Gx;
-    const T qy_s = qy - s6 * (qy + rho * uy) - ((T)1 - (T)0.5 * s6) * Gy;
-    const T pxx_s = pxx - s7 * (pxx - rho * (ux * ux - uy * uy)) + ((T)1 - (T)0.5 * s7) * ((T)2 * (ux * Gx - uy * Gy));
-    const T pxy_s = pxy - s8 * (pxy - rho * ux * uy) + ((T)1 - (T)0.5 * s8) * (ux * Gy + uy * Gx);
+    const T qx_s = fma((T)k.om4, qx, fma(-par<T>(p.s[4], p.sf[4]), rho * ux, (T)k.mh4 * Gx));
+    const T qy_s = fma((T)k.om6, qy, fma(-par<T>(p.s[6], p.sf[6]), rho * uy, (T)k.mh6 * Gy));
+    const T pxx_s = fma((T)k.om7, pxx, fma(par<T>(p.s[7], p.sf[7]), rho * (ux2 - uy2), (T)k.h7x2 * fma(ux, Gx, -uy * Gy)));
+    const T pxy_s = fma((T)k.om8, pxy, fma(par<T>(p.s[8], p.sf[8]), rho * (ux * uy), (T)k.h8 * fma(ux, Gy, uy * Gx)));
 
     // back to populations, M^-1 = M^T diag(1/|row|^2)
     const T r9 = rs * (T)(1.0 / 9.0);

@@ -80,3 +80,42 @@ def test_adjoint_rejects_free_bodies():
     with pytest.raises(vp.VplbmError) as ei:
         g.adjoint(10, 5)
     assert ei.value.status == 6
+
+
+def _objective_gpu(p, N, w0):
+    import paper_1905_05110_gb300 as vp
+    g = vp.Simulation(p, precision="f64", history_capacity=N + 8)
+    g.init_from_problem()
+    g.step(N)
+    h = g.history(0, N)
+    g.close()
+    return h[w0:, 4].mean() + np.sqrt(np.mean(h[w0:, 5] ** 2))
+
+
+def test_adjoint_directional_derivatives_match_central_differences():
+    # The oscillating-disk gradient workload, scaled down: 8 random directions
+    # in the 99-dimensional parameter space (inlet profile, eta, s_nu, s_e),
+    # central differences with h = 1e-4 of each parameter's scale, FP64.
+    p = wl.adjoint_disk(nx=192, ny=96, diameter=12, steps=400, checkpoint_interval=20)
+    p["eta"] = 0.02
+    N, w0 = 400, 200
+    import paper_1905_05110_gb300 as vp
+    g = vp.Simulation(p, precision="f64", history_capacity=N + 8)
+    g.init_from_problem()
+    grad, js = g.adjoint(N, w0, 1.0, 1.0, checkpoint_interval=20)
+    prof = p["bc"]["west"]["ux_profile"]
+    scale = np.concatenate([np.full(p["ny"], 0.04), [p["eta"], p["s"][7], p["s"][1]]])
+    rng = np.random.default_rng(5)
+    h = 1e-4
+    for _ in range(8):
+        v = rng.standard_normal(p["ny"] + 3)
+        v /= np.linalg.norm(v)
+        dth = h * scale * v
+
+        def perturbed(sign):
+            return wl.with_params(p, u_in_profile=prof + sign * dth[:-3], eta=p["eta"] + sign * dth[-3],
+                                  s_nu=p["s"][7] + sign * dth[-2], s_e=p["s"][1] + sign * dth[-1])
+
+        fd = (_objective_gpu(perturbed(1), N, w0) - _objective_gpu(perturbed(-1), N, w0)) / (2 * h)
+        adj = float(grad @ (scale * v))
+        assert abs(fd - adj) < 1e-4 * abs(adj) + 1e-10, (fd, adj)

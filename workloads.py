@@ -185,11 +185,16 @@ def viv_sweep(n=64, steps=50_000) -> list:
 
 
 def adjoint_disk(nx=1024, ny=512, diameter=32.0, u0=0.04, re=100.0, eta=1e-3,
-                 amp_over_d=0.2, steps=20_000) -> dict:
-    """Imposed oscillation used for the gradient workload."""
+                 amp_over_d=0.2, steps=20_000, checkpoint_interval=141) -> dict:
+    """Imposed oscillation used for the gradient workload: the inlet is a
+    per-node u_x profile (ny entries, uniform u0) so that its gradient has one
+    entry per inlet node."""
     p = oscillating_disk(nx=nx, ny=ny, diameter=diameter, x_c=0.2 * nx, u0=u0,
                          re=re, eta=eta, amp_over_d=amp_over_d, steps=steps)
     p["name"] = f"adjoint_disk_{nx}x{ny}"
+    p["bc"] = dict(p["bc"])
+    p["bc"]["west"] = _bc("velocity", ux_profile=np.full(ny, u0))
+    p["checkpoint_interval"] = checkpoint_interval
     return p
 
 
