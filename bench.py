@@ -43,10 +43,10 @@ CSRC = os.path.join(ROOT, "paper_1905_05110_gb300", "csrc")
 
 
 def kernel_name(prec: str, launch) -> str:
-    base = {"tma": "vp_mrt_step_tma", "pair": "vp_mrt_step_pair", "scalar": "vp_mrt_step",
-            "async": "vp_mrt_step_async", "pipe": "vp_mrt_step_pipe",
-            "stream": "vp_mrt_step_stream", "scalar48": "vp_mrt_step", "scalar40": "vp_mrt_step"}[launch[0]]
-    return f"{base}<{PREC_ID[prec]}>"
+    if launch[0] == "tma":
+        return f"vp_mrt_step_tma<{PREC_ID[prec]}>"
+    minb = {"scalar": 4, "scalar48": 5, "scalar40": 6}[launch[0]]
+    return f"vp_mrt_step<{PREC_ID[prec]}, {minb}>"
 
 
 def workload(name: str) -> dict:
@@ -86,7 +86,7 @@ def kernel_source_hash() -> str:
 
 def profiled_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if still valid."""
-    stem = kernel.replace("<", "_").replace(">", "")
+    stem = kernel.replace("<", "_").replace(">", "").replace(", ", "_")
     path = os.path.join(PROFILE_DIR, f"{stem}_{workload}.md")
     try:
         text = open(path).read()
@@ -337,7 +337,7 @@ def run_batched(args, torch, stream):
     nodes = sum(p["nx"] * p["ny"] for p in probs)
     b = vp.Batch(probs, precision="f32", history_capacity=4096, stream=stream)
     b.init_from_problems()
-    bx = b.autotune(4)
+    shape = b.autotune(4)
     b.init_from_problems()
     b.step(64)
     b.sync()
@@ -370,7 +370,7 @@ def run_batched(args, torch, stream):
     half = acc_steps // 2
     cd32, cd64 = h32[half:, 4].mean(), h64[half:, 4].mean()
     b.close()
-    return {"members": len(probs), "nodes": nodes, "mlups": mlups, "steps": k, "block_x": bx,
+    return {"members": len(probs), "nodes": nodes, "mlups": mlups, "steps": k, "block": list(shape),
             "gbs_algorithmic": 72 * nodes * k / t / 1e9,
             "f64_plain_sequential_mlups": mlups64, "speedup_vs_f64_plain": mlups / mlups64,
             "accuracy_member0_3000_steps": {

@@ -202,36 +202,22 @@ vplbm_status vplbm_get_history(vplbm_ctx *ctx, long long first, long long count,
 /* Pose (x, y, theta), velocity (vx, vy, omega) and step counter. */
 vplbm_status vplbm_get_body(vplbm_ctx *ctx, double q[3], double v[3], long long *step);
 
-/* Step kernels.  All compute the same method; they differ in data movement:
- *  VPLBM_KERNEL_SCALAR  one node per thread (every precision), register
- *                       budget for 4 blocks of 256 threads per SM;
- *  VPLBM_KERNEL_SCALAR_48 / _40  the same with the budget of 5 / 6 blocks
- *                       (48 / 40 registers); _48 is the default;
- *  VPLBM_KERNEL_PAIR    two x-adjacent nodes per thread with packed FP32x2
- *                       arithmetic (FP32/FP16 storage, even nx);
- *  VPLBM_KERNEL_TMA     persistent blocks fed by tensor-memory-accelerator
- *                       copies into a shared-memory ring (FP32/FP16 storage,
- *                       nx * element size a multiple of 16 bytes,
- *                       nx >= 136 (FP32) / 144 (FP16), ny >= 6);
- *  VPLBM_KERNEL_ASYNC   four nodes per thread down a column, their
- *                       populations copied to shared memory two nodes ahead
- *                       of the collision (FP32/FP16 storage);
- *  VPLBM_KERNEL_PIPE    a warp walks four rows of a 64-column strip, two
- *                       nodes per lane, the rows it pulls copied to shared
- *                       memory two rows ahead, packed FP32x2 collision
- *                       (FP32/FP16 storage, even nx; block_x 128 or 256,
- *                       block_y 1);
- *  VPLBM_KERNEL_STREAM  persistent blocks walk runs of 2*block_x x block_y
- *                       tiles, two nodes per thread, the next tile's
- *                       populations prefetched into registers while the
- *                       current one collides on the packed FP32x2 pipe
- *                       (FP32/FP16 storage, even nx).
- * Nodes on the lattice edges and near the body always take the scalar
- * arithmetic.  The results of different kernels agree to the rounding of
- * the storage precision. */
+/* Step kernels.  Both compute the same method; they differ in data movement:
+ *  VPLBM_KERNEL_SCALAR     one node per thread, its nine pulls loaded straight
+ *                          into registers (every precision), register budget
+ *                          of 4 blocks of 256 threads per SM (64 registers);
+ *  VPLBM_KERNEL_SCALAR_48  the same sized for 5 blocks (48 registers): the
+ *                          default;
+ *  VPLBM_KERNEL_SCALAR_40  the same sized for 6 blocks (40 registers);
+ *  VPLBM_KERNEL_TMA        persistent blocks fed by tensor-memory-accelerator
+ *                          copies into a shared-memory ring (FP32/FP16
+ *                          storage, nx * element size a multiple of 16 bytes,
+ *                          nx >= 136 (FP32) / 144 (FP16), ny >= 4).
+ * Nodes on the lattice edges and near the body always take the same code.
+ * The results of different kernels agree to the rounding of the storage
+ * precision. */
 typedef enum {
-    VPLBM_KERNEL_SCALAR = 0, VPLBM_KERNEL_PAIR = 1, VPLBM_KERNEL_TMA = 2, VPLBM_KERNEL_ASYNC = 3,
-    VPLBM_KERNEL_PIPE = 4, VPLBM_KERNEL_STREAM = 5, VPLBM_KERNEL_SCALAR_48 = 6, VPLBM_KERNEL_SCALAR_40 = 7
+    VPLBM_KERNEL_SCALAR = 0, VPLBM_KERNEL_SCALAR_48 = 1, VPLBM_KERNEL_SCALAR_40 = 2, VPLBM_KERNEL_TMA = 3
 } vplbm_kernel;
 
 /* Kernel and block shape: block_x * block_y threads, block_x a multiple of
@@ -290,13 +276,13 @@ vplbm_status vplbm_adjoint(vplbm_ctx *ctx, const vplbm_adjoint_desc *desc, doubl
  * Many independent simulations of uneven lattice sizes (a parameter sweep:
  * stiffness, reduced velocity, ... as in the vortex-induced-vibration study
  * of Sec. 3.3) advanced together: one kernel launch per time step covers the
- * tiles of every member (warp-pipelined paired kernel), K steps at a time
+ * tiles of every member (the scalar step's tile code), K steps at a time
  * as CUDA graphs, each member keeping its own body, force reduction, tail
  * and history.  Members are ordinary contexts (vplbm_batch_member): every
  * per-simulation call (init, fields, history, body, checkpoints) works on
  * them; vplbm_step on a single member would take it out of step with the
  * others, which vplbm_batch_step then rejects with VPLBM_EINVAL.
- * All members: same precision, FP32 or FP16 deviation storage, even nx. */
+ * All members: the same precision. */
 typedef struct vplbm_batch vplbm_batch;
 
 /* lats[0..n-1] describe the members; bodies is NULL (no body anywhere) or an
@@ -309,11 +295,12 @@ vplbm_status vplbm_batch_member(vplbm_batch *batch, int k, vplbm_ctx **member);
 vplbm_status vplbm_batch_step(vplbm_batch *batch, long long nsteps);
 /* Wait; returns the first member's latched device error, if any. */
 vplbm_status vplbm_batch_sync(vplbm_batch *batch);
-/* Threads per block of the batched kernel (128 or 256) and the number of
- * batched step launches made so far. */
-vplbm_status vplbm_batch_set_launch(vplbm_batch *batch, int block_x);
-vplbm_status vplbm_batch_get_launch(vplbm_batch *batch, int *block_x, long long *launches);
-/* Time each block width over 2 x steps_per_trial steps and keep the fastest;
+/* Block (tile) shape of the batched kernel: block_x a multiple of 32,
+ * block_x * block_y in {128, 256}; and the number of batched step launches
+ * made so far. */
+vplbm_status vplbm_batch_set_launch(vplbm_batch *batch, int block_x, int block_y);
+vplbm_status vplbm_batch_get_launch(vplbm_batch *batch, int *block_x, int *block_y, long long *launches);
+/* Time four block shapes over 2 x steps_per_trial steps each, keep the fastest;
  * the trial steps advance the members (they are real steps). */
 vplbm_status vplbm_batch_autotune(vplbm_batch *batch, int steps_per_trial);
 

@@ -135,8 +135,9 @@ _SIGS = {
     "vplbm_batch_member": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(_CTX)]),
     "vplbm_batch_step": (C.c_int, [C.c_void_p, C.c_longlong]),
     "vplbm_batch_sync": (C.c_int, [C.c_void_p]),
-    "vplbm_batch_set_launch": (C.c_int, [C.c_void_p, C.c_int]),
-    "vplbm_batch_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
+    "vplbm_batch_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "vplbm_batch_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.POINTER(C.c_longlong)]),
     "vplbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int]),
     "vplbm_adjoint": (C.c_int, [_CTX, C.c_void_p, _D, _D]),
     "vplbm_last_error": (C.c_char_p, []),
@@ -324,7 +325,7 @@ def vplbm_get_body(ctx):
     return q, v, int(step.value)
 
 
-KERNELS = {"scalar": 0, "pair": 1, "tma": 2, "async": 3, "pipe": 4, "stream": 5, "scalar48": 6, "scalar40": 7}
+KERNELS = {"scalar": 0, "scalar48": 1, "scalar40": 2, "tma": 3}
 KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
 
 
@@ -391,14 +392,14 @@ def vplbm_batch_sync(batch):
     _check(load_library().vplbm_batch_sync(batch))
 
 
-def vplbm_batch_set_launch(batch, block_x: int):
-    _check(load_library().vplbm_batch_set_launch(batch, int(block_x)))
+def vplbm_batch_set_launch(batch, block_x: int, block_y: int = 1):
+    _check(load_library().vplbm_batch_set_launch(batch, int(block_x), int(block_y)))
 
 
 def vplbm_batch_get_launch(batch):
-    bx, n = C.c_int(), C.c_longlong()
-    _check(load_library().vplbm_batch_get_launch(batch, C.byref(bx), C.byref(n)))
-    return bx.value, int(n.value)
+    bx, by, n = C.c_int(), C.c_int(), C.c_longlong()
+    _check(load_library().vplbm_batch_get_launch(batch, C.byref(bx), C.byref(by), C.byref(n)))
+    return bx.value, by.value, int(n.value)
 
 
 def vplbm_batch_autotune(batch, steps_per_trial: int = 8):
@@ -612,12 +613,13 @@ class Batch:
     def sync(self):
         vplbm_batch_sync(self.handle)
 
-    def set_launch(self, block_x: int):
-        vplbm_batch_set_launch(self.handle, block_x)
+    def set_launch(self, block_x: int, block_y: int = 1):
+        vplbm_batch_set_launch(self.handle, block_x, block_y)
 
     def launch(self):
+        """(block_x, block_y, batched launches so far)."""
         return vplbm_batch_get_launch(self.handle)
 
     def autotune(self, steps_per_trial: int = 8):
         vplbm_batch_autotune(self.handle, steps_per_trial)
-        return self.launch()[0]
+        return self.launch()[:2]

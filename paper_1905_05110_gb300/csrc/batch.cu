@@ -1,6 +1,7 @@
 // Batched sweep: many simulations of uneven lattice sizes stepped together,
-// one launch per time step covering every member's tiles (captured as CUDA
-// graphs of 32 steps), each member with its own body, reduction and tail.
+// one launch per time step covering every member's tiles (the scalar step's
+// tile code, captured as CUDA graphs of 32 steps), each member with its own
+// body, reduction and tail.
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -34,27 +35,26 @@ struct vplbm_batch {
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;
     int precision = 0;
-    int bx = 256;                     // threads per block of the batched kernel
+    int bx = 256, by = 1;             // block (tile) shape of the batched kernel
     StepParams *params_dev = nullptr; // [2][n]: parameters of each member per step parity
     int *tile_start_dev = nullptr;    // [n + 1]
     int total_tiles = 0;
     cudaGraphExec_t graph = nullptr;
-    int graph_bx = -1;
+    int graph_bx = -1, graph_by = -1;
     long long launches = 0;
 };
 
 namespace {
 
-// Tile prefix of the members for block width bx (tiles of 64 x bx/32*rows).
+// Tile prefix of the members for the block shape bx x by.
 vplbm_status build_tiles(vplbm_batch *b)
 {
     std::vector<int> start(b->n + 1, 0);
-    const int tile_h = (b->bx / 32) * pipe_rows_per_warp();
     long long total = 0;
     for (int k = 0; k < b->n; ++k) {
         const vplbm_ctx *c = b->members[k];
         start[k] = (int)total;
-        total += (long long)((c->nx + 63) / 64) * ((c->ny + tile_h - 1) / tile_h);
+        total += (long long)((c->nx + b->bx - 1) / b->bx) * ((c->ny + b->by - 1) / b->by);
     }
     if (total > (1LL << 30)) return berr(VPLBM_EINVAL, "batch too large (%lld tiles)", total);
     start[b->n] = (int)total;
@@ -84,7 +84,7 @@ cudaError_t launch_batch_step(const vplbm_batch *b, long long step, cudaStream_t
     bl.params = b->params_dev + (size_t)(step & 1) * b->n;
     bl.tile_start = b->tile_start_dev;
     bl.n = b->n;
-    return launch_step_pipe_batch(b->precision, bl, b->total_tiles, b->bx, stream);
+    return launch_step_batch(b->precision, bl, b->total_tiles, b->bx, b->by, stream);
 }
 
 // All members must stand at the same step (they advance together).
@@ -100,7 +100,7 @@ vplbm_status common_step(const vplbm_batch *b, long long *step)
 
 vplbm_status ensure_batch_graph(vplbm_batch *b)
 {
-    if (b->graph && b->graph_bx == b->bx) return VPLBM_OK;
+    if (b->graph && b->graph_bx == b->bx && b->graph_by == b->by) return VPLBM_OK;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -119,6 +119,7 @@ vplbm_status ensure_batch_graph(vplbm_batch *b)
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return berr(VPLBM_ECUDA, "batch graph instantiate failed: %s", cudaGetErrorString(e));
     b->graph_bx = b->bx;
+    b->graph_by = b->by;
     return VPLBM_OK;
 }
 
@@ -170,12 +171,8 @@ vplbm_status vplbm_batch_create(const vplbm_lattice_desc *lats, const vplbm_body
     if (!out || !lats || n < 1) return berr(VPLBM_EINVAL, "need n >= 1 lattice descriptors and an out pointer");
     *out = nullptr;
     const int prec = lats[0].precision;
-    for (int k = 0; k < n; ++k) {
+    for (int k = 0; k < n; ++k)
         if (lats[k].precision != prec) return berr(VPLBM_EINVAL, "member %d: all members need the same precision", k);
-        if (prec != VPLBM_F32_DEV && prec != VPLBM_F16_DEV)
-            return berr(VPLBM_EUNSUPPORTED, "the batched step runs FP32/FP16 deviation storage");
-        if (lats[k].nx % 2) return berr(VPLBM_EUNSUPPORTED, "member %d: the batched step needs an even nx", k);
-    }
     vplbm_batch *b = new (std::nothrow) vplbm_batch();
     if (!b) return berr(VPLBM_ENOMEM, "host allocation failed");
     b->n = n;
@@ -195,7 +192,6 @@ vplbm_status vplbm_batch_create(const vplbm_lattice_desc *lats, const vplbm_body
         e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaMalloc(&b->params_dev, 2 * (size_t)n * sizeof(StepParams));
         if (e == cudaSuccess) e = cudaMalloc(&b->tile_start_dev, (size_t)(n + 1) * sizeof(int));
-        if (e == cudaSuccess) e = pipe_batch_prepare(prec, b->bx);
         if (e != cudaSuccess) st = berr(VPLBM_ECUDA, "batch setup failed: %s", cudaGetErrorString(e));
     }
     if (st == VPLBM_OK) st = upload_params(b);
@@ -234,33 +230,35 @@ vplbm_status vplbm_batch_sync(vplbm_batch *b)
     return VPLBM_OK;
 }
 
-vplbm_status vplbm_batch_set_launch(vplbm_batch *b, int block_x)
+vplbm_status vplbm_batch_set_launch(vplbm_batch *b, int block_x, int block_y)
 {
     if (!b) return berr(VPLBM_EINVAL, "batch is NULL");
-    if (block_x != 128 && block_x != 256) return berr(VPLBM_EINVAL, "block_x must be 128 or 256");
+    const int t = block_x * block_y;
+    if (block_x < 32 || block_x % 32 || block_y < 1 || (t != 128 && t != 256))
+        return berr(VPLBM_EINVAL, "block shape %dx%d not allowed", block_x, block_y);
     for (int k = 0; k < b->n; ++k) {
         const vplbm_ctx *c = b->members[k];
-        const int tile_h = (block_x / 32) * pipe_rows_per_warp();
-        if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, 64, tile_h) >
+        if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, block_x, block_y) >
             c->max_parts)
-            return berr(VPLBM_EINVAL, "member %d: launch shape needs more reduction scratch than allocated", k);
+            return berr(VPLBM_EINVAL, "member %d: block shape needs more reduction scratch than allocated", k);
     }
-    cudaError_t e = pipe_batch_prepare(b->precision, block_x);
-    if (e != cudaSuccess) return berr(VPLBM_ECUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(e));
-    const int old = b->bx;
+    const int obx = b->bx, oby = b->by;
     b->bx = block_x;
+    b->by = block_y;
     vplbm_status st = build_tiles(b);
     if (st != VPLBM_OK) {
-        b->bx = old;
+        b->bx = obx;
+        b->by = oby;
         build_tiles(b);
     }
     return st;
 }
 
-vplbm_status vplbm_batch_get_launch(vplbm_batch *b, int *block_x, long long *launches)
+vplbm_status vplbm_batch_get_launch(vplbm_batch *b, int *block_x, int *block_y, long long *launches)
 {
     if (!b) return berr(VPLBM_EINVAL, "batch is NULL");
     if (block_x) *block_x = b->bx;
+    if (block_y) *block_y = b->by;
     if (launches) *launches = b->launches;
     return VPLBM_OK;
 }
@@ -274,11 +272,12 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int steps_per_trial)
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return berr(VPLBM_ECUDA, "event creation failed");
     float best = 1e30f;
-    int best_bx = b->bx;
+    int best_bx = b->bx, best_by = b->by;
     vplbm_status st = VPLBM_OK;
-    const int cands[2] = {256, 128};
-    for (int bx : cands) {
-        st = vplbm_batch_set_launch(b, bx);
+    const int cands[4][2] = {{256, 1}, {128, 1}, {128, 2}, {64, 2}};
+    for (const auto &cb : cands) {
+        const int bx = cb[0], by = cb[1];
+        st = vplbm_batch_set_launch(b, bx, by);
         if (st != VPLBM_OK) break;
         for (int rep = 0; rep < 2 && st == VPLBM_OK; ++rep) {
             cudaEventRecord(e0, b->stream);
@@ -290,13 +289,14 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int steps_per_trial)
             if (rep == 1 && ms < best) {
                 best = ms;
                 best_bx = bx;
+                best_by = by;
             }
         }
         if (st != VPLBM_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    vplbm_status st2 = vplbm_batch_set_launch(b, best_bx);
+    vplbm_status st2 = vplbm_batch_set_launch(b, best_bx, best_by);
     return st != VPLBM_OK ? st : st2;
 }
 

@@ -146,7 +146,7 @@ void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long 
     long long parts = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr,
                                            TMA_TILE_W, TMA_TILE_H);
     for (int k = 0; k < N_SHAPES; ++k)
-        for (int kern = KERNEL_SCALAR; kern <= KERNEL_SCALAR_40; ++kern) {   // every kernel's tiling
+        for (int kern = KERNEL_SCALAR; kern <= KERNEL_TMA; ++kern) {   // every kernel's tiling
             int w, h;
             tile_of(kern, SHAPES[k][0], SHAPES[k][1], &w, &h);
             const long long m = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr, w, h);
@@ -192,27 +192,15 @@ cudaError_t launch_one(const vplbm_ctx *c, long long step, cudaStream_t stream)
 {
     const StepParams p = params_for(c, step);
     if (c->kernel == KERNEL_TMA) return launch_step_tma(c->precision, p, c->tmap[step & 1], c->tma_grid, stream);
-    if (c->kernel == KERNEL_PAIR) return launch_step_pair(c->precision, p, c->bx, c->by, stream);
-    if (c->kernel == KERNEL_ASYNC) return launch_step_async(c->precision, p, c->bx, c->by, stream);
-    if (c->kernel == KERNEL_PIPE) return launch_step_pipe(c->precision, p, c->bx, stream);
-    if (c->kernel == KERNEL_STREAM) return launch_step_stream(c->precision, p, c->bx, c->by, c->stream_grid, stream);
     const int minb = c->kernel == KERNEL_SCALAR_40 ? 6 : c->kernel == KERNEL_SCALAR_48 ? 5 : 4;
     return launch_step(c->precision, p, c->bx, c->by, stream, minb);
 }
 
-bool pair_ok(const vplbm_ctx *c)
-{
-    return (c->precision == VPLBM_F32_DEV || c->precision == VPLBM_F16_DEV) && c->nx % 2 == 0;
-}
 
 // Reduction tile of a launch choice (the pair kernel's block covers 2*bx).
 void tile_of(int kernel, int bx, int by, int *w, int *h)
 {
     if (kernel == KERNEL_TMA) { *w = TMA_TILE_W; *h = TMA_TILE_H; }
-    else if (kernel == KERNEL_PAIR) { *w = 2 * bx; *h = by; }
-    else if (kernel == KERNEL_ASYNC) { *w = bx; *h = by * async_rows_per_thread(); }
-    else if (kernel == KERNEL_PIPE) { *w = 64; *h = (bx / 32) * pipe_rows_per_warp(); }
-    else if (kernel == KERNEL_STREAM) { *w = 2 * bx; *h = by; }
     else { *w = bx; *h = by; }   // the scalar kernels
 }
 
@@ -721,28 +709,8 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
         c->by = 2;
         return VPLBM_OK;
     }
-    if (kernel == KERNEL_PIPE) {
-        if (!pair_ok(c)) return fail(VPLBM_EUNSUPPORTED, "the warp-pipelined kernel needs FP32/FP16 storage and an even nx");
-        if (bx != 128 && bx != 256) return fail(VPLBM_EINVAL, "the warp-pipelined kernel takes 128 or 256 threads");
-        int w, h;
-        tile_of(kernel, bx, 1, &w, &h);
-        if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, w, h) > c->max_parts)
-            return fail(VPLBM_EINVAL, "launch shape needs more reduction scratch than allocated");
-        cudaError_t e = pipe_prepare(c->precision, bx);
-        if (e != cudaSuccess) return fail(VPLBM_ECUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(e));
-        c->kernel = kernel;
-        c->bx = bx;
-        c->by = 1;
-        return VPLBM_OK;
-    }
-    if (kernel < KERNEL_SCALAR || kernel > KERNEL_SCALAR_40 || kernel == KERNEL_TMA || kernel == KERNEL_PIPE)
+    if (kernel != KERNEL_SCALAR && kernel != KERNEL_SCALAR_48 && kernel != KERNEL_SCALAR_40)
         return fail(VPLBM_EINVAL, "unknown kernel %d", kernel);
-    if (kernel == KERNEL_STREAM && !pair_ok(c))
-        return fail(VPLBM_EUNSUPPORTED, "the streaming kernel needs FP32/FP16 storage and an even nx");
-    if (kernel == KERNEL_PAIR && !pair_ok(c))
-        return fail(VPLBM_EUNSUPPORTED, "the paired kernel needs FP32/FP16 storage and an even nx");
-    if (kernel == KERNEL_ASYNC && c->precision == VPLBM_F64)
-        return fail(VPLBM_EUNSUPPORTED, "the pipelined kernel needs FP32/FP16 storage");
     const int t = bx * by;
     if (bx < 32 || bx % 32 || by < 1 || (t != 128 && t != 256))
         return fail(VPLBM_EINVAL, "launch shape %dx%d not allowed", bx, by);
@@ -750,13 +718,6 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
     tile_of(kernel, bx, by, &w, &h);
     if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, w, h) > c->max_parts)
         return fail(VPLBM_EINVAL, "launch shape %dx%d needs more reduction scratch than allocated", bx, by);
-    if (kernel == KERNEL_STREAM) {
-        int per_sm = 0, nsm = 0;
-        cudaError_t e = stream_prepare(c->precision, bx, by, &per_sm);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-        if (e != cudaSuccess || per_sm < 1) return fail(VPLBM_ECUDA, "occupancy query failed");
-        c->stream_grid = per_sm * nsm;
-    }
     c->kernel = kernel;
     c->bx = bx;
     c->by = by;
@@ -827,11 +788,12 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
         }
         // candidates: the TMA-staged kernel, then every shape of the paired
         // and of the scalar kernel
-        static const int kinds[6] = {KERNEL_SCALAR_48, KERNEL_SCALAR_40, KERNEL_SCALAR, KERNEL_PAIR, KERNEL_ASYNC,
-                                     KERNEL_STREAM};
-        for (int cand = -3; cand < 6 * N_SHAPES; ++cand) {
-            const int ck = cand == -3 ? KERNEL_TMA : cand < 0 ? KERNEL_PIPE : kinds[cand / N_SHAPES];
-            const int cbx = cand == -3 ? 0 : cand == -2 ? 256 : cand == -1 ? 128 : SHAPES[cand % N_SHAPES][0];
+        // candidates: the TMA-staged kernel, then every block shape of the
+        // three register budgets of the scalar kernel
+        static const int kinds[3] = {KERNEL_SCALAR_48, KERNEL_SCALAR_40, KERNEL_SCALAR};
+        for (int cand = -1; cand < 3 * N_SHAPES; ++cand) {
+            const int ck = cand < 0 ? KERNEL_TMA : kinds[cand / N_SHAPES];
+            const int cbx = cand < 0 ? 0 : SHAPES[cand % N_SHAPES][0];
             const int cby = cand < 0 ? 1 : SHAPES[cand % N_SHAPES][1];
             if (vplbm_set_launch(c, ck, cbx, cby) != VPLBM_OK) continue;
             for (int rep = 0; rep < 2; ++rep) {   // first pass warms up

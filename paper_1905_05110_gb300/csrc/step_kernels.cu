@@ -33,24 +33,21 @@ namespace {
 
 // ---- the fused step ----------------------------------------------------
 
-// MINB: blocks of 256 threads per SM the register budget is sized for
-// (4: 64 registers, 5: 48, 6: 40).
-template <int P, int MINB>
-__global__ void __launch_bounds__(256, MINB) vp_mrt_step(const StepParams p)
+// One tile of the step: blockDim.x x blockDim.y nodes at tile (tile_x,
+// tile_y); p may live in shared memory (batched launch).
+template <int P>
+__device__ __forceinline__ void scalar_tile(const StepParams &p, int tile_x, int tile_y, double (*red)[NPART],
+                                            int *s_last)
 {
     using S = typename Prec<P>::S;
     using T = typename Prec<P>::T;
-
-    __shared__ double red[8][NPART];
-    __shared__ int s_last;
-
-    const int bi0 = blockIdx.x * blockDim.x, bj0 = blockIdx.y * blockDim.y;
+    const int bi0 = tile_x * blockDim.x, bj0 = tile_y * blockDim.y;
     const int i = bi0 + threadIdx.x;
     const int j = bj0 + threadIdx.y;
     const S *__restrict__ fin = static_cast<const S *>(p.fin);
     S *__restrict__ fout = static_cast<S *>(p.fout);
     const BodyState *__restrict__ bs = p.bs_in;
-    // no node of the block on a lattice edge (uniform over the block)
+    // no node of the tile on a lattice edge (uniform over the block)
     const bool block_interior = bi0 > 0 && bj0 > 0 && bi0 + (int)blockDim.x < p.nx && bj0 + (int)blockDim.y < p.ny;
     const bool inside = block_interior || (i < p.nx && j < p.ny);
 
@@ -60,7 +57,7 @@ __global__ void __launch_bounds__(256, MINB) vp_mrt_step(const StepParams p)
     else if (inside) pull_all<P>(p, fin, i, j, f);
 
     const int4 range = __ldg(reinterpret_cast<const int4 *>(&bs->ilo));   // ilo, ihi, jlo, jhi
-    const bool part_block = tile_near_body(range, bi0, bj0, blockDim.x, blockDim.y, blockIdx.x == 0 && blockIdx.y == 0);
+    const bool part_block = tile_near_body(range, bi0, bj0, blockDim.x, blockDim.y, tile_x == 0 && tile_y == 0);
     bool chi = false;
     T cr = 0, cax = 0, cay = 0;   // kept for the solid-node sums (converted there)
     if (inside)
@@ -71,7 +68,47 @@ __global__ void __launch_bounds__(256, MINB) vp_mrt_step(const StepParams p)
 #pragma unroll
     for (int k = 0; k < NPART - 1; ++k) part[k] = 0.0;
     if (chi) solid_node_sums<P>(p, fin, i, j, (double)cr, (double)cax, (double)cay, part);
-    tile_reduce(p, range, blockIdx.x, blockIdx.y, blockDim.x, blockDim.y, chi, part, red, &s_last);
+    tile_reduce(p, range, tile_x, tile_y, blockDim.x, blockDim.y, chi, part, red, s_last);
+}
+
+// MINB: blocks of 256 threads per SM the register budget is sized for
+// (4: 64 registers, 5: 48, 6: 40).
+template <int P, int MINB>
+__global__ void __launch_bounds__(256, MINB) vp_mrt_step(const StepParams p)
+{
+    __shared__ double red[8][NPART];
+    __shared__ int s_last;
+    scalar_tile<P>(p, blockIdx.x, blockIdx.y, red, &s_last);
+}
+
+// Every member of a batch in one launch: block b runs tile b of the
+// concatenated tile lists; its member is found in the tile prefix and its
+// step parameters are staged in shared memory.
+template <int P>
+__global__ void __launch_bounds__(256, 5) vp_mrt_step_batch(const BatchLaunch bl)
+{
+    __shared__ double red[8][NPART];
+    __shared__ int s_last;
+    __shared__ __align__(16) StepParams sp;
+    __shared__ int s_member, s_local;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        int lo = 0, hi = bl.n - 1;   // last member whose first tile is <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bl.tile_start[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        s_member = lo;
+        s_local = (int)blockIdx.x - bl.tile_start[lo];
+    }
+    __syncthreads();
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(bl.params + s_member);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&sp);
+    for (int k = tid; k < (int)(sizeof(StepParams) / 4); k += blockDim.x * blockDim.y) dst[k] = src[k];
+    __syncthreads();
+    const int ntx = (sp.nx + blockDim.x - 1) / blockDim.x;
+    scalar_tile<P>(sp, s_local % ntx, s_local / ntx, red, &s_last);
 }
 
 // ---- equilibrium initialisation (Eq. 11) -------------------------------
@@ -159,6 +196,17 @@ long long max_reduction_blocks(int nx, int ny, double radius, int present, int b
     if (tx > gx) tx = gx;
     if (ty > gy) ty = gy;
     return tx * ty;
+}
+
+cudaError_t launch_step_batch(int precision, const BatchLaunch &bl, int total_tiles, int bx, int by,
+                              cudaStream_t stream)
+{
+    dim3 block(bx, by);
+    if (precision == VPLBM_F32_DEV) vp_mrt_step_batch<VPLBM_F32_DEV><<<total_tiles, block, 0, stream>>>(bl);
+    else if (precision == VPLBM_F16_DEV) vp_mrt_step_batch<VPLBM_F16_DEV><<<total_tiles, block, 0, stream>>>(bl);
+    else if (precision == VPLBM_F64) vp_mrt_step_batch<VPLBM_F64><<<total_tiles, block, 0, stream>>>(bl);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb)

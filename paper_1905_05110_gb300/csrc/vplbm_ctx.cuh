@@ -28,7 +28,7 @@ struct vplbm_ctx {
     double *prof = nullptr;
     void *owned = nullptr;                // single allocation when the library owns memory
     long long nstep = 0;
-    int kernel = vplbm::KERNEL_SCALAR;           // KERNEL_SCALAR / KERNEL_PAIR / KERNEL_TMA
+    int kernel = vplbm::KERNEL_SCALAR;    // KERNEL_SCALAR / _48 / _40 / KERNEL_TMA
     int bx = 128, by = 2;
     cudaGraphExec_t graph = nullptr;
     int graph_kernel = -1, graph_bx = -1, graph_by = -1;
@@ -38,7 +38,6 @@ struct vplbm_ctx {
     bool tma_ok = false;
     CUtensorMap tmap[2];
     int tma_grid = 0;
-    int stream_grid = 0;                  // persistent grid of the streaming kernel
 };
 
 namespace vplbm {

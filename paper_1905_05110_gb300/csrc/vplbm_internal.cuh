@@ -55,15 +55,14 @@ struct DevBody {
 // th, n_solid, (pad).
 constexpr int NPART = 8;
 
-// Host-folded constants of the paired FP32x2 kernel (uniform over a run):
-// 1 - s_k, the (1 - s_k/2) factors of Eq. (17) with the signs and integer
-// factors of the closed-form M F folded in, and g/2.
+// Host-folded relaxation factors (uniform over a run): 1 - s_k, the
+// (1 - s_k/2) factors of Eq. (17) with the signs and integer factors of the
+// closed-form M F folded in, and g/2.
 template <typename R> struct FoldedConsts {
     R hgx, hgy;
     R om1, om2, om4, om6, om7, om8;
     R h1x6, mh2x6, mh4, mh6, h7x2, h8;
 };
-using PairConsts = FoldedConsts<float>;
 
 // Fill the folded factors from the relaxation rates and fluid acceleration.
 template <typename R> inline void fold_consts(FoldedConsts<R> &k, const double *sv, double gx, double gy)
@@ -90,7 +89,7 @@ struct StepParams {
     // runs on the FP64 pipe, which is narrow on GB300)
     float sf[NQ];
     float rho0f, gxf, gyf, pen_kf, r2f;
-    PairConsts pc;                // FP32 folded factors
+    FoldedConsts<float> pc;       // FP32 folded factors
     FoldedConsts<double> pcd;     // FP64 folded factors
     int bc[4];
     double wall_u0[4][2];
@@ -162,37 +161,19 @@ __host__ __device__ inline void derive_pose(BodyState &s, int present, double ra
     s.xf = (float)(s.q[0] - fx); s.yf = (float)(s.q[1] - fy);
 }
 
-// Step kernels a context can launch.
-enum { KERNEL_SCALAR = 0, KERNEL_PAIR = 1, KERNEL_TMA = 2, KERNEL_ASYNC = 3, KERNEL_PIPE = 4, KERNEL_STREAM = 5,
-       KERNEL_SCALAR_48 = 6, KERNEL_SCALAR_40 = 7 };
+// Step kernels a context can launch: the scalar kernel with the register
+// budget of 4 / 5 / 6 blocks of 256 threads per SM, and the TMA-staged one.
+enum { KERNEL_SCALAR = 0, KERNEL_SCALAR_48 = 1, KERNEL_SCALAR_40 = 2, KERNEL_TMA = 3 };
 
-// Streaming paired step (step_stream.cu): persistent grid, block (bx, by)
-// walks items of 2*bx x by nodes with the next item prefetched.
-cudaError_t stream_prepare(int precision, int bx, int by, int *blocks_per_sm);
-cudaError_t launch_step_stream(int precision, const StepParams &p, int bx, int by, int grid, cudaStream_t stream);
-
-// Warp-pipelined paired step (step_pipe.cu): block (bx, 1), bx in {128, 256},
-// covers 64 x (bx / 32 * pipe_rows_per_warp()) nodes.
-int pipe_rows_per_warp();
-cudaError_t pipe_prepare(int precision, int bx);
-cudaError_t launch_step_pipe(int precision, const StepParams &p, int bx, cudaStream_t stream);
-
-// Batched launch of the warp-pipelined step over many lattices.
+// Batched launch of the scalar step over many lattices.
 struct BatchLaunch {
     const StepParams *params;   // one per member (device), for this step's parity
     const int *tile_start;      // n + 1 prefix sums of the members' tile counts (device)
     int n;
 };
-cudaError_t pipe_batch_prepare(int precision, int bx);
-cudaError_t launch_step_pipe_batch(int precision, const BatchLaunch &bl, int total_tiles, int bx, cudaStream_t stream);
-
-// Software-pipelined step (step_async.cu): block (bx, by) covers
-// bx x (by * async_rows_per_thread()) nodes.
-int async_rows_per_thread();
-cudaError_t launch_step_async(int precision, const StepParams &p, int bx, int by, cudaStream_t stream);
-
-// Paired FP32x2 step (step_pair.cu): block (bx, by) covers 2*bx x by nodes.
-cudaError_t launch_step_pair(int precision, const StepParams &p, int bx, int by, cudaStream_t stream);
+// Batched scalar step (step_kernels.cu): tiles of bx x by nodes.
+cudaError_t launch_step_batch(int precision, const BatchLaunch &bl, int total_tiles, int bx, int by,
+                              cudaStream_t stream);
 
 // Launchers (step_kernels.cu).  All are asynchronous on `stream`.
 cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb = 4);

@@ -27,28 +27,28 @@ def _members():
     return out
 
 
-@pytest.mark.parametrize("precision", ["f32", "f16"])
+@pytest.mark.parametrize("precision", ["f32", "f16", "f64"])
 def test_batch_members_match_standalone_runs(precision):
     import paper_1905_05110_gb300 as vp
     probs = _members()
     batch = vp.Batch(probs, precision=precision, history_capacity=256)
-    batch.set_launch(256)
+    batch.set_launch(256, 1)
     batch.init_from_problems()
     batch.step(70)   # two graphs of 32 and 6 single launches
     batch.sync()
     for k, p in enumerate(probs):
         alone = vp.Simulation(p, precision=precision, history_capacity=256)
-        alone.set_launch("pipe", 256, 1)   # the same tile code as the batched kernel
+        alone.set_launch("scalar48", 256, 1)   # the same tile code and budget as the batched kernel
         alone.init_from_problem()
         alone.step(70)
         m = batch.members[k]
         assert m.nstep == 70
-        assert dev_err(m.populations(), alone.populations()) < 1e-6
+        assert dev_err(m.populations(), alone.populations()) < (1e-6 if precision == "f32" else 1e-3)
         hm, ha = m.history(), alone.history()
         assert np.array_equal(hm[:, REC["n_solid"]], ha[:, REC["n_solid"]])
         assert rel_err(hm[:, REC["fy"]], ha[:, REC["fy"]]) < 1e-4
         alone.close()
-    assert batch.launch()[1] == 70
+    assert batch.launch()[2] == 70
     batch.close()
 
 
@@ -79,7 +79,7 @@ def test_batch_rejects_members_out_of_step_and_autotunes():
         batch.step(1)
     assert ei.value.status == 1
     batch.init_from_problems()
-    bx = batch.autotune(4)
-    assert bx in (128, 256)
+    shape = batch.autotune(4)
+    assert shape in ((256, 1), (128, 1), (128, 2), (64, 2))
     batch.sync()
     batch.close()

@@ -172,12 +172,8 @@ SCALAR_SHAPES = [(128, 2), (256, 1), (64, 4), (32, 8), (128, 1), (64, 2), (32, 4
 
 def vp_shapes():
     """Every kernel and block shape the runtime can launch."""
-    return ([("tma", 0, 0), ("pipe", 256, 1), ("pipe", 128, 1)]
-            + [("stream", bx, by) for bx, by in SCALAR_SHAPES]
-            + [("async", bx, by) for bx, by in SCALAR_SHAPES]
-            + [("pair", bx, by) for bx, by in SCALAR_SHAPES]
+    return ([("tma", 0, 0)] + [("scalar48", bx, by) for bx, by in SCALAR_SHAPES]
             + [("scalar", bx, by) for bx, by in SCALAR_SHAPES]
-            + [("scalar48", bx, by) for bx, by in SCALAR_SHAPES]
             + [("scalar40", bx, by) for bx, by in SCALAR_SHAPES])
 
 
@@ -369,90 +365,3 @@ def test_tma_bounded_wait_reports_timeout_and_context_survives():
     ref.init_from_problem()
     ref.step(40)
     assert np.array_equal(g.populations(), ref.populations())
-
-
-@pytest.mark.parametrize("bcs", BC_SETS)
-@pytest.mark.parametrize("precision", ["f32", "f16"])
-@pytest.mark.parametrize("size", [(98, 45), (66, 3), (6, 5)])
-def test_pair_kernel_steps_from_random_state(bcs, precision, size):
-    # the paired FP32x2 kernel, ragged against its 2*bx x by blocks, with the
-    # warp-edge lanes and every boundary set
-    nx, ny = size
-    body = moving_bodies(nx, ny)["free"] if min(nx, ny) > 20 else None
-    p = _box(nx, ny, bcs, seed=nx * ny, body=body)
-    f0 = wl.random_populations(nx, ny, seed=13, amp=0.03, u_amp=0.05)
-    g, _ = make_pair(p, precision, init=None, f0=f0)
-    f0 = g.populations()
-    for bx, by in ((32, 4), (64, 4), (128, 1)):
-        gpu, orc = make_pair(p, precision, f0=f0)
-        gpu.set_launch("pair", bx, by)
-        for n in (1, 2):
-            gpu.step(1)
-            orc.step(1)
-            tol = ONE_STEP_TOL[precision] * (3 if n == 2 else 1)
-            assert dev_err(gpu.populations(), orc.populations()) < tol, (bx, by, n)
-
-
-@pytest.mark.parametrize("bcs", BC_SETS)
-@pytest.mark.parametrize("precision", ["f32", "f16"])
-@pytest.mark.parametrize("size", [(99, 45), (67, 3), (5, 7)])
-def test_async_kernel_steps_from_random_state(bcs, precision, size):
-    # the cp.async-pipelined kernel, ragged against its bx x 4*by tiles
-    nx, ny = size
-    body = moving_bodies(nx, ny)["free"] if min(nx, ny) > 20 else None
-    p = _box(nx, ny, bcs, seed=nx * ny + 1, body=body)
-    f0 = wl.random_populations(nx, ny, seed=14, amp=0.03, u_amp=0.05)
-    g, _ = make_pair(p, precision, init=None, f0=f0)
-    f0 = g.populations()
-    for bx, by in ((32, 4), (128, 2), (256, 1)):
-        gpu, orc = make_pair(p, precision, f0=f0)
-        gpu.set_launch("async", bx, by)
-        for n in (1, 2):
-            gpu.step(1)
-            orc.step(1)
-            tol = ONE_STEP_TOL[precision] * (3 if n == 2 else 1)
-            assert dev_err(gpu.populations(), orc.populations()) < tol, (bx, by, n)
-
-
-@pytest.mark.parametrize("bcs", BC_SETS)
-@pytest.mark.parametrize("precision", ["f32", "f16"])
-@pytest.mark.parametrize("size", [(130, 45), (66, 3), (6, 37), (200, 70)])
-def test_pipe_kernel_steps_from_random_state(bcs, precision, size):
-    # the warp-pipelined paired kernel: ragged strips and row blocks, the
-    # strip halos at both ends, every boundary set, a body in the larger boxes
-    nx, ny = size
-    body = moving_bodies(nx, ny)["free"] if min(nx, ny) > 20 else None
-    p = _box(nx, ny, bcs, seed=nx * ny + 2, body=body)
-    f0 = wl.random_populations(nx, ny, seed=15, amp=0.03, u_amp=0.05)
-    g, _ = make_pair(p, precision, init=None, f0=f0)
-    f0 = g.populations()
-    for bx in (256, 128):
-        gpu, orc = make_pair(p, precision, f0=f0)
-        gpu.set_launch("pipe", bx, 1)
-        for n in (1, 2):
-            gpu.step(1)
-            orc.step(1)
-            tol = ONE_STEP_TOL[precision] * (3 if n == 2 else 1)
-            assert dev_err(gpu.populations(), orc.populations()) < tol, (bx, n)
-
-
-@pytest.mark.parametrize("bcs", BC_SETS)
-@pytest.mark.parametrize("precision", ["f32", "f16"])
-@pytest.mark.parametrize("size", [(130, 45), (66, 3), (6, 37), (262, 70)])
-def test_stream_kernel_steps_from_random_state(bcs, precision, size):
-    # the streaming paired kernel: persistent item runs crossing strips,
-    # warp-edge lanes, every boundary set, a body in the larger boxes
-    nx, ny = size
-    body = moving_bodies(nx, ny)["free"] if min(nx, ny) > 20 else None
-    p = _box(nx, ny, bcs, seed=nx * ny + 3, body=body)
-    f0 = wl.random_populations(nx, ny, seed=16, amp=0.03, u_amp=0.05)
-    g, _ = make_pair(p, precision, init=None, f0=f0)
-    f0 = g.populations()
-    for bx, by in ((64, 4), (32, 8), (128, 1)):
-        gpu, orc = make_pair(p, precision, f0=f0)
-        gpu.set_launch("stream", bx, by)
-        for n in (1, 2):
-            gpu.step(1)
-            orc.step(1)
-            tol = ONE_STEP_TOL[precision] * (3 if n == 2 else 1)
-            assert dev_err(gpu.populations(), orc.populations()) < tol, (bx, by, n)
