@@ -73,11 +73,18 @@ __device__ __forceinline__ void scalar_tile(const StepParams &p, int tile_x, int
 
 // MINB: blocks of 256 threads per SM the register budget is sized for
 // (4: 64 registers, 5: 48, 6: 40).
+//
+// Launched with programmatic dependent launch: every block lets the next
+// step's grid start launching at once, and waits (in hardware) until the
+// previous step's grid has completed and its writes are visible before it
+// reads anything, so the next launch overlaps the end of this one.
 template <int P, int MINB>
 __global__ void __launch_bounds__(256, MINB) vp_mrt_step(const StepParams p)
 {
     __shared__ double red[8][NPART];
     __shared__ int s_last;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     scalar_tile<P>(p, blockIdx.x, blockIdx.y, red, &s_last);
 }
 
@@ -177,12 +184,19 @@ __global__ void fields_kernel(const StepParams p, double *rho_o, double *ux_o, d
 template <int P>
 cudaError_t launch_step_t(const StepParams &p, int bx, int by, int minb, cudaStream_t stream)
 {
-    dim3 block(bx, by);
-    dim3 grid((p.nx + bx - 1) / bx, (p.ny + by - 1) / by);
-    if (minb == 6) vp_mrt_step<P, 6><<<grid, block, 0, stream>>>(p);
-    else if (minb == 5) vp_mrt_step<P, 5><<<grid, block, 0, stream>>>(p);
-    else vp_mrt_step<P, 4><<<grid, block, 0, stream>>>(p);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.nx + bx - 1) / bx, (p.ny + by - 1) / by);
+    cfg.blockDim = dim3(bx, by);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (minb == 6) return cudaLaunchKernelEx(&cfg, vp_mrt_step<P, 6>, p);
+    if (minb == 5) return cudaLaunchKernelEx(&cfg, vp_mrt_step<P, 5>, p);
+    return cudaLaunchKernelEx(&cfg, vp_mrt_step<P, 4>, p);
 }
 
 }  // namespace
