@@ -245,7 +245,11 @@ def run_ours(args, rank, world, local_rank):
     sim = vp.Simulation(p, precision=prec, history_capacity=max(1024, args.steps + args.warmup + 64),
                         stream=stream)
     sim.init_from_problem()
-    if not args.no_autotune:
+    if args.launch:
+        kern, shape = args.launch.split(":")
+        bx, by = (int(v) for v in shape.split("x"))
+        sim.set_launch(kern, bx, by)
+    elif not args.no_autotune:
         sim.autotune(20)
     launch = sim.launch()
     sim.step(args.warmup)
@@ -451,6 +455,7 @@ def main():
     ap.add_argument("--workload", default="oscillating_2048x1024")
     ap.add_argument("--precision", default="f32", choices=["f32", "f16", "f64"])
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch", default="", help="fixed step kernel and block, e.g. scalar40:256x1 (no autotune)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

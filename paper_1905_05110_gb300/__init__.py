@@ -529,7 +529,7 @@ class Simulation:
         return vplbm_get_body(self.ctx)[2]
 
     def set_launch(self, kernel, bx=0, by=0):
-        """kernel: "scalar", "pair" or "tma" (or its number)."""
+        """kernel: "scalar" (64-register budget), "scalar48", "scalar40" or "tma" (or its number)."""
         k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         vplbm_set_launch(self.ctx, k, bx, by)
 
