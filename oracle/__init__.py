@@ -52,7 +52,11 @@ class Lattice(C.Structure):
                 ("s", C.c_double * Q), ("eta", C.c_double), ("rho0", C.c_double),
                 ("gx", C.c_double), ("gy", C.c_double),
                 ("bc_kind", C.c_int * 4), ("bc_u", (C.c_double * 2) * 4),
-                ("bc_ux", C.POINTER(C.c_double) * 4), ("bc_uy", C.POINTER(C.c_double) * 4)]
+                ("bc_ux", C.POINTER(C.c_double) * 4), ("bc_uy", C.POINTER(C.c_double) * 4),
+                ("collision", C.c_int)]
+
+
+COLLISIONS = {"mrt": 0, "bgk": 1}
 
 
 class Body(C.Structure):
@@ -102,6 +106,7 @@ def lib():
             L.orc_moment_equilibrium.argtypes = [C.c_double, C.c_double, C.c_double, _D]
             L.orc_guo_forcing.argtypes = [C.c_double] * 4 + [_D]
             L.orc_collide.argtypes = [_D, _D] + [C.c_double] * 5 + [_D]
+            L.orc_collide_bgk.argtypes = [_D] + [C.c_double] * 6 + [_D]
             L.orc_penalized_velocity.argtypes = ([C.c_double] * 3 + [C.c_int]
                                                  + [C.c_double] * 5 + [_D])
             L.orc_body_advance.argtypes = [C.POINTER(Body), C.c_longlong, C.c_double,
@@ -128,6 +133,7 @@ def make_lattice(p: dict, keep: list) -> Lattice:
         lat.s[k] = float(p["s"][k])
     lat.eta = float(p.get("eta", 1e-3))
     lat.rho0 = float(p.get("rho0", 1.0))
+    lat.collision = COLLISIONS[p.get("collision", "mrt")]
     g = p.get("g_fluid", (0.0, 0.0))
     lat.gx, lat.gy = float(g[0]), float(g[1])
     bcs = p["bc"]
@@ -303,6 +309,14 @@ def collide(f, s, rho, ux, uy, gx, gy) -> np.ndarray:
     s = _f64(s)
     out = np.zeros(Q)
     lib().orc_collide(_dptr(f), _dptr(s), rho, ux, uy, gx, gy, _dptr(out))
+    return out
+
+
+def collide_bgk(f, omega, rho, ux, uy, gx, gy) -> np.ndarray:
+    """BGK collision of Sec. 2.1 with the Eq. (12) forcing (rate omega = 1/tau)."""
+    f = _f64(f)
+    out = np.zeros(Q)
+    lib().orc_collide_bgk(_dptr(f), omega, rho, ux, uy, gx, gy, _dptr(out))
     return out
 
 

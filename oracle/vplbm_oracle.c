@@ -15,6 +15,8 @@
  *      Eqs. (20)-(22);
  *   3. MRT collision with a source term (Eqs. 8, 17), moments by the
  *      matrix M of Eq. (15), equilibria of Eq. (14), forcing of Eq. (12);
+ *      or, when the lattice asks for it, the single-relaxation-time (BGK)
+ *      operator of Sec. 2.1 in velocity space with the Eq. (12) forcing;
  *   4. force and torque on the body, then the rigid-body update of
  *      Eqs. (23)-(24) by fourth-order Runge-Kutta (Algorithm 1, step 3).
  * Matrix-vector products are written as plain loops over the 9x9 matrices;
@@ -131,6 +133,7 @@ static void setup_constants(void)
 enum { ORC_PERIODIC = 0, ORC_NOSLIP = 1, ORC_VELOCITY = 2, ORC_ZEROGRAD = 3 };
 enum { ORC_WEST = 0, ORC_EAST = 1, ORC_SOUTH = 2, ORC_NORTH = 3 };
 enum { ORC_FIXED = 0, ORC_IMPOSED = 1, ORC_FREE = 2 };
+enum { ORC_MRT = 0, ORC_BGK = 1 };
 
 typedef struct {
     int nx, ny;
@@ -142,6 +145,7 @@ typedef struct {
     double bc_u[4][2];    /* uniform wall velocity per edge */
     const double *bc_ux[4]; /* optional per-node wall velocity, edge length */
     const double *bc_uy[4];
+    int collision;        /* ORC_MRT (Eq. 17) or ORC_BGK (Sec. 2.1, rate s[7]) */
 } orc_lattice;
 
 typedef struct {
@@ -275,6 +279,20 @@ static void collide(const double f[Q], const double s[Q], double rho,
         ft[a] = 0.0;
         for (int r = 0; r < Q; ++r) ft[a] += MINV[a][r] * ms[r];
     }
+}
+
+/* Single-relaxation-time (BGK) collision of Sec. 2.1 with the forcing
+ * term of Eq. (12) as printed there, (1 - 1/(2 tau)) prefactor included:
+ *   f~ = f - (f - f_eq) / tau + (1 - 1/(2 tau)) F,   1/tau = omega.
+ * Written in velocity space, independent of M. */
+static void collide_bgk(const double f[Q], double omega, double rho,
+                        double ux, double uy, double Gx, double Gy, double ft[Q])
+{
+    double feq[Q], F[Q];
+    equilibrium(rho, ux, uy, feq);
+    guo_forcing(ux, uy, Gx, Gy, F);
+    for (int a = 0; a < Q; ++a)
+        ft[a] = f[a] - omega * (f[a] - feq[a]) + (1.0 - 0.5 * omega) * F[a];
 }
 
 /* ---- streaming with boundary rules (Eq. 18) ------------------------- */
@@ -492,7 +510,10 @@ static void one_step(orc_sim *s)
             node_macro(s, i, j, &ns);
             double Gx = ns.rho * (s->lat.gx + ns.ax);
             double Gy = ns.rho * (s->lat.gy + ns.ay);
-            collide(ns.f, s->lat.s, ns.rho, ns.ux, ns.uy, Gx, Gy, ft);
+            if (s->lat.collision == ORC_BGK)
+                collide_bgk(ns.f, s->lat.s[7], ns.rho, ns.ux, ns.uy, Gx, Gy, ft);
+            else
+                collide(ns.f, s->lat.s, ns.rho, ns.ux, ns.uy, Gx, Gy, ft);
             for (int a = 0; a < Q; ++a) s->fn[((size_t)a * ny + j) * nx + i] = ft[a];
             if (ns.chi) {
                 /* reaction of the penalization force on the body */
@@ -583,6 +604,13 @@ void orc_collide(const double f[Q], const double s[Q], double rho, double ux,
 {
     setup_constants();
     collide(f, s, rho, ux, uy, Gx, Gy, ft);
+}
+
+void orc_collide_bgk(const double f[Q], double omega, double rho, double ux,
+                     double uy, double Gx, double Gy, double ft[Q])
+{
+    setup_constants();
+    collide_bgk(f, omega, rho, ux, uy, Gx, Gy, ft);
 }
 
 void orc_penalized_velocity(double rho, double jx, double jy, int chi, double usx,
@@ -741,6 +769,7 @@ int orc_adjoint(orc_sim *s, const orc_adjoint_desc *d, double *grad, double out_
     const int nx = s->lat.nx, ny = s->lat.ny;
     const long long N = d->nsteps;
     if (s->body.present && s->body.motion == ORC_FREE) return -1;
+    if (s->lat.collision != ORC_MRT) return -1;
     if (N < 1 || d->w0 < 0 || d->w0 >= N || s->hist_cap < s->step + N) return -1;
     const size_t nf = (size_t)Q * nx * ny;
     const long long step0 = s->step;

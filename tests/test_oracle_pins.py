@@ -316,6 +316,87 @@ def test_poiseuille_bounce_back_exact():
     assert np.max(np.abs(uy)) < 1e-15
 
 
+@pytest.mark.parametrize("seed", range(5))
+def test_bgk_equals_mrt_with_uniform_rates(seed):
+    # The BGK collision of Sec. 2.1 (velocity space, Eq. 12 forcing with its
+    # (1 - 1/(2 tau)) prefactor) is the MRT collision of Eq. (17) with
+    # S = I / tau: two different formulations of the same operator.
+    rng = np.random.default_rng(100 + seed)
+    f = oracle.equilibrium(1.01, -0.02, 0.04) * (1 + 0.08 * rng.uniform(-1, 1, 9))
+    omega = rng.uniform(0.55, 1.95)
+    rho = 1.0 + rng.uniform(-0.05, 0.05)
+    ux, uy, gx, gy = rng.uniform(-0.05, 0.05, size=4)
+    bgk = oracle.collide_bgk(f, omega, rho, ux, uy, gx, gy)
+    mrt = oracle.collide(f, np.full(9, omega), rho, ux, uy, gx, gy)
+    assert np.allclose(bgk, mrt, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_bgk_conserves_mass_and_adds_force(seed):
+    rng = np.random.default_rng(200 + seed)
+    c, _, _, _ = oracle.constants()
+    f = oracle.equilibrium(0.98, 0.01, 0.03) * (1 + 0.05 * rng.uniform(-1, 1, 9))
+    omega = rng.uniform(0.55, 1.95)
+    gx, gy = rng.uniform(-1e-3, 1e-3, size=2)
+    rho = f.sum()
+    j = c.T @ f
+    ux, uy = (j + 0.5 * np.array([gx, gy])) / rho
+    out = oracle.collide_bgk(f, omega, rho, ux, uy, gx, gy)
+    assert abs(out.sum() - rho) < 1e-15
+    assert np.allclose(c.T @ out - j, [gx, gy], atol=1e-16)
+
+
+def test_bgk_poiseuille_bounce_back_exact():
+    # Single-relaxation-time counterpart of the MRT Poiseuille pin: with
+    # half-way bounce-back walls the steady body-force profile is the exact
+    # parabola when (tau - 1/2)^2 = 3/16.  A missing or doubled forcing
+    # prefactor, or a wrong rate, moves the profile off it.
+    tau = 0.5 + math.sqrt(3.0) / 4.0
+    nu = (tau - 0.5) / 3.0
+    ny, g = 12, 1e-6
+    p = wl.periodic_box(3, ny, tau=tau, g_fluid=(g, 0.0))
+    p["collision"] = "bgk"
+    p["bc"]["south"] = {"kind": "noslip", "u": (0.0, 0.0)}
+    p["bc"]["north"] = {"kind": "noslip", "u": (0.0, 0.0)}
+    sim = oracle.OracleSim(p)
+    sim.init_equilibrium()
+    sim.step(6000)
+    _, ux, uy = sim.fields()
+    y = np.arange(ny, dtype=float)
+    exact = g / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    assert np.max(np.abs(ux[:, 1] - exact)) < 1e-9 * np.max(exact)
+    # and away from 3/16 it is not exact (the pin has teeth)
+    p2 = dict(p)
+    p2["s"] = [1.0 / 0.8] * 9
+    sim2 = oracle.OracleSim(p2)
+    sim2.init_equilibrium()
+    sim2.step(6000)
+    _, ux2, _ = sim2.fields()
+    exact2 = g / (2 * (0.3 / 3.0)) * (y + 0.5) * (ny - 0.5 - y)
+    assert np.max(np.abs(ux2[:, 1] - exact2)) > 1e-4 * np.max(exact2)
+
+
+def test_bgk_run_equals_mrt_run_with_uniform_rates():
+    # Whole steps (every boundary kind, a moving body, penalization): the
+    # BGK path and the MRT path with S = I / tau give the same state.
+    tau = 0.7
+    body = {"radius": 4.5, "x": 20.3, "y": 11.6, "motion": "imposed", "axis": 1,
+            "amp": 1.5, "freq": 0.01, "u_ref": 0.04, "d_ref": 9.0}
+    base = wl.mixed_bc_box(41, 23, seed=3, west="velocity", east="zerograd", south="noslip",
+                           north="velocity", tau=tau, body=body, rates=[1.0 / tau] * 9)
+    sims = []
+    for coll in ("bgk", "mrt"):
+        p = dict(base)
+        p["collision"] = coll
+        sim = oracle.OracleSim(p, hist_cap=64)
+        sim.set_populations(wl.random_populations(41, 23, seed=5))
+        sim.step(30)
+        sims.append(sim)
+    assert np.max(np.abs(sims[0].populations() - sims[1].populations())) < 1e-14
+    hb, hm = sims[0].history(), sims[1].history()
+    assert np.allclose(hb, hm, rtol=1e-12, atol=1e-15)
+
+
 def test_rk4_free_fall_is_exact():
     body = {"radius": 1.0, "x": 0, "y": 0, "motion": "free", "mass": 3.0, "inertia": 5.0,
             "f_ext": (0.2, -0.5, 0.1), "dof_mask": 7}
