@@ -63,6 +63,7 @@
 static int C[Q][2];      /* Eq. (10) */
 static double W[Q];      /* Eq. (13) */
 static int OPP[Q];       /* index of -c_a */
+static int MIRY[Q];      /* index of (c_ax, -c_ay): mirror image about a wall of constant y */
 /* Eq. (15): rows rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy */
 static const double M[Q][Q] = {
     { 1,  1,  1,  1,  1,  1,  1,  1,  1},
@@ -101,6 +102,9 @@ static void setup_constants(void)
     for (int a = 0; a < Q; ++a)
         for (int b = 0; b < Q; ++b)
             if (C[b][0] == -C[a][0] && C[b][1] == -C[a][1]) OPP[a] = b;
+    for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < Q; ++b)
+            if (C[b][0] == C[a][0] && C[b][1] == -C[a][1]) MIRY[a] = b;
     /* M^-1 by Gauss-Jordan elimination with partial pivoting. */
     double A[Q][2 * Q];
     for (int r = 0; r < Q; ++r)
@@ -130,7 +134,7 @@ static void setup_constants(void)
 
 /* ---- public descriptors (ctypes mirrors them) ------------------------ */
 
-enum { ORC_PERIODIC = 0, ORC_NOSLIP = 1, ORC_VELOCITY = 2, ORC_ZEROGRAD = 3 };
+enum { ORC_PERIODIC = 0, ORC_NOSLIP = 1, ORC_VELOCITY = 2, ORC_ZEROGRAD = 3, ORC_SYMMETRY = 4 };
 enum { ORC_WEST = 0, ORC_EAST = 1, ORC_SOUTH = 2, ORC_NORTH = 3 };
 enum { ORC_FIXED = 0, ORC_IMPOSED = 1, ORC_FREE = 2 };
 enum { ORC_MRT = 0, ORC_BGK = 1 };
@@ -309,6 +313,14 @@ static double pulled(const orc_sim *s, int a, int i, int j)
         int kind = s->lat.bc_kind[side];
         if (kind == ORC_PERIODIC) {
             sj = (sj + ny) % ny;
+        } else if (kind == ORC_SYMMETRY) {
+            /* specular reflection at the half-way wall (u.n = 0, no shear
+             * stress): the population left node (i - c_ax, j) in the
+             * mirrored direction; at a corner whose x edge is not periodic
+             * the node's own mirrored population is taken */
+            int mi = i - C[a][0];
+            if (mi < 0 || mi >= nx) mi = s->lat.bc_kind[ORC_WEST] == ORC_PERIODIC ? (mi + nx) % nx : i;
+            return FT(MIRY[a], mi, j);
         } else {
             /* half-way bounce-back at y = -1/2 or y = ny - 1/2 */
             double val = FT(OPP[a], i, j);
@@ -422,6 +434,7 @@ orc_sim *orc_create(const orc_lattice *lat, const orc_body *body, long long hist
 {
     setup_constants();
     if (lat->nx < 2 || lat->ny < 2) return NULL;
+    if (lat->bc_kind[ORC_WEST] == ORC_SYMMETRY || lat->bc_kind[ORC_EAST] == ORC_SYMMETRY) return NULL;   /* y walls only */
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     if (!s) return NULL;
     s->lat = *lat;
@@ -661,6 +674,11 @@ static void pull_source(const orc_sim *s, int a, int i, int j, int *b, int *si_o
         int side = sj < 0 ? ORC_SOUTH : ORC_NORTH;
         if (s->lat.bc_kind[side] == ORC_PERIODIC) {
             sj = (sj + ny) % ny;
+        } else if (s->lat.bc_kind[side] == ORC_SYMMETRY) {
+            int mi = i - C[a][0];
+            if (mi < 0 || mi >= nx) mi = s->lat.bc_kind[ORC_WEST] == ORC_PERIODIC ? (mi + nx) % nx : i;
+            *b = MIRY[a]; *si_out = mi; *sj_out = j;
+            return;
         } else {
             *b = OPP[a]; *si_out = i; *sj_out = j;
             if (s->lat.bc_kind[side] == ORC_VELOCITY) *wall = side;

@@ -397,6 +397,76 @@ def test_bgk_run_equals_mrt_run_with_uniform_rates():
     assert np.allclose(hb, hm, rtol=1e-12, atol=1e-15)
 
 
+def _symmetry_channel(nx, ny, seed, g=(0.0, 0.0)):
+    p = wl.periodic_box(nx, ny, g_fluid=g, rates=wl.random_rates(seed))
+    p["bc"]["south"] = {"kind": "symmetry"}
+    p["bc"]["north"] = {"kind": "symmetry"}
+    return p
+
+
+def test_symmetry_walls_keep_a_uniform_stream():
+    # Free-slip (specular) walls of Sec. 3.1's oscillating-cylinder setup
+    # exert no shear: a uniform stream along them is an exact steady state
+    # (bounce-back walls would brake it).
+    p = _symmetry_channel(9, 7, seed=3)
+    sim = oracle.OracleSim(p)
+    shape = (7, 9)
+    sim.init_equilibrium(np.ones(shape), np.full(shape, 0.05), np.zeros(shape))
+    f0 = sim.populations()
+    sim.step(50)
+    assert np.max(np.abs(sim.populations() - f0)) < 1e-15
+    q = wl.periodic_box(9, 7, rates=wl.random_rates(3))
+    q["bc"]["south"] = {"kind": "noslip", "u": (0.0, 0.0)}
+    q["bc"]["north"] = {"kind": "noslip", "u": (0.0, 0.0)}
+    ref = oracle.OracleSim(q)
+    ref.init_equilibrium(np.ones(shape), np.full(shape, 0.05), np.zeros(shape))
+    ref.step(50)
+    assert np.max(np.abs(ref.populations() - f0)) > 1e-4
+
+
+def test_symmetry_wall_is_the_mirror_plane_of_a_doubled_periodic_box():
+    # A channel of ny rows between specular walls evolves exactly like the
+    # lower half of a periodic channel of 2 ny rows whose upper half is the
+    # mirror image (c_y -> -c_y about y = ny - 1/2) of the lower one.
+    nx, ny = 11, 6
+    rates = wl.random_rates(8)
+    f0 = wl.random_populations(nx, ny, seed=21, amp=0.04, u_amp=0.05)
+    c, _, _, _ = oracle.constants()
+    mir = [int(np.where((c[:, 0] == c[a, 0]) & (c[:, 1] == -c[a, 1]))[0][0]) for a in range(9)]
+    big = np.zeros((9, 2 * ny, nx))
+    big[:, :ny] = f0
+    big[:, ny:] = f0[mir][:, ::-1, :]
+    a = oracle.OracleSim(_symmetry_channel(nx, ny, seed=8))
+    a.set_populations(f0)
+    b = oracle.OracleSim(wl.periodic_box(nx, 2 * ny, rates=rates))
+    b.set_populations(big)
+    a.step(25)
+    b.step(25)
+    fa, fb = a.populations(), b.populations()
+    assert np.max(np.abs(fa - fb[:, :ny])) < 1e-14
+    assert np.max(np.abs(fb[:, ny:] - fb[mir][:, :ny][:, ::-1])) < 1e-14
+
+
+def test_symmetry_walls_conserve_mass_and_tangential_momentum():
+    # Specular reflection keeps c_x: with periodic x edges the total mass is
+    # constant and the x momentum grows by exactly sum rho g_x per step.
+    nx, ny, gx = 10, 8, 2e-5
+    p = _symmetry_channel(nx, ny, seed=4, g=(gx, 0.0))
+    sim = oracle.OracleSim(p)
+    sim.set_populations(wl.random_populations(nx, ny, seed=2, amp=0.03, u_amp=0.04))
+    c, _, _, _ = oracle.constants()
+    def totals():
+        f = sim.populations()
+        return f.sum(), np.tensordot(c[:, 0], f, axes=1).sum()
+    m0, px0 = totals()
+    for _ in range(5):
+        sim.step(1)
+        m1, px1 = totals()
+        assert abs(m1 - m0) < 1e-12
+        assert abs((px1 - px0) - gx * m1) < 1e-15
+        px0 = px1
+
+
 def test_rk4_free_fall_is_exact():
     body = {"radius": 1.0, "x": 0, "y": 0, "motion": "free", "mass": 3.0, "inertia": 5.0,
             "f_ext": (0.2, -0.5, 0.1), "dof_mask": 7}
