@@ -374,7 +374,7 @@ def run_batched(args, torch, stream):
     half = acc_steps // 2
     cd32, cd64 = h32[half:, 4].mean(), h64[half:, 4].mean()
     b.close()
-    return {"members": len(probs), "nodes": nodes, "mlups": mlups, "steps": k, "block": list(shape),
+    return {"members": len(probs), "nodes": nodes, "mlups": mlups, "steps": k, "launch": list(shape),
             "gbs_algorithmic": 72 * nodes * k / t / 1e9,
             "f64_plain_sequential_mlups": mlups64, "speedup_vs_f64_plain": mlups / mlups64,
             "accuracy_member0_3000_steps": {

@@ -63,11 +63,16 @@ typedef enum { VPLBM_F64 = 0, VPLBM_F32_DEV = 1, VPLBM_F16_DEV = 2 } vplbm_preci
  *  NOSLIP    half-way bounce-back, f_a(x) = f~_abar(x);
  *  VELOCITY  half-way bounce-back of a moving wall,
  *            f_a(x) = f~_abar(x) + 6 w_a rho0 (c_a . u_w);
- *  ZEROGRAD  west/east only: f_a(x) = f~_a(i, j - c_ay) from the edge column.
+ *  ZEROGRAD  west/east only: f_a(x) = f~_a(i, j - c_ay) from the edge column;
+ *  SYMMETRY  south/north only: specular reflection at the half-way wall
+ *            (u.n = 0, no shear stress), f_a(i, j) = f~_a*(i - c_ax, j) with
+ *            a* the mirror image of a (c_ay -> -c_ay); where i - c_ax lies
+ *            outside a non-periodic x edge, f~_a*(i, j).
  * When the source node of a pull lies outside in y, the south/north rule
  * applies, otherwise the west/east rule. */
 typedef enum {
-    VPLBM_BC_PERIODIC = 0, VPLBM_BC_NOSLIP = 1, VPLBM_BC_VELOCITY = 2, VPLBM_BC_ZEROGRAD = 3
+    VPLBM_BC_PERIODIC = 0, VPLBM_BC_NOSLIP = 1, VPLBM_BC_VELOCITY = 2, VPLBM_BC_ZEROGRAD = 3,
+    VPLBM_BC_SYMMETRY = 4
 } vplbm_bc_kind;
 
 enum { VPLBM_WEST = 0, VPLBM_EAST = 1, VPLBM_SOUTH = 2, VPLBM_NORTH = 3 };
@@ -78,6 +83,13 @@ typedef struct {
     const double *ux_profile; /* optional per-node wall velocity along the */
     const double *uy_profile; /* edge (ny values west/east, nx south/north) */
 } vplbm_bc;
+
+/* Collision operator.  MRT: Eq. (17) with the rates s[0..8].  BGK: the
+ * single-relaxation-time operator of Sec. 2.1, f~ = f - (f - f_eq)/tau +
+ * (1 - 1/(2 tau)) F with the equilibrium of Eq. (11) and the forcing of
+ * Eq. (12); it relaxes at 1/tau = s[7] and ignores the other rates.  BGK
+ * runs on the scalar step kernels only (no TMA kernel, no adjoint). */
+typedef enum { VPLBM_COLLISION_MRT = 0, VPLBM_COLLISION_BGK = 1 } vplbm_collision;
 
 /* Lattice and fluid.  s: diagonal of S (Eq. 16) in the moment order of
  * Eq. (15), each in (0, 2); eta > 0: penalization factor (Eq. 2);
@@ -91,6 +103,7 @@ typedef struct {
     double gx, gy;
     vplbm_bc bc[4];           /* indexed by VPLBM_WEST .. VPLBM_NORTH */
     int precision;            /* vplbm_precision */
+    int collision;            /* vplbm_collision (0: MRT) */
 } vplbm_lattice_desc;
 
 typedef enum {
@@ -295,13 +308,27 @@ vplbm_status vplbm_batch_member(vplbm_batch *batch, int k, vplbm_ctx **member);
 vplbm_status vplbm_batch_step(vplbm_batch *batch, long long nsteps);
 /* Wait; returns the first member's latched device error, if any. */
 vplbm_status vplbm_batch_sync(vplbm_batch *batch);
-/* Block (tile) shape of the batched kernel: block_x a multiple of 32,
- * block_x * block_y in {128, 256}; and the number of batched step launches
- * made so far. */
-vplbm_status vplbm_batch_set_launch(vplbm_batch *batch, int block_x, int block_y);
-vplbm_status vplbm_batch_get_launch(vplbm_batch *batch, int *block_x, int *block_y, long long *launches);
-/* Time four block shapes over 2 x steps_per_trial steps each, keep the fastest;
- * the trial steps advance the members (they are real steps). */
+/* How a batch steps its members.  BRANCHES (default): each member's own step
+ * kernel (its launch shape is set through vplbm_batch_member +
+ * vplbm_set_launch), one CUDA-graph branch per member so the members run
+ * concurrently.  TILES: one launch per time step over the concatenated
+ * tiles of every member, shaped by vplbm_batch_set_launch. */
+typedef enum { VPLBM_BATCH_BRANCHES = 0, VPLBM_BATCH_TILES = 1 } vplbm_batch_mode;
+vplbm_status vplbm_batch_set_mode(vplbm_batch *batch, int mode);
+vplbm_status vplbm_batch_get_mode(vplbm_batch *batch, int *mode);
+/* Launch shape of the batched kernel (TILES mode): blocks of block_x x block_y threads
+ * (block_x a multiple of 32, block_x * block_y in {128, 256}), each running
+ * tiles_per_block (1..64) tiles of that shape stacked in y, so the member
+ * lookup and parameter staging of a block are shared by that many tiles.
+ * get_launch also returns the number of batched step launches made so far.
+ * EINVAL for a shape outside these limits or one that needs more reduction
+ * slots than a member allocated (the previous shape is kept). */
+vplbm_status vplbm_batch_set_launch(vplbm_batch *batch, int block_x, int block_y, int tiles_per_block);
+vplbm_status vplbm_batch_get_launch(vplbm_batch *batch, int *block_x, int *block_y, int *tiles_per_block,
+                                   long long *launches);
+/* Time the branch mode and six tile-mode launch shapes over 2 x
+ * steps_per_trial steps each and keep the fastest; the trial steps advance
+ * the members (they are real steps). */
 vplbm_status vplbm_batch_autotune(vplbm_batch *batch, int steps_per_trial);
 
 /* ---- allocation-free stepping --------------------------------------------

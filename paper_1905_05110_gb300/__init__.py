@@ -29,6 +29,7 @@ __all__ = [
     "vplbm_step_noalloc", "BodyState", "vplbm_inject_wait_timeout", "Batch",
     "vplbm_batch_create", "vplbm_batch_destroy", "vplbm_batch_member", "vplbm_batch_step",
     "vplbm_batch_sync", "vplbm_batch_set_launch", "vplbm_batch_get_launch", "vplbm_batch_autotune",
+    "vplbm_batch_set_mode", "vplbm_batch_get_mode",
     "EXPORTED_SYMBOLS", "RECORD_FIELDS",
 ]
 
@@ -37,7 +38,7 @@ STATUS = {0: "VPLBM_OK", 1: "VPLBM_EINVAL", 2: "VPLBM_ENOMEM", 3: "VPLBM_ECUDA",
           4: "VPLBM_ENONFINITE", 5: "VPLBM_ETIMEOUT", 6: "VPLBM_EUNSUPPORTED",
           7: "VPLBM_ERANGE", 8: "VPLBM_EIO"}
 PRECISIONS = {"f64": 0, "f32": 1, "f16": 2}
-BC_KINDS = {"periodic": 0, "noslip": 1, "velocity": 2, "zerograd": 3}
+BC_KINDS = {"periodic": 0, "noslip": 1, "velocity": 2, "zerograd": 3, "symmetry": 4}
 MOTIONS = {"fixed": 0, "imposed": 1, "free": 2}
 SIDES = ("west", "east", "south", "north")
 RECORD_FIELDS = ("t", "fx", "fy", "torque", "cd", "cl", "x", "y", "theta",
@@ -60,7 +61,7 @@ class BC(C.Structure):
 class LatticeDesc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("s", C.c_double * 9), ("eta", C.c_double),
                 ("rho0", C.c_double), ("gx", C.c_double), ("gy", C.c_double),
-                ("bc", BC * 4), ("precision", C.c_int)]
+                ("bc", BC * 4), ("precision", C.c_int), ("collision", C.c_int)]
 
 
 class BodyDesc(C.Structure):
@@ -135,10 +136,12 @@ _SIGS = {
     "vplbm_batch_member": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(_CTX)]),
     "vplbm_batch_step": (C.c_int, [C.c_void_p, C.c_longlong]),
     "vplbm_batch_sync": (C.c_int, [C.c_void_p]),
-    "vplbm_batch_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "vplbm_batch_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "vplbm_batch_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                         C.POINTER(C.c_longlong)]),
+                                         C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     "vplbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int]),
+    "vplbm_batch_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "vplbm_batch_get_mode": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "vplbm_adjoint": (C.c_int, [_CTX, C.c_void_p, _D, _D]),
     "vplbm_last_error": (C.c_char_p, []),
     "vplbm_version": (C.c_char_p, []),
@@ -215,6 +218,7 @@ def lattice_desc(problem: dict, precision: str = "f64", keep: list | None = None
                 keep.append(arr)
                 setattr(d.bc[k], field, _dptr(arr))
     d.precision = PRECISIONS[precision]
+    d.collision = COLLISIONS[problem.get("collision", "mrt")]
     return d
 
 
@@ -325,6 +329,9 @@ def vplbm_get_body(ctx):
     return q, v, int(step.value)
 
 
+COLLISIONS = {"mrt": 0, "bgk": 1}
+BATCH_MODES = {"branches": 0, "tiles": 1}
+BATCH_MODE_NAMES = {v: k for k, v in BATCH_MODES.items()}
 KERNELS = {"scalar": 0, "scalar48": 1, "scalar40": 2, "tma": 3}
 KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
 
@@ -392,14 +399,24 @@ def vplbm_batch_sync(batch):
     _check(load_library().vplbm_batch_sync(batch))
 
 
-def vplbm_batch_set_launch(batch, block_x: int, block_y: int = 1):
-    _check(load_library().vplbm_batch_set_launch(batch, int(block_x), int(block_y)))
+def vplbm_batch_set_launch(batch, block_x: int, block_y: int = 1, tiles_per_block: int = 1):
+    _check(load_library().vplbm_batch_set_launch(batch, int(block_x), int(block_y), int(tiles_per_block)))
 
 
 def vplbm_batch_get_launch(batch):
-    bx, by, n = C.c_int(), C.c_int(), C.c_longlong()
-    _check(load_library().vplbm_batch_get_launch(batch, C.byref(bx), C.byref(by), C.byref(n)))
-    return bx.value, by.value, int(n.value)
+    bx, by, rows, n = C.c_int(), C.c_int(), C.c_int(), C.c_longlong()
+    _check(load_library().vplbm_batch_get_launch(batch, C.byref(bx), C.byref(by), C.byref(rows), C.byref(n)))
+    return bx.value, by.value, rows.value, int(n.value)
+
+
+def vplbm_batch_set_mode(batch, mode: int):
+    _check(load_library().vplbm_batch_set_mode(batch, int(mode)))
+
+
+def vplbm_batch_get_mode(batch) -> int:
+    m = C.c_int()
+    _check(load_library().vplbm_batch_get_mode(batch, C.byref(m)))
+    return m.value
 
 
 def vplbm_batch_autotune(batch, steps_per_trial: int = 8):
@@ -613,13 +630,22 @@ class Batch:
     def sync(self):
         vplbm_batch_sync(self.handle)
 
-    def set_launch(self, block_x: int, block_y: int = 1):
-        vplbm_batch_set_launch(self.handle, block_x, block_y)
+    def set_launch(self, block_x: int, block_y: int = 1, tiles_per_block: int = 1):
+        vplbm_batch_set_launch(self.handle, block_x, block_y, tiles_per_block)
 
     def launch(self):
-        """(block_x, block_y, batched launches so far)."""
+        """(block_x, block_y, tiles_per_block, batched launches so far)."""
         return vplbm_batch_get_launch(self.handle)
 
+    def set_mode(self, mode):
+        """"branches" (each member's own kernel, concurrent graph branches) or "tiles"."""
+        vplbm_batch_set_mode(self.handle, BATCH_MODES[mode] if isinstance(mode, str) else int(mode))
+
+    @property
+    def mode(self) -> str:
+        return BATCH_MODE_NAMES[vplbm_batch_get_mode(self.handle)]
+
     def autotune(self, steps_per_trial: int = 8):
+        """Fastest of the branch mode and the tile-mode shapes: (mode, block_x, block_y, tiles_per_block)."""
         vplbm_batch_autotune(self.handle, steps_per_trial)
-        return self.launch()[:2]
+        return (self.mode,) + tuple(self.launch()[:3])

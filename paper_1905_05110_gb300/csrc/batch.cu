@@ -1,7 +1,13 @@
 // Batched sweep: many simulations of uneven lattice sizes stepped together,
-// one launch per time step covering every member's tiles (the scalar step's
-// tile code, captured as CUDA graphs of 32 steps), each member with its own
-// body, reduction and tail.
+// each member with its own body, reduction and tail, captured as CUDA graphs
+// of 32 steps.  Two modes:
+//   branches: every member's own step kernel (parameters in the constant
+//             bank, its own launch shape), one graph branch per member, so
+//             the members' kernels run concurrently and fill each other's
+//             waves and tails;
+//   tiles:    one launch per time step covering every member's tiles (the
+//             scalar step's tile code, member found per block, parameters
+//             staged in shared memory).
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -35,18 +41,24 @@ struct vplbm_batch {
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;
     int precision = 0;
+    int collision = 0;
     int bx = 256, by = 1;             // block (tile) shape of the batched kernel
+    int rows = 8;                     // tiles per block, stacked in y
     StepParams *params_dev = nullptr; // [2][n]: parameters of each member per step parity
     int *tile_start_dev = nullptr;    // [n + 1]
     int total_tiles = 0;
+    int mode = VPLBM_BATCH_BRANCHES;
+    std::vector<cudaStream_t> branch;  // capture streams of the per-member graph branches
+    std::vector<cudaEvent_t> join;     // [0]: fork, [1 + k]: end of branch k
     cudaGraphExec_t graph = nullptr;
-    int graph_bx = -1, graph_by = -1;
+    int graph_bx = -1, graph_by = -1, graph_rows = -1, graph_mode = -1;
     long long launches = 0;
 };
 
 namespace {
 
-// Tile prefix of the members for the block shape bx x by.
+// Macro-tile prefix of the members for blocks of bx x by threads that run
+// `rows` tiles each.
 vplbm_status build_tiles(vplbm_batch *b)
 {
     std::vector<int> start(b->n + 1, 0);
@@ -54,7 +66,8 @@ vplbm_status build_tiles(vplbm_batch *b)
     for (int k = 0; k < b->n; ++k) {
         const vplbm_ctx *c = b->members[k];
         start[k] = (int)total;
-        total += (long long)((c->nx + b->bx - 1) / b->bx) * ((c->ny + b->by - 1) / b->by);
+        const long long nty = (c->ny + b->by - 1) / b->by;
+        total += (long long)((c->nx + b->bx - 1) / b->bx) * ((nty + b->rows - 1) / b->rows);
     }
     if (total > (1LL << 30)) return berr(VPLBM_EINVAL, "batch too large (%lld tiles)", total);
     start[b->n] = (int)total;
@@ -80,10 +93,19 @@ vplbm_status upload_params(vplbm_batch *b)
 
 cudaError_t launch_batch_step(const vplbm_batch *b, long long step, cudaStream_t stream)
 {
+    if (b->mode == VPLBM_BATCH_BRANCHES) {
+        for (int k = 0; k < b->n; ++k) {
+            const cudaError_t e = ctx_launch(b->members[k], step, stream);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     BatchLaunch bl;
     bl.params = b->params_dev + (size_t)(step & 1) * b->n;
     bl.tile_start = b->tile_start_dev;
     bl.n = b->n;
+    bl.rows = b->rows;
+    bl.collision = b->collision;
     return launch_step_batch(b->precision, bl, b->total_tiles, b->bx, b->by, stream);
 }
 
@@ -98,17 +120,61 @@ vplbm_status common_step(const vplbm_batch *b, long long *step)
     return VPLBM_OK;
 }
 
+// Streams and events of the branch graph, created on first use.
+cudaError_t ensure_branches(vplbm_batch *b)
+{
+    if ((int)b->branch.size() == b->n) return cudaSuccess;
+    b->branch.assign(b->n, nullptr);
+    b->join.assign(b->n + 1, nullptr);
+    for (int k = 0; k < b->n; ++k) {
+        const cudaError_t e = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    for (int k = 0; k <= b->n; ++k) {
+        const cudaError_t e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// BATCH_GRAPH_STEPS steps of every member: tile mode, one launch per step;
+// branch mode, one branch per member forked from and joined into the
+// capture stream.
+cudaError_t capture_batch_steps(vplbm_batch *b)
+{
+    if (b->mode != VPLBM_BATCH_BRANCHES) {
+        for (int k = 0; k < BATCH_GRAPH_STEPS; ++k) {
+            const cudaError_t e = launch_batch_step(b, k, b->capture);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaEventRecord(b->join[0], b->capture);
+    for (int m = 0; m < b->n && e == cudaSuccess; ++m) {
+        e = cudaStreamWaitEvent(b->branch[m], b->join[0], 0);
+        for (int k = 0; k < BATCH_GRAPH_STEPS && e == cudaSuccess; ++k) e = ctx_launch(b->members[m], k, b->branch[m]);
+        if (e == cudaSuccess) e = cudaEventRecord(b->join[1 + m], b->branch[m]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->capture, b->join[1 + m], 0);
+    }
+    return e;
+}
+
 vplbm_status ensure_batch_graph(vplbm_batch *b)
 {
-    if (b->graph && b->graph_bx == b->bx && b->graph_by == b->by) return VPLBM_OK;
+    if (b->graph && b->graph_mode == b->mode && b->graph_bx == b->bx && b->graph_by == b->by &&
+        b->graph_rows == b->rows)
+        return VPLBM_OK;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
+    if (b->mode == VPLBM_BATCH_BRANCHES) {
+        const cudaError_t e = ensure_branches(b);
+        if (e != cudaSuccess) return berr(VPLBM_ECUDA, "branch streams: %s", cudaGetErrorString(e));
+    }
     cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return berr(VPLBM_ECUDA, "capture begin failed: %s", cudaGetErrorString(e));
-    cudaError_t err = cudaSuccess;
-    for (int k = 0; k < BATCH_GRAPH_STEPS && err == cudaSuccess; ++k) err = launch_batch_step(b, k, b->capture);
+    const cudaError_t err = capture_batch_steps(b);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->capture, &g);
     if (err != cudaSuccess || e != cudaSuccess) {
@@ -118,8 +184,10 @@ vplbm_status ensure_batch_graph(vplbm_batch *b)
     e = cudaGraphInstantiate(&b->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return berr(VPLBM_ECUDA, "batch graph instantiate failed: %s", cudaGetErrorString(e));
+    b->graph_mode = b->mode;
     b->graph_bx = b->bx;
     b->graph_by = b->by;
+    b->graph_rows = b->rows;
     return VPLBM_OK;
 }
 
@@ -158,6 +226,10 @@ void vplbm_batch_destroy(vplbm_batch *b)
     if (!b) return;
     if (b->stream || b->params_dev) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaStream_t st : b->branch)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->join)
+        if (ev) cudaEventDestroy(ev);
     if (b->capture) cudaStreamDestroy(b->capture);
     if (b->params_dev) cudaFree(b->params_dev);
     if (b->tile_start_dev) cudaFree(b->tile_start_dev);
@@ -173,11 +245,15 @@ vplbm_status vplbm_batch_create(const vplbm_lattice_desc *lats, const vplbm_body
     const int prec = lats[0].precision;
     for (int k = 0; k < n; ++k)
         if (lats[k].precision != prec) return berr(VPLBM_EINVAL, "member %d: all members need the same precision", k);
+    for (int k = 0; k < n; ++k)
+        if (lats[k].collision != lats[0].collision)
+            return berr(VPLBM_EINVAL, "member %d: all members need the same collision operator", k);
     vplbm_batch *b = new (std::nothrow) vplbm_batch();
     if (!b) return berr(VPLBM_ENOMEM, "host allocation failed");
     b->n = n;
     b->stream = (cudaStream_t)cuda_stream;
     b->precision = prec;
+    b->collision = lats[0].collision;
     vplbm_status st = VPLBM_OK;
     try {
         b->members.assign(n, nullptr);
@@ -230,35 +306,56 @@ vplbm_status vplbm_batch_sync(vplbm_batch *b)
     return VPLBM_OK;
 }
 
-vplbm_status vplbm_batch_set_launch(vplbm_batch *b, int block_x, int block_y)
+vplbm_status vplbm_batch_set_launch(vplbm_batch *b, int block_x, int block_y, int tiles_per_block)
 {
     if (!b) return berr(VPLBM_EINVAL, "batch is NULL");
     const int t = block_x * block_y;
     if (block_x < 32 || block_x % 32 || block_y < 1 || (t != 128 && t != 256))
         return berr(VPLBM_EINVAL, "block shape %dx%d not allowed", block_x, block_y);
+    if (tiles_per_block < 1 || tiles_per_block > 64)
+        return berr(VPLBM_EINVAL, "tiles per block %d not in [1, 64]", tiles_per_block);
     for (int k = 0; k < b->n; ++k) {
         const vplbm_ctx *c = b->members[k];
         if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, block_x, block_y) >
             c->max_parts)
             return berr(VPLBM_EINVAL, "member %d: block shape needs more reduction scratch than allocated", k);
     }
-    const int obx = b->bx, oby = b->by;
+    const int obx = b->bx, oby = b->by, orows = b->rows;
     b->bx = block_x;
     b->by = block_y;
+    b->rows = tiles_per_block;
     vplbm_status st = build_tiles(b);
     if (st != VPLBM_OK) {
         b->bx = obx;
         b->by = oby;
+        b->rows = orows;
         build_tiles(b);
     }
     return st;
 }
 
-vplbm_status vplbm_batch_get_launch(vplbm_batch *b, int *block_x, int *block_y, long long *launches)
+vplbm_status vplbm_batch_set_mode(vplbm_batch *b, int mode)
+{
+    if (!b) return berr(VPLBM_EINVAL, "batch is NULL");
+    if (mode != VPLBM_BATCH_BRANCHES && mode != VPLBM_BATCH_TILES) return berr(VPLBM_EINVAL, "unknown batch mode %d", mode);
+    b->mode = mode;
+    return VPLBM_OK;
+}
+
+vplbm_status vplbm_batch_get_mode(vplbm_batch *b, int *mode)
+{
+    if (!b || !mode) return berr(VPLBM_EINVAL, "NULL argument");
+    *mode = b->mode;
+    return VPLBM_OK;
+}
+
+vplbm_status vplbm_batch_get_launch(vplbm_batch *b, int *block_x, int *block_y, int *tiles_per_block,
+                                   long long *launches)
 {
     if (!b) return berr(VPLBM_EINVAL, "batch is NULL");
     if (block_x) *block_x = b->bx;
     if (block_y) *block_y = b->by;
+    if (tiles_per_block) *tiles_per_block = b->rows;
     if (launches) *launches = b->launches;
     return VPLBM_OK;
 }
@@ -272,13 +369,19 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int steps_per_trial)
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return berr(VPLBM_ECUDA, "event creation failed");
     float best = 1e30f;
-    int best_bx = b->bx, best_by = b->by;
+    int best_bx = b->bx, best_by = b->by, best_rows = b->rows, best_mode = b->mode;
     vplbm_status st = VPLBM_OK;
-    const int cands[4][2] = {{256, 1}, {128, 1}, {128, 2}, {64, 2}};
+    // {-1, 0, 0}: branch mode (the members' own launch shapes); the rest: tile mode shapes
+    const int cands[7][3] = {{-1, 0, 0}, {256, 1, 8}, {256, 1, 4}, {256, 1, 16}, {128, 2, 4}, {128, 1, 8}, {256, 1, 1}};
     for (const auto &cb : cands) {
-        const int bx = cb[0], by = cb[1];
-        st = vplbm_batch_set_launch(b, bx, by);
-        if (st != VPLBM_OK) break;
+        const int bx = cb[0], by = cb[1], rows = cb[2];
+        if (bx < 0) {
+            b->mode = VPLBM_BATCH_BRANCHES;
+        } else {
+            b->mode = VPLBM_BATCH_TILES;
+            st = vplbm_batch_set_launch(b, bx, by, rows);
+            if (st != VPLBM_OK) break;
+        }
         for (int rep = 0; rep < 2 && st == VPLBM_OK; ++rep) {
             cudaEventRecord(e0, b->stream);
             st = batch_step_impl(b, steps_per_trial);
@@ -288,15 +391,18 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int steps_per_trial)
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep == 1 && ms < best) {
                 best = ms;
-                best_bx = bx;
-                best_by = by;
+                best_mode = b->mode;
+                best_bx = b->bx;
+                best_by = b->by;
+                best_rows = b->rows;
             }
         }
         if (st != VPLBM_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    vplbm_status st2 = vplbm_batch_set_launch(b, best_bx, best_by);
+    b->mode = best_mode;
+    vplbm_status st2 = vplbm_batch_set_launch(b, best_bx, best_by, best_rows);
     return st != VPLBM_OK ? st : st2;
 }
 

@@ -108,10 +108,13 @@ vplbm_status check_lattice(const vplbm_lattice_desc *lat)
     if (!(lat->rho0 > 0.0) || !isfinite(lat->rho0)) return fail(VPLBM_EINVAL, "rho0 must be > 0");
     if (!isfinite(lat->gx) || !isfinite(lat->gy)) return fail(VPLBM_EINVAL, "fluid acceleration not finite");
     if (lat->precision < VPLBM_F64 || lat->precision > VPLBM_F16_DEV) return fail(VPLBM_EINVAL, "unknown precision %d", lat->precision);
+    if (lat->collision != VPLBM_COLLISION_MRT && lat->collision != VPLBM_COLLISION_BGK)
+        return fail(VPLBM_EINVAL, "unknown collision operator %d", lat->collision);
     for (int s = 0; s < 4; ++s) {
         const int k = lat->bc[s].kind;
-        if (k < VPLBM_BC_PERIODIC || k > VPLBM_BC_ZEROGRAD) return fail(VPLBM_EINVAL, "edge %d: unknown boundary kind %d", s, k);
+        if (k < VPLBM_BC_PERIODIC || k > VPLBM_BC_SYMMETRY) return fail(VPLBM_EINVAL, "edge %d: unknown boundary kind %d", s, k);
         if (k == VPLBM_BC_ZEROGRAD && s >= VPLBM_SOUTH) return fail(VPLBM_EUNSUPPORTED, "zero-gradient is supported on west/east edges only");
+        if (k == VPLBM_BC_SYMMETRY && s < VPLBM_SOUTH) return fail(VPLBM_EUNSUPPORTED, "symmetry is supported on south/north edges only");
     }
     if ((lat->bc[VPLBM_WEST].kind == VPLBM_BC_PERIODIC) != (lat->bc[VPLBM_EAST].kind == VPLBM_BC_PERIODIC))
         return fail(VPLBM_EINVAL, "west and east must both be periodic or neither");
@@ -214,6 +217,7 @@ void setup_tma(vplbm_ctx *c)
 {
     c->tma_ok = false;
     if (c->precision != VPLBM_F32_DEV && c->precision != VPLBM_F16_DEV) return;
+    if (c->collision != VPLBM_COLLISION_MRT) return;
     const int es = (int)elem_size(c->precision);
     const int halo = tma_halo(c->precision);
     const int boxw = TMA_TILE_W + 2 * halo;
@@ -266,6 +270,7 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     CUDA_TRY(cudaGetDevice(&c->device));
     CUDA_TRY(cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking));
     c->precision = lat->precision;
+    c->collision = lat->collision;
     c->nx = lat->nx;
     c->ny = lat->ny;
     c->hist_cap = cap;
@@ -274,6 +279,7 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
 
     StepParams &p = c->base;
     p.nx = lat->nx;
+    p.collision = lat->collision;
     p.ny = lat->ny;
     p.ps = c->ps;
     for (int k = 0; k < 9; ++k) p.s[k] = lat->s[k];
@@ -703,7 +709,7 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
     if (!c) return fail(VPLBM_EINVAL, "context is NULL");
     if (kernel == KERNEL_TMA) {
         if (!c->tma_ok)
-            return fail(VPLBM_EUNSUPPORTED, "the TMA-staged kernel needs FP32/FP16 storage, nx*elem a multiple of 16 bytes and nx >= 136/144");
+            return fail(VPLBM_EUNSUPPORTED, "the TMA-staged kernel needs the MRT operator, FP32/FP16 storage, nx*elem a multiple of 16 bytes and nx >= 136/144");
         c->kernel = KERNEL_TMA;
         c->bx = TMA_TILE_W;
         c->by = 2;

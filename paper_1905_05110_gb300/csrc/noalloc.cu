@@ -145,6 +145,7 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const 
     // step parameters, filled as vplbm_create fills them
     StepParams p{};
     p.nx = lat->nx;
+    p.collision = lat->collision;
     p.ny = lat->ny;
     p.ps = ((long long)lat->nx * lat->ny + 127) / 128 * 128;
     for (int k = 0; k < 9; ++k) {

@@ -35,7 +35,7 @@ namespace {
 
 // One tile of the step: blockDim.x x blockDim.y nodes at tile (tile_x,
 // tile_y); p may live in shared memory (batched launch).
-template <int P>
+template <int P, int COLL>
 __device__ __forceinline__ void scalar_tile(const StepParams &p, int tile_x, int tile_y, double (*red)[NPART],
                                             int *s_last)
 {
@@ -61,14 +61,9 @@ __device__ __forceinline__ void scalar_tile(const StepParams &p, int tile_x, int
     bool chi = false;
     T cr = 0, cax = 0, cay = 0;   // kept for the solid-node sums (converted there)
     if (inside)
-        chi = node_update<P>(p, bs, part_block && range.x <= range.y, i, j, f, fout, cr, cax, cay);
+        chi = node_update<P, COLL>(p, bs, part_block && range.x <= range.y, i, j, f, fout, cr, cax, cay);
     if (!part_block) return;   // uniform over the block
-
-    double part[NPART - 1];
-#pragma unroll
-    for (int k = 0; k < NPART - 1; ++k) part[k] = 0.0;
-    if (chi) solid_node_sums<P>(p, fin, i, j, (double)cr, (double)cax, (double)cay, part);
-    tile_reduce(p, range, tile_x, tile_y, blockDim.x, blockDim.y, chi, part, red, s_last);
+    tile_solid_sums<P>(p, fin, range, tile_x, tile_y, blockDim.x, blockDim.y, chi, i, j, cr, cax, cay, red, s_last);
 }
 
 // MINB: blocks of 256 threads per SM the register budget is sized for
@@ -77,21 +72,27 @@ __device__ __forceinline__ void scalar_tile(const StepParams &p, int tile_x, int
 // Launched with programmatic dependent launch: every block lets the next
 // step's grid start launching at once, and waits (in hardware) until the
 // previous step's grid has completed and its writes are visible before it
-// reads anything, so the next launch overlaps the end of this one.
-template <int P, int MINB>
+// reads anything, so the next launch overlaps the end of this one.  The
+// first block also computes the next pose of a body on a prescribed path.
+template <int P, int MINB, int COLL>
 __global__ void __launch_bounds__(256, MINB) vp_mrt_step(const StepParams p)
 {
     __shared__ double red[8][NPART];
     __shared__ int s_last;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    scalar_tile<P>(p, blockIdx.x, blockIdx.y, red, &s_last);
+    scalar_tile<P, COLL>(p, blockIdx.x, blockIdx.y, red, &s_last);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0 && prescribed_motion(p))
+        advance_prescribed(p);
 }
 
-// Every member of a batch in one launch: block b runs tile b of the
-// concatenated tile lists; its member is found in the tile prefix and its
-// step parameters are staged in shared memory.
-template <int P>
+// Every member of a batch in one launch: block b runs macro tile b of the
+// concatenated macro-tile lists (bl.rows tiles of blockDim.x x blockDim.y
+// stacked in y); its member is found in the macro-tile prefix and its step
+// parameters are staged in shared memory.  The lookup and the staging read
+// only data that no step writes, so they run before the wait on the previous
+// step's grid (programmatic dependent launch).
+template <int P, int COLL>
 __global__ void __launch_bounds__(256, 5) vp_mrt_step_batch(const BatchLaunch bl)
 {
     __shared__ double red[8][NPART];
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(256, 5) vp_mrt_step_batch(const BatchLaunch bl
     __shared__ __align__(16) StepParams sp;
     __shared__ int s_member, s_local;
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-        int lo = 0, hi = bl.n - 1;   // last member whose first tile is <= blockIdx.x
+        int lo = 0, hi = bl.n - 1;   // last member whose first macro tile is <= blockIdx.x
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (bl.tile_start[mid] <= (int)blockIdx.x) lo = mid;
@@ -114,8 +115,14 @@ __global__ void __launch_bounds__(256, 5) vp_mrt_step_batch(const BatchLaunch bl
     uint32_t *dst = reinterpret_cast<uint32_t *>(&sp);
     for (int k = tid; k < (int)(sizeof(StepParams) / 4); k += blockDim.x * blockDim.y) dst[k] = src[k];
     __syncthreads();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int ntx = (sp.nx + blockDim.x - 1) / blockDim.x;
-    scalar_tile<P>(sp, s_local % ntx, s_local / ntx, red, &s_last);
+    const int nty = (sp.ny + blockDim.y - 1) / blockDim.y;
+    const int tx = s_local % ntx, ty0 = (s_local / ntx) * bl.rows;
+#pragma unroll 1
+    for (int r = 0; r < bl.rows && ty0 + r < nty; ++r) scalar_tile<P, COLL>(sp, tx, ty0 + r, red, &s_last);
+    if (s_local == 0 && tid == 0 && prescribed_motion(sp)) advance_prescribed(sp);
 }
 
 // ---- equilibrium initialisation (Eq. 11) -------------------------------
@@ -194,9 +201,14 @@ cudaError_t launch_step_t(const StepParams &p, int bx, int by, int minb, cudaStr
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (minb == 6) return cudaLaunchKernelEx(&cfg, vp_mrt_step<P, 6>, p);
-    if (minb == 5) return cudaLaunchKernelEx(&cfg, vp_mrt_step<P, 5>, p);
-    return cudaLaunchKernelEx(&cfg, vp_mrt_step<P, 4>, p);
+    if (p.collision == VPLBM_COLLISION_BGK) {
+        if (minb == 6) return cudaLaunchKernelEx(&cfg, vp_mrt_step<P, 6, VPLBM_COLLISION_BGK>, p);
+        if (minb == 5) return cudaLaunchKernelEx(&cfg, vp_mrt_step<P, 5, VPLBM_COLLISION_BGK>, p);
+        return cudaLaunchKernelEx(&cfg, vp_mrt_step<P, 4, VPLBM_COLLISION_BGK>, p);
+    }
+    if (minb == 6) return cudaLaunchKernelEx(&cfg, vp_mrt_step<P, 6, VPLBM_COLLISION_MRT>, p);
+    if (minb == 5) return cudaLaunchKernelEx(&cfg, vp_mrt_step<P, 5, VPLBM_COLLISION_MRT>, p);
+    return cudaLaunchKernelEx(&cfg, vp_mrt_step<P, 4, VPLBM_COLLISION_MRT>, p);
 }
 
 }  // namespace
@@ -215,12 +227,28 @@ long long max_reduction_blocks(int nx, int ny, double radius, int present, int b
 cudaError_t launch_step_batch(int precision, const BatchLaunch &bl, int total_tiles, int bx, int by,
                               cudaStream_t stream)
 {
-    dim3 block(bx, by);
-    if (precision == VPLBM_F32_DEV) vp_mrt_step_batch<VPLBM_F32_DEV><<<total_tiles, block, 0, stream>>>(bl);
-    else if (precision == VPLBM_F16_DEV) vp_mrt_step_batch<VPLBM_F16_DEV><<<total_tiles, block, 0, stream>>>(bl);
-    else if (precision == VPLBM_F64) vp_mrt_step_batch<VPLBM_F64><<<total_tiles, block, 0, stream>>>(bl);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(total_tiles);
+    cfg.blockDim = dim3(bx, by);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const bool bgk = bl.collision == VPLBM_COLLISION_BGK;
+    switch (precision) {
+    case VPLBM_F32_DEV:
+        return bgk ? cudaLaunchKernelEx(&cfg, vp_mrt_step_batch<VPLBM_F32_DEV, VPLBM_COLLISION_BGK>, bl)
+                   : cudaLaunchKernelEx(&cfg, vp_mrt_step_batch<VPLBM_F32_DEV, VPLBM_COLLISION_MRT>, bl);
+    case VPLBM_F16_DEV:
+        return bgk ? cudaLaunchKernelEx(&cfg, vp_mrt_step_batch<VPLBM_F16_DEV, VPLBM_COLLISION_BGK>, bl)
+                   : cudaLaunchKernelEx(&cfg, vp_mrt_step_batch<VPLBM_F16_DEV, VPLBM_COLLISION_MRT>, bl);
+    case VPLBM_F64:
+        return bgk ? cudaLaunchKernelEx(&cfg, vp_mrt_step_batch<VPLBM_F64, VPLBM_COLLISION_BGK>, bl)
+                   : cudaLaunchKernelEx(&cfg, vp_mrt_step_batch<VPLBM_F64, VPLBM_COLLISION_MRT>, bl);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb)

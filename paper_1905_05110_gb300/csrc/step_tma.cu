@@ -160,9 +160,10 @@ __global__ void __launch_bounds__(256, 4) vp_mrt_step_tma(const StepParams p, co
         const unsigned char *st = ring + stage * C::STAGE_BYTES;
         const bool near = tile_near_body(range, i0, j0, TW, CR, c == 0);
 
-        double part[NPART - 1];
+        using A = typename SumT<P>::A;
+        A part[NPART - 1];
 #pragma unroll
-        for (int q = 0; q < NPART - 1; ++q) part[q] = 0.0;
+        for (int q = 0; q < NPART - 1; ++q) acc_zero(part[q]);
         bool any_chi = false;
 #pragma unroll
         for (int rr = 0; rr < CR / TY; ++rr) {
@@ -183,18 +184,19 @@ __global__ void __launch_bounds__(256, 4) vp_mrt_step_tma(const StepParams p, co
                 T cr = 0, cax = 0, cay = 0;
                 const bool chi = node_update<P>(p, bs, near && range.x <= range.y, i, j, f, fout, cr, cax, cay);
                 if (chi) {
-                    double one[NPART - 1];
-                    solid_node_sums<P>(p, fin, i, j, (double)cr, (double)cax, (double)cay, one);
+                    float one[NPART - 1];
+                    solid_node_terms<P>(p, fin, i, j, cr, cax, cay, one);
 #pragma unroll
-                    for (int q = 0; q < NPART - 1; ++q) part[q] += one[q];
+                    for (int q = 0; q < NPART - 1; ++q) acc_add(part[q], one[q]);
                     any_chi = true;
                 }
             }
         }
-        if (near) tile_reduce(p, range, cxi, cyi, TW, CR, any_chi, part, red, &s_last);
+        if (near) tile_reduce<A>(p, range, cxi, cyi, TW, CR, any_chi, part, red, &s_last);
         __syncthreads();   // every thread is done with this stage
         if (tid == 0 && k + NSTAGE < nmine) issue(k + NSTAGE);
     }
+    if (blockIdx.x == 0 && tid == 0 && prescribed_motion(p)) advance_prescribed(p);
 }
 
 }  // namespace

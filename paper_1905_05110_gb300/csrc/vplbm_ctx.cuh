@@ -12,6 +12,7 @@ struct vplbm_ctx {
     cudaStream_t stream = nullptr;        // caller's stream
     cudaStream_t capture = nullptr;       // private stream used only to capture graphs
     int precision = 0;
+    int collision = 0;
     int nx = 0, ny = 0;
     long long ps = 0;                     // plane stride (elements)
     size_t pop_bytes = 0;

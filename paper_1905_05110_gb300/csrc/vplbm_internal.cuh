@@ -111,6 +111,7 @@ struct StepParams {
     vplbm_record *hist;
     long long hist_cap;
     unsigned tx_extra;            // test hook: bytes the first TMA stage waits for in vain
+    int collision;                // vplbm_collision: picks the kernel instantiation on the host
 };
 
 // Error bits latched in the control word.
@@ -168,10 +169,12 @@ enum { KERNEL_SCALAR = 0, KERNEL_SCALAR_48 = 1, KERNEL_SCALAR_40 = 2, KERNEL_TMA
 // Batched launch of the scalar step over many lattices.
 struct BatchLaunch {
     const StepParams *params;   // one per member (device), for this step's parity
-    const int *tile_start;      // n + 1 prefix sums of the members' tile counts (device)
+    const int *tile_start;      // n + 1 prefix sums of the members' macro-tile counts (device)
     int n;
+    int rows;                   // tiles per macro tile (stacked in y), one macro tile per block
+    int collision;              // shared by every member (host-side dispatch)
 };
-// Batched scalar step (step_kernels.cu): tiles of bx x by nodes.
+// Batched scalar step (step_kernels.cu): macro tiles of bx x (by * rows) nodes.
 cudaError_t launch_step_batch(int precision, const BatchLaunch &bl, int total_tiles, int bx, int by,
                               cudaStream_t stream);
 

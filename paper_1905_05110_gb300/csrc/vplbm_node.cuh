@@ -29,10 +29,12 @@ __device__ __forceinline__ void stv(__half *p, float x) { *p = __float2half_rn(x
 __host__ __device__ constexpr int cx_of(int a) { return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0); }
 __host__ __device__ constexpr int cy_of(int a) { return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0); }
 __host__ __device__ constexpr int opp_of(int a) { return a == 0 ? 0 : (a <= 4 ? ((a + 1) % 4) + 1 : ((a - 5 + 2) % 4) + 5); }
+__host__ __device__ constexpr int miry_of(int a) { return a == 2 ? 4 : a == 4 ? 2 : a == 5 ? 8 : a == 8 ? 5 : a == 6 ? 7 : a == 7 ? 6 : a; }
 __host__ __device__ constexpr double w_of(int a) { return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
 
 static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 && opp_of(4) == 2, "opp axis");
 static_assert(opp_of(5) == 7 && opp_of(6) == 8 && opp_of(7) == 5 && opp_of(8) == 6, "opp diag");
+static_assert(cx_of(miry_of(6)) == cx_of(6) && cy_of(miry_of(6)) == -cy_of(6) && cy_of(miry_of(2)) == -1, "mirror");
 
 // A parameter in the kernel's arithmetic type: the FP64 value for the FP64
 // kernel, the host-rounded FP32 copy otherwise (no conversion on the device).
@@ -65,6 +67,10 @@ __device__ typename Prec<P>::T pull_edge(const StepParams &p, const typename Pre
         const int kind = p.bc[side];
         if (kind == VPLBM_BC_PERIODIC) {
             sj = sj < 0 ? sj + ny : sj - ny;
+        } else if (kind == VPLBM_BC_SYMMETRY) {   // specular reflection at the half-way wall
+            int mi = i - cx_of(a);
+            if (mi < 0 || mi >= nx) mi = p.bc[VPLBM_WEST] == VPLBM_BC_PERIODIC ? (mi < 0 ? mi + nx : mi - nx) : i;
+            return ldv(fin + miry_of(a) * ps + (long long)j * nx + mi);
         } else {
             T val = ldv(fin + opp_of(a) * ps + (long long)j * nx + i);
             if (kind == VPLBM_BC_VELOCITY) {
@@ -162,27 +168,85 @@ __device__ void body_advance(const DevBody &b, long long step, const double F[3]
     }
 }
 
-// Last participating block: fixed-order sum of the partials, history
-// record, body update, next pose.  Runs on warp 0.
+// ---- the 7 solid-node sums (Eqs. 25-27 and the penalization reaction) ---
+//
+// FP64 kernel: the terms and their sums in FP64.  FP32 / FP16 kernels: the
+// terms in FP32 and their sums in float-float (hi + lo): GB300's FP64 pipe
+// is narrow, and a block that meets the body would otherwise spend most of
+// its time on FP64 adds.  A float-float sum carries about 44 bits, and the
+// block's sum is converted to FP64 exactly before it is published.
+
+// Float-float addition: Knuth's TwoSum of the high parts, the low parts
+// added to its error term, then a fast renormalisation (Dekker).
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b)
+{
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = ((a.x - (s - bb)) + (b.x - bb)) + (a.y + b.y);
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+
+template <int P> struct SumT { using A = float2; using V = float; };
+template <> struct SumT<VPLBM_F64> { using A = double; using V = double; };
+
+__device__ __forceinline__ void acc_add(double &a, double b) { a += b; }
+__device__ __forceinline__ void acc_add(float2 &a, float2 b) { a = ff_add(a, b); }
+__device__ __forceinline__ void acc_add(float2 &a, float b) { a = ff_add(a, make_float2(b, 0.f)); }
+__device__ __forceinline__ void acc_zero(double &a) { a = 0.0; }
+__device__ __forceinline__ void acc_zero(float2 &a) { a = make_float2(0.f, 0.f); }
+__device__ __forceinline__ double acc_shfl_down(double a, int off) { return __shfl_down_sync(0xffffffffu, a, off); }
+__device__ __forceinline__ float2 acc_shfl_down(float2 a, int off)
+{
+    return make_float2(__shfl_down_sync(0xffffffffu, a.x, off), __shfl_down_sync(0xffffffffu, a.y, off));
+}
+__device__ __forceinline__ double acc_value(double a) { return a; }
+__device__ __forceinline__ double acc_value(float2 a) { return (double)a.x + (double)a.y; }   // exact
+
+// Bodies on a prescribed path (absent, fixed or imposed) move independently
+// of the forces: their next pose is computed by one thread of the first
+// block of the step (advance_prescribed), off the tail's critical path.
+__device__ __forceinline__ bool prescribed_motion(const StepParams &p)
+{
+    return !p.body.present || p.body.motion != VPLBM_MOTION_FREE;
+}
+
+__device__ __noinline__ void advance_prescribed(const StepParams &p)
+{
+    BodyState nb = *p.bs_in;
+    const double F0[3] = {0.0, 0.0, 0.0};   // not used by fixed / imposed motion
+    body_advance(p.body, nb.step, F0, nb.q, nb.v);
+    nb.step += 1;
+    derive_pose(nb, p.body.present, p.body.radius, p.nx, p.ny);
+    *p.bs_out = nb;
+}
+
+// Last participating block: fixed-order sum of the partials (accumulator
+// type A, as the blocks published them), history record, and for a free
+// body the RK4 update and next pose.  Runs on warp 0.
+template <typename A>
 __device__ __noinline__ void step_tail(const StepParams &p, int nparts)
 {
     const int lane = threadIdx.x & 31;
-    double acc[NPART - 1];
+    A acc[NPART - 1];
 #pragma unroll
-    for (int k = 0; k < NPART - 1; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NPART - 1; ++k) acc_zero(acc[k]);
     for (int s = lane; s < nparts; s += 32) {
-        const double *src = p.partials + (size_t)s * NPART;
+        const A *src = reinterpret_cast<const A *>(p.partials + (size_t)s * NPART);
 #pragma unroll
-        for (int k = 0; k < NPART - 1; ++k) acc[k] += __ldcg(src + k);
+        for (int k = 0; k < NPART - 1; ++k) acc_add(acc[k], __ldcg(src + k));
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-        for (int k = 0; k < NPART - 1; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
+        for (int k = 0; k < NPART - 1; ++k) acc_add(acc[k], acc_shfl_down(acc[k], off));
     if (lane != 0) return;
+    double sum[NPART - 1];
+#pragma unroll
+    for (int k = 0; k < NPART - 1; ++k) sum[k] = acc_value(acc[k]);
 
     const BodyState cur = *p.bs_in;
-    const double Fh[3] = {acc[3], acc[4], acc[5]};
+    const double Fh[3] = {sum[3], sum[4], sum[5]};
     vplbm_record r;
     r.t = (double)cur.step;
     r.fx = Fh[0]; r.fy = Fh[1]; r.torque = Fh[2];
@@ -190,50 +254,60 @@ __device__ __noinline__ void step_tail(const StepParams &p, int nparts)
     r.cl = p.body.qref > 0 ? Fh[1] / p.body.qref : 0.0;
     r.x = cur.q[0]; r.y = cur.q[1]; r.theta = cur.q[2];
     r.vx = cur.v[0]; r.vy = cur.v[1]; r.omega = cur.v[2];
-    r.fpen_x = acc[0]; r.fpen_y = acc[1]; r.tpen = acc[2];
-    r.n_solid = acc[6];
+    r.fpen_x = sum[0]; r.fpen_y = sum[1]; r.tpen = sum[2];
+    r.n_solid = sum[6];
     p.hist[cur.step % p.hist_cap] = r;
 
-    BodyState nb = cur;
-    body_advance(p.body, cur.step, Fh, nb.q, nb.v);
-    nb.step = cur.step + 1;
-    derive_pose(nb, p.body.present, p.body.radius, p.nx, p.ny);
-    *p.bs_out = nb;
+    if (!prescribed_motion(p)) {
+        BodyState nb = cur;
+        body_advance(p.body, cur.step, Fh, nb.q, nb.v);
+        nb.step = cur.step + 1;
+        derive_pose(nb, p.body.present, p.body.radius, p.nx, p.ny);
+        *p.bs_out = nb;
+    }
     *p.ticket = 0u;   // ready for the next launch (stream order)
 }
 
-// Contributions of one solid node to the 7 FP64 sums: penalization
-// reaction (force, torque) and momentum exchanged through its links during
-// the streaming into this step (force, torque), plus the node count.
+// Terms of one solid node: penalization reaction (force, torque about x_G),
+// momentum exchanged through its links during the streaming into this step
+// (force, torque), and the node count.  The pulled populations are loaded
+// again (cache hits) so that they are not live across the stores.
 template <int P>
-__device__ __forceinline__ void solid_node_sums(const StepParams &p, const typename Prec<P>::S *fin, int i, int j,
-                                                double rho, double ax, double ay, double part[NPART - 1])
+__device__ __forceinline__ void solid_node_terms(const StepParams &p, const typename Prec<P>::S *fin, int i, int j,
+                                                 typename SumT<P>::V rho, typename SumT<P>::V ax,
+                                                 typename SumT<P>::V ay, typename SumT<P>::V out[NPART - 1])
 {
     using T = typename Prec<P>::T;
+    using V = typename SumT<P>::V;
     const BodyState *bs = p.bs_in;
     T f[NQ];
-    pull_all<P>(p, fin, i, j, f);   // reloaded (cache hits) so f is not live across the stores
+    pull_all<P>(p, fin, i, j, f);
     const long long b = (long long)j * p.nx + i;
-    const double dxd = (double)i - bs->q[0], dyd = (double)j - bs->q[1];
-    const double px = -rho * ax, py = -rho * ay;
-    double jxd = 0, jyd = 0, oxd = 0, oyd = 0;
+    V dx, dy;
+    if constexpr (P == VPLBM_F64) {
+        dx = (double)i - bs->q[0];
+        dy = (double)j - bs->q[1];
+    } else {
+        const int2 xy = __ldg(reinterpret_cast<const int2 *>(&bs->xi));
+        const float2 fr = __ldg(reinterpret_cast<const float2 *>(&bs->xf));
+        dx = (float)(i - xy.x) - fr.x;
+        dy = (float)(j - xy.y) - fr.y;
+    }
+    const V px = -rho * ax, py = -rho * ay;
+    V ex = 0, ey = 0;
 #pragma unroll
     for (int a = 1; a < NQ; ++a) {
-        const double fa = (double)f[a];
-        const double own = (double)ldv(fin + a * p.ps + b);
-        jxd += cx_of(a) * fa;
-        jyd += cy_of(a) * fa;
-        oxd += cx_of(a) * own;
-        oyd += cy_of(a) * own;
+        const V d = (V)f[a] - (V)ldv(fin + a * p.ps + b);   // pulled minus own
+        ex += cx_of(a) * d;
+        ey += cy_of(a) * d;
     }
-    const double ex = jxd - oxd, ey = jyd - oyd;
-    part[0] = px;
-    part[1] = py;
-    part[2] = dxd * py - dyd * px;
-    part[3] = ex;
-    part[4] = ey;
-    part[5] = dxd * ey - dyd * ex;
-    part[6] = 1.0;
+    out[0] = px;
+    out[1] = py;
+    out[2] = dx * py - dy * px;
+    out[3] = ex;
+    out[4] = ey;
+    out[5] = dx * ey - dy * ex;
+    out[6] = 1;
 }
 
 
@@ -241,7 +315,7 @@ __device__ __forceinline__ void solid_node_sums(const StepParams &p, const typen
 // populations f: moments, chi and u_s, penalized velocity (Eq. 22),
 // collision with forcing (Eq. 17) and the store of f~.  Returns chi and
 // keeps rho, a for the solid-node sums.
-template <int P>
+template <int P, int COLL = VPLBM_COLLISION_MRT>
 __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState *__restrict__ bs, bool near_body,
                                             int i, int j, const typename Prec<P>::T f[NQ],
                                             typename Prec<P>::S *__restrict__ fout, typename Prec<P>::T &cr,
@@ -283,8 +357,15 @@ __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState
 
     // penalized velocity, Eq. (22) in the eta-stable form
     T inv_rho;
-    if constexpr (DEV) inv_rho = __frcp_rn(rho);
-    else inv_rho = (T)1 / rho;
+    if constexpr (DEV) {
+        // hardware reciprocal estimate refined by one Newton-Raphson step,
+        // r1 = r0 + r0 (1 - rho r0): within an ulp or two of 1/rho
+        float r0;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"((float)rho));
+        inv_rho = fmaf(r0, fmaf(-(float)rho, r0, 1.0f), r0);
+    } else {
+        inv_rho = (T)1 / rho;
+    }
     const T gx = par<T>(p.gx, p.gxf), gy = par<T>(p.gy, p.gyf);
     const T vx = jx * inv_rho + (T)0.5 * gx;
     const T vy = jy * inv_rho + (T)0.5 * gy;
@@ -305,6 +386,42 @@ __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState
     const T uy = vy + (T)0.5 * ay;
     const T Gx = rho * (gx + ax);
     const T Gy = rho * (gy + ay);
+    using S = typename Prec<P>::S;
+    S *const *dp = reinterpret_cast<S *const *>(p.dst_plane);
+    const int b = j * p.nx + i;
+
+    if constexpr (COLL == VPLBM_COLLISION_BGK) {
+        // Sec. 2.1: f~ = (1 - omega) f + omega f_eq + (1 - omega/2) F with
+        // f_eq of Eq. (11) and F of Eq. (12), by pairs of opposite
+        // directions a, a': f~_a = (1 - omega) f_a + w_a (even +- odd),
+        //   even = omega (base + rho (9/2 (c.u)^2 - 3/2 u^2)) + 3k (3 (c.u)(c.G) - u.G),
+        //   odd  = 3 omega rho (c.u) + 3k (c.G),   k = 1 - omega/2,
+        // base = rho (FP64 storage) or rho - rho0 (deviation storage).
+        const T om = par<T>(p.s[7], p.sf[7]);
+        const T om1 = (T)1 - om;
+        const T k3 = fma((T)-1.5, om, (T)3);
+        const T k9 = (T)3 * k3;
+        const T orho = om * rho;
+        const T orho3 = (T)3 * orho, orho45 = (T)4.5 * orho;
+        const T u2 = fma(ux, ux, uy * uy);
+        const T uG = fma(ux, Gx, uy * Gy);
+        const T c0 = fma(om, fma((T)-1.5 * rho, u2, DEV ? rs : rho), -k3 * uG);
+        auto pair = [&](int a, int ao, T cu, T cG, T w) {
+            const T we = w * fma(cu, fma(orho45, cu, k9 * cG), c0);
+            const T wo = w * fma(orho3, cu, k3 * cG);
+            stv(dp[a] + b, fma(om1, f[a], we + wo));
+            stv(dp[ao] + b, fma(om1, f[ao], we - wo));
+        };
+        stv(dp[0] + b, fma(om1, f[0], (T)(4.0 / 9.0) * c0));
+        pair(1, 3, ux, Gx, (T)(1.0 / 9.0));
+        pair(2, 4, uy, Gy, (T)(1.0 / 9.0));
+        pair(5, 7, ux + uy, Gx + Gy, (T)(1.0 / 36.0));
+        pair(6, 8, uy - ux, Gy - Gx, (T)(1.0 / 36.0));
+        (void)fout;
+        if (!(rho > (T)0) || !(rho < (T)1e30)) *p.err = ERR_NONFINITE;
+        cr = rho; cax = ax; cay = ay;
+        return chi;
+    }
 
     // moments (rows of Eq. 15); equilibria (Eq. 14); M F closed form;
     // Eq. (17) with the host-folded factors 1 - s_k and (1 - s_k/2)
@@ -339,9 +456,6 @@ __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState
     const T Pq = pxx_s * (T)0.25;
     const T Rq = pxy_s * (T)0.25;
 
-    using S = typename Prec<P>::S;
-    const int b = j * p.nx + i;
-    S *const *dp = reinterpret_cast<S *const *>(p.dst_plane);
     stv(dp[0] + b, r9 - e_s * (T)(1.0 / 9.0) + ep_s * (T)(1.0 / 9.0));
     stv(dp[1] + b, A + X1 + Pq);
     stv(dp[2] + b, A + Y1 - Pq);
@@ -367,14 +481,18 @@ __device__ __forceinline__ bool tile_near_body(const int4 range, int i0, int j0,
     return i0 + w - 1 >= range.x && i0 <= range.y && j0 + h - 1 >= range.z && j0 <= range.w;
 }
 
-// Block-wide fixed-order reduction of the 7 FP64 sums of one tile, its
-// partial slot, the ticket, and the tail in the last tile.  Every thread
-// of the block calls it (it contains block barriers); tile (tx, ty) is the
-// tile's index in the w x h tiling.
+// Block-wide fixed-order reduction of the 7 sums of one tile (accumulator
+// type A: double, or float2 float-float), its partial slot (8 bytes per
+// sum, in type A), the ticket, and the tail in the last tile.  Every thread of the block calls
+// it (it contains block barriers); tile (tx, ty) is the tile's index in the
+// w x h tiling.
+template <typename A>
 __device__ __forceinline__ void tile_reduce(const StepParams &p, const int4 range, int tx, int ty, int w, int h,
-                                            bool any_chi_thread, double part[NPART - 1], double (*red)[NPART],
+                                            bool any_chi_thread, A part[NPART - 1], double (*red_mem)[NPART],
                                             int *s_last)
 {
+    static_assert(sizeof(A) == sizeof(double), "the shared scratch holds one A per entry");
+    A (*red)[NPART] = reinterpret_cast<A (*)[NPART]>(red_mem);
     const int nthreads = blockDim.x * blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -383,7 +501,7 @@ __device__ __forceinline__ void tile_reduce(const StepParams &p, const int4 rang
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-            for (int k = 0; k < NPART - 1; ++k) part[k] += __shfl_down_sync(0xffffffffu, part[k], off);
+            for (int k = 0; k < NPART - 1; ++k) acc_add(part[k], acc_shfl_down(part[k], off));
     }
     if (lane == 0)
 #pragma unroll
@@ -402,18 +520,21 @@ __device__ __forceinline__ void tile_reduce(const StepParams &p, const int4 rang
         return;
     }
     if (warp == 0) {
-        double v[NPART - 1];
+        A v[NPART - 1];
 #pragma unroll
-        for (int k = 0; k < NPART - 1; ++k) v[k] = lane < nwarps ? red[lane][k] : 0.0;
+        for (int k = 0; k < NPART - 1; ++k) {
+            if (lane < nwarps) v[k] = red[lane][k];
+            else acc_zero(v[k]);
+        }
 #pragma unroll
         for (int off = 4; off > 0; off >>= 1)
 #pragma unroll
-            for (int k = 0; k < NPART - 1; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+            for (int k = 0; k < NPART - 1; ++k) acc_add(v[k], acc_shfl_down(v[k], off));
         if (lane == 0) {
             const int slot = (ty - ty0) * ntx + (tx - tx0);
             double *dst = p.partials + (size_t)slot * NPART;
 #pragma unroll
-            for (int k = 0; k < NPART - 1; ++k) __stcg(dst + k, v[k]);
+            for (int k = 0; k < NPART - 1; ++k) __stcg(reinterpret_cast<A *>(dst) + k, v[k]);
             __threadfence();
             const unsigned t = atomicAdd(p.ticket, 1u);
             *s_last = (t == (unsigned)(nparts - 1));
@@ -422,9 +543,31 @@ __device__ __forceinline__ void tile_reduce(const StepParams &p, const int4 rang
     __syncthreads();
     if (*s_last && warp == 0) {
         __threadfence();
-        step_tail(p, nparts);
+        step_tail<A>(p, nparts);
     }
     __syncthreads();   // red and s_last are reused by the next tile
+}
+
+// Solid-node sums of one thread's node and the tile reduction (the part of
+// a tile's step that only blocks meeting the body run).
+template <int P>
+__device__ __forceinline__ void tile_solid_sums(const StepParams &p, const typename Prec<P>::S *fin, const int4 range,
+                                                int tx, int ty, int w, int h, bool chi, int i, int j,
+                                                typename Prec<P>::T rho, typename Prec<P>::T ax,
+                                                typename Prec<P>::T ay, double (*red)[NPART], int *s_last)
+{
+    using A = typename SumT<P>::A;
+    using V = typename SumT<P>::V;
+    A part[NPART - 1];
+#pragma unroll
+    for (int k = 0; k < NPART - 1; ++k) acc_zero(part[k]);
+    if (chi) {
+        V one[NPART - 1];
+        solid_node_terms<P>(p, fin, i, j, (V)rho, (V)ax, (V)ay, one);
+#pragma unroll
+        for (int k = 0; k < NPART - 1; ++k) acc_add(part[k], one[k]);
+    }
+    tile_reduce<A>(p, range, tx, ty, w, h, chi, part, red, s_last);
 }
 
 }  // namespace

@@ -27,12 +27,23 @@ def _members():
     return out
 
 
-@pytest.mark.parametrize("precision", ["f32", "f16", "f64"])
-def test_batch_members_match_standalone_runs(precision):
+@pytest.mark.parametrize("precision,tiles_per_block", [("f32", 0), ("f16", 0), ("f64", 0),
+                                                     ("f32", 1), ("f32", 8), ("f16", 5), ("f64", 3)])
+def test_batch_members_match_standalone_runs(precision, tiles_per_block):
+    """Branch mode (0), and tile mode with macro tiles of 1, 3, 5 and 8
+    tiles: ragged last macro rows (66, 96 and 70 rows) and the reduction
+    tiles of a body spread over several blocks."""
     import paper_1905_05110_gb300 as vp
     probs = _members()
     batch = vp.Batch(probs, precision=precision, history_capacity=256)
-    batch.set_launch(256, 1)
+    if tiles_per_block == 0:
+        batch.set_mode("branches")
+        for m in batch.members:
+            vp.vplbm_set_launch(m.ctx, vp.KERNELS["scalar48"], 256, 1)
+    else:
+        batch.set_mode("tiles")
+        batch.set_launch(256, 1, tiles_per_block)
+        assert batch.launch()[:3] == (256, 1, tiles_per_block)
     batch.init_from_problems()
     batch.step(70)   # two graphs of 32 and 6 single launches
     batch.sync()
@@ -48,7 +59,7 @@ def test_batch_members_match_standalone_runs(precision):
         assert np.array_equal(hm[:, REC["n_solid"]], ha[:, REC["n_solid"]])
         assert rel_err(hm[:, REC["fy"]], ha[:, REC["fy"]]) < 1e-4
         alone.close()
-    assert batch.launch()[2] == 70
+    assert batch.launch()[3] == 70
     batch.close()
 
 
@@ -80,6 +91,14 @@ def test_batch_rejects_members_out_of_step_and_autotunes():
     assert ei.value.status == 1
     batch.init_from_problems()
     shape = batch.autotune(4)
-    assert shape in ((256, 1), (128, 1), (128, 2), (64, 2))
+    assert shape[0] == "branches" or shape[1:] in ((256, 1, 8), (256, 1, 4), (256, 1, 16), (128, 2, 4),
+                                                   (128, 1, 8), (256, 1, 1))
+    with pytest.raises(vp.VplbmError):
+        batch.set_launch(256, 1, 0)
+    with pytest.raises(vp.VplbmError):
+        batch.set_launch(96, 1, 1)
+    assert batch.launch()[:3] == shape[1:]
+    with pytest.raises(vp.VplbmError):
+        batch.set_mode(5)
     batch.sync()
     batch.close()

@@ -25,6 +25,8 @@ BC_SETS = [
     ("velocity", "velocity", "noslip", "noslip"),
     ("zerograd", "zerograd", "velocity", "noslip"),
     ("periodic", "periodic", "velocity", "velocity"),
+    ("velocity", "zerograd", "symmetry", "symmetry"),
+    ("periodic", "periodic", "symmetry", "noslip"),
 ]
 
 ONE_STEP_TOL = {"f64": 1e-13, "f32": 2e-6, "f16": 2e-3}
@@ -365,3 +367,117 @@ def test_tma_bounded_wait_reports_timeout_and_context_survives():
     ref.init_from_problem()
     ref.step(40)
     assert np.array_equal(g.populations(), ref.populations())
+
+
+# ---- single-relaxation-time (BGK) operator of Sec. 2.1 ------------------
+
+@pytest.mark.parametrize("bcs", BC_SETS)
+@pytest.mark.parametrize("size", [(67, 45), (130, 3)])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16"])
+def test_bgk_steps_from_random_state(bcs, size, precision):
+    nx, ny = size
+    p = _box(nx, ny, bcs, seed=nx + 2 * ny)
+    p["collision"] = "bgk"
+    f0 = wl.random_populations(nx, ny, seed=13, amp=0.03, u_amp=0.05)
+    if precision != "f64":
+        gpu, _ = make_pair(p, precision, init=None, f0=f0)
+        f0 = gpu.populations()
+    gpu, orc = make_pair(p, precision, f0=f0)
+    for n in (1, 2):
+        gpu.step(1)
+        orc.step(1)
+        tol = ONE_STEP_TOL[precision] * (3 if n == 2 else 1)
+        assert dev_err(gpu.populations(), orc.populations()) < tol
+        gr, gx, gy = gpu.fields()
+        orr, ox, oy = orc.fields()
+        assert rel_err(gr - 1, orr - 1) < 10 * tol
+        assert rel_err(gx, ox) < 10 * tol and rel_err(gy, oy) < 10 * tol
+
+
+@pytest.mark.parametrize("motion", ["imposed", "free"])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_bgk_body_runs_match_oracle(motion, precision):
+    nx, ny = 97, 70
+    body = moving_bodies(nx, ny)[motion]
+    p = _box(nx, ny, ("velocity", "zerograd", "noslip", "noslip"), seed=7, body=body, tau=0.62)
+    p["collision"] = "bgk"
+    p["s"] = [1.0 / 0.62] * 9
+    p["bc"]["west"] = {"kind": "velocity", "u": (0.05, 0.0)}
+    gpu, orc = make_pair(p, precision)
+    steps = 150
+    gpu.step(steps)
+    orc.step(steps)
+    tol = RUN_TOL[precision]
+    assert dev_err(gpu.populations(), orc.populations()) < tol
+    hg, ho = gpu.history(), orc.history()
+    assert np.array_equal(hg[:, REC["n_solid"]], ho[:, REC["n_solid"]])
+    ftol = 1e-10 if precision == "f64" else 1e-3
+    for key in ("fx", "fy", "torque", "fpen_x", "fpen_y", "tpen"):
+        assert rel_err(hg[:, REC[key]], ho[:, REC[key]]) < ftol, key
+
+
+def test_bgk_register_budgets_agree_and_unsupported_paths_refuse():
+    import paper_1905_05110_gb300 as vp
+    nx, ny = 300, 96
+    body = moving_bodies(nx, ny)["imposed"]
+    p = _box(nx, ny, ("velocity", "zerograd", "noslip", "noslip"), seed=9, body=body)
+    p["collision"] = "bgk"
+    p["bc"]["west"] = {"kind": "velocity", "u": (0.04, 0.0)}
+    out = []
+    for kern, bx, by in (("scalar", 256, 1), ("scalar48", 128, 2), ("scalar40", 64, 4)):
+        sim = vp.Simulation(p, precision="f32", history_capacity=128)
+        sim.set_launch(kern, bx, by)
+        sim.init_from_problem()
+        sim.step(40)
+        out.append((sim.populations(), sim.history()))
+        if kern == "scalar":
+            with pytest.raises(vp.VplbmError) as ei:
+                sim.set_launch("tma")
+            assert ei.value.status == 6
+            with pytest.raises(vp.VplbmError) as ei:
+                sim.adjoint(10, 5)
+            assert ei.value.status == 6
+        sim.close()
+    for pops, hist in out[1:]:
+        assert np.array_equal(pops, out[0][0])
+        assert np.array_equal(hist[:, REC["n_solid"]], out[0][1][:, REC["n_solid"]])
+        assert rel_err(hist[:, REC["fy"]], out[0][1][:, REC["fy"]]) < 1e-5
+
+
+# ---- symmetry walls (the oscillating-cylinder setup of Sec. 3.1) ----------
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_symmetry_channel_with_oscillating_disk_matches_oracle(precision):
+    nx, ny = 120, 50
+    body = moving_bodies(nx, ny)["imposed"]
+    p = wl.mixed_bc_box(nx, ny, seed=12, west="velocity", east="zerograd", south="symmetry",
+                        north="symmetry", tau=0.56, body=body)   # the paper's rates for tau = 0.56
+    p["bc"]["west"] = {"kind": "velocity", "u": (0.048, 0.0)}
+    p["init"] = {"rho": 1.0, "u": (0.048, 0.0)}
+    gpu, orc = make_pair(p, precision)
+    gpu.step(120)
+    orc.step(120)
+    tol = RUN_TOL[precision]
+    assert dev_err(gpu.populations(), orc.populations()) < tol
+    hg, ho = gpu.history(), orc.history()
+    assert np.array_equal(hg[:, REC["n_solid"]], ho[:, REC["n_solid"]])
+    ftol = 1e-10 if precision == "f64" else 1e-3
+    for key in ("fx", "fy", "torque"):
+        assert rel_err(hg[:, REC[key]], ho[:, REC[key]]) < ftol, key
+
+
+def test_symmetry_rejected_where_not_defined():
+    import paper_1905_05110_gb300 as vp
+    p = _box(40, 20, ("velocity", "zerograd", "symmetry", "symmetry"), seed=1)
+    p["bc"]["east"] = {"kind": "symmetry"}
+    with pytest.raises(vp.VplbmError) as ei:
+        vp.Simulation(p, precision="f32")
+    assert ei.value.status == 6
+    p = _box(40, 20, ("velocity", "zerograd", "symmetry", "symmetry"), seed=1,
+             body=moving_bodies(40, 20)["imposed"])
+    sim = vp.Simulation(p, precision="f64", history_capacity=64)
+    sim.init_from_problem()
+    with pytest.raises(vp.VplbmError) as ei:
+        sim.adjoint(10, 5)
+    assert ei.value.status == 6
+    sim.close()
