@@ -23,7 +23,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
 
 Q = 9
-BC_KINDS = {"periodic": 0, "noslip": 1, "velocity": 2, "zerograd": 3, "symmetry": 4}
+BC_KINDS = {"periodic": 0, "noslip": 1, "velocity": 2, "zerograd": 3, "symmetry": 4, "convective": 5}
 MOTIONS = {"fixed": 0, "imposed": 1, "free": 2}
 SIDES = ("west", "east", "south", "north")
 RECORD_FIELDS = ("t", "fx", "fy", "torque", "cd", "cl", "x", "y", "theta",

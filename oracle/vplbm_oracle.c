@@ -134,7 +134,8 @@ static void setup_constants(void)
 
 /* ---- public descriptors (ctypes mirrors them) ------------------------ */
 
-enum { ORC_PERIODIC = 0, ORC_NOSLIP = 1, ORC_VELOCITY = 2, ORC_ZEROGRAD = 3, ORC_SYMMETRY = 4 };
+enum { ORC_PERIODIC = 0, ORC_NOSLIP = 1, ORC_VELOCITY = 2, ORC_ZEROGRAD = 3, ORC_SYMMETRY = 4,
+       ORC_CONVECTIVE = 5 };
 enum { ORC_WEST = 0, ORC_EAST = 1, ORC_SOUTH = 2, ORC_NORTH = 3 };
 enum { ORC_FIXED = 0, ORC_IMPOSED = 1, ORC_FREE = 2 };
 enum { ORC_MRT = 0, ORC_BGK = 1 };
@@ -182,6 +183,8 @@ typedef struct {
     double q_center;       /* centre of the imposed sinusoid */
     orc_record *hist;
     long long hist_cap;
+    double *conv_prev;     /* convective outlet: pulled f_a(nx-1, j) of the previous step, [a][j] */
+    double *conv_next;
 } orc_sim;
 
 /* ---- small building blocks ------------------------------------------ */
@@ -338,6 +341,13 @@ static double pulled(const orc_sim *s, int a, int i, int j)
             si = (si + nx) % nx;
         } else if (kind == ORC_ZEROGRAD) {
             return FT(a, i, sj);
+        } else if (kind == ORC_CONVECTIVE) {
+            /* advection of f_a out of the domain, d f/dt + U d f/dx = 0,
+             * implicit in time and upwind in space between the outlet node
+             * and its inner neighbour (whose pulled value is the
+             * zero-gradient one): f(N, n+1) = (f(N, n) + U f(N-1, n+1)) / (1 + U) */
+            const double U = s->lat.bc_u[side][0];
+            return (s->conv_prev[(size_t)a * ny + j] + U * FT(a, i, sj)) / (1.0 + U);
         } else {
             double val = FT(OPP[a], i, j);
             if (kind == ORC_VELOCITY) {
@@ -435,6 +445,9 @@ orc_sim *orc_create(const orc_lattice *lat, const orc_body *body, long long hist
     setup_constants();
     if (lat->nx < 2 || lat->ny < 2) return NULL;
     if (lat->bc_kind[ORC_WEST] == ORC_SYMMETRY || lat->bc_kind[ORC_EAST] == ORC_SYMMETRY) return NULL;   /* y walls only */
+    for (int side = 0; side < 4; ++side)
+        if (lat->bc_kind[side] == ORC_CONVECTIVE && (side != ORC_EAST || !(lat->bc_u[side][0] >= 0.0)))
+            return NULL;   /* east outlet only, convective velocity >= 0 */
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     if (!s) return NULL;
     s->lat = *lat;
@@ -454,6 +467,8 @@ orc_sim *orc_create(const orc_lattice *lat, const orc_body *body, long long hist
     size_t n = (size_t)Q * lat->nx * lat->ny;
     s->ft = (double *)calloc(n, sizeof(double));
     s->fn = (double *)calloc(n, sizeof(double));
+    s->conv_prev = (double *)calloc((size_t)Q * lat->ny, sizeof(double));
+    s->conv_next = (double *)calloc((size_t)Q * lat->ny, sizeof(double));
     s->hist_cap = hist_cap > 0 ? hist_cap : 1;
     s->hist = (orc_record *)calloc((size_t)s->hist_cap, sizeof(orc_record));
     if (!s->ft || !s->fn || !s->hist) { orc_free(s); return NULL; }
@@ -469,8 +484,10 @@ void orc_free(orc_sim *s)
 {
     if (!s) return;
     for (int side = 0; side < 4; ++side) { free(s->prof_ux[side]); free(s->prof_uy[side]); }
-    free(s->ft); free(s->fn); free(s->hist); free(s);
+    free(s->ft); free(s->fn); free(s->hist); free(s->conv_prev); free(s->conv_next); free(s);
 }
+
+static void reset_outlet(orc_sim *s);
 
 /* State = equilibrium (Eq. 11) of the given fields (NULL: rho0, 0). */
 void orc_init_equilibrium(orc_sim *s, const double *rho, const double *ux, const double *uy)
@@ -483,11 +500,22 @@ void orc_init_equilibrium(orc_sim *s, const double *rho, const double *ux, const
             equilibrium(rho ? rho[k] : s->lat.rho0, ux ? ux[k] : 0.0, uy ? uy[k] : 0.0, feq);
             for (int a = 0; a < Q; ++a) s->ft[((size_t)a * ny + j) * nx + i] = feq[a];
         }
+    reset_outlet(s);
+}
+
+/* The convective outlet's "previous step" values at step 0 are the given
+ * populations of the outlet column. */
+static void reset_outlet(orc_sim *s)
+{
+    const int nx = s->lat.nx, ny = s->lat.ny;
+    for (int a = 0; a < Q; ++a)
+        for (int j = 0; j < ny; ++j) s->conv_prev[(size_t)a * ny + j] = s->ft[((size_t)a * ny + j) * nx + nx - 1];
 }
 
 void orc_set_populations(orc_sim *s, const double *f)
 {
     memcpy(s->ft, f, sizeof(double) * (size_t)Q * s->lat.nx * s->lat.ny);
+    reset_outlet(s);
 }
 
 void orc_get_populations(const orc_sim *s, double *f)
@@ -521,6 +549,8 @@ static void one_step(orc_sim *s)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             node_macro(s, i, j, &ns);
+            if (i == nx - 1)
+                for (int a = 0; a < Q; ++a) s->conv_next[(size_t)a * ny + j] = ns.f[a];
             double Gx = ns.rho * (s->lat.gx + ns.ax);
             double Gy = ns.rho * (s->lat.gy + ns.ay);
             if (s->lat.collision == ORC_BGK)
@@ -549,6 +579,7 @@ static void one_step(orc_sim *s)
             }
         }
     double *t = s->ft; s->ft = s->fn; s->fn = t;
+    t = s->conv_prev; s->conv_prev = s->conv_next; s->conv_next = t;
 
     orc_record *r = &s->hist[s->step % s->hist_cap];
     r->t = (double)s->step;
@@ -788,6 +819,8 @@ int orc_adjoint(orc_sim *s, const orc_adjoint_desc *d, double *grad, double out_
     const long long N = d->nsteps;
     if (s->body.present && s->body.motion == ORC_FREE) return -1;
     if (s->lat.collision != ORC_MRT) return -1;
+    for (int side = 0; side < 4; ++side)
+        if (s->lat.bc_kind[side] == ORC_CONVECTIVE) return -1;
     if (N < 1 || d->w0 < 0 || d->w0 >= N || s->hist_cap < s->step + N) return -1;
     const size_t nf = (size_t)Q * nx * ny;
     const long long step0 = s->step;

@@ -467,6 +467,65 @@ def test_symmetry_walls_conserve_mass_and_tangential_momentum():
         px0 = px1
 
 
+def _outlet_channel(nx, ny, east, u_in=0.04, seed=5):
+    p = wl.periodic_box(nx, ny, rates=wl.random_rates(seed))
+    p["bc"]["west"] = {"kind": "velocity", "u": (u_in, 0.0)}
+    p["bc"]["east"] = east
+    p["bc"]["south"] = {"kind": "noslip", "u": (0.0, 0.0)}
+    p["bc"]["north"] = {"kind": "noslip", "u": (0.0, 0.0)}
+    return p
+
+
+def test_convective_outlet_keeps_a_uniform_stream():
+    # The outflow rule is an average of the outlet's previous value and its
+    # zero-gradient value with weights that sum to one: a uniform stream
+    # through a channel (periodic y) is an exact steady state.
+    nx, ny, u = 12, 6, 0.04
+    p = _outlet_channel(nx, ny, {"kind": "convective", "u": (0.7, 0.0)}, u_in=u)
+    for side in ("south", "north"):
+        p["bc"][side] = {"kind": "periodic"}
+    sim = oracle.OracleSim(p)
+    shape = (ny, nx)
+    sim.init_equilibrium(np.ones(shape), np.full(shape, u), np.zeros(shape))
+    f0 = sim.populations()
+    sim.step(40)
+    assert np.max(np.abs(sim.populations() - f0)) < 1e-15
+
+
+def test_convective_outlet_limits():
+    # U -> infinity: the outlet value is its inner neighbour's, i.e. the
+    # zero-gradient rule.  U = 0: nothing is advected, the inward populations
+    # pulled at the outlet keep the values given at step 0 for ever.  The two
+    # limits fix both weights of the rule and that "previous" means the
+    # previous step's pulled value (not the stored post-collision one).
+    nx, ny = 14, 7
+    f0 = wl.random_populations(nx, ny, seed=31, amp=0.03, u_amp=0.05)
+    fast = oracle.OracleSim(_outlet_channel(nx, ny, {"kind": "convective", "u": (1e13, 0.0)}))
+    zg = oracle.OracleSim(_outlet_channel(nx, ny, {"kind": "zerograd"}))
+    fast.set_populations(f0)
+    zg.set_populations(f0)
+    fast.step(20)
+    zg.step(20)
+    assert np.max(np.abs(fast.populations() - zg.populations())) < 1e-11
+
+    c, _, _, _ = oracle.constants()
+    inward = [a for a in range(9) if c[a, 0] == -1]
+    frozen = oracle.OracleSim(_outlet_channel(nx, ny, {"kind": "convective", "u": (0.0, 0.0)}))
+    frozen.set_populations(f0)
+    frozen.step(6)
+    st = frozen.populations()
+    # a run restarted from the step-6 state takes the outlet's previous
+    # values from that state; the frozen run still uses f0's
+    restart = oracle.OracleSim(_outlet_channel(nx, ny, {"kind": "convective", "u": (0.0, 0.0)}))
+    restart.set_populations(st)
+    rho_f, _, _ = frozen.fields()
+    rho_r, _, _ = restart.fields()
+    expect = sum(f0[a][:, -1] - st[a][:, -1] for a in inward)
+    # corner nodes pull their diagonal inward populations from the walls
+    assert np.allclose((rho_f - rho_r)[1:-1, -1], expect[1:-1], rtol=0, atol=1e-15)
+    assert np.max(np.abs((rho_f - rho_r)[:, :-1])) == 0.0
+
+
 def test_rk4_free_fall_is_exact():
     body = {"radius": 1.0, "x": 0, "y": 0, "motion": "free", "mass": 3.0, "inertia": 5.0,
             "f_ext": (0.2, -0.5, 0.1), "dof_mask": 7}
