@@ -67,12 +67,20 @@ typedef enum { VPLBM_F64 = 0, VPLBM_F32_DEV = 1, VPLBM_F16_DEV = 2 } vplbm_preci
  *  SYMMETRY  south/north only: specular reflection at the half-way wall
  *            (u.n = 0, no shear stress), f_a(i, j) = f~_a*(i - c_ax, j) with
  *            a* the mirror image of a (c_ay -> -c_ay); where i - c_ax lies
- *            outside a non-periodic x edge, f~_a*(i, j).
+ *            outside a non-periodic x edge, f~_a*(i, j);
+ *  CONVECTIVE east only: outflow advected at the speed U = ux of this edge
+ *            (>= 0), df/dt + U df/dx = 0 implicit in time and upwind in
+ *            space: f_a(N, n+1) = (f_a(N, n) + U f_a(N-1, n+1)) / (1 + U),
+ *            where f_a(N-1, n+1) is the zero-gradient value and f_a(N, n)
+ *            the value the rule gave at the previous step (at the first
+ *            step after the populations are set: their outlet column).
+ *            The previous values are part of the state (checkpoints keep
+ *            them).  Not with vplbm_step_noalloc or the adjoint.
  * When the source node of a pull lies outside in y, the south/north rule
  * applies, otherwise the west/east rule. */
 typedef enum {
     VPLBM_BC_PERIODIC = 0, VPLBM_BC_NOSLIP = 1, VPLBM_BC_VELOCITY = 2, VPLBM_BC_ZEROGRAD = 3,
-    VPLBM_BC_SYMMETRY = 4
+    VPLBM_BC_SYMMETRY = 4, VPLBM_BC_CONVECTIVE = 5
 } vplbm_bc_kind;
 
 enum { VPLBM_WEST = 0, VPLBM_EAST = 1, VPLBM_SOUTH = 2, VPLBM_NORTH = 3 };
@@ -149,7 +157,7 @@ typedef struct {
     size_t body_state;    /* bytes of the body-state pair */
     size_t partials;      /* bytes of the per-block reduction scratch */
     size_t history;       /* bytes of the history ring */
-    size_t profiles;      /* bytes of the wall-velocity profiles */
+    size_t profiles;      /* bytes of the wall-velocity profiles and the outlet state */
     size_t control;       /* bytes of the ticket / error words */
 } vplbm_buffer_sizes;
 

@@ -38,7 +38,7 @@ STATUS = {0: "VPLBM_OK", 1: "VPLBM_EINVAL", 2: "VPLBM_ENOMEM", 3: "VPLBM_ECUDA",
           4: "VPLBM_ENONFINITE", 5: "VPLBM_ETIMEOUT", 6: "VPLBM_EUNSUPPORTED",
           7: "VPLBM_ERANGE", 8: "VPLBM_EIO"}
 PRECISIONS = {"f64": 0, "f32": 1, "f16": 2}
-BC_KINDS = {"periodic": 0, "noslip": 1, "velocity": 2, "zerograd": 3, "symmetry": 4}
+BC_KINDS = {"periodic": 0, "noslip": 1, "velocity": 2, "zerograd": 3, "symmetry": 4, "convective": 5}
 MOTIONS = {"fixed": 0, "imposed": 1, "free": 2}
 SIDES = ("west", "east", "south", "north")
 RECORD_FIELDS = ("t", "fx", "fy", "torque", "cd", "cl", "x", "y", "theta",

@@ -319,6 +319,7 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
     if (c->collision != VPLBM_COLLISION_MRT) return aerr(VPLBM_EUNSUPPORTED, "the adjoint differentiates the MRT operator only");
     for (int e = VPLBM_SOUTH; e <= VPLBM_NORTH; ++e)
         if (c->base.bc[e] == VPLBM_BC_SYMMETRY) return aerr(VPLBM_EUNSUPPORTED, "the adjoint has no symmetry-wall rule");
+    if (c->base.bc[VPLBM_EAST] == VPLBM_BC_CONVECTIVE) return aerr(VPLBM_EUNSUPPORTED, "the adjoint has no convective-outlet rule");
     const long long N = d->nsteps;
     if (N < 1 || d->window_start < 0 || d->window_start >= N) return aerr(VPLBM_EINVAL, "need 0 <= window_start < nsteps");
     if (c->hist_cap < N) return aerr(VPLBM_EINVAL, "history capacity %lld < nsteps %lld", c->hist_cap, N);

@@ -38,7 +38,7 @@ vplbm_status fail(vplbm_status st, const char *fmt, ...)
 
 constexpr size_t ALIGN = 256;
 constexpr int GRAPH_STEPS = 32;   // steps per captured graph (even)
-constexpr char CKPT_MAGIC[8] = {'V', 'P', 'L', 'B', 'M', 'C', 'K', '1'};
+constexpr char CKPT_MAGIC[8] = {'V', 'P', 'L', 'B', 'M', 'C', 'K', '2'};
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -112,9 +112,12 @@ vplbm_status check_lattice(const vplbm_lattice_desc *lat)
         return fail(VPLBM_EINVAL, "unknown collision operator %d", lat->collision);
     for (int s = 0; s < 4; ++s) {
         const int k = lat->bc[s].kind;
-        if (k < VPLBM_BC_PERIODIC || k > VPLBM_BC_SYMMETRY) return fail(VPLBM_EINVAL, "edge %d: unknown boundary kind %d", s, k);
+        if (k < VPLBM_BC_PERIODIC || k > VPLBM_BC_CONVECTIVE) return fail(VPLBM_EINVAL, "edge %d: unknown boundary kind %d", s, k);
         if (k == VPLBM_BC_ZEROGRAD && s >= VPLBM_SOUTH) return fail(VPLBM_EUNSUPPORTED, "zero-gradient is supported on west/east edges only");
         if (k == VPLBM_BC_SYMMETRY && s < VPLBM_SOUTH) return fail(VPLBM_EUNSUPPORTED, "symmetry is supported on south/north edges only");
+        if (k == VPLBM_BC_CONVECTIVE && s != VPLBM_EAST) return fail(VPLBM_EUNSUPPORTED, "the convective outlet is supported on the east edge only");
+        if (k == VPLBM_BC_CONVECTIVE && !(lat->bc[s].ux >= 0.0 && lat->bc[s].ux < 1e6))
+            return fail(VPLBM_EINVAL, "convective velocity (east ux) must be >= 0 and finite");
     }
     if ((lat->bc[VPLBM_WEST].kind == VPLBM_BC_PERIODIC) != (lat->bc[VPLBM_EAST].kind == VPLBM_BC_PERIODIC))
         return fail(VPLBM_EINVAL, "west and east must both be periodic or neither");
@@ -159,7 +162,10 @@ void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long 
     s->body_state = round_up(2 * sizeof(BodyState), ALIGN);
     s->partials = round_up((size_t)parts * NPART * sizeof(double), ALIGN);
     s->history = round_up((size_t)cap * sizeof(vplbm_record), ALIGN);
-    s->profiles = round_up((size_t)8 * (lat->nx > lat->ny ? lat->nx : lat->ny) * sizeof(double), ALIGN);
+    // FP64 profiles, then their FP32 copies: [side][comp][maxlen] each; then
+    // the convective outlet state: [parity][3][ny] 8-byte slots
+    s->profiles = round_up((size_t)8 * (lat->nx > lat->ny ? lat->nx : lat->ny) * (sizeof(double) + sizeof(float)), ALIGN) +
+                  round_up((size_t)6 * lat->ny * sizeof(double), ALIGN);
     s->control = sizeof(Control);
     if (ps_out) *ps_out = ps;
     if (parts_out) *parts_out = parts;
@@ -187,6 +193,9 @@ StepParams params_for(const vplbm_ctx *c, long long step)
     p.bs_in = c->bs + par;
     p.bs_out = c->bs + (par ^ 1);
     set_planes(p, (int)elem_size(c->precision));
+    double *ob = static_cast<double *>(c->outlet);
+    p.conv_in = ob + (size_t)par * 3 * c->ny;
+    p.conv_out = ob + (size_t)(par ^ 1) * 3 * c->ny;
     return p;
 }
 
@@ -255,6 +264,7 @@ void setup_tma(vplbm_ctx *c)
 // Reset step counter, body state and control word (after a new state).
 vplbm_status reset_run(vplbm_ctx *c)
 {
+    if (c->base.bc[VPLBM_EAST] == VPLBM_BC_CONVECTIVE) CUDA_TRY(launch_outlet_reset(c->precision, params_for(c, 0), c->stream));
     BodyState s[2] = {initial_state(c), initial_state(c)};
     CUDA_TRY(cudaMemcpyAsync(c->bs, s, sizeof s, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaMemsetAsync(c->ctrl, 0, sizeof(Control), c->stream));
@@ -297,25 +307,44 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     fold_consts(p.pcd, lat->s, lat->gx, lat->gy);
     // wall velocity profiles: [side][comp][maxlen]
     const int maxlen = lat->nx > lat->ny ? lat->nx : lat->ny;
-    std::vector<double> prof((size_t)8 * maxlen, 0.0);
+    const size_t nprof = (size_t)8 * maxlen;
+    std::vector<double> prof(nprof, 0.0);
+    std::vector<float> proff(nprof, 0.f);
+    float *proff_dev = reinterpret_cast<float *>(c->prof + nprof);
     for (int s = 0; s < 4; ++s) {
         p.bc[s] = lat->bc[s].kind;
         p.wall_u0[s][0] = lat->bc[s].ux;
         p.wall_u0[s][1] = lat->bc[s].uy;
+        p.wall_u0f[s][0] = (float)lat->bc[s].ux;
+        p.wall_u0f[s][1] = (float)lat->bc[s].uy;
         const int len = s < 2 ? lat->ny : lat->nx;
         const double *src[2] = {lat->bc[s].ux_profile, lat->bc[s].uy_profile};
         for (int comp = 0; comp < 2; ++comp) {
             p.wall_prof[s][comp] = nullptr;
+            p.wall_proff[s][comp] = nullptr;
             if (src[comp] && lat->bc[s].kind == VPLBM_BC_VELOCITY) {
+                const size_t off = (size_t)(s * 2 + comp) * maxlen;
                 for (int k = 0; k < len; ++k) {
                     if (!isfinite(src[comp][k])) return fail(VPLBM_EINVAL, "edge %d: wall velocity not finite", s);
-                    prof[(size_t)(s * 2 + comp) * maxlen + k] = src[comp][k];
+                    prof[off + k] = src[comp][k];
+                    proff[off + k] = (float)src[comp][k];
                 }
-                p.wall_prof[s][comp] = c->prof + (size_t)(s * 2 + comp) * maxlen;
+                p.wall_prof[s][comp] = c->prof + off;
+                p.wall_proff[s][comp] = proff_dev + off;
             }
         }
     }
-    CUDA_TRY(cudaMemcpyAsync(c->prof, prof.data(), prof.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->prof, prof.data(), nprof * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    c->outlet = reinterpret_cast<char *>(c->prof) + round_up(nprof * (sizeof(double) + sizeof(float)), ALIGN);
+    CUDA_TRY(cudaMemsetAsync(c->outlet, 0, (size_t)6 * lat->ny * sizeof(double), c->stream));
+    {
+        const double U = lat->bc[VPLBM_EAST].kind == VPLBM_BC_CONVECTIVE ? lat->bc[VPLBM_EAST].ux : 0.0;
+        p.conv_k1 = 1.0 / (1.0 + U);
+        p.conv_k2 = U / (1.0 + U);
+        p.conv_k1f = (float)p.conv_k1;
+        p.conv_k2f = (float)p.conv_k2;
+    }
+    CUDA_TRY(cudaMemcpyAsync(proff_dev, proff.data(), nprof * sizeof(float), cudaMemcpyHostToDevice, c->stream));
 
     DevBody &b = p.body;
     memset(&b, 0, sizeof b);
@@ -334,6 +363,8 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
         b.q_center = body->motion == VPLBM_MOTION_IMPOSED ? q0[body->axis] - body->amp * sin(body->phase) : 0.0;
         b.mass = body->mass;
         b.inertia = body->inertia;
+        b.inv_mass = body->mass > 0.0 ? 1.0 / body->mass : 0.0;
+        b.inv_inertia = body->inertia > 0.0 ? 1.0 / body->inertia : 0.0;
         for (int d = 0; d < 3; ++d) {
             b.damp[d] = body->damp[d];
             b.stiff[d] = body->stiff[d];
@@ -341,6 +372,7 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
             b.f_ext[d] = body->f_ext[d];
         }
         b.qref = 0.5 * lat->rho0 * body->d_ref * body->u_ref * body->u_ref;
+        b.inv_qref = b.qref > 0.0 ? 1.0 / b.qref : 0.0;
     }
     p.partials = c->partials;
     p.max_parts = c->max_parts;
@@ -775,8 +807,13 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
     vplbm_status st = VPLBM_OK;
     float best = 1e30f;
     int best_kernel = -1, best_bx = 0, best_by = 0;
+    std::vector<double> save_outlet((size_t)3 * c->ny);
+    void *outlet0 = const_cast<void *>(params_for(c, nstep0).conv_in);
     auto restore = [&]() -> cudaError_t {
         cudaError_t e = cudaMemcpyAsync(c->f[nstep0 & 1], save_f, c->pop_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(outlet0, save_outlet.data(), save_outlet.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c->hist, save_h, hbytes, cudaMemcpyDeviceToDevice, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c->bs, save_bs, sizeof save_bs, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -787,6 +824,8 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
         if (cudaMemcpyAsync(save_f, c->f[nstep0 & 1], c->pop_bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
             cudaMemcpyAsync(save_h, c->hist, hbytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
             cudaMemcpyAsync(save_bs, c->bs, sizeof save_bs, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaMemcpyAsync(save_outlet.data(), outlet0, save_outlet.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream) != cudaSuccess ||
             cudaStreamSynchronize(c->stream) != cudaSuccess ||
             cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
             st = fail(VPLBM_ECUDA, "autotune setup failed");
@@ -848,7 +887,10 @@ vplbm_status vplbm_save(vplbm_ctx *c, const char *path)
     try {
         std::vector<char> raw(c->pop_bytes);
         std::vector<vplbm_record> hist((size_t)c->hist_cap);
+        std::vector<double> outlet((size_t)3 * c->ny);
         BodyState bs;
+        CUDA_TRY(cudaMemcpyAsync(outlet.data(), params_for(c, c->nstep).conv_in, outlet.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaMemcpyAsync(raw.data(), c->f[c->nstep & 1], c->pop_bytes, cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaMemcpyAsync(hist.data(), c->hist, hist.size() * sizeof(vplbm_record), cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaMemcpyAsync(&bs, c->bs + (c->nstep & 1), sizeof bs, cudaMemcpyDeviceToHost, c->stream));
@@ -861,7 +903,8 @@ vplbm_status vplbm_save(vplbm_ctx *c, const char *path)
         if (!fp) return fail(VPLBM_EIO, "cannot open %s for writing", path);
         bool ok = fwrite(&h, sizeof h, 1, fp) == 1 && fwrite(&bs, sizeof bs, 1, fp) == 1 &&
                   fwrite(raw.data(), 1, raw.size(), fp) == raw.size() &&
-                  fwrite(hist.data(), sizeof(vplbm_record), hist.size(), fp) == hist.size();
+                  fwrite(hist.data(), sizeof(vplbm_record), hist.size(), fp) == hist.size() &&
+                  fwrite(outlet.data(), sizeof(double), outlet.size(), fp) == outlet.size();
         ok = (fclose(fp) == 0) && ok;
         if (!ok) return fail(VPLBM_EIO, "write to %s failed", path);
     } catch (const std::bad_alloc &) {
@@ -889,11 +932,15 @@ vplbm_status vplbm_load(vplbm_ctx *c, const char *path)
         }
         std::vector<char> raw(c->pop_bytes);
         std::vector<vplbm_record> hist((size_t)c->hist_cap);
+        std::vector<double> outlet((size_t)3 * c->ny);
         ok = fread(raw.data(), 1, raw.size(), fp) == raw.size() &&
-             fread(hist.data(), sizeof(vplbm_record), hist.size(), fp) == hist.size();
+             fread(hist.data(), sizeof(vplbm_record), hist.size(), fp) == hist.size() &&
+             fread(outlet.data(), sizeof(double), outlet.size(), fp) == outlet.size();
         fclose(fp);
         if (!ok) return fail(VPLBM_EIO, "%s is truncated", path);
         const int par = (int)(h.nstep & 1);
+        CUDA_TRY(cudaMemcpyAsync(const_cast<void *>(params_for(c, h.nstep).conv_in), outlet.data(),
+                                 outlet.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(cudaMemcpyAsync(c->f[par], raw.data(), raw.size(), cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(cudaMemcpyAsync(c->hist, hist.data(), hist.size() * sizeof(vplbm_record), cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(cudaMemcpyAsync(c->bs + par, &bs, sizeof bs, cudaMemcpyHostToDevice, c->stream));

@@ -126,6 +126,8 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const 
     for (int s = 0; s < 4; ++s)
         if (lat->bc[s].ux_profile || lat->bc[s].uy_profile)
             return report_error(VPLBM_EUNSUPPORTED, "vplbm_step_noalloc takes uniform wall velocities only");
+    if (lat->bc[VPLBM_EAST].kind == VPLBM_BC_CONVECTIVE)
+        return report_error(VPLBM_EUNSUPPORTED, "vplbm_step_noalloc has no outlet state (convective outlet)");
     const int present = body ? 1 : 0;
     const double radius = body ? body->radius : 0.0;
     const long long parts = max_reduction_blocks(lat->nx, lat->ny, radius, present, NOALLOC_BX, NOALLOC_BY);
@@ -167,7 +169,10 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const 
         p.bc[s] = lat->bc[s].kind;
         p.wall_u0[s][0] = lat->bc[s].ux;
         p.wall_u0[s][1] = lat->bc[s].uy;
+        p.wall_u0f[s][0] = (float)lat->bc[s].ux;
+        p.wall_u0f[s][1] = (float)lat->bc[s].uy;
         p.wall_prof[s][0] = p.wall_prof[s][1] = nullptr;
+        p.wall_proff[s][0] = p.wall_proff[s][1] = nullptr;
     }
     DevBody &b = p.body;
     b.present = present;
@@ -185,6 +190,8 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const 
         b.q_center = body->motion == VPLBM_MOTION_IMPOSED ? q0[body->axis] - body->amp * sin(body->phase) : 0.0;
         b.mass = body->mass;
         b.inertia = body->inertia;
+        b.inv_mass = body->mass > 0.0 ? 1.0 / body->mass : 0.0;
+        b.inv_inertia = body->inertia > 0.0 ? 1.0 / body->inertia : 0.0;
         for (int d = 0; d < 3; ++d) {
             b.damp[d] = body->damp[d];
             b.stiff[d] = body->stiff[d];
@@ -192,6 +199,7 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const 
             b.f_ext[d] = body->f_ext[d];
         }
         b.qref = 0.5 * lat->rho0 * body->d_ref * body->u_ref * body->u_ref;
+        b.inv_qref = b.qref > 0.0 ? 1.0 / b.qref : 0.0;
     }
     p.partials = scratch->partials;
     p.max_parts = NOALLOC_MAX_PARTS;

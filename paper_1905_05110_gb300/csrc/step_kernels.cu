@@ -37,7 +37,7 @@ namespace {
 // tile_y); p may live in shared memory (batched launch).
 template <int P, int COLL>
 __device__ __forceinline__ void scalar_tile(const StepParams &p, int tile_x, int tile_y, double (*red)[NPART],
-                                            int *s_last)
+                                            float (*rows)[256], int *s_last)
 {
     using S = typename Prec<P>::S;
     using T = typename Prec<P>::T;
@@ -53,8 +53,12 @@ __device__ __forceinline__ void scalar_tile(const StepParams &p, int tile_x, int
 
     // streaming loads first: nothing below them waits on the pose
     T f[NQ];
-    if (block_interior) pull_all<P, true>(p, fin, i, j, f);
-    else if (inside) pull_all<P>(p, fin, i, j, f);
+    if (block_interior) {
+        pull_all<P, true>(p, fin, i, j, f);
+    } else if (inside) {
+        pull_all<P>(p, fin, i, j, f);
+        if (i == p.nx - 1 && p.bc[VPLBM_EAST] == VPLBM_BC_CONVECTIVE) record_outlet<P>(p, j, f);
+    }
 
     const int4 range = __ldg(reinterpret_cast<const int4 *>(&bs->ilo));   // ilo, ihi, jlo, jhi
     const bool part_block = tile_near_body(range, bi0, bj0, blockDim.x, blockDim.y, tile_x == 0 && tile_y == 0);
@@ -63,7 +67,8 @@ __device__ __forceinline__ void scalar_tile(const StepParams &p, int tile_x, int
     if (inside)
         chi = node_update<P, COLL>(p, bs, part_block && range.x <= range.y, i, j, f, fout, cr, cax, cay);
     if (!part_block) return;   // uniform over the block
-    tile_solid_sums<P>(p, fin, range, tile_x, tile_y, blockDim.x, blockDim.y, chi, i, j, cr, cax, cay, red, s_last);
+    tile_solid_sums<P>(p, fin, range, tile_x, tile_y, blockDim.x, blockDim.y, chi, i, j, cr, cax, cay, red, rows,
+                       s_last);
 }
 
 // MINB: blocks of 256 threads per SM the register budget is sized for
@@ -78,10 +83,11 @@ template <int P, int MINB, int COLL>
 __global__ void __launch_bounds__(256, MINB) vp_mrt_step(const StepParams p)
 {
     __shared__ double red[8][NPART];
+    __shared__ float rows[NPART - 1][256];
     __shared__ int s_last;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    scalar_tile<P, COLL>(p, blockIdx.x, blockIdx.y, red, &s_last);
+    scalar_tile<P, COLL>(p, blockIdx.x, blockIdx.y, red, rows, &s_last);
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0 && prescribed_motion(p))
         advance_prescribed(p);
 }
@@ -96,6 +102,7 @@ template <int P, int COLL>
 __global__ void __launch_bounds__(256, 5) vp_mrt_step_batch(const BatchLaunch bl)
 {
     __shared__ double red[8][NPART];
+    __shared__ float rows[NPART - 1][256];
     __shared__ int s_last;
     __shared__ __align__(16) StepParams sp;
     __shared__ int s_member, s_local;
@@ -121,7 +128,7 @@ __global__ void __launch_bounds__(256, 5) vp_mrt_step_batch(const BatchLaunch bl
     const int nty = (sp.ny + blockDim.y - 1) / blockDim.y;
     const int tx = s_local % ntx, ty0 = (s_local / ntx) * bl.rows;
 #pragma unroll 1
-    for (int r = 0; r < bl.rows && ty0 + r < nty; ++r) scalar_tile<P, COLL>(sp, tx, ty0 + r, red, &s_last);
+    for (int r = 0; r < bl.rows && ty0 + r < nty; ++r) scalar_tile<P, COLL>(sp, tx, ty0 + r, red, rows, &s_last);
     if (s_local == 0 && tid == 0 && prescribed_motion(sp)) advance_prescribed(sp);
 }
 
@@ -149,6 +156,23 @@ __global__ void init_equilibrium_kernel(const StepParams p, const double *rho_f,
         else val = w_of(a) * rho * (1.0 + poly);
         stv(fout + a * p.ps + k, (typename Prec<P>::T)val);
     }
+}
+
+// ---- convective outlet: previous values := the state's outlet column -----
+
+template <int P>
+__global__ void outlet_reset_kernel(const StepParams p)
+{
+    using S = typename Prec<P>::S;
+    using T = typename Prec<P>::T;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= p.ny) return;
+    const S *fin = static_cast<const S *>(p.fin);
+    T *out = static_cast<T *>(const_cast<void *>(p.conv_in));
+    const long long b = (long long)j * p.nx + p.nx - 1;
+    out[outlet_slot(3) * p.ny + j] = ldv(fin + 3 * p.ps + b);
+    out[outlet_slot(6) * p.ny + j] = ldv(fin + 6 * p.ps + b);
+    out[outlet_slot(7) * p.ny + j] = ldv(fin + 7 * p.ps + b);
 }
 
 // ---- macroscopic fields of the current step (Eqs. 19-22) ---------------
@@ -270,6 +294,18 @@ cudaError_t launch_init_equilibrium(int precision, const StepParams &p, const do
     case VPLBM_F64: init_equilibrium_kernel<VPLBM_F64><<<grid, block, 0, stream>>>(p, rho_dev, ux_dev, uy_dev); break;
     case VPLBM_F32_DEV: init_equilibrium_kernel<VPLBM_F32_DEV><<<grid, block, 0, stream>>>(p, rho_dev, ux_dev, uy_dev); break;
     case VPLBM_F16_DEV: init_equilibrium_kernel<VPLBM_F16_DEV><<<grid, block, 0, stream>>>(p, rho_dev, ux_dev, uy_dev); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_outlet_reset(int precision, const StepParams &p, cudaStream_t stream)
+{
+    const int grid = (p.ny + 127) / 128;
+    switch (precision) {
+    case VPLBM_F64: outlet_reset_kernel<VPLBM_F64><<<grid, 128, 0, stream>>>(p); break;
+    case VPLBM_F32_DEV: outlet_reset_kernel<VPLBM_F32_DEV><<<grid, 128, 0, stream>>>(p); break;
+    case VPLBM_F16_DEV: outlet_reset_kernel<VPLBM_F16_DEV><<<grid, 128, 0, stream>>>(p); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

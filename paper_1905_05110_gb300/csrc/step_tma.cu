@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(256, 4) vp_mrt_step_tma(const StepParams p, co
                     }
                 } else {
                     pull_all<P>(p, fin, i, j, f);
+                    if (i == p.nx - 1 && p.bc[VPLBM_EAST] == VPLBM_BC_CONVECTIVE) record_outlet<P>(p, j, f);
                 }
                 T cr = 0, cax = 0, cay = 0;
                 const bool chi = node_update<P>(p, bs, near && range.x <= range.y, i, j, f, fout, cr, cax, cay);

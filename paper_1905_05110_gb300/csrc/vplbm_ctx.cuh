@@ -27,6 +27,7 @@ struct vplbm_ctx {
     vplbm_record *hist = nullptr;
     long long hist_cap = 0;
     double *prof = nullptr;
+    void *outlet = nullptr;               // convective outlet state, 2 parities x 3 x ny (8-byte slots)
     void *owned = nullptr;                // single allocation when the library owns memory
     long long nstep = 0;
     int kernel = vplbm::KERNEL_SCALAR;    // KERNEL_SCALAR / _48 / _40 / KERNEL_TMA

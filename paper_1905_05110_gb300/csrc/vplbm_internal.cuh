@@ -47,8 +47,10 @@ struct DevBody {
     double radius, r2;
     double amp, freq, phase, q_center;
     double mass, inertia;
+    double inv_mass, inv_inertia;   // 1 / mass, 1 / inertia (free motion), host-computed
     double damp[3], stiff[3], q0[3], f_ext[3];
     double qref;       // rho0 d_ref u_ref^2 / 2 (0: no C_D / C_L)
+    double inv_qref;   // 1 / qref (0 when qref is 0)
 };
 
 // Number of doubles per block partial: fpen_x, fpen_y, tpen, fh_x, fh_y,
@@ -94,6 +96,17 @@ struct StepParams {
     int bc[4];
     double wall_u0[4][2];
     const double *wall_prof[4][2];
+    // FP32 copies for the FP32/FP16 kernels' wall terms
+    float wall_u0f[4][2];
+    const float *wall_proff[4][2];
+    // convective outlet (east): the previous step's inward pulled values
+    // [3][ny] (a = 3, 6, 7; FP64 for the FP64 kernel, FP32 otherwise), read
+    // from conv_in and written to conv_out (parity buffers);
+    // f = k1 f_prev + k2 f_zero-gradient, k1 = 1/(1+U), k2 = U/(1+U)
+    const void *conv_in;
+    void *conv_out;
+    double conv_k1, conv_k2;
+    float conv_k1f, conv_k2f;
     DevBody body;
     const void *fin;
     void *fout;
@@ -182,6 +195,8 @@ cudaError_t launch_step_batch(int precision, const BatchLaunch &bl, int total_ti
 cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb = 4);
 cudaError_t launch_init_equilibrium(int precision, const StepParams &p, const double *rho_dev,
                                     const double *ux_dev, const double *uy_dev, cudaStream_t stream);
+// Convective outlet: previous values := the outlet column of p.fin (into p.conv_in).
+cudaError_t launch_outlet_reset(int precision, const StepParams &p, cudaStream_t stream);
 cudaError_t launch_fields(int precision, const StepParams &p, double *rho_dev, double *ux_dev,
                           double *uy_dev, cudaStream_t stream);
 

@@ -30,6 +30,8 @@ __host__ __device__ constexpr int cx_of(int a) { return a == 1 || a == 5 || a ==
 __host__ __device__ constexpr int cy_of(int a) { return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0); }
 __host__ __device__ constexpr int opp_of(int a) { return a == 0 ? 0 : (a <= 4 ? ((a + 1) % 4) + 1 : ((a - 5 + 2) % 4) + 5); }
 __host__ __device__ constexpr int miry_of(int a) { return a == 2 ? 4 : a == 4 ? 2 : a == 5 ? 8 : a == 8 ? 5 : a == 6 ? 7 : a == 7 ? 6 : a; }
+// Slot of an inward population of the east outlet (c_ax = -1: a = 3, 6, 7).
+__host__ __device__ constexpr int outlet_slot(int a) { return a == 3 ? 0 : (a == 6 ? 1 : 2); }
 __host__ __device__ constexpr double w_of(int a) { return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
 
 static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 && opp_of(4) == 2, "opp axis");
@@ -52,6 +54,29 @@ __device__ __forceinline__ double wall_u(const StepParams &p, int side, int comp
     const double *prof = p.wall_prof[side][comp];
     return prof ? prof[k] : p.wall_u0[side][comp];
 }
+__device__ __forceinline__ float wall_uf(const StepParams &p, int side, int comp, int k)
+{
+    const float *prof = p.wall_proff[side][comp];
+    return prof ? prof[k] : p.wall_u0f[side][comp];
+}
+
+// Moving-wall term 6 w_a rho0 (c_a . u_w) of the velocity rule, in the
+// kernel's arithmetic type (FP32 for the FP32/FP16 kernels: no FP64 on the
+// edge path).
+template <typename T>
+__device__ __forceinline__ T wall_term(const StepParams &p, int a, int side, int k);
+template <>
+__device__ __forceinline__ double wall_term<double>(const StepParams &p, int a, int side, int k)
+{
+    const double cu = cx_of(a) * wall_u(p, side, 0, k) + cy_of(a) * wall_u(p, side, 1, k);
+    return 6.0 * w_of(a) * p.rho0 * cu;
+}
+template <>
+__device__ __forceinline__ float wall_term<float>(const StepParams &p, int a, int side, int k)
+{
+    const float cu = (float)cx_of(a) * wall_uf(p, side, 0, k) + (float)cy_of(a) * wall_uf(p, side, 1, k);
+    return ((float)(6.0 * w_of(a)) * p.rho0f) * cu;
+}
 
 // Pull of population a into edge node (i, j), with the boundary rules.
 template <int P>
@@ -73,10 +98,7 @@ __device__ typename Prec<P>::T pull_edge(const StepParams &p, const typename Pre
             return ldv(fin + miry_of(a) * ps + (long long)j * nx + mi);
         } else {
             T val = ldv(fin + opp_of(a) * ps + (long long)j * nx + i);
-            if (kind == VPLBM_BC_VELOCITY) {
-                double cu = cx_of(a) * wall_u(p, side, 0, i) + cy_of(a) * wall_u(p, side, 1, i);
-                val += (T)(6.0 * w_of(a) * p.rho0 * cu);
-            }
+            if (kind == VPLBM_BC_VELOCITY) val += wall_term<T>(p, a, side, i);
             return val;
         }
     }
@@ -87,12 +109,13 @@ __device__ typename Prec<P>::T pull_edge(const StepParams &p, const typename Pre
             si = si < 0 ? si + nx : si - nx;
         } else if (kind == VPLBM_BC_ZEROGRAD) {
             return ldv(fin + a * ps + (long long)sj * nx + i);
+        } else if (kind == VPLBM_BC_CONVECTIVE) {   // east only (checked on the host)
+            const T z = ldv(fin + a * ps + (long long)sj * nx + i);
+            const T prev = static_cast<const T *>(p.conv_in)[outlet_slot(a) * ny + j];
+            return par<T>(p.conv_k1, p.conv_k1f) * prev + par<T>(p.conv_k2, p.conv_k2f) * z;
         } else {
             T val = ldv(fin + opp_of(a) * ps + (long long)j * nx + i);
-            if (kind == VPLBM_BC_VELOCITY) {
-                double cu = cx_of(a) * wall_u(p, side, 0, j) + cy_of(a) * wall_u(p, side, 1, j);
-                val += (T)(6.0 * w_of(a) * p.rho0 * cu);
-            }
+            if (kind == VPLBM_BC_VELOCITY) val += wall_term<T>(p, a, side, j);
             return val;
         }
     }
@@ -116,6 +139,18 @@ __device__ __forceinline__ void pull_all(const StepParams &p, const typename Pre
     }
 }
 
+// Convective outlet: keep this step's pulled inward populations of an
+// outlet node for the next step's rule.
+template <int P>
+__device__ __forceinline__ void record_outlet(const StepParams &p, int j, const typename Prec<P>::T f[NQ])
+{
+    using T = typename Prec<P>::T;
+    T *out = static_cast<T *>(p.conv_out);
+    out[outlet_slot(3) * p.ny + j] = f[3];
+    out[outlet_slot(6) * p.ny + j] = f[6];
+    out[outlet_slot(7) * p.ny + j] = f[7];
+}
+
 // Exact chi predicate of Eq. (2) in FP64 without contraction.
 __device__ __forceinline__ bool chi_exact(int i, int j, double xg, double yg, double r2)
 {
@@ -130,8 +165,8 @@ __device__ __forceinline__ bool chi_exact(int i, int j, double xg, double yg, do
 __device__ void body_acc(const DevBody &b, const double F[3], const double q[3], const double v[3], double acc[3])
 {
     for (int d = 0; d < 3; ++d) {
-        const double m = d < 2 ? b.mass : b.inertia;
-        acc[d] = (F[d] + b.f_ext[d] - b.damp[d] * v[d] - b.stiff[d] * (q[d] - b.q0[d])) / m;
+        const double inv_m = d < 2 ? b.inv_mass : b.inv_inertia;   // a multiply: FP64 divides are long on GB300
+        acc[d] = (F[d] + b.f_ext[d] - b.damp[d] * v[d] - b.stiff[d] * (q[d] - b.q0[d])) * inv_m;
     }
 }
 
@@ -228,13 +263,36 @@ template <typename A>
 __device__ __noinline__ void step_tail(const StepParams &p, int nparts)
 {
     const int lane = threadIdx.x & 31;
+    BodyState cur;
+    if (lane == 0) cur = *p.bs_in;   // issued before the partial loads
     A acc[NPART - 1];
 #pragma unroll
     for (int k = 0; k < NPART - 1; ++k) acc_zero(acc[k]);
-    for (int s = lane; s < nparts; s += 32) {
-        const A *src = reinterpret_cast<const A *>(p.partials + (size_t)s * NPART);
+    // two partials per lane are loaded together (one memory round trip up
+    // to 64 partials), then added in lane order
+    for (int s0 = 0; s0 < nparts; s0 += 64) {
+        const int sa = s0 + lane, sb = s0 + 32 + lane;
+        A va[NPART - 1], vb[NPART - 1];
 #pragma unroll
-        for (int k = 0; k < NPART - 1; ++k) acc_add(acc[k], __ldcg(src + k));
+        for (int k = 0; k < NPART - 1; ++k) {
+            acc_zero(va[k]);
+            acc_zero(vb[k]);
+        }
+        if (sa < nparts) {
+            const A *src = reinterpret_cast<const A *>(p.partials + (size_t)sa * NPART);
+#pragma unroll
+            for (int k = 0; k < NPART - 1; ++k) va[k] = __ldcg(src + k);
+        }
+        if (sb < nparts) {
+            const A *src = reinterpret_cast<const A *>(p.partials + (size_t)sb * NPART);
+#pragma unroll
+            for (int k = 0; k < NPART - 1; ++k) vb[k] = __ldcg(src + k);
+        }
+#pragma unroll
+        for (int k = 0; k < NPART - 1; ++k) {
+            acc_add(acc[k], va[k]);
+            acc_add(acc[k], vb[k]);
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
@@ -245,13 +303,12 @@ __device__ __noinline__ void step_tail(const StepParams &p, int nparts)
 #pragma unroll
     for (int k = 0; k < NPART - 1; ++k) sum[k] = acc_value(acc[k]);
 
-    const BodyState cur = *p.bs_in;
     const double Fh[3] = {sum[3], sum[4], sum[5]};
     vplbm_record r;
     r.t = (double)cur.step;
     r.fx = Fh[0]; r.fy = Fh[1]; r.torque = Fh[2];
-    r.cd = p.body.qref > 0 ? Fh[0] / p.body.qref : 0.0;
-    r.cl = p.body.qref > 0 ? Fh[1] / p.body.qref : 0.0;
+    r.cd = Fh[0] * p.body.inv_qref;
+    r.cl = Fh[1] * p.body.inv_qref;
     r.x = cur.q[0]; r.y = cur.q[1]; r.theta = cur.q[2];
     r.vx = cur.v[0]; r.vy = cur.v[1]; r.omega = cur.v[2];
     r.fpen_x = sum[0]; r.fpen_y = sum[1]; r.tpen = sum[2];
@@ -481,11 +538,47 @@ __device__ __forceinline__ bool tile_near_body(const int4 range, int i0, int j0,
     return i0 + w - 1 >= range.x && i0 <= range.y && j0 + h - 1 >= range.z && j0 <= range.w;
 }
 
-// Block-wide fixed-order reduction of the 7 sums of one tile (accumulator
-// type A: double, or float2 float-float), its partial slot (8 bytes per
-// sum, in type A), the ticket, and the tail in the last tile.  Every thread of the block calls
-// it (it contains block barriers); tile (tx, ty) is the tile's index in the
-// w x h tiling.
+// Partial slot of tile (tx, ty) of a w x h tiling, the ticket, and the
+// tail in the last tile to publish.  sums (shared memory) holds the tile's
+// 7 sums in accumulator type A; every thread of the block calls it (it
+// contains block barriers).
+template <typename A>
+__device__ __forceinline__ void publish_tile(const StepParams &p, const int4 range, int tx, int ty, int w, int h,
+                                             const A *sums, int *s_last)
+{
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;
+    if (range.x <= range.y) {
+        tx0 = range.x / w; tx1 = range.y / w;
+        ty0 = range.z / h; ty1 = range.w / h;
+    }
+    const int ntx = tx1 - tx0 + 1;
+    const int nparts = ntx * (ty1 - ty0 + 1);
+    if (nparts > p.max_parts) {          // cannot happen for a finite pose; never overrun
+        if (tid == 0) *p.err |= ERR_INTERNAL;
+        __syncthreads();
+        return;
+    }
+    if (tid == 0) {
+        const int slot = (ty - ty0) * ntx + (tx - tx0);
+        A *dst = reinterpret_cast<A *>(p.partials + (size_t)slot * NPART);
+#pragma unroll
+        for (int k = 0; k < NPART - 1; ++k) __stcg(dst + k, sums[k]);
+        __threadfence();
+        const unsigned t = atomicAdd(p.ticket, 1u);
+        *s_last = (t == (unsigned)(nparts - 1));
+    }
+    __syncthreads();
+    if (*s_last && tid < 32) {
+        __threadfence();
+        step_tail<A>(p, nparts);
+    }
+    __syncthreads();   // the shared scratch and s_last are reused by the next tile
+}
+
+// Block-wide fixed-order reduction of per-thread accumulators (type A:
+// double, or float2 float-float), then publish_tile.  Used where a thread
+// has accumulated several nodes (TMA-staged kernel).
 template <typename A>
 __device__ __forceinline__ void tile_reduce(const StepParams &p, const int4 range, int tx, int ty, int w, int h,
                                             bool any_chi_thread, A part[NPART - 1], double (*red_mem)[NPART],
@@ -507,18 +600,6 @@ __device__ __forceinline__ void tile_reduce(const StepParams &p, const int4 rang
 #pragma unroll
         for (int k = 0; k < NPART - 1; ++k) red[warp][k] = part[k];
     __syncthreads();
-    int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;
-    if (range.x <= range.y) {
-        tx0 = range.x / w; tx1 = range.y / w;
-        ty0 = range.z / h; ty1 = range.w / h;
-    }
-    const int ntx = tx1 - tx0 + 1;
-    const int nparts = ntx * (ty1 - ty0 + 1);
-    if (nparts > p.max_parts) {          // cannot happen for a finite pose; never overrun
-        if (tid == 0) *p.err |= ERR_INTERNAL;
-        __syncthreads();
-        return;
-    }
     if (warp == 0) {
         A v[NPART - 1];
 #pragma unroll
@@ -530,44 +611,63 @@ __device__ __forceinline__ void tile_reduce(const StepParams &p, const int4 rang
         for (int off = 4; off > 0; off >>= 1)
 #pragma unroll
             for (int k = 0; k < NPART - 1; ++k) acc_add(v[k], acc_shfl_down(v[k], off));
-        if (lane == 0) {
-            const int slot = (ty - ty0) * ntx + (tx - tx0);
-            double *dst = p.partials + (size_t)slot * NPART;
+        __syncwarp();
+        if (lane == 0)
 #pragma unroll
-            for (int k = 0; k < NPART - 1; ++k) __stcg(reinterpret_cast<A *>(dst) + k, v[k]);
-            __threadfence();
-            const unsigned t = atomicAdd(p.ticket, 1u);
-            *s_last = (t == (unsigned)(nparts - 1));
-        }
+            for (int k = 0; k < NPART - 1; ++k) red[0][k] = v[k];
     }
     __syncthreads();
-    if (*s_last && warp == 0) {
-        __threadfence();
-        step_tail<A>(p, nparts);
-    }
-    __syncthreads();   // red and s_last are reused by the next tile
+    publish_tile<A>(p, range, tx, ty, w, h, red[0], s_last);
 }
 
-// Solid-node sums of one thread's node and the tile reduction (the part of
-// a tile's step that only blocks meeting the body run).
+// Solid-node sums of a tile where every thread owns one node: the terms go
+// to shared memory as rows [quantity][thread], and warp q reduces row q
+// (8 float-float adds per lane in thread order, then a shuffle tree), so
+// the 7 quantities are summed by 7 warps at once instead of one after the
+// other by every warp.  rows holds 7 x 256 floats.
 template <int P>
 __device__ __forceinline__ void tile_solid_sums(const StepParams &p, const typename Prec<P>::S *fin, const int4 range,
                                                 int tx, int ty, int w, int h, bool chi, int i, int j,
                                                 typename Prec<P>::T rho, typename Prec<P>::T ax,
-                                                typename Prec<P>::T ay, double (*red)[NPART], int *s_last)
+                                                typename Prec<P>::T ay, double (*red)[NPART], float (*rows)[256],
+                                                int *s_last)
 {
     using A = typename SumT<P>::A;
     using V = typename SumT<P>::V;
-    A part[NPART - 1];
+    if constexpr (P == VPLBM_F64) {
+        (void)rows;
+        A part[NPART - 1];
 #pragma unroll
-    for (int k = 0; k < NPART - 1; ++k) acc_zero(part[k]);
-    if (chi) {
-        V one[NPART - 1];
-        solid_node_terms<P>(p, fin, i, j, (V)rho, (V)ax, (V)ay, one);
+        for (int k = 0; k < NPART - 1; ++k) acc_zero(part[k]);
+        if (chi) {
+            V one[NPART - 1];
+            solid_node_terms<P>(p, fin, i, j, (V)rho, (V)ax, (V)ay, one);
 #pragma unroll
-        for (int k = 0; k < NPART - 1; ++k) acc_add(part[k], one[k]);
+            for (int k = 0; k < NPART - 1; ++k) acc_add(part[k], one[k]);
+        }
+        tile_reduce<A>(p, range, tx, ty, w, h, chi, part, red, s_last);
+    } else {
+        const int nthreads = blockDim.x * blockDim.y;
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
+        float one[NPART - 1];
+#pragma unroll
+        for (int k = 0; k < NPART - 1; ++k) one[k] = 0.f;
+        if (chi) solid_node_terms<P>(p, fin, i, j, (float)rho, (float)ax, (float)ay, one);
+#pragma unroll
+        for (int k = 0; k < NPART - 1; ++k) rows[k][tid] = one[k];
+        __syncthreads();
+        float2 *sums = reinterpret_cast<float2 *>(red[0]);
+        for (int q = warp; q < NPART - 1; q += nwarps) {
+            float2 a = make_float2(0.f, 0.f);
+            for (int t = lane; t < nthreads; t += 32) acc_add(a, rows[q][t]);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc_add(a, acc_shfl_down(a, off));
+            if (lane == 0) sums[q] = a;
+        }
+        __syncthreads();
+        publish_tile<float2>(p, range, tx, ty, w, h, sums, s_last);
     }
-    tile_reduce<A>(p, range, tx, ty, w, h, chi, part, red, s_last);
 }
 
 }  // namespace

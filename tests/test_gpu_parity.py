@@ -27,6 +27,8 @@ BC_SETS = [
     ("periodic", "periodic", "velocity", "velocity"),
     ("velocity", "zerograd", "symmetry", "symmetry"),
     ("periodic", "periodic", "symmetry", "noslip"),
+    ("velocity", "convective", "noslip", "symmetry"),
+    ("noslip", "convective", "velocity", "velocity"),
 ]
 
 ONE_STEP_TOL = {"f64": 1e-13, "f32": 2e-6, "f16": 2e-3}
@@ -40,8 +42,11 @@ def _library(gpu_library):
 
 def _box(nx, ny, bcs, seed, body=None, tau=0.7):
     w, e, s, n = bcs
-    return wl.mixed_bc_box(nx, ny, seed=seed, west=w, east=e, south=s, north=n, tau=tau, body=body,
-                           rates=wl.random_rates(seed))
+    p = wl.mixed_bc_box(nx, ny, seed=seed, west=w, east=e, south=s, north=n, tau=tau, body=body,
+                        rates=wl.random_rates(seed))
+    if e == "convective":
+        p["bc"]["east"] = {"kind": "convective", "u": (0.31, 0.0)}
+    return p
 
 
 @pytest.mark.parametrize("bcs", BC_SETS)
@@ -475,6 +480,85 @@ def test_symmetry_rejected_where_not_defined():
     assert ei.value.status == 6
     p = _box(40, 20, ("velocity", "zerograd", "symmetry", "symmetry"), seed=1,
              body=moving_bodies(40, 20)["imposed"])
+    sim = vp.Simulation(p, precision="f64", history_capacity=64)
+    sim.init_from_problem()
+    with pytest.raises(vp.VplbmError) as ei:
+        sim.adjoint(10, 5)
+    assert ei.value.status == 6
+    sim.close()
+
+
+# ---- convective outlet (the oscillating-cylinder setup of Sec. 3.1) -------
+
+def _paper_channel(nx, ny, body):
+    """Velocity inlet, convective outlet, symmetry walls, as in Sec. 3.1."""
+    p = wl.mixed_bc_box(nx, ny, seed=3, west="velocity", east="convective", south="symmetry",
+                        north="symmetry", tau=0.56, body=body)
+    p["bc"]["west"] = {"kind": "velocity", "u": (0.048, 0.0)}
+    p["bc"]["east"] = {"kind": "convective", "u": (0.048, 0.0)}
+    p["init"] = {"rho": 1.0, "u": (0.048, 0.0)}
+    return p
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16"])
+def test_paper_channel_with_cosine_oscillation_matches_oracle(precision):
+    nx, ny = 130, 52
+    r = 6.0
+    body = {"radius": r, "x": 40.0, "y": 26.0, "motion": "imposed", "axis": 1, "amp": r / 2,
+            "freq": 0.004, "phase": np.pi / 2, "u_ref": 0.048, "d_ref": 2 * r}
+    p = _paper_channel(nx, ny, body)
+    gpu, orc = make_pair(p, precision)
+    gpu.step(150)
+    orc.step(150)
+    tol = RUN_TOL[precision]
+    assert dev_err(gpu.populations(), orc.populations()) < tol
+    gr, gx, gy = gpu.fields()
+    orr, ox, oy = orc.fields()
+    assert rel_err(gx, ox) < tol and rel_err(gy, oy) < tol
+    hg, ho = gpu.history(), orc.history()
+    assert np.array_equal(hg[:, REC["n_solid"]], ho[:, REC["n_solid"]])
+    if precision != "f16":
+        ftol = 1e-10 if precision == "f64" else 1e-3
+        for key in ("fx", "fy", "torque"):
+            assert rel_err(hg[:, REC[key]], ho[:, REC[key]]) < ftol, key
+
+
+def test_convective_outlet_state_survives_checkpoint_and_autotune(tmp_path):
+    import paper_1905_05110_gb300 as vp
+    p = _paper_channel(300, 40, None)
+    a = vp.Simulation(p, precision="f32", history_capacity=128)
+    a.init_from_problem()
+    a.step(17)
+    a.autotune(4)           # trial steps are undone, outlet state included
+    assert a.nstep == 17
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    a.step(30)
+    b = vp.Simulation(p, precision="f32", history_capacity=128)
+    b.load(path)
+    b.set_launch(*a.launch())
+    b.step(30)
+    assert np.array_equal(a.populations(), b.populations())
+    c = vp.Simulation(p, precision="f32", history_capacity=128)
+    c.set_launch(*a.launch())
+    c.init_from_problem()
+    c.step(47)
+    assert np.array_equal(a.populations(), c.populations())
+
+
+def test_convective_outlet_rejected_where_not_defined():
+    import paper_1905_05110_gb300 as vp
+    p = _paper_channel(60, 20, moving_bodies(60, 20)["imposed"])
+    p["bc"]["west"] = {"kind": "convective", "u": (0.1, 0.0)}
+    with pytest.raises(vp.VplbmError) as ei:
+        vp.Simulation(p, precision="f32")
+    assert ei.value.status == 6
+    p = _paper_channel(60, 20, moving_bodies(60, 20)["imposed"])
+    p["bc"]["east"] = {"kind": "convective", "u": (-0.1, 0.0)}
+    with pytest.raises(vp.VplbmError) as ei:
+        vp.Simulation(p, precision="f32")
+    assert ei.value.status == 1
+    p = _paper_channel(60, 20, moving_bodies(60, 20)["imposed"])
     sim = vp.Simulation(p, precision="f64", history_capacity=64)
     sim.init_from_problem()
     with pytest.raises(vp.VplbmError) as ei:

@@ -109,3 +109,9 @@ def test_noalloc_rejects_what_it_cannot_hold(gpu_library):
         vp.vplbm_step_noalloc(vp.lattice_desc(prof, "f32"), vp.body_desc(prof["body"]), [1 << 20, 1 << 21],
                               1 << 22, None, 0, 1, 0)
     assert ei.value.status == 6
+    conv = wl.oscillating_disk(nx=256, ny=128, diameter=16, x_c=60)
+    conv["bc"]["east"] = {"kind": "convective", "u": (0.04, 0.0)}
+    with pytest.raises(vp.VplbmError) as ei:
+        vp.vplbm_step_noalloc(vp.lattice_desc(conv, "f32"), vp.body_desc(conv["body"]), [1 << 20, 1 << 21],
+                              1 << 22, None, 0, 1, 0)
+    assert ei.value.status == 6 and "outlet" in str(ei.value)
