@@ -34,10 +34,11 @@ namespace {
 // ---- the fused step ----------------------------------------------------
 
 // One tile of the step: blockDim.x x blockDim.y nodes at tile (tile_x,
-// tile_y); p may live in shared memory (batched launch).
+// tile_y); p may live in shared memory (batched launch).  sums: this block
+// also reduces the tile's solid-node sums (and may run the tail).
 template <int P, int COLL>
 __device__ __forceinline__ void scalar_tile(const StepParams &p, int tile_x, int tile_y, double (*red)[NPART],
-                                            float (*rows)[256], int *s_last)
+                                            float (*rows)[256], int *s_last, bool sums)
 {
     using S = typename Prec<P>::S;
     using T = typename Prec<P>::T;
@@ -66,7 +67,7 @@ __device__ __forceinline__ void scalar_tile(const StepParams &p, int tile_x, int
     T cr = 0, cax = 0, cay = 0;   // kept for the solid-node sums (converted there)
     if (inside)
         chi = node_update<P, COLL>(p, bs, part_block && range.x <= range.y, i, j, f, fout, cr, cax, cay);
-    if (!part_block) return;   // uniform over the block
+    if (!part_block || !sums) return;   // uniform over the block
     tile_solid_sums<P>(p, fin, range, tile_x, tile_y, blockDim.x, blockDim.y, chi, i, j, cr, cax, cay, red, rows,
                        s_last);
 }
@@ -77,8 +78,17 @@ __device__ __forceinline__ void scalar_tile(const StepParams &p, int tile_x, int
 // Launched with programmatic dependent launch: every block lets the next
 // step's grid start launching at once, and waits (in hardware) until the
 // previous step's grid has completed and its writes are visible before it
-// reads anything, so the next launch overlaps the end of this one.  The
-// first block also computes the next pose of a body on a prescribed path.
+// reads anything, so the next launch overlaps the end of this one.
+//
+// The grid's first rows hold p.nbody body blocks, the rest one block per
+// tile.  The body blocks are dispatched first: they take the
+// tiles that meet the body's node range, reduce the solid-node sums and
+// run the tail, so the step's FP64 critical path starts at the beginning
+// of the grid instead of wherever the body sits in it.  The row-major
+// blocks update every tile without the sums (a body tile is updated twice,
+// to identical values) and never wait on the pose before their streaming
+// loads.  Body block 0 also computes the next pose of a body on a
+// prescribed path.
 template <int P, int MINB, int COLL>
 __global__ void __launch_bounds__(256, MINB) vp_mrt_step(const StepParams p)
 {
@@ -87,9 +97,32 @@ __global__ void __launch_bounds__(256, MINB) vp_mrt_step(const StepParams p)
     __shared__ int s_last;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    scalar_tile<P, COLL>(p, blockIdx.x, blockIdx.y, red, rows, &s_last);
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0 && prescribed_motion(p))
-        advance_prescribed(p);
+    const int nbr = p.nbody_rows;
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;   // body block index (first rows)
+    int tx = -1, ty = 0;
+    bool sums = false;
+    if ((int)blockIdx.y < nbr) {
+        if (b >= p.nbody) return;
+        const int4 range = __ldg(reinterpret_cast<const int4 *>(&p.bs_in->ilo));
+        int tx0 = 0, ty0 = 0, rw = 1, nrect = 1;   // no solid node: tile (0, 0) runs the tail
+        if (range.x <= range.y) {
+            tx0 = range.x / (int)blockDim.x;
+            ty0 = range.z / (int)blockDim.y;
+            rw = range.y / (int)blockDim.x - tx0 + 1;
+            nrect = rw * (range.w / (int)blockDim.y - ty0 + 1);
+        }
+        if (b < nrect) {
+            tx = tx0 + b % rw;
+            ty = ty0 + b / rw;
+            sums = true;
+        }
+        if (b == 0 && nrect > p.nbody && threadIdx.x == 0 && threadIdx.y == 0) *p.err |= ERR_INTERNAL;
+    } else {
+        tx = blockIdx.x;
+        ty = blockIdx.y - nbr;
+    }
+    if (tx >= 0) scalar_tile<P, COLL>(p, tx, ty, red, rows, &s_last, sums);
+    if (b == 0 && threadIdx.x == 0 && threadIdx.y == 0 && prescribed_motion(p)) advance_prescribed(p);
 }
 
 // Every member of a batch in one launch: block b runs macro tile b of the
@@ -128,7 +161,7 @@ __global__ void __launch_bounds__(256, 5) vp_mrt_step_batch(const BatchLaunch bl
     const int nty = (sp.ny + blockDim.y - 1) / blockDim.y;
     const int tx = s_local % ntx, ty0 = (s_local / ntx) * bl.rows;
 #pragma unroll 1
-    for (int r = 0; r < bl.rows && ty0 + r < nty; ++r) scalar_tile<P, COLL>(sp, tx, ty0 + r, red, rows, &s_last);
+    for (int r = 0; r < bl.rows && ty0 + r < nty; ++r) scalar_tile<P, COLL>(sp, tx, ty0 + r, red, rows, &s_last, true);
     if (s_local == 0 && tid == 0 && prescribed_motion(sp)) advance_prescribed(sp);
 }
 
@@ -213,10 +246,15 @@ __global__ void fields_kernel(const StepParams p, double *rho_o, double *ux_o, d
 }
 
 template <int P>
-cudaError_t launch_step_t(const StepParams &p, int bx, int by, int minb, cudaStream_t stream)
+cudaError_t launch_step_t(const StepParams &p0, int bx, int by, int minb, cudaStream_t stream)
 {
+    StepParams p = p0;
+    p.nbody = (int)max_reduction_blocks(p.nx, p.ny, p.body.radius, p.body.present, bx, by);
+    const int ntx = (p.nx + bx - 1) / bx, nty = (p.ny + by - 1) / by;
+    const int nbr = (p.nbody + ntx - 1) / ntx;
+    p.nbody_rows = nbr;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((p.nx + bx - 1) / bx, (p.ny + by - 1) / by);
+    cfg.gridDim = dim3(ntx, nty + nbr);
     cfg.blockDim = dim3(bx, by);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = stream;

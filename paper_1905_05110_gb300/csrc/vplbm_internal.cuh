@@ -125,6 +125,12 @@ struct StepParams {
     long long hist_cap;
     unsigned tx_extra;            // test hook: bytes the first TMA stage waits for in vain
     int collision;                // vplbm_collision: picks the kernel instantiation on the host
+    // body blocks of a scalar launch: blocks 0 .. nbody-1 take the tiles
+    // that meet the body (and the tail); the others take every tile in
+    // row-major order without the solid-node sums.  Set by the launcher,
+    // with the number of grid rows they occupy.
+    int nbody;
+    int nbody_rows;
 };
 
 // Error bits latched in the control word.
