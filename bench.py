@@ -54,6 +54,8 @@ def workload(name: str) -> dict:
         return wl.oscillating_disk()
     if name == "sedimenting_1024x4096":
         return wl.sedimenting_disk()
+    if name == "paper_cylinder_1230x410":
+        return wl.paper_oscillating_cylinder()
     if name == "channel_256x128":
         return wl.channel_fixed_disk()
     raise SystemExit(f"unknown workload {name}")
@@ -312,6 +314,8 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_compare and rank == 0:
         compare["batched"] = run_batched(args, torch, stream)
         compare["adjoint"] = run_adjoint(args, torch, compare.get("f64"))
+        compare["sedimenting_disk"] = run_other_workload("sedimenting_1024x4096", 8000, torch, stream)
+        compare["paper_oscillating_cylinder"] = run_other_workload("paper_cylinder_1230x410", 40000, torch, stream)
 
     base = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -332,6 +336,28 @@ def run_ours(args, rank, world, local_rank):
     sim.close()
 
 
+def run_other_workload(name, steps, torch, stream):
+    """FP32 rate of another workload (free body / the paper's own setup),
+    with the mean C_D and RMS C_L of the second half of the run."""
+    import paper_1905_05110_gb300 as vp
+    p = workload(name)
+    nodes = p["nx"] * p["ny"]
+    sim = vp.Simulation(p, precision="f32", history_capacity=steps + 64, stream=stream)
+    sim.init_from_problem()
+    launch = sim.autotune(8)
+    t = time_device(sim, steps, stream, torch)
+    sim.sync()
+    h = sim.history(0, steps)
+    half = steps // 2
+    out = {"workload": p["name"], "mlups": nodes * steps / t / 1e6, "steps": steps, "launch": list(launch),
+           "mean_cd_2nd_half": float(h[half:, 4].mean()), "rms_cl_2nd_half": float(np.sqrt((h[half:, 5] ** 2).mean()))}
+    if p["body"]["motion"] == "free":
+        out["final_pose"] = [float(v) for v in h[-1, 6:9]]
+        out["final_velocity"] = [float(v) for v in h[-1, 9:12]]
+    sim.close()
+    return out
+
+
 def run_batched(args, torch, stream):
     """The 64-member spring-mounted sweep (uneven lattices) in one launch per
     step, against the same members on the FP64 plain path, with the C_D / C_L
@@ -341,7 +367,7 @@ def run_batched(args, torch, stream):
     nodes = sum(p["nx"] * p["ny"] for p in probs)
     b = vp.Batch(probs, precision="f32", history_capacity=4096, stream=stream)
     b.init_from_problems()
-    shape = b.autotune(4)
+    shape = b.autotune(16)
     b.init_from_problems()
     b.step(64)
     b.sync()

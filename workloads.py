@@ -112,6 +112,31 @@ def oscillating_disk(nx=2048, ny=1024, diameter=40.0, x_c=400.0, u0=0.04,
     }
 
 
+def paper_oscillating_cylinder(nx=1230, ny=410, diameter=41.0, x_c=None, tau=0.56, u0=0.04878,
+                               omega_star=1.55, b_star=0.25, eta=1e-3, steps=20_000) -> dict:
+    """The imposed-oscillation validation of Sec. 3.1 as printed there:
+    tau = 0.56, U0 = 0.04878, D = 41, lattice L1 x L2 = 1230 x 410 (the
+    paper gives no channel height; its two lengths are taken as the lattice),
+    constant-velocity inlet, convective outlet, symmetry walls, and
+    y_G(t) = (y_G(0) - D/4) + (D/4) cos(omega t), omega* = omega D / U0 = 1.55:
+    the sinusoid q_c + A sin(2 pi f t + pi/2) with A = B* D."""
+    x_c = 8 * diameter if x_c is None else x_c
+    omega = omega_star * u0 / diameter
+    return {
+        "name": f"paper_oscillating_cylinder_{nx}x{ny}",
+        "nx": nx, "ny": ny, "s": paper_rates(tau), "eta": eta, "rho0": RHO0,
+        "g_fluid": (0.0, 0.0),
+        "bc": {"west": _bc("velocity", u=(u0, 0.0)), "east": _bc("convective", u=(u0, 0.0)),
+               "south": _bc("symmetry"), "north": _bc("symmetry")},
+        "body": {"radius": diameter / 2, "x": x_c, "y": ny / 2.0,
+                 "motion": "imposed", "axis": 1, "amp": b_star * diameter,
+                 "freq": omega / (2 * math.pi), "phase": math.pi / 2,
+                 "u_ref": u0, "d_ref": diameter},
+        "init": {"rho": RHO0, "u": (u0, 0.0)},
+        "steps": steps,
+    }
+
+
 def happel_kappa(h_tilde: float) -> float:
     """Confinement factor of Eq. (34)."""
     h = h_tilde
