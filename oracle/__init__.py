@@ -68,7 +68,11 @@ class Body(C.Structure):
                 ("mass", C.c_double), ("inertia", C.c_double),
                 ("damp", C.c_double * 3), ("stiff", C.c_double * 3),
                 ("q0", C.c_double * 3), ("f_ext", C.c_double * 3),
-                ("dof_mask", C.c_uint), ("u_ref", C.c_double), ("d_ref", C.c_double)]
+                ("dof_mask", C.c_uint), ("u_ref", C.c_double), ("d_ref", C.c_double),
+                ("shape", C.c_int), ("radius_b", C.c_double)]
+
+
+SHAPES = {"disk": 0, "ellipse": 1}
 
 
 class Record(C.Structure):
@@ -111,6 +115,8 @@ def lib():
                                                  + [C.c_double] * 5 + [_D])
             L.orc_body_advance.argtypes = [C.POINTER(Body), C.c_longlong, C.c_double,
                                            _D, _D, _D]
+            L.orc_chi.restype = C.c_int
+            L.orc_chi.argtypes = [C.c_void_p, C.c_int, C.c_int]
             L.orc_adjoint.restype = C.c_int
             L.orc_adjoint.argtypes = [C.c_void_p, C.POINTER(AdjointDesc), _D, _D]
             _lib = L
@@ -185,6 +191,8 @@ def make_body(b: dict | None) -> Body:
     body.dof_mask = int(b.get("dof_mask", 0))
     body.u_ref = float(b.get("u_ref", 0.0))
     body.d_ref = float(b.get("d_ref", 0.0))
+    body.shape = SHAPES[b.get("shape", "disk")]
+    body.radius_b = float(b.get("radius_b", b["radius"]))
     return body
 
 
@@ -273,6 +281,15 @@ class OracleSim:
         v = np.zeros(3)
         lib().orc_get_body(self._h, _dptr(q), _dptr(v))
         return q, v
+
+    def chi(self) -> np.ndarray:
+        """chi of every node at the current pose, [ny, nx] (0 / 1)."""
+        out = np.zeros((self.ny, self.nx), dtype=np.int8)
+        L = lib()
+        for j in range(self.ny):
+            for i in range(self.nx):
+                out[j, i] = L.orc_chi(self._h, i, j)
+        return out
 
 
 # ---- single-node functions (for pinning the oracle) -------------------------

@@ -139,6 +139,7 @@ enum { ORC_PERIODIC = 0, ORC_NOSLIP = 1, ORC_VELOCITY = 2, ORC_ZEROGRAD = 3, ORC
 enum { ORC_WEST = 0, ORC_EAST = 1, ORC_SOUTH = 2, ORC_NORTH = 3 };
 enum { ORC_FIXED = 0, ORC_IMPOSED = 1, ORC_FREE = 2 };
 enum { ORC_MRT = 0, ORC_BGK = 1 };
+enum { ORC_DISK = 0, ORC_ELLIPSE = 1 };
 
 typedef struct {
     int nx, ny;
@@ -164,6 +165,8 @@ typedef struct {
     double damp[3], stiff[3], q0[3], f_ext[3];  /* Eqs. (23)-(24), per x, y, theta */
     unsigned dof_mask;                   /* bit0 x, bit1 y, bit2 theta */
     double u_ref, d_ref;                 /* C_D, C_L normalisation (Sec. 3.1) */
+    int shape;                           /* ORC_DISK or ORC_ELLIPSE */
+    double radius_b;                     /* ellipse: semi-axis along the body's y axis (radius: along its x axis) */
 } orc_body;
 
 /* One record per step n: force and torque of that step, pose used by it. */
@@ -196,16 +199,28 @@ static double edge_u(const orc_sim *s, int side, int comp, int k)
     return s->lat.bc_u[side][comp];
 }
 
-/* chi of Eq. (2) for the disk at the current pose (reading R1). */
+/* chi of Eq. (2) for the body at the current pose (reading R1).  Disk:
+ * |x - x_G| <= R.  Ellipse of semi-axes a (along the body's x axis, at the
+ * angle theta of the pose) and b: with u, v the node's coordinates in the
+ * body frame, b^2 u^2 + a^2 v^2 <= a^2 b^2. */
 static int chi_at(const orc_sim *s, int i, int j)
 {
     if (!s->body.present) return 0;
     double dx = (double)i - s->q[0];
     double dy = (double)j - s->q[1];
+    if (s->body.shape == ORC_ELLIPSE) {
+        double c = cos(s->q[2]), sn = sin(s->q[2]);
+        double a2 = s->body.radius * s->body.radius, b2 = s->body.radius_b * s->body.radius_b;
+        double u = dx * c + dy * sn;
+        double v = dy * c - dx * sn;
+        return b2 * (u * u) + a2 * (v * v) <= a2 * b2;
+    }
     double d2 = dx * dx + dy * dy;
     double r2 = s->body.radius * s->body.radius;
     return d2 <= r2;
 }
+
+int orc_chi(const orc_sim *s, int i, int j) { return chi_at(s, i, j); }
 
 /* Equilibrium of Eq. (11). */
 static void equilibrium(double rho, double ux, double uy, double feq[Q])
@@ -819,6 +834,7 @@ int orc_adjoint(orc_sim *s, const orc_adjoint_desc *d, double *grad, double out_
     const long long N = d->nsteps;
     if (s->body.present && s->body.motion == ORC_FREE) return -1;
     if (s->lat.collision != ORC_MRT) return -1;
+    if (s->body.present && s->body.shape != ORC_DISK) return -1;
     for (int side = 0; side < 4; ++side)
         if (s->lat.bc_kind[side] == ORC_CONVECTIVE) return -1;
     if (N < 1 || d->w0 < 0 || d->w0 >= N || s->hist_cap < s->step + N) return -1;

@@ -526,6 +526,85 @@ def test_convective_outlet_limits():
     assert np.max(np.abs((rho_f - rho_r)[:, :-1])) == 0.0
 
 
+def _ellipse_sim(a, b, theta, x=20.37, y=15.61, nx=41, ny=31):
+    body = {"radius": a, "radius_b": b, "shape": "ellipse", "x": x, "y": y, "theta": theta,
+            "motion": "fixed"}
+    return oracle.OracleSim(wl.periodic_box(nx, ny, body=body))
+
+
+def test_ellipse_geometry():
+    # Semi-axis a lies along the body's x axis at angle theta, b across it:
+    # nodes on the major axis are solid, nodes past either tip or past the
+    # minor axis' ends are fluid, for several angles; a rotation by pi gives
+    # the same set, and so does the swap (a, b, theta) -> (b, a, theta + pi/2).
+    a, b = 9.3, 4.2
+    for theta in (0.0, 0.4, math.pi / 2, 2.0):
+        sim = _ellipse_sim(a, b, theta)
+        chi = sim.chi()
+        xg, yg = 20.37, 15.61
+        c, s = math.cos(theta), math.sin(theta)
+        # nodes on the major axis (rounded) well inside are solid
+        for t in (-0.6, 0.0, 0.6):
+            i, j = int(round(xg + t * a * c)), int(round(yg + t * a * s))
+            assert chi[j, i] == 1
+        # nodes beyond the tips of the major axis are fluid
+        for sign in (1, -1):
+            i, j = int(round(xg + sign * (a + 1.5) * c)), int(round(yg + sign * (a + 1.5) * s))
+            assert chi[j, i] == 0
+        # along the minor axis the body ends at b
+        for sign in (1, -1):
+            i, j = int(round(xg - sign * (b + 1.5) * s)), int(round(yg + sign * (b + 1.5) * c))
+            assert chi[j, i] == 0
+        same = _ellipse_sim(a, b, theta + math.pi).chi()
+        swap = _ellipse_sim(b, a, theta + math.pi / 2).chi()
+        assert np.array_equal(chi, same)
+        assert np.sum(chi != swap) <= 2   # ties at the boundary only
+        # node count approaches the area pi a b within a perimeter's worth
+        assert abs(chi.sum() - math.pi * a * b) < 2 * math.pi * a
+
+
+def test_ellipse_with_equal_axes_is_the_disk():
+    r = 6.3
+    e = _ellipse_sim(r, r, 0.7)
+    d = oracle.OracleSim(wl.periodic_box(41, 31, body={"radius": r, "x": 20.37, "y": 15.61, "motion": "fixed"}))
+    assert np.sum(e.chi() != d.chi()) == 0
+
+
+def test_rotating_ellipse_angular_momentum_balance():
+    # An ellipse free to rotate only, in a periodic box: the fluid's angular
+    # momentum about x_G changes by -T_pen per step (the lever arms and the
+    # rotating solid set enter through chi), and the body's by T_h.
+    a, b = 7.5, 3.5
+    inertia = 400.0
+    body = {"radius": a, "radius_b": b, "shape": "ellipse", "x": 31.4, "y": 32.2, "theta": 0.2,
+            "omega": 0.02, "motion": "free", "mass": 1.0, "inertia": inertia, "dof_mask": 4}
+    n = 64   # large enough that nothing reaches the periodic edges in the run
+    p = wl.periodic_box(n, n, tau=0.7, eta=1e-3, body=body)
+    sim = oracle.OracleSim(p)
+    sim.init_equilibrium()
+    c, _, _, _ = oracle.constants()
+    X, Y = np.meshgrid(np.arange(float(n)), np.arange(float(n)))
+
+    def ang(f):
+        jx = np.tensordot(c[:, 0], f, axes=1)
+        jy = np.tensordot(c[:, 1], f, axes=1)
+        return np.sum((X - body["x"]) * jy - (Y - body["y"]) * jx)
+
+    L_prev = ang(sim.populations())
+    w_prev = sim.body_state()[1][2]
+    nsolid = set()
+    for k in range(16):
+        sim.step(1)
+        rec = sim.history(k, 1)[0]
+        L = ang(sim.populations())
+        assert abs((L - L_prev) + rec[14]) < 1e-13
+        w = sim.body_state()[1][2]
+        assert abs(inertia * (w - w_prev) - rec[3]) < 1e-13
+        L_prev, w_prev = L, w
+        nsolid.add(rec[15])
+    assert sim.body_state()[0][2] > 0.2 and len(nsolid) > 1   # it turned, and its solid set changed
+
+
 def test_rk4_free_fall_is_exact():
     body = {"radius": 1.0, "x": 0, "y": 0, "motion": "free", "mass": 3.0, "inertia": 5.0,
             "f_ext": (0.2, -0.5, 0.1), "dof_mask": 7}
