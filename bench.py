@@ -46,7 +46,7 @@ def kernel_name(prec: str, launch) -> str:
     if launch[0] == "tma":
         return f"vp_mrt_step_tma<{PREC_ID[prec]}>"
     minb = {"scalar": 4, "scalar48": 5, "scalar40": 6}[launch[0]]
-    return f"vp_mrt_step<{PREC_ID[prec]}, {minb}, 0>"   # MRT collision
+    return f"vp_mrt_step<{PREC_ID[prec]}, {minb}, 0, 0>"   # MRT collision, disk
 
 
 def workload(name: str) -> dict:

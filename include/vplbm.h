@@ -120,8 +120,18 @@ typedef enum {
     VPLBM_MOTION_FREE = 2     /* Eqs. (23)-(24) for the DOFs in dof_mask, RK4 */
 } vplbm_motion;
 
-/* Rigid disk.  chi(x) = 1 iff (i - x_G)^2 + (j - y_G)^2 <= radius^2 (FP64,
- * no fused multiply-add).  The rigid velocity at a node is
+/* Body shapes.  DISK: chi(x) = 1 iff (i - x_G)^2 + (j - y_G)^2 <= radius^2.
+ * ELLIPSE: semi-axis `radius` along the body's x axis, at the angle theta
+ * of the pose, and `radius_b` across it: with u = dx cos(theta) + dy
+ * sin(theta), v = dy cos(theta) - dx sin(theta), chi = 1 iff
+ * radius_b^2 u^2 + radius^2 v^2 <= radius^2 radius_b^2.  Both in FP64
+ * without fused multiply-add; the ellipse's cos / sin come from the host's
+ * math library for a pose set on the host and from CUDA's for a pose the
+ * GPU advanced (they may differ in the last bit).  The ellipse is not
+ * supported by the adjoint. */
+typedef enum { VPLBM_SHAPE_DISK = 0, VPLBM_SHAPE_ELLIPSE = 1 } vplbm_shape;
+
+/* Rigid body (disk or ellipse, see vplbm_shape).  The rigid velocity at a node is
  * u_s = (vx - omega (y - y_G), vy + omega (x - x_G)).
  * Imposed motion: q_c is chosen so that q_axis(0) equals the initial pose.
  * Free motion: m q'' + damp q' + stiff (q - q0) = F_h + f_ext per DOF
@@ -136,6 +146,8 @@ typedef struct {
     double damp[3], stiff[3], q0[3], f_ext[3];
     unsigned dof_mask;        /* bit0 x, bit1 y, bit2 theta */
     double u_ref, d_ref;      /* C_D = F_x / (rho0 d_ref u_ref^2 / 2), C_L alike */
+    int shape;                /* vplbm_shape (0: disk) */
+    double radius_b;          /* ellipse: semi-axis along the body's y axis */
 } vplbm_body_desc;
 
 /* One record per time step n.  (fx, fy, torque) is the momentum exchanged

@@ -72,7 +72,8 @@ class BodyDesc(C.Structure):
                 ("mass", C.c_double), ("inertia", C.c_double),
                 ("damp", C.c_double * 3), ("stiff", C.c_double * 3),
                 ("q0", C.c_double * 3), ("f_ext", C.c_double * 3),
-                ("dof_mask", C.c_uint), ("u_ref", C.c_double), ("d_ref", C.c_double)]
+                ("dof_mask", C.c_uint), ("u_ref", C.c_double), ("d_ref", C.c_double),
+                ("shape", C.c_int), ("radius_b", C.c_double)]
 
 
 class Record(C.Structure):
@@ -243,6 +244,8 @@ def body_desc(body: dict | None) -> BodyDesc | None:
             arr[k] = float(vals[k])
     b.dof_mask = int(body.get("dof_mask", 0))
     b.u_ref, b.d_ref = float(body.get("u_ref", 0.0)), float(body.get("d_ref", 0.0))
+    b.shape = SHAPES[body.get("shape", "disk")]
+    b.radius_b = float(body.get("radius_b", body["radius"]))
     return b
 
 
@@ -330,6 +333,7 @@ def vplbm_get_body(ctx):
 
 
 COLLISIONS = {"mrt": 0, "bgk": 1}
+SHAPES = {"disk": 0, "ellipse": 1}
 BATCH_MODES = {"branches": 0, "tiles": 1}
 BATCH_MODE_NAMES = {v: k for k, v in BATCH_MODES.items()}
 KERNELS = {"scalar": 0, "scalar48": 1, "scalar40": 2, "tma": 3}

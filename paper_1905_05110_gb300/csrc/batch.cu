@@ -316,7 +316,7 @@ vplbm_status vplbm_batch_set_launch(vplbm_batch *b, int block_x, int block_y, in
         return berr(VPLBM_EINVAL, "tiles per block %d not in [1, 64]", tiles_per_block);
     for (int k = 0; k < b->n; ++k) {
         const vplbm_ctx *c = b->members[k];
-        if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, block_x, block_y) >
+        if (max_reduction_blocks(c->nx, c->ny, c->has_body ? bounding_radius(&c->body_desc) : 0.0, c->has_body, block_x, block_y) >
             c->max_parts)
             return berr(VPLBM_EINVAL, "member %d: block shape needs more reduction scratch than allocated", k);
     }

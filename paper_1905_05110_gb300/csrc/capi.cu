@@ -38,7 +38,7 @@ vplbm_status fail(vplbm_status st, const char *fmt, ...)
 
 constexpr size_t ALIGN = 256;
 constexpr int GRAPH_STEPS = 32;   // steps per captured graph (even)
-constexpr char CKPT_MAGIC[8] = {'V', 'P', 'L', 'B', 'M', 'C', 'K', '2'};
+constexpr char CKPT_MAGIC[8] = {'V', 'P', 'L', 'B', 'M', 'C', 'K', '3'};
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -130,6 +130,9 @@ vplbm_status check_body(const vplbm_body_desc *b)
 {
     if (!b) return VPLBM_OK;
     if (!(b->radius >= 0.0) || b->radius > 1e6) return fail(VPLBM_EINVAL, "radius must be in [0, 1e6]");
+    if (b->shape != VPLBM_SHAPE_DISK && b->shape != VPLBM_SHAPE_ELLIPSE) return fail(VPLBM_EINVAL, "unknown shape %d", b->shape);
+    if (b->shape == VPLBM_SHAPE_ELLIPSE && (!(b->radius > 0.0) || !(b->radius_b > 0.0) || b->radius_b > 1e6))
+        return fail(VPLBM_EINVAL, "ellipse semi-axes must be in (0, 1e6]");
     const double vals[6] = {b->x, b->y, b->theta, b->vx, b->vy, b->omega};
     for (double v : vals)
         if (!isfinite(v) || fabs(v) > 1e7) return fail(VPLBM_EINVAL, "body pose/velocity must be finite and < 1e7");
@@ -149,13 +152,13 @@ void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long 
 {
     const long long n = (long long)lat->nx * lat->ny;
     const long long ps = (long long)round_up((size_t)n, 128);
-    long long parts = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr,
+    long long parts = max_reduction_blocks(lat->nx, lat->ny, bounding_radius(body), body != nullptr,
                                            TMA_TILE_W, TMA_TILE_H);
     for (int k = 0; k < N_SHAPES; ++k)
         for (int kern = KERNEL_SCALAR; kern <= KERNEL_TMA; ++kern) {   // every kernel's tiling
             int w, h;
             tile_of(kern, SHAPES[k][0], SHAPES[k][1], &w, &h);
-            const long long m = max_reduction_blocks(lat->nx, lat->ny, body ? body->radius : 0.0, body != nullptr, w, h);
+            const long long m = max_reduction_blocks(lat->nx, lat->ny, bounding_radius(body), body != nullptr, w, h);
             if (m > parts) parts = m;
         }
     s->populations = round_up((size_t)(9 * ps) * elem_size(lat->precision), ALIGN);
@@ -180,7 +183,8 @@ BodyState initial_state(const vplbm_ctx *c)
         s.v[0] = b.vx; s.v[1] = b.vy; s.v[2] = b.omega;
     }
     s.step = 0;
-    derive_pose(s, c->has_body ? 1 : 0, c->has_body ? c->body_desc.radius : 0.0, c->nx, c->ny);
+    derive_pose(s, c->has_body ? 1 : 0, c->has_body ? bounding_radius(&c->body_desc) : 0.0, c->nx, c->ny,
+                c->has_body ? c->body_desc.shape : VPLBM_SHAPE_DISK);
     return s;
 }
 
@@ -273,6 +277,55 @@ vplbm_status reset_run(vplbm_ctx *c)
     return VPLBM_OK;
 }
 
+}  // namespace
+
+namespace vplbm {
+// Body constants of a launch's parameters from the public descriptors
+// (also used by the allocation-free entry point).
+void fill_dev_body(StepParams &p, const vplbm_lattice_desc *lat, const vplbm_body_desc *body)
+{
+    DevBody &b = p.body;
+    memset(&b, 0, sizeof b);
+    b.present = body ? 1 : 0;
+    if (!body) return;
+    b.motion = body->motion;
+    b.axis = body->axis;
+    b.dof_mask = body->dof_mask;
+    b.radius = bounding_radius(body);
+    b.r2 = body->radius * body->radius;
+    b.shape = body->shape;
+    // FP32 predicate b^2 u^2 + a^2 v^2 <= a^2 b^2 of both shapes (disk: a = b)
+    const double ra = body->radius, rb = body->shape == VPLBM_SHAPE_ELLIPSE ? body->radius_b : body->radius;
+    b.a2 = ra * ra;
+    b.b2 = rb * rb;
+    b.ab2 = b.a2 * b.b2;
+    b.a2f = (float)b.a2; b.b2f = (float)b.b2; b.ab2f = (float)b.ab2;
+    // its FP32 error stays below ~1e-6 a^2 b^2 (max / min semi-axis); 100x margin
+    const double ratio = ra > 0.0 && rb > 0.0 ? fmax(ra, rb) / fmin(ra, rb) : 1.0;
+    b.bandf = (float)(1e-4 * b.ab2 * ratio + 1e-5);
+    p.r2f = (float)b.r2;
+    b.amp = body->amp;
+    b.freq = body->freq;
+    b.phase = body->phase;
+    const double q0[3] = {body->x, body->y, body->theta};
+    b.q_center = body->motion == VPLBM_MOTION_IMPOSED ? q0[body->axis] - body->amp * sin(body->phase) : 0.0;
+    b.mass = body->mass;
+    b.inertia = body->inertia;
+    b.inv_mass = body->mass > 0.0 ? 1.0 / body->mass : 0.0;
+    b.inv_inertia = body->inertia > 0.0 ? 1.0 / body->inertia : 0.0;
+    for (int d = 0; d < 3; ++d) {
+        b.damp[d] = body->damp[d];
+        b.stiff[d] = body->stiff[d];
+        b.q0[d] = body->q0[d];
+        b.f_ext[d] = body->f_ext[d];
+    }
+    b.qref = 0.5 * lat->rho0 * body->d_ref * body->u_ref * body->u_ref;
+    b.inv_qref = b.qref > 0.0 ? 1.0 / b.qref : 0.0;
+}
+}  // namespace vplbm
+
+namespace {
+
 vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body_desc *body,
                    long long cap, void *stream)
 {
@@ -346,34 +399,7 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     }
     CUDA_TRY(cudaMemcpyAsync(proff_dev, proff.data(), nprof * sizeof(float), cudaMemcpyHostToDevice, c->stream));
 
-    DevBody &b = p.body;
-    memset(&b, 0, sizeof b);
-    b.present = body ? 1 : 0;
-    if (body) {
-        b.motion = body->motion;
-        b.axis = body->axis;
-        b.dof_mask = body->dof_mask;
-        b.radius = body->radius;
-        b.r2 = body->radius * body->radius;
-        p.r2f = (float)b.r2;
-        b.amp = body->amp;
-        b.freq = body->freq;
-        b.phase = body->phase;
-        const double q0[3] = {body->x, body->y, body->theta};
-        b.q_center = body->motion == VPLBM_MOTION_IMPOSED ? q0[body->axis] - body->amp * sin(body->phase) : 0.0;
-        b.mass = body->mass;
-        b.inertia = body->inertia;
-        b.inv_mass = body->mass > 0.0 ? 1.0 / body->mass : 0.0;
-        b.inv_inertia = body->inertia > 0.0 ? 1.0 / body->inertia : 0.0;
-        for (int d = 0; d < 3; ++d) {
-            b.damp[d] = body->damp[d];
-            b.stiff[d] = body->stiff[d];
-            b.q0[d] = body->q0[d];
-            b.f_ext[d] = body->f_ext[d];
-        }
-        b.qref = 0.5 * lat->rho0 * body->d_ref * body->u_ref * body->u_ref;
-        b.inv_qref = b.qref > 0.0 ? 1.0 / b.qref : 0.0;
-    }
+    fill_dev_body(p, lat, body);
     p.partials = c->partials;
     p.max_parts = c->max_parts;
     p.ticket = &c->ctrl->ticket;
@@ -754,7 +780,7 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
         return fail(VPLBM_EINVAL, "launch shape %dx%d not allowed", bx, by);
     int w, h;
     tile_of(kernel, bx, by, &w, &h);
-    if (max_reduction_blocks(c->nx, c->ny, c->has_body ? c->body_desc.radius : 0.0, c->has_body, w, h) > c->max_parts)
+    if (max_reduction_blocks(c->nx, c->ny, c->has_body ? bounding_radius(&c->body_desc) : 0.0, c->has_body, w, h) > c->max_parts)
         return fail(VPLBM_EINVAL, "launch shape %dx%d needs more reduction scratch than allocated", bx, by);
     c->kernel = kernel;
     c->bx = bx;

@@ -53,7 +53,7 @@ NoallocScratch *g_scratch_addr[MAX_DEVICES] = {};
 
 // Copy the caller's body state into the internal record, derive the
 // pose-dependent values and clear the words that must start at zero.
-__global__ void noalloc_prepare(const vplbm_body_state *state, int present, double radius, int nx, int ny)
+__global__ void noalloc_prepare(const vplbm_body_state *state, int present, double radius, int nx, int ny, int shape)
 {
     NoallocScratch &s = g_noalloc_scratch;
     BodyState b{};
@@ -62,7 +62,7 @@ __global__ void noalloc_prepare(const vplbm_body_state *state, int present, doub
         b.v[d] = state->v[d];
     }
     b.step = state->step;
-    derive_pose(b, present, radius, nx, ny);
+    derive_pose(b, present, radius, nx, ny, shape);
     s.bs[0] = b;
     s.ctrl.ticket = 0u;
     s.ctrl.err = 0;
@@ -129,7 +129,7 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const 
     if (lat->bc[VPLBM_EAST].kind == VPLBM_BC_CONVECTIVE)
         return report_error(VPLBM_EUNSUPPORTED, "vplbm_step_noalloc has no outlet state (convective outlet)");
     const int present = body ? 1 : 0;
-    const double radius = body ? body->radius : 0.0;
+    const double radius = bounding_radius(body);
     const long long parts = max_reduction_blocks(lat->nx, lat->ny, radius, present, NOALLOC_BX, NOALLOC_BY);
     if (parts > NOALLOC_MAX_PARTS) {
         char msg[256];
@@ -174,33 +174,7 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const 
         p.wall_prof[s][0] = p.wall_prof[s][1] = nullptr;
         p.wall_proff[s][0] = p.wall_proff[s][1] = nullptr;
     }
-    DevBody &b = p.body;
-    b.present = present;
-    if (body) {
-        b.motion = body->motion;
-        b.axis = body->axis;
-        b.dof_mask = body->dof_mask;
-        b.radius = body->radius;
-        b.r2 = body->radius * body->radius;
-        p.r2f = (float)b.r2;
-        b.amp = body->amp;
-        b.freq = body->freq;
-        b.phase = body->phase;
-        const double q0[3] = {body->x, body->y, body->theta};
-        b.q_center = body->motion == VPLBM_MOTION_IMPOSED ? q0[body->axis] - body->amp * sin(body->phase) : 0.0;
-        b.mass = body->mass;
-        b.inertia = body->inertia;
-        b.inv_mass = body->mass > 0.0 ? 1.0 / body->mass : 0.0;
-        b.inv_inertia = body->inertia > 0.0 ? 1.0 / body->inertia : 0.0;
-        for (int d = 0; d < 3; ++d) {
-            b.damp[d] = body->damp[d];
-            b.stiff[d] = body->stiff[d];
-            b.q0[d] = body->q0[d];
-            b.f_ext[d] = body->f_ext[d];
-        }
-        b.qref = 0.5 * lat->rho0 * body->d_ref * body->u_ref * body->u_ref;
-        b.inv_qref = b.qref > 0.0 ? 1.0 / b.qref : 0.0;
-    }
+    fill_dev_body(p, lat, body);
     p.partials = scratch->partials;
     p.max_parts = NOALLOC_MAX_PARTS;
     p.ticket = &scratch->ctrl.ticket;
@@ -208,7 +182,8 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const 
     p.hist = history_dev ? history_dev : &scratch->record;
     p.hist_cap = history_dev ? history_capacity : 1;
 
-    noalloc_prepare<<<1, 1, 0, stream>>>(state_dev, present, radius, lat->nx, lat->ny);
+    noalloc_prepare<<<1, 1, 0, stream>>>(state_dev, present, radius, lat->nx, lat->ny,
+                                         body ? body->shape : VPLBM_SHAPE_DISK);
     cudaError_t e = cudaGetLastError();
     for (long long k = 0; k < nsteps && e == cudaSuccess; ++k) {
         const int par = (int)(k & 1);

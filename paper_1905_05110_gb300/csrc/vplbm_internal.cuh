@@ -29,14 +29,17 @@ struct BodyState {
     int xi, yi;        // floor(x_G), floor(y_G)               (80, int2)
     float xf, yf;      // x_G - xi, y_G - yi, rounded to FP32   (88, float2)
     float vxf, vyf, omf, pad1;   // velocities in FP32          (96, float4)
-    int pad[4];        //                                      (112)
+    float cthf, sthf;  // cos(theta), sin(theta) in FP32 (ellipse) (112, float2)
+    int pad[2];        //                                      (120)
+    double cth, sth;   // cos(theta), sin(theta) (ellipse)      (128)
 };
-static_assert(sizeof(BodyState) == 128, "BodyState layout");
+static_assert(sizeof(BodyState) == 144, "BodyState layout");
 // the step kernel reads these groups with vector loads
 static_assert(offsetof(BodyState, ilo) % 16 == 0, "int4 load of the solid range");
 static_assert(offsetof(BodyState, xi) % 8 == 0, "int2 load of floor(x_G)");
 static_assert(offsetof(BodyState, xf) % 8 == 0, "float2 load of the fractions");
 static_assert(offsetof(BodyState, vxf) % 16 == 0, "float4 load of the velocities");
+static_assert(offsetof(BodyState, cthf) % 8 == 0, "float2 load of the orientation");
 
 // Body constants over a run (copied into every launch's parameters).
 struct DevBody {
@@ -51,6 +54,10 @@ struct DevBody {
     double damp[3], stiff[3], q0[3], f_ext[3];
     double qref;       // rho0 d_ref u_ref^2 / 2 (0: no C_D / C_L)
     double inv_qref;   // 1 / qref (0 when qref is 0)
+    int shape;         // vplbm_shape; radius above is the bounding radius
+    int pad_shape;
+    double a2, b2, ab2;          // ellipse: semi-axes squared and their product
+    float a2f, b2f, ab2f, bandf; // FP32 copies; bandf: FP32 test band of the ellipse predicate
 };
 
 // Number of doubles per block partial: fpen_x, fpen_y, tpen, fh_x, fh_y,
@@ -161,7 +168,8 @@ inline void set_planes(StepParams &p, int es)
 
 // Fill the derived fields of s from its pose (host and device, same IEEE
 // operations on both).
-__host__ __device__ inline void derive_pose(BodyState &s, int present, double radius, int nx, int ny)
+__host__ __device__ inline void derive_pose(BodyState &s, int present, double radius, int nx, int ny,
+                                            int shape = VPLBM_SHAPE_DISK)
 {
     s.ilo = 1; s.ihi = 0; s.jlo = 1; s.jhi = 0;
     s.xi = s.yi = 0;
@@ -169,7 +177,13 @@ __host__ __device__ inline void derive_pose(BodyState &s, int present, double ra
     s.vxf = (float)s.v[0]; s.vyf = (float)s.v[1]; s.omf = (float)s.v[2];
     s.pad0 = 0;
     s.pad1 = 0.f;
-    for (int k = 0; k < 4; ++k) s.pad[k] = 0;
+    s.pad[0] = s.pad[1] = 0;
+    s.cth = 1.0; s.sth = 0.0;
+    if (shape == VPLBM_SHAPE_ELLIPSE && isfinite(s.q[2])) {
+        s.cth = cos(s.q[2]);
+        s.sth = sin(s.q[2]);
+    }
+    s.cthf = (float)s.cth; s.sthf = (float)s.sth;
     if (!present || !isfinite(s.q[0]) || !isfinite(s.q[1])) return;
     // nodes that may satisfy the chi predicate, one node of margin
     const double ilo = fmax(floor(s.q[0] - radius) - 1.0, 0.0), ihi = fmin(ceil(s.q[0] + radius) + 1.0, (double)(nx - 1));
@@ -179,6 +193,17 @@ __host__ __device__ inline void derive_pose(BodyState &s, int present, double ra
     const double fx = floor(s.q[0]), fy = floor(s.q[1]);
     s.xi = (int)fx; s.yi = (int)fy;
     s.xf = (float)(s.q[0] - fx); s.yf = (float)(s.q[1] - fy);
+}
+
+// Body constants of a launch's parameters (capi.cu).
+void fill_dev_body(StepParams &p, const vplbm_lattice_desc *lat, const vplbm_body_desc *body);
+
+// Radius of the disk, or of the circle around the ellipse: sizes the node
+// range and the reduction scratch.
+inline double bounding_radius(const vplbm_body_desc *b)
+{
+    if (!b) return 0.0;
+    return b->shape == VPLBM_SHAPE_ELLIPSE ? fmax(b->radius, b->radius_b) : b->radius;
 }
 
 // Step kernels a context can launch: the scalar kernel with the register
@@ -199,6 +224,8 @@ cudaError_t launch_step_batch(int precision, const BatchLaunch &bl, int total_ti
 
 // Launchers (step_kernels.cu).  All are asynchronous on `stream`.
 cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb = 4);
+// The same for an elliptic body (step_ellipse.cu).
+cudaError_t launch_step_ellipse(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb);
 cudaError_t launch_init_equilibrium(int precision, const StepParams &p, const double *rho_dev,
                                     const double *ux_dev, const double *uy_dev, cudaStream_t stream);
 // Convective outlet: previous values := the outlet column of p.fin (into p.conv_in).

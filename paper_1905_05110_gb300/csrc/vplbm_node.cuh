@@ -160,6 +160,19 @@ __device__ __forceinline__ bool chi_exact(int i, int j, double xg, double yg, do
     return d2 <= r2;
 }
 
+// Ellipse: b^2 u^2 + a^2 v^2 <= a^2 b^2 with (u, v) the node in the body
+// frame, FP64 without contraction, in a fixed order.
+__device__ __forceinline__ bool chi_exact_ellipse(int i, int j, const BodyState *bs, const DevBody &b)
+{
+    const double dx = __dsub_rn((double)i, bs->q[0]);
+    const double dy = __dsub_rn((double)j, bs->q[1]);
+    const double c = bs->cth, s = bs->sth;
+    const double u = __dadd_rn(__dmul_rn(dx, c), __dmul_rn(dy, s));
+    const double v = __dsub_rn(__dmul_rn(dy, c), __dmul_rn(dx, s));
+    const double lhs = __dadd_rn(__dmul_rn(b.b2, __dmul_rn(u, u)), __dmul_rn(b.a2, __dmul_rn(v, v)));
+    return lhs <= b.ab2;
+}
+
 // ---- rigid body (Eqs. 23-24 and Algorithm 1 step 3) --------------------
 
 __device__ void body_acc(const DevBody &b, const double F[3], const double q[3], const double v[3], double acc[3])
@@ -252,7 +265,7 @@ __device__ __noinline__ void advance_prescribed(const StepParams &p)
     const double F0[3] = {0.0, 0.0, 0.0};   // not used by fixed / imposed motion
     body_advance(p.body, nb.step, F0, nb.q, nb.v);
     nb.step += 1;
-    derive_pose(nb, p.body.present, p.body.radius, p.nx, p.ny);
+    derive_pose(nb, p.body.present, p.body.radius, p.nx, p.ny, p.body.shape);
     *p.bs_out = nb;
 }
 
@@ -319,7 +332,7 @@ __device__ __noinline__ void step_tail(const StepParams &p, int nparts)
         BodyState nb = cur;
         body_advance(p.body, cur.step, Fh, nb.q, nb.v);
         nb.step = cur.step + 1;
-        derive_pose(nb, p.body.present, p.body.radius, p.nx, p.ny);
+        derive_pose(nb, p.body.present, p.body.radius, p.nx, p.ny, p.body.shape);
         *p.bs_out = nb;
     }
     *p.ticket = 0u;   // ready for the next launch (stream order)
@@ -372,7 +385,11 @@ __device__ __forceinline__ void solid_node_terms(const StepParams &p, const type
 // populations f: moments, chi and u_s, penalized velocity (Eq. 22),
 // collision with forcing (Eq. 17) and the store of f~.  Returns chi and
 // keeps rho, a for the solid-node sums.
-template <int P, int COLL = VPLBM_COLLISION_MRT>
+// SHAPE: VPLBM_SHAPE_DISK or VPLBM_SHAPE_ELLIPSE fixed at compile time, or
+// SHAPE_ANY to read it from the parameters.
+constexpr int SHAPE_ANY = -1;
+
+template <int P, int COLL = VPLBM_COLLISION_MRT, int SHAPE = SHAPE_ANY>
 __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState *__restrict__ bs, bool near_body,
                                             int i, int j, const typename Prec<P>::T f[NQ],
                                             typename Prec<P>::S *__restrict__ fout, typename Prec<P>::T &cr,
@@ -398,15 +415,28 @@ __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState
             const float2 fr = __ldg(reinterpret_cast<const float2 *>(&bs->xf));
             const float dxf = (float)(i - xy.x) - fr.x;
             const float dyf = (float)(j - xy.y) - fr.y;
-            const float d2 = dxf * dxf + dyf * dyf;
-            const float r2 = p.r2f;
-            const float band = 1e-5f * r2 + 1e-5f;
-            if (fabsf(d2 - r2) <= band) chi = chi_exact(i, j, bs->q[0], bs->q[1], p.body.r2);
-            else chi = d2 <= r2;
+            const bool ellipse = SHAPE == SHAPE_ANY ? p.body.shape == VPLBM_SHAPE_ELLIPSE : SHAPE == VPLBM_SHAPE_ELLIPSE;
+            if (ellipse) {
+                // b^2 u^2 + a^2 v^2 <= a^2 b^2 in the body frame, in FP32,
+                // exact FP64 re-test inside the band
+                const float2 cs = __ldg(reinterpret_cast<const float2 *>(&bs->cthf));
+                const float uf = dxf * cs.x + dyf * cs.y;
+                const float vf = dyf * cs.x - dxf * cs.y;
+                const float lhs = p.body.b2f * (uf * uf) + p.body.a2f * (vf * vf);
+                if (fabsf(lhs - p.body.ab2f) <= p.body.bandf) chi = chi_exact_ellipse(i, j, bs, p.body);
+                else chi = lhs <= p.body.ab2f;
+            } else {
+                const float d2 = dxf * dxf + dyf * dyf;
+                const float r2 = p.r2f;
+                const float band = 1e-5f * r2 + 1e-5f;
+                if (fabsf(d2 - r2) <= band) chi = chi_exact(i, j, bs->q[0], bs->q[1], p.body.r2);
+                else chi = d2 <= r2;
+            }
             dxl = dxf; dyl = dyf;
         } else {
             const double xg = __ldg(&bs->q[0]), yg = __ldg(&bs->q[1]);
-            chi = chi_exact(i, j, xg, yg, p.body.r2);
+            const bool ellipse = SHAPE == SHAPE_ANY ? p.body.shape == VPLBM_SHAPE_ELLIPSE : SHAPE == VPLBM_SHAPE_ELLIPSE;
+            chi = ellipse ? chi_exact_ellipse(i, j, bs, p.body) : chi_exact(i, j, xg, yg, p.body.r2);
             dxl = (double)i - xg;
             dyl = (double)j - yg;
         }

@@ -102,3 +102,32 @@ def test_batch_rejects_members_out_of_step_and_autotunes():
         batch.set_mode(5)
     batch.sync()
     batch.close()
+
+
+@pytest.mark.parametrize("mode", ["branches", "tiles"])
+def test_batch_with_ellipse_and_disk_members(mode):
+    """Members of different body shapes in one batch (the tile-mode kernel
+    reads the shape per member) match the same simulations stepped alone."""
+    import paper_1905_05110_gb300 as vp
+    probs = _members()
+    e = dict(probs[1]["body"], shape="ellipse", radius_b=0.5 * probs[1]["body"]["radius"], theta=0.4)
+    probs[1] = dict(probs[1], body=e)
+    batch = vp.Batch(probs, precision="f32", history_capacity=128)
+    batch.set_mode(mode)
+    if mode == "tiles":
+        batch.set_launch(256, 1, 4)
+    else:
+        for m in batch.members:
+            vp.vplbm_set_launch(m.ctx, vp.KERNELS["scalar48"], 256, 1)
+    batch.init_from_problems()
+    batch.step(40)
+    for k, p in enumerate(probs):
+        alone = vp.Simulation(p, precision="f32", history_capacity=128)
+        alone.set_launch("scalar48", 256, 1)
+        alone.init_from_problem()
+        alone.step(40)
+        m = batch.members[k]
+        assert dev_err(m.populations(), alone.populations()) < 1e-6
+        assert np.array_equal(m.history()[:, REC["n_solid"]], alone.history()[:, REC["n_solid"]])
+        alone.close()
+    batch.close()

@@ -565,3 +565,75 @@ def test_convective_outlet_rejected_where_not_defined():
         sim.adjoint(10, 5)
     assert ei.value.status == 6
     sim.close()
+
+
+# ---- elliptic body ---------------------------------------------------------
+
+def _ellipse_body(motion, nx, ny):
+    a, b = 0.2 * ny, 0.09 * ny
+    m = 2.0 * np.pi * a * b
+    common = {"shape": "ellipse", "radius": a, "radius_b": b, "u_ref": 0.05, "d_ref": 2 * b}
+    if motion == "fixed":
+        return dict(common, x=0.41 * nx + 0.13, y=0.52 * ny + 0.37, theta=0.5, motion="fixed")
+    if motion == "imposed":   # pitching about its centre
+        return dict(common, x=0.43 * nx + 0.21, y=0.47 * ny + 0.09, theta=0.3, motion="imposed", axis=2,
+                    amp=0.4, freq=0.01, phase=0.0)
+    return dict(common, x=0.45 * nx + 0.31, y=0.5 * ny + 0.17, theta=0.1, omega=0.004, vy=-0.002,
+                motion="free", mass=m, inertia=m * (a * a + b * b) / 4, dof_mask=7,
+                stiff=(0.0, 1e-3, 0.0), q0=(0.0, 0.5 * ny, 0.0))
+
+
+@pytest.mark.parametrize("motion", ["fixed", "imposed", "free"])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_ellipse_runs_match_oracle(motion, precision):
+    nx, ny = 97, 70
+    p = _box(nx, ny, ("velocity", "zerograd", "noslip", "noslip"), seed=6, body=_ellipse_body(motion, nx, ny),
+             tau=0.62)
+    p["s"] = wl.paper_rates(0.62)
+    p["bc"]["west"] = {"kind": "velocity", "u": (0.05, 0.0)}
+    gpu, orc = make_pair(p, precision)
+    steps = 150
+    gpu.step(steps)
+    orc.step(steps)
+    tol = RUN_TOL[precision]
+    assert dev_err(gpu.populations(), orc.populations()) < tol
+    hg, ho = gpu.history(), orc.history()
+    assert np.array_equal(hg[:, REC["n_solid"]], ho[:, REC["n_solid"]])
+    ftol = 1e-10 if precision == "f64" else 1e-3
+    for key in ("fx", "fy", "torque", "fpen_x", "fpen_y", "tpen"):
+        assert rel_err(hg[:, REC[key]], ho[:, REC[key]]) < ftol, key
+    ptol = 1e-12 if precision == "f64" else 1e-6
+    for key in ("x", "y", "theta", "vx", "vy", "omega"):
+        assert np.max(np.abs(hg[:, REC[key]] - ho[:, REC[key]])) <= ptol * max(1.0, np.max(np.abs(ho[:, REC[key]]))), key
+    if motion != "fixed":
+        assert np.ptp(hg[:, REC["n_solid"]]) > 0   # the solid set changes as it turns
+
+
+def test_ellipse_with_equal_axes_is_the_disk_and_refusals():
+    import paper_1905_05110_gb300 as vp
+    nx, ny = 130, 66
+    disk = {"radius": 9.3, "x": 52.37, "y": 31.61, "motion": "imposed", "axis": 1, "amp": 2.0, "freq": 0.01,
+            "u_ref": 0.05, "d_ref": 18.6}
+    ell = dict(disk, shape="ellipse", radius_b=9.3, theta=0.0)
+    out = []
+    for body in (disk, ell):
+        p = _box(nx, ny, ("velocity", "zerograd", "noslip", "noslip"), seed=2, body=body)
+        p["s"] = wl.paper_rates(0.7)
+        sim = vp.Simulation(p, precision="f32", history_capacity=64)
+        sim.init_from_problem()
+        sim.step(40)
+        out.append((sim.populations(), sim.history()))
+        sim.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1][:, REC["n_solid"]], out[1][1][:, REC["n_solid"]])
+    p = _box(nx, ny, ("velocity", "zerograd", "noslip", "noslip"), seed=2, body=dict(ell, radius_b=0.0))
+    with pytest.raises(vp.VplbmError) as ei:
+        vp.Simulation(p, precision="f32")
+    assert ei.value.status == 1
+    p = _box(nx, ny, ("velocity", "zerograd", "noslip", "noslip"), seed=2, body=dict(ell, radius_b=4.0))
+    sim = vp.Simulation(p, precision="f64", history_capacity=64)
+    sim.init_from_problem()
+    with pytest.raises(vp.VplbmError) as ei:
+        sim.adjoint(10, 5)
+    assert ei.value.status == 6
+    sim.close()
