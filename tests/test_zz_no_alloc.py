@@ -35,12 +35,14 @@ def _stored_to_full(raw: np.ndarray, nx: int, ny: int, precision: str) -> np.nda
     return planes if precision == "f64" else planes + W[:, None, None]
 
 
-@pytest.mark.parametrize("precision", ["f32", "f64"])
-def test_noalloc_two_calls_match_regular_step(gpu_library, precision):
+@pytest.mark.parametrize("precision,shape", [("f32", "disk"), ("f64", "disk"), ("f32", "ellipse")])
+def test_noalloc_two_calls_match_regular_step(gpu_library, precision, shape):
     import torch
     import paper_1905_05110_gb300 as vp
 
     p = wl.oscillating_disk(nx=300, ny=160, diameter=24, x_c=80)
+    if shape == "ellipse":
+        p["body"] = dict(p["body"], shape="ellipse", radius_b=6.0, theta=0.3)
     nx, ny = p["nx"], p["ny"]
     n1, n2 = 40, 23
     cap = 128
