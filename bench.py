@@ -160,6 +160,15 @@ class ClockSampler:
                 "power_w_max": max(r[2] for r in rows)}
 
 
+def max_over_ranks(value: float, world: int, device, torch) -> float:
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return value
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_device(sim, steps, stream, torch):
     """CUDA-event time of `steps` time steps on the simulation's stream."""
     e0 = torch.cuda.Event(enable_timing=True)
@@ -266,10 +275,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
     launches = sim.launches - launches0
     sim.sync()
-    if world > 1:
-        t = torch.tensor([dt], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks(dt, world, dev, torch)
     value = world * nodes * args.steps / dt / 1e6
     clock = clocks.summary()
 
@@ -311,6 +317,8 @@ def run_ours(args, rank, world, local_rank):
         if "f64" in compare:
             compare["speedup_vs_f64"] = (nodes * args.steps / dt / 1e6) / compare["f64"]["mlups"]
 
+    if not args.no_compare and world > 1:
+        compare["batched_sharded"] = run_sharded_sweep(args, torch, stream, rank, world, dev)
     if not args.no_compare and rank == 0:
         compare["batched"] = run_batched(args, torch, stream)
         compare["adjoint"] = run_adjoint(args, torch, compare.get("f64"))
@@ -356,6 +364,30 @@ def run_other_workload(name, steps, torch, stream):
         out["final_velocity"] = [float(v) for v in h[-1, 9:12]]
     sim.close()
     return out
+
+
+def run_sharded_sweep(args, torch, stream, rank, world, dev):
+    """The 64-member sweep sharded over the ranks (greedy longest-processing-
+    time by node count, the same partition on every rank, no exchange): the
+    units all ranks processed over the slowest rank's time."""
+    import paper_1905_05110_gb300 as vp
+    from paper_1905_05110_gb300.sweep import member_nodes, partition_members
+    probs = wl.viv_sweep()
+    nodes = member_nodes(probs)
+    mine = partition_members(nodes, world)[rank]
+    b = vp.Batch([probs[k] for k in mine], precision="f32", history_capacity=1024, stream=stream)
+    b.init_from_problems()
+    b.step(64)
+    b.sync()
+    k = max(64, min(512, args.steps // 50))
+    torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t = time_device(b, k, stream, torch)
+    b.sync()
+    b.close()
+    t = max_over_ranks(t, world, dev, torch)
+    return {"ranks": world, "members": len(probs), "nodes": sum(nodes), "steps": k,
+            "mlups": sum(nodes) * k / t / 1e6, "scaling": "strong (fixed 64-member sweep)"}
 
 
 def run_batched(args, torch, stream):
