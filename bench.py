@@ -37,6 +37,7 @@ METRIC = "D2Q9 VP-MRT MLUPS & % HBM roofline; FP32/batched/adjoint vs FP64 plain
 UNIT = "MLUPS"
 BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36}   # 9 loads + 9 stores of one population
 PREC_ID = {"f64": 0, "f32": 1, "f16": 2}
+LEGS = ("f64", "f16", "batched", "adjoint", "sedimenting", "paper")   # comparison legs after the headline
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 CSRC = os.path.join(ROOT, "paper_1905_05110_gb300", "csrc")
@@ -299,7 +300,7 @@ def run_ours(args, rank, world, local_rank):
     compare = {}
     if not args.no_compare and rank == 0:
         for other in ("f64", "f16"):
-            if other == prec:
+            if other == prec or (args.legs and other not in args.legs.split(",")):
                 continue
             s2 = vp.Simulation(p, precision=other, history_capacity=4096, stream=stream)
             s2.init_from_problem()
@@ -317,13 +318,19 @@ def run_ours(args, rank, world, local_rank):
         if "f64" in compare:
             compare["speedup_vs_f64"] = (nodes * args.steps / dt / 1e6) / compare["f64"]["mlups"]
 
-    if not args.no_compare and world > 1:
+    legs = set(args.legs.split(",")) if args.legs else set(LEGS)
+    if not args.no_compare and world > 1 and "batched" in legs:
         compare["batched_sharded"] = run_sharded_sweep(args, torch, stream, rank, world, dev)
     if not args.no_compare and rank == 0:
-        compare["batched"] = run_batched(args, torch, stream)
-        compare["adjoint"] = run_adjoint(args, torch, compare.get("f64"))
-        compare["sedimenting_disk"] = run_other_workload("sedimenting_1024x4096", 8000, torch, stream)
-        compare["paper_oscillating_cylinder"] = run_other_workload("paper_cylinder_1230x410", 40000, torch, stream)
+        if "batched" in legs:
+            compare["batched"] = run_batched(args, torch, stream)
+        if "adjoint" in legs:
+            compare["adjoint"] = run_adjoint(args, torch, compare.get("f64"))
+        if "sedimenting" in legs:
+            compare["sedimenting_disk"] = run_other_workload("sedimenting_1024x4096", 8000, torch, stream)
+        if "paper" in legs:
+            compare["paper_oscillating_cylinder"] = run_other_workload("paper_cylinder_1230x410", 40000, torch,
+                                                                       stream)
 
     base = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -453,6 +460,7 @@ def run_adjoint(args, torch, f64_compare):
     nodes = p["nx"] * p["ny"]
     sim = vp.Simulation(p, precision="f32", history_capacity=nsteps + 8)
     sim.init_from_problem()
+    launch = sim.autotune(8)   # the forward and recomputed steps use the tuned step kernel
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     grad, js = sim.adjoint(nsteps, nsteps // 2, 1.0, 1.0, checkpoint_interval=ck)
@@ -462,7 +470,7 @@ def run_adjoint(args, torch, f64_compare):
     sim.close()
     nparams = p["ny"] + 3
     out = {"lattice": f"{p['nx']}x{p['ny']}", "steps": nsteps, "checkpoint_interval": ck, "params": nparams,
-           "seconds": dt, "forward_f32_seconds": t_fwd, "J": js,
+           "seconds": dt, "forward_f32_seconds": t_fwd, "J": js, "launch": list(launch),
            "speedup_vs_fd_f32_forward": 2 * nparams * t_fwd / dt,
            "grad_norm": float(np.linalg.norm(grad))}
     if f64_compare:
@@ -517,6 +525,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="", help="comma-separated subset of " + ",".join(LEGS) + " (default: all)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -27,11 +27,39 @@
 namespace vplbm {
 namespace {
 
-// Per-step inputs of the reverse kernels.
+// Per-step inputs of the reverse kernels, with the FP32 copies and the
+// pose-derived values the FP32 kernels use (no FP64 on their main path:
+// GB300's FP64 pipe is narrow).
 struct AdjStep {
     double xg, yg, vx, vy, om;   // pose and velocity of step n
     double wx, wy;               // dJ/dF_h(n)
+    int ilo, ihi, jlo, jhi;      // node range that may be solid (ilo > ihi: none)
+    int xi, yi;                  // floor(x_G), floor(y_G)
+    float xf, yf;                // x_G - xi, y_G - yi
+    float vxf, vyf, omf, wxf, wyf;
 };
+
+// chi of node (i, j) at the pose of a, decided exactly as by the forward
+// kernel (FP32 test relative to floor(x_G), FP64 re-test inside the band).
+template <typename T>
+__device__ __forceinline__ bool chi_adj(const StepParams &p, const AdjStep &a, int i, int j, T &dx, T &dy)
+{
+    dx = 0;
+    dy = 0;
+    if (!p.body.present || i < a.ilo || i > a.ihi || j < a.jlo || j > a.jhi) return false;
+    if constexpr (sizeof(T) == 4) {
+        dx = (float)(i - a.xi) - a.xf;
+        dy = (float)(j - a.yi) - a.yf;
+        const float d2 = dx * dx + dy * dy;
+        const float r2 = p.r2f;
+        if (fabsf(d2 - r2) <= 1e-5f * r2 + 1e-5f) return chi_exact(i, j, a.xg, a.yg, p.body.r2);
+        return d2 <= r2;
+    } else {
+        dx = (double)i - a.xg;
+        dy = (double)j - a.yg;
+        return chi_exact(i, j, a.xg, a.yg, p.body.r2);
+    }
+}
 
 // Moments of a 9-vector with the rows of Eq. (15): (rho, e, eps, jx, qx, jy, qy, pxx, pxy).
 template <typename T> __device__ __forceinline__ void moments9(const T f[NQ], T m[NQ])
@@ -63,12 +91,6 @@ template <typename T> __device__ __forceinline__ void mt9(const T L[NQ], T out[N
     out[8] = L[0] + (T)2 * L[1] + L[2] + L[3] + L[4] - L[5] - L[6] - L[8];
 }
 
-__device__ __forceinline__ bool chi_near(int i, int j, double xg, double yg, double radius, double r2)
-{
-    if (fabs((double)i - xg) > radius + 1.0 || fabs((double)j - yg) > radius + 1.0) return false;
-    return chi_exact(i, j, xg, yg, r2);
-}
-
 // (a) mu = (dC/df)^T lam_next + objective term; parameter-gradient partials
 // acc[block][0..3] += (d_eta, d_s1, d_s7, d_s8).
 template <int P>
@@ -96,17 +118,18 @@ __global__ void __launch_bounds__(256) adj_collide(const StepParams p, const Adj
         T m[NQ];
         moments9<T>(f, m);
         const T rs = m[0];
-        const T rho = DEV ? (T)p.rho0 + rs : rs;
+        const T rho = DEV ? par<T>(p.rho0, p.rho0f) + rs : rs;
+        const T inv_rho = recip(rho);
         const T jx = m[3], jy = m[5];
-        const bool chi = p.body.present && chi_near(i, j, a.xg, a.yg, p.body.radius, p.body.r2);
-        const T gx = (T)p.gx, gy = (T)p.gy;
-        const T vx = jx / rho + (T)0.5 * gx, vy = jy / rho + (T)0.5 * gy;
+        T dx, dy;
+        const bool chi = chi_adj<T>(p, a, i, j, dx, dy);
+        const T gx = par<T>(p.gx, p.gxf), gy = par<T>(p.gy, p.gyf);
+        const T vx = jx * inv_rho + (T)0.5 * gx, vy = jy * inv_rho + (T)0.5 * gy;
         T ax = 0, ay = 0, usx = 0, usy = 0, k = 0;
         if (chi) {
-            const double dx = (double)i - a.xg, dy = (double)j - a.yg;
-            usx = (T)(a.vx - a.om * dy);
-            usy = (T)(a.vy + a.om * dx);
-            k = (T)p.pen_k;
+            usx = par<T>(a.vx, a.vxf) - par<T>(a.om, a.omf) * dy;
+            usy = par<T>(a.vy, a.vyf) + par<T>(a.om, a.omf) * dx;
+            k = par<T>(p.pen_k, p.pen_kf);
             ax = -k * (vx - usx);
             ay = -k * (vy - usy);
         }
@@ -116,7 +139,8 @@ __global__ void __launch_bounds__(256) adj_collide(const StepParams p, const Adj
         const T uG = ux * Gx + uy * Gy;
         const T W1 = rho * (ux * ux - uy * uy), W2 = ux * Gx - uy * Gy;
         const T W3 = rho * ux * uy, W4 = ux * Gy + uy * Gx;
-        const T s1 = (T)p.s[1], s2 = (T)p.s[2], s4 = (T)p.s[4], s6 = (T)p.s[6], s7 = (T)p.s[7], s8 = (T)p.s[8];
+        const T s1 = par<T>(p.s[1], p.sf[1]), s2 = par<T>(p.s[2], p.sf[2]), s4 = par<T>(p.s[4], p.sf[4]);
+        const T s6 = par<T>(p.s[6], p.sf[6]), s7 = par<T>(p.s[7], p.sf[7]), s8 = par<T>(p.s[8], p.sf[8]);
         const T h1 = (T)1 - (T)0.5 * s1, h2 = (T)1 - (T)0.5 * s2, h4 = (T)1 - (T)0.5 * s4;
         const T h6 = (T)1 - (T)0.5 * s6, h7 = (T)1 - (T)0.5 * s7, h8 = (T)1 - (T)0.5 * s8;
 
@@ -164,9 +188,9 @@ __global__ void __launch_bounds__(256) adj_collide(const StepParams p, const Adj
             g4[0] = k * k * ((vx - usx) * l_ax + (vy - usy) * l_ay);
         }
         // v = j / rho + g/2
-        l_jx += l_vx / rho;
-        l_jy += l_vy / rho;
-        l_rho += -(l_vx * jx + l_vy * jy) / (rho * rho);
+        l_jx += l_vx * inv_rho;
+        l_jy += l_vy * inv_rho;
+        l_rho += -(l_vx * jx + l_vy * jy) * (inv_rho * inv_rho);
         l_rs += l_rho;
         lm[0] = l_rs;
         lm[3] = l_jx;
@@ -174,8 +198,9 @@ __global__ void __launch_bounds__(256) adj_collide(const StepParams p, const Adj
         T out[NQ];
         mt9<T>(lm, out);
         if (chi) {
+            const T wx = par<T>(a.wx, a.wxf), wy = par<T>(a.wy, a.wyf);
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) out[q] += (T)(a.wx * cx_of(q) + a.wy * cy_of(q));
+            for (int q = 0; q < NQ; ++q) out[q] += (T)cx_of(q) * wx + (T)cy_of(q) * wy;
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) mu[q * p.ps + b] = out[q];
@@ -228,7 +253,9 @@ __global__ void __launch_bounds__(256) adj_stream(const StepParams p, const AdjS
     const int nx = p.nx, ny = p.ny;
     const long long ps = p.ps;
     auto MU = [&](int q, int ii, int jj) { return mu[q * ps + (long long)jj * nx + ii]; };
-    const bool chi = p.body.present && chi_near(i, j, a.xg, a.yg, p.body.radius, p.body.r2);
+    T dxu, dyu;
+    const bool chi = chi_adj<T>(p, a, i, j, dxu, dyu);
+    const T wx = par<T>(a.wx, a.wxf), wy = par<T>(a.wy, a.wyf);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         T acc = 0;
@@ -265,7 +292,7 @@ __global__ void __launch_bounds__(256) adj_stream(const StepParams p, const AdjS
                 if (pull_kind(p, q, i, zj, &sd) == PULL_ZEROGRAD) acc += MU(q, i, zj);
             }
         }
-        if (chi) acc -= (T)(a.wx * cx_of(q) + a.wy * cy_of(q));
+        if (chi) acc -= (T)cx_of(q) * wx + (T)cy_of(q) * wy;
         lam[q * ps + (long long)j * nx + i] = acc;
     }
     // inlet profile: the west velocity-wall pulls of this node
@@ -391,7 +418,12 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
     const double J1 = qref > 0 ? scd / nh : 0.0, J2 = qref > 0 ? sqrt(scl2 / nh) : 0.0;
     if (j_out) { j_out[0] = J1; j_out[1] = J2; }
 
-    // reverse sweep, segment by segment
+    // reverse sweep, segment by segment; the recomputation runs the
+    // context's scalar step kernel (a TMA-staged choice falls back to the
+    // 48-register scalar kernel on 256 x 1 blocks)
+    const bool scalar = c->kernel != KERNEL_TMA;
+    const int rbx = scalar ? c->bx : 256, rby = scalar ? c->by : 1;
+    const int rminb = !scalar ? 5 : c->kernel == KERNEL_SCALAR_40 ? 6 : c->kernel == KERNEL_SCALAR_48 ? 5 : 4;
     int cur = 0;   // work: lam[0], lam[1], mu
     for (long long s = nck - 1; s >= 0; --s) {
         const long long s0 = s * K, len = std::min(K, N - s0);
@@ -403,13 +435,15 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
         b.step = step0 + s0;
         derive_pose(b, c->has_body, c->has_body ? c->body_desc.radius : 0.0, c->nx, c->ny);
         ATRY(cudaMemcpyAsync(c->bs + (c->nstep & 1), &b, sizeof b, cudaMemcpyHostToDevice, st));
-        ATRY(cudaMemcpyAsync(c->f[c->nstep & 1], ckpt + pop * s, pop, cudaMemcpyDeviceToDevice, st));
-        for (long long k = 0; k < len; ++k) {
-            ATRY(cudaMemcpyAsync(store + pop * k, c->f[c->nstep & 1], pop, cudaMemcpyDeviceToDevice, st));
-            if (k + 1 < len) {
-                r = vplbm_step(c, 1);
-                if (r != VPLBM_OK) { cleanup(); return r; }
-            }
+        ATRY(cudaMemcpyAsync(store, ckpt + pop * s, pop, cudaMemcpyDeviceToDevice, st));
+        for (long long k = 0; k + 1 < len; ++k) {
+            // S_{s0+k} -> S_{s0+k+1} straight from one slot of the store to
+            // the next (the context's scalar kernel and block shape)
+            StepParams q = ctx_params(c, step0 + s0 + k);
+            q.fin = store + pop * k;
+            q.fout = store + pop * (k + 1);
+            set_planes(q, (int)es);
+            ATRY(launch_step(c->precision, q, rbx, rby, st, rminb));
         }
         for (long long n = s0 + len - 1; n >= s0; --n) {
             StepParams p = ctx_params(c, step0 + n);
@@ -422,6 +456,16 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
             if (n >= d->window_start && qref > 0) {
                 a.wx = d->w_cd / (qref * nh);
                 a.wy = J2 > 0 ? d->w_cl * (h[n].fy / qref) / (J2 * qref * nh) : 0.0;
+            }
+            {   // the pose-derived values, as the forward step derived them
+                BodyState bsn{};
+                bsn.q[0] = a.xg; bsn.q[1] = a.yg;
+                bsn.v[0] = a.vx; bsn.v[1] = a.vy; bsn.v[2] = a.om;
+                derive_pose(bsn, c->has_body, c->has_body ? c->body_desc.radius : 0.0, c->nx, c->ny);
+                a.ilo = bsn.ilo; a.ihi = bsn.ihi; a.jlo = bsn.jlo; a.jhi = bsn.jhi;
+                a.xi = bsn.xi; a.yi = bsn.yi; a.xf = bsn.xf; a.yf = bsn.yf;
+                a.vxf = bsn.vxf; a.vyf = bsn.vyf; a.omf = bsn.omf;
+                a.wxf = (float)a.wx; a.wyf = (float)a.wy;
             }
             void *lam_next = work + lam_bytes * cur, *lam_new = work + lam_bytes * (cur ^ 1), *mu = work + 2 * lam_bytes;
             cudaError_t e = c->precision == VPLBM_F64

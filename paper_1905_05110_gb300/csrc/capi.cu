@@ -213,7 +213,8 @@ cudaError_t launch_one(const vplbm_ctx *c, long long step, cudaStream_t stream)
 }
 
 
-// Reduction tile of a launch choice (the pair kernel's block covers 2*bx).
+// Reduction tile of a launch choice: the block for the scalar kernels, the
+// TMA kernel's fixed tile otherwise.
 void tile_of(int kernel, int bx, int by, int *w, int *h)
 {
     if (kernel == KERNEL_TMA) { *w = TMA_TILE_W; *h = TMA_TILE_H; }
@@ -857,8 +858,6 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
             st = fail(VPLBM_ECUDA, "autotune setup failed");
             break;
         }
-        // candidates: the TMA-staged kernel, then every shape of the paired
-        // and of the scalar kernel
         // candidates: the TMA-staged kernel, then every block shape of the
         // three register budgets of the scalar kernel
         static const int kinds[3] = {KERNEL_SCALAR_48, KERNEL_SCALAR_40, KERNEL_SCALAR};

@@ -38,6 +38,16 @@ static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 && opp_of(4) ==
 static_assert(opp_of(5) == 7 && opp_of(6) == 8 && opp_of(7) == 5 && opp_of(8) == 6, "opp diag");
 static_assert(cx_of(miry_of(6)) == cx_of(6) && cy_of(miry_of(6)) == -cy_of(6) && cy_of(miry_of(2)) == -1, "mirror");
 
+// 1/x: FP64 division, or in FP32 the hardware reciprocal estimate refined
+// by one Newton-Raphson step, r1 = r0 + r0 (1 - x r0) (within an ulp or two).
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x)
+{
+    float r0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(x));
+    return fmaf(r0, fmaf(-x, r0, 1.0f), r0);
+}
+
 // A parameter in the kernel's arithmetic type: the FP64 value for the FP64
 // kernel, the host-rounded FP32 copy otherwise (no conversion on the device).
 template <typename T> __device__ __forceinline__ T par(double d, float f);
@@ -443,16 +453,7 @@ __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState
     }
 
     // penalized velocity, Eq. (22) in the eta-stable form
-    T inv_rho;
-    if constexpr (DEV) {
-        // hardware reciprocal estimate refined by one Newton-Raphson step,
-        // r1 = r0 + r0 (1 - rho r0): within an ulp or two of 1/rho
-        float r0;
-        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"((float)rho));
-        inv_rho = fmaf(r0, fmaf(-(float)rho, r0, 1.0f), r0);
-    } else {
-        inv_rho = (T)1 / rho;
-    }
+    const T inv_rho = recip(rho);
     const T gx = par<T>(p.gx, p.gxf), gy = par<T>(p.gy, p.gyf);
     const T vx = jx * inv_rho + (T)0.5 * gx;
     const T vy = jy * inv_rho + (T)0.5 * gy;
