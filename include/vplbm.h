@@ -347,8 +347,8 @@ vplbm_status vplbm_batch_set_launch(vplbm_batch *batch, int block_x, int block_y
 vplbm_status vplbm_batch_get_launch(vplbm_batch *batch, int *block_x, int *block_y, int *tiles_per_block,
                                    long long *launches);
 /* Time the branch mode and six tile-mode launch shapes over 2 x
- * steps_per_trial steps each and keep the fastest; the trial steps advance
- * the members (they are real steps). */
+ * steps_per_trial steps each (rounded up to whole 32-step graphs) and keep
+ * the fastest; the trial steps advance the members (they are real steps). */
 vplbm_status vplbm_batch_autotune(vplbm_batch *batch, int steps_per_trial);
 
 /* ---- allocation-free stepping --------------------------------------------

@@ -52,6 +52,7 @@ struct vplbm_batch {
     std::vector<cudaEvent_t> join;     // [0]: fork, [1 + k]: end of branch k
     cudaGraphExec_t graph = nullptr;
     int graph_bx = -1, graph_by = -1, graph_rows = -1, graph_mode = -1;
+    std::vector<int> graph_members;   // branch mode: each member's (kernel, bx, by) when captured
     long long launches = 0;
 };
 
@@ -159,10 +160,24 @@ cudaError_t capture_batch_steps(vplbm_batch *b)
     return e;
 }
 
+// The members' launch choices a branch graph bakes in.
+std::vector<int> member_launches(const vplbm_batch *b)
+{
+    std::vector<int> v;
+    v.reserve(3 * (size_t)b->n);
+    for (const vplbm_ctx *c : b->members) {
+        v.push_back(c->kernel);
+        v.push_back(c->bx);
+        v.push_back(c->by);
+    }
+    return v;
+}
+
 vplbm_status ensure_batch_graph(vplbm_batch *b)
 {
+    const std::vector<int> ml = b->mode == VPLBM_BATCH_BRANCHES ? member_launches(b) : std::vector<int>();
     if (b->graph && b->graph_mode == b->mode && b->graph_bx == b->bx && b->graph_by == b->by &&
-        b->graph_rows == b->rows)
+        b->graph_rows == b->rows && b->graph_members == ml)
         return VPLBM_OK;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
@@ -188,6 +203,7 @@ vplbm_status ensure_batch_graph(vplbm_batch *b)
     b->graph_bx = b->bx;
     b->graph_by = b->by;
     b->graph_rows = b->rows;
+    b->graph_members = ml;
     return VPLBM_OK;
 }
 
@@ -363,8 +379,19 @@ vplbm_status vplbm_batch_get_launch(vplbm_batch *b, int *block_x, int *block_y, 
 vplbm_status vplbm_batch_autotune(vplbm_batch *b, int steps_per_trial)
 {
     if (!b) return berr(VPLBM_EINVAL, "batch is NULL");
-    if (steps_per_trial < 2) steps_per_trial = 2;
-    steps_per_trial += steps_per_trial & 1;
+    // whole graphs: the modes are compared as they run (a branch-mode step
+    // outside a graph launches the members one after another)
+    if (steps_per_trial < BATCH_GRAPH_STEPS) steps_per_trial = BATCH_GRAPH_STEPS;
+    steps_per_trial = (steps_per_trial + BATCH_GRAPH_STEPS - 1) / BATCH_GRAPH_STEPS * BATCH_GRAPH_STEPS;
+    {   // start the trials at an even step so that they run as graphs
+        long long step;
+        vplbm_status st0 = common_step(b, &step);
+        if (st0 != VPLBM_OK) return st0;
+        if (step & 1) {
+            st0 = batch_step_impl(b, 1);
+            if (st0 != VPLBM_OK) return st0;
+        }
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return berr(VPLBM_ECUDA, "event creation failed");
