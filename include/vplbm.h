@@ -1,9 +1,10 @@
 /*
  * vplbm.h - C ABI of the GB300 volume-penalization lattice Boltzmann library.
  *
- * The library advances a D2Q9 multiple-relaxation-time lattice Boltzmann
- * fluid in which a rigid disk is represented by a characteristic function
- * chi and enters the fluid as a penalization force (Liberge & Beghein,
+ * The library advances a D2Q9 multiple-relaxation-time (or BGK) lattice
+ * Boltzmann fluid in which a rigid body (disk or ellipse) is represented by
+ * a characteristic function chi and enters the fluid as a penalization
+ * force (Liberge & Beghein,
  * "Fluid Structure Interaction modelling using Lattice Boltzmann and Volume
  * Penalization method", Sec. 2).  One time step is Algorithm 1 of Sec. 2.3:
  * collide and stream (Eqs. 17-18), macroscopic moments with the penalized
@@ -54,8 +55,10 @@ typedef enum {
 } vplbm_status;
 
 /* Storage precision of the populations.  Arithmetic is FP64 for VPLBM_F64
- * and FP32 otherwise; force/torque sums and the body update are always FP64.
- * The _DEV variants store f_a - w_a rho0 (deviation from rest). */
+ * and FP32 otherwise.  The force/torque sums are FP64 for VPLBM_F64 and
+ * float-float (about 44 bits, converted exactly to FP64) otherwise; the body
+ * update is always FP64.  The _DEV variants store f_a - w_a rho0 (deviation
+ * from rest). */
 typedef enum { VPLBM_F64 = 0, VPLBM_F32_DEV = 1, VPLBM_F16_DEV = 2 } vplbm_precision;
 
 /* Boundary kinds of one lattice edge (Sec. 3.1 / 3.2):
@@ -238,10 +241,11 @@ vplbm_status vplbm_get_body(vplbm_ctx *ctx, double q[3], double v[3], long long 
 /* Step kernels.  Both compute the same method; they differ in data movement:
  *  VPLBM_KERNEL_SCALAR     one node per thread, its nine pulls loaded straight
  *                          into registers (every precision), register budget
- *                          of 4 blocks of 256 threads per SM (64 registers);
- *  VPLBM_KERNEL_SCALAR_48  the same sized for 5 blocks (48 registers): the
- *                          default;
- *  VPLBM_KERNEL_SCALAR_40  the same sized for 6 blocks (40 registers);
+ *                          of 4 blocks of 256 threads per SM (64 registers):
+ *                          the default for FP64 storage;
+ *  VPLBM_KERNEL_SCALAR_48  the same sized for 5 blocks (48 registers);
+ *  VPLBM_KERNEL_SCALAR_40  the same sized for 6 blocks (40 registers): the
+ *                          default for FP32 / FP16 storage (256 x 1 blocks);
  *  VPLBM_KERNEL_TMA        persistent blocks fed by tensor-memory-accelerator
  *                          copies into a shared-memory ring (FP32/FP16
  *                          storage, nx * element size a multiple of 16 bytes,
@@ -346,9 +350,11 @@ vplbm_status vplbm_batch_get_mode(vplbm_batch *batch, int *mode);
 vplbm_status vplbm_batch_set_launch(vplbm_batch *batch, int block_x, int block_y, int tiles_per_block);
 vplbm_status vplbm_batch_get_launch(vplbm_batch *batch, int *block_x, int *block_y, int *tiles_per_block,
                                    long long *launches);
-/* Time the branch mode and six tile-mode launch shapes over 2 x
- * steps_per_trial steps each (rounded up to whole 32-step graphs) and keep
- * the fastest; the trial steps advance the members (they are real steps). */
+/* Time the branch mode with four member launch choices (every member set to
+ * one scalar kernel and block shape) and six tile-mode launch shapes over
+ * 2 x steps_per_trial steps each (rounded up to whole 32-step graphs) and
+ * keep the fastest (members keep the winning launch choice); the trial
+ * steps advance the members (they are real steps). */
 vplbm_status vplbm_batch_autotune(vplbm_batch *batch, int steps_per_trial);
 
 /* ---- allocation-free stepping --------------------------------------------

@@ -397,16 +397,26 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int steps_per_trial)
         return berr(VPLBM_ECUDA, "event creation failed");
     float best = 1e30f;
     int best_bx = b->bx, best_by = b->by, best_rows = b->rows, best_mode = b->mode;
+    int best_mk = -1, best_mbx = 0, best_mby = 0;   // branch mode: the members' launch choice
     vplbm_status st = VPLBM_OK;
-    // {-1, 0, 0}: branch mode (the members' own launch shapes); the rest: tile mode shapes
-    const int cands[7][3] = {{-1, 0, 0}, {256, 1, 8}, {256, 1, 4}, {256, 1, 16}, {128, 2, 4}, {128, 1, 8}, {256, 1, 1}};
+    // branch mode with every member on one scalar kernel and block shape
+    // (mode, kernel, bx, by), then tile-mode shapes (mode, bx, by, rows)
+    const int cands[10][4] = {{VPLBM_BATCH_BRANCHES, KERNEL_SCALAR_40, 256, 1},
+                              {VPLBM_BATCH_BRANCHES, KERNEL_SCALAR_48, 256, 1},
+                              {VPLBM_BATCH_BRANCHES, KERNEL_SCALAR_48, 128, 2},
+                              {VPLBM_BATCH_BRANCHES, KERNEL_SCALAR_40, 64, 2},
+                              {VPLBM_BATCH_TILES, 256, 1, 8}, {VPLBM_BATCH_TILES, 256, 1, 4},
+                              {VPLBM_BATCH_TILES, 256, 1, 16}, {VPLBM_BATCH_TILES, 128, 2, 4},
+                              {VPLBM_BATCH_TILES, 128, 1, 8}, {VPLBM_BATCH_TILES, 256, 1, 1}};
     for (const auto &cb : cands) {
-        const int bx = cb[0], by = cb[1], rows = cb[2];
-        if (bx < 0) {
+        if (cb[0] == VPLBM_BATCH_BRANCHES) {
+            bool ok = true;
+            for (vplbm_ctx *m : b->members) ok = ok && vplbm_set_launch(m, cb[1], cb[2], cb[3]) == VPLBM_OK;
+            if (!ok) continue;   // a member's reduction scratch does not fit this shape
             b->mode = VPLBM_BATCH_BRANCHES;
         } else {
             b->mode = VPLBM_BATCH_TILES;
-            st = vplbm_batch_set_launch(b, bx, by, rows);
+            st = vplbm_batch_set_launch(b, cb[1], cb[2], cb[3]);
             if (st != VPLBM_OK) break;
         }
         for (int rep = 0; rep < 2 && st == VPLBM_OK; ++rep) {
@@ -422,10 +432,17 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int steps_per_trial)
                 best_bx = b->bx;
                 best_by = b->by;
                 best_rows = b->rows;
+                if (cb[0] == VPLBM_BATCH_BRANCHES) {
+                    best_mk = cb[1];
+                    best_mbx = cb[2];
+                    best_mby = cb[3];
+                }
             }
         }
         if (st != VPLBM_OK) break;
     }
+    if (best_mk >= 0)
+        for (vplbm_ctx *m : b->members) vplbm_set_launch(m, best_mk, best_mbx, best_mby);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->mode = best_mode;

@@ -409,8 +409,9 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     p.hist_cap = cap;
 
     setup_tma(c);
-    // default: the scalar kernel sized for 5 blocks of 256 threads per SM
-    c->kernel = KERNEL_SCALAR_48;
+    // default: the scalar kernel sized for 6 blocks of 256 threads per SM
+    // (FP32 / FP16: no spills at 40 registers), 4 for the FP64 one
+    c->kernel = c->precision == VPLBM_F64 ? KERNEL_SCALAR : KERNEL_SCALAR_40;
     c->bx = 256;
     c->by = 1;
     // populations at rest
