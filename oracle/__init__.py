@@ -72,7 +72,7 @@ class Body(C.Structure):
                 ("shape", C.c_int), ("radius_b", C.c_double)]
 
 
-SHAPES = {"disk": 0, "ellipse": 1}
+SHAPES = {"disk": 0, "ellipse": 1, "rectangle": 2}
 
 
 class Record(C.Structure):

@@ -139,7 +139,7 @@ enum { ORC_PERIODIC = 0, ORC_NOSLIP = 1, ORC_VELOCITY = 2, ORC_ZEROGRAD = 3, ORC
 enum { ORC_WEST = 0, ORC_EAST = 1, ORC_SOUTH = 2, ORC_NORTH = 3 };
 enum { ORC_FIXED = 0, ORC_IMPOSED = 1, ORC_FREE = 2 };
 enum { ORC_MRT = 0, ORC_BGK = 1 };
-enum { ORC_DISK = 0, ORC_ELLIPSE = 1 };
+enum { ORC_DISK = 0, ORC_ELLIPSE = 1, ORC_RECT = 2 };
 
 typedef struct {
     int nx, ny;
@@ -202,7 +202,8 @@ static double edge_u(const orc_sim *s, int side, int comp, int k)
 /* chi of Eq. (2) for the body at the current pose (reading R1).  Disk:
  * |x - x_G| <= R.  Ellipse of semi-axes a (along the body's x axis, at the
  * angle theta of the pose) and b: with u, v the node's coordinates in the
- * body frame, b^2 u^2 + a^2 v^2 <= a^2 b^2. */
+ * body frame, b^2 u^2 + a^2 v^2 <= a^2 b^2.  Rectangle of half-sides a, b
+ * along the same axes: |u| <= a and |v| <= b. */
 static int chi_at(const orc_sim *s, int i, int j)
 {
     if (!s->body.present) return 0;
@@ -214,6 +215,12 @@ static int chi_at(const orc_sim *s, int i, int j)
         double u = dx * c + dy * sn;
         double v = dy * c - dx * sn;
         return b2 * (u * u) + a2 * (v * v) <= a2 * b2;
+    }
+    if (s->body.shape == ORC_RECT) {
+        double c = cos(s->q[2]), sn = sin(s->q[2]);
+        double u = dx * c + dy * sn;
+        double v = dy * c - dx * sn;
+        return fabs(u) <= s->body.radius && fabs(v) <= s->body.radius_b;
     }
     double d2 = dx * dx + dy * dy;
     double r2 = s->body.radius * s->body.radius;

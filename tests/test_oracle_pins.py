@@ -605,6 +605,75 @@ def test_rotating_ellipse_angular_momentum_balance():
     assert sim.body_state()[0][2] > 0.2 and len(nsolid) > 1   # it turned, and its solid set changed
 
 
+def _rect_sim(a, b, theta, x=20.37, y=15.61, nx=41, ny=31):
+    body = {"radius": a, "radius_b": b, "shape": "rectangle", "x": x, "y": y, "theta": theta,
+            "motion": "fixed"}
+    return oracle.OracleSim(wl.periodic_box(nx, ny, body=body))
+
+
+def test_rectangle_geometry():
+    # Half-sides a along the body's x axis at angle theta and b across it:
+    # the four corners' neighbourhoods, the mid-sides, the symmetries of a
+    # rectangle (theta + pi, and (a, b, theta) -> (b, a, theta + pi/2)), and
+    # the area 4ab within a perimeter's worth of nodes.
+    a, b = 8.6, 3.3
+    xg, yg = 20.37, 15.61
+    for theta in (0.0, 0.3, math.pi / 2, 1.9):
+        chi = _rect_sim(a, b, theta).chi()
+        c, s = math.cos(theta), math.sin(theta)
+        ex, ey = (c, s), (-s, c)
+
+        def node(u, v):
+            return int(round(xg + u * ex[0] + v * ey[0])), int(round(yg + u * ex[1] + v * ey[1]))
+
+        for su in (1, -1):
+            for sv in (1, -1):
+                i, j = node(su * (a - 1.2), sv * (b - 1.2))   # inside near each corner
+                assert chi[j, i] == 1
+                i, j = node(su * (a + 1.2), sv * (b + 1.2))   # outside past each corner
+                assert chi[j, i] == 0
+        for su in (1, -1):
+            i, j = node(su * (a + 1.2), 0.0)
+            assert chi[j, i] == 0
+            i, j = node(0.0, su * (b + 1.2))
+            assert chi[j, i] == 0
+        assert np.array_equal(chi, _rect_sim(a, b, theta + math.pi).chi()) or theta == 0.0
+        assert np.sum(chi != _rect_sim(b, a, theta + math.pi / 2).chi()) <= 2
+        assert abs(chi.sum() - 4 * a * b) < 2 * 2 * (a + b)
+
+
+def test_rotating_rectangle_angular_momentum_balance():
+    a, b = 7.5, 2.5
+    inertia = 4000.0   # 2.5x the displaced fluid's: a stable explicit coupling
+    body = {"radius": a, "radius_b": b, "shape": "rectangle", "x": 31.4, "y": 32.2, "theta": 0.2,
+            "omega": 0.02, "motion": "free", "mass": 1.0, "inertia": inertia, "dof_mask": 4}
+    n = 64
+    p = wl.periodic_box(n, n, tau=0.7, eta=1e-3, body=body)
+    sim = oracle.OracleSim(p)
+    sim.init_equilibrium()
+    c, _, _, _ = oracle.constants()
+    X, Y = np.meshgrid(np.arange(float(n)), np.arange(float(n)))
+
+    def ang(f):
+        jx = np.tensordot(c[:, 0], f, axes=1)
+        jy = np.tensordot(c[:, 1], f, axes=1)
+        return np.sum((X - body["x"]) * jy - (Y - body["y"]) * jx)
+
+    L_prev = ang(sim.populations())
+    w_prev = sim.body_state()[1][2]
+    nsolid = set()
+    for k in range(16):
+        sim.step(1)
+        rec = sim.history(k, 1)[0]
+        L = ang(sim.populations())
+        assert abs((L - L_prev) + rec[14]) < 1e-13 + 1e-15 * (abs(L) + abs(L_prev))   # rounding of sums of ~1e2
+        w = sim.body_state()[1][2]
+        assert abs(inertia * (w - w_prev) - rec[3]) < 1e-13 + 1e-12 * abs(rec[3])
+        L_prev, w_prev = L, w
+        nsolid.add(rec[15])
+    assert len(nsolid) > 1
+
+
 def test_rk4_free_fall_is_exact():
     body = {"radius": 1.0, "x": 0, "y": 0, "motion": "free", "mass": 3.0, "inertia": 5.0,
             "f_ext": (0.2, -0.5, 0.1), "dof_mask": 7}
