@@ -127,12 +127,13 @@ typedef enum {
  * ELLIPSE: semi-axis `radius` along the body's x axis, at the angle theta
  * of the pose, and `radius_b` across it: with u = dx cos(theta) + dy
  * sin(theta), v = dy cos(theta) - dx sin(theta), chi = 1 iff
- * radius_b^2 u^2 + radius^2 v^2 <= radius^2 radius_b^2.  Both in FP64
- * without fused multiply-add; the ellipse's cos / sin come from the host's
- * math library for a pose set on the host and from CUDA's for a pose the
- * GPU advanced (they may differ in the last bit).  The ellipse is not
- * supported by the adjoint. */
-typedef enum { VPLBM_SHAPE_DISK = 0, VPLBM_SHAPE_ELLIPSE = 1 } vplbm_shape;
+ * radius_b^2 u^2 + radius^2 v^2 <= radius^2 radius_b^2.  RECTANGLE: half-
+ * sides `radius` and `radius_b` along the same axes, chi = 1 iff |u| <=
+ * radius and |v| <= radius_b.  All in FP64 without fused multiply-add; the
+ * cos / sin of theta come from the host's math library for a pose set on
+ * the host and from CUDA's for a pose the GPU advanced (they may differ in
+ * the last bit).  The adjoint takes the disk only. */
+typedef enum { VPLBM_SHAPE_DISK = 0, VPLBM_SHAPE_ELLIPSE = 1, VPLBM_SHAPE_RECTANGLE = 2 } vplbm_shape;
 
 /* Rigid body (disk or ellipse, see vplbm_shape).  The rigid velocity at a node is
  * u_s = (vx - omega (y - y_G), vy + omega (x - x_G)).

@@ -333,7 +333,7 @@ def vplbm_get_body(ctx):
 
 
 COLLISIONS = {"mrt": 0, "bgk": 1}
-SHAPES = {"disk": 0, "ellipse": 1}
+SHAPES = {"disk": 0, "ellipse": 1, "rectangle": 2}
 BATCH_MODES = {"branches": 0, "tiles": 1}
 BATCH_MODE_NAMES = {v: k for k, v in BATCH_MODES.items()}
 KERNELS = {"scalar": 0, "scalar48": 1, "scalar40": 2, "tma": 3}

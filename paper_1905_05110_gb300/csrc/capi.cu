@@ -130,9 +130,10 @@ vplbm_status check_body(const vplbm_body_desc *b)
 {
     if (!b) return VPLBM_OK;
     if (!(b->radius >= 0.0) || b->radius > 1e6) return fail(VPLBM_EINVAL, "radius must be in [0, 1e6]");
-    if (b->shape != VPLBM_SHAPE_DISK && b->shape != VPLBM_SHAPE_ELLIPSE) return fail(VPLBM_EINVAL, "unknown shape %d", b->shape);
-    if (b->shape == VPLBM_SHAPE_ELLIPSE && (!(b->radius > 0.0) || !(b->radius_b > 0.0) || b->radius_b > 1e6))
-        return fail(VPLBM_EINVAL, "ellipse semi-axes must be in (0, 1e6]");
+    if (b->shape != VPLBM_SHAPE_DISK && b->shape != VPLBM_SHAPE_ELLIPSE && b->shape != VPLBM_SHAPE_RECTANGLE)
+        return fail(VPLBM_EINVAL, "unknown shape %d", b->shape);
+    if (b->shape != VPLBM_SHAPE_DISK && (!(b->radius > 0.0) || !(b->radius_b > 0.0) || b->radius_b > 1e6))
+        return fail(VPLBM_EINVAL, "semi-axes / half-sides must be in (0, 1e6]");
     const double vals[6] = {b->x, b->y, b->theta, b->vx, b->vy, b->omega};
     for (double v : vals)
         if (!isfinite(v) || fabs(v) > 1e7) return fail(VPLBM_EINVAL, "body pose/velocity must be finite and < 1e7");
@@ -296,7 +297,7 @@ void fill_dev_body(StepParams &p, const vplbm_lattice_desc *lat, const vplbm_bod
     b.r2 = body->radius * body->radius;
     b.shape = body->shape;
     // FP32 predicate b^2 u^2 + a^2 v^2 <= a^2 b^2 of both shapes (disk: a = b)
-    const double ra = body->radius, rb = body->shape == VPLBM_SHAPE_ELLIPSE ? body->radius_b : body->radius;
+    const double ra = body->radius, rb = body->shape == VPLBM_SHAPE_DISK ? body->radius : body->radius_b;
     b.a2 = ra * ra;
     b.b2 = rb * rb;
     b.ab2 = b.a2 * b.b2;
@@ -304,6 +305,13 @@ void fill_dev_body(StepParams &p, const vplbm_lattice_desc *lat, const vplbm_bod
     // its FP32 error stays below ~1e-6 a^2 b^2 (max / min semi-axis); 100x margin
     const double ratio = ra > 0.0 && rb > 0.0 ? fmax(ra, rb) / fmin(ra, rb) : 1.0;
     b.bandf = (float)(1e-4 * b.ab2 * ratio + 1e-5);
+    // rectangle: |u| <= a, |v| <= b; the FP32 error of u, v stays below
+    // ~3e-7 of the bounding radius, 30x margin
+    b.ra = ra;
+    b.rb = rb;
+    b.raf = (float)ra;
+    b.rbf = (float)rb;
+    b.bandr = (float)(1e-5 * bounding_radius(body) + 1e-5);
     p.r2f = (float)b.r2;
     b.amp = body->amp;
     b.freq = body->freq;

@@ -132,8 +132,9 @@ __global__ void fields_kernel(const StepParams p, double *rho_o, double *ux_o, d
     }
     const double rho = Prec<P>::DEV ? p.rho0 + rs : rs;
     const BodyState bs = *p.bs_in;
-    bool chi = p.body.present && (p.body.shape == VPLBM_SHAPE_ELLIPSE ? chi_exact_ellipse(i, j, &bs, p.body)
-                                                                    : chi_exact(i, j, bs.q[0], bs.q[1], p.body.r2));
+    bool chi = p.body.present && (p.body.shape == VPLBM_SHAPE_ELLIPSE     ? chi_exact_ellipse(i, j, &bs, p.body)
+                                  : p.body.shape == VPLBM_SHAPE_RECTANGLE ? chi_exact_rect(i, j, &bs, p.body)
+                                                                          : chi_exact(i, j, bs.q[0], bs.q[1], p.body.r2));
     double vx = jx / rho + 0.5 * p.gx, vy = jy / rho + 0.5 * p.gy;
     double ax = 0, ay = 0;
     if (chi) {
@@ -192,6 +193,8 @@ cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cuda
 {
     if (p.body.present && p.body.shape == VPLBM_SHAPE_ELLIPSE)
         return launch_step_ellipse(precision, p, bx, by, stream, minb);
+    if (p.body.present && p.body.shape == VPLBM_SHAPE_RECTANGLE)
+        return launch_step_rectangle(precision, p, bx, by, stream, minb);
     return launch_step_shape<VPLBM_SHAPE_DISK>(precision, p, bx, by, stream, minb);
 }
 

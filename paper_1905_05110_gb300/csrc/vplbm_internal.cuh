@@ -58,6 +58,8 @@ struct DevBody {
     int pad_shape;
     double a2, b2, ab2;          // ellipse: semi-axes squared and their product
     float a2f, b2f, ab2f, bandf; // FP32 copies; bandf: FP32 test band of the ellipse predicate
+    double ra, rb;               // rectangle: half-sides
+    float raf, rbf, bandr, pad_r; // FP32 copies; bandr: FP32 test band of |u| - a, |v| - b
 };
 
 // Number of doubles per block partial: fpen_x, fpen_y, tpen, fh_x, fh_y,
@@ -179,7 +181,7 @@ __host__ __device__ inline void derive_pose(BodyState &s, int present, double ra
     s.pad1 = 0.f;
     s.pad[0] = s.pad[1] = 0;
     s.cth = 1.0; s.sth = 0.0;
-    if (shape == VPLBM_SHAPE_ELLIPSE && isfinite(s.q[2])) {
+    if (shape != VPLBM_SHAPE_DISK && isfinite(s.q[2])) {
         s.cth = cos(s.q[2]);
         s.sth = sin(s.q[2]);
     }
@@ -203,7 +205,9 @@ void fill_dev_body(StepParams &p, const vplbm_lattice_desc *lat, const vplbm_bod
 inline double bounding_radius(const vplbm_body_desc *b)
 {
     if (!b) return 0.0;
-    return b->shape == VPLBM_SHAPE_ELLIPSE ? fmax(b->radius, b->radius_b) : b->radius;
+    if (b->shape == VPLBM_SHAPE_ELLIPSE) return fmax(b->radius, b->radius_b);
+    if (b->shape == VPLBM_SHAPE_RECTANGLE) return sqrt(b->radius * b->radius + b->radius_b * b->radius_b);
+    return b->radius;
 }
 
 // Step kernels a context can launch: the scalar kernel with the register
@@ -224,8 +228,9 @@ cudaError_t launch_step_batch(int precision, const BatchLaunch &bl, int total_ti
 
 // Launchers (step_kernels.cu).  All are asynchronous on `stream`.
 cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb = 4);
-// The same for an elliptic body (step_ellipse.cu).
+// The same for an elliptic body (step_ellipse.cu) and a rectangular one (step_rectangle.cu).
 cudaError_t launch_step_ellipse(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb);
+cudaError_t launch_step_rectangle(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb);
 cudaError_t launch_init_equilibrium(int precision, const StepParams &p, const double *rho_dev,
                                     const double *ux_dev, const double *uy_dev, cudaStream_t stream);
 // Convective outlet: previous values := the outlet column of p.fin (into p.conv_in).

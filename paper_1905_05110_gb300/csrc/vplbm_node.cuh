@@ -170,6 +170,18 @@ __device__ __forceinline__ bool chi_exact(int i, int j, double xg, double yg, do
     return d2 <= r2;
 }
 
+// Rectangle: |u| <= a and |v| <= b with (u, v) the node in the body frame,
+// FP64 without contraction.
+__device__ __forceinline__ bool chi_exact_rect(int i, int j, const BodyState *bs, const DevBody &b)
+{
+    const double dx = __dsub_rn((double)i, bs->q[0]);
+    const double dy = __dsub_rn((double)j, bs->q[1]);
+    const double c = bs->cth, s = bs->sth;
+    const double u = __dadd_rn(__dmul_rn(dx, c), __dmul_rn(dy, s));
+    const double v = __dsub_rn(__dmul_rn(dy, c), __dmul_rn(dx, s));
+    return fabs(u) <= b.ra && fabs(v) <= b.rb;
+}
+
 // Ellipse: b^2 u^2 + a^2 v^2 <= a^2 b^2 with (u, v) the node in the body
 // frame, FP64 without contraction, in a fixed order.
 __device__ __forceinline__ bool chi_exact_ellipse(int i, int j, const BodyState *bs, const DevBody &b)
@@ -425,8 +437,19 @@ __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState
             const float2 fr = __ldg(reinterpret_cast<const float2 *>(&bs->xf));
             const float dxf = (float)(i - xy.x) - fr.x;
             const float dyf = (float)(j - xy.y) - fr.y;
-            const bool ellipse = SHAPE == SHAPE_ANY ? p.body.shape == VPLBM_SHAPE_ELLIPSE : SHAPE == VPLBM_SHAPE_ELLIPSE;
-            if (ellipse) {
+            const int shape = SHAPE == SHAPE_ANY ? p.body.shape : SHAPE;
+            if (shape == VPLBM_SHAPE_RECTANGLE) {
+                // |u| <= a and |v| <= b in the body frame, in FP32, exact
+                // FP64 re-test where either is within the band of its edge
+                const float2 cs = __ldg(reinterpret_cast<const float2 *>(&bs->cthf));
+                const float uf = fabsf(dxf * cs.x + dyf * cs.y);
+                const float vf = fabsf(dyf * cs.x - dxf * cs.y);
+                const float band = p.body.bandr;
+                if (fabsf(uf - p.body.raf) <= band || fabsf(vf - p.body.rbf) <= band)
+                    chi = chi_exact_rect(i, j, bs, p.body);
+                else
+                    chi = uf <= p.body.raf && vf <= p.body.rbf;
+            } else if (shape == VPLBM_SHAPE_ELLIPSE) {
                 // b^2 u^2 + a^2 v^2 <= a^2 b^2 in the body frame, in FP32,
                 // exact FP64 re-test inside the band
                 const float2 cs = __ldg(reinterpret_cast<const float2 *>(&bs->cthf));
@@ -445,8 +468,10 @@ __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState
             dxl = dxf; dyl = dyf;
         } else {
             const double xg = __ldg(&bs->q[0]), yg = __ldg(&bs->q[1]);
-            const bool ellipse = SHAPE == SHAPE_ANY ? p.body.shape == VPLBM_SHAPE_ELLIPSE : SHAPE == VPLBM_SHAPE_ELLIPSE;
-            chi = ellipse ? chi_exact_ellipse(i, j, bs, p.body) : chi_exact(i, j, xg, yg, p.body.r2);
+            const int shape = SHAPE == SHAPE_ANY ? p.body.shape : SHAPE;
+            chi = shape == VPLBM_SHAPE_ELLIPSE   ? chi_exact_ellipse(i, j, bs, p.body)
+                  : shape == VPLBM_SHAPE_RECTANGLE ? chi_exact_rect(i, j, bs, p.body)
+                                                   : chi_exact(i, j, xg, yg, p.body.r2);
             dxl = (double)i - xg;
             dyl = (double)j - yg;
         }

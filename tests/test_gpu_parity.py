@@ -569,10 +569,10 @@ def test_convective_outlet_rejected_where_not_defined():
 
 # ---- elliptic body ---------------------------------------------------------
 
-def _ellipse_body(motion, nx, ny):
+def _ellipse_body(motion, nx, ny, shape="ellipse"):
     a, b = 0.2 * ny, 0.09 * ny
     m = 2.0 * np.pi * a * b
-    common = {"shape": "ellipse", "radius": a, "radius_b": b, "u_ref": 0.05, "d_ref": 2 * b}
+    common = {"shape": shape, "radius": a, "radius_b": b, "u_ref": 0.05, "d_ref": 2 * b}
     if motion == "fixed":
         return dict(common, x=0.41 * nx + 0.13, y=0.52 * ny + 0.37, theta=0.5, motion="fixed")
     if motion == "imposed":   # pitching about its centre
@@ -583,12 +583,13 @@ def _ellipse_body(motion, nx, ny):
                 stiff=(0.0, 1e-3, 0.0), q0=(0.0, 0.5 * ny, 0.0))
 
 
+@pytest.mark.parametrize("shape", ["ellipse", "rectangle"])
 @pytest.mark.parametrize("motion", ["fixed", "imposed", "free"])
 @pytest.mark.parametrize("precision", ["f64", "f32"])
-def test_ellipse_runs_match_oracle(motion, precision):
+def test_shaped_body_runs_match_oracle(shape, motion, precision):
     nx, ny = 97, 70
-    p = _box(nx, ny, ("velocity", "zerograd", "noslip", "noslip"), seed=6, body=_ellipse_body(motion, nx, ny),
-             tau=0.62)
+    p = _box(nx, ny, ("velocity", "zerograd", "noslip", "noslip"), seed=6,
+             body=_ellipse_body(motion, nx, ny, shape), tau=0.62)
     p["s"] = wl.paper_rates(0.62)
     p["bc"]["west"] = {"kind": "velocity", "u": (0.05, 0.0)}
     gpu, orc = make_pair(p, precision)
