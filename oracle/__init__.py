@@ -94,6 +94,11 @@ def lib():
             L = C.CDLL(LIB_PATH)
             L.orc_create.restype = C.c_void_p
             L.orc_create.argtypes = [C.POINTER(Lattice), C.POINTER(Body), C.c_longlong]
+            L.orc_create_bodies.restype = C.c_void_p
+            L.orc_create_bodies.argtypes = [C.POINTER(Lattice), C.POINTER(Body), C.c_int, C.c_longlong]
+            L.orc_get_history_body.restype = C.c_int
+            L.orc_get_history_body.argtypes = [C.c_void_p, C.c_int, C.c_longlong, C.c_longlong, C.POINTER(Record)]
+            L.orc_get_body_k.argtypes = [C.c_void_p, C.c_int, _D, _D]
             L.orc_free.argtypes = [C.c_void_p]
             L.orc_init_equilibrium.argtypes = [C.c_void_p, _D, _D, _D]
             L.orc_set_populations.argtypes = [C.c_void_p, _D]
@@ -196,6 +201,13 @@ def make_body(b: dict | None) -> Body:
     return body
 
 
+def problem_bodies(problem: dict) -> list:
+    """The bodies of a problem: its "bodies" list, or its single "body"."""
+    if problem.get("bodies"):
+        return list(problem["bodies"])
+    return [problem["body"]] if problem.get("body") else []
+
+
 class OracleSim:
     """One FP64 VP-LBM simulation on the CPU (plain loops, Algorithm 1)."""
 
@@ -205,8 +217,10 @@ class OracleSim:
         self.nx, self.ny = int(problem["nx"]), int(problem["ny"])
         self._keep: list = []
         self._lat = make_lattice(problem, self._keep)
-        self._body = make_body(problem.get("body"))
-        self._h = L.orc_create(C.byref(self._lat), C.byref(self._body), int(hist_cap))
+        bodies = problem_bodies(problem)
+        self.nbodies = len(bodies)
+        self._bodies = (Body * max(1, len(bodies)))(*[make_body(b) for b in bodies])
+        self._h = L.orc_create_bodies(C.byref(self._lat), self._bodies, len(bodies), int(hist_cap))
         if not self._h:
             raise ValueError("oracle: invalid lattice")
 
@@ -251,11 +265,11 @@ class OracleSim:
     def nstep(self) -> int:
         return int(lib().orc_get_step(self._h))
 
-    def history(self, first: int = 0, count: int | None = None) -> np.ndarray:
+    def history(self, first: int = 0, count: int | None = None, body: int = 0) -> np.ndarray:
         if count is None:
             count = self.nstep - first
         buf = (Record * max(count, 1))()
-        if lib().orc_get_history(self._h, first, count, buf) != 0:
+        if lib().orc_get_history_body(self._h, int(body), first, count, buf) != 0:
             raise IndexError("oracle history range not available")
         out = np.zeros((count, len(RECORD_FIELDS)))
         for k in range(count):
@@ -276,10 +290,10 @@ class OracleSim:
             raise ValueError("oracle adjoint: free body or history ring too short")
         return grad, (float(js[0]), float(js[1]))
 
-    def body_state(self):
+    def body_state(self, body: int = 0):
         q = np.zeros(3)
         v = np.zeros(3)
-        lib().orc_get_body(self._h, _dptr(q), _dptr(v))
+        lib().orc_get_body_k(self._h, int(body), _dptr(q), _dptr(v))
         return q, v
 
     def chi(self) -> np.ndarray:

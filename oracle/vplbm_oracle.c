@@ -175,16 +175,19 @@ typedef struct {
     double fpen_x, fpen_y, tpen, n_solid;
 } orc_record;
 
+#define ORC_MAXB 4   /* bodies per lattice */
+
 typedef struct {
     orc_lattice lat;
-    orc_body body;
+    int nb;                        /* number of bodies, 0 .. ORC_MAXB */
+    orc_body body[ORC_MAXB];
     double *prof_ux[4], *prof_uy[4];
     double *ft;            /* post-collision populations (the state) */
     double *fn;            /* scratch for the next state */
     long long step;
-    double q[3], v[3];     /* pose (x, y, theta) and velocity */
-    double q_center;       /* centre of the imposed sinusoid */
-    orc_record *hist;
+    double q[ORC_MAXB][3], v[ORC_MAXB][3];   /* pose (x, y, theta) and velocity of each body */
+    double q_center[ORC_MAXB];               /* centre of an imposed sinusoid */
+    orc_record *hist;      /* [max(nb, 1)][hist_cap] */
     long long hist_cap;
     double *conv_prev;     /* convective outlet: pulled f_a(nx-1, j) of the previous step, [a][j] */
     double *conv_next;
@@ -199,35 +202,46 @@ static double edge_u(const orc_sim *s, int side, int comp, int k)
     return s->lat.bc_u[side][comp];
 }
 
-/* chi of Eq. (2) for the body at the current pose (reading R1).  Disk:
+/* chi of Eq. (2) for body k at its current pose (reading R1).  Disk:
  * |x - x_G| <= R.  Ellipse of semi-axes a (along the body's x axis, at the
  * angle theta of the pose) and b: with u, v the node's coordinates in the
  * body frame, b^2 u^2 + a^2 v^2 <= a^2 b^2.  Rectangle of half-sides a, b
  * along the same axes: |u| <= a and |v| <= b. */
-static int chi_at(const orc_sim *s, int i, int j)
+static int chi_body(const orc_sim *s, int k, int i, int j)
 {
-    if (!s->body.present) return 0;
-    double dx = (double)i - s->q[0];
-    double dy = (double)j - s->q[1];
-    if (s->body.shape == ORC_ELLIPSE) {
-        double c = cos(s->q[2]), sn = sin(s->q[2]);
-        double a2 = s->body.radius * s->body.radius, b2 = s->body.radius_b * s->body.radius_b;
+    const orc_body *b = &s->body[k];
+    if (!b->present) return 0;
+    double dx = (double)i - s->q[k][0];
+    double dy = (double)j - s->q[k][1];
+    if (b->shape == ORC_ELLIPSE) {
+        double c = cos(s->q[k][2]), sn = sin(s->q[k][2]);
+        double a2 = b->radius * b->radius, b2 = b->radius_b * b->radius_b;
         double u = dx * c + dy * sn;
         double v = dy * c - dx * sn;
         return b2 * (u * u) + a2 * (v * v) <= a2 * b2;
     }
-    if (s->body.shape == ORC_RECT) {
-        double c = cos(s->q[2]), sn = sin(s->q[2]);
+    if (b->shape == ORC_RECT) {
+        double c = cos(s->q[k][2]), sn = sin(s->q[k][2]);
         double u = dx * c + dy * sn;
         double v = dy * c - dx * sn;
-        return fabs(u) <= s->body.radius && fabs(v) <= s->body.radius_b;
+        return fabs(u) <= b->radius && fabs(v) <= b->radius_b;
     }
     double d2 = dx * dx + dy * dy;
-    double r2 = s->body.radius * s->body.radius;
+    double r2 = b->radius * b->radius;
     return d2 <= r2;
 }
 
-int orc_chi(const orc_sim *s, int i, int j) { return chi_at(s, i, j); }
+/* The body a node belongs to (-1: fluid).  Bodies do not overlap (the
+ * caller's responsibility); where they would, the first one listed wins. */
+static int owner_at(const orc_sim *s, int i, int j)
+{
+    for (int k = 0; k < s->nb; ++k)
+        if (chi_body(s, k, i, j)) return k;
+    return -1;
+}
+
+/* 0: fluid, else 1 + the index of the body the node belongs to. */
+int orc_chi(const orc_sim *s, int i, int j) { return owner_at(s, i, j) + 1; }
 
 /* Equilibrium of Eq. (11). */
 static void equilibrium(double rho, double ux, double uy, double feq[Q])
@@ -389,6 +403,7 @@ typedef struct {
     double f[Q];
     double rho, jx, jy, ux, uy, ax, ay, usx, usy, dx, dy;
     int chi;
+    int owner;   /* body of a solid node (-1: fluid) */
 } node_state;
 
 static void node_macro(const orc_sim *s, int i, int j, node_state *ns)
@@ -400,12 +415,14 @@ static void node_macro(const orc_sim *s, int i, int j, node_state *ns)
         ns->jx += C[a][0] * ns->f[a];
         ns->jy += C[a][1] * ns->f[a];
     }
-    ns->chi = chi_at(s, i, j);
-    ns->dx = (double)i - s->q[0];
-    ns->dy = (double)j - s->q[1];
-    /* rigid-body velocity at the node */
-    ns->usx = s->v[0] - s->v[2] * ns->dy;
-    ns->usy = s->v[1] + s->v[2] * ns->dx;
+    ns->owner = owner_at(s, i, j);
+    ns->chi = ns->owner >= 0;
+    const int k = ns->owner >= 0 ? ns->owner : 0;
+    ns->dx = (double)i - s->q[k][0];
+    ns->dy = (double)j - s->q[k][1];
+    /* rigid-body velocity at the node (of the body it belongs to) */
+    ns->usx = s->v[k][0] - s->v[k][2] * ns->dy;
+    ns->usy = s->v[k][1] + s->v[k][2] * ns->dx;
     penalized_velocity(ns->rho, ns->jx, ns->jy, ns->chi, ns->usx, ns->usy,
                        s->lat.eta, s->lat.gx, s->lat.gy,
                        &ns->ux, &ns->uy, &ns->ax, &ns->ay);
@@ -462,7 +479,7 @@ static void body_advance(const orc_body *b, long long step, double q_center,
 
 void orc_free(orc_sim *s);
 
-orc_sim *orc_create(const orc_lattice *lat, const orc_body *body, long long hist_cap)
+orc_sim *orc_create_bodies(const orc_lattice *lat, const orc_body *bodies, int nb, long long hist_cap)
 {
     setup_constants();
     if (lat->nx < 2 || lat->ny < 2) return NULL;
@@ -470,10 +487,12 @@ orc_sim *orc_create(const orc_lattice *lat, const orc_body *body, long long hist
     for (int side = 0; side < 4; ++side)
         if (lat->bc_kind[side] == ORC_CONVECTIVE && (side != ORC_EAST || !(lat->bc_u[side][0] >= 0.0)))
             return NULL;   /* east outlet only, convective velocity >= 0 */
+    if (nb < 0 || nb > ORC_MAXB || (nb > 0 && !bodies)) return NULL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     if (!s) return NULL;
     s->lat = *lat;
-    if (body) s->body = *body; else s->body.present = 0;
+    s->nb = nb;
+    for (int k = 0; k < nb; ++k) s->body[k] = bodies[k];
     for (int side = 0; side < 4; ++side) {
         int len = side < 2 ? lat->ny : lat->nx;
         s->lat.bc_ux[side] = NULL; s->lat.bc_uy[side] = NULL;
@@ -492,14 +511,22 @@ orc_sim *orc_create(const orc_lattice *lat, const orc_body *body, long long hist
     s->conv_prev = (double *)calloc((size_t)Q * lat->ny, sizeof(double));
     s->conv_next = (double *)calloc((size_t)Q * lat->ny, sizeof(double));
     s->hist_cap = hist_cap > 0 ? hist_cap : 1;
-    s->hist = (orc_record *)calloc((size_t)s->hist_cap, sizeof(orc_record));
+    s->hist = (orc_record *)calloc((size_t)s->hist_cap * (nb > 0 ? nb : 1), sizeof(orc_record));
     if (!s->ft || !s->fn || !s->hist) { orc_free(s); return NULL; }
-    s->q[0] = s->body.x; s->q[1] = s->body.y; s->q[2] = s->body.theta;
-    s->v[0] = s->body.vx; s->v[1] = s->body.vy; s->v[2] = s->body.omega;
-    if (s->body.present && s->body.motion == ORC_IMPOSED)
-        s->q_center = s->q[s->body.axis] - s->body.amp * sin(s->body.phase);
+    for (int k = 0; k < nb; ++k) {
+        const orc_body *b = &s->body[k];
+        s->q[k][0] = b->x; s->q[k][1] = b->y; s->q[k][2] = b->theta;
+        s->v[k][0] = b->vx; s->v[k][1] = b->vy; s->v[k][2] = b->omega;
+        if (b->present && b->motion == ORC_IMPOSED)
+            s->q_center[k] = s->q[k][b->axis] - b->amp * sin(b->phase);
+    }
     s->step = 0;
     return s;
+}
+
+orc_sim *orc_create(const orc_lattice *lat, const orc_body *body, long long hist_cap)
+{
+    return orc_create_bodies(lat, body, body && body->present ? 1 : 0, hist_cap);
 }
 
 void orc_free(orc_sim *s)
@@ -566,8 +593,8 @@ static void one_step(orc_sim *s)
     const int nx = s->lat.nx, ny = s->lat.ny;
     node_state ns;
     double ft[Q];
-    double fpen[3] = {0, 0, 0}, fh[3] = {0, 0, 0};
-    double nsolid = 0.0;
+    double fpen[ORC_MAXB][3] = {{0}}, fh[ORC_MAXB][3] = {{0}};
+    double nsolid[ORC_MAXB] = {0};
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             node_macro(s, i, j, &ns);
@@ -581,11 +608,12 @@ static void one_step(orc_sim *s)
                 collide(ns.f, s->lat.s, ns.rho, ns.ux, ns.uy, Gx, Gy, ft);
             for (int a = 0; a < Q; ++a) s->fn[((size_t)a * ny + j) * nx + i] = ft[a];
             if (ns.chi) {
+                const int k = ns.owner;
                 /* reaction of the penalization force on the body */
                 double px = -ns.rho * ns.ax, py = -ns.rho * ns.ay;
-                fpen[0] += px;
-                fpen[1] += py;
-                fpen[2] += ns.dx * py - ns.dy * px;
+                fpen[k][0] += px;
+                fpen[k][1] += py;
+                fpen[k][2] += ns.dx * py - ns.dy * px;
                 /* momentum brought into the node by the streaming (Eq. 25) */
                 double ox = 0.0, oy = 0.0;
                 for (int a = 0; a < Q; ++a) {
@@ -594,27 +622,29 @@ static void one_step(orc_sim *s)
                     oy += C[a][1] * own;
                 }
                 double ex = ns.jx - ox, ey = ns.jy - oy;
-                fh[0] += ex;
-                fh[1] += ey;
-                fh[2] += ns.dx * ey - ns.dy * ex;   /* Eq. (27) */
-                nsolid += 1.0;
+                fh[k][0] += ex;
+                fh[k][1] += ey;
+                fh[k][2] += ns.dx * ey - ns.dy * ex;   /* Eq. (27) */
+                nsolid[k] += 1.0;
             }
         }
     double *t = s->ft; s->ft = s->fn; s->fn = t;
     t = s->conv_prev; s->conv_prev = s->conv_next; s->conv_next = t;
 
-    orc_record *r = &s->hist[s->step % s->hist_cap];
-    r->t = (double)s->step;
-    r->fx = fh[0]; r->fy = fh[1]; r->torque = fh[2];
-    double qref = 0.5 * s->lat.rho0 * s->body.d_ref * s->body.u_ref * s->body.u_ref;
-    r->cd = qref > 0 ? fh[0] / qref : 0.0;
-    r->cl = qref > 0 ? fh[1] / qref : 0.0;
-    r->x = s->q[0]; r->y = s->q[1]; r->theta = s->q[2];
-    r->vx = s->v[0]; r->vy = s->v[1]; r->omega = s->v[2];
-    r->fpen_x = fpen[0]; r->fpen_y = fpen[1]; r->tpen = fpen[2];
-    r->n_solid = nsolid;
-
-    if (s->body.present) body_advance(&s->body, s->step, s->q_center, fh, s->q, s->v);
+    for (int k = 0; k < (s->nb > 0 ? s->nb : 1); ++k) {
+        const orc_body *b = &s->body[k];
+        orc_record *r = &s->hist[(size_t)k * s->hist_cap + s->step % s->hist_cap];
+        r->t = (double)s->step;
+        r->fx = fh[k][0]; r->fy = fh[k][1]; r->torque = fh[k][2];
+        double qref = 0.5 * s->lat.rho0 * b->d_ref * b->u_ref * b->u_ref;
+        r->cd = qref > 0 ? fh[k][0] / qref : 0.0;
+        r->cl = qref > 0 ? fh[k][1] / qref : 0.0;
+        r->x = s->q[k][0]; r->y = s->q[k][1]; r->theta = s->q[k][2];
+        r->vx = s->v[k][0]; r->vy = s->v[k][1]; r->omega = s->v[k][2];
+        r->fpen_x = fpen[k][0]; r->fpen_y = fpen[k][1]; r->tpen = fpen[k][2];
+        r->n_solid = nsolid[k];
+        if (b->present) body_advance(b, s->step, s->q_center[k], fh[k], s->q[k], s->v[k]);
+    }
     s->step += 1;
 }
 
@@ -625,19 +655,27 @@ void orc_step(orc_sim *s, long long n)
 
 long long orc_get_step(const orc_sim *s) { return s->step; }
 
-/* Copies records first .. first+count-1 (must still be in the ring). */
-int orc_get_history(const orc_sim *s, long long first, long long count, orc_record *dst)
+/* Copies records first .. first+count-1 of body k (must still be in the ring). */
+int orc_get_history_body(const orc_sim *s, int k, long long first, long long count, orc_record *dst)
 {
+    if (k < 0 || k >= (s->nb > 0 ? s->nb : 1)) return -1;
     if (first < 0 || count < 0 || first + count > s->step) return -1;
     if (first < s->step - s->hist_cap) return -1;
-    for (long long k = 0; k < count; ++k) dst[k] = s->hist[(first + k) % s->hist_cap];
+    for (long long n = 0; n < count; ++n) dst[n] = s->hist[(size_t)k * s->hist_cap + (first + n) % s->hist_cap];
     return 0;
 }
 
-void orc_get_body(const orc_sim *s, double q[3], double v[3])
+int orc_get_history(const orc_sim *s, long long first, long long count, orc_record *dst)
 {
-    for (int d = 0; d < 3; ++d) { q[d] = s->q[d]; v[d] = s->v[d]; }
+    return orc_get_history_body(s, 0, first, count, dst);
 }
+
+void orc_get_body_k(const orc_sim *s, int k, double q[3], double v[3])
+{
+    for (int d = 0; d < 3; ++d) { q[d] = s->q[k][d]; v[d] = s->v[k][d]; }
+}
+
+void orc_get_body(const orc_sim *s, double q[3], double v[3]) { orc_get_body_k(s, 0, q, v); }
 
 /* ---- single-node entry points used by the pinning tests ------------- */
 
@@ -839,9 +877,10 @@ int orc_adjoint(orc_sim *s, const orc_adjoint_desc *d, double *grad, double out_
 {
     const int nx = s->lat.nx, ny = s->lat.ny;
     const long long N = d->nsteps;
-    if (s->body.present && s->body.motion == ORC_FREE) return -1;
+    if (s->nb > 1) return -1;
+    if (s->body[0].present && s->body[0].motion == ORC_FREE) return -1;
     if (s->lat.collision != ORC_MRT) return -1;
-    if (s->body.present && s->body.shape != ORC_DISK) return -1;
+    if (s->body[0].present && s->body[0].shape != ORC_DISK) return -1;
     for (int side = 0; side < 4; ++side)
         if (s->lat.bc_kind[side] == ORC_CONVECTIVE) return -1;
     if (N < 1 || d->w0 < 0 || d->w0 >= N || s->hist_cap < s->step + N) return -1;
@@ -857,7 +896,7 @@ int orc_adjoint(orc_sim *s, const orc_adjoint_desc *d, double *grad, double out_
         one_step(s);
     }
     /* objectives from the recorded forces */
-    const double qref = 0.5 * s->lat.rho0 * s->body.d_ref * s->body.u_ref * s->body.u_ref;
+    const double qref = 0.5 * s->lat.rho0 * s->body[0].d_ref * s->body[0].u_ref * s->body[0].u_ref;
     const double nh = (double)(N - d->w0);
     double sum_cd = 0, sum_cl2 = 0;
     for (long long n = d->w0; n < N; ++n) {
@@ -872,13 +911,13 @@ int orc_adjoint(orc_sim *s, const orc_adjoint_desc *d, double *grad, double out_
     double d_eta = 0, d_s[Q] = {0};
     double *saved_ft = s->ft;
     double saved_q[3], saved_v[3];
-    for (int dd = 0; dd < 3; ++dd) { saved_q[dd] = s->q[dd]; saved_v[dd] = s->v[dd]; }
+    for (int dd = 0; dd < 3; ++dd) { saved_q[dd] = s->q[0][dd]; saved_v[dd] = s->v[0][dd]; }
     node_state ns;
     for (long long n = N - 1; n >= 0; --n) {
         const orc_record *r = &s->hist[(step0 + n) % s->hist_cap];
         s->ft = states + nf * (size_t)n;
-        s->q[0] = r->x; s->q[1] = r->y; s->q[2] = r->theta;
-        s->v[0] = r->vx; s->v[1] = r->vy; s->v[2] = r->omega;
+        s->q[0][0] = r->x; s->q[0][1] = r->y; s->q[0][2] = r->theta;
+        s->v[0][0] = r->vx; s->v[0][1] = r->vy; s->v[0][2] = r->omega;
         double wx = 0, wy = 0;   /* dJ/dF_h(n) */
         if (n >= d->w0) {
             wx = d->w_cd / (qref * nh);
@@ -908,7 +947,7 @@ int orc_adjoint(orc_sim *s, const orc_adjoint_desc *d, double *grad, double out_
                     if (wall == ORC_WEST && s->prof_ux[ORC_WEST])
                         grad[j] += g * 6.0 * W[a] * s->lat.rho0 * C[a][0];
                 }
-                if (chi_at(s, i, j))
+                if (owner_at(s, i, j) >= 0)
                     for (int a = 0; a < Q; ++a) nlam[((size_t)a * ny + j) * nx + i] -= wx * C[a][0] + wy * C[a][1];
             }
         double *t = lam; lam = nlam; nlam = t;
@@ -918,7 +957,7 @@ int orc_adjoint(orc_sim *s, const orc_adjoint_desc *d, double *grad, double out_
     grad[ny + 2] = d_s[1];
     /* leave the simulation after its forward run */
     s->ft = saved_ft;
-    for (int dd = 0; dd < 3; ++dd) { s->q[dd] = saved_q[dd]; s->v[dd] = saved_v[dd]; }
+    for (int dd = 0; dd < 3; ++dd) { s->q[0][dd] = saved_q[dd]; s->v[0][dd] = saved_v[dd]; }
     free(states); free(lam); free(nlam); free(mu);
     return 0;
 }
