@@ -37,7 +37,7 @@ METRIC = "D2Q9 VP-MRT MLUPS & % HBM roofline; FP32/batched/adjoint vs FP64 plain
 UNIT = "MLUPS"
 BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36}   # 9 loads + 9 stores of one population
 PREC_ID = {"f64": 0, "f32": 1, "f16": 2}
-LEGS = ("f64", "f16", "batched", "adjoint", "sedimenting", "paper")   # comparison legs after the headline
+LEGS = ("f64", "f16", "batched", "adjoint", "sedimenting", "paper", "several")   # comparison legs after the headline
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 CSRC = os.path.join(ROOT, "paper_1905_05110_gb300", "csrc")
@@ -59,6 +59,8 @@ def workload(name: str) -> dict:
         return wl.paper_oscillating_cylinder()
     if name == "channel_256x128":
         return wl.channel_fixed_disk()
+    if name == "several_bodies_2048x1024":
+        return wl.several_bodies()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -331,6 +333,8 @@ def run_ours(args, rank, world, local_rank):
         if "paper" in legs:
             compare["paper_oscillating_cylinder"] = run_other_workload("paper_cylinder_1230x410", 40000, torch,
                                                                        stream)
+        if "several" in legs:
+            compare["several_bodies"] = run_other_workload("several_bodies_2048x1024", 8000, torch, stream)
 
     base = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -362,13 +366,23 @@ def run_other_workload(name, steps, torch, stream):
     launch = sim.autotune(8)
     t = time_device(sim, steps, stream, torch)
     sim.sync()
-    h = sim.history(0, steps)
     half = steps // 2
-    out = {"workload": p["name"], "mlups": nodes * steps / t / 1e6, "steps": steps, "launch": list(launch),
-           "mean_cd_2nd_half": float(h[half:, 4].mean()), "rms_cl_2nd_half": float(np.sqrt((h[half:, 5] ** 2).mean()))}
-    if p["body"]["motion"] == "free":
-        out["final_pose"] = [float(v) for v in h[-1, 6:9]]
-        out["final_velocity"] = [float(v) for v in h[-1, 9:12]]
+    out = {"workload": p["name"], "mlups": nodes * steps / t / 1e6, "steps": steps, "launch": list(launch)}
+    bodies = p.get("bodies") or [p["body"]]
+    per_body = []
+    for k, b in enumerate(bodies):
+        h = sim.history(0, steps, body=k)
+        d = {"motion": b["motion"], "mean_cd_2nd_half": float(h[half:, 4].mean()),
+             "rms_cl_2nd_half": float(np.sqrt((h[half:, 5] ** 2).mean()))}
+        if b["motion"] == "free":
+            d["final_pose"] = [float(v) for v in h[-1, 6:9]]
+            d["final_velocity"] = [float(v) for v in h[-1, 9:12]]
+        per_body.append(d)
+    if len(bodies) == 1:
+        out.update(per_body[0])
+        del out["motion"]
+    else:
+        out["bodies"] = per_body
     sim.close()
     return out
 

@@ -2,9 +2,9 @@
  * vplbm.h - C ABI of the GB300 volume-penalization lattice Boltzmann library.
  *
  * The library advances a D2Q9 multiple-relaxation-time (or BGK) lattice
- * Boltzmann fluid in which a rigid body (disk or ellipse) is represented by
- * a characteristic function chi and enters the fluid as a penalization
- * force (Liberge & Beghein,
+ * Boltzmann fluid in which a rigid body (disk, ellipse or rectangle; up to
+ * VPLBM_MAX_BODIES of them) is represented by a characteristic function chi
+ * and enters the fluid as a penalization force (Liberge & Beghein,
  * "Fluid Structure Interaction modelling using Lattice Boltzmann and Volume
  * Penalization method", Sec. 2).  One time step is Algorithm 1 of Sec. 2.3:
  * collide and stream (Eqs. 17-18), macroscopic moments with the penalized
@@ -41,6 +41,9 @@
 #ifdef __cplusplus
 extern "C" {
 #endif
+
+/* Most bodies one lattice can hold (vplbm_create_bodies). */
+#define VPLBM_MAX_BODIES 4
 
 typedef enum {
     VPLBM_OK = 0,
@@ -135,7 +138,7 @@ typedef enum {
  * the last bit).  The adjoint takes the disk only. */
 typedef enum { VPLBM_SHAPE_DISK = 0, VPLBM_SHAPE_ELLIPSE = 1, VPLBM_SHAPE_RECTANGLE = 2 } vplbm_shape;
 
-/* Rigid body (disk or ellipse, see vplbm_shape).  The rigid velocity at a node is
+/* Rigid body (disk, ellipse or rectangle, see vplbm_shape).  The rigid velocity at a node is
  * u_s = (vx - omega (y - y_G), vy + omega (x - x_G)).
  * Imposed motion: q_c is chosen so that q_axis(0) equals the initial pose.
  * Free motion: m q'' + damp q' + stiff (q - q0) = F_h + f_ext per DOF
@@ -204,6 +207,17 @@ vplbm_status vplbm_create_with_buffers(const vplbm_lattice_desc *lat, const vplb
                                        long long history_capacity, void *cuda_stream,
                                        const vplbm_buffers *buffers, vplbm_ctx **out);
 
+/* Several bodies in one lattice (1 <= nbodies <= VPLBM_MAX_BODIES; bodies
+ * is an array of nbodies descriptors).  Each body has its own chi, force
+ * and torque sums (Eqs. 25-27 over its own solid nodes), history ring and
+ * motion.  A node belongs to the first body in the array whose chi holds
+ * there; bodies are meant not to overlap (Eq. 2 gives each node at most one
+ * solid velocity).  The library allocates its device memory.  The scalar
+ * kernels run it (VPLBM_KERNEL_TMA, the adjoint and the allocation-free
+ * entry point take one body).  nbodies == 1 is the same as vplbm_create. */
+vplbm_status vplbm_create_bodies(const vplbm_lattice_desc *lat, const vplbm_body_desc *bodies, int nbodies,
+                                 long long history_capacity, void *cuda_stream, vplbm_ctx **out);
+
 void vplbm_destroy(vplbm_ctx *ctx);
 
 /* State := equilibrium (Eq. 11) of the host fields rho, ux, uy ([ny][nx]);
@@ -238,6 +252,14 @@ vplbm_status vplbm_get_history(vplbm_ctx *ctx, long long first, long long count,
 
 /* Pose (x, y, theta), velocity (vx, vy, omega) and step counter. */
 vplbm_status vplbm_get_body(vplbm_ctx *ctx, double q[3], double v[3], long long *step);
+
+/* Number of bodies of the context (0 when it was created without one). */
+vplbm_status vplbm_get_num_bodies(vplbm_ctx *ctx, int *nbodies);
+
+/* vplbm_get_history and vplbm_get_body for body k (0 <= k < the number
+ * of bodies; k = 0 also for a context without a body). */
+vplbm_status vplbm_get_history_body(vplbm_ctx *ctx, int k, long long first, long long count, vplbm_record *dst);
+vplbm_status vplbm_get_body_k(vplbm_ctx *ctx, int k, double q[3], double v[3], long long *step);
 
 /* Step kernels.  Both compute the same method; they differ in data movement:
  *  VPLBM_KERNEL_SCALAR     one node per thread, its nine pulls loaded straight

@@ -24,7 +24,8 @@ __all__ = [
     "vplbm_create", "vplbm_create_with_buffers", "vplbm_buffer_sizes_for", "vplbm_destroy",
     "vplbm_init_equilibrium", "vplbm_set_populations", "vplbm_step", "vplbm_sync",
     "vplbm_get_populations", "vplbm_get_fields", "vplbm_get_fields_dev", "vplbm_get_history",
-    "vplbm_get_body", "vplbm_set_launch", "vplbm_get_launch", "vplbm_autotune",
+    "vplbm_get_body", "vplbm_create_bodies", "vplbm_get_num_bodies", "vplbm_get_history_body",
+    "vplbm_get_body_k", "MAX_BODIES", "vplbm_set_launch", "vplbm_get_launch", "vplbm_autotune",
     "vplbm_get_launch_count", "vplbm_save", "vplbm_load", "vplbm_last_error", "vplbm_version",
     "vplbm_step_noalloc", "BodyState", "vplbm_inject_wait_timeout", "Batch",
     "vplbm_batch_create", "vplbm_batch_destroy", "vplbm_batch_member", "vplbm_batch_step",
@@ -122,6 +123,11 @@ _SIGS = {
     "vplbm_get_fields_dev": (C.c_int, [_CTX, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vplbm_get_history": (C.c_int, [_CTX, C.c_longlong, C.c_longlong, C.POINTER(Record)]),
     "vplbm_get_body": (C.c_int, [_CTX, _D, _D, C.POINTER(C.c_longlong)]),
+    "vplbm_create_bodies": (C.c_int, [C.POINTER(LatticeDesc), C.POINTER(BodyDesc), C.c_int, C.c_longlong,
+                                      C.c_void_p, C.POINTER(_CTX)]),
+    "vplbm_get_num_bodies": (C.c_int, [_CTX, C.POINTER(C.c_int)]),
+    "vplbm_get_history_body": (C.c_int, [_CTX, C.c_int, C.c_longlong, C.c_longlong, C.POINTER(Record)]),
+    "vplbm_get_body_k": (C.c_int, [_CTX, C.c_int, _D, _D, C.POINTER(C.c_longlong)]),
     "vplbm_set_launch": (C.c_int, [_CTX, C.c_int, C.c_int, C.c_int]),
     "vplbm_get_launch": (C.c_int, [_CTX, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "vplbm_autotune": (C.c_int, [_CTX, C.c_int]),
@@ -285,6 +291,15 @@ def vplbm_create_with_buffers(lat: LatticeDesc, body: BodyDesc | None, history_c
     return ctx
 
 
+def vplbm_create_bodies(lat: LatticeDesc, bodies: list, history_capacity: int, stream: int = 0):
+    """Context with several bodies (a list of BodyDesc, 1 .. MAX_BODIES)."""
+    arr = (BodyDesc * max(len(bodies), 1))(*bodies)
+    ctx = _CTX()
+    _check(load_library().vplbm_create_bodies(C.byref(lat), arr, len(bodies), int(history_capacity),
+                                              C.c_void_p(stream), C.byref(ctx)))
+    return ctx
+
+
 def vplbm_destroy(ctx):
     load_library().vplbm_destroy(ctx)
 
@@ -330,6 +345,29 @@ def vplbm_get_body(ctx):
     step = C.c_longlong()
     _check(load_library().vplbm_get_body(ctx, _dptr(q), _dptr(v), C.byref(step)))
     return q, v, int(step.value)
+
+
+def vplbm_get_num_bodies(ctx) -> int:
+    n = C.c_int()
+    _check(load_library().vplbm_get_num_bodies(ctx, C.byref(n)))
+    return int(n.value)
+
+
+def vplbm_get_history_body(ctx, k: int, first: int, count: int):
+    buf = (Record * max(int(count), 1))()
+    _check(load_library().vplbm_get_history_body(ctx, int(k), int(first), int(count), buf))
+    return buf
+
+
+def vplbm_get_body_k(ctx, k: int):
+    q = np.zeros(3)
+    v = np.zeros(3)
+    step = C.c_longlong()
+    _check(load_library().vplbm_get_body_k(ctx, int(k), _dptr(q), _dptr(v), C.byref(step)))
+    return q, v, int(step.value)
+
+
+MAX_BODIES = 4   # VPLBM_MAX_BODIES
 
 
 COLLISIONS = {"mrt": 0, "bgk": 1}
@@ -451,7 +489,9 @@ class Simulation:
     """One VP-LBM simulation on the current CUDA device.
 
     Device buffers are torch tensors handed to ``vplbm_create_with_buffers``;
-    work runs on ``stream`` (default: torch's current stream).
+    work runs on ``stream`` (default: torch's current stream).  A problem
+    with a "bodies" list of two or more bodies is created with
+    ``vplbm_create_bodies`` (the library allocates its memory).
     """
 
     def __init__(self, problem: dict, precision: str = "f32", history_capacity: int = 1 << 16,
@@ -466,8 +506,17 @@ class Simulation:
         self.nx, self.ny = int(problem["nx"]), int(problem["ny"])
         self._keep: list = []
         self._lat = lattice_desc(problem, precision, self._keep)
-        self._body = body_desc(problem.get("body"))
+        bodies = list(problem["bodies"]) if problem.get("bodies") else (
+            [problem["body"]] if problem.get("body") else [])
+        self.nbodies = len(bodies)
         self.history_capacity = int(history_capacity)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if len(bodies) > 1:
+            self._bodies = [body_desc(b) for b in bodies]
+            self.ctx = vplbm_create_bodies(self._lat, self._bodies, self.history_capacity,
+                                           self.stream.cuda_stream)
+            return
+        self._body = body_desc(bodies[0] if bodies else None)
         sizes = vplbm_buffer_sizes_for(self._lat, self._body, self.history_capacity)
         self._tensors = {}
 
@@ -486,7 +535,6 @@ class Simulation:
         bufs.history_dev = alloc("hist", sizes.history)
         bufs.profiles_dev = alloc("prof", sizes.profiles)
         bufs.control_dev = alloc("ctrl", sizes.control)
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.ctx = vplbm_create_with_buffers(self._lat, self._body, self.history_capacity,
                                              self.stream.cuda_stream, bufs)
 
@@ -534,15 +582,16 @@ class Simulation:
         vplbm_get_fields(self.ctx, rho, ux, uy)
         return rho, ux, uy
 
-    def history(self, first: int = 0, count: int | None = None) -> np.ndarray:
+    def history(self, first: int = 0, count: int | None = None, body: int = 0) -> np.ndarray:
+        """Records [first, first + count) of body `body`, one row per step."""
         if count is None:
             count = self.nstep - first
-        buf = vplbm_get_history(self.ctx, first, count)
+        buf = vplbm_get_history_body(self.ctx, body, first, count)
         arr = np.frombuffer(buf, dtype=np.float64, count=count * len(RECORD_FIELDS))
         return arr.reshape(count, len(RECORD_FIELDS)).copy()
 
-    def body_state(self):
-        q, v, _ = vplbm_get_body(self.ctx)
+    def body_state(self, body: int = 0):
+        q, v, _ = vplbm_get_body_k(self.ctx, body)
         return q, v
 
     @property

@@ -345,6 +345,7 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
         return aerr(VPLBM_EUNSUPPORTED, "the adjoint needs a body on a prescribed path (fixed or imposed)");
     if (c->collision != VPLBM_COLLISION_MRT) return aerr(VPLBM_EUNSUPPORTED, "the adjoint differentiates the MRT operator only");
     if (c->has_body && c->body_desc.shape != VPLBM_SHAPE_DISK) return aerr(VPLBM_EUNSUPPORTED, "the adjoint takes a disk");
+    if (c->nbodies > 1) return aerr(VPLBM_EUNSUPPORTED, "the adjoint takes one body");
     for (int e = VPLBM_SOUTH; e <= VPLBM_NORTH; ++e)
         if (c->base.bc[e] == VPLBM_BC_SYMMETRY) return aerr(VPLBM_EUNSUPPORTED, "the adjoint has no symmetry-wall rule");
     if (c->base.bc[VPLBM_EAST] == VPLBM_BC_CONVECTIVE) return aerr(VPLBM_EUNSUPPORTED, "the adjoint has no convective-outlet rule");

@@ -148,24 +148,37 @@ vplbm_status check_body(const vplbm_body_desc *b)
 
 void tile_of(int kernel, int bx, int by, int *w, int *h);
 
-void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long long cap, vplbm_buffer_sizes *s,
-               long long *ps_out, long long *parts_out)
+// Bodies of a context: nb descriptors (nb = 0: no body); per-body buffers
+// have max(nb, 1) slots.
+inline int body_slots(int nb) { return nb > 1 ? nb : 1; }
+
+void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *bodies, int nb, long long cap,
+               vplbm_buffer_sizes *s, long long *ps_out, long long *parts_out)
 {
     const long long n = (long long)lat->nx * lat->ny;
     const long long ps = (long long)round_up((size_t)n, 128);
-    long long parts = max_reduction_blocks(lat->nx, lat->ny, bounding_radius(body), body != nullptr,
-                                           TMA_TILE_W, TMA_TILE_H);
-    for (int k = 0; k < N_SHAPES; ++k)
-        for (int kern = KERNEL_SCALAR; kern <= KERNEL_TMA; ++kern) {   // every kernel's tiling
-            int w, h;
-            tile_of(kern, SHAPES[k][0], SHAPES[k][1], &w, &h);
-            const long long m = max_reduction_blocks(lat->nx, lat->ny, bounding_radius(body), body != nullptr, w, h);
-            if (m > parts) parts = m;
-        }
+    const int slots = body_slots(nb);
+    long long parts = 1;   // per body: the largest over the kernels' tilings
+    for (int b = 0; b < slots; ++b) {
+        const vplbm_body_desc *body = nb > 0 ? &bodies[b] : nullptr;
+        const long long m0 = max_reduction_blocks(lat->nx, lat->ny, bounding_radius(body), body != nullptr,
+                                                  TMA_TILE_W, TMA_TILE_H);
+        if (m0 > parts) parts = m0;
+        for (int k = 0; k < N_SHAPES; ++k)
+            for (int kern = KERNEL_SCALAR; kern <= KERNEL_TMA; ++kern) {   // every kernel's tiling
+                int w, h;
+                tile_of(kern, SHAPES[k][0], SHAPES[k][1], &w, &h);
+                const long long m = max_reduction_blocks(lat->nx, lat->ny, bounding_radius(body), body != nullptr, w, h);
+                if (m > parts) parts = m;
+            }
+    }
     s->populations = round_up((size_t)(9 * ps) * elem_size(lat->precision), ALIGN);
-    s->body_state = round_up(2 * sizeof(BodyState), ALIGN);
-    s->partials = round_up((size_t)parts * NPART * sizeof(double), ALIGN);
-    s->history = round_up((size_t)cap * sizeof(vplbm_record), ALIGN);
+    // the body states [parity][slot], then (several bodies) the per-body
+    // parameter views [parity][body]
+    s->body_state = round_up(2 * (size_t)slots * sizeof(BodyState) + (nb > 1 ? 2 * (size_t)nb * sizeof(StepParams) : 0),
+                             ALIGN);
+    s->partials = round_up((size_t)slots * parts * NPART * sizeof(double), ALIGN);
+    s->history = round_up((size_t)slots * cap * sizeof(vplbm_record), ALIGN);
     // FP64 profiles, then their FP32 copies: [side][comp][maxlen] each; then
     // the convective outlet state: [parity][3][ny] 8-byte slots
     s->profiles = round_up((size_t)8 * (lat->nx > lat->ny ? lat->nx : lat->ny) * (sizeof(double) + sizeof(float)), ALIGN) +
@@ -175,17 +188,18 @@ void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long 
     if (parts_out) *parts_out = parts;
 }
 
-BodyState initial_state(const vplbm_ctx *c)
+BodyState initial_state(const vplbm_ctx *c, int k)
 {
     BodyState s{};
-    if (c->has_body) {
-        const vplbm_body_desc &b = c->body_desc;
+    const bool present = k < c->nbodies;
+    if (present) {
+        const vplbm_body_desc &b = c->bodies[k];
         s.q[0] = b.x; s.q[1] = b.y; s.q[2] = b.theta;
         s.v[0] = b.vx; s.v[1] = b.vy; s.v[2] = b.omega;
     }
     s.step = 0;
-    derive_pose(s, c->has_body ? 1 : 0, c->has_body ? bounding_radius(&c->body_desc) : 0.0, c->nx, c->ny,
-                c->has_body ? c->body_desc.shape : VPLBM_SHAPE_DISK);
+    derive_pose(s, present ? 1 : 0, present ? bounding_radius(&c->bodies[k]) : 0.0, c->nx, c->ny,
+                present ? c->bodies[k].shape : VPLBM_SHAPE_DISK);
     return s;
 }
 
@@ -195,8 +209,10 @@ StepParams params_for(const vplbm_ctx *c, long long step)
     const int par = (int)(step & 1);
     p.fin = c->f[par];
     p.fout = c->f[par ^ 1];
-    p.bs_in = c->bs + par;
-    p.bs_out = c->bs + (par ^ 1);
+    const int slots = body_slots(c->nbodies);
+    p.bs_in = c->bs + par * slots;
+    p.bs_out = c->bs + (par ^ 1) * slots;
+    p.views = c->views ? c->views + (size_t)par * c->nbodies : nullptr;
     set_planes(p, (int)elem_size(c->precision));
     double *ob = static_cast<double *>(c->outlet);
     p.conv_in = ob + (size_t)par * 3 * c->ny;
@@ -232,6 +248,7 @@ void setup_tma(vplbm_ctx *c)
 {
     c->tma_ok = false;
     if (c->precision != VPLBM_F32_DEV && c->precision != VPLBM_F16_DEV) return;
+    if (c->nbodies > 1) return;   // the TMA-staged kernel takes one body
     if (c->collision != VPLBM_COLLISION_MRT) return;
     const int es = (int)elem_size(c->precision);
     const int halo = tma_halo(c->precision);
@@ -271,8 +288,11 @@ void setup_tma(vplbm_ctx *c)
 vplbm_status reset_run(vplbm_ctx *c)
 {
     if (c->base.bc[VPLBM_EAST] == VPLBM_BC_CONVECTIVE) CUDA_TRY(launch_outlet_reset(c->precision, params_for(c, 0), c->stream));
-    BodyState s[2] = {initial_state(c), initial_state(c)};
-    CUDA_TRY(cudaMemcpyAsync(c->bs, s, sizeof s, cudaMemcpyHostToDevice, c->stream));
+    const int slots = body_slots(c->nbodies);
+    BodyState s[2 * VPLBM_MAX_BODIES];
+    for (int par = 0; par < 2; ++par)
+        for (int k = 0; k < slots; ++k) s[par * slots + k] = initial_state(c, k);
+    CUDA_TRY(cudaMemcpyAsync(c->bs, s, 2 * slots * sizeof(BodyState), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaMemsetAsync(c->ctrl, 0, sizeof(Control), c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     c->nstep = 0;
@@ -313,6 +333,7 @@ void fill_dev_body(StepParams &p, const vplbm_lattice_desc *lat, const vplbm_bod
     b.rbf = (float)rb;
     b.bandr = (float)(1e-5 * bounding_radius(body) + 1e-5);
     p.r2f = (float)b.r2;
+    b.r2f = p.r2f;
     b.amp = body->amp;
     b.freq = body->freq;
     b.phase = body->phase;
@@ -335,9 +356,10 @@ void fill_dev_body(StepParams &p, const vplbm_lattice_desc *lat, const vplbm_bod
 
 namespace {
 
-vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body_desc *body,
+vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body_desc *bodies, int nb,
                    long long cap, void *stream)
 {
+    const vplbm_body_desc *body = nb > 0 ? &bodies[0] : nullptr;
     c->stream = (cudaStream_t)stream;
     CUDA_TRY(cudaGetDevice(&c->device));
     CUDA_TRY(cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking));
@@ -348,6 +370,8 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     c->hist_cap = cap;
     c->has_body = body != nullptr;
     if (body) c->body_desc = *body;
+    c->nbodies = nb;
+    for (int k = 0; k < nb; ++k) c->bodies[k] = bodies[k];
 
     StepParams &p = c->base;
     p.nx = lat->nx;
@@ -411,10 +435,33 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     fill_dev_body(p, lat, body);
     p.partials = c->partials;
     p.max_parts = c->max_parts;
-    p.ticket = &c->ctrl->ticket;
+    p.ticket = &c->ctrl->ticket[0];
     p.err = &c->ctrl->err;
     p.hist = c->hist;
     p.hist_cap = cap;
+    p.nbodies = nb;
+    for (int k = 0; k < nb; ++k) p.body_radius[k] = bounding_radius(&bodies[k]);
+    if (nb > 1) {
+        // per-body views of each parity's parameters
+        std::vector<StepParams> views((size_t)2 * nb);
+        for (int par = 0; par < 2; ++par) {
+            const StepParams q = params_for(c, par);
+            for (int k = 0; k < nb; ++k) {
+                StepParams &w = views[(size_t)par * nb + k];
+                w = q;
+                fill_dev_body(w, lat, &bodies[k]);
+                w.bs_in = q.bs_in + k;
+                w.bs_out = q.bs_out + k;
+                w.partials = c->partials + (size_t)k * c->max_parts * NPART;
+                w.ticket = &c->ctrl->ticket[k];
+                w.hist = c->hist + (size_t)k * cap;
+                w.views = nullptr;
+                w.nbodies = 1;
+            }
+        }
+        CUDA_TRY(cudaMemcpyAsync(c->views, views.data(), views.size() * sizeof(StepParams), cudaMemcpyHostToDevice,
+                                 c->stream));
+    }
 
     setup_tma(c);
     // default: the scalar kernel sized for 6 blocks of 256 threads per SM
@@ -426,23 +473,28 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     StepParams q = params_for(c, 0);
     q.fout = c->f[0];
     CUDA_TRY(launch_init_equilibrium(c->precision, q, nullptr, nullptr, nullptr, c->stream));
-    CUDA_TRY(cudaMemsetAsync(c->hist, 0, (size_t)cap * sizeof(vplbm_record), c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->hist, 0, (size_t)body_slots(nb) * cap * sizeof(vplbm_record), c->stream));
     return reset_run(c);
 }
 
-vplbm_status create_impl(const vplbm_lattice_desc *lat, const vplbm_body_desc *body, long long cap,
+vplbm_status create_impl(const vplbm_lattice_desc *lat, const vplbm_body_desc *bodies, int nb, long long cap,
                          void *stream, const vplbm_buffers *user, vplbm_ctx **out)
 {
     if (!out) return fail(VPLBM_EINVAL, "out pointer is NULL");
     *out = nullptr;
     vplbm_status st = check_lattice(lat);
     if (st != VPLBM_OK) return st;
-    st = check_body(body);
-    if (st != VPLBM_OK) return st;
+    if (nb < 0 || nb > VPLBM_MAX_BODIES || (nb > 0 && !bodies))
+        return fail(VPLBM_EINVAL, "number of bodies must be in [1, %d] with a non-NULL array", VPLBM_MAX_BODIES);
+    for (int k = 0; k < nb; ++k) {
+        st = check_body(&bodies[k]);
+        if (st != VPLBM_OK) return st;
+    }
+    if (nb > 1 && user) return fail(VPLBM_EUNSUPPORTED, "several bodies need library-allocated memory");
     if (cap < 1) return fail(VPLBM_EINVAL, "history capacity must be >= 1");
     vplbm_buffer_sizes sz;
     long long ps = 0, parts = 0;
-    sizes_for(lat, body, cap, &sz, &ps, &parts);
+    sizes_for(lat, bodies, nb, cap, &sz, &ps, &parts);
 
     vplbm_ctx *c = new (std::nothrow) vplbm_ctx();
     if (!c) return fail(VPLBM_ENOMEM, "host allocation failed");
@@ -475,13 +527,15 @@ vplbm_status create_impl(const vplbm_lattice_desc *lat, const vplbm_body_desc *b
         char *base = (char *)c->owned;
         c->f[0] = base; base += sz.populations;
         c->f[1] = base; base += sz.populations;
-        c->bs = (BodyState *)base; base += sz.body_state;
+        c->bs = (BodyState *)base;
+        if (nb > 1) c->views = reinterpret_cast<StepParams *>(base + 2 * (size_t)nb * sizeof(BodyState));
+        base += sz.body_state;
         c->partials = (double *)base; base += sz.partials;
         c->hist = (vplbm_record *)base; base += sz.history;
         c->prof = (double *)base; base += sz.profiles;
         c->ctrl = (Control *)base;
     }
-    st = setup(c, lat, body, cap, stream);
+    st = setup(c, lat, bodies, nb, cap, stream);
     if (st != VPLBM_OK) {
         vplbm_destroy(c);
         return st;
@@ -581,9 +635,12 @@ void full_to_stored(const vplbm_ctx *c, const double *f, void *raw)
     }
 }
 
+// Checkpoint layout: header, the body states of the current parity
+// (extra_bodies + 1), the stored populations, the history rings
+// ([body][hist_cap]), the outlet state.
 struct CkptHeader {
     char magic[8];
-    int nx, ny, precision, pad;
+    int nx, ny, precision, extra_bodies;
     long long ps, nstep, hist_cap, launches;
 };
 
@@ -612,7 +669,7 @@ vplbm_status vplbm_buffer_sizes_for(const vplbm_lattice_desc *lat, const vplbm_b
     st = check_body(body);
     if (st != VPLBM_OK) return st;
     if (history_capacity < 1) return fail(VPLBM_EINVAL, "history capacity must be >= 1");
-    sizes_for(lat, body, history_capacity, out, nullptr, nullptr);
+    sizes_for(lat, body, body ? 1 : 0, history_capacity, out, nullptr, nullptr);
     return VPLBM_OK;
 }
 
@@ -620,7 +677,7 @@ vplbm_status vplbm_create(const vplbm_lattice_desc *lat, const vplbm_body_desc *
                           long long history_capacity, void *cuda_stream, vplbm_ctx **out)
 {
     try {
-        return create_impl(lat, body, history_capacity, cuda_stream, nullptr, out);
+        return create_impl(lat, body, body ? 1 : 0, history_capacity, cuda_stream, nullptr, out);
     } catch (...) {
         return fail(VPLBM_ENOMEM, "host allocation failed");
     }
@@ -632,7 +689,20 @@ vplbm_status vplbm_create_with_buffers(const vplbm_lattice_desc *lat, const vplb
 {
     if (!buffers) return fail(VPLBM_EINVAL, "buffers is NULL");
     try {
-        return create_impl(lat, body, history_capacity, cuda_stream, buffers, out);
+        return create_impl(lat, body, body ? 1 : 0, history_capacity, cuda_stream, buffers, out);
+    } catch (...) {
+        return fail(VPLBM_ENOMEM, "host allocation failed");
+    }
+}
+
+vplbm_status vplbm_create_bodies(const vplbm_lattice_desc *lat, const vplbm_body_desc *bodies, int nbodies,
+                                 long long history_capacity, void *cuda_stream, vplbm_ctx **out)
+{
+    if (out) *out = nullptr;
+    if (nbodies < 1 || nbodies > VPLBM_MAX_BODIES || !bodies)
+        return fail(VPLBM_EINVAL, "number of bodies must be in [1, %d] with a non-NULL array", VPLBM_MAX_BODIES);
+    try {
+        return create_impl(lat, bodies, nbodies, history_capacity, cuda_stream, nullptr, out);
     } catch (...) {
         return fail(VPLBM_ENOMEM, "host allocation failed");
     }
@@ -740,7 +810,14 @@ vplbm_status vplbm_get_fields(vplbm_ctx *c, double *rho, double *ux, double *uy)
 
 vplbm_status vplbm_get_history(vplbm_ctx *c, long long first, long long count, vplbm_record *dst)
 {
+    return vplbm_get_history_body(c, 0, first, count, dst);
+}
+
+vplbm_status vplbm_get_history_body(vplbm_ctx *c, int k, long long first, long long count, vplbm_record *dst)
+{
     if (!c || (!dst && count > 0)) return fail(VPLBM_EINVAL, "NULL argument");
+    if (k < 0 || k >= body_slots(c->nbodies)) return fail(VPLBM_EINVAL, "body %d out of range", k);
+    const vplbm_record *ring = c->hist + (size_t)k * c->hist_cap;
     if (first < 0 || count < 0) return fail(VPLBM_EINVAL, "negative range");
     if (first + count > c->nstep || first < c->nstep - c->hist_cap)
         return fail(VPLBM_ERANGE, "records [%lld, %lld) not available (step %lld, capacity %lld)", first,
@@ -750,7 +827,7 @@ vplbm_status vplbm_get_history(vplbm_ctx *c, long long first, long long count, v
         const long long slot = (first + done) % c->hist_cap;
         long long len = c->hist_cap - slot;
         if (len > count - done) len = count - done;
-        CUDA_TRY(cudaMemcpyAsync(dst + done, c->hist + slot, (size_t)len * sizeof(vplbm_record),
+        CUDA_TRY(cudaMemcpyAsync(dst + done, ring + slot, (size_t)len * sizeof(vplbm_record),
                                  cudaMemcpyDeviceToHost, c->stream));
         done += len;
     }
@@ -760,9 +837,23 @@ vplbm_status vplbm_get_history(vplbm_ctx *c, long long first, long long count, v
 
 vplbm_status vplbm_get_body(vplbm_ctx *c, double q[3], double v[3], long long *step)
 {
+    return vplbm_get_body_k(c, 0, q, v, step);
+}
+
+vplbm_status vplbm_get_num_bodies(vplbm_ctx *c, int *nbodies)
+{
+    if (!c || !nbodies) return fail(VPLBM_EINVAL, "NULL argument");
+    *nbodies = c->nbodies;
+    return VPLBM_OK;
+}
+
+vplbm_status vplbm_get_body_k(vplbm_ctx *c, int k, double q[3], double v[3], long long *step)
+{
     if (!c) return fail(VPLBM_EINVAL, "context is NULL");
+    if (k < 0 || k >= body_slots(c->nbodies)) return fail(VPLBM_EINVAL, "body %d out of range", k);
     BodyState s;
-    CUDA_TRY(cudaMemcpyAsync(&s, c->bs + (c->nstep & 1), sizeof s, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(&s, c->bs + (c->nstep & 1) * body_slots(c->nbodies) + k, sizeof s, cudaMemcpyDeviceToHost,
+                             c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     for (int d = 0; d < 3; ++d) {
         if (q) q[d] = s.q[d];
@@ -790,8 +881,11 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
         return fail(VPLBM_EINVAL, "launch shape %dx%d not allowed", bx, by);
     int w, h;
     tile_of(kernel, bx, by, &w, &h);
-    if (max_reduction_blocks(c->nx, c->ny, c->has_body ? bounding_radius(&c->body_desc) : 0.0, c->has_body, w, h) > c->max_parts)
-        return fail(VPLBM_EINVAL, "launch shape %dx%d needs more reduction scratch than allocated", bx, by);
+    for (int k = 0; k < body_slots(c->nbodies); ++k) {
+        const bool present = k < c->nbodies;
+        if (max_reduction_blocks(c->nx, c->ny, present ? bounding_radius(&c->bodies[k]) : 0.0, present, w, h) > c->max_parts)
+            return fail(VPLBM_EINVAL, "launch shape %dx%d needs more reduction scratch than allocated", bx, by);
+    }
     c->kernel = kernel;
     c->bx = bx;
     c->by = by;
@@ -830,8 +924,9 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
     steps_per_trial += steps_per_trial & 1;
     // save the run state
     void *save_f = nullptr, *save_h = nullptr;
-    BodyState save_bs[2];
-    const size_t hbytes = (size_t)c->hist_cap * sizeof(vplbm_record);
+    BodyState save_bs[2 * VPLBM_MAX_BODIES];
+    const size_t bsbytes = 2 * (size_t)body_slots(c->nbodies) * sizeof(BodyState);
+    const size_t hbytes = (size_t)body_slots(c->nbodies) * c->hist_cap * sizeof(vplbm_record);
     CUDA_TRY(cudaMalloc(&save_f, c->pop_bytes));
     if (cudaMalloc(&save_h, hbytes) != cudaSuccess) {
         cudaFree(save_f);
@@ -851,7 +946,7 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
             e = cudaMemcpyAsync(outlet0, save_outlet.data(), save_outlet.size() * sizeof(double), cudaMemcpyHostToDevice,
                                 c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c->hist, save_h, hbytes, cudaMemcpyDeviceToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(c->bs, save_bs, sizeof save_bs, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->bs, save_bs, bsbytes, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         c->nstep = nstep0;
         return e;
@@ -859,7 +954,7 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
     do {
         if (cudaMemcpyAsync(save_f, c->f[nstep0 & 1], c->pop_bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
             cudaMemcpyAsync(save_h, c->hist, hbytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
-            cudaMemcpyAsync(save_bs, c->bs, sizeof save_bs, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaMemcpyAsync(save_bs, c->bs, bsbytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
             cudaMemcpyAsync(save_outlet.data(), outlet0, save_outlet.size() * sizeof(double), cudaMemcpyDeviceToHost,
                             c->stream) != cudaSuccess ||
             cudaStreamSynchronize(c->stream) != cudaSuccess ||
@@ -919,23 +1014,25 @@ vplbm_status vplbm_save(vplbm_ctx *c, const char *path)
 {
     if (!c || !path) return fail(VPLBM_EINVAL, "NULL argument");
     try {
+        const int slots = body_slots(c->nbodies);
         std::vector<char> raw(c->pop_bytes);
-        std::vector<vplbm_record> hist((size_t)c->hist_cap);
+        std::vector<vplbm_record> hist((size_t)slots * c->hist_cap);
         std::vector<double> outlet((size_t)3 * c->ny);
-        BodyState bs;
+        BodyState bs[VPLBM_MAX_BODIES];
         CUDA_TRY(cudaMemcpyAsync(outlet.data(), params_for(c, c->nstep).conv_in, outlet.size() * sizeof(double),
                                  cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaMemcpyAsync(raw.data(), c->f[c->nstep & 1], c->pop_bytes, cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaMemcpyAsync(hist.data(), c->hist, hist.size() * sizeof(vplbm_record), cudaMemcpyDeviceToHost, c->stream));
-        CUDA_TRY(cudaMemcpyAsync(&bs, c->bs + (c->nstep & 1), sizeof bs, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(bs, c->bs + (c->nstep & 1) * slots, slots * sizeof(BodyState), cudaMemcpyDeviceToHost,
+                                 c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
         CkptHeader h{};
         memcpy(h.magic, CKPT_MAGIC, 8);
-        h.nx = c->nx; h.ny = c->ny; h.precision = c->precision;
+        h.nx = c->nx; h.ny = c->ny; h.precision = c->precision; h.extra_bodies = slots - 1;
         h.ps = c->ps; h.nstep = c->nstep; h.hist_cap = c->hist_cap; h.launches = c->launches;
         FILE *fp = fopen(path, "wb");
         if (!fp) return fail(VPLBM_EIO, "cannot open %s for writing", path);
-        bool ok = fwrite(&h, sizeof h, 1, fp) == 1 && fwrite(&bs, sizeof bs, 1, fp) == 1 &&
+        bool ok = fwrite(&h, sizeof h, 1, fp) == 1 && fwrite(bs, sizeof(BodyState), slots, fp) == (size_t)slots &&
                   fwrite(raw.data(), 1, raw.size(), fp) == raw.size() &&
                   fwrite(hist.data(), sizeof(vplbm_record), hist.size(), fp) == hist.size() &&
                   fwrite(outlet.data(), sizeof(double), outlet.size(), fp) == outlet.size();
@@ -953,19 +1050,25 @@ vplbm_status vplbm_load(vplbm_ctx *c, const char *path)
     try {
         FILE *fp = fopen(path, "rb");
         if (!fp) return fail(VPLBM_EIO, "cannot open %s", path);
+        const int slots = body_slots(c->nbodies);
         CkptHeader h;
-        BodyState bs;
-        bool ok = fread(&h, sizeof h, 1, fp) == 1 && fread(&bs, sizeof bs, 1, fp) == 1;
+        BodyState bs[VPLBM_MAX_BODIES];
+        bool ok = fread(&h, sizeof h, 1, fp) == 1;
         if (!ok || memcmp(h.magic, CKPT_MAGIC, 8) != 0) {
             fclose(fp);
             return fail(VPLBM_EIO, "%s is not a checkpoint", path);
         }
-        if (h.nx != c->nx || h.ny != c->ny || h.precision != c->precision || h.ps != c->ps || h.hist_cap != c->hist_cap) {
+        if (h.nx != c->nx || h.ny != c->ny || h.precision != c->precision || h.ps != c->ps || h.hist_cap != c->hist_cap ||
+            h.extra_bodies != slots - 1) {
             fclose(fp);
             return fail(VPLBM_EINVAL, "checkpoint %s does not match this context", path);
         }
+        if (fread(bs, sizeof(BodyState), slots, fp) != (size_t)slots) {
+            fclose(fp);
+            return fail(VPLBM_EIO, "%s is truncated", path);
+        }
         std::vector<char> raw(c->pop_bytes);
-        std::vector<vplbm_record> hist((size_t)c->hist_cap);
+        std::vector<vplbm_record> hist((size_t)slots * c->hist_cap);
         std::vector<double> outlet((size_t)3 * c->ny);
         ok = fread(raw.data(), 1, raw.size(), fp) == raw.size() &&
              fread(hist.data(), sizeof(vplbm_record), hist.size(), fp) == hist.size() &&
@@ -977,7 +1080,7 @@ vplbm_status vplbm_load(vplbm_ctx *c, const char *path)
                                  outlet.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(cudaMemcpyAsync(c->f[par], raw.data(), raw.size(), cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(cudaMemcpyAsync(c->hist, hist.data(), hist.size() * sizeof(vplbm_record), cudaMemcpyHostToDevice, c->stream));
-        CUDA_TRY(cudaMemcpyAsync(c->bs + par, &bs, sizeof bs, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->bs + par * slots, bs, slots * sizeof(BodyState), cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(cudaMemsetAsync(c->ctrl, 0, sizeof(Control), c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
         c->nstep = h.nstep;

@@ -64,7 +64,7 @@ __global__ void noalloc_prepare(const vplbm_body_state *state, int present, doub
     b.step = state->step;
     derive_pose(b, present, radius, nx, ny, shape);
     s.bs[0] = b;
-    s.ctrl.ticket = 0u;
+    for (unsigned &t : s.ctrl.ticket) t = 0u;
     s.ctrl.err = 0;
 }
 
@@ -177,7 +177,7 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const 
     fill_dev_body(p, lat, body);
     p.partials = scratch->partials;
     p.max_parts = NOALLOC_MAX_PARTS;
-    p.ticket = &scratch->ctrl.ticket;
+    p.ticket = &scratch->ctrl.ticket[0];
     p.err = &scratch->ctrl.err;
     p.hist = history_dev ? history_dev : &scratch->record;
     p.hist_cap = history_dev ? history_capacity : 1;

@@ -131,10 +131,22 @@ __global__ void fields_kernel(const StepParams p, double *rho_o, double *ux_o, d
         jy += cy_of(a) * (double)f[a];
     }
     const double rho = Prec<P>::DEV ? p.rho0 + rs : rs;
-    const BodyState bs = *p.bs_in;
-    bool chi = p.body.present && (p.body.shape == VPLBM_SHAPE_ELLIPSE     ? chi_exact_ellipse(i, j, &bs, p.body)
-                                  : p.body.shape == VPLBM_SHAPE_RECTANGLE ? chi_exact_rect(i, j, &bs, p.body)
-                                                                          : chi_exact(i, j, bs.q[0], bs.q[1], p.body.r2));
+    // chi: the first body whose predicate holds (Eq. 2)
+    auto chi_of = [&](const DevBody &body, const BodyState &s) {
+        return body.present && (body.shape == VPLBM_SHAPE_ELLIPSE     ? chi_exact_ellipse(i, j, &s, body)
+                                : body.shape == VPLBM_SHAPE_RECTANGLE ? chi_exact_rect(i, j, &s, body)
+                                                                      : chi_exact(i, j, s.q[0], s.q[1], body.r2));
+    };
+    BodyState bs = *p.bs_in;
+    bool chi = false;
+    if (p.nbodies > 1) {
+        for (int k = 0; k < p.nbodies && !chi; ++k) {
+            bs = p.bs_in[k];
+            chi = chi_of(p.views[k].body, bs);
+        }
+    } else {
+        chi = chi_of(p.body, bs);
+    }
     double vx = jx / rho + 0.5 * p.gx, vy = jy / rho + 0.5 * p.gy;
     double ax = 0, ay = 0;
     if (chi) {
@@ -191,6 +203,7 @@ cudaError_t launch_step_batch(int precision, const BatchLaunch &bl, int total_ti
 
 cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb)
 {
+    if (p.nbodies > 1) return launch_step_multi(precision, p, bx, by, stream, minb);
     if (p.body.present && p.body.shape == VPLBM_SHAPE_ELLIPSE)
         return launch_step_ellipse(precision, p, bx, by, stream, minb);
     if (p.body.present && p.body.shape == VPLBM_SHAPE_RECTANGLE)

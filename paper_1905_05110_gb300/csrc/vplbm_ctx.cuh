@@ -17,14 +17,17 @@ struct vplbm_ctx {
     long long ps = 0;                     // plane stride (elements)
     size_t pop_bytes = 0;
     StepParams base{};
-    vplbm_body_desc body_desc{};
+    vplbm_body_desc body_desc{};          // body 0
     bool has_body = false;
+    int nbodies = 0;                      // 0 .. VPLBM_MAX_BODIES
+    vplbm_body_desc bodies[VPLBM_MAX_BODIES] = {};
     void *f[2] = {nullptr, nullptr};
-    BodyState *bs = nullptr;              // [2]
+    BodyState *bs = nullptr;              // [parity][max(nbodies, 1)]
+    StepParams *views = nullptr;          // [parity][nbodies] per-body parameters (nbodies > 1)
     double *partials = nullptr;
     long long max_parts = 0;
     Control *ctrl = nullptr;
-    vplbm_record *hist = nullptr;
+    vplbm_record *hist = nullptr;         // [max(nbodies, 1)][hist_cap]
     long long hist_cap = 0;
     double *prof = nullptr;
     void *outlet = nullptr;               // convective outlet state, 2 parities x 3 x ny (8-byte slots)

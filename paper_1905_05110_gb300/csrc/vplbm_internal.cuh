@@ -55,7 +55,7 @@ struct DevBody {
     double qref;       // rho0 d_ref u_ref^2 / 2 (0: no C_D / C_L)
     double inv_qref;   // 1 / qref (0 when qref is 0)
     int shape;         // vplbm_shape; radius above is the bounding radius
-    int pad_shape;
+    float r2f;         // r2 in FP32 (the disk predicate of the storage kernels)
     double a2, b2, ab2;          // ellipse: semi-axes squared and their product
     float a2f, b2f, ab2f, bandf; // FP32 copies; bandf: FP32 test band of the ellipse predicate
     double ra, rb;               // rectangle: half-sides
@@ -140,6 +140,17 @@ struct StepParams {
     // with the number of grid rows they occupy.
     int nbody;
     int nbody_rows;
+    // several bodies in the lattice (nbodies > 1, step_multi.cu).  views:
+    // one copy of these parameters per body for this step's parity, in
+    // device memory, whose body, r2f, bs_in, bs_out, partials, ticket and
+    // hist are that body's; bs_in / bs_out above then point at the first of
+    // nbodies consecutive states.  body_blocks: the body blocks of body k
+    // are [body_blocks[k], body_blocks[k + 1]) (set by the launcher from
+    // the bounding radii).
+    const StepParams *views;
+    int nbodies;
+    int body_blocks[VPLBM_MAX_BODIES + 1];
+    double body_radius[VPLBM_MAX_BODIES];
 };
 
 // Error bits latched in the control word.
@@ -147,11 +158,11 @@ constexpr int ERR_NONFINITE = 1;
 constexpr int ERR_INTERNAL = 2;
 constexpr int ERR_TIMEOUT = 4;
 
-// Control block: ticket counter and error word.
+// Control block: ticket counter of each body and error word.
 struct Control {
-    unsigned ticket;
+    unsigned ticket[VPLBM_MAX_BODIES];
     int err;
-    unsigned pad[62];
+    unsigned pad[59];
 };
 static_assert(sizeof(Control) == 256, "Control layout");
 
@@ -231,6 +242,8 @@ cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cuda
 // The same for an elliptic body (step_ellipse.cu) and a rectangular one (step_rectangle.cu).
 cudaError_t launch_step_ellipse(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb);
 cudaError_t launch_step_rectangle(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb);
+// Several bodies of any shapes (step_multi.cu); p.nbodies > 1.
+cudaError_t launch_step_multi(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb);
 cudaError_t launch_init_equilibrium(int precision, const StepParams &p, const double *rho_dev,
                                     const double *ux_dev, const double *uy_dev, cudaStream_t stream);
 // Convective outlet: previous values := the outlet column of p.fin (into p.conv_in).

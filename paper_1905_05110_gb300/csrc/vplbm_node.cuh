@@ -403,23 +403,81 @@ __device__ __forceinline__ void solid_node_terms(const StepParams &p, const type
 }
 
 
-// The VP-MRT update of one interior-or-edge node from its pulled
-// populations f: moments, chi and u_s, penalized velocity (Eq. 22),
-// collision with forcing (Eq. 17) and the store of f~.  Returns chi and
-// keeps rho, a for the solid-node sums.
-// SHAPE: VPLBM_SHAPE_DISK or VPLBM_SHAPE_ELLIPSE fixed at compile time, or
-// SHAPE_ANY to read it from the parameters.
+// Body shape read from the parameters instead of fixed at compile time.
 constexpr int SHAPE_ANY = -1;
 
-template <int P, int COLL = VPLBM_COLLISION_MRT, int SHAPE = SHAPE_ANY>
-__device__ __forceinline__ bool node_update(const StepParams &p, const BodyState *__restrict__ bs, bool near_body,
-                                            int i, int j, const typename Prec<P>::T f[NQ],
-                                            typename Prec<P>::S *__restrict__ fout, typename Prec<P>::T &cr,
-                                            typename Prec<P>::T &cax, typename Prec<P>::T &cay)
+// chi of node (i, j) for one body (Eq. 2, Alg. 1 step 4) and its lever arm
+// (dxl, dyl) = x - x_G.  The storage kernels test in FP32 and re-test in
+// FP64 where the FP32 value is within the band of the boundary, so the
+// result is the exact FP64 predicate.  SHAPE: VPLBM_SHAPE_DISK, _ELLIPSE or
+// _RECTANGLE fixed at compile time, or SHAPE_ANY to read it from the body.
+template <int P, int SHAPE>
+__device__ __forceinline__ bool body_chi(const DevBody &body, float r2f, const BodyState *__restrict__ bs, int i,
+                                         int j, typename Prec<P>::T &dxl, typename Prec<P>::T &dyl)
 {
     using T = typename Prec<P>::T;
     constexpr bool DEV = Prec<P>::DEV;
     bool chi = false;
+    if constexpr (DEV) {
+        const int2 xy = __ldg(reinterpret_cast<const int2 *>(&bs->xi));
+        const float2 fr = __ldg(reinterpret_cast<const float2 *>(&bs->xf));
+        const float dxf = (float)(i - xy.x) - fr.x;
+        const float dyf = (float)(j - xy.y) - fr.y;
+        const int shape = SHAPE == SHAPE_ANY ? body.shape : SHAPE;
+        if (shape == VPLBM_SHAPE_RECTANGLE) {
+            // |u| <= a and |v| <= b in the body frame, in FP32, exact
+            // FP64 re-test where either is within the band of its edge
+            const float2 cs = __ldg(reinterpret_cast<const float2 *>(&bs->cthf));
+            const float uf = fabsf(dxf * cs.x + dyf * cs.y);
+            const float vf = fabsf(dyf * cs.x - dxf * cs.y);
+            const float band = body.bandr;
+            if (fabsf(uf - body.raf) <= band || fabsf(vf - body.rbf) <= band)
+                chi = chi_exact_rect(i, j, bs, body);
+            else
+                chi = uf <= body.raf && vf <= body.rbf;
+        } else if (shape == VPLBM_SHAPE_ELLIPSE) {
+            // b^2 u^2 + a^2 v^2 <= a^2 b^2 in the body frame, in FP32,
+            // exact FP64 re-test inside the band
+            const float2 cs = __ldg(reinterpret_cast<const float2 *>(&bs->cthf));
+            const float uf = dxf * cs.x + dyf * cs.y;
+            const float vf = dyf * cs.x - dxf * cs.y;
+            const float lhs = body.b2f * (uf * uf) + body.a2f * (vf * vf);
+            if (fabsf(lhs - body.ab2f) <= body.bandf) chi = chi_exact_ellipse(i, j, bs, body);
+            else chi = lhs <= body.ab2f;
+        } else {
+            const float d2 = dxf * dxf + dyf * dyf;
+            const float r2 = r2f;
+            const float band = 1e-5f * r2 + 1e-5f;
+            if (fabsf(d2 - r2) <= band) chi = chi_exact(i, j, bs->q[0], bs->q[1], body.r2);
+            else chi = d2 <= r2;
+        }
+        dxl = dxf; dyl = dyf;
+    } else {
+        const double xg = __ldg(&bs->q[0]), yg = __ldg(&bs->q[1]);
+        const int shape = SHAPE == SHAPE_ANY ? body.shape : SHAPE;
+        chi = shape == VPLBM_SHAPE_ELLIPSE   ? chi_exact_ellipse(i, j, bs, body)
+              : shape == VPLBM_SHAPE_RECTANGLE ? chi_exact_rect(i, j, bs, body)
+                                               : chi_exact(i, j, xg, yg, body.r2);
+        dxl = (double)i - xg;
+        dyl = (double)j - yg;
+    }
+    return chi;
+}
+
+// The VP-MRT (or BGK) update of one node from its pulled populations f
+// given chi and the lever arm from body_chi: moments, u_s of the body
+// state bs, penalized velocity (Eq. 22), collision with forcing (Eq. 17)
+// and the store of f~.  Returns chi and keeps rho, a for the solid-node
+// sums.
+template <int P, int COLL>
+__device__ __forceinline__ bool node_collide(const StepParams &p, const BodyState *__restrict__ bs, bool chi,
+                                             typename Prec<P>::T dxl, typename Prec<P>::T dyl, int i, int j,
+                                             const typename Prec<P>::T f[NQ], typename Prec<P>::S *__restrict__ fout,
+                                             typename Prec<P>::T &cr, typename Prec<P>::T &cax,
+                                             typename Prec<P>::T &cay)
+{
+    using T = typename Prec<P>::T;
+    constexpr bool DEV = Prec<P>::DEV;
     // sums shared by the moments (rows of Eq. 15)
     const T d13 = f[1] - f[3], d24 = f[2] - f[4], b13 = f[1] + f[3], b24 = f[2] + f[4];
     const T d56 = f[5] - f[6], d87 = f[8] - f[7], a56 = f[5] + f[6], a78 = f[7] + f[8];
@@ -428,54 +486,6 @@ __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState
     const T rho = DEV ? par<T>(p.rho0, p.rho0f) + rs : rs;
     const T jx = d13 + sx;
     const T jy = d24 + ty;
-
-    // chi and u_s (Eq. 2, Alg. 1 step 4), only where the disk can be
-    T dxl = 0, dyl = 0;
-    if (near_body) {
-        if constexpr (DEV) {
-            const int2 xy = __ldg(reinterpret_cast<const int2 *>(&bs->xi));
-            const float2 fr = __ldg(reinterpret_cast<const float2 *>(&bs->xf));
-            const float dxf = (float)(i - xy.x) - fr.x;
-            const float dyf = (float)(j - xy.y) - fr.y;
-            const int shape = SHAPE == SHAPE_ANY ? p.body.shape : SHAPE;
-            if (shape == VPLBM_SHAPE_RECTANGLE) {
-                // |u| <= a and |v| <= b in the body frame, in FP32, exact
-                // FP64 re-test where either is within the band of its edge
-                const float2 cs = __ldg(reinterpret_cast<const float2 *>(&bs->cthf));
-                const float uf = fabsf(dxf * cs.x + dyf * cs.y);
-                const float vf = fabsf(dyf * cs.x - dxf * cs.y);
-                const float band = p.body.bandr;
-                if (fabsf(uf - p.body.raf) <= band || fabsf(vf - p.body.rbf) <= band)
-                    chi = chi_exact_rect(i, j, bs, p.body);
-                else
-                    chi = uf <= p.body.raf && vf <= p.body.rbf;
-            } else if (shape == VPLBM_SHAPE_ELLIPSE) {
-                // b^2 u^2 + a^2 v^2 <= a^2 b^2 in the body frame, in FP32,
-                // exact FP64 re-test inside the band
-                const float2 cs = __ldg(reinterpret_cast<const float2 *>(&bs->cthf));
-                const float uf = dxf * cs.x + dyf * cs.y;
-                const float vf = dyf * cs.x - dxf * cs.y;
-                const float lhs = p.body.b2f * (uf * uf) + p.body.a2f * (vf * vf);
-                if (fabsf(lhs - p.body.ab2f) <= p.body.bandf) chi = chi_exact_ellipse(i, j, bs, p.body);
-                else chi = lhs <= p.body.ab2f;
-            } else {
-                const float d2 = dxf * dxf + dyf * dyf;
-                const float r2 = p.r2f;
-                const float band = 1e-5f * r2 + 1e-5f;
-                if (fabsf(d2 - r2) <= band) chi = chi_exact(i, j, bs->q[0], bs->q[1], p.body.r2);
-                else chi = d2 <= r2;
-            }
-            dxl = dxf; dyl = dyf;
-        } else {
-            const double xg = __ldg(&bs->q[0]), yg = __ldg(&bs->q[1]);
-            const int shape = SHAPE == SHAPE_ANY ? p.body.shape : SHAPE;
-            chi = shape == VPLBM_SHAPE_ELLIPSE   ? chi_exact_ellipse(i, j, bs, p.body)
-                  : shape == VPLBM_SHAPE_RECTANGLE ? chi_exact_rect(i, j, bs, p.body)
-                                                   : chi_exact(i, j, xg, yg, p.body.r2);
-            dxl = (double)i - xg;
-            dyl = (double)j - yg;
-        }
-    }
 
     // penalized velocity, Eq. (22) in the eta-stable form
     const T inv_rho = recip(rho);
@@ -583,6 +593,21 @@ __device__ __forceinline__ bool node_update(const StepParams &p, const BodyState
     if (!(rho > (T)0) || !(rho < (T)1e30)) *p.err = ERR_NONFINITE;
     cr = rho; cax = ax; cay = ay;
     return chi;
+}
+
+// The update of one interior-or-edge node of a lattice with one body: chi
+// where the body can be (near_body, uniform over the block), then
+// node_collide.
+template <int P, int COLL = VPLBM_COLLISION_MRT, int SHAPE = SHAPE_ANY>
+__device__ __forceinline__ bool node_update(const StepParams &p, const BodyState *__restrict__ bs, bool near_body,
+                                            int i, int j, const typename Prec<P>::T f[NQ],
+                                            typename Prec<P>::S *__restrict__ fout, typename Prec<P>::T &cr,
+                                            typename Prec<P>::T &cax, typename Prec<P>::T &cay)
+{
+    typename Prec<P>::T dxl = 0, dyl = 0;
+    bool chi = false;
+    if (near_body) chi = body_chi<P, SHAPE>(p.body, p.r2f, bs, i, j, dxl, dyl);
+    return node_collide<P, COLL>(p, bs, chi, dxl, dyl, i, j, f, fout, cr, cax, cay);
 }
 
 // Does the tile [i0, i0+w) x [j0, j0+h) meet the node range that may hold

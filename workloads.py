@@ -137,6 +137,32 @@ def paper_oscillating_cylinder(nx=1230, ny=410, diameter=41.0, x_c=None, tau=0.5
     }
 
 
+def several_bodies(nx=2048, ny=1024, diameter=40.0, u0=0.04, re=100.0, eta=1e-3, u_star=5.0,
+                   mass_ratio=10.0, steps=20_000) -> dict:
+    """The oscillating-disk channel holding four bodies: the imposed
+    oscillating disk of `oscillating_disk` at x = 400, a fixed disk 5 D
+    behind it on the axis, and two disks free in y on springs (m* = 10,
+    U* = 5, no damping, as in `viv_disk`) side by side 10 D behind it,
+    3 D off the axis."""
+    p = oscillating_disk(nx=nx, ny=ny, diameter=diameter, u0=u0, re=re, eta=eta, steps=steps)
+    lead = p.pop("body")
+    radius = diameter / 2
+    y0 = ny / 2.0
+    m, inertia = disk_mass(radius, mass_ratio)
+    f_n = u0 / (u_star * diameter)
+    k = m * (2.0 * math.pi * f_n) ** 2
+    x0 = lead["x"]
+    common = {"radius": radius, "u_ref": u0, "d_ref": diameter}
+    p["bodies"] = [
+        lead,
+        dict(common, x=x0 + 5 * diameter, y=y0, motion="fixed"),
+    ] + [dict(common, x=x0 + 10 * diameter, y=y0 + side * 3 * diameter, motion="free", mass=m,
+              inertia=inertia, stiff=(0.0, k, 0.0), q0=(0.0, y0 + side * 3 * diameter, 0.0), dof_mask=2)
+         for side in (-1, 1)]
+    p["name"] = f"several_bodies_{nx}x{ny}"
+    return p
+
+
 def happel_kappa(h_tilde: float) -> float:
     """Confinement factor of Eq. (34)."""
     h = h_tilde
