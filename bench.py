@@ -78,14 +78,24 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
-    """Hash of every CUDA source of the library (any change invalidates counters)."""
+# Sources that make up each step kernel's code: the public header, the
+# internal headers and the translation unit that instantiates it.
+KERNEL_SOURCES = {
+    "vp_mrt_step<": ("vplbm_internal.cuh", "vplbm_node.cuh", "step_scalar.cuh", "step_kernels.cu"),
+    "vp_mrt_step_tma<": ("vplbm_internal.cuh", "vplbm_node.cuh", "step_tma.cu"),
+}
+
+
+def kernel_source_hash(kernel: str = "vp_mrt_step<") -> str:
+    """Hash of the sources of one step kernel (any change to them invalidates
+    its counters)."""
+    files = next(v for k, v in KERNEL_SOURCES.items() if kernel.startswith(k))
     h = hashlib.sha256()
-    for name in sorted(os.listdir(CSRC)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(CSRC, name), "rb") as fh:
-                h.update(name.encode())
-                h.update(fh.read())
+    paths = [os.path.join(ROOT, "include", "vplbm.h")] + [os.path.join(CSRC, f) for f in files]
+    for path in paths:
+        with open(path, "rb") as fh:
+            h.update(os.path.basename(path).encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -99,7 +109,7 @@ def profiled_traffic(kernel: str, workload: str):
         return None
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     m_bytes = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.e+]+)", text)
-    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash(kernel):
         return None
     return float(m_bytes.group(1))
 
@@ -291,7 +301,7 @@ def run_ours(args, rank, world, local_rank):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                 "kernel": kname, "algorithmic_bytes_per_launch": BYTES_PER_NODE[prec] * nodes,
-                "kernel_source_sha256_16": kernel_source_hash()}
+                "kernel_source_sha256_16": kernel_source_hash(kname)}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None

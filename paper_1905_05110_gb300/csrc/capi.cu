@@ -38,6 +38,7 @@ vplbm_status fail(vplbm_status st, const char *fmt, ...)
 
 constexpr size_t ALIGN = 256;
 constexpr int GRAPH_STEPS = 32;   // steps per captured graph (even)
+constexpr int MAX_GRID_ROWS = 65535;   // gridDim.y limit of the scalar kernels
 constexpr char CKPT_MAGIC[8] = {'V', 'P', 'L', 'B', 'M', 'C', 'K', '3'};
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -147,6 +148,7 @@ vplbm_status check_body(const vplbm_body_desc *b)
 }
 
 void tile_of(int kernel, int bx, int by, int *w, int *h);
+long long grid_rows(const vplbm_ctx *c, int bx, int by);
 
 // Bodies of a context: nb descriptors (nb = 0: no body); per-body buffers
 // have max(nb, 1) slots.
@@ -232,6 +234,19 @@ cudaError_t launch_one(const vplbm_ctx *c, long long step, cudaStream_t stream)
 
 // Reduction tile of a launch choice: the block for the scalar kernels, the
 // TMA kernel's fixed tile otherwise.
+// Rows of a scalar kernel's grid for blocks of bx x by: one row of blocks
+// per row of tiles plus the rows of the body blocks.
+long long grid_rows(const vplbm_ctx *c, int bx, int by)
+{
+    const long long ntx = (c->nx + bx - 1) / bx, nty = (c->ny + by - 1) / by;
+    long long nbody = 0;
+    for (int k = 0; k < body_slots(c->nbodies); ++k) {
+        const bool present = k < c->nbodies;
+        nbody += max_reduction_blocks(c->nx, c->ny, present ? bounding_radius(&c->bodies[k]) : 0.0, present, bx, by);
+    }
+    return nty + (nbody + ntx - 1) / ntx;
+}
+
 void tile_of(int kernel, int bx, int by, int *w, int *h)
 {
     if (kernel == KERNEL_TMA) { *w = TMA_TILE_W; *h = TMA_TILE_H; }
@@ -469,6 +484,13 @@ vplbm_status setup(vplbm_ctx *c, const vplbm_lattice_desc *lat, const vplbm_body
     c->kernel = c->precision == VPLBM_F64 ? KERNEL_SCALAR : KERNEL_SCALAR_40;
     c->bx = 256;
     c->by = 1;
+    // a lattice too tall for 256 x 1 blocks (grid rows <= 65535) takes
+    // taller blocks; 32 x 8 fits every lattice check_lattice accepts
+    static const int taller[3][2] = {{128, 2}, {64, 4}, {32, 8}};
+    for (int k = 0; k < 3 && grid_rows(c, c->bx, c->by) > MAX_GRID_ROWS; ++k) {
+        c->bx = taller[k][0];
+        c->by = taller[k][1];
+    }
     // populations at rest
     StepParams q = params_for(c, 0);
     q.fout = c->f[0];
@@ -886,6 +908,9 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
         if (max_reduction_blocks(c->nx, c->ny, present ? bounding_radius(&c->bodies[k]) : 0.0, present, w, h) > c->max_parts)
             return fail(VPLBM_EINVAL, "launch shape %dx%d needs more reduction scratch than allocated", bx, by);
     }
+    if (grid_rows(c, bx, by) > MAX_GRID_ROWS)
+        return fail(VPLBM_EINVAL, "launch shape %dx%d needs more than %d grid rows on this lattice", bx, by,
+                    MAX_GRID_ROWS);
     c->kernel = kernel;
     c->bx = bx;
     c->by = by;

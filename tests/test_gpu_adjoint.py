@@ -119,3 +119,32 @@ def test_adjoint_directional_derivatives_match_central_differences():
         fd = (_objective_gpu(perturbed(1), N, w0) - _objective_gpu(perturbed(-1), N, w0)) / (2 * h)
         adj = float(grad @ (scale * v))
         assert abs(fd - adj) < 1e-4 * abs(adj) + 1e-10, (fd, adj)
+
+
+def test_autograd_function_gives_the_adjoint_gradient_and_passes_gradcheck():
+    # The torch.autograd.Function: the forward's (J1, J2) equal the
+    # adjoint's, the backward of g . J is the adjoint run with weights g, and
+    # torch's own gradcheck (central differences of the forward through the
+    # C ABI, FP64) accepts it.
+    import torch
+    from paper_1905_05110_gb300.autograd import adjoint_objectives
+    p = wl.adjoint_channel()
+    N, w0 = 30, 15
+    dev = torch.device("cuda")
+    u = torch.tensor(p["bc"]["west"]["ux_profile"], dtype=torch.float64, device=dev, requires_grad=True)
+    eta = torch.tensor(p["eta"], dtype=torch.float64, device=dev, requires_grad=True)
+    s_nu = torch.tensor(p["s"][7], dtype=torch.float64, device=dev, requires_grad=True)
+    s_e = torch.tensor(p["s"][1], dtype=torch.float64, device=dev, requires_grad=True)
+    J = adjoint_objectives(u, eta, s_nu, s_e, p, N, w0)
+    g, o = _init_both(p, "f64")
+    grad, js = g.adjoint(N, w0, 0.7, 0.3)
+    assert np.allclose(J.detach().cpu().numpy(), js, rtol=1e-13)
+    (0.7 * J[0] + 0.3 * J[1]).backward()
+    got = np.concatenate([u.grad.cpu().numpy(), [eta.grad.item(), s_nu.grad.item(), s_e.grad.item()]])
+    assert np.array_equal(got, grad)
+
+    def f(u_, eta_, s_nu_, s_e_):
+        return adjoint_objectives(u_, eta_, s_nu_, s_e_, p, N, w0)
+
+    args = tuple(t.detach().clone().requires_grad_(True) for t in (u, eta, s_nu, s_e))
+    assert torch.autograd.gradcheck(f, args, eps=1e-6, atol=1e-7, rtol=1e-4)

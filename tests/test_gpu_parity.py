@@ -638,3 +638,26 @@ def test_ellipse_with_equal_axes_is_the_disk_and_refusals():
         sim.adjoint(10, 5)
     assert ei.value.status == 6
     sim.close()
+
+
+def test_tall_lattice_takes_taller_blocks_within_the_grid_row_limit():
+    # 40 x 65535: 256 x 1 blocks would need 65536 grid rows (65535 tile rows
+    # and one body-block row); the context takes 128 x 2 and refuses 256 x 1.
+    import paper_1905_05110_gb300 as vp
+    p = wl.periodic_box(40, 65535, tau=0.7)
+    sim = vp.Simulation(p, precision="f16", history_capacity=8)
+    sim.init_from_problem()
+    kernel, bx, by = sim.launch()
+    assert (bx, by) == (128, 2)
+    sim.step(3)
+    sim.sync()
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    f = sim.populations()
+    assert np.array_equal(f, np.broadcast_to(w[:, None, None], f.shape))   # rest stays rest
+    with pytest.raises(vp.VplbmError) as ei:
+        sim.set_launch("scalar40", 256, 1)
+    assert ei.value.status == 1
+    sim.set_launch("scalar40", 32, 8)
+    sim.step(2)
+    sim.sync()
+    sim.close()
