@@ -273,11 +273,24 @@ vplbm_status vplbm_get_body_k(vplbm_ctx *ctx, int k, double q[3], double v[3], l
  *                          copies into a shared-memory ring (FP32/FP16
  *                          storage, nx * element size a multiple of 16 bytes,
  *                          nx >= 136 (FP32) / 144 (FP16), ny >= 4).
+ *  VPLBM_KERNEL_FUSED2     two time steps per launch (FP32/FP16 storage,
+ *                          a body on a prescribed path or none, no
+ *                          convective outlet, one body): a block computes
+ *                          step n on its 64 x 16 tile and a one-node ring
+ *                          around it into shared memory, then step n + 1
+ *                          from there, so HBM is read and written once per
+ *                          two steps.  Runs of 32 steps from an even step
+ *                          use it; other steps run the 40-register scalar
+ *                          kernel on the (block_x, block_y) given to
+ *                          vplbm_set_launch (0 x 0: the current blocks).
+ *                          Its populations equal the scalar kernel's bit
+ *                          for bit.
  * Nodes on the lattice edges and near the body always take the same code.
  * The results of different kernels agree to the rounding of the storage
  * precision. */
 typedef enum {
-    VPLBM_KERNEL_SCALAR = 0, VPLBM_KERNEL_SCALAR_48 = 1, VPLBM_KERNEL_SCALAR_40 = 2, VPLBM_KERNEL_TMA = 3
+    VPLBM_KERNEL_SCALAR = 0, VPLBM_KERNEL_SCALAR_48 = 1, VPLBM_KERNEL_SCALAR_40 = 2, VPLBM_KERNEL_TMA = 3,
+    VPLBM_KERNEL_FUSED2 = 4
 } vplbm_kernel;
 
 /* Kernel and block shape: block_x * block_y threads, block_x a multiple of

@@ -421,10 +421,11 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
 
     // reverse sweep, segment by segment; the recomputation runs the
     // context's scalar step kernel (a TMA-staged choice falls back to the
-    // 48-register scalar kernel on 256 x 1 blocks)
+    // 48-register scalar kernel on 256 x 1 blocks, a two-step choice to its
+    // single-step blocks)
     const bool scalar = c->kernel != KERNEL_TMA;
     const int rbx = scalar ? c->bx : 256, rby = scalar ? c->by : 1;
-    const int rminb = !scalar ? 5 : c->kernel == KERNEL_SCALAR_40 ? 6 : c->kernel == KERNEL_SCALAR_48 ? 5 : 4;
+    const int rminb = !scalar ? 5 : c->kernel == KERNEL_SCALAR_40 || c->kernel == KERNEL_FUSED2 ? 6 : c->kernel == KERNEL_SCALAR_48 ? 5 : 4;
     int cur = 0;   // work: lam[0], lam[1], mu
     for (long long s = nck - 1; s >= 0; --s) {
         const long long s0 = s * K, len = std::min(K, N - s0);

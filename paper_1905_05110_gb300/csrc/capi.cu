@@ -173,13 +173,21 @@ void sizes_for(const vplbm_lattice_desc *lat, const vplbm_body_desc *bodies, int
                 const long long m = max_reduction_blocks(lat->nx, lat->ny, bounding_radius(body), body != nullptr, w, h);
                 if (m > parts) parts = m;
             }
+        // the two-step kernel: the union of two consecutive node ranges
+        const long long m2 = max_reduction_blocks(lat->nx, lat->ny, bounding_radius(body) + 1.0, body != nullptr,
+                                                  FUSED2_W, FUSED2_H);
+        if (m2 > parts) parts = m2;
     }
     s->populations = round_up((size_t)(9 * ps) * elem_size(lat->precision), ALIGN);
-    // the body states [parity][slot], then (several bodies) the per-body
+    // the body states [parity][slot] (one body: two more, the two-step
+    // kernel's other pose pair), then (several bodies) the per-body
     // parameter views [parity][body]
-    s->body_state = round_up(2 * (size_t)slots * sizeof(BodyState) + (nb > 1 ? 2 * (size_t)nb * sizeof(StepParams) : 0),
+    s->body_state = round_up((nb > 1 ? 2 * (size_t)nb : 4) * sizeof(BodyState) +
+                                 (nb > 1 ? 2 * (size_t)nb * sizeof(StepParams) : 0),
                              ALIGN);
-    s->partials = round_up((size_t)slots * parts * NPART * sizeof(double), ALIGN);
+    // one partials region per body; one body: two (one per step of the
+    // two-step kernel)
+    s->partials = round_up((size_t)(slots > 2 ? slots : 2) * parts * NPART * sizeof(double), ALIGN);
     s->history = round_up((size_t)slots * cap * sizeof(vplbm_record), ALIGN);
     // FP64 profiles, then their FP32 copies: [side][comp][maxlen] each; then
     // the convective outlet state: [parity][3][ny] 8-byte slots
@@ -227,9 +235,55 @@ cudaError_t launch_one(const vplbm_ctx *c, long long step, cudaStream_t stream)
 {
     const StepParams p = params_for(c, step);
     if (c->kernel == KERNEL_TMA) return launch_step_tma(c->precision, p, c->tmap[step & 1], c->tma_grid, stream);
-    const int minb = c->kernel == KERNEL_SCALAR_40 ? 6 : c->kernel == KERNEL_SCALAR_48 ? 5 : 4;
+    // a single step of a two-step choice runs the 40-register scalar kernel
+    const int minb = c->kernel == KERNEL_SCALAR_40 || c->kernel == KERNEL_FUSED2 ? 6 : c->kernel == KERNEL_SCALAR_48 ? 5 : 4;
     return launch_step(c->precision, p, c->bx, c->by, stream, minb);
 }
+
+// Launch L of a run of two-step launches that starts at an even step with
+// the state in f[0] and poses n, n + 1 in bs[0], bs[1]: even launches go
+// f[0] -> f[1] and take their poses from bs[0..1], writing the next pair to
+// bs[2..3]; odd launches go back.  After an even number of launches the
+// state, pose and lookahead pose are where single steps expect them.
+cudaError_t launch_two(const vplbm_ctx *c, int L, cudaStream_t stream)
+{
+    const int odd = L & 1;
+    Fused2Params q;
+    q.a = params_for(c, 0);
+    q.b = params_for(c, 1);
+    const int es = (int)elem_size(c->precision);
+    q.a.fin = c->f[odd];
+    q.a.fout = c->f[odd ^ 1];
+    set_planes(q.a, es);
+    q.b.fin = c->f[odd ^ 1];
+    q.b.fout = c->f[odd ^ 1];
+    set_planes(q.b, es);
+    q.a.bs_in = c->bs + (odd ? 2 : 0);
+    q.b.bs_in = c->bs + (odd ? 3 : 1);
+    q.a.bs_out = q.b.bs_out = nullptr;
+    q.next0 = c->bs + (odd ? 0 : 2);
+    q.next1 = c->bs + (odd ? 1 : 3);
+    q.b.partials = c->partials + (size_t)c->max_parts * NPART;
+    q.b.ticket = &c->ctrl->ticket[1];
+    return launch_step_fused2(c->precision, q, stream);
+}
+
+// Why the two-step kernel cannot run this context (nullptr: it can).
+const char *fused2_refusal(const vplbm_ctx *c)
+{
+    if (c->precision == VPLBM_F64) return "the two-step kernel needs FP32 or FP16 storage";
+    if (c->nbodies > 1) return "the two-step kernel takes one body";
+    if (c->has_body && c->body_desc.motion == VPLBM_MOTION_FREE)
+        return "the two-step kernel needs a body on a prescribed path (fixed or imposed)";
+    if (c->base.bc[VPLBM_EAST] == VPLBM_BC_CONVECTIVE) return "the two-step kernel has no convective outlet";
+    if (max_reduction_blocks(c->nx, c->ny, c->has_body ? bounding_radius(&c->body_desc) + 1.0 : 0.0, c->has_body,
+                             FUSED2_W, FUSED2_H) > c->max_parts)
+        return "the two-step kernel needs more reduction scratch than allocated";
+    return nullptr;
+}
+
+// Steps of one captured graph, launches per graph.
+int graph_launches(const vplbm_ctx *c) { return c->kernel == KERNEL_FUSED2 ? 1 + GRAPH_STEPS / 2 : GRAPH_STEPS; }
 
 
 // Reduction tile of a launch choice: the block for the scalar kernels, the
@@ -303,11 +357,12 @@ void setup_tma(vplbm_ctx *c)
 vplbm_status reset_run(vplbm_ctx *c)
 {
     if (c->base.bc[VPLBM_EAST] == VPLBM_BC_CONVECTIVE) CUDA_TRY(launch_outlet_reset(c->precision, params_for(c, 0), c->stream));
+    // [parity][body]; one body: also the two-step kernel's other pose pair
     const int slots = body_slots(c->nbodies);
+    const int nstates = c->nbodies > 1 ? 2 * slots : 4;
     BodyState s[2 * VPLBM_MAX_BODIES];
-    for (int par = 0; par < 2; ++par)
-        for (int k = 0; k < slots; ++k) s[par * slots + k] = initial_state(c, k);
-    CUDA_TRY(cudaMemcpyAsync(c->bs, s, 2 * slots * sizeof(BodyState), cudaMemcpyHostToDevice, c->stream));
+    for (int m = 0; m < nstates; ++m) s[m] = initial_state(c, m % slots);
+    CUDA_TRY(cudaMemcpyAsync(c->bs, s, nstates * sizeof(BodyState), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaMemsetAsync(c->ctrl, 0, sizeof(Control), c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     c->nstep = 0;
@@ -575,8 +630,13 @@ vplbm_status ensure_graph(vplbm_ctx *c)
     }
     CUDA_TRY(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = cudaSuccess;
-    for (int k = 0; k < GRAPH_STEPS && err == cudaSuccess; ++k)
-        err = launch_one(c, k, c->capture);
+    if (c->kernel == KERNEL_FUSED2) {
+        // pose n + 1 ahead, then GRAPH_STEPS / 2 (even) two-step launches
+        err = launch_lookahead(params_for(c, 0), c->capture);
+        for (int L = 0; L < GRAPH_STEPS / 2 && err == cudaSuccess; ++L) err = launch_two(c, L, c->capture);
+    } else {
+        for (int k = 0; k < GRAPH_STEPS && err == cudaSuccess; ++k) err = launch_one(c, k, c->capture);
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c->capture, &g);
     if (err != cudaSuccess || e2 != cudaSuccess) {
@@ -600,7 +660,7 @@ vplbm_status step_impl(vplbm_ctx *c, long long n)
             if (st != VPLBM_OK) return st;
             CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
             c->nstep += GRAPH_STEPS;
-            c->launches += GRAPH_STEPS;
+            c->launches += graph_launches(c);
             n -= GRAPH_STEPS;
         } else {
             CUDA_TRY(launch_one(c, c->nstep, c->stream));
@@ -896,6 +956,24 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
         c->by = 2;
         return VPLBM_OK;
     }
+    if (kernel == KERNEL_FUSED2) {
+        const char *why = fused2_refusal(c);
+        if (why) return fail(VPLBM_EUNSUPPORTED, "%s", why);
+        // (bx, by): the 40-register scalar kernel's blocks for single
+        // steps; 0 x 0 keeps the current scalar blocks (TMA: 256 x 1)
+        if (bx == 0 && by == 0) {
+            bx = c->kernel == KERNEL_TMA ? 256 : c->bx;
+            by = c->kernel == KERNEL_TMA ? 1 : c->by;
+        }
+        const int k0 = c->kernel, bx0 = c->bx, by0 = c->by;
+        vplbm_status st = vplbm_set_launch(c, KERNEL_SCALAR_40, bx, by);
+        if (st != VPLBM_OK) {
+            c->kernel = k0; c->bx = bx0; c->by = by0;
+            return st;
+        }
+        c->kernel = KERNEL_FUSED2;
+        return VPLBM_OK;
+    }
     if (kernel != KERNEL_SCALAR && kernel != KERNEL_SCALAR_48 && kernel != KERNEL_SCALAR_40)
         return fail(VPLBM_EINVAL, "unknown kernel %d", kernel);
     const int t = bx * by;
@@ -945,12 +1023,12 @@ vplbm_status vplbm_get_launch_count(vplbm_ctx *c, long long *launches)
 vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
 {
     if (!c) return fail(VPLBM_EINVAL, "context is NULL");
-    if (steps_per_trial < 2) steps_per_trial = 2;
-    steps_per_trial += steps_per_trial & 1;
+    if (steps_per_trial < 4) steps_per_trial = 4;
+    steps_per_trial = (steps_per_trial + 3) / 4 * 4;   // whole pairs of two-step launches
     // save the run state
     void *save_f = nullptr, *save_h = nullptr;
     BodyState save_bs[2 * VPLBM_MAX_BODIES];
-    const size_t bsbytes = 2 * (size_t)body_slots(c->nbodies) * sizeof(BodyState);
+    const size_t bsbytes = (c->nbodies > 1 ? 2 * (size_t)c->nbodies : 4) * sizeof(BodyState);
     const size_t hbytes = (size_t)body_slots(c->nbodies) * c->hist_cap * sizeof(vplbm_record);
     CUDA_TRY(cudaMalloc(&save_f, c->pop_bytes));
     if (cudaMalloc(&save_h, hbytes) != cudaSuccess) {
@@ -987,18 +1065,33 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
             st = fail(VPLBM_ECUDA, "autotune setup failed");
             break;
         }
-        // candidates: the TMA-staged kernel, then every block shape of the
-        // three register budgets of the scalar kernel
+        // candidates: the TMA-staged kernel, every block shape of the three
+        // register budgets of the scalar kernel, then the two-step kernel
+        // (from an even step only: its runs start there)
         static const int kinds[3] = {KERNEL_SCALAR_48, KERNEL_SCALAR_40, KERNEL_SCALAR};
-        for (int cand = -1; cand < 3 * N_SHAPES; ++cand) {
-            const int ck = cand < 0 ? KERNEL_TMA : kinds[cand / N_SHAPES];
-            const int cbx = cand < 0 ? 0 : SHAPES[cand % N_SHAPES][0];
-            const int cby = cand < 0 ? 1 : SHAPES[cand % N_SHAPES][1];
-            if (vplbm_set_launch(c, ck, cbx, cby) != VPLBM_OK) continue;
+        for (int cand = -1; cand <= 3 * N_SHAPES; ++cand) {
+            const bool two = cand == 3 * N_SHAPES;
+            const int ck = cand < 0 ? KERNEL_TMA : two ? KERNEL_FUSED2 : kinds[cand / N_SHAPES];
+            const int cbx = cand < 0 || two ? 0 : SHAPES[cand % N_SHAPES][0];
+            const int cby = cand < 0 ? 1 : two ? 0 : SHAPES[cand % N_SHAPES][1];
+            if (two) {   // single steps of the two-step choice: 256 x 1 blocks where allowed
+                if ((nstep0 & 1) || (vplbm_set_launch(c, KERNEL_FUSED2, 256, 1) != VPLBM_OK &&
+                                     vplbm_set_launch(c, KERNEL_FUSED2, 128, 2) != VPLBM_OK))
+                    continue;
+            } else if (vplbm_set_launch(c, ck, cbx, cby) != VPLBM_OK) {
+                continue;
+            }
             for (int rep = 0; rep < 2; ++rep) {   // first pass warms up
                 if (restore() != cudaSuccess) { st = fail(VPLBM_ECUDA, "autotune restore failed"); break; }
                 cudaEventRecord(e0, c->stream);
-                for (int s = 0; s < steps_per_trial && st == VPLBM_OK; ++s) {
+                if (two) {
+                    if (launch_lookahead(params_for(c, c->nstep), c->stream) != cudaSuccess)
+                        st = fail(VPLBM_ECUDA, "autotune launch failed");
+                    for (int L = 0; L < steps_per_trial / 2 && st == VPLBM_OK; ++L)
+                        if (launch_two(c, L, c->stream) != cudaSuccess) st = fail(VPLBM_ECUDA, "autotune launch failed");
+                    c->nstep += steps_per_trial;
+                }
+                for (int s = 0; !two && s < steps_per_trial && st == VPLBM_OK; ++s) {
                     if (launch_one(c, c->nstep, c->stream) != cudaSuccess)
                         st = fail(VPLBM_ECUDA, "autotune launch failed");
                     c->nstep++;

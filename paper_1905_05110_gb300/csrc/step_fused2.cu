@@ -1,0 +1,295 @@
+// The two-step kernel: time steps n and n + 1 of Algorithm 1 in one launch,
+// for a lattice whose body moves on a prescribed path (fixed or imposed) or
+// that has none, so that the pose of step n + 1 does not depend on the
+// force of step n.
+//
+// A block owns a FUSED2_W x FUSED2_H tile.  It first computes step n (pull,
+// chi, Eq. 22, collision) for the tile and a one-node ring around it, the
+// nodes the pulls of step n + 1 reach, and keeps the post-collision
+// populations in shared memory, rounded to the storage precision; then it
+// computes step n + 1 for the tile from there and stores it.  Each step
+// reads and writes HBM once per two steps instead of once per step, and the
+// launch boundary is paid once per two steps.  The node arithmetic is the
+// one-step kernel's (node_collide_to, body_chi, the same pull rules through
+// a shared-memory source), so the populations are those of two one-step
+// launches, bit for bit.
+//
+// Body blocks come first, as in the one-step kernel: they take the tiles
+// that meet the union of the node ranges of poses n and n + 1, reduce the
+// solid-node sums of both steps (float-float in FP32) and elect a tail for
+// each step (record only: the motion is prescribed).  The first body block
+// computes poses n + 2 and n + 3 for the next launch.
+#include "vplbm_node.cuh"
+
+namespace vplbm {
+namespace {
+
+constexpr int F2_TX = 64, F2_TY = 4;                      // threads per block (x, y)
+constexpr int F2_NT = F2_TX * F2_TY;                      // 256
+constexpr int F2_RW = FUSED2_W + 2, F2_RH = FUSED2_H + 2;  // first-step region: tile and its ring
+constexpr int F2_RN = F2_RW * F2_RH;                      // 1188 nodes
+constexpr int F2_ITER = (F2_RN + F2_NT - 1) / F2_NT;      // 5 region nodes per thread at most
+constexpr int F2_ROWS = FUSED2_H / F2_TY;                 // 4 tile nodes per thread
+static_assert(FUSED2_W == F2_TX && FUSED2_H % F2_TY == 0, "tile and block shapes");
+
+__device__ __forceinline__ float ld_stage(const float *s) { return *s; }
+__device__ __forceinline__ float ld_stage(const __half *s) { return __half2float(*s); }
+
+// Stage reader: lattice node (i, j) -> its slot in the region of the tile
+// at (bi0, bj0).  A node reached across a periodic edge sits at its
+// unwrapped position in the region (the first step computed it there).
+template <int P> struct StageSrc {
+    const typename Prec<P>::S *stage;
+    int bi0, bj0, nx, ny;
+    __device__ __forceinline__ typename Prec<P>::T operator()(int a, int i, int j) const
+    {
+        int li = i - bi0 + 1, lj = j - bj0 + 1;
+        if (li >= F2_RW) li -= nx;
+        else if (li < 0) li += nx;
+        if (lj >= F2_RH) lj -= ny;
+        else if (lj < 0) lj += ny;
+        return ld_stage(stage + a * F2_RN + lj * F2_RW + li);
+    }
+};
+
+// Poses n + 2 and n + 3 of a prescribed path from pose n + 1 (the same
+// operations as advance_prescribed, twice).
+__device__ __noinline__ void advance_two(const StepParams &pb, BodyState *next0, BodyState *next1)
+{
+    BodyState s = *pb.bs_in;
+    const double F0[3] = {0.0, 0.0, 0.0};
+    body_advance(pb.body, s.step, F0, s.q, s.v);
+    s.step += 1;
+    derive_pose(s, pb.body.present, pb.body.radius, pb.nx, pb.ny, pb.body.shape);
+    *next0 = s;
+    body_advance(pb.body, s.step, F0, s.q, s.v);
+    s.step += 1;
+    derive_pose(s, pb.body.present, pb.body.radius, pb.nx, pb.ny, pb.body.shape);
+    *next1 = s;
+}
+
+// Both steps of one tile.  sums: this block also reduces both steps'
+// solid-node sums into partial `slot` of `nparts` and may run the tails.
+template <int P, int COLL, int SHAPE>
+__device__ __forceinline__ void two_steps(const Fused2Params &q, typename Prec<P>::S *stage, int tx, int ty,
+                                          bool sums, int slot, int nparts, int4 ra, int4 rb, double (*red)[NPART],
+                                          int *s_last)
+{
+    using S = typename Prec<P>::S;
+    using T = typename Prec<P>::T;
+    using A = typename SumT<P>::A;
+    using V = typename SumT<P>::V;
+    const StepParams &pa = q.a;
+    const StepParams &pb = q.b;
+    const int nx = pa.nx, ny = pa.ny;
+    const int bi0 = tx * FUSED2_W, bj0 = ty * FUSED2_H;
+    const int tid = threadIdx.y * F2_TX + threadIdx.x;
+    // every region node is at least one node away from the lattice edges
+    const bool interior = bi0 >= 2 && bj0 >= 2 && bi0 + FUSED2_W + 2 <= nx && bj0 + FUSED2_H + 2 <= ny;
+    const S *__restrict__ fin = static_cast<const S *>(pa.fin);
+    const BodyState *__restrict__ bsa = pa.bs_in;
+    const BodyState *__restrict__ bsb = pb.bs_in;
+
+    // ---- step n on the region, into the stage ----
+    const bool near_a =
+        ra.x <= ra.y && (!interior || tile_near_body(ra, bi0 - 1, bj0 - 1, F2_RW, F2_RH, false));
+    A part[NPART - 1];
+#pragma unroll
+    for (int k = 0; k < NPART - 1; ++k) acc_zero(part[k]);
+    bool any_chi = false;
+    for (int it = 0; it < F2_ITER; ++it) {
+        const int k = it * F2_NT + tid;
+        if (k >= F2_RN) break;
+        const int lj = k / F2_RW, li = k - lj * F2_RW;
+        const int ui = bi0 - 1 + li, uj = bj0 - 1 + lj;   // unwrapped lattice position
+        int i = ui, j = uj;
+        if (!interior) {
+            if (i < 0 || i >= nx) {   // beyond a wall, or across a periodic edge
+                if (pa.bc[VPLBM_WEST] != VPLBM_BC_PERIODIC) continue;
+                i = ((i % nx) + nx) % nx;
+            }
+            if (j < 0 || j >= ny) {
+                if (pa.bc[VPLBM_SOUTH] != VPLBM_BC_PERIODIC) continue;
+                j = ((j % ny) + ny) % ny;
+            }
+        }
+        T f[NQ];
+        if (interior) pull_all<P, true>(pa, fin, i, j, f);
+        else pull_all<P>(pa, fin, i, j, f);
+        T dxl = 0, dyl = 0;
+        bool chi = false;
+        if (near_a && i >= ra.x && i <= ra.y && j >= ra.z && j <= ra.w)
+            chi = body_chi<P, SHAPE>(pa.body, pa.r2f, bsa, i, j, dxl, dyl);
+        T cr = 0, cax = 0, cay = 0;
+        S *dst = stage + k;
+        chi = node_collide_to<P, COLL>(pa, bsa, chi, dxl, dyl, f, [&](int a, T v) { stv(dst + a * F2_RN, v); }, cr,
+                                       cax, cay);
+        // the tile's own nodes (not the ring, not a wrapped copy) enter the sums
+        if (sums && chi && li >= 1 && li <= FUSED2_W && lj >= 1 && lj <= FUSED2_H && ui < nx && uj < ny) {
+            V one[NPART - 1];
+            solid_node_terms<P>(pa, fin, i, j, (V)cr, (V)cax, (V)cay, one);
+#pragma unroll
+            for (int m = 0; m < NPART - 1; ++m) acc_add(part[m], one[m]);
+            any_chi = true;
+        }
+    }
+    if (sums) {
+        block_reduce<A>(any_chi, part, red);
+        publish_slot<A>(pa, slot, nparts, reinterpret_cast<A *>(red[0]), s_last);
+    }
+    __syncthreads();   // the stage is complete
+
+    // ---- step n + 1 on the tile, from the stage ----
+    const bool near_b = rb.x <= rb.y && tile_near_body(rb, bi0, bj0, FUSED2_W, FUSED2_H, false);
+    const StageSrc<P> src{stage, bi0, bj0, nx, ny};
+#pragma unroll
+    for (int k = 0; k < NPART - 1; ++k) acc_zero(part[k]);
+    any_chi = false;
+    for (int r = 0; r < F2_ROWS; ++r) {
+        const int lx = threadIdx.x, ly = threadIdx.y + r * F2_TY;
+        const int i = bi0 + lx, j = bj0 + ly;
+        if (i >= nx || j >= ny) continue;
+        const int k0 = (ly + 1) * F2_RW + lx + 1;
+        const bool plain = interior || (i > 0 && i < nx - 1 && j > 0 && j < ny - 1);
+        T f[NQ];
+        if (plain) {
+#pragma unroll
+            for (int a = 0; a < NQ; ++a) f[a] = ld_stage(stage + a * F2_RN + k0 - cy_of(a) * F2_RW - cx_of(a));
+        } else {
+#pragma unroll
+            for (int a = 0; a < NQ; ++a) f[a] = pull_edge_src<P>(pb, src, a, i, j);
+        }
+        T dxl = 0, dyl = 0;
+        bool chi = false;
+        if (near_b) chi = body_chi<P, SHAPE>(pb.body, pb.r2f, bsb, i, j, dxl, dyl);
+        T cr = 0, cax = 0, cay = 0;
+        chi = node_collide<P, COLL>(pb, bsb, chi, dxl, dyl, i, j, f, nullptr, cr, cax, cay);
+        if (sums && chi) {
+            T g[NQ];   // pulled again: not kept live across the stores
+            if (plain) {
+#pragma unroll
+                for (int a = 0; a < NQ; ++a) g[a] = ld_stage(stage + a * F2_RN + k0 - cy_of(a) * F2_RW - cx_of(a));
+            } else {
+#pragma unroll
+                for (int a = 0; a < NQ; ++a) g[a] = pull_edge_src<P>(pb, src, a, i, j);
+            }
+            V one[NPART - 1];
+            solid_terms_from<P>(bsb, g, [&](int a) { return ld_stage(stage + a * F2_RN + k0); }, i, j, (V)cr,
+                                (V)cax, (V)cay, one);
+#pragma unroll
+            for (int m = 0; m < NPART - 1; ++m) acc_add(part[m], one[m]);
+            any_chi = true;
+        }
+    }
+    if (sums) {
+        block_reduce<A>(any_chi, part, red);
+        publish_slot<A>(pb, slot, nparts, reinterpret_cast<A *>(red[0]), s_last);
+    }
+}
+
+// Grid: (tile columns) x (body-block rows + tile rows), programmatic
+// dependent launch as in the one-step kernel.
+template <int P, int COLL, int SHAPE>
+__global__ void __launch_bounds__(F2_NT, 4) vp_mrt_step2(const Fused2Params q)
+{
+    using S = typename Prec<P>::S;
+    extern __shared__ __align__(16) unsigned char f2_smem[];
+    S *stage = reinterpret_cast<S *>(f2_smem);   // [NQ][F2_RN]
+    __shared__ double red[8][NPART];
+    __shared__ int s_last;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int tid = threadIdx.y * F2_TX + threadIdx.x;
+    const int nbr = q.a.nbody_rows;
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    const int4 ra = __ldg(reinterpret_cast<const int4 *>(&q.a.bs_in->ilo));
+    const int4 rb = __ldg(reinterpret_cast<const int4 *>(&q.b.bs_in->ilo));
+    int tx = -1, ty = 0, slot = 0, nparts = 1;
+    bool sums = false;
+    if ((int)blockIdx.y < nbr) {
+        if (b >= q.a.nbody) return;
+        // union of the two solid-node ranges (ilo > ihi: empty)
+        int4 u = ra;
+        if (rb.x <= rb.y) {
+            if (u.x <= u.y)
+                u = make_int4(min(u.x, rb.x), max(u.y, rb.y), min(u.z, rb.z), max(u.w, rb.w));
+            else
+                u = rb;
+        }
+        int tx0 = 0, ty0 = 0, rw = 1, nrect = 1;   // no solid node: tile (0, 0) runs the tails
+        if (u.x <= u.y) {
+            tx0 = u.x / FUSED2_W;
+            ty0 = u.z / FUSED2_H;
+            rw = u.y / FUSED2_W - tx0 + 1;
+            nrect = rw * (u.w / FUSED2_H - ty0 + 1);
+        }
+        if (b < nrect) {
+            tx = tx0 + b % rw;
+            ty = ty0 + b / rw;
+            sums = true;
+            slot = b;
+            nparts = nrect;
+        }
+        if (b == 0 && nrect > q.a.nbody && tid == 0) *q.a.err |= ERR_INTERNAL;
+    } else {
+        tx = blockIdx.x;
+        ty = blockIdx.y - nbr;
+    }
+    if (tx >= 0) two_steps<P, COLL, SHAPE>(q, stage, tx, ty, sums, slot, nparts, ra, rb, red, &s_last);
+    if (b == 0 && tid == 0) advance_two(q.b, q.next0, q.next1);
+}
+
+__global__ void lookahead_kernel(const StepParams p)
+{
+    if (threadIdx.x == 0) advance_prescribed(p);
+}
+
+template <int P>
+cudaError_t launch_p(const Fused2Params &q0, cudaStream_t stream)
+{
+    Fused2Params q = q0;
+    const int nx = q.a.nx, ny = q.a.ny;
+    const int ntx = (nx + FUSED2_W - 1) / FUSED2_W, nty = (ny + FUSED2_H - 1) / FUSED2_H;
+    // the union of two node ranges one step apart: one node more of radius
+    const long long nbody = max_reduction_blocks(nx, ny, q.a.body.radius + 1.0, q.a.body.present, FUSED2_W, FUSED2_H);
+    q.a.nbody = (int)nbody;
+    q.a.nbody_rows = (int)((nbody + ntx - 1) / ntx);
+    const size_t smem = (size_t)NQ * F2_RN * sizeof(typename Prec<P>::S);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ntx, nty + q.a.nbody_rows);
+    cfg.blockDim = dim3(F2_TX, F2_TY);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const bool bgk = q.a.collision == VPLBM_COLLISION_BGK;
+    const bool disk = !q.a.body.present || q.a.body.shape == VPLBM_SHAPE_DISK;
+    if (bgk)
+        return disk ? cudaLaunchKernelEx(&cfg, vp_mrt_step2<P, VPLBM_COLLISION_BGK, VPLBM_SHAPE_DISK>, q)
+                    : cudaLaunchKernelEx(&cfg, vp_mrt_step2<P, VPLBM_COLLISION_BGK, SHAPE_ANY>, q);
+    return disk ? cudaLaunchKernelEx(&cfg, vp_mrt_step2<P, VPLBM_COLLISION_MRT, VPLBM_SHAPE_DISK>, q)
+                : cudaLaunchKernelEx(&cfg, vp_mrt_step2<P, VPLBM_COLLISION_MRT, SHAPE_ANY>, q);
+}
+
+}  // namespace
+
+cudaError_t launch_step_fused2(int precision, const Fused2Params &q, cudaStream_t stream)
+{
+    if (q.a.body.present && q.a.body.motion == VPLBM_MOTION_FREE) return cudaErrorInvalidValue;
+    switch (precision) {
+    case VPLBM_F32_DEV: return launch_p<VPLBM_F32_DEV>(q, stream);
+    case VPLBM_F16_DEV: return launch_p<VPLBM_F16_DEV>(q, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_lookahead(const StepParams &p, cudaStream_t stream)
+{
+    lookahead_kernel<<<1, 32, 0, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace vplbm

@@ -222,8 +222,28 @@ inline double bounding_radius(const vplbm_body_desc *b)
 }
 
 // Step kernels a context can launch: the scalar kernel with the register
-// budget of 4 / 5 / 6 blocks of 256 threads per SM, and the TMA-staged one.
-enum { KERNEL_SCALAR = 0, KERNEL_SCALAR_48 = 1, KERNEL_SCALAR_40 = 2, KERNEL_TMA = 3 };
+// budget of 4 / 5 / 6 blocks of 256 threads per SM, the TMA-staged one, and
+// the two-step kernel (two time steps per launch).
+enum { KERNEL_SCALAR = 0, KERNEL_SCALAR_48 = 1, KERNEL_SCALAR_40 = 2, KERNEL_TMA = 3, KERNEL_FUSED2 = 4 };
+
+// Two-step kernel (step_fused2.cu): a block computes time step n on its
+// tile and a one-node ring around it into shared memory, then step n + 1 on
+// the tile from there.  Tile of the second step: FUSED2_W x FUSED2_H nodes.
+constexpr int FUSED2_W = 64, FUSED2_H = 16;
+struct Fused2Params {
+    StepParams a;      // step n: fin, src planes, pose n (bs_in), partials region 0, ticket 0
+    StepParams b;      // step n + 1: dst planes, pose n + 1 (bs_in), partials region 1, ticket 1
+    BodyState *next0;  // receives pose n + 2 (prescribed motion)
+    BodyState *next1;  // receives pose n + 3
+};
+// Steps n and n + 1 (asynchronous on `stream`); bodies on a prescribed path
+// only, FP32 / FP16 storage, no convective outlet.  max_parts of both views
+// must cover the union of the node ranges of poses n and n + 1 in
+// FUSED2_W x FUSED2_H tiles.
+cudaError_t launch_step_fused2(int precision, const Fused2Params &q, cudaStream_t stream);
+// Pose n + 1 := the prescribed motion applied to pose n (one thread;
+// p.bs_in -> p.bs_out), so that a run of two-step launches can start at n.
+cudaError_t launch_lookahead(const StepParams &p, cudaStream_t stream);
 
 // Batched launch of the scalar step over many lattices.
 struct BatchLaunch {

@@ -88,13 +88,25 @@ __device__ __forceinline__ float wall_term<float>(const StepParams &p, int a, in
     return ((float)(6.0 * w_of(a)) * p.rho0f) * cu;
 }
 
+// Source of a pull: population a of the previous post-collision field at
+// lattice node (i, j) (inside the lattice).  GlobalSrc reads the population
+// buffer; the two-step kernel reads its shared-memory stage instead.
+template <int P> struct GlobalSrc {
+    const typename Prec<P>::S *fin;
+    long long ps;
+    int nx;
+    __device__ __forceinline__ typename Prec<P>::T operator()(int a, int i, int j) const
+    {
+        return ldv(fin + a * ps + (long long)j * nx + i);
+    }
+};
+
 // Pull of population a into edge node (i, j), with the boundary rules.
-template <int P>
-__device__ typename Prec<P>::T pull_edge(const StepParams &p, const typename Prec<P>::S *fin, int a, int i, int j)
+template <int P, class Src>
+__device__ __forceinline__ typename Prec<P>::T pull_edge_src(const StepParams &p, const Src &src, int a, int i, int j)
 {
     using T = typename Prec<P>::T;
     const int nx = p.nx, ny = p.ny;
-    const long long ps = p.ps;
     int si = i - cx_of(a);
     int sj = j - cy_of(a);
     if (sj < 0 || sj >= ny) {
@@ -105,9 +117,9 @@ __device__ typename Prec<P>::T pull_edge(const StepParams &p, const typename Pre
         } else if (kind == VPLBM_BC_SYMMETRY) {   // specular reflection at the half-way wall
             int mi = i - cx_of(a);
             if (mi < 0 || mi >= nx) mi = p.bc[VPLBM_WEST] == VPLBM_BC_PERIODIC ? (mi < 0 ? mi + nx : mi - nx) : i;
-            return ldv(fin + miry_of(a) * ps + (long long)j * nx + mi);
+            return src(miry_of(a), mi, j);
         } else {
-            T val = ldv(fin + opp_of(a) * ps + (long long)j * nx + i);
+            T val = src(opp_of(a), i, j);
             if (kind == VPLBM_BC_VELOCITY) val += wall_term<T>(p, a, side, i);
             return val;
         }
@@ -118,18 +130,24 @@ __device__ typename Prec<P>::T pull_edge(const StepParams &p, const typename Pre
         if (kind == VPLBM_BC_PERIODIC) {
             si = si < 0 ? si + nx : si - nx;
         } else if (kind == VPLBM_BC_ZEROGRAD) {
-            return ldv(fin + a * ps + (long long)sj * nx + i);
+            return src(a, i, sj);
         } else if (kind == VPLBM_BC_CONVECTIVE) {   // east only (checked on the host)
-            const T z = ldv(fin + a * ps + (long long)sj * nx + i);
+            const T z = src(a, i, sj);
             const T prev = static_cast<const T *>(p.conv_in)[outlet_slot(a) * ny + j];
             return par<T>(p.conv_k1, p.conv_k1f) * prev + par<T>(p.conv_k2, p.conv_k2f) * z;
         } else {
-            T val = ldv(fin + opp_of(a) * ps + (long long)j * nx + i);
+            T val = src(opp_of(a), i, j);
             if (kind == VPLBM_BC_VELOCITY) val += wall_term<T>(p, a, side, j);
             return val;
         }
     }
-    return ldv(fin + a * ps + (long long)sj * nx + si);
+    return src(a, si, sj);
+}
+
+template <int P>
+__device__ typename Prec<P>::T pull_edge(const StepParams &p, const typename Prec<P>::S *fin, int a, int i, int j)
+{
+    return pull_edge_src<P>(p, GlobalSrc<P>{fin, p.ps, p.nx}, a, i, j);
 }
 
 // Pull-stream all 9 populations of node (i, j); INTERIOR: the caller knows
@@ -364,17 +382,14 @@ __device__ __noinline__ void step_tail(const StepParams &p, int nparts)
 // momentum exchanged through its links during the streaming into this step
 // (force, torque), and the node count.  The pulled populations are loaded
 // again (cache hits) so that they are not live across the stores.
-template <int P>
-__device__ __forceinline__ void solid_node_terms(const StepParams &p, const typename Prec<P>::S *fin, int i, int j,
-                                                 typename SumT<P>::V rho, typename SumT<P>::V ax,
+// f: the node's pulled populations; own(a): its own previous post-collision
+// population a.
+template <int P, class Own>
+__device__ __forceinline__ void solid_terms_from(const BodyState *bs, const typename Prec<P>::T f[NQ], const Own &own,
+                                                 int i, int j, typename SumT<P>::V rho, typename SumT<P>::V ax,
                                                  typename SumT<P>::V ay, typename SumT<P>::V out[NPART - 1])
 {
-    using T = typename Prec<P>::T;
     using V = typename SumT<P>::V;
-    const BodyState *bs = p.bs_in;
-    T f[NQ];
-    pull_all<P>(p, fin, i, j, f);
-    const long long b = (long long)j * p.nx + i;
     V dx, dy;
     if constexpr (P == VPLBM_F64) {
         dx = (double)i - bs->q[0];
@@ -389,7 +404,7 @@ __device__ __forceinline__ void solid_node_terms(const StepParams &p, const type
     V ex = 0, ey = 0;
 #pragma unroll
     for (int a = 1; a < NQ; ++a) {
-        const V d = (V)f[a] - (V)ldv(fin + a * p.ps + b);   // pulled minus own
+        const V d = (V)f[a] - (V)own(a);   // pulled minus own
         ex += cx_of(a) * d;
         ey += cy_of(a) * d;
     }
@@ -400,6 +415,18 @@ __device__ __forceinline__ void solid_node_terms(const StepParams &p, const type
     out[4] = ey;
     out[5] = dx * ey - dy * ex;
     out[6] = 1;
+}
+
+template <int P>
+__device__ __forceinline__ void solid_node_terms(const StepParams &p, const typename Prec<P>::S *fin, int i, int j,
+                                                 typename SumT<P>::V rho, typename SumT<P>::V ax,
+                                                 typename SumT<P>::V ay, typename SumT<P>::V out[NPART - 1])
+{
+    using T = typename Prec<P>::T;
+    T f[NQ];
+    pull_all<P>(p, fin, i, j, f);
+    const long long b = (long long)j * p.nx + i;
+    solid_terms_from<P>(p.bs_in, f, [&](int a) { return ldv(fin + a * p.ps + b); }, i, j, rho, ax, ay, out);
 }
 
 
@@ -469,12 +496,12 @@ __device__ __forceinline__ bool body_chi(const DevBody &body, float r2f, const B
 // state bs, penalized velocity (Eq. 22), collision with forcing (Eq. 17)
 // and the store of f~.  Returns chi and keeps rho, a for the solid-node
 // sums.
-template <int P, int COLL>
-__device__ __forceinline__ bool node_collide(const StepParams &p, const BodyState *__restrict__ bs, bool chi,
-                                             typename Prec<P>::T dxl, typename Prec<P>::T dyl, int i, int j,
-                                             const typename Prec<P>::T f[NQ], typename Prec<P>::S *__restrict__ fout,
-                                             typename Prec<P>::T &cr, typename Prec<P>::T &cax,
-                                             typename Prec<P>::T &cay)
+template <int P, int COLL, class Store>
+__device__ __forceinline__ bool node_collide_to(const StepParams &p, const BodyState *__restrict__ bs, bool chi,
+                                                typename Prec<P>::T dxl, typename Prec<P>::T dyl,
+                                                const typename Prec<P>::T f[NQ], const Store &store,
+                                                typename Prec<P>::T &cr, typename Prec<P>::T &cax,
+                                                typename Prec<P>::T &cay)
 {
     using T = typename Prec<P>::T;
     constexpr bool DEV = Prec<P>::DEV;
@@ -509,9 +536,6 @@ __device__ __forceinline__ bool node_collide(const StepParams &p, const BodyStat
     const T uy = vy + (T)0.5 * ay;
     const T Gx = rho * (gx + ax);
     const T Gy = rho * (gy + ay);
-    using S = typename Prec<P>::S;
-    S *const *dp = reinterpret_cast<S *const *>(p.dst_plane);
-    const int b = j * p.nx + i;
 
     if constexpr (COLL == VPLBM_COLLISION_BGK) {
         // Sec. 2.1: f~ = (1 - omega) f + omega f_eq + (1 - omega/2) F with
@@ -532,15 +556,14 @@ __device__ __forceinline__ bool node_collide(const StepParams &p, const BodyStat
         auto pair = [&](int a, int ao, T cu, T cG, T w) {
             const T we = w * fma(cu, fma(orho45, cu, k9 * cG), c0);
             const T wo = w * fma(orho3, cu, k3 * cG);
-            stv(dp[a] + b, fma(om1, f[a], we + wo));
-            stv(dp[ao] + b, fma(om1, f[ao], we - wo));
+            store(a, fma(om1, f[a], we + wo));
+            store(ao, fma(om1, f[ao], we - wo));
         };
-        stv(dp[0] + b, fma(om1, f[0], (T)(4.0 / 9.0) * c0));
+        store(0, fma(om1, f[0], (T)(4.0 / 9.0) * c0));
         pair(1, 3, ux, Gx, (T)(1.0 / 9.0));
         pair(2, 4, uy, Gy, (T)(1.0 / 9.0));
         pair(5, 7, ux + uy, Gx + Gy, (T)(1.0 / 36.0));
         pair(6, 8, uy - ux, Gy - Gx, (T)(1.0 / 36.0));
-        (void)fout;
         if (!(rho > (T)0) || !(rho < (T)1e30)) *p.err = ERR_NONFINITE;
         cr = rho; cax = ax; cay = ay;
         return chi;
@@ -579,20 +602,35 @@ __device__ __forceinline__ bool node_collide(const StepParams &p, const BodyStat
     const T Pq = pxx_s * (T)0.25;
     const T Rq = pxy_s * (T)0.25;
 
-    stv(dp[0] + b, r9 - e_s * (T)(1.0 / 9.0) + ep_s * (T)(1.0 / 9.0));
-    stv(dp[1] + b, A + X1 + Pq);
-    stv(dp[2] + b, A + Y1 - Pq);
-    stv(dp[3] + b, A - X1 + Pq);
-    stv(dp[4] + b, A - Y1 - Pq);
-    stv(dp[5] + b, B + X2 + Y2 + Rq);
-    stv(dp[6] + b, B - X2 + Y2 - Rq);
-    stv(dp[7] + b, B - X2 - Y2 + Rq);
-    stv(dp[8] + b, B + X2 - Y2 - Rq);
-    (void)fout;
+    store(0, r9 - e_s * (T)(1.0 / 9.0) + ep_s * (T)(1.0 / 9.0));
+    store(1, A + X1 + Pq);
+    store(2, A + Y1 - Pq);
+    store(3, A - X1 + Pq);
+    store(4, A - Y1 - Pq);
+    store(5, B + X2 + Y2 + Rq);
+    store(6, B - X2 + Y2 - Rq);
+    store(7, B - X2 - Y2 + Rq);
+    store(8, B + X2 - Y2 - Rq);
 
     if (!(rho > (T)0) || !(rho < (T)1e30)) *p.err = ERR_NONFINITE;
     cr = rho; cax = ax; cay = ay;
     return chi;
+}
+
+// node_collide_to storing f~ into the step's destination buffer.
+template <int P, int COLL>
+__device__ __forceinline__ bool node_collide(const StepParams &p, const BodyState *__restrict__ bs, bool chi,
+                                             typename Prec<P>::T dxl, typename Prec<P>::T dyl, int i, int j,
+                                             const typename Prec<P>::T f[NQ], typename Prec<P>::S *__restrict__ fout,
+                                             typename Prec<P>::T &cr, typename Prec<P>::T &cax,
+                                             typename Prec<P>::T &cay)
+{
+    using S = typename Prec<P>::S;
+    using T = typename Prec<P>::T;
+    S *const *dp = reinterpret_cast<S *const *>(p.dst_plane);
+    const int b = j * p.nx + i;
+    (void)fout;
+    return node_collide_to<P, COLL>(p, bs, chi, dxl, dyl, f, [&](int a, T v) { stv(dp[a] + b, v); }, cr, cax, cay);
 }
 
 // The update of one interior-or-edge node of a lattice with one body: chi
@@ -623,25 +661,17 @@ __device__ __forceinline__ bool tile_near_body(const int4 range, int i0, int j0,
 // tail in the last tile to publish.  sums (shared memory) holds the tile's
 // 7 sums in accumulator type A; every thread of the block calls it (it
 // contains block barriers).
+// publish_slot: the same with the slot and the number of partials given.
 template <typename A>
-__device__ __forceinline__ void publish_tile(const StepParams &p, const int4 range, int tx, int ty, int w, int h,
-                                             const A *sums, int *s_last)
+__device__ __forceinline__ void publish_slot(const StepParams &p, int slot, int nparts, const A *sums, int *s_last)
 {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;
-    if (range.x <= range.y) {
-        tx0 = range.x / w; tx1 = range.y / w;
-        ty0 = range.z / h; ty1 = range.w / h;
-    }
-    const int ntx = tx1 - tx0 + 1;
-    const int nparts = ntx * (ty1 - ty0 + 1);
     if (nparts > p.max_parts) {          // cannot happen for a finite pose; never overrun
         if (tid == 0) *p.err |= ERR_INTERNAL;
         __syncthreads();
         return;
     }
     if (tid == 0) {
-        const int slot = (ty - ty0) * ntx + (tx - tx0);
         A *dst = reinterpret_cast<A *>(p.partials + (size_t)slot * NPART);
 #pragma unroll
         for (int k = 0; k < NPART - 1; ++k) __stcg(dst + k, sums[k]);
@@ -657,13 +687,26 @@ __device__ __forceinline__ void publish_tile(const StepParams &p, const int4 ran
     __syncthreads();   // the shared scratch and s_last are reused by the next tile
 }
 
+template <typename A>
+__device__ __forceinline__ void publish_tile(const StepParams &p, const int4 range, int tx, int ty, int w, int h,
+                                             const A *sums, int *s_last)
+{
+    int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;
+    if (range.x <= range.y) {
+        tx0 = range.x / w; tx1 = range.y / w;
+        ty0 = range.z / h; ty1 = range.w / h;
+    }
+    const int ntx = tx1 - tx0 + 1;
+    const int nparts = ntx * (ty1 - ty0 + 1);
+    publish_slot<A>(p, (ty - ty0) * ntx + (tx - tx0), nparts, sums, s_last);
+}
+
 // Block-wide fixed-order reduction of per-thread accumulators (type A:
 // double, or float2 float-float), then publish_tile.  Used where a thread
 // has accumulated several nodes (TMA-staged kernel).
+// block_reduce leaves the block's sums in red_mem[0] (type A).
 template <typename A>
-__device__ __forceinline__ void tile_reduce(const StepParams &p, const int4 range, int tx, int ty, int w, int h,
-                                            bool any_chi_thread, A part[NPART - 1], double (*red_mem)[NPART],
-                                            int *s_last)
+__device__ __forceinline__ void block_reduce(bool any_chi_thread, A part[NPART - 1], double (*red_mem)[NPART])
 {
     static_assert(sizeof(A) == sizeof(double), "the shared scratch holds one A per entry");
     A (*red)[NPART] = reinterpret_cast<A (*)[NPART]>(red_mem);
@@ -698,7 +741,15 @@ __device__ __forceinline__ void tile_reduce(const StepParams &p, const int4 rang
             for (int k = 0; k < NPART - 1; ++k) red[0][k] = v[k];
     }
     __syncthreads();
-    publish_tile<A>(p, range, tx, ty, w, h, red[0], s_last);
+}
+
+template <typename A>
+__device__ __forceinline__ void tile_reduce(const StepParams &p, const int4 range, int tx, int ty, int w, int h,
+                                            bool any_chi_thread, A part[NPART - 1], double (*red_mem)[NPART],
+                                            int *s_last)
+{
+    block_reduce<A>(any_chi_thread, part, red_mem);
+    publish_tile<A>(p, range, tx, ty, w, h, reinterpret_cast<A *>(red_mem[0]), s_last);
 }
 
 // Solid-node sums of a tile where every thread owns one node: the terms go
