@@ -276,7 +276,7 @@ vplbm_status vplbm_get_body_k(vplbm_ctx *ctx, int k, double q[3], double v[3], l
  *  VPLBM_KERNEL_FUSED2     two time steps per launch (FP32/FP16 storage,
  *                          a body on a prescribed path or none, no
  *                          convective outlet, one body): a block computes
- *                          step n on its 64 x 16 tile and a one-node ring
+ *                          step n on its 64 x 8 tile and a one-node ring
  *                          around it into shared memory, then step n + 1
  *                          from there, so HBM is read and written once per
  *                          two steps.  Runs of 32 steps from an even step

@@ -27,9 +27,9 @@ namespace {
 constexpr int F2_TX = 64, F2_TY = 4;                      // threads per block (x, y)
 constexpr int F2_NT = F2_TX * F2_TY;                      // 256
 constexpr int F2_RW = FUSED2_W + 2, F2_RH = FUSED2_H + 2;  // first-step region: tile and its ring
-constexpr int F2_RN = F2_RW * F2_RH;                      // 1188 nodes
-constexpr int F2_ITER = (F2_RN + F2_NT - 1) / F2_NT;      // 5 region nodes per thread at most
-constexpr int F2_ROWS = FUSED2_H / F2_TY;                 // 4 tile nodes per thread
+constexpr int F2_RN = F2_RW * F2_RH;                      // 660 nodes
+constexpr int F2_ITER = (F2_RN + F2_NT - 1) / F2_NT;      // 3 region nodes per thread at most
+constexpr int F2_ROWS = FUSED2_H / F2_TY;                 // 2 tile nodes per thread
 static_assert(FUSED2_W == F2_TX && FUSED2_H % F2_TY == 0, "tile and block shapes");
 
 __device__ __forceinline__ float ld_stage(const float *s) { return *s; }
@@ -190,7 +190,7 @@ __device__ __forceinline__ void two_steps(const Fused2Params &q, typename Prec<P
 // Grid: (tile columns) x (body-block rows + tile rows), programmatic
 // dependent launch as in the one-step kernel.
 template <int P, int COLL, int SHAPE>
-__global__ void __launch_bounds__(F2_NT, 4) vp_mrt_step2(const Fused2Params q)
+__global__ void __launch_bounds__(F2_NT, 5) vp_mrt_step2(const Fused2Params q)
 {
     using S = typename Prec<P>::S;
     extern __shared__ __align__(16) unsigned char f2_smem[];

@@ -229,7 +229,7 @@ enum { KERNEL_SCALAR = 0, KERNEL_SCALAR_48 = 1, KERNEL_SCALAR_40 = 2, KERNEL_TMA
 // Two-step kernel (step_fused2.cu): a block computes time step n on its
 // tile and a one-node ring around it into shared memory, then step n + 1 on
 // the tile from there.  Tile of the second step: FUSED2_W x FUSED2_H nodes.
-constexpr int FUSED2_W = 64, FUSED2_H = 16;
+constexpr int FUSED2_W = 64, FUSED2_H = 8;
 struct Fused2Params {
     StepParams a;      // step n: fin, src planes, pose n (bs_in), partials region 0, ticket 0
     StepParams b;      // step n + 1: dst planes, pose n + 1 (bs_in), partials region 1, ticket 1
