@@ -24,12 +24,12 @@
 namespace vplbm {
 namespace {
 
-constexpr int F2_TX = 64, F2_TY = 4;                      // threads per block (x, y)
+constexpr int F2_TX = FUSED2_W, F2_TY = 256 / FUSED2_W;    // threads per block (x, y): 256
 constexpr int F2_NT = F2_TX * F2_TY;                      // 256
 constexpr int F2_RW = FUSED2_W + 2, F2_RH = FUSED2_H + 2;  // first-step region: tile and its ring
-constexpr int F2_RN = F2_RW * F2_RH;                      // 660 nodes
-constexpr int F2_ITER = (F2_RN + F2_NT - 1) / F2_NT;      // 3 region nodes per thread at most
-constexpr int F2_ROWS = FUSED2_H / F2_TY;                 // 2 tile nodes per thread
+constexpr int F2_RN = F2_RW * F2_RH;                      // 660 nodes (64 x 8 tiles)
+constexpr int F2_ITER = (F2_RN + F2_NT - 1) / F2_NT;      // region nodes per thread at most
+constexpr int F2_ROWS = FUSED2_H / F2_TY;                 // tile nodes per thread
 static_assert(FUSED2_W == F2_TX && FUSED2_H % F2_TY == 0, "tile and block shapes");
 
 __device__ __forceinline__ float ld_stage(const float *s) { return *s; }
