@@ -334,6 +334,8 @@ def run_ours(args, rank, world, local_rank):
             s2.close()
         if "f64" in compare:
             compare["speedup_vs_f64"] = (nodes * args.steps / dt / 1e6) / compare["f64"]["mlups"]
+        if not args.legs or "f64" in args.legs.split(","):
+            compare["accuracy_vs_f64"] = run_accuracy(p, 4000, torch, stream, not args.no_autotune)
 
     legs = set(args.legs.split(",")) if args.legs else set(LEGS)
     if not args.no_compare and world > 1 and "batched" in legs:
@@ -368,6 +370,42 @@ def run_ours(args, rank, world, local_rank):
                 "gpu_launches": launches, "clocks": clock, "compare": compare}
         print(json.dumps(line), flush=True)
     sim.close()
+
+
+def run_accuracy(p, steps, torch, stream, autotune):
+    """FP32 and FP16 deviation storage against FP64 storage on the same
+    workload, GPU against GPU from the same initial state: C_D and C_L over
+    the run, and the fields at its end."""
+    import paper_1905_05110_gb300 as vp
+    u0 = max(abs(p["init"]["u"][0]), abs(p["init"]["u"][1]), 1e-12)
+    runs = {}
+    for prec in ("f64", "f32", "f16"):
+        sim = vp.Simulation(p, precision=prec, history_capacity=steps + 8, stream=stream)
+        sim.init_from_problem()
+        if autotune and prec != "f64":
+            sim.autotune(8)
+        sim.step(steps)
+        sim.sync()
+        runs[prec] = (sim.history(0, steps), sim.fields(), list(sim.launch()))
+        sim.close()
+    h64, (r64, ux64, uy64), _ = runs["f64"]
+    half = steps // 2
+    out = {"steps": steps, "workload": p["name"]}
+    for prec in ("f32", "f16"):
+        h, (r, ux, uy), launch = runs[prec]
+        cd, cl = h[:, 4], h[:, 5]
+        out[prec] = {
+            "launch": launch,
+            "max_abs_dcd": float(np.max(np.abs(cd - h64[:, 4]))),
+            "max_abs_dcl": float(np.max(np.abs(cl - h64[:, 5]))),
+            "mean_cd_2nd_half": float(cd[half:].mean()),
+            "mean_cd_2nd_half_f64": float(h64[half:, 4].mean()),
+            "rms_cl_2nd_half": float(np.sqrt((cl[half:] ** 2).mean())),
+            "rms_cl_2nd_half_f64": float(np.sqrt((h64[half:, 5] ** 2).mean())),
+            "max_abs_du_over_u0": float(max(np.max(np.abs(ux - ux64)), np.max(np.abs(uy - uy64))) / u0),
+            "max_abs_drho": float(np.max(np.abs(r - r64))),
+        }
+    return out
 
 
 def run_other_workload(name, steps, torch, stream):
