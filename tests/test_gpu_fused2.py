@@ -67,7 +67,26 @@ def _bgk_channel():
     return p
 
 
+def _tiny_walls():
+    # smaller than one tile in both directions, walls on every side
+    p = wl.mixed_bc_box(7, 5, seed=12, west="velocity", east="zerograd", south="noslip", north="velocity", tau=0.7)
+    p["init"] = {"rho": 1.0, "u": (0.02, 0.0)}
+    return p
+
+
+def _periodic_x_symmetry_y():
+    # the mirror rule's corner nodes wrap across the periodic x edges
+    p = wl.mixed_bc_box(90, 40, seed=13, west="periodic", east="periodic", south="symmetry", north="symmetry",
+                        tau=0.65, body={"radius": 6.5, "x": 44.3, "y": 19.6, "motion": "imposed", "axis": 1,
+                                        "amp": 2.0, "freq": 0.015})
+    p["g_fluid"] = (2e-5, 0.0)
+    p["f0"] = wl.random_populations(90, 40, seed=14, amp=0.02, u_amp=0.03)
+    return p
+
+
 CASES = {
+    "tiny_walls": _tiny_walls,
+    "periodic_x_symmetry_y": _periodic_x_symmetry_y,
     "channel_imposed": _channel_imposed,
     "fixed_ellipse": _fixed_ellipse,
     "pitching_rectangle_symmetry": _pitching_rectangle_symmetry,
