@@ -196,3 +196,24 @@ def test_two_step_kernel_refusals():
             sim.set_launch("fused2", 128, 1)
         assert ei.value.status == 6
         sim.close()
+
+
+def test_full_size_headline_two_step_kernel_equals_one_step_kernel():
+    # The oscillating disk at its full 2048 x 1024 size, in the launch
+    # configuration the benchmark times (two-step launches in 32-step graphs,
+    # single steps on the 40-register kernel): bitwise the one-step kernel's
+    # populations, whose full-size step is checked against the oracle node by
+    # node in test_gpu_parity.
+    p = wl.oscillating_disk()
+    one = _make(p, "f32", "scalar40", hist=256)
+    two = _make(p, "f32", "fused2", hist=256)
+    one.step(70)
+    for k in (3, 64, 3):
+        two.step(k)
+    assert np.array_equal(one.populations(), two.populations())
+    h1, h2 = one.history(), two.history()
+    assert np.array_equal(h1[:, REC["n_solid"]], h2[:, REC["n_solid"]])
+    for key in ("fx", "fy", "torque"):
+        assert rel_err(h2[:, REC[key]], h1[:, REC[key]]) < 1e-9, key
+    one.close()
+    two.close()
