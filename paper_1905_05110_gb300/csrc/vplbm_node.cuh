@@ -579,28 +579,62 @@ __device__ __forceinline__ bool node_collide_to(const StepParams &p, const BodyS
     const T pxy = (f[5] + f[7]) - (f[6] + f[8]);
 
     const auto &k = folded<T>(p);
-    const T ux2 = ux * ux, uy2 = uy * uy;
-    const T u2r = rho * (ux2 + uy2);
-    const T uG = fma(ux, Gx, uy * Gy);
-    const T e_s = fma((T)k.om1, e, fma(par<T>(p.s[1], p.sf[1]), fma((T)3, u2r, (T)-2 * rs), (T)k.h1x6 * uG));
-    const T ep_s = fma((T)k.om2, ep, fma(par<T>(p.s[2], p.sf[2]), fma((T)-3, u2r, rs), (T)k.mh2x6 * uG));
-    const T jx_s = jx + Gx;
-    const T jy_s = jy + Gy;
-    const T qx_s = fma((T)k.om4, qx, fma(-par<T>(p.s[4], p.sf[4]), rho * ux, (T)k.mh4 * Gx));
-    const T qy_s = fma((T)k.om6, qy, fma(-par<T>(p.s[6], p.sf[6]), rho * uy, (T)k.mh6 * Gy));
-    const T pxx_s = fma((T)k.om7, pxx, fma(par<T>(p.s[7], p.sf[7]), rho * (ux2 - uy2), (T)k.h7x2 * fma(ux, Gx, -uy * Gy)));
-    const T pxy_s = fma((T)k.om8, pxy, fma(par<T>(p.s[8], p.sf[8]), rho * (ux * uy), (T)k.h8 * fma(ux, Gy, uy * Gx)));
+    T e_s, ep_s, A, B, X1, Y1, X2, Y2, Pq, Rq, r9;
+    if constexpr (DEV) {
+        // the same operations with the (x, y) and (e, eps) pairs on the
+        // paired FP32 instructions (each lane rounds like the scalar op)
+        const float2 U = make_float2(ux, uy), G = make_float2(Gx, Gy);
+        const float2 rr = make_float2(rho, rho);
+        const float2 U2 = __fmul2_rn(U, U);
+        const T u2r = rho * (U2.x + U2.y);
+        const T uG = fma(ux, Gx, uy * Gy);
+        const float2 t1 = __ffma2_rn(make_float2(3.f, -3.f), make_float2(u2r, u2r), make_float2(-2.f * rs, rs));
+        const float2 t2 = __fmul2_rn(make_float2(k.h1x6, k.mh2x6), make_float2(uG, uG));
+        const float2 t3 = __ffma2_rn(make_float2(p.sf[1], p.sf[2]), t1, t2);
+        const float2 ES = __ffma2_rn(make_float2(k.om1, k.om2), make_float2(e, ep), t3);
+        e_s = ES.x;
+        ep_s = ES.y;
+        const float2 JS = __fadd2_rn(make_float2(jx, jy), G);
+        const float2 Q = make_float2(qx, qy);
+        const float2 QS = __ffma2_rn(make_float2(k.om4, k.om6), Q,
+                                     __ffma2_rn(make_float2(-p.sf[4], -p.sf[6]), __fmul2_rn(rr, U),
+                                                __fmul2_rn(make_float2(k.mh4, k.mh6), G)));
+        const float2 D = make_float2(U2.x - U2.y, ux * uy);
+        const float2 C = make_float2(fma(ux, Gx, -uy * Gy), fma(ux, Gy, uy * Gx));
+        const float2 PS = __ffma2_rn(make_float2(k.om7, k.om8), make_float2(pxx, pxy),
+                                     __ffma2_rn(make_float2(p.sf[7], p.sf[8]), __fmul2_rn(rr, D),
+                                                __fmul2_rn(make_float2(k.h7x2, k.h8), C)));
+        r9 = rs * (T)(1.0 / 9.0);
+        A = r9 - e_s * (T)(1.0 / 36.0) - ep_s * (T)(1.0 / 18.0);
+        B = r9 + e_s * (T)(1.0 / 18.0) + ep_s * (T)(1.0 / 36.0);
+        const float2 XY1 = __fmul2_rn(__ffma2_rn(QS, make_float2(-1.f, -1.f), JS), make_float2(1.f / 6.f, 1.f / 6.f));
+        const float2 XY2 = __ffma2_rn(QS, make_float2(1.f / 12.f, 1.f / 12.f), __fmul2_rn(JS, make_float2(1.f / 6.f, 1.f / 6.f)));
+        const float2 PR = __fmul2_rn(PS, make_float2(0.25f, 0.25f));
+        X1 = XY1.x; Y1 = XY1.y; X2 = XY2.x; Y2 = XY2.y; Pq = PR.x; Rq = PR.y;
+    } else {
+        const T ux2 = ux * ux, uy2 = uy * uy;
+        const T u2r = rho * (ux2 + uy2);
+        const T uG = fma(ux, Gx, uy * Gy);
+        e_s = fma((T)k.om1, e, fma(par<T>(p.s[1], p.sf[1]), fma((T)3, u2r, (T)-2 * rs), (T)k.h1x6 * uG));
+        ep_s = fma((T)k.om2, ep, fma(par<T>(p.s[2], p.sf[2]), fma((T)-3, u2r, rs), (T)k.mh2x6 * uG));
+        const T jx_s = jx + Gx;
+        const T jy_s = jy + Gy;
+        const T qx_s = fma((T)k.om4, qx, fma(-par<T>(p.s[4], p.sf[4]), rho * ux, (T)k.mh4 * Gx));
+        const T qy_s = fma((T)k.om6, qy, fma(-par<T>(p.s[6], p.sf[6]), rho * uy, (T)k.mh6 * Gy));
+        const T pxx_s = fma((T)k.om7, pxx, fma(par<T>(p.s[7], p.sf[7]), rho * (ux2 - uy2), (T)k.h7x2 * fma(ux, Gx, -uy * Gy)));
+        const T pxy_s = fma((T)k.om8, pxy, fma(par<T>(p.s[8], p.sf[8]), rho * (ux * uy), (T)k.h8 * fma(ux, Gy, uy * Gx)));
 
-    // back to populations, M^-1 = M^T diag(1/|row|^2)
-    const T r9 = rs * (T)(1.0 / 9.0);
-    const T A = r9 - e_s * (T)(1.0 / 36.0) - ep_s * (T)(1.0 / 18.0);
-    const T B = r9 + e_s * (T)(1.0 / 18.0) + ep_s * (T)(1.0 / 36.0);
-    const T X1 = (jx_s - qx_s) * (T)(1.0 / 6.0);
-    const T Y1 = (jy_s - qy_s) * (T)(1.0 / 6.0);
-    const T X2 = jx_s * (T)(1.0 / 6.0) + qx_s * (T)(1.0 / 12.0);
-    const T Y2 = jy_s * (T)(1.0 / 6.0) + qy_s * (T)(1.0 / 12.0);
-    const T Pq = pxx_s * (T)0.25;
-    const T Rq = pxy_s * (T)0.25;
+        // back to populations, M^-1 = M^T diag(1/|row|^2)
+        r9 = rs * (T)(1.0 / 9.0);
+        A = r9 - e_s * (T)(1.0 / 36.0) - ep_s * (T)(1.0 / 18.0);
+        B = r9 + e_s * (T)(1.0 / 18.0) + ep_s * (T)(1.0 / 36.0);
+        X1 = (jx_s - qx_s) * (T)(1.0 / 6.0);
+        Y1 = (jy_s - qy_s) * (T)(1.0 / 6.0);
+        X2 = jx_s * (T)(1.0 / 6.0) + qx_s * (T)(1.0 / 12.0);
+        Y2 = jy_s * (T)(1.0 / 6.0) + qy_s * (T)(1.0 / 12.0);
+        Pq = pxx_s * (T)0.25;
+        Rq = pxy_s * (T)0.25;
+    }
 
     store(0, r9 - e_s * (T)(1.0 / 9.0) + ep_s * (T)(1.0 / 9.0));
     store(1, A + X1 + Pq);
