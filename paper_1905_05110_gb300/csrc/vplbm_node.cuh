@@ -517,8 +517,16 @@ __device__ __forceinline__ bool node_collide_to(const StepParams &p, const BodyS
     // penalized velocity, Eq. (22) in the eta-stable form
     const T inv_rho = recip(rho);
     const T gx = par<T>(p.gx, p.gxf), gy = par<T>(p.gy, p.gyf);
-    const T vx = jx * inv_rho + (T)0.5 * gx;
-    const T vy = jy * inv_rho + (T)0.5 * gy;
+    T vx, vy;
+    if constexpr (DEV) {   // (vx, vy) = j / rho + g / 2 as one paired FMA (g / 2 host-folded, exact)
+        const float2 v = __ffma2_rn(make_float2(jx, jy), make_float2(inv_rho, inv_rho),
+                                    make_float2(p.pc.hgx, p.pc.hgy));
+        vx = v.x;
+        vy = v.y;
+    } else {
+        vx = jx * inv_rho + (T)0.5 * gx;
+        vy = jy * inv_rho + (T)0.5 * gy;
+    }
     T ax = 0, ay = 0;
     if (chi) {
         T usx, usy;
