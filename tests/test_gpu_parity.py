@@ -661,3 +661,30 @@ def test_tall_lattice_takes_taller_blocks_within_the_grid_row_limit():
     sim.step(2)
     sim.sync()
     sim.close()
+
+
+def test_penalized_wall_poiseuille_on_the_gpu():
+    # The penalized-wall channel of the oracle pin run to its steady state
+    # on the GPU: FP64 lands on the oracle's profile, and both FP64 and FP32
+    # on the continuum Brinkman solution within the discretisation error the
+    # oracle shows at this resolution (3.4e-3 of the peak velocity).
+    import math
+    import paper_1905_05110_gb300 as vp
+    from test_oracle_pins import _brinkman_channel
+    p, u, nu = _brinkman_channel(1)
+    ny, nx = p["ny"], p["nx"]
+    steps = int(12 * ny * ny / (math.pi ** 2 * nu))
+    init = (np.ones((ny, nx)), np.tile(u[:, None], (1, nx)), np.zeros((ny, nx)))
+    orc = oracle.OracleSim(p, hist_cap=4)
+    orc.init_equilibrium(*init)
+    orc.step(steps)
+    uo = orc.fields()[1].mean(axis=1)
+    for precision in ("f64", "f32"):
+        sim = vp.Simulation(p, precision=precision, history_capacity=steps + 8)
+        sim.init_equilibrium(*init)
+        sim.step(steps)
+        ug = sim.fields()[1].mean(axis=1)
+        if precision == "f64":
+            assert np.max(np.abs(ug - uo)) < 1e-10 * np.max(u)
+        assert np.max(np.abs(ug - u)) / np.max(u) < 4e-3, precision
+        sim.close()

@@ -828,3 +828,53 @@ def test_adjoint_gradient_matches_central_differences(weights):
         h = 1e-6 * base
         v = (J(wl.with_params(p, **{key: base + h})) - J(wl.with_params(p, **{key: base - h}))) / (2 * h)
         assert abs(grad[idx] - v) < 1e-6 * abs(v), key
+
+
+def _brinkman_channel(r, tau=0.8, fluid=20, solid=20, delta=3.0, umax=0.01):
+    """Penalized-wall Poiseuille flow at refinement r: a periodic box whose
+    solid walls are a chi = 1 band (a rectangle spanning the periodic x
+    width, u_s = 0), driven by a uniform acceleration g.  The continuum
+    steady state of Eq. (1) across the channel, nu u'' + g - (chi/eta) u = 0,
+    with the band's edges half-way between its outer nodes and the fluid's:
+    in the fluid u = C1 - g y^2 / (2 nu) (y from the fluid centre), in the
+    solid u = g eta + C2 cosh(s / delta) (s from the band centre), delta =
+    sqrt(nu eta); u and u' continuous at the edges.  Lengths, delta (eta)
+    and g scale with r so that the continuum profile is the same in units of
+    the channel width."""
+    nu = (tau - 0.5) / 3.0
+    F, S = fluid * r, solid * r
+    nx, ny = 3, F + S
+    d = delta * r
+    eta = d * d / nu
+    g = umax * 8.0 * nu / F ** 2
+    body = {"shape": "rectangle", "radius": 10.0 * nx, "radius_b": (S - 1) / 2.0 + 0.25, "x": nx / 2.0,
+            "y": F + (S - 1) / 2.0, "theta": 0.0, "motion": "fixed"}
+    p = wl.periodic_box(nx, ny, tau=tau, eta=eta, body=body, g_fluid=(g, 0.0))
+    y = np.arange(ny) - (F - 1) / 2.0
+    y = (y + ny / 2.0) % ny - ny / 2.0
+    c2 = g * F * d / (2.0 * nu * math.sinh(S / (2.0 * d)))
+    c1 = g * eta + c2 * math.cosh(S / (2.0 * d)) + g * F * F / (8.0 * nu)
+    ay = np.abs(y)
+    u = np.where(ay <= F / 2.0, c1 - g / (2.0 * nu) * y * y, g * eta + c2 * np.cosh((ay - ny / 2.0) / d))
+    return p, u, nu
+
+
+def test_penalized_wall_poiseuille_converges_to_brinkman_at_second_order():
+    # The penalization (Eq. 1 through the eta-stable Eq. 22 and the forcing
+    # of Eq. 17) against the continuum solution with resolved Brinkman
+    # layers (delta = 3 and 6 nodes): the steady profile converges at second
+    # order in the node spacing.  A wrong factor in the penalization changes
+    # delta or the flow rate at O(1); a wrong sign has no steady state.
+    errs = []
+    for r in (1, 2):
+        p, u, nu = _brinkman_channel(r)
+        sim = oracle.OracleSim(p, hist_cap=4)
+        ny, nx = p["ny"], p["nx"]
+        sim.init_equilibrium(np.ones((ny, nx)), np.tile(u[:, None], (1, nx)), np.zeros((ny, nx)))
+        sim.step(int(12 * ny * ny / (math.pi ** 2 * nu)))   # 12 e-folds of the slowest mode
+        assert np.array_equal(sim.chi()[:, 0] > 0, np.arange(ny) >= ny // 2)   # the band
+        _, ux, uy = sim.fields()
+        assert np.max(np.abs(uy)) < 1e-14
+        errs.append(np.max(np.abs(ux.mean(axis=1) - u)) / np.max(u))
+    assert errs[0] < 5e-3 and errs[1] < 1.5e-3, errs
+    assert math.log2(errs[0] / errs[1]) > 1.6, errs
