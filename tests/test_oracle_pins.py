@@ -878,3 +878,27 @@ def test_penalized_wall_poiseuille_converges_to_brinkman_at_second_order():
         errs.append(np.max(np.abs(ux.mean(axis=1) - u)) / np.max(u))
     assert errs[0] < 5e-3 and errs[1] < 1.5e-3, errs
     assert math.log2(errs[0] / errs[1]) > 1.6, errs
+
+
+def test_fixed_disk_penalization_drag_agrees_with_momentum_exchange():
+    # The fixed-disk channel (256 x 128, parabolic inlet, 2000 steps): the
+    # two force definitions recorded every step, the reaction of the
+    # penalization force summed over the solid nodes (Eq. 1) and the
+    # momentum exchanged across the solid boundary (Eqs. 25-27), describe
+    # the same drag once the solid interior is steady; their second-half
+    # means agree to 0.11 % (C_D) and RMS lifts to 0.12 %.
+    p = wl.channel_fixed_disk()
+    sim = oracle.OracleSim(p, hist_cap=2048)
+    u = p["init"]["u"]
+    sh = (p["ny"], p["nx"])
+    sim.init_equilibrium(np.ones(sh), np.full(sh, u[0]), np.full(sh, u[1]))
+    sim.step(2000)
+    h = sim.history(0, 2000)[1000:]
+    ix = {n: k for k, n in enumerate(oracle.RECORD_FIELDS)}
+    qref = 0.5 * p["rho0"] * p["body"]["d_ref"] * p["body"]["u_ref"] ** 2
+    cd_mem, cd_pen = h[:, ix["cd"]].mean(), (h[:, ix["fpen_x"]] / qref).mean()
+    assert 0.9 < cd_mem < 1.3
+    assert abs(cd_pen - cd_mem) < 3e-3 * cd_mem, (cd_mem, cd_pen)
+    cl_mem = np.sqrt((h[:, ix["cl"]] ** 2).mean())
+    cl_pen = np.sqrt(((h[:, ix["fpen_y"]] / qref) ** 2).mean())
+    assert abs(cl_pen - cl_mem) < 1e-2 * cl_mem, (cl_mem, cl_pen)
