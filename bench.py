@@ -346,7 +346,7 @@ def run_ours(args, rank, world, local_rank):
         if "adjoint" in legs:
             compare["adjoint"] = run_adjoint(args, torch, compare.get("f64"))
         if "sedimenting" in legs:
-            compare["sedimenting_disk"] = run_other_workload("sedimenting_1024x4096", 8000, torch, stream)
+            compare["sedimenting_disk"] = run_other_workload("sedimenting_1024x4096", 200_000, torch, stream)
         if "paper" in legs:
             compare["paper_oscillating_cylinder"] = run_other_workload("paper_cylinder_1230x410", 40000, torch,
                                                                        stream)
@@ -430,6 +430,13 @@ def run_other_workload(name, steps, torch, stream):
         if b["motion"] == "free":
             d["final_pose"] = [float(v) for v in h[-1, 6:9]]
             d["final_velocity"] = [float(v) for v in h[-1, 9:12]]
+            if "gravity" in p:   # settling: terminal velocity against the design value (Happel, Stokes regime)
+                nu = (1.0 / p["s"][7] - 0.5) / 3.0
+                vt = float(-h[-max(1, steps // 20):, 10].mean())
+                d["terminal_vy_last_5pct"] = vt
+                d["terminal_re"] = vt * b["d_ref"] / nu
+                d["design_v_s"] = b["u_ref"]
+                d["terminal_over_design"] = vt / b["u_ref"]
         per_body.append(d)
     if len(bodies) == 1:
         out.update(per_body[0])
