@@ -260,3 +260,30 @@ def test_several_bodies_refusals_and_queries():
     with pytest.raises(vp.VplbmError):
         one.history(0, 0, body=1)
     one.close()
+
+
+def _mixed_bgk():
+    p = _mixed()
+    p["collision"] = "bgk"
+    return p
+
+
+def _mixed_paper_walls():
+    # the paper's channel boundaries: symmetry walls and a convective outlet
+    p = _mixed()
+    p["bc"]["south"] = {"kind": "symmetry"}
+    p["bc"]["north"] = {"kind": "symmetry"}
+    p["bc"]["east"] = {"kind": "convective", "u": (0.05, 0.0)}
+    return p
+
+
+@pytest.mark.parametrize("variant", ["bgk", "paper_walls"])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_several_bodies_with_bgk_and_with_the_papers_boundaries(variant, precision):
+    p = _mixed_bgk() if variant == "bgk" else _mixed_paper_walls()
+    gpu, orc = make_pair(p, precision)
+    gpu.step(100)
+    orc.step(100)
+    assert dev_err(gpu.populations(), orc.populations()) < RUN_TOL[precision]
+    _check_records(gpu, orc, 3, precision)
+    gpu.close()
