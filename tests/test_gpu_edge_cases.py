@@ -103,3 +103,30 @@ def test_widest_lattice_at_rest_stays_at_rest():
         vp.Simulation(wl.periodic_box(nx + 1, ny, tau=0.7), precision="f16", history_capacity=8)
     assert ei.value.status == 1
     sim.close()
+
+
+def test_largest_node_count_at_rest_stays_at_rest():
+    # 2^22 x 511 = 2.14e9 nodes, just under the 2^31 limit the library
+    # checks (FP16: 2 x 38.6 GB of populations): both kernels, fields of a
+    # few sampled rows checked on the device; 2^22 x 512 is refused.
+    import torch
+    import paper_1905_05110_gb300 as vp
+    nx, ny = 1 << 22, 511
+    p = wl.periodic_box(nx, ny, tau=0.7)
+    sim = vp.Simulation(p, precision="f16", history_capacity=64)
+    sim.init_from_problem()
+    for kernel in ("scalar40", "fused2"):
+        sim.set_launch(kernel, 256, 1)
+        sim.step(34)
+        sim.sync()
+    out = torch.empty((3, ny, nx), dtype=torch.float64, device="cuda")
+    vp.vplbm_get_fields_dev(sim.ctx, out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr())
+    sim.sync()
+    rows = [0, 1, 255, 509, 510]
+    assert torch.all(out[0, rows] == 1.0).item()
+    assert torch.all(out[1:, rows] == 0.0).item()
+    del out
+    sim.close()
+    with pytest.raises(vp.VplbmError) as ei:
+        vp.Simulation(wl.periodic_box(nx, ny + 1, tau=0.7), precision="f16", history_capacity=8)
+    assert ei.value.status == 1
