@@ -274,8 +274,8 @@ vplbm_status vplbm_get_body_k(vplbm_ctx *ctx, int k, double q[3], double v[3], l
  *                          storage, nx * element size a multiple of 16 bytes,
  *                          nx >= 136 (FP32) / 144 (FP16), ny >= 4).
  *  VPLBM_KERNEL_FUSED2     two time steps per launch (FP32/FP16 storage,
- *                          a body on a prescribed path or none, no
- *                          convective outlet, one body): a block computes
+ *                          a body on a prescribed path or none, one
+ *                          body): a block computes
  *                          step n on its 64 x 8 tile and a one-node ring
  *                          around it into shared memory, then step n + 1
  *                          from there, so HBM is read and written once per

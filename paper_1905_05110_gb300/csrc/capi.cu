@@ -265,6 +265,13 @@ cudaError_t launch_two(const vplbm_ctx *c, int L, cudaStream_t stream)
     q.next1 = c->bs + (odd ? 1 : 3);
     q.b.partials = c->partials + (size_t)c->max_parts * NPART;
     q.b.ticket = &c->ctrl->ticket[1];
+    // convective outlet: step n reads the record of step n - 1 and step
+    // n + 1 writes the one of step n + 1, alternating between the two slots
+    // with the launch (the same slot would race with other blocks' reads);
+    // step n's own record stays in each block's shared memory
+    double *ob = static_cast<double *>(c->outlet);
+    q.a.conv_in = q.b.conv_in = ob + (size_t)odd * 3 * c->ny;
+    q.a.conv_out = q.b.conv_out = ob + (size_t)(odd ^ 1) * 3 * c->ny;
     return launch_step_fused2(c->precision, q, stream);
 }
 
@@ -275,7 +282,6 @@ const char *fused2_refusal(const vplbm_ctx *c)
     if (c->nbodies > 1) return "the two-step kernel takes one body";
     if (c->has_body && c->body_desc.motion == VPLBM_MOTION_FREE)
         return "the two-step kernel needs a body on a prescribed path (fixed or imposed)";
-    if (c->base.bc[VPLBM_EAST] == VPLBM_BC_CONVECTIVE) return "the two-step kernel has no convective outlet";
     if (max_reduction_blocks(c->nx, c->ny, c->has_body ? bounding_radius(&c->body_desc) + 1.0 : 0.0, c->has_body,
                              FUSED2_W, FUSED2_H) > c->max_parts)
         return "the two-step kernel needs more reduction scratch than allocated";

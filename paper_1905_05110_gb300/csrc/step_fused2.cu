@@ -12,7 +12,10 @@
 // launch boundary is paid once per two steps.  The node arithmetic is the
 // one-step kernel's (node_collide_to, body_chi, the same pull rules through
 // a shared-memory source), so the populations are those of two one-step
-// launches, bit for bit.
+// launches, bit for bit.  A convective outlet's rule at step n + 1 takes
+// the values its outlet nodes pulled at step n: the block keeps those of its
+// rows in shared memory, and only step n + 1 writes the outlet state (for
+// step n + 2, into the other slot than the one step n reads).
 //
 // Body blocks come first, as in the one-step kernel: they take the tiles
 // that meet the union of the node ranges of poses n and n + 1, reduce the
@@ -32,13 +35,20 @@ constexpr int F2_ITER = (F2_RN + F2_NT - 1) / F2_NT;      // region nodes per th
 constexpr int F2_ROWS = FUSED2_H / F2_TY;                 // tile nodes per thread
 static_assert(FUSED2_W == F2_TX && FUSED2_H % F2_TY == 0, "tile and block shapes");
 
+// Inward populations (a = 3, 6, 7) pulled by the tile's east-outlet nodes at
+// step n, [outlet_slot(a)][row in the tile].
+__shared__ float f2_outlet[3 * FUSED2_H];
+
 __device__ __forceinline__ float ld_stage(const float *s) { return *s; }
 __device__ __forceinline__ float ld_stage(const __half *s) { return __half2float(*s); }
 
 // Stage reader: lattice node (i, j) -> its slot in the region of the tile
 // at (bi0, bj0).  A node reached across a periodic edge sits at its
 // unwrapped position in the region (the first step computed it there).
-template <int P> struct StageSrc {
+// The outlet's previous values are the tile rows' record of step n (CONV:
+// the lattice has a convective outlet; otherwise the outlet rule is never
+// reached).
+template <int P, bool CONV> struct StageSrc {
     const typename Prec<P>::S *stage;
     int bi0, bj0, nx, ny;
     __device__ __forceinline__ typename Prec<P>::T operator()(int a, int i, int j) const
@@ -49,6 +59,11 @@ template <int P> struct StageSrc {
         if (lj >= F2_RH) lj -= ny;
         else if (lj < 0) lj += ny;
         return ld_stage(stage + a * F2_RN + lj * F2_RW + li);
+    }
+    __device__ __forceinline__ float outlet_prev(const StepParams &, int a, int j) const
+    {
+        if constexpr (CONV) return f2_outlet[outlet_slot(a) * FUSED2_H + (j - bj0)];
+        else return 0.f;
     }
 };
 
@@ -70,7 +85,7 @@ __device__ __noinline__ void advance_two(const StepParams &pb, BodyState *next0,
 
 // Both steps of one tile.  sums: this block also reduces both steps'
 // solid-node sums into partial `slot` of `nparts` and may run the tails.
-template <int P, int COLL, int SHAPE>
+template <int P, int COLL, int SHAPE, bool CONV>
 __device__ __forceinline__ void two_steps(const Fused2Params &q, typename Prec<P>::S *stage, int tx, int ty,
                                           bool sums, int slot, int nparts, int4 ra, int4 rb, double (*red)[NPART],
                                           int *s_last)
@@ -114,8 +129,16 @@ __device__ __forceinline__ void two_steps(const Fused2Params &q, typename Prec<P
             }
         }
         T f[NQ];
-        if (interior) pull_all<P, true>(pa, fin, i, j, f);
-        else pull_all<P>(pa, fin, i, j, f);
+        if (interior) {
+            pull_all<P, true>(pa, fin, i, j, f);
+        } else {
+            pull_all<P>(pa, fin, i, j, f);
+            if (CONV && ui == nx - 1 && lj >= 1 && lj <= FUSED2_H) {
+                f2_outlet[outlet_slot(3) * FUSED2_H + lj - 1] = f[3];
+                f2_outlet[outlet_slot(6) * FUSED2_H + lj - 1] = f[6];
+                f2_outlet[outlet_slot(7) * FUSED2_H + lj - 1] = f[7];
+            }
+        }
         T dxl = 0, dyl = 0;
         bool chi = false;
         if (near_a && i >= ra.x && i <= ra.y && j >= ra.z && j <= ra.w)
@@ -137,11 +160,11 @@ __device__ __forceinline__ void two_steps(const Fused2Params &q, typename Prec<P
         block_reduce<A>(any_chi, part, red);
         publish_slot<A>(pa, slot, nparts, reinterpret_cast<A *>(red[0]), s_last);
     }
-    __syncthreads();   // the stage is complete
+    __syncthreads();   // the stage and the outlet record are complete
 
     // ---- step n + 1 on the tile, from the stage ----
     const bool near_b = rb.x <= rb.y && tile_near_body(rb, bi0, bj0, FUSED2_W, FUSED2_H, false);
-    const StageSrc<P> src{stage, bi0, bj0, nx, ny};
+    const StageSrc<P, CONV> src{stage, bi0, bj0, nx, ny};
 #pragma unroll
     for (int k = 0; k < NPART - 1; ++k) acc_zero(part[k]);
     any_chi = false;
@@ -158,6 +181,7 @@ __device__ __forceinline__ void two_steps(const Fused2Params &q, typename Prec<P
         } else {
 #pragma unroll
             for (int a = 0; a < NQ; ++a) f[a] = pull_edge_src<P>(pb, src, a, i, j);
+            if (CONV && i == nx - 1) record_outlet<P>(pb, j, f);
         }
         T dxl = 0, dyl = 0;
         bool chi = false;
@@ -189,8 +213,8 @@ __device__ __forceinline__ void two_steps(const Fused2Params &q, typename Prec<P
 
 // Grid: (tile columns) x (body-block rows + tile rows), programmatic
 // dependent launch as in the one-step kernel.
-template <int P, int COLL, int SHAPE>
-__global__ void __launch_bounds__(F2_NT, 5) vp_mrt_step2(const Fused2Params q)
+template <int P, int COLL, int SHAPE, bool CONV>
+__device__ __forceinline__ void step2_grid(const Fused2Params &q)
 {
     using S = typename Prec<P>::S;
     extern __shared__ __align__(16) unsigned char f2_smem[];
@@ -235,8 +259,21 @@ __global__ void __launch_bounds__(F2_NT, 5) vp_mrt_step2(const Fused2Params q)
         tx = blockIdx.x;
         ty = blockIdx.y - nbr;
     }
-    if (tx >= 0) two_steps<P, COLL, SHAPE>(q, stage, tx, ty, sums, slot, nparts, ra, rb, red, &s_last);
+    if (tx >= 0) two_steps<P, COLL, SHAPE, CONV>(q, stage, tx, ty, sums, slot, nparts, ra, rb, red, &s_last);
     if (b == 0 && tid == 0) advance_two(q.b, q.next0, q.next1);
+}
+
+template <int P, int COLL, int SHAPE>
+__global__ void __launch_bounds__(F2_NT, 5) vp_mrt_step2(const Fused2Params q)
+{
+    step2_grid<P, COLL, SHAPE, false>(q);
+}
+
+// The same for a lattice with a convective east outlet (any body shape).
+template <int P, int COLL>
+__global__ void __launch_bounds__(F2_NT, 5) vp_mrt_step2_conv(const Fused2Params q)
+{
+    step2_grid<P, COLL, SHAPE_ANY, true>(q);
 }
 
 __global__ void lookahead_kernel(const StepParams p)
@@ -267,6 +304,9 @@ cudaError_t launch_p(const Fused2Params &q0, cudaStream_t stream)
     cfg.numAttrs = 1;
     const bool bgk = q.a.collision == VPLBM_COLLISION_BGK;
     const bool disk = !q.a.body.present || q.a.body.shape == VPLBM_SHAPE_DISK;
+    if (q.a.bc[VPLBM_EAST] == VPLBM_BC_CONVECTIVE)
+        return bgk ? cudaLaunchKernelEx(&cfg, vp_mrt_step2_conv<P, VPLBM_COLLISION_BGK>, q)
+                   : cudaLaunchKernelEx(&cfg, vp_mrt_step2_conv<P, VPLBM_COLLISION_MRT>, q);
     if (bgk)
         return disk ? cudaLaunchKernelEx(&cfg, vp_mrt_step2<P, VPLBM_COLLISION_BGK, VPLBM_SHAPE_DISK>, q)
                     : cudaLaunchKernelEx(&cfg, vp_mrt_step2<P, VPLBM_COLLISION_BGK, SHAPE_ANY>, q);

@@ -237,7 +237,7 @@ struct Fused2Params {
     BodyState *next1;  // receives pose n + 3
 };
 // Steps n and n + 1 (asynchronous on `stream`); bodies on a prescribed path
-// only, FP32 / FP16 storage, no convective outlet.  max_parts of both views
+// only, FP32 / FP16 storage.  max_parts of both views
 // must cover the union of the node ranges of poses n and n + 1 in
 // FUSED2_W x FUSED2_H tiles.
 cudaError_t launch_step_fused2(int precision, const Fused2Params &q, cudaStream_t stream);

@@ -89,8 +89,10 @@ __device__ __forceinline__ float wall_term<float>(const StepParams &p, int a, in
 }
 
 // Source of a pull: population a of the previous post-collision field at
-// lattice node (i, j) (inside the lattice).  GlobalSrc reads the population
-// buffer; the two-step kernel reads its shared-memory stage instead.
+// lattice node (i, j) (inside the lattice), and the convective outlet's
+// previous pulled value of inward population a at row j.  GlobalSrc reads
+// the population buffer and the outlet state; the two-step kernel reads its
+// shared-memory stage and its own record of the first step instead.
 template <int P> struct GlobalSrc {
     const typename Prec<P>::S *fin;
     long long ps;
@@ -98,6 +100,10 @@ template <int P> struct GlobalSrc {
     __device__ __forceinline__ typename Prec<P>::T operator()(int a, int i, int j) const
     {
         return ldv(fin + a * ps + (long long)j * nx + i);
+    }
+    __device__ __forceinline__ typename Prec<P>::T outlet_prev(const StepParams &p, int a, int j) const
+    {
+        return static_cast<const typename Prec<P>::T *>(p.conv_in)[outlet_slot(a) * p.ny + j];
     }
 };
 
@@ -133,7 +139,7 @@ __device__ __forceinline__ typename Prec<P>::T pull_edge_src(const StepParams &p
             return src(a, i, sj);
         } else if (kind == VPLBM_BC_CONVECTIVE) {   // east only (checked on the host)
             const T z = src(a, i, sj);
-            const T prev = static_cast<const T *>(p.conv_in)[outlet_slot(a) * ny + j];
+            const T prev = src.outlet_prev(p, a, j);
             return par<T>(p.conv_k1, p.conv_k1f) * prev + par<T>(p.conv_k2, p.conv_k2f) * z;
         } else {
             T val = src(opp_of(a), i, j);

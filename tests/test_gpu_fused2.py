@@ -84,6 +84,45 @@ def _periodic_x_symmetry_y():
     return p
 
 
+def _convective_channel(nx, ny, body, u=0.048, seed=3):
+    # the channel of Sec. 3.1: velocity inlet, convective outlet, symmetry walls
+    p = wl.mixed_bc_box(nx, ny, seed=seed, west="velocity", east="convective", south="symmetry",
+                        north="symmetry", tau=0.56, body=body)
+    p["bc"]["west"] = {"kind": "velocity", "u": (u, 0.0)}
+    p["bc"]["east"] = {"kind": "convective", "u": (u, 0.0)}
+    p["init"] = {"rho": 1.0, "u": (u, 0.0)}
+    return p
+
+
+def _paper_channel_cosine():
+    r = 6.0
+    return _convective_channel(130, 52, {"radius": r, "x": 40.0, "y": 26.0, "motion": "imposed", "axis": 1,
+                                         "amp": r / 2, "freq": 0.004, "phase": np.pi / 2, "u_ref": 0.048,
+                                         "d_ref": 2 * r})
+
+
+def _convective_lone_column():
+    # nx = 2 * 64 + 1: the outlet column is a tile column of its own and the
+    # ring of the tiles west of it; random populations so that the outlet
+    # record differs row by row, a pitching ellipse near the outlet, no-slip
+    # and moving walls
+    p = wl.mixed_bc_box(129, 37, seed=15, west="velocity", east="convective", south="noslip", north="velocity",
+                        tau=0.6, body={"shape": "ellipse", "radius": 7.0, "radius_b": 3.5, "x": 112.4,
+                                       "y": 17.7, "theta": 0.3, "motion": "imposed", "axis": 2, "amp": 0.4,
+                                       "freq": 0.02, "u_ref": 0.05, "d_ref": 7.0})
+    p["bc"]["east"] = {"kind": "convective", "u": (0.31, 0.0)}
+    p["f0"] = wl.random_populations(129, 37, seed=16, amp=0.02, u_amp=0.03)
+    return p
+
+
+def _convective_tiny_bgk():
+    # smaller than one tile, BGK collision
+    p = _convective_channel(7, 5, None, u=0.03, seed=17)
+    p["collision"] = "bgk"
+    p["f0"] = wl.random_populations(7, 5, seed=18, amp=0.02, u_amp=0.03)
+    return p
+
+
 CASES = {
     "tiny_walls": _tiny_walls,
     "periodic_x_symmetry_y": _periodic_x_symmetry_y,
@@ -96,6 +135,9 @@ CASES = {
     "periodic_tiny": lambda: _periodic_random(5, 4),
     "ragged_walls": _ragged_walls,
     "bgk_channel": _bgk_channel,
+    "paper_channel_cosine": _paper_channel_cosine,
+    "convective_lone_column": _convective_lone_column,
+    "convective_tiny_bgk": _convective_tiny_bgk,
 }
 
 
@@ -144,8 +186,9 @@ def test_two_step_kernel_equals_one_step_kernel_bitwise(case, precision):
     two.close()
 
 
-def test_two_step_kernel_matches_oracle():
-    p = _channel_imposed()
+@pytest.mark.parametrize("case", ["channel_imposed", "paper_channel_cosine"])
+def test_two_step_kernel_matches_oracle(case):
+    p = CASES[case]()
     gpu, orc = make_pair(p, "f32")
     gpu.set_launch("fused2", 128, 1)
     gpu.step(96)
@@ -158,8 +201,9 @@ def test_two_step_kernel_matches_oracle():
     gpu.close()
 
 
-def test_two_step_kernel_launch_count_checkpoint_and_autotune(tmp_path):
-    p = _channel_imposed()
+@pytest.mark.parametrize("case", ["channel_imposed", "paper_channel_cosine"])
+def test_two_step_kernel_launch_count_checkpoint_and_autotune(case, tmp_path):
+    p = CASES[case]()
     sim = _make(p, "f32", "fused2")
     l0 = sim.launches
     sim.step(64)   # two graphs: a lookahead and 16 two-step launches each
@@ -185,8 +229,6 @@ def test_two_step_kernel_refusals():
     free = _channel_imposed()
     free["body"] = dict(free["body"], motion="free", mass=600.0, inertia=3e4, dof_mask=2)
     cases.append((free, "f32"))
-    conv = wl.paper_oscillating_cylinder(nx=200, ny=80, diameter=10.0)
-    cases.append((conv, "f32"))
     multi = _channel_imposed()
     multi["bodies"] = [multi["body"], dict(multi["body"], x=200.0, motion="fixed")]
     cases.append((multi, "f32"))
@@ -209,6 +251,26 @@ def test_full_size_headline_two_step_kernel_equals_one_step_kernel():
     two = _make(p, "f32", "fused2", hist=256)
     one.step(70)
     for k in (3, 64, 3):
+        two.step(k)
+    assert np.array_equal(one.populations(), two.populations())
+    h1, h2 = one.history(), two.history()
+    assert np.array_equal(h1[:, REC["n_solid"]], h2[:, REC["n_solid"]])
+    for key in ("fx", "fy", "torque"):
+        assert rel_err(h2[:, REC[key]], h1[:, REC[key]]) < 1e-9, key
+    one.close()
+    two.close()
+
+
+def test_full_size_paper_cylinder_two_step_kernel_equals_one_step_kernel():
+    # The oscillating cylinder of Sec. 3.1 at its full 1230 x 410 size
+    # (velocity inlet, convective outlet, symmetry walls, cosine law):
+    # two-step launches in 32-step graphs between single steps, bitwise the
+    # one-step kernel's populations and solid-node counts.
+    p = wl.paper_oscillating_cylinder()
+    one = _make(p, "f32", "scalar40", hist=256)
+    two = _make(p, "f32", "fused2", hist=256)
+    one.step(134)
+    for k in (3, 64, 3, 64):
         two.step(k)
     assert np.array_equal(one.populations(), two.populations())
     h1, h2 = one.history(), two.history()
