@@ -17,6 +17,13 @@
 // rows in shared memory, and only step n + 1 writes the outlet state (for
 // step n + 2, into the other slot than the one step n reads).
 //
+// Tiles are dispatched edge first: a tile whose region reaches a lattice
+// edge takes the boundary rules node by node and runs about twice as long
+// as an interior one, and the blocks dispatched last set the end of the
+// launch.  The grid runs column by column (blockIdx.x over the tile rows;
+// row by row where the tile columns exceed the grid's y limit), the two
+// edge columns first and, in each column, its two edge rows first.
+//
 // Body blocks come first, as in the one-step kernel: they take the tiles
 // that meet the union of the node ranges of poses n and n + 1, reduce the
 // solid-node sums of both steps (float-float in FP32) and elect a tail for
@@ -211,8 +218,9 @@ __device__ __forceinline__ void two_steps(const Fused2Params &q, typename Prec<P
     }
 }
 
-// Grid: (tile columns) x (body-block rows + tile rows), programmatic
-// dependent launch as in the one-step kernel.
+// Grid: (tile rows) x (body-block lines + tile columns), or (tile columns) x
+// (body-block lines + tile rows) for a lattice of more than 65 535 - lines
+// tile columns; programmatic dependent launch as in the one-step kernel.
 template <int P, int COLL, int SHAPE, bool CONV>
 __device__ __forceinline__ void step2_grid(const Fused2Params &q)
 {
@@ -256,8 +264,12 @@ __device__ __forceinline__ void step2_grid(const Fused2Params &q)
         }
         if (b == 0 && nrect > q.a.nbody && tid == 0) *q.a.err |= ERR_INTERNAL;
     } else {
-        tx = blockIdx.x;
-        ty = blockIdx.y - nbr;
+        const bool colmajor = (int)gridDim.x == (q.a.ny + FUSED2_H - 1) / FUSED2_H;
+        const int lines = gridDim.y - nbr;
+        const int ntx = colmajor ? lines : gridDim.x, nty = colmajor ? gridDim.x : lines;
+        const int c = colmajor ? blockIdx.y - nbr : blockIdx.x, r = colmajor ? blockIdx.x : blockIdx.y - nbr;
+        tx = c == 0 ? 0 : (c == 1 ? ntx - 1 : c - 1);   // edge columns first
+        ty = r == 0 ? 0 : (r == 1 ? nty - 1 : r - 1);   // edge rows first
     }
     if (tx >= 0) two_steps<P, COLL, SHAPE, CONV>(q, stage, tx, ty, sums, slot, nparts, ra, rb, red, &s_last);
     if (b == 0 && tid == 0) advance_two(q.b, q.next0, q.next1);
@@ -290,10 +302,14 @@ cudaError_t launch_p(const Fused2Params &q0, cudaStream_t stream)
     // the union of two node ranges one step apart: one node more of radius
     const long long nbody = max_reduction_blocks(nx, ny, q.a.body.radius + 1.0, q.a.body.present, FUSED2_W, FUSED2_H);
     q.a.nbody = (int)nbody;
-    q.a.nbody_rows = (int)((nbody + ntx - 1) / ntx);
+    // grid lines (rows of a row-major grid, columns of a column-major one)
+    // of body blocks; column-major where the tile columns fit the y limit
+    const bool colmajor = ntx + (nbody + nty - 1) / nty <= 65535;
+    const int line = colmajor ? nty : ntx;
+    q.a.nbody_rows = (int)((nbody + line - 1) / line);
     const size_t smem = (size_t)NQ * F2_RN * sizeof(typename Prec<P>::S);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ntx, nty + q.a.nbody_rows);
+    cfg.gridDim = colmajor ? dim3(nty, ntx + q.a.nbody_rows) : dim3(ntx, nty + q.a.nbody_rows);
     cfg.blockDim = dim3(F2_TX, F2_TY);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
