@@ -20,7 +20,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "vplbm_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
-LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
+# VPLBM_ORACLE_PLANT=k (k > 0) loads the oracle built with planted mistake k
+# into a library of its own (the test of the pins); unset or 0: the oracle.
+PLANT = int(os.environ.get("VPLBM_ORACLE_PLANT", "0") or 0)
+LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so" if PLANT == 0 else f"liboracle_plant{PLANT}.so")
 
 Q = 9
 BC_KINDS = {"periodic": 0, "noslip": 1, "velocity": 2, "zerograd": 3, "symmetry": 4, "convective": 5}
@@ -41,7 +44,7 @@ def build(force: bool = False) -> str:
         return LIB_PATH
     tmp = LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
+           "-fPIC", "-shared", "-o", tmp, SRC, "-lm"] + ([f"-DORACLE_PLANT={PLANT}"] if PLANT else [])
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH

@@ -58,6 +58,15 @@
 
 #define Q 9
 
+/* Planted mistakes, for the test that checks that the pins catch them
+ * (tests/test_oracle_plants.py builds this file with -DORACLE_PLANT=k into
+ * a library of its own); the oracle itself is built with ORACLE_PLANT = 0,
+ * where every PLANT(k) is a constant false and plants nothing. */
+#ifndef ORACLE_PLANT
+#define ORACLE_PLANT 0
+#endif
+#define PLANT(k) (ORACLE_PLANT == (k))
+
 /* ---- lattice constants, restated from Sec. 2.2 ---------------------- */
 
 static int C[Q][2];      /* Eq. (10) */
@@ -98,7 +107,7 @@ static void setup_constants(void)
     /* Eq. (13) */
     W[0] = 4.0 / 9.0;
     for (int a = 1; a <= 4; ++a) W[a] = 1.0 / 9.0;
-    for (int a = 5; a <= 8; ++a) W[a] = 1.0 / 36.0;
+    for (int a = 5; a <= 8; ++a) W[a] = PLANT(3) ? 1.0 / 18.0 : 1.0 / 36.0;
     for (int a = 0; a < Q; ++a)
         for (int b = 0; b < Q; ++b)
             if (C[b][0] == -C[a][0] && C[b][1] == -C[a][1]) OPP[a] = b;
@@ -265,7 +274,7 @@ static void moment_equilibrium(double rho, double ux, double uy, double meq[Q])
     meq[1] = rho * (-2.0 + 3.0 * u2);
     meq[2] = rho * (1.0 - 3.0 * u2);
     meq[3] = rho * ux;
-    meq[4] = -rho * ux;
+    meq[4] = PLANT(1) ? rho * ux : -rho * ux;
     meq[5] = rho * uy;
     meq[6] = -rho * uy;
     meq[7] = rho * (ux * ux - uy * uy);
@@ -279,8 +288,8 @@ static void guo_forcing(double ux, double uy, double Gx, double Gy, double F[Q])
     const double cs2 = 1.0 / 3.0;
     for (int a = 0; a < Q; ++a) {
         double cu = C[a][0] * ux + C[a][1] * uy;
-        double vx = (C[a][0] - ux) / cs2 + cu * C[a][0] / (cs2 * cs2);
-        double vy = (C[a][1] - uy) / cs2 + cu * C[a][1] / (cs2 * cs2);
+        double vx = (C[a][0] - ux) / cs2 + (PLANT(2) ? 0.0 : cu * C[a][0] / (cs2 * cs2));
+        double vy = (C[a][1] - uy) / cs2 + (PLANT(2) ? 0.0 : cu * C[a][1] / (cs2 * cs2));
         F[a] = W[a] * (vx * Gx + vy * Gy);
     }
 }
@@ -295,8 +304,8 @@ static void penalized_velocity(double rho, double jx, double jy, int chi,
     double vx = jx / rho + 0.5 * gx;
     double vy = jy / rho + 0.5 * gy;
     double c = (double)chi;
-    *ax = -c * (vx - usx) / (eta + 0.5 * c);
-    *ay = -c * (vy - usy) / (eta + 0.5 * c);
+    *ax = -c * (vx - usx) / (eta + (PLANT(4) ? 1.0 : 0.5) * c);
+    *ay = -c * (vy - usy) / (eta + (PLANT(4) ? 1.0 : 0.5) * c);
     *ux = vx + 0.5 * *ax;
     *uy = vy + 0.5 * *ay;
 }
@@ -365,7 +374,7 @@ static double pulled(const orc_sim *s, int a, int i, int j)
             double val = FT(OPP[a], i, j);
             if (kind == ORC_VELOCITY) {
                 double cu = C[a][0] * edge_u(s, side, 0, i) + C[a][1] * edge_u(s, side, 1, i);
-                val += 6.0 * W[a] * s->lat.rho0 * cu;
+                val += (PLANT(7) ? -6.0 : 6.0) * W[a] * s->lat.rho0 * cu;
             }
             return val;
         }
@@ -388,7 +397,7 @@ static double pulled(const orc_sim *s, int a, int i, int j)
             double val = FT(OPP[a], i, j);
             if (kind == ORC_VELOCITY) {
                 double cu = C[a][0] * edge_u(s, side, 0, j) + C[a][1] * edge_u(s, side, 1, j);
-                val += 6.0 * W[a] * s->lat.rho0 * cu;
+                val += (PLANT(7) ? -6.0 : 6.0) * W[a] * s->lat.rho0 * cu;
             }
             return val;
         }
@@ -470,8 +479,8 @@ static void body_advance(const orc_body *b, long long step, double q_center,
     body_rhs(b, F, qt, vt, k4v);
     for (int d = 0; d < 3; ++d) {
         if (!((b->dof_mask >> d) & 1u)) continue;
-        q[d] = q[d] + h / 6.0 * (k1q[d] + 2.0 * k2q[d] + 2.0 * k3q[d] + k4q[d]);
-        v[d] = v[d] + h / 6.0 * (k1v[d] + 2.0 * k2v[d] + 2.0 * k3v[d] + k4v[d]);
+        q[d] = PLANT(5) ? q[d] + h * k1q[d] : q[d] + h / 6.0 * (k1q[d] + 2.0 * k2q[d] + 2.0 * k3q[d] + k4q[d]);
+        v[d] = PLANT(5) ? v[d] + h * k1v[d] : v[d] + h / 6.0 * (k1v[d] + 2.0 * k2v[d] + 2.0 * k3v[d] + k4v[d]);
     }
 }
 
@@ -624,7 +633,7 @@ static void one_step(orc_sim *s)
                 double ex = ns.jx - ox, ey = ns.jy - oy;
                 fh[k][0] += ex;
                 fh[k][1] += ey;
-                fh[k][2] += ns.dx * ey - ns.dy * ex;   /* Eq. (27) */
+                fh[k][2] += PLANT(6) ? ns.dy * ex - ns.dx * ey : ns.dx * ey - ns.dy * ex;   /* Eq. (27) */
                 nsolid[k] += 1.0;
             }
         }

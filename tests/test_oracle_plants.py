@@ -1,0 +1,33 @@
+"""The pins bind the oracle: each of these plausible mistakes, planted in
+the oracle at compile time (ORACLE_PLANT=k), makes the paper-based pins of
+test_oracle_pins.py and test_golden.py fail (the regression fixtures are
+left out, since they would catch any change at all)."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+PLANTS = {
+    1: "the sign of q_x in the moment equilibria (Eq. 14)",
+    2: "the (c.u) c term of the Guo forcing (Eq. 12) dropped",
+    3: "the diagonal weights 1/18 instead of 1/36 (Eq. 13)",
+    4: "the 1/2 of the eta-stable penalized velocity (Eq. 22) dropped",
+    5: "RK4 reduced to forward Euler",
+    6: "the sign of the momentum-exchange torque (Eq. 27)",
+    7: "the sign of the moving-wall term of the bounce-back",
+}
+
+
+@pytest.mark.parametrize("k", sorted(PLANTS))
+def test_pins_catch_planted_mistake(k):
+    env = dict(os.environ, VPLBM_ORACLE_PLANT=str(k))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
+                        "-k", "not regression", "tests/test_oracle_pins.py", "tests/test_golden.py"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    # exit status 1: tests ran and one failed (not a collection or build error)
+    assert r.returncode == 1, f"plant {k} ({PLANTS[k]}) not caught:\n{r.stdout[-3000:]}\n{r.stderr[-2000:]}"
+    failed = [line for line in r.stdout.splitlines() if line.startswith("FAILED")]
+    assert failed, r.stdout[-2000:]
