@@ -385,14 +385,14 @@ static double pulled(const orc_sim *s, int a, int i, int j)
         if (kind == ORC_PERIODIC) {
             si = (si + nx) % nx;
         } else if (kind == ORC_ZEROGRAD) {
-            return FT(a, i, sj);
+            return FT(a, i, PLANT(8) ? j : sj);
         } else if (kind == ORC_CONVECTIVE) {
             /* advection of f_a out of the domain, d f/dt + U d f/dx = 0,
              * implicit in time and upwind in space between the outlet node
              * and its inner neighbour (whose pulled value is the
              * zero-gradient one): f(N, n+1) = (f(N, n) + U f(N-1, n+1)) / (1 + U) */
             const double U = s->lat.bc_u[side][0];
-            return (s->conv_prev[(size_t)a * ny + j] + U * FT(a, i, sj)) / (1.0 + U);
+            return (s->conv_prev[(size_t)a * ny + j] + U * FT(a, i, PLANT(8) ? j : sj)) / (1.0 + U);
         } else {
             double val = FT(OPP[a], i, j);
             if (kind == ORC_VELOCITY) {

@@ -526,6 +526,72 @@ def test_convective_outlet_limits():
     assert np.max(np.abs((rho_f - rho_r)[:, :-1])) == 0.0
 
 
+def _streaming_only(east, south, north, nx=13, ny=9, seed=41):
+    # BGK at relaxation rate 0 with no body and no forcing: the collision
+    # f - 0 (f - f_eq) + (1 - 0) F with F = 0 returns f exactly, so the
+    # state after one step is the pulled populations of Eq. 18 themselves
+    p = _outlet_channel(nx, ny, east)
+    p["collision"] = "bgk"
+    p["s"] = [0.0] * 9
+    p["bc"]["south"] = south
+    p["bc"]["north"] = north
+    f0 = wl.random_populations(nx, ny, seed=seed, amp=0.03, u_amp=0.05)
+    sim = oracle.OracleSim(p)
+    sim.set_populations(f0)
+    sim.step(1)
+    return f0, sim.populations(), p
+
+
+@pytest.mark.parametrize("walls", ["noslip", "moving"])
+def test_zero_gradient_outlet_is_the_inner_column(walls):
+    # Reading B2 (zero-gradient outlet, d f / d x = 0): every inward
+    # population (c_ax = -1) pulled at the outlet column nx - 1 equals the one
+    # pulled at column nx - 2 of the same row, i.e. the post-collision value
+    # at (nx - 1, j - c_ay).  Where j - c_ay is outside the lattice, the
+    # south / north rule takes over at both columns (reading B3): half-way
+    # bounce-back f_a = f~_abar plus the moving-wall term 6 w_a rho0 c_a . u_w.
+    c, w, _, _ = oracle.constants()
+    opp = [next(b for b in range(9) if (c[b] == -c[a]).all()) for a in range(9)]
+    uw = {"south": (0.013, 0.0), "north": (-0.021, 0.0)} if walls == "moving" else {"south": (0, 0), "north": (0, 0)}
+    wall = lambda side: {"kind": "velocity" if walls == "moving" else "noslip", "u": uw[side]}
+    nx, ny = 13, 9
+    f0, f1, _ = _streaming_only({"kind": "zerograd"}, wall("south"), wall("north"), nx, ny)
+    inward = [a for a in range(9) if c[a, 0] == -1]
+    assert len(inward) == 3
+    checked_inside = checked_wall = 0
+    for a in inward:
+        for j in range(ny):
+            sj = j - c[a, 1]
+            if 0 <= sj < ny:
+                assert f1[a, j, nx - 1] == f1[a, j, nx - 2] == f0[a, sj, nx - 1], (a, j)
+                checked_inside += 1
+            else:
+                u = uw["south" if sj < 0 else "north"]
+                for i in (nx - 2, nx - 1):
+                    expect = f0[opp[a], j, i] + 6.0 * w[a] * (c[a, 0] * u[0] + c[a, 1] * u[1])
+                    assert abs(f1[a, j, i] - expect) <= 1e-16, (a, j, i)
+                checked_wall += 1
+    assert checked_inside == 3 * ny - 2 and checked_wall == 2
+
+
+def test_convective_outlet_upwind_value_is_the_inner_column():
+    # The convective rule's upwind value f(N - 1, n + 1) is the population
+    # pulled at column nx - 2 of the same row (the shifted source row
+    # j - c_ay), and its previous value at step 0 is the given population at
+    # the outlet node: f(N, 1) = (f0(N, j) + U f0(N, j - c_ay)) / (1 + U).
+    c, _, _, _ = oracle.constants()
+    nx, ny, U = 13, 9, 0.37
+    noslip = {"kind": "noslip", "u": (0.0, 0.0)}
+    f0, f1, _ = _streaming_only({"kind": "convective", "u": (U, 0.0)}, noslip, noslip, nx, ny)
+    for a in (a for a in range(9) if c[a, 0] == -1):
+        for j in range(ny):
+            sj = j - c[a, 1]
+            if 0 <= sj < ny:
+                expect = (f0[a, j, nx - 1] + U * f0[a, sj, nx - 1]) / (1.0 + U)
+                assert abs(f1[a, j, nx - 1] - expect) <= 1e-17, (a, j)
+                assert f1[a, j, nx - 2] == f0[a, sj, nx - 1]
+
+
 def _ellipse_sim(a, b, theta, x=20.37, y=15.61, nx=41, ny=31):
     body = {"radius": a, "radius_b": b, "shape": "ellipse", "x": x, "y": y, "theta": theta,
             "motion": "fixed"}

@@ -18,6 +18,7 @@ PLANTS = {
     5: "RK4 reduced to forward Euler",
     6: "the sign of the momentum-exchange torque (Eq. 27)",
     7: "the sign of the moving-wall term of the bounce-back",
+    8: "the outlet's source row j instead of j - c_ay (zero-gradient and convective rules)",
 }
 
 
