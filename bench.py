@@ -39,17 +39,24 @@ BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36}   # 9 loads + 9 stores of on
 PREC_ID = {"f64": 0, "f32": 1, "f16": 2}
 LEGS = ("f64", "f16", "batched", "adjoint", "sedimenting", "paper", "several")   # comparison legs after the headline
 FALLBACK_HBM_GBS = 6800.0
+REPEATS = 5   # timed regions of K steps; the line reports the median
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 CSRC = os.path.join(ROOT, "paper_1905_05110_gb300", "csrc")
 
 
-def kernel_name(prec: str, launch) -> str:
-    if launch[0] == "tma":
+def dominant_kernel(prec: str, launch, kinds: dict) -> str:
+    """The step kernel that made most of the node updates of a timed region,
+    from the launches of each kind made inside it (MRT collision, disk)."""
+    work = {"two_step": 2 * kinds.get("two_step", 0), "one_step": kinds.get("one_step", 0),
+            "tma": kinds.get("tma", 0)}
+    top = max(work, key=work.get)
+    if top == "two_step":
+        return f"vp_mrt_step2<{PREC_ID[prec]}, 0, 0>"
+    if top == "tma":
         return f"vp_mrt_step_tma<{PREC_ID[prec]}>"
-    if launch[0] == "fused2":
-        return f"vp_mrt_step2<{PREC_ID[prec]}, 0, 0>"   # MRT collision, disk
-    minb = {"scalar": 4, "scalar48": 5, "scalar40": 6}[launch[0]]
-    return f"vp_mrt_step<{PREC_ID[prec]}, {minb}, 0, 0>"   # MRT collision, disk
+    # single steps of a two-step choice run the 40-register kernel
+    minb = {"scalar": 4, "scalar48": 5, "scalar40": 6, "fused2": 6, "tma": 6}[launch[0]]
+    return f"vp_mrt_step<{PREC_ID[prec]}, {minb}, 0, 0>"
 
 
 def workload(name: str) -> dict:
@@ -64,6 +71,16 @@ def workload(name: str) -> dict:
     if name == "several_bodies_2048x1024":
         return wl.several_bodies()
     raise SystemExit(f"unknown workload {name}")
+
+
+def bench_config(p: dict, prec: str, world: int) -> dict:
+    """The workload's config, the same on both arms of the comparison."""
+    pop_mb = p["nx"] * p["ny"] * BYTES_PER_NODE[prec] / 1e6   # read + written per step
+    return {"workload": p["name"], "nx": p["nx"], "ny": p["ny"],
+            "storage": {"f32": "f32 deviation", "f16": "f16 deviation", "f64": "f64"}[prec],
+            "parallelism": f"replicas x{world}",
+            "l2": f"not flushed: populations {pop_mb:.0f} MB read+write per step > 129 MB L2"
+                  if pop_mb > 129 else f"not flushed: populations {pop_mb:.0f} MB per step fit the 129 MB L2"}
 
 
 def dist_env():
@@ -246,7 +263,7 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": p["name"], "nx": p["nx"], "ny": p["ny"]},
+            "config": bench_config(p, args.precision, world),
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -282,31 +299,46 @@ def run_ours(args, rank, world, local_rank):
     sim.step(args.warmup)
     sim.sync()
 
-    launches0 = sim.launches
+    # REPEATS timed regions of exactly K steps each (device-synchronized on
+    # both sides); the line reports the median one, with the launches of each
+    # kernel kind made inside it
+    samples = []
     with ClockSampler(local_rank) as clocks:
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        dt = time_device(sim, args.steps, stream, torch)
-        torch.cuda.synchronize()
-    launches = sim.launches - launches0
+        for _ in range(REPEATS):
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            k0 = sim.kernel_launches()
+            t = time_device(sim, args.steps, stream, torch)
+            torch.cuda.synchronize()
+            k1 = sim.kernel_launches()
+            samples.append((max_over_ranks(t, world, dev, torch), {k: k1[k] - k0[k] for k in k1}))
     sim.sync()
-    dt = max_over_ranks(dt, world, dev, torch)
+    times = sorted(t for t, _ in samples)
+    dt, kinds = next(s for s in samples if s[0] == times[REPEATS // 2])
+    launches = sum(kinds.values())
     value = world * nodes * args.steps / dt / 1e6
     clock = clocks.summary()
 
-    # roofline of the fused step kernel (the only kernel in the timed region)
+    # roofline of the step kernel that did most of the region's node updates
+    # (a two-step launch does the work, and the algorithmic bytes, of two
+    # steps; the one-thread lookahead launches move no lattice bytes)
     peak, peak_kind = measured_peak()
-    # a two-step launch does the work (and the algorithmic bytes) of two steps
-    steps_per_launch = 2 if launch[0] == "fused2" else 1
-    per_launch = dt / (args.steps / steps_per_launch)
-    achieved = steps_per_launch * BYTES_PER_NODE[prec] * nodes / per_launch / 1e9
-    kname = kernel_name(prec, launch)
+    kname = dominant_kernel(prec, launch, kinds)
+    steps_per_launch = 2 if kname.startswith("vp_mrt_step2<") else 1
+    algorithmic = BYTES_PER_NODE[prec] * nodes * args.steps
+    achieved = algorithmic / dt / 1e9
     traffic = profiled_traffic(kname, args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                 "kernel": kname, "algorithmic_bytes_per_launch": steps_per_launch * BYTES_PER_NODE[prec] * nodes,
+                "launches_in_region": kinds,
                 "kernel_source_sha256_16": kernel_source_hash(kname)}
+    repeats = {"n": REPEATS, "ms_per_step": [t / args.steps * 1e3 for t, _ in samples],
+               "median_ms_per_step": dt / args.steps * 1e3,
+               "spread": (times[-1] - times[0]) / dt,
+               "mlups_min_max": [world * nodes * args.steps / times[-1] / 1e6,
+                                 world * nodes * args.steps / times[0] / 1e6]}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -362,10 +394,7 @@ def run_ours(args, rank, world, local_rank):
                 "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec != "f64" else "f64",
                 "data": "synthetic",
-                "config": {"workload": p["name"], "nx": p["nx"], "ny": p["ny"],
-                           "storage": {"f32": "f32 deviation", "f16": "f16 deviation", "f64": "f64"}[prec],
-                           "launch": list(launch), "parallelism": f"replicas x{world}",
-                           "l2": "not flushed: populations 151 MB read+write per step > 129 MB L2"},
+                "config": bench_config(p, prec, world), "launch": list(launch), "repeats": repeats,
                 "roofline": roofline, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clock, "compare": compare}
         print(json.dumps(line), flush=True)

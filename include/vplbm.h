@@ -279,12 +279,19 @@ vplbm_status vplbm_get_body_k(vplbm_ctx *ctx, int k, double q[3], double v[3], l
  *                          step n on its 64 x 8 tile and a one-node ring
  *                          around it into shared memory, then step n + 1
  *                          from there, so HBM is read and written once per
- *                          two steps.  Runs of 32 steps from an even step
- *                          use it; other steps run the 40-register scalar
- *                          kernel on the (block_x, block_y) given to
- *                          vplbm_set_launch (0 x 0: the current blocks).
- *                          Its populations equal the scalar kernel's bit
- *                          for bit.
+ *                          two steps.  A launch advances the state by
+ *                          two steps but the two population buffers by
+ *                          one, so vplbm_step issues them in pairs: every
+ *                          call of 4 or more steps runs as pairs of
+ *                          two-step launches (in 32-step graphs from an
+ *                          even step, as direct launches otherwise), except
+ *                          for the last nsteps mod 4 steps and, in a call
+ *                          of more than 32 steps from an odd step, its
+ *                          first step; those single steps run the
+ *                          40-register scalar kernel on the (block_x,
+ *                          block_y) given to vplbm_set_launch (0 x 0: the
+ *                          current blocks).  Its populations equal the
+ *                          scalar kernel's bit for bit.
  * Nodes on the lattice edges and near the body always take the same code.
  * The results of different kernels agree to the rounding of the storage
  * precision. */
@@ -311,8 +318,29 @@ vplbm_status vplbm_autotune(vplbm_ctx *ctx, int steps_per_trial);
  * VPLBM_EUNSUPPORTED unless the TMA-staged kernel is selected. */
 vplbm_status vplbm_inject_wait_timeout(vplbm_ctx *ctx, int enable);
 
-/* Number of step-kernel launches made by vplbm_step since creation. */
+/* Number of step-kernel launches made by vplbm_step since creation
+ * (vplbm_load restores the count saved in the checkpoint). */
 vplbm_status vplbm_get_launch_count(vplbm_ctx *ctx, long long *launches);
+
+/* Kinds of kernel launches vplbm_step makes (an index into the counts of
+ * vplbm_get_kernel_launches):
+ *  VPLBM_LAUNCH_ONE_STEP   one time step on a scalar step kernel (any
+ *                          register budget, shape, or several bodies);
+ *  VPLBM_LAUNCH_TWO_STEP   two time steps on the two-step kernel;
+ *  VPLBM_LAUNCH_LOOKAHEAD  the one-thread launch that computes pose n + 1
+ *                          of a prescribed path ahead of a run of two-step
+ *                          launches (no lattice work);
+ *  VPLBM_LAUNCH_TMA        one time step on the TMA-staged kernel. */
+typedef enum {
+    VPLBM_LAUNCH_ONE_STEP = 0, VPLBM_LAUNCH_TWO_STEP = 1, VPLBM_LAUNCH_LOOKAHEAD = 2, VPLBM_LAUNCH_TMA = 3,
+    VPLBM_LAUNCH_KINDS = 4
+} vplbm_launch_kind;
+
+/* counts[k] := launches of kind k that vplbm_step made on this context
+ * since its creation (not saved in checkpoints).  Their sum equals the
+ * vplbm_get_launch_count increase over the same calls; a caller that reads
+ * the counts around a call learns which kernels ran it. */
+vplbm_status vplbm_get_kernel_launches(vplbm_ctx *ctx, long long counts[VPLBM_LAUNCH_KINDS]);
 
 /* Write / read a checkpoint: populations (storage precision), body state,
  * step counter and history ring.  vplbm_load requires a context created

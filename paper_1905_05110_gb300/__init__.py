@@ -26,7 +26,7 @@ __all__ = [
     "vplbm_get_populations", "vplbm_get_fields", "vplbm_get_fields_dev", "vplbm_get_history",
     "vplbm_get_body", "vplbm_create_bodies", "vplbm_get_num_bodies", "vplbm_get_history_body",
     "vplbm_get_body_k", "MAX_BODIES", "vplbm_set_launch", "vplbm_get_launch", "vplbm_autotune",
-    "vplbm_get_launch_count", "vplbm_save", "vplbm_load", "vplbm_last_error", "vplbm_version",
+    "vplbm_get_launch_count", "vplbm_get_kernel_launches", "LAUNCH_KINDS", "vplbm_save", "vplbm_load", "vplbm_last_error", "vplbm_version",
     "vplbm_step_noalloc", "BodyState", "vplbm_inject_wait_timeout", "Batch",
     "vplbm_batch_create", "vplbm_batch_destroy", "vplbm_batch_member", "vplbm_batch_step",
     "vplbm_batch_sync", "vplbm_batch_set_launch", "vplbm_batch_get_launch", "vplbm_batch_autotune",
@@ -132,6 +132,7 @@ _SIGS = {
     "vplbm_get_launch": (C.c_int, [_CTX, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "vplbm_autotune": (C.c_int, [_CTX, C.c_int]),
     "vplbm_get_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_longlong)]),
+    "vplbm_get_kernel_launches": (C.c_int, [_CTX, C.POINTER(C.c_longlong)]),
     "vplbm_inject_wait_timeout": (C.c_int, [_CTX, C.c_int]),
     "vplbm_save": (C.c_int, [_CTX, C.c_char_p]),
     "vplbm_load": (C.c_int, [_CTX, C.c_char_p]),
@@ -402,6 +403,17 @@ def vplbm_get_launch_count(ctx) -> int:
     return int(n.value)
 
 
+# Kinds of step-kernel launches (vplbm_launch_kind), in the order of the
+# counts of vplbm_get_kernel_launches.
+LAUNCH_KINDS = ("one_step", "two_step", "lookahead", "tma")
+
+
+def vplbm_get_kernel_launches(ctx) -> dict:
+    counts = (C.c_longlong * len(LAUNCH_KINDS))()
+    _check(load_library().vplbm_get_kernel_launches(ctx, counts))
+    return {k: int(counts[n]) for n, k in enumerate(LAUNCH_KINDS)}
+
+
 def vplbm_step_noalloc(lat: LatticeDesc, body: BodyDesc | None, populations_ptrs, state_ptr: int,
                        history_ptr: int | None, history_capacity: int, nsteps: int, stream: int = 0):
     """Allocation-free steps on caller-owned device buffers (see include/vplbm.h)."""
@@ -616,6 +628,10 @@ class Simulation:
     @property
     def launches(self) -> int:
         return vplbm_get_launch_count(self.ctx)
+
+    def kernel_launches(self) -> dict:
+        """Launches made so far by kind: one_step, two_step, lookahead, tma."""
+        return vplbm_get_kernel_launches(self.ctx)
 
     def adjoint(self, nsteps: int, window_start: int, w_cd: float = 1.0, w_cl: float = 0.0,
                 checkpoint_interval: int = 0):

@@ -240,29 +240,33 @@ cudaError_t launch_one(const vplbm_ctx *c, long long step, cudaStream_t stream)
     return launch_step(c->precision, p, c->bx, c->by, stream, minb);
 }
 
-// Launch L of a run of two-step launches that starts at an even step with
-// the state in f[0] and poses n, n + 1 in bs[0], bs[1]: even launches go
-// f[0] -> f[1] and take their poses from bs[0..1], writing the next pair to
-// bs[2..3]; odd launches go back.  After an even number of launches the
-// state, pose and lookahead pose are where single steps expect them.
-cudaError_t launch_two(const vplbm_ctx *c, int L, cudaStream_t stream)
+// Launch L of a run of two-step launches that starts at a step of parity P
+// with the state in f[P] and poses n, n + 1 in bs[P], bs[P ^ 1]: even
+// launches go f[P] -> f[P ^ 1] and take their poses from that pair of
+// slots, writing the next pair to bs[2 + P], bs[2 + (P ^ 1)]; odd launches
+// go back.  After an even number of launches the state, pose and lookahead
+// pose are where single steps of the same parity expect them (a two-step
+// launch advances the step by two, the buffers by one, so runs come in
+// pairs).
+cudaError_t launch_two(const vplbm_ctx *c, int L, int P, cudaStream_t stream)
 {
-    const int odd = L & 1;
+    const int odd = L & 1, src = P ^ odd;
     Fused2Params q;
     q.a = params_for(c, 0);
     q.b = params_for(c, 1);
     const int es = (int)elem_size(c->precision);
-    q.a.fin = c->f[odd];
-    q.a.fout = c->f[odd ^ 1];
+    q.a.fin = c->f[src];
+    q.a.fout = c->f[src ^ 1];
     set_planes(q.a, es);
-    q.b.fin = c->f[odd ^ 1];
-    q.b.fout = c->f[odd ^ 1];
+    q.b.fin = c->f[src ^ 1];
+    q.b.fout = c->f[src ^ 1];
     set_planes(q.b, es);
-    q.a.bs_in = c->bs + (odd ? 2 : 0);
-    q.b.bs_in = c->bs + (odd ? 3 : 1);
+    BodyState *cur = c->bs + (odd ? 2 : 0), *nxt = c->bs + (odd ? 0 : 2);
+    q.a.bs_in = cur + P;
+    q.b.bs_in = cur + (P ^ 1);
     q.a.bs_out = q.b.bs_out = nullptr;
-    q.next0 = c->bs + (odd ? 0 : 2);
-    q.next1 = c->bs + (odd ? 1 : 3);
+    q.next0 = nxt + P;
+    q.next1 = nxt + (P ^ 1);
     q.b.partials = c->partials + (size_t)c->max_parts * NPART;
     q.b.ticket = &c->ctrl->ticket[1];
     // convective outlet: step n reads the record of step n - 1 and step
@@ -270,8 +274,8 @@ cudaError_t launch_two(const vplbm_ctx *c, int L, cudaStream_t stream)
     // with the launch (the same slot would race with other blocks' reads);
     // step n's own record stays in each block's shared memory
     double *ob = static_cast<double *>(c->outlet);
-    q.a.conv_in = q.b.conv_in = ob + (size_t)odd * 3 * c->ny;
-    q.a.conv_out = q.b.conv_out = ob + (size_t)(odd ^ 1) * 3 * c->ny;
+    q.a.conv_in = q.b.conv_in = ob + (size_t)src * 3 * c->ny;
+    q.a.conv_out = q.b.conv_out = ob + (size_t)(src ^ 1) * 3 * c->ny;
     return launch_step_fused2(c->precision, q, stream);
 }
 
@@ -639,7 +643,7 @@ vplbm_status ensure_graph(vplbm_ctx *c)
     if (c->kernel == KERNEL_FUSED2) {
         // pose n + 1 ahead, then GRAPH_STEPS / 2 (even) two-step launches
         err = launch_lookahead(params_for(c, 0), c->capture);
-        for (int L = 0; L < GRAPH_STEPS / 2 && err == cudaSuccess; ++L) err = launch_two(c, L, c->capture);
+        for (int L = 0; L < GRAPH_STEPS / 2 && err == cudaSuccess; ++L) err = launch_two(c, L, 0, c->capture);
     } else {
         for (int k = 0; k < GRAPH_STEPS && err == cudaSuccess; ++k) err = launch_one(c, k, c->capture);
     }
@@ -658,22 +662,65 @@ vplbm_status ensure_graph(vplbm_ctx *c)
     return VPLBM_OK;
 }
 
+// One single step on the context's kernel choice (the 40-register scalar
+// kernel for a two-step choice).
+vplbm_status step_one(vplbm_ctx *c)
+{
+    CUDA_TRY(launch_one(c, c->nstep, c->stream));
+    c->kcount[c->kernel == KERNEL_TMA ? VPLBM_LAUNCH_TMA : VPLBM_LAUNCH_ONE_STEP] += 1;
+    c->nstep += 1;
+    c->launches += 1;
+    return VPLBM_OK;
+}
+
+// 4 * pairs steps as 2 * pairs two-step launches from the current step
+// (either parity), after a lookahead launch that computes pose n + 1.
+vplbm_status step_pairs(vplbm_ctx *c, long long pairs)
+{
+    const int P = (int)(c->nstep & 1);
+    CUDA_TRY(launch_lookahead(params_for(c, c->nstep), c->stream));
+    for (long long L = 0; L < 2 * pairs; ++L) CUDA_TRY(launch_two(c, (int)(L & 1), P, c->stream));
+    c->kcount[VPLBM_LAUNCH_LOOKAHEAD] += 1;
+    c->kcount[VPLBM_LAUNCH_TWO_STEP] += 2 * pairs;
+    c->nstep += 4 * pairs;
+    c->launches += 1 + 2 * pairs;
+    return VPLBM_OK;
+}
+
+// The time loop.  Graphs of GRAPH_STEPS steps from even steps; with the
+// two-step kernel, shorter runs (and runs from an odd step that a graph
+// cannot take) go as pairs of two-step launches, so every run of 4 or more
+// steps is made of two-step launches but for at most 3 single steps at its
+// end (and one at its start, from an odd step, before a graph).
 vplbm_status step_impl(vplbm_ctx *c, long long n)
 {
+    const bool two = c->kernel == KERNEL_FUSED2;
     while (n > 0) {
+        vplbm_status st = VPLBM_OK;
         if ((c->nstep & 1) == 0 && n >= GRAPH_STEPS) {
-            vplbm_status st = ensure_graph(c);
+            st = ensure_graph(c);
             if (st != VPLBM_OK) return st;
             CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
             c->nstep += GRAPH_STEPS;
             c->launches += graph_launches(c);
+            if (two) {
+                c->kcount[VPLBM_LAUNCH_LOOKAHEAD] += 1;
+                c->kcount[VPLBM_LAUNCH_TWO_STEP] += GRAPH_STEPS / 2;
+            } else {
+                c->kcount[c->kernel == KERNEL_TMA ? VPLBM_LAUNCH_TMA : VPLBM_LAUNCH_ONE_STEP] += GRAPH_STEPS;
+            }
             n -= GRAPH_STEPS;
+            continue;
+        }
+        if (two && n >= 4 && !((c->nstep & 1) && n > GRAPH_STEPS)) {
+            const long long pairs = (n < GRAPH_STEPS ? n : GRAPH_STEPS) / 4;
+            st = step_pairs(c, pairs);
+            n -= 4 * pairs;
         } else {
-            CUDA_TRY(launch_one(c, c->nstep, c->stream));
-            c->nstep += 1;
-            c->launches += 1;
+            st = step_one(c);
             n -= 1;
         }
+        if (st != VPLBM_OK) return st;
     }
     return VPLBM_OK;
 }
@@ -1026,6 +1073,13 @@ vplbm_status vplbm_get_launch_count(vplbm_ctx *c, long long *launches)
     return VPLBM_OK;
 }
 
+vplbm_status vplbm_get_kernel_launches(vplbm_ctx *c, long long counts[VPLBM_LAUNCH_KINDS])
+{
+    if (!c || !counts) return fail(VPLBM_EINVAL, "NULL argument");
+    for (int k = 0; k < VPLBM_LAUNCH_KINDS; ++k) counts[k] = c->kcount[k];
+    return VPLBM_OK;
+}
+
 vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
 {
     if (!c) return fail(VPLBM_EINVAL, "context is NULL");
@@ -1094,7 +1148,7 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
                     if (launch_lookahead(params_for(c, c->nstep), c->stream) != cudaSuccess)
                         st = fail(VPLBM_ECUDA, "autotune launch failed");
                     for (int L = 0; L < steps_per_trial / 2 && st == VPLBM_OK; ++L)
-                        if (launch_two(c, L, c->stream) != cudaSuccess) st = fail(VPLBM_ECUDA, "autotune launch failed");
+                        if (launch_two(c, L, 0, c->stream) != cudaSuccess) st = fail(VPLBM_ECUDA, "autotune launch failed");
                     c->nstep += steps_per_trial;
                 }
                 for (int s = 0; !two && s < steps_per_trial && st == VPLBM_OK; ++s) {

@@ -38,6 +38,7 @@ struct vplbm_ctx {
     cudaGraphExec_t graph = nullptr;
     int graph_kernel = -1, graph_bx = -1, graph_by = -1;
     long long launches = 0;
+    long long kcount[VPLBM_LAUNCH_KINDS] = {};   // launches by kernel kind (vplbm_launch_kind)
     // TMA-staged kernel (FP32/FP16 storage): tensor maps of the two
     // population buffers as sources, persistent grid size
     bool tma_ok = false;

@@ -279,3 +279,68 @@ def test_full_size_paper_cylinder_two_step_kernel_equals_one_step_kernel():
         assert rel_err(h2[:, REC[key]], h1[:, REC[key]]) < 1e-9, key
     one.close()
     two.close()
+
+
+# (first step, steps in one call) -> launches the call must make, by kind:
+# every call of 4 or more steps runs as pairs of two-step launches after one
+# lookahead launch, but for its last nsteps mod 4 steps and, for more than
+# 32 steps from an odd step, its first step (which takes it to an even step
+# for a 32-step graph).
+DISPATCH = {
+    (1, 20): {"two_step": 10, "lookahead": 1, "one_step": 0},
+    (0, 20): {"two_step": 10, "lookahead": 1, "one_step": 0},
+    (1, 7): {"two_step": 2, "lookahead": 1, "one_step": 3},
+    (3, 2): {"two_step": 0, "lookahead": 0, "one_step": 2},
+    (1, 32): {"two_step": 16, "lookahead": 1, "one_step": 0},
+    (1, 33): {"two_step": 16, "lookahead": 1, "one_step": 1},
+    (3, 50): {"two_step": 24, "lookahead": 2, "one_step": 2},
+}
+
+
+@pytest.mark.parametrize("case", ["channel_imposed", "paper_channel_cosine", "periodic_x_symmetry_y"])
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+@pytest.mark.parametrize("start,n", list(DISPATCH))
+def test_step_call_runs_two_step_pairs_from_any_step(case, precision, start, n):
+    # One call of n steps from step `start` against n calls of one step
+    # (each a single launch of the one-step kernel): the same populations
+    # bit for bit, the same poses and solid-node counts, and the launches
+    # the dispatch rule gives.
+    p = CASES[case]()
+    one = _make(p, precision, "fused2")
+    two = _make(p, precision, "fused2")
+    one.step(start)
+    two.step(start)
+    for _ in range(n):
+        one.step(1)
+    k0 = two.kernel_launches()
+    two.step(n)
+    k1 = two.kernel_launches()
+    made = {k: k1[k] - k0[k] for k in k1}
+    assert made == dict(DISPATCH[(start, n)], tma=0)
+    assert np.array_equal(one.populations(), two.populations())
+    if p.get("body"):
+        h1, h2 = one.history(), two.history()
+        for key in ("t", "x", "y", "theta", "vx", "vy", "omega", "n_solid"):
+            assert np.array_equal(h1[:, REC[key]], h2[:, REC[key]]), key
+        for key in ("fx", "fy", "torque"):
+            assert rel_err(h2[:, REC[key]], h1[:, REC[key]]) < 1e-9, key
+        q1, v1 = one.body_state()
+        q2, v2 = two.body_state()
+        assert np.array_equal(q1, q2) and np.array_equal(v1, v2)
+    one.close()
+    two.close()
+
+
+def test_launch_counts_by_kind_sum_to_launch_count():
+    p = CASES["channel_imposed"]()
+    sim = _make(p, "f32", "fused2")
+    for n in (3, 20, 64, 5):
+        sim.step(n)
+    k = sim.kernel_launches()
+    assert sum(k.values()) == sim.launches
+    sim.set_launch("scalar40", 256, 1)
+    k0, l0 = sim.kernel_launches(), sim.launches
+    sim.step(40)
+    k1 = sim.kernel_launches()
+    assert k1["one_step"] - k0["one_step"] == 40 == sim.launches - l0
+    sim.close()
