@@ -459,13 +459,15 @@ def run_other_workload(name, steps, torch, stream):
         if b["motion"] == "free":
             d["final_pose"] = [float(v) for v in h[-1, 6:9]]
             d["final_velocity"] = [float(v) for v in h[-1, 9:12]]
-            if "gravity" in p:   # settling: terminal velocity against the design value (Happel, Stokes regime)
+            if "gravity" in p:   # settling: terminal velocity against the design value v_s = Re_t nu / D
                 nu = (1.0 / p["s"][7] - 0.5) / 3.0
                 vt = float(-h[-max(1, steps // 20):, 10].mean())
                 d["terminal_vy_last_5pct"] = vt
                 d["terminal_re"] = vt * b["d_ref"] / nu
                 d["design_v_s"] = b["u_ref"]
                 d["terminal_over_design"] = vt / b["u_ref"]
+                d["gravity"] = p["gravity"]
+                d["gravity_over_happel"] = wl.SETTLING_G_FACTOR
         per_body.append(d)
     if len(bodies) == 1:
         out.update(per_body[0])

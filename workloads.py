@@ -174,16 +174,28 @@ def happel_kappa(h_tilde: float) -> float:
                   + 2.4056 * h**-6 - 4.5913 * h**-8)
 
 
+# Gravity of the sedimenting disk over the Happel (Stokes-regime) value for
+# the same design velocity.  Eqs. (33)/(35) leave out the inertial drag, so
+# at a terminal Reynolds number of 5 the disk settled at Re_t = 2.9 with the
+# Happel gravity; measured on the FP32 path (1024 x 4096, D = 32, density
+# ratio 1.5, 200 000 steps, mean of the last 5 %), Re_t was 4.45, 4.79,
+# 5.13 and 5.45 at 1.8, 2.0, 2.2 and 2.4 times it, and a quadratic through
+# those four points reaches 5.0 at 2.123.
+SETTLING_G_FACTOR = 2.123
+
+
 def sedimenting_disk(nx=1024, ny=4096, diameter=32.0, density_ratio=1.5,
                      re_terminal=5.0, tau=0.8, eta=1e-3, offset=1.0,
-                     steps=200_000) -> dict:
-    """Free disk settling in a closed box (translation + rotation)."""
+                     steps=200_000, g_factor=SETTLING_G_FACTOR) -> dict:
+    """Free disk settling in a closed box (translation + rotation).  The
+    gravity is Happel's for the design velocity v_s = Re_t nu / D, times
+    g_factor (1.0: the Stokes-regime relation alone)."""
     nu = (tau - 0.5) / 3.0
     mu = RHO0 * nu
     v_s = re_terminal * nu / diameter
     kappa = happel_kappa(nx / diameter)
-    # Eqs. (33)/(35) with the gravity factor restored
-    g = 16.0 * kappa * mu * v_s / (diameter**2 * (density_ratio - 1.0) * RHO0)
+    # Eqs. (33)/(35) with the gravity factor restored, then calibrated
+    g = g_factor * 16.0 * kappa * mu * v_s / (diameter**2 * (density_ratio - 1.0) * RHO0)
     radius = diameter / 2
     m, inertia = disk_mass(radius, density_ratio)
     x0 = (nx - 1) / 2.0 + offset
