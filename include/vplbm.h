@@ -435,7 +435,10 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *batch, int steps_per_trial);
  * pose records) is one static device array of about 260 KB that every GPU
  * loading this library holds until the process exits.  Its device address is
  * looked up on the first call on each device (with that device current), so
- * make that first call before any stream capture.  All calls share the
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process and belongs to the context that was current at
+ * that first call: do not use this entry point on a device after
+ * cudaDeviceReset (or from another context on it).  All calls share the
  * array: calls whose work overlaps on the GPU (other streams, other threads)
  * race on it and must be serialized by the caller.
  *
@@ -452,6 +455,9 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *batch, int steps_per_trial);
  *                      became non-positive or non-finite).
  *  history_dev         NULL, or a device ring of history_capacity records;
  *                      the record of step n goes to slot n % capacity.
+ * Buffers must be aligned: the population buffers to the storage element
+ * size, state_dev and history_dev to 8 bytes (VPLBM_EINVAL otherwise, before
+ * any device work).
  * Walls take uniform velocities only (bc[].ux_profile/uy_profile must be
  * NULL: VPLBM_EUNSUPPORTED).  A disk too large for the fixed scratch (radius
  * above about 450 lattice units) is rejected with VPLBM_ERANGE before any
@@ -469,6 +475,15 @@ vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const vplbm_body_
                                 void *const populations_dev[2], vplbm_body_state *state_dev,
                                 vplbm_record *history_dev, long long history_capacity,
                                 long long nsteps, void *cuda_stream);
+
+/* ---- diagnostics ---------------------------------------------------------
+ * y_dev[k] := the FP32 reciprocal the FP32 / FP16 step kernels use for
+ * 1/rho in u = j / rho (Eq. 22): the hardware reciprocal estimate refined
+ * by one Newton-Raphson step, r0 + r0 (1 - x r0) with fused multiply-adds.
+ * Subnormal inputs and outputs are flushed to zero.  x_dev and y_dev are
+ * device arrays of n floats (4-byte aligned; VPLBM_EINVAL otherwise);
+ * asynchronous on cuda_stream.  For tests of the reciprocal's error bound. */
+vplbm_status vplbm_eval_recip_f32(const float *x_dev, float *y_dev, long long n, void *cuda_stream);
 
 /* Message of the last failed call on this thread (never NULL). */
 const char *vplbm_last_error(void);

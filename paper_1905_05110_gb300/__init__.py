@@ -26,7 +26,7 @@ __all__ = [
     "vplbm_get_populations", "vplbm_get_fields", "vplbm_get_fields_dev", "vplbm_get_history",
     "vplbm_get_body", "vplbm_create_bodies", "vplbm_get_num_bodies", "vplbm_get_history_body",
     "vplbm_get_body_k", "MAX_BODIES", "vplbm_set_launch", "vplbm_get_launch", "vplbm_autotune",
-    "vplbm_get_launch_count", "vplbm_get_kernel_launches", "LAUNCH_KINDS", "vplbm_save", "vplbm_load", "vplbm_last_error", "vplbm_version",
+    "vplbm_get_launch_count", "vplbm_get_kernel_launches", "vplbm_eval_recip_f32", "LAUNCH_KINDS", "vplbm_save", "vplbm_load", "vplbm_last_error", "vplbm_version",
     "vplbm_step_noalloc", "BodyState", "vplbm_inject_wait_timeout", "Batch",
     "vplbm_batch_create", "vplbm_batch_destroy", "vplbm_batch_member", "vplbm_batch_step",
     "vplbm_batch_sync", "vplbm_batch_set_launch", "vplbm_batch_get_launch", "vplbm_batch_autotune",
@@ -133,6 +133,7 @@ _SIGS = {
     "vplbm_autotune": (C.c_int, [_CTX, C.c_int]),
     "vplbm_get_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_longlong)]),
     "vplbm_get_kernel_launches": (C.c_int, [_CTX, C.POINTER(C.c_longlong)]),
+    "vplbm_eval_recip_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
     "vplbm_inject_wait_timeout": (C.c_int, [_CTX, C.c_int]),
     "vplbm_save": (C.c_int, [_CTX, C.c_char_p]),
     "vplbm_load": (C.c_int, [_CTX, C.c_char_p]),
@@ -412,6 +413,11 @@ def vplbm_get_kernel_launches(ctx) -> dict:
     counts = (C.c_longlong * len(LAUNCH_KINDS))()
     _check(load_library().vplbm_get_kernel_launches(ctx, counts))
     return {k: int(counts[n]) for n, k in enumerate(LAUNCH_KINDS)}
+
+
+def vplbm_eval_recip_f32(x_ptr: int, y_ptr: int, n: int, stream: int = 0):
+    """y[k] := the step kernels' FP32 reciprocal of x[k] (device arrays)."""
+    _check(load_library().vplbm_eval_recip_f32(C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(n), C.c_void_p(stream)))
 
 
 def vplbm_step_noalloc(lat: LatticeDesc, body: BodyDesc | None, populations_ptrs, state_ptr: int,

@@ -15,6 +15,7 @@
 // The step kernel itself is the one every other entry point uses
 // (launch_step); only where its scratch lives differs.
 #include <math.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -121,6 +122,12 @@ extern "C" vplbm_status vplbm_step_noalloc(const vplbm_lattice_desc *lat, const 
     if (st != VPLBM_OK) return st;
     if (!populations_dev || !populations_dev[0] || !populations_dev[1] || !state_dev)
         return report_error(VPLBM_EINVAL, "populations_dev[0..1] and state_dev must be device pointers");
+    // misaligned buffers would fault in the kernels: refuse them here
+    const uintptr_t es = lat->precision == VPLBM_F64 ? 8 : (lat->precision == VPLBM_F32_DEV ? 4 : 2);
+    if ((uintptr_t)populations_dev[0] % es || (uintptr_t)populations_dev[1] % es)
+        return report_error(VPLBM_EINVAL, "populations_dev[0..1] must be aligned to the storage element size");
+    if ((uintptr_t)state_dev % 8 || (uintptr_t)history_dev % 8)
+        return report_error(VPLBM_EINVAL, "state_dev and history_dev must be 8-byte aligned");
     if (nsteps < 0) return report_error(VPLBM_EINVAL, "nsteps must be >= 0");
     if (history_dev && history_capacity < 1) return report_error(VPLBM_EINVAL, "history_capacity must be >= 1");
     for (int s = 0; s < 4; ++s)
