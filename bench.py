@@ -214,8 +214,60 @@ def time_device(sim, steps, stream, torch):
     return e0.elapsed_time(e1) / 1e3
 
 
-def cpu_baseline(problem: dict, budget_s: float = 12.0):
-    """The FP64 oracle, single-threaded, on time steps of the same lattice."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def strip_problems(p: dict, n: int) -> list:
+    """The workload cut into n disjoint full-width strips of rows, each an
+    independent lattice (no-slip walls at its cut edges); the body stays in
+    the strip that holds its centre, at the same place relative to it."""
+    ny = p["ny"]
+    bounds = [round(k * ny / n) for k in range(n + 1)]
+    out = []
+    for k in range(n):
+        lo, hi = bounds[k], bounds[k + 1]
+        q = dict(p, ny=hi - lo, bc=dict(p["bc"], south={"kind": "noslip", "u": (0.0, 0.0)},
+                                        north={"kind": "noslip", "u": (0.0, 0.0)}))
+        b = p.get("body")
+        q["body"] = dict(b, y=b["y"] - lo) if b is not None and lo <= b["y"] < hi else None
+        out.append(q)
+    return out
+
+
+def _oracle_strip(args):
+    """One host process: `warmup` untimed then `steps` timed FP64 oracle
+    steps of one strip; returns (node updates timed, seconds)."""
+    q, warmup, steps = args
+    import oracle
+    sim = oracle.OracleSim(q, hist_cap=16)
+    u = q["init"]["u"]
+    shape = (q["ny"], q["nx"])
+    sim.init_equilibrium(np.ones(shape), np.full(shape, u[0]), np.full(shape, u[1]))
+    sim.step(warmup)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    return q["nx"] * q["ny"] * steps, time.perf_counter() - t0
+
+
+def oracle_all_cores(p: dict, warmup: int, steps: int, cores: int):
+    """The oracle as it stands (single-threaded C) in one spawned process per
+    host core, each on its own strip of the workload: node updates of all
+    strips over the slowest strip's time (MLUPS)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_strip, [(q, warmup, steps) for q in strip_problems(p, cores)])
+    return sum(r[0] for r in res) / max(r[1] for r in res) / 1e6
+
+
+def cpu_baseline(problem: dict, budget_s: float = 10.0):
+    """The FP64 oracle on the host cores: one thread on time steps of the
+    full lattice, and one process per core on the lattice cut into strips."""
     import oracle
     sim = oracle.OracleSim(problem, hist_cap=64)
     u = problem["init"]["u"]
@@ -232,40 +284,36 @@ def cpu_baseline(problem: dict, budget_s: float = 12.0):
     if extra == 0:
         dt = one
     nodes = problem["nx"] * problem["ny"]
-    return {"value": nodes * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} FP64 time steps of the full {problem['nx']}x{problem['ny']} lattice "
-                      f"(after 1 untimed), plain C, one thread"}
+    one_core = nodes * steps / dt / 1e6
+    cores = host_cores()
+    # as many steps of the full lattice (in strips) as one core would do in
+    # about budget_s seconds on its strip
+    strip_steps = max(2, int(budget_s * one_core * 1e6 * cores / nodes))
+    all_cores = oracle_all_cores(problem, 1, strip_steps, cores)
+    return {"value": all_cores, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value_1core": one_core, "value_allcores": all_cores,
+            "sample": f"all cores: {strip_steps} FP64 time steps of the full {problem['nx']}x{problem['ny']} lattice "
+                      f"cut into {cores} full-width strips, one single-threaded oracle process per core, "
+                      f"after 1 untimed step (node updates of all strips over the slowest strip's time); "
+                      f"one core: {steps} steps of the whole lattice after 1 untimed"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     p = workload(args.workload)
-    import oracle
+    cores = host_cores()
+    value = oracle_all_cores(p, args.warmup, args.steps, cores)
+    desc = (f"{args.steps} FP64 oracle time steps (after {args.warmup} untimed) of the full "
+            f"{p['nx']}x{p['ny']} lattice cut into {cores} full-width strips, one single-threaded "
+            f"oracle process per host core; node updates of all strips over the slowest strip's time")
     nodes = p["nx"] * p["ny"]
-    per_step_est = nodes * 0.5e-6
-    sample = p
-    if (args.steps + args.warmup) * per_step_est > 150:
-        # bounded sample: a strip of the same lattice (same physics per node)
-        ny = max(16, int(p["ny"] * 150 / ((args.steps + args.warmup) * per_step_est)))
-        sample = dict(p, ny=ny, body=dict(p["body"], y=ny / 2.0))
-    sim = oracle.OracleSim(sample, hist_cap=max(16, args.steps + args.warmup))
-    u = sample["init"]["u"]
-    shape = (sample["ny"], sample["nx"])
-    sim.init_equilibrium(np.ones(shape), np.full(shape, u[0]), np.full(shape, u[1]))
-    sim.step(args.warmup)
-    t0 = time.perf_counter()
-    sim.step(args.steps)
-    dt = time.perf_counter() - t0
-    value = sample["nx"] * sample["ny"] * args.steps / dt / 1e6
-    desc = (f"{args.steps} FP64 oracle time steps of a {sample['nx']}x{sample['ny']} lattice "
-            f"({'full workload' if sample is p else 'strip of the workload'}), one thread")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": nodes / (value * 1e6) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": bench_config(p, args.precision, world),
             "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -503,85 +551,179 @@ def run_sharded_sweep(args, torch, stream, rank, world, dev):
 
 
 def run_batched(args, torch, stream):
-    """The 64-member spring-mounted sweep (uneven lattices) in one launch per
-    step, against the same members on the FP64 plain path, with the C_D / C_L
-    difference of one member over a run stated."""
+    """The 64-member spring-mounted sweep (uneven lattices, reduced velocity
+    in [3, 12], m/(rho pi R^2) = 10): both batch modes timed over the same
+    2 000 steps, the full 50 000-step run on the autotuned mode with the
+    response of every member (A*, omega*, k*_eff of Sec. 3.3 over the second
+    half), the FP64 plain path (one member after another) over 2 000 steps,
+    and the FP32 records of the smallest, a median and the largest member
+    against their FP64 runs."""
     import paper_1905_05110_gb300 as vp
+    from paper_1905_05110_gb300.viv import viv_response
     probs = wl.viv_sweep()
+    steps = probs[0]["steps"]
     nodes = sum(p["nx"] * p["ny"] for p in probs)
-    b = vp.Batch(probs, precision="f32", history_capacity=4096, stream=stream)
+    peak, _ = measured_peak()
+    k_cmp = 2000
+    b = vp.Batch(probs, precision="f32", history_capacity=steps + 64, stream=stream)
     b.init_from_problems()
-    shape = b.autotune(16)
+    tuned = b.autotune(32)
+    modes = {}
+    for mode in ("branches", "tiles"):
+        b.set_mode(mode)
+        b.init_from_problems()
+        b.step(64)
+        b.sync()
+        t = time_device(b, k_cmp, stream, torch)
+        b.sync()
+        gbs = 72 * nodes * k_cmp / t / 1e9
+        modes[mode] = {"mlups": nodes * k_cmp / t / 1e6, "steps": k_cmp, "gbs_algorithmic": gbs,
+                       "frac_of_hbm": gbs / peak, "launch": list(b.launch()[:3]) if mode == "tiles" else
+                       list(b.members[0].launch())}
+    b.set_mode(tuned[0])
     b.init_from_problems()
-    b.step(64)
     b.sync()
-    k = max(64, min(512, args.steps // 50))
-    t = time_device(b, k, stream, torch)
+    t = time_device(b, steps, stream, torch)
     b.sync()
-    mlups = nodes * k / t / 1e6
-    # FP64 plain path: every member on its own, a few steps each
+    mlups = nodes * steps / t / 1e6
+    half = steps // 2
+    rows = []
+    hists = []
+    for p, m in zip(probs, b.members):
+        h = m.history(0, steps)
+        hists.append(h)
+        body = p["body"]
+        u_star = body["u_ref"] / (math.sqrt(body["stiff"][1] / body["mass"]) / (2 * math.pi) * body["d_ref"])
+        r = viv_response(h[half:, 7], body["q0"][1], body["d_ref"], body["u_ref"], body["mass"],
+                         body["stiff"][1])
+        rows.append({"lattice": f"{p['nx']}x{p['ny']}", "u_star": round(u_star, 6), **r,
+                     "mean_cd": float(h[half:, 4].mean()), "rms_cl": float(np.sqrt((h[half:, 5] ** 2).mean()))})
+    # FP64 plain path: every member on its own over the same 2 000 steps
     t64 = 0.0
-    k64 = 8
     for p in probs:
         s64 = vp.Simulation(p, precision="f64", history_capacity=64, stream=stream)
         s64.init_from_problem()
         s64.step(2)
         s64.sync()
-        t64 += time_device(s64, k64, stream, torch)
+        t64 += time_device(s64, k_cmp, stream, torch)
         s64.close()
-    mlups64 = nodes * k64 / t64 / 1e6
-    # accuracy: member 0 over 3000 steps, FP32 batched vs FP64
+    mlups64 = nodes * k_cmp / t64 / 1e6
+    # accuracy: FP32 batched records against FP64 runs of the same members
     acc_steps = 3000
-    m = b.members[0]
-    b.init_from_problems()
-    b.step(acc_steps)
-    h32 = m.history(0, acc_steps)
-    s64 = vp.Simulation(probs[0], precision="f64", history_capacity=acc_steps, stream=stream)
-    s64.init_from_problem()
-    s64.step(acc_steps)
-    h64 = s64.history(0, acc_steps)
-    s64.close()
-    half = acc_steps // 2
-    cd32, cd64 = h32[half:, 4].mean(), h64[half:, 4].mean()
+    order = sorted(range(len(probs)), key=lambda k: probs[k]["nx"] * probs[k]["ny"])
+    acc = {}
+    for label, k in (("smallest", order[0]), ("median", order[len(order) // 2]), ("largest", order[-1])):
+        s64 = vp.Simulation(probs[k], precision="f64", history_capacity=acc_steps, stream=stream)
+        s64.init_from_problem()
+        s64.step(acc_steps)
+        h64 = s64.history(0, acc_steps)
+        s64.close()
+        h32 = hists[k][:acc_steps]
+        hh = acc_steps // 2
+        acc[label] = {"member": k, "lattice": f"{probs[k]['nx']}x{probs[k]['ny']}",
+                      "max_abs_dcl": float(np.max(np.abs(h32[:, 5] - h64[:, 5]))),
+                      "max_abs_dcd": float(np.max(np.abs(h32[:, 4] - h64[:, 4]))),
+                      "p99_abs_dcl": float(np.percentile(np.abs(h32[:, 5] - h64[:, 5]), 99)),
+                      "p99_abs_dcd": float(np.percentile(np.abs(h32[:, 4] - h64[:, 4]), 99)),
+                      "steps_solid_count_differs": int(np.sum(h32[:, 15] != h64[:, 15])),
+                      "max_abs_dy_over_d": float(np.max(np.abs(h32[:, 7] - h64[:, 7])) / probs[k]["body"]["d_ref"]),
+                      "mean_cd_rel_diff_2nd_half": float(abs(h32[hh:, 4].mean() - h64[hh:, 4].mean())
+                                                         / abs(h64[hh:, 4].mean()))}
     b.close()
-    return {"members": len(probs), "nodes": nodes, "mlups": mlups, "steps": k, "launch": list(shape),
-            "gbs_algorithmic": 72 * nodes * k / t / 1e9,
-            "f64_plain_sequential_mlups": mlups64, "speedup_vs_f64_plain": mlups / mlups64,
-            "accuracy_member0_3000_steps": {
-                "lattice": f"{probs[0]['nx']}x{probs[0]['ny']}",
-                "max_abs_dcl": float(np.max(np.abs(h32[:, 5] - h64[:, 5]))),
-                "max_abs_dcd": float(np.max(np.abs(h32[:, 4] - h64[:, 4]))),
-                "mean_cd_rel_diff_2nd_half": float(abs(cd32 - cd64) / abs(cd64))}}
+    gbs = 72 * nodes * steps / t / 1e9
+    return {"members": len(probs), "nodes": nodes, "steps": steps, "mode": tuned[0], "launch": list(tuned),
+            "mlups": mlups, "gbs_algorithmic": gbs, "frac_of_hbm": gbs / peak, "seconds": t,
+            "modes_2000_steps": modes,
+            "f64_plain_sequential_mlups": mlups64, "f64_plain_steps": k_cmp,
+            "speedup_vs_f64_plain": mlups / mlups64,
+            "accuracy_vs_f64_3000_steps": acc,
+            "response_window": [half, steps],
+            "response": rows,
+            "paper_context_k_eff": {"note": "Sec. 3.3 (D = 41, U0 = 0.0488, another lattice): context only",
+                                    "k_star": [9, 19, 28], "k_eff_star": [0.058, 3.20, 16.37]}}
+
+
+def _objective_f64(p, nsteps, w0, stream, torch):
+    """J = mean C_D + RMS C_L over [w0, nsteps) of an FP64 forward run, and
+    the run's CUDA-event time."""
+    import paper_1905_05110_gb300 as vp
+    g = vp.Simulation(p, precision="f64", history_capacity=nsteps + 8, stream=stream)
+    g.init_from_problem()
+    t = time_device(g, nsteps, stream, torch)
+    h = g.history(0, nsteps)
+    g.close()
+    return float(h[w0:, 4].mean() + np.sqrt(np.mean(h[w0:, 5] ** 2))), t
 
 
 def run_adjoint(args, torch, f64_compare):
-    """Gradient of mean C_D + RMS C_L over the second half of 1024 x 512 runs
-    w.r.t. the 512-entry inlet profile, eta, s_nu, s_e (515 values), by the
-    FP32 discrete adjoint with checkpoints every 141 steps."""
+    """The gradient workload as specified: 1024 x 512 imposed-oscillation
+    disk, 20 000 steps, checkpoints every 141 steps; gradient of
+    J = mean C_D + RMS C_L over the second half w.r.t. the 512-entry inlet
+    profile, eta, s_nu and s_e (515 values), by the FP32 discrete adjoint
+    (the timed product path) and the FP64 one, each checked against central
+    finite differences of FP64 forward runs on the GPU along 8 seeded random
+    unit directions, h = 1e-4 of each parameter's scale."""
     import paper_1905_05110_gb300 as vp
     p = wl.adjoint_disk()
-    nsteps = min(p["steps"], max(2000, args.steps // 2))
-    ck = p["checkpoint_interval"] if nsteps == p["steps"] else max(1, int(round(nsteps ** 0.5)))
+    nsteps, ck = p["steps"], p["checkpoint_interval"]
+    w0 = nsteps // 2
     nodes = p["nx"] * p["ny"]
-    sim = vp.Simulation(p, precision="f32", history_capacity=nsteps + 8)
-    sim.init_from_problem()
-    launch = sim.autotune(8)   # the forward and recomputed steps use the tuned step kernel
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    grad, js = sim.adjoint(nsteps, nsteps // 2, 1.0, 1.0, checkpoint_interval=ck)
-    dt = time.perf_counter() - t0
-    sim.init_from_problem()
-    t_fwd = time_device(sim, nsteps, torch.cuda.current_stream(), torch)
-    sim.close()
     nparams = p["ny"] + 3
-    out = {"lattice": f"{p['nx']}x{p['ny']}", "steps": nsteps, "checkpoint_interval": ck, "params": nparams,
-           "seconds": dt, "forward_f32_seconds": t_fwd, "J": js, "launch": list(launch),
-           "speedup_vs_fd_f32_forward": 2 * nparams * t_fwd / dt,
-           "grad_norm": float(np.linalg.norm(grad))}
-    if f64_compare:
-        t_fd64 = 2 * nparams * nodes * nsteps / (f64_compare["mlups"] * 1e6)
-        out["speedup_vs_fd_f64_plain"] = t_fd64 / dt
-    return out
+    stream = torch.cuda.current_stream()
+    peak, _ = measured_peak()
+    grads, js, secs = {}, {}, {}
+    for prec in ("f32", "f64"):
+        sim = vp.Simulation(p, precision=prec, history_capacity=nsteps + 8, stream=stream)
+        sim.init_from_problem()
+        if prec == "f32":
+            launch = sim.autotune(8)   # the forward and recomputed steps use the tuned step kernel
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        grads[prec], js[prec] = sim.adjoint(nsteps, w0, 1.0, 1.0, checkpoint_interval=ck)
+        secs[prec] = time.perf_counter() - t0
+        if prec == "f32":
+            sim.init_from_problem()
+            t_fwd32 = time_device(sim, nsteps, stream, torch)
+        sim.close()
+    # central differences of FP64 forward runs
+    prof = p["bc"]["west"]["ux_profile"]
+    scale = np.concatenate([np.full(p["ny"], 0.04), [p["eta"], p["s"][7], p["s"][1]]])
+    rng = np.random.default_rng(2024)
+    h = 1e-4
+    rows, t_runs = [], []
+    for _ in range(8):
+        v = rng.standard_normal(nparams)
+        v /= np.linalg.norm(v)
+        dth = h * scale * v
+        jpm = []
+        for sign in (1.0, -1.0):
+            q = wl.with_params(p, u_in_profile=prof + sign * dth[:-3], eta=p["eta"] + sign * dth[-3],
+                               s_nu=p["s"][7] + sign * dth[-2], s_e=p["s"][1] + sign * dth[-1])
+            jv, tr = _objective_f64(q, nsteps, w0, stream, torch)
+            jpm.append(jv)
+            t_runs.append(tr)
+        fd = (jpm[0] - jpm[1]) / (2 * h)
+        a64 = float(grads["f64"] @ (scale * v))
+        a32 = float(grads["f32"] @ (scale * v))
+        rows.append({"fd": fd, "adjoint_f64": a64, "adjoint_f32": a32,
+                     "rel_diff_f64": abs(a64 - fd) / abs(fd), "rel_diff_f32": abs(a32 - fd) / abs(fd)})
+    t_fwd64 = float(np.mean(t_runs))
+    gbs = 216 * nodes * nsteps / secs["f32"] / 1e9
+    return {"lattice": f"{p['nx']}x{p['ny']}", "steps": nsteps, "window": [w0, nsteps], "checkpoint_interval": ck,
+            "params": nparams, "launch": list(launch),
+            "seconds": secs["f32"], "seconds_f64_adjoint": secs["f64"], "J": js["f32"], "J_f64": js["f64"],
+            "grad_norm": float(np.linalg.norm(grads["f32"])),
+            "grad_rel_diff_f32_vs_f64": float(np.linalg.norm(grads["f32"] - grads["f64"]) /
+                                              np.linalg.norm(grads["f64"])),
+            "gbs_at_216_bytes_per_node_step": gbs, "frac_of_hbm": gbs / peak,
+            "forward_f32_seconds": t_fwd32, "forward_f64_seconds_measured": t_fwd64,
+            "speedup_vs_fd_f64": 2 * nparams * t_fwd64 / secs["f32"],
+            "speedup_vs_fd_f64_how": "2 x 515 FP64 forward runs at the mean CUDA-event time of the 16 FD runs "
+                                     "measured here, over the FP32 adjoint's wall time",
+            "speedup_vs_fd_f32_forward": 2 * nparams * t_fwd32 / secs["f32"],
+            "fd_check": {"directions": 8, "h_relative": h, "seed": 2024,
+                         "max_rel_diff_f64": max(r["rel_diff_f64"] for r in rows),
+                         "max_rel_diff_f32": max(r["rel_diff_f32"] for r in rows), "rows": rows}}
 
 
 def run_e2e(sim, p, steps, torch):

@@ -417,7 +417,9 @@ vplbm_status vplbm_batch_get_launch(vplbm_batch *batch, int *block_x, int *block
 /* Time the branch mode with four member launch choices (every member set to
  * one scalar kernel and block shape) and six tile-mode launch shapes over
  * 2 x steps_per_trial steps each (rounded up to whole 32-step graphs) and
- * keep the fastest (members keep the winning launch choice); the trial
+ * keep the fastest (members keep the winning launch choice; the tile-mode
+ * launch shape is the fastest tile shape whichever mode won, so that
+ * vplbm_batch_set_mode(VPLBM_BATCH_TILES) afterwards runs at it); the trial
  * steps advance the members (they are real steps). */
 vplbm_status vplbm_batch_autotune(vplbm_batch *batch, int steps_per_trial);
 

@@ -667,6 +667,7 @@ class _Member:
     history = Simulation.history
     body_state = Simulation.body_state
     nstep = Simulation.nstep
+    launch = Simulation.launch
 
 
 class Batch:

@@ -395,8 +395,9 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int steps_per_trial)
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return berr(VPLBM_ECUDA, "event creation failed");
-    float best = 1e30f;
+    float best = 1e30f, best_tiles = 1e30f;
     int best_bx = b->bx, best_by = b->by, best_rows = b->rows, best_mode = b->mode;
+    int tile_bx = b->bx, tile_by = b->by, tile_rows = b->rows;   // the fastest tile-mode shape
     int best_mk = -1, best_mbx = 0, best_mby = 0;   // branch mode: the members' launch choice
     vplbm_status st = VPLBM_OK;
     // branch mode with every member on one scalar kernel and block shape
@@ -426,6 +427,12 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int steps_per_trial)
             if (cudaEventSynchronize(e1) != cudaSuccess) st = berr(VPLBM_ECUDA, "autotune timing failed");
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1 && cb[0] == VPLBM_BATCH_TILES && ms < best_tiles) {
+                best_tiles = ms;
+                tile_bx = b->bx;
+                tile_by = b->by;
+                tile_rows = b->rows;
+            }
             if (rep == 1 && ms < best) {
                 best = ms;
                 best_mode = b->mode;
@@ -446,7 +453,9 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int steps_per_trial)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->mode = best_mode;
-    vplbm_status st2 = vplbm_batch_set_launch(b, best_bx, best_by, best_rows);
+    // the tile mode keeps its own fastest shape whichever mode won
+    vplbm_status st2 = best_mode == VPLBM_BATCH_TILES ? vplbm_batch_set_launch(b, best_bx, best_by, best_rows)
+                                                      : vplbm_batch_set_launch(b, tile_bx, tile_by, tile_rows);
     return st != VPLBM_OK ? st : st2;
 }
 
