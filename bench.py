@@ -54,6 +54,8 @@ def dominant_kernel(prec: str, launch, kinds: dict) -> str:
         return f"vp_mrt_step2<{PREC_ID[prec]}, 0, 0>"
     if top == "tma":
         return f"vp_mrt_step_tma<{PREC_ID[prec]}>"
+    if launch[0] == "pair":
+        return "vp_mrt_step_pair<5, 0>"
     # single steps of a two-step choice run the 40-register kernel
     minb = {"scalar": 4, "scalar48": 5, "scalar40": 6, "fused2": 6, "tma": 6}[launch[0]]
     return f"vp_mrt_step<{PREC_ID[prec]}, {minb}, 0, 0>"
@@ -103,6 +105,7 @@ KERNEL_SOURCES = {
     "vp_mrt_step<": ("vplbm_internal.cuh", "vplbm_node.cuh", "step_scalar.cuh", "step_kernels.cu"),
     "vp_mrt_step2<": ("vplbm_internal.cuh", "vplbm_node.cuh", "step_fused2.cu"),
     "vp_mrt_step_tma<": ("vplbm_internal.cuh", "vplbm_node.cuh", "step_tma.cu"),
+    "vp_mrt_step_pair<": ("vplbm_internal.cuh", "vplbm_node.cuh", "step_scalar.cuh", "step_pair.cu"),
 }
 
 

@@ -292,12 +292,21 @@ vplbm_status vplbm_get_body_k(vplbm_ctx *ctx, int k, double q[3], double v[3], l
  *                          block_y) given to vplbm_set_launch (0 x 0: the
  *                          current blocks).  Its populations equal the
  *                          scalar kernel's bit for bit.
+ *  VPLBM_KERNEL_PAIR       two x-adjacent nodes per thread (FP16 storage,
+ *                          MRT collision, one body, even nx): a block of
+ *                          block_x x block_y threads updates a tile of
+ *                          2 block_x x block_y nodes, loading the pulls of
+ *                          both nodes, running the update on paired FP32
+ *                          instructions and storing 32-bit pairs; tiles on
+ *                          a lattice edge or near the body take the
+ *                          one-node code.  Its populations equal the
+ *                          scalar kernel's bit for bit.
  * Nodes on the lattice edges and near the body always take the same code.
  * The results of different kernels agree to the rounding of the storage
  * precision. */
 typedef enum {
     VPLBM_KERNEL_SCALAR = 0, VPLBM_KERNEL_SCALAR_48 = 1, VPLBM_KERNEL_SCALAR_40 = 2, VPLBM_KERNEL_TMA = 3,
-    VPLBM_KERNEL_FUSED2 = 4
+    VPLBM_KERNEL_FUSED2 = 4, VPLBM_KERNEL_PAIR = 5
 } vplbm_kernel;
 
 /* Kernel and block shape: block_x * block_y threads, block_x a multiple of
@@ -325,7 +334,8 @@ vplbm_status vplbm_get_launch_count(vplbm_ctx *ctx, long long *launches);
 /* Kinds of kernel launches vplbm_step makes (an index into the counts of
  * vplbm_get_kernel_launches):
  *  VPLBM_LAUNCH_ONE_STEP   one time step on a scalar step kernel (any
- *                          register budget, shape, or several bodies);
+ *                          register budget, shape, or several bodies) or
+ *                          on the node-pair kernel;
  *  VPLBM_LAUNCH_TWO_STEP   two time steps on the two-step kernel;
  *  VPLBM_LAUNCH_LOOKAHEAD  the one-thread launch that computes pose n + 1
  *                          of a prescribed path ahead of a run of two-step

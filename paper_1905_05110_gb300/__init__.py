@@ -376,7 +376,7 @@ COLLISIONS = {"mrt": 0, "bgk": 1}
 SHAPES = {"disk": 0, "ellipse": 1, "rectangle": 2}
 BATCH_MODES = {"branches": 0, "tiles": 1}
 BATCH_MODE_NAMES = {v: k for k, v in BATCH_MODES.items()}
-KERNELS = {"scalar": 0, "scalar48": 1, "scalar40": 2, "tma": 3, "fused2": 4}
+KERNELS = {"scalar": 0, "scalar48": 1, "scalar40": 2, "tma": 3, "fused2": 4, "pair": 5}
 KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
 
 
@@ -617,8 +617,9 @@ class Simulation:
         return vplbm_get_body(self.ctx)[2]
 
     def set_launch(self, kernel, bx=0, by=0):
-        """kernel: "scalar" (64-register budget), "scalar48", "scalar40", "tma" or "fused2"
-        (two steps per launch; bx, by: the blocks of its single steps) (or its number)."""
+        """kernel: "scalar" (64-register budget), "scalar48", "scalar40", "tma", "fused2"
+        (two steps per launch; bx, by: the blocks of its single steps) or "pair" (two
+        nodes per thread, FP16 storage) (or its number)."""
         k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         vplbm_set_launch(self.ctx, k, bx, by)
 

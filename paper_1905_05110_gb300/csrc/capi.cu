@@ -148,7 +148,7 @@ vplbm_status check_body(const vplbm_body_desc *b)
 }
 
 void tile_of(int kernel, int bx, int by, int *w, int *h);
-long long grid_rows(const vplbm_ctx *c, int bx, int by);
+long long grid_rows(const vplbm_ctx *c, int bx, int by, int kernel = KERNEL_SCALAR);
 
 // Bodies of a context: nb descriptors (nb = 0: no body); per-body buffers
 // have max(nb, 1) slots.
@@ -235,6 +235,7 @@ cudaError_t launch_one(const vplbm_ctx *c, long long step, cudaStream_t stream)
 {
     const StepParams p = params_for(c, step);
     if (c->kernel == KERNEL_TMA) return launch_step_tma(c->precision, p, c->tmap[step & 1], c->tma_grid, stream);
+    if (c->kernel == KERNEL_PAIR) return launch_step_pair(c->precision, p, c->bx, c->by, stream);
     // a single step of a two-step choice runs the 40-register scalar kernel
     const int minb = c->kernel == KERNEL_SCALAR_40 || c->kernel == KERNEL_FUSED2 ? 6 : c->kernel == KERNEL_SCALAR_48 ? 5 : 4;
     return launch_step(c->precision, p, c->bx, c->by, stream, minb);
@@ -292,6 +293,16 @@ const char *fused2_refusal(const vplbm_ctx *c)
     return nullptr;
 }
 
+// Why the node-pair kernel cannot run this context (nullptr: it can).
+const char *pair_refusal(const vplbm_ctx *c)
+{
+    if (c->precision != VPLBM_F16_DEV) return "the node-pair kernel needs FP16 storage";
+    if (c->collision != VPLBM_COLLISION_MRT) return "the node-pair kernel runs the MRT collision";
+    if (c->nbodies > 1) return "the node-pair kernel takes one body";
+    if (c->nx & 1) return "the node-pair kernel needs an even nx";
+    return nullptr;
+}
+
 // Steps of one captured graph, launches per graph.
 int graph_launches(const vplbm_ctx *c) { return c->kernel == KERNEL_FUSED2 ? 1 + GRAPH_STEPS / 2 : GRAPH_STEPS; }
 
@@ -300,8 +311,10 @@ int graph_launches(const vplbm_ctx *c) { return c->kernel == KERNEL_FUSED2 ? 1 +
 // TMA kernel's fixed tile otherwise.
 // Rows of a scalar kernel's grid for blocks of bx x by: one row of blocks
 // per row of tiles plus the rows of the body blocks.
-long long grid_rows(const vplbm_ctx *c, int bx, int by)
+long long grid_rows(const vplbm_ctx *c, int bx, int by, int kernel)
 {
+    if (kernel == KERNEL_PAIR)
+        return pair_grid_rows(c->nx, c->ny, c->has_body ? bounding_radius(&c->body_desc) : 0.0, c->has_body, bx, by);
     const long long ntx = (c->nx + bx - 1) / bx, nty = (c->ny + by - 1) / by;
     long long nbody = 0;
     for (int k = 0; k < body_slots(c->nbodies); ++k) {
@@ -1027,8 +1040,12 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
         c->kernel = KERNEL_FUSED2;
         return VPLBM_OK;
     }
-    if (kernel != KERNEL_SCALAR && kernel != KERNEL_SCALAR_48 && kernel != KERNEL_SCALAR_40)
+    if (kernel == KERNEL_PAIR) {
+        const char *why = pair_refusal(c);
+        if (why) return fail(VPLBM_EUNSUPPORTED, "%s", why);
+    } else if (kernel != KERNEL_SCALAR && kernel != KERNEL_SCALAR_48 && kernel != KERNEL_SCALAR_40) {
         return fail(VPLBM_EINVAL, "unknown kernel %d", kernel);
+    }
     const int t = bx * by;
     if (bx < 32 || bx % 32 || by < 1 || (t != 128 && t != 256))
         return fail(VPLBM_EINVAL, "launch shape %dx%d not allowed", bx, by);
@@ -1039,7 +1056,7 @@ vplbm_status vplbm_set_launch(vplbm_ctx *c, int kernel, int bx, int by)
         if (max_reduction_blocks(c->nx, c->ny, present ? bounding_radius(&c->bodies[k]) : 0.0, present, w, h) > c->max_parts)
             return fail(VPLBM_EINVAL, "launch shape %dx%d needs more reduction scratch than allocated", bx, by);
     }
-    if (grid_rows(c, bx, by) > MAX_GRID_ROWS)
+    if (grid_rows(c, bx, by, kernel) > MAX_GRID_ROWS)
         return fail(VPLBM_EINVAL, "launch shape %dx%d needs more than %d grid rows on this lattice", bx, by,
                     MAX_GRID_ROWS);
     c->kernel = kernel;
@@ -1128,9 +1145,9 @@ vplbm_status vplbm_autotune(vplbm_ctx *c, int steps_per_trial)
         // candidates: the TMA-staged kernel, every block shape of the three
         // register budgets of the scalar kernel, then the two-step kernel
         // (from an even step only: its runs start there)
-        static const int kinds[3] = {KERNEL_SCALAR_48, KERNEL_SCALAR_40, KERNEL_SCALAR};
-        for (int cand = -1; cand <= 3 * N_SHAPES; ++cand) {
-            const bool two = cand == 3 * N_SHAPES;
+        static const int kinds[4] = {KERNEL_SCALAR_48, KERNEL_SCALAR_40, KERNEL_SCALAR, KERNEL_PAIR};
+        for (int cand = -1; cand <= 4 * N_SHAPES; ++cand) {
+            const bool two = cand == 4 * N_SHAPES;
             const int ck = cand < 0 ? KERNEL_TMA : two ? KERNEL_FUSED2 : kinds[cand / N_SHAPES];
             const int cbx = cand < 0 || two ? 0 : SHAPES[cand % N_SHAPES][0];
             const int cby = cand < 0 ? 1 : two ? 0 : SHAPES[cand % N_SHAPES][1];

@@ -1,0 +1,161 @@
+// The node-pair step kernel for FP16-deviation storage: the one-step fused
+// update of Algorithm 1 with two x-adjacent nodes per thread.
+//
+// FP16 storage halves the bytes of a node update against FP32, but the
+// one-node-per-thread kernel then runs out of instruction issue before it
+// runs out of bandwidth.  Here a thread of an interior tile away from the
+// body loads the two nodes' pulls (one 32-bit load for the three
+// populations with c_ax = 0, two 16-bit loads for the others), runs the
+// MRT update once on float2 lanes with paired FP32 instructions
+// (mrt_dev_lanes<Lane2>: every lane rounds as the scalar update does, so
+// the populations are those of the one-node kernel bit for bit) and stores
+// the nine results as 32-bit pairs.  Tiles on a lattice edge or meeting the
+// body's node range take the one-node code for each of their nodes.
+//
+// Grid: the scalar kernel's body blocks first (tiles of blockDim.x x
+// blockDim.y nodes, one node per thread: they reduce the solid-node sums
+// and run the tail), then one block per pair tile of 2 blockDim.x x
+// blockDim.y nodes, edge rows and columns first.  Requires an even nx, so that every
+// row starts on a 4-byte boundary of the planes.
+#include "step_scalar.cuh"
+
+namespace vplbm {
+namespace {
+
+// Blocks of 256 threads per SM the register budget is sized for (48
+// registers; 40 and 64 measured within 2 % of it, 5 blocks per SM ahead).
+constexpr int PAIR_MINB = 5;
+
+__device__ __forceinline__ float2 ld_pair(const __half *p) { return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p))); }
+__device__ __forceinline__ float2 ld_two(const __half *p) { return make_float2(__half2float(__ldg(p)), __half2float(__ldg(p + 1))); }
+
+// Nodes (i, j), (i + 1, j) of one pair tile, i even.
+template <int SHAPE>
+__device__ __forceinline__ void pair_tile(const StepParams &p, int tile_x, int tile_y)
+{
+    constexpr int P = VPLBM_F16_DEV;
+    using S = __half;
+    const int w = 2 * (int)blockDim.x;
+    const int bi0 = tile_x * w, bj0 = tile_y * (int)blockDim.y;
+    const int i = bi0 + 2 * (int)threadIdx.x, j = bj0 + (int)threadIdx.y;
+    const S *__restrict__ fin = static_cast<const S *>(p.fin);
+    S *__restrict__ fout = static_cast<S *>(p.fout);
+    const BodyState *__restrict__ bs = p.bs_in;
+    float cr, cax, cay;
+    if (!(bi0 > 0 && bj0 > 0 && bi0 + w < p.nx && bj0 + (int)blockDim.y < p.ny)) {
+        // a tile on a lattice edge: the one-node code, node by node
+        const int4 range = __ldg(reinterpret_cast<const int4 *>(&bs->ilo));
+        const bool near = range.x <= range.y && tile_near_body(range, bi0, bj0, w, blockDim.y, false);
+        for (int k = 0; k < 2; ++k) {
+            if (i + k >= p.nx || j >= p.ny) continue;
+            float f[NQ];
+            pull_all<P>(p, fin, i + k, j, f);
+            if (i + k == p.nx - 1 && p.bc[VPLBM_EAST] == VPLBM_BC_CONVECTIVE) record_outlet<P>(p, j, f);
+            node_update<P, VPLBM_COLLISION_MRT, SHAPE>(p, bs, near, i + k, j, f, fout, cr, cax, cay);
+        }
+        return;
+    }
+    // streaming loads first: nothing below them waits on the pose
+    const int b = j * p.nx + i;
+    float2 f2[NQ];
+#pragma unroll
+    for (int a = 0; a < NQ; ++a) {
+        const S *src = static_cast<const S *>(p.src_plane[a]) + b;
+        f2[a] = cx_of(a) == 0 ? ld_pair(src) : ld_two(src);
+    }
+    const int4 range = __ldg(reinterpret_cast<const int4 *>(&bs->ilo));
+    if (range.x <= range.y && tile_near_body(range, bi0, bj0, w, blockDim.y, false)) {
+        // the tile meets the body's node range: chi node by node
+        for (int k = 0; k < 2; ++k) {
+            float f[NQ];
+#pragma unroll
+            for (int a = 0; a < NQ; ++a) f[a] = k ? f2[a].y : f2[a].x;
+            node_update<P, VPLBM_COLLISION_MRT, SHAPE>(p, bs, true, i + k, j, f, fout, cr, cax, cay);
+        }
+        return;
+    }
+    S *const *dp = reinterpret_cast<S *const *>(p.dst_plane);
+    float ax, ay;
+    mrt_dev_lanes<Lane2>(p, f2, false, 0.f, 0.f, bs,
+                         [&](int a, float2 v) { *reinterpret_cast<__half2 *>(dp[a] + b) = __floats2half2_rn(v.x, v.y); },
+                         ax, ay);
+}
+
+// MINB: blocks of 256 threads per SM the register budget is sized for.
+// Programmatic dependent launch as in the one-node kernel.
+template <int MINB, int SHAPE>
+__global__ void __launch_bounds__(256, MINB) vp_mrt_step_pair(const StepParams p)
+{
+    __shared__ double red[8][NPART];
+    __shared__ float rows[NPART - 1][256];
+    __shared__ int s_last;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int nbr = p.nbody_rows;
+    if ((int)blockIdx.y < nbr) {
+        // body blocks: one node per thread on tiles of blockDim.x x blockDim.y
+        const int b = blockIdx.y * gridDim.x + blockIdx.x;
+        if (b >= p.nbody) return;
+        const int4 range = __ldg(reinterpret_cast<const int4 *>(&p.bs_in->ilo));
+        int tx0 = 0, ty0 = 0, rw = 1, nrect = 1;   // no solid node: tile (0, 0) runs the tail
+        if (range.x <= range.y) {
+            tx0 = range.x / (int)blockDim.x;
+            ty0 = range.z / (int)blockDim.y;
+            rw = range.y / (int)blockDim.x - tx0 + 1;
+            nrect = rw * (range.w / (int)blockDim.y - ty0 + 1);
+        }
+        if (b < nrect)
+            scalar_tile<VPLBM_F16_DEV, VPLBM_COLLISION_MRT, SHAPE>(p, tx0 + b % rw, ty0 + b / rw, red, rows, &s_last,
+                                                                 true);
+        if (b == 0 && nrect > p.nbody && threadIdx.x == 0 && threadIdx.y == 0) *p.err |= ERR_INTERNAL;
+        if (b == 0 && threadIdx.x == 0 && threadIdx.y == 0 && prescribed_motion(p)) advance_prescribed(p);
+        return;
+    }
+    // row-major over the pair tiles, the two edge rows first and, in each
+    // row, its two edge columns first: an edge tile runs the one-node code
+    // and takes about twice as long, so it should not be among the last
+    // blocks of the launch
+    const int ntx = gridDim.x, nty = gridDim.y - nbr;
+    const int c = blockIdx.x, r = blockIdx.y - nbr;
+    pair_tile<SHAPE>(p, c == 0 ? 0 : (c == 1 ? ntx - 1 : c - 1), r == 0 ? 0 : (r == 1 ? nty - 1 : r - 1));
+}
+
+template <int SHAPE>
+cudaError_t launch_pair_t(const StepParams &p0, int bx, int by, cudaStream_t stream)
+{
+    StepParams p = p0;
+    p.nbody = (int)max_reduction_blocks(p.nx, p.ny, p.body.radius, p.body.present, bx, by);
+    const int ntx = (p.nx + 2 * bx - 1) / (2 * bx), nty = (p.ny + by - 1) / by;
+    const int nbr = (p.nbody + ntx - 1) / ntx;
+    p.nbody_rows = nbr;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ntx, nty + nbr);
+    cfg.blockDim = dim3(bx, by);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, vp_mrt_step_pair<PAIR_MINB, SHAPE>, p);
+}
+
+}  // namespace
+
+long long pair_grid_rows(int nx, int ny, double radius, int present, int bx, int by)
+{
+    const long long nbody = max_reduction_blocks(nx, ny, radius, present, bx, by);
+    const long long ntx = (nx + 2LL * bx - 1) / (2LL * bx), nty = (ny + by - 1) / by;
+    return nty + (nbody + ntx - 1) / ntx;
+}
+
+cudaError_t launch_step_pair(int precision, const StepParams &p, int bx, int by, cudaStream_t stream)
+{
+    if (precision != VPLBM_F16_DEV || p.collision != VPLBM_COLLISION_MRT || p.nbodies > 1 || (p.nx & 1))
+        return cudaErrorInvalidValue;
+    if (p.body.present && p.body.shape != VPLBM_SHAPE_DISK) return launch_pair_t<SHAPE_ANY>(p, bx, by, stream);
+    return launch_pair_t<VPLBM_SHAPE_DISK>(p, bx, by, stream);
+}
+
+}  // namespace vplbm

@@ -224,7 +224,13 @@ inline double bounding_radius(const vplbm_body_desc *b)
 // Step kernels a context can launch: the scalar kernel with the register
 // budget of 4 / 5 / 6 blocks of 256 threads per SM, the TMA-staged one, and
 // the two-step kernel (two time steps per launch).
-enum { KERNEL_SCALAR = 0, KERNEL_SCALAR_48 = 1, KERNEL_SCALAR_40 = 2, KERNEL_TMA = 3, KERNEL_FUSED2 = 4 };
+enum { KERNEL_SCALAR = 0, KERNEL_SCALAR_48 = 1, KERNEL_SCALAR_40 = 2, KERNEL_TMA = 3, KERNEL_FUSED2 = 4, KERNEL_PAIR = 5 };
+
+// Node-pair kernel (step_pair.cu): FP16 storage, MRT, one body, even nx;
+// blocks of bx x by threads on tiles of 2 bx x by nodes (the body blocks on
+// tiles of bx x by, one node per thread).  Grid rows it needs.
+cudaError_t launch_step_pair(int precision, const StepParams &p, int bx, int by, cudaStream_t stream);
+long long pair_grid_rows(int nx, int ny, double radius, int present, int bx, int by);
 
 // Two-step kernel (step_fused2.cu): a block computes time step n on its
 // tile and a one-node ring around it into shared memory, then step n + 1 on

@@ -497,6 +497,129 @@ __device__ __forceinline__ bool body_chi(const DevBody &body, float r2f, const B
     return chi;
 }
 
+// ---- FP16-storage MRT update in explicit lane operations ---------------
+//
+// The FP16-deviation kernels run the MRT update through these lane types:
+// Lane1 on one node (a float per quantity), Lane2 on two x-adjacent nodes
+// at once (a float2 per quantity, one paired FP32 instruction per
+// operation).  Every operation rounds once, as written, with no
+// contraction left to the compiler, and a paired instruction rounds each
+// lane like its scalar counterpart, so a node updated in a pair gets the
+// bits it gets alone.
+struct Lane1 {
+    using L = float;
+    static constexpr bool SCALAR = true;
+    static __device__ __forceinline__ L c(float x) { return x; }
+    static __device__ __forceinline__ L add(L a, L b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ L sub(L a, L b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ L mul(L a, L b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ L fma(L a, L b, L d) { return __fmaf_rn(a, b, d); }
+    static __device__ __forceinline__ L fms(L a, L b, L d) { return __fmaf_rn(a, b, -d); }   // a b - d
+    static __device__ __forceinline__ L recip(L x) { return vplbm::recip(x); }
+    static __device__ __forceinline__ bool bad(L rho) { return !(rho > 0.f) || !(rho < 1e30f); }
+};
+struct Lane2 {
+    using L = float2;
+    static constexpr bool SCALAR = false;
+    static __device__ __forceinline__ L c(float x) { return make_float2(x, x); }
+    static __device__ __forceinline__ L add(L a, L b) { return __fadd2_rn(a, b); }
+    // a - b: the product b (-1) is exact, so one rounding, as __fsub_rn
+    static __device__ __forceinline__ L sub(L a, L b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+    static __device__ __forceinline__ L mul(L a, L b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ L fma(L a, L b, L d) { return __ffma2_rn(a, b, d); }
+    static __device__ __forceinline__ L fms(L a, L b, L d) { return __ffma2_rn(a, b, make_float2(-d.x, -d.y)); }
+    static __device__ __forceinline__ L recip(L x)
+    {
+        // the hardware estimate per lane, the Newton-Raphson step paired:
+        // the same two roundings as recip(float)
+        float r0x, r0y;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0x) : "f"(x.x));
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0y) : "f"(x.y));
+        const float2 r0 = make_float2(r0x, r0y);
+        return __ffma2_rn(r0, __ffma2_rn(make_float2(-x.x, -x.y), r0, make_float2(1.f, 1.f)), r0);
+    }
+    static __device__ __forceinline__ bool bad(L rho) { return Lane1::bad(rho.x) || Lane1::bad(rho.y); }
+};
+
+// The MRT update (Eqs. 14-17 with the closed-form M F) of the pulled
+// deviation populations f (f_a - w_a rho0) of one node or a pair, from
+// rho, j and the penalized velocity u with forcing G = rho (g + a) (Eq. 22;
+// a = 0 off the body: u = j / rho + g / 2), stored through store(a, value).
+// Returns rho.  Lane1 only: chi and the lever arm (dxl, dyl) of the node,
+// and (ax, ay) = a for the solid-node sums.
+template <class Ln, class Store>
+__device__ __forceinline__ typename Ln::L mrt_dev_lanes(const StepParams &p, const typename Ln::L f[NQ], bool chi,
+                                                        float dxl, float dyl, const BodyState *__restrict__ bs,
+                                                        const Store &store, float &ax_out, float &ay_out)
+{
+    using L = typename Ln::L;
+    const L d13 = Ln::sub(f[1], f[3]), d24 = Ln::sub(f[2], f[4]), b13 = Ln::add(f[1], f[3]), b24 = Ln::add(f[2], f[4]);
+    const L d56 = Ln::sub(f[5], f[6]), d87 = Ln::sub(f[8], f[7]), a56 = Ln::add(f[5], f[6]), a78 = Ln::add(f[7], f[8]);
+    const L sx = Ln::add(d56, d87), ty = Ln::sub(a56, a78), sa = Ln::add(b13, b24), sd = Ln::add(a56, a78);
+    const L rs = Ln::add(Ln::add(f[0], sa), sd);
+    const L rho = Ln::add(Ln::c(p.rho0f), rs);
+    const L jx = Ln::add(d13, sx), jy = Ln::add(d24, ty);
+    const L inv_rho = Ln::recip(rho);
+    L ux = Ln::fma(jx, inv_rho, Ln::c(p.pc.hgx)), uy = Ln::fma(jy, inv_rho, Ln::c(p.pc.hgy));
+    L Gx = Ln::mul(rho, Ln::c(p.gxf)), Gy = Ln::mul(rho, Ln::c(p.gyf));
+    ax_out = 0.f;
+    ay_out = 0.f;
+    if constexpr (Ln::SCALAR) {
+        if (chi) {   // Eq. (22), eta-stable form: a = (u_s - v) / (eta + 1/2), u = v + a / 2
+            const float4 vv = __ldg(reinterpret_cast<const float4 *>(&bs->vxf));
+            const float usx = __fmaf_rn(-vv.z, dyl, vv.x), usy = __fmaf_rn(vv.z, dxl, vv.y);
+            const float ax = __fmul_rn(__fsub_rn(usx, ux), p.pen_kf), ay = __fmul_rn(__fsub_rn(usy, uy), p.pen_kf);
+            Gx = __fmul_rn(rho, __fadd_rn(p.gxf, ax));
+            Gy = __fmul_rn(rho, __fadd_rn(p.gyf, ay));
+            ux = __fmaf_rn(0.5f, ax, ux);
+            uy = __fmaf_rn(0.5f, ay, uy);
+            ax_out = ax;
+            ay_out = ay;
+        }
+    }
+    const auto &k = p.pc;
+    const L e = Ln::fma(Ln::c(-4.f), f[0], Ln::fms(Ln::c(2.f), sd, sa));
+    const L ep = Ln::fma(Ln::c(4.f), f[0], Ln::fma(Ln::c(-2.f), sa, sd));
+    const L qx = Ln::fma(Ln::c(-2.f), d13, sx), qy = Ln::fma(Ln::c(-2.f), d24, ty);
+    const L pxx = Ln::sub(b13, b24);
+    const L pxy = Ln::sub(Ln::add(f[5], f[7]), Ln::add(f[6], f[8]));
+    const L ux2 = Ln::mul(ux, ux), uy2 = Ln::mul(uy, uy);
+    const L u2r = Ln::mul(rho, Ln::add(ux2, uy2));
+    const L uG = Ln::fma(ux, Gx, Ln::mul(uy, Gy));
+    const L es = Ln::fma(Ln::c(k.om1), e,
+                         Ln::fma(Ln::c(p.sf[1]), Ln::fma(Ln::c(3.f), u2r, Ln::mul(Ln::c(-2.f), rs)),
+                                 Ln::mul(Ln::c(k.h1x6), uG)));
+    const L eps = Ln::fma(Ln::c(k.om2), ep,
+                          Ln::fma(Ln::c(p.sf[2]), Ln::fma(Ln::c(-3.f), u2r, rs), Ln::mul(Ln::c(k.mh2x6), uG)));
+    const L jxs = Ln::add(jx, Gx), jys = Ln::add(jy, Gy);
+    const L qxs = Ln::fma(Ln::c(k.om4), qx, Ln::fma(Ln::c(-p.sf[4]), Ln::mul(rho, ux), Ln::mul(Ln::c(k.mh4), Gx)));
+    const L qys = Ln::fma(Ln::c(k.om6), qy, Ln::fma(Ln::c(-p.sf[6]), Ln::mul(rho, uy), Ln::mul(Ln::c(k.mh6), Gy)));
+    const L cxx = Ln::fms(ux, Gx, Ln::mul(uy, Gy)), cxy = Ln::fma(ux, Gy, Ln::mul(uy, Gx));
+    const L pxxs = Ln::fma(Ln::c(k.om7), pxx,
+                           Ln::fma(Ln::c(p.sf[7]), Ln::mul(rho, Ln::sub(ux2, uy2)), Ln::mul(Ln::c(k.h7x2), cxx)));
+    const L pxys = Ln::fma(Ln::c(k.om8), pxy,
+                           Ln::fma(Ln::c(p.sf[8]), Ln::mul(rho, Ln::mul(ux, uy)), Ln::mul(Ln::c(k.h8), cxy)));
+    // back to populations, M^-1 = M^T diag(1/|row|^2)
+    const L r9 = Ln::mul(rs, Ln::c(1.f / 9.f));
+    const L A = Ln::fma(eps, Ln::c(-1.f / 18.f), Ln::fma(es, Ln::c(-1.f / 36.f), r9));
+    const L B = Ln::fma(eps, Ln::c(1.f / 36.f), Ln::fma(es, Ln::c(1.f / 18.f), r9));
+    const L X1 = Ln::mul(Ln::sub(jxs, qxs), Ln::c(1.f / 6.f)), Y1 = Ln::mul(Ln::sub(jys, qys), Ln::c(1.f / 6.f));
+    const L X2 = Ln::fma(qxs, Ln::c(1.f / 12.f), Ln::mul(jxs, Ln::c(1.f / 6.f)));
+    const L Y2 = Ln::fma(qys, Ln::c(1.f / 12.f), Ln::mul(jys, Ln::c(1.f / 6.f)));
+    const L Pq = Ln::mul(pxxs, Ln::c(0.25f)), Rq = Ln::mul(pxys, Ln::c(0.25f));
+    store(0, Ln::fma(eps, Ln::c(1.f / 9.f), Ln::fma(es, Ln::c(-1.f / 9.f), r9)));
+    store(1, Ln::add(Ln::add(A, X1), Pq));
+    store(2, Ln::sub(Ln::add(A, Y1), Pq));
+    store(3, Ln::add(Ln::sub(A, X1), Pq));
+    store(4, Ln::sub(Ln::sub(A, Y1), Pq));
+    store(5, Ln::add(Ln::add(Ln::add(B, X2), Y2), Rq));
+    store(6, Ln::sub(Ln::add(Ln::sub(B, X2), Y2), Rq));
+    store(7, Ln::add(Ln::sub(Ln::sub(B, X2), Y2), Rq));
+    store(8, Ln::sub(Ln::sub(Ln::add(B, X2), Y2), Rq));
+    if (Ln::bad(rho)) *p.err = ERR_NONFINITE;
+    return rho;
+}
+
 // The VP-MRT (or BGK) update of one node from its pulled populations f
 // given chi and the lever arm from body_chi: moments, u_s of the body
 // state bs, penalized velocity (Eq. 22), collision with forcing (Eq. 17)
@@ -511,6 +634,14 @@ __device__ __forceinline__ bool node_collide_to(const StepParams &p, const BodyS
 {
     using T = typename Prec<P>::T;
     constexpr bool DEV = Prec<P>::DEV;
+    if constexpr (P == VPLBM_F16_DEV && COLL == VPLBM_COLLISION_MRT) {
+        // FP16 storage: the lane form, shared with the node-pair kernel
+        float ax, ay;
+        cr = mrt_dev_lanes<Lane1>(p, f, chi, dxl, dyl, bs, store, ax, ay);
+        cax = ax;
+        cay = ay;
+        return chi;
+    }
     // sums shared by the moments (rows of Eq. 15)
     const T d13 = f[1] - f[3], d24 = f[2] - f[4], b13 = f[1] + f[3], b24 = f[2] + f[4];
     const T d56 = f[5] - f[6], d87 = f[8] - f[7], a56 = f[5] + f[6], a78 = f[7] + f[8];
