@@ -7,9 +7,16 @@
 // node sum).  With J = w_cd mean C_D + w_cl RMS C_L over [w0, N), the
 // reverse sweep carries L_n = dJ/dS_n:
 //   (a) mu(x) = (dC/df)^T L_{n+1}(x) + [x in R(n)] dJ/dF_h(n) . c   (node local)
-//   (b) L_n(y) = (Pull^T mu)(y) - [y in R(n)] dJ/dF_h(n) . c        (a gather)
+//   (b) L_n(y) = (Pull^T mu)(y) - [y in R(n)] dJ/dF_h(n) . c
 // and the parameter gradients: dJ/ds_e, dJ/ds_nu (= s7 = s8), dJ/deta from
 // (a), dJ/du_in(j) of the west wall's u_x profile from (b).
+// One kernel per reverse step does both: a node computes mu(x) and pushes
+// each mu_q(x) to the one population its pull read (Pull^T as a scatter:
+// every population but those of a zero-gradient outlet column has exactly
+// one reader), so mu never reaches memory.  A zero-gradient column's
+// populations have a second reader, the outlet's own copy rule; those
+// contributions go to a per-row buffer that the next reverse step adds in
+// as it loads L there.
 // The reverse of C is written on the closed-form moments of the forward
 // kernel (vplbm_node.cuh): M^-T = diag(1/|row|^2) M for the incoming
 // adjoint, M^T for the outgoing one.
@@ -26,6 +33,14 @@
 
 namespace vplbm {
 namespace {
+
+constexpr int ADJ_BX = 32, ADJ_BY = 8;   // block of the reverse kernel (a tile of nodes)
+constexpr int ADJ_BLOCK = ADJ_BX * ADJ_BY;
+// blocks per SM the reverse kernel's register budget is sized for: 64
+// registers in FP32, 96 in FP64 (no spills)
+template <int P> constexpr int adj_minb() { return P == VPLBM_F64 ? 2 : 4; }
+inline int cx_host(int q) { static const int c[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1}; return c[q]; }
+inline int cy_host(int q) { static const int c[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1}; return c[q]; }
 
 // Per-step inputs of the reverse kernels, with the FP32 copies and the
 // pose-derived values the FP32 kernels use (no FP64 on their main path:
@@ -91,137 +106,6 @@ template <typename T> __device__ __forceinline__ void mt9(const T L[NQ], T out[N
     out[8] = L[0] + (T)2 * L[1] + L[2] + L[3] + L[4] - L[5] - L[6] - L[8];
 }
 
-// (a) mu = (dC/df)^T lam_next + objective term; parameter-gradient partials
-// acc[block][0..3] += (d_eta, d_s1, d_s7, d_s8).
-template <int P>
-__global__ void __launch_bounds__(256) adj_collide(const StepParams p, const AdjStep a, const typename Prec<P>::T *lam_next,
-                                                   typename Prec<P>::T *mu, double *acc)
-{
-    using T = typename Prec<P>::T;
-    using S = typename Prec<P>::S;
-    constexpr bool DEV = Prec<P>::DEV;
-    __shared__ double red[8][4];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    T g4[4] = {0, 0, 0, 0};
-    if (i < p.nx) {
-        const S *fin = static_cast<const S *>(p.fin);
-        T f[NQ];
-        pull_all<P>(p, fin, i, j, f);
-        const long long b = (long long)j * p.nx + i;
-        T xi[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) xi[q] = lam_next[q * p.ps + b];
-
-        // forward intermediates (as in node_update)
-        T m[NQ];
-        moments9<T>(f, m);
-        const T rs = m[0];
-        const T rho = DEV ? par<T>(p.rho0, p.rho0f) + rs : rs;
-        const T inv_rho = recip(rho);
-        const T jx = m[3], jy = m[5];
-        T dx, dy;
-        const bool chi = chi_adj<T>(p, a, i, j, dx, dy);
-        const T gx = par<T>(p.gx, p.gxf), gy = par<T>(p.gy, p.gyf);
-        const T vx = jx * inv_rho + (T)0.5 * gx, vy = jy * inv_rho + (T)0.5 * gy;
-        T ax = 0, ay = 0, usx = 0, usy = 0, k = 0;
-        if (chi) {
-            usx = par<T>(a.vx, a.vxf) - par<T>(a.om, a.omf) * dy;
-            usy = par<T>(a.vy, a.vyf) + par<T>(a.om, a.omf) * dx;
-            k = par<T>(p.pen_k, p.pen_kf);
-            ax = -k * (vx - usx);
-            ay = -k * (vy - usy);
-        }
-        const T ux = vx + (T)0.5 * ax, uy = vy + (T)0.5 * ay;
-        const T Gx = rho * (gx + ax), Gy = rho * (gy + ay);
-        const T u2r = rho * (ux * ux + uy * uy);
-        const T uG = ux * Gx + uy * Gy;
-        const T W1 = rho * (ux * ux - uy * uy), W2 = ux * Gx - uy * Gy;
-        const T W3 = rho * ux * uy, W4 = ux * Gy + uy * Gx;
-        const T s1 = par<T>(p.s[1], p.sf[1]), s2 = par<T>(p.s[2], p.sf[2]), s4 = par<T>(p.s[4], p.sf[4]);
-        const T s6 = par<T>(p.s[6], p.sf[6]), s7 = par<T>(p.s[7], p.sf[7]), s8 = par<T>(p.s[8], p.sf[8]);
-        const T h1 = (T)1 - (T)0.5 * s1, h2 = (T)1 - (T)0.5 * s2, h4 = (T)1 - (T)0.5 * s4;
-        const T h6 = (T)1 - (T)0.5 * s6, h7 = (T)1 - (T)0.5 * s7, h8 = (T)1 - (T)0.5 * s8;
-
-        // adjoint of the post-collision moments: M^-T xi = diag(1/|row|^2) M xi
-        T L[NQ];
-        moments9<T>(xi, L);
-        L[0] *= (T)(1.0 / 9.0); L[1] *= (T)(1.0 / 36.0); L[2] *= (T)(1.0 / 36.0);
-        L[3] *= (T)(1.0 / 6.0); L[4] *= (T)(1.0 / 12.0); L[5] *= (T)(1.0 / 6.0);
-        L[6] *= (T)(1.0 / 12.0); L[7] *= (T)0.25; L[8] *= (T)0.25;
-
-        // parameter partials (before L is consumed)
-        const T e_eq = (T)-2 * rs + (T)3 * u2r;
-        g4[1] = L[1] * (-(m[1] - e_eq) - (T)3 * uG);
-        g4[2] = L[7] * (-(m[7] - W1) - W2);
-        g4[3] = L[8] * (-(m[8] - W3) - (T)0.5 * W4);
-
-        // back through the relaxation (Eq. 17 in closed form)
-        T lm[NQ];   // adjoint of the pre-collision moments
-        lm[1] = ((T)1 - s1) * L[1];
-        lm[2] = ((T)1 - s2) * L[2];
-        lm[4] = ((T)1 - s4) * L[4];
-        lm[6] = ((T)1 - s6) * L[6];
-        lm[7] = ((T)1 - s7) * L[7];
-        lm[8] = ((T)1 - s8) * L[8];
-        T l_rs = L[0] - (T)2 * s1 * L[1] + s2 * L[2];
-        const T l_u2r = (T)3 * s1 * L[1] - (T)3 * s2 * L[2];
-        const T l_uG = (T)6 * h1 * L[1] - (T)6 * h2 * L[2];
-        T l_jx = L[3], l_jy = L[5];
-        T l_Gx = L[3] - h4 * L[4], l_Gy = L[5] - h6 * L[6];
-        T l_rho = -s4 * L[4] * ux - s6 * L[6] * uy;
-        T l_ux = -s4 * L[4] * rho, l_uy = -s6 * L[6] * rho;
-        const T lW1 = s7 * L[7], lW2 = (T)2 * h7 * L[7], lW3 = s8 * L[8], lW4 = h8 * L[8];
-        l_rho += lW1 * (ux * ux - uy * uy) + lW3 * ux * uy + l_u2r * (ux * ux + uy * uy);
-        l_ux += lW1 * (T)2 * rho * ux + lW2 * Gx + lW3 * rho * uy + lW4 * Gy + l_u2r * (T)2 * rho * ux + l_uG * Gx;
-        l_uy += -lW1 * (T)2 * rho * uy - lW2 * Gy + lW3 * rho * ux + lW4 * Gx + l_u2r * (T)2 * rho * uy + l_uG * Gy;
-        l_Gx += lW2 * ux + lW4 * uy + l_uG * ux;
-        l_Gy += -lW2 * uy + lW4 * ux + l_uG * uy;
-        // G = rho (g + a)
-        l_rho += l_Gx * (gx + ax) + l_Gy * (gy + ay);
-        T l_ax = rho * l_Gx + (T)0.5 * l_ux, l_ay = rho * l_Gy + (T)0.5 * l_uy;
-        T l_vx = l_ux, l_vy = l_uy;
-        if (chi) {
-            l_vx += -k * l_ax;
-            l_vy += -k * l_ay;
-            g4[0] = k * k * ((vx - usx) * l_ax + (vy - usy) * l_ay);
-        }
-        // v = j / rho + g/2
-        l_jx += l_vx * inv_rho;
-        l_jy += l_vy * inv_rho;
-        l_rho += -(l_vx * jx + l_vy * jy) * (inv_rho * inv_rho);
-        l_rs += l_rho;
-        lm[0] = l_rs;
-        lm[3] = l_jx;
-        lm[5] = l_jy;
-        T out[NQ];
-        mt9<T>(lm, out);
-        if (chi) {
-            const T wx = par<T>(a.wx, a.wxf), wy = par<T>(a.wy, a.wyf);
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) out[q] += (T)cx_of(q) * wx + (T)cy_of(q) * wy;
-        }
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) mu[q * p.ps + b] = out[q];
-    }
-    // deterministic block sums of the parameter partials
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        T v = g4[q];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) red[warp][q] = (double)v;
-    }
-    __syncthreads();
-    if (tid < 4) {
-        double s = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][tid];
-        double *dst = acc + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4 + tid;
-        *dst += s;
-    }
-}
-
 // Is the pull of population a into node (i, j) a plain (possibly periodic)
 // pull, a wall rule (then *side), or a zero-gradient copy?
 enum { PULL_PLAIN = 0, PULL_WALL = 1, PULL_ZEROGRAD = 2 };
@@ -240,84 +124,242 @@ __device__ __forceinline__ int pull_kind(const StepParams &p, int a, int i, int 
     return PULL_PLAIN;
 }
 
-// (b) L_n(y) = sum of mu over the pulls that read population (b, y), minus
-// the momentum-exchange own term; west velocity-wall pulls give dJ/du_in.
+// Slot of a population crossing the west (c_ax = +1) or east (c_ax = -1)
+// edge in a zero-gradient buffer [side][3][ny]: side 0 west, 1 east.
+__device__ __forceinline__ int zg_slot(int q)
+{
+    const int side = cx_of(q) == 1 ? 0 : 1;
+    const int k = cy_of(q) == 0 ? 0 : (cy_of(q) == 1 ? 1 : 2);
+    return side * 3 + k;
+}
+
+// Per-plane pointers of the adjoint fields: src[q] = &lam_next[q][0][0],
+// dst[q] = &lam[q][-c_qy][-c_qx], so that the push of mu_q from interior
+// node b writes dst[q][b].
+template <typename T> struct LamPlanes {
+    const T *src[NQ];
+    T *dst[NQ];
+};
+
+// The reverse step at node (i, j) with its pulled populations f: (a) mu =
+// (dC/df)^T L_{n+1} + objective term, (b) mu pushed into L_n, the
+// parameter partials into g.
 template <int P>
-__global__ void __launch_bounds__(256) adj_stream(const StepParams p, const AdjStep a, const typename Prec<P>::T *mu,
-                                                  typename Prec<P>::T *lam, double *grad_uin)
+__device__ __forceinline__ void adj_one_node(const StepParams &p, const AdjStep &a,
+                                             const LamPlanes<typename Prec<P>::T> &lp,
+                                             const typename Prec<P>::T *zg_in, typename Prec<P>::T *lam,
+                                             typename Prec<P>::T *zg_out, double *grad_uin, int i, int j,
+                                             const typename Prec<P>::T f[NQ], typename Prec<P>::T g[4])
 {
     using T = typename Prec<P>::T;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (i >= p.nx) return;
-    const int nx = p.nx, ny = p.ny;
-    const long long ps = p.ps;
-    auto MU = [&](int q, int ii, int jj) { return mu[q * ps + (long long)jj * nx + ii]; };
-    T dxu, dyu;
-    const bool chi = chi_adj<T>(p, a, i, j, dxu, dyu);
+    constexpr bool DEV = Prec<P>::DEV;
+    const long long b = (long long)j * p.nx + i;
+    T xi[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) xi[q] = lp.src[q][b];
+    if (i == 0 || i == p.nx - 1) {   // pending zero-gradient contributions of a column
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            if ((cx_of(q) == 1 && i == 0) || (cx_of(q) == -1 && i == p.nx - 1)) xi[q] += zg_in[zg_slot(q) * p.ny + j];
+    }
+
+    // forward intermediates (as in node_update)
+    T m[NQ];
+    moments9<T>(f, m);
+    const T rs = m[0];
+    const T rho = DEV ? par<T>(p.rho0, p.rho0f) + rs : rs;
+    const T inv_rho = recip(rho);
+    const T jx = m[3], jy = m[5];
+    T dx, dy;
+    const bool chi = chi_adj<T>(p, a, i, j, dx, dy);
+    const T gx = par<T>(p.gx, p.gxf), gy = par<T>(p.gy, p.gyf);
+    const T vx = jx * inv_rho + (T)0.5 * gx, vy = jy * inv_rho + (T)0.5 * gy;
+    T ax = 0, ay = 0, usx = 0, usy = 0, k = 0;
+    if (chi) {
+        usx = par<T>(a.vx, a.vxf) - par<T>(a.om, a.omf) * dy;
+        usy = par<T>(a.vy, a.vyf) + par<T>(a.om, a.omf) * dx;
+        k = par<T>(p.pen_k, p.pen_kf);
+        ax = -k * (vx - usx);
+        ay = -k * (vy - usy);
+    }
+    const T ux = vx + (T)0.5 * ax, uy = vy + (T)0.5 * ay;
+    const T Gx = rho * (gx + ax), Gy = rho * (gy + ay);
+    const T u2r = rho * (ux * ux + uy * uy);
+    const T uG = ux * Gx + uy * Gy;
+    const T W1 = rho * (ux * ux - uy * uy), W2 = ux * Gx - uy * Gy;
+    const T W3 = rho * ux * uy, W4 = ux * Gy + uy * Gx;
+    const T s1 = par<T>(p.s[1], p.sf[1]), s2 = par<T>(p.s[2], p.sf[2]), s4 = par<T>(p.s[4], p.sf[4]);
+    const T s6 = par<T>(p.s[6], p.sf[6]), s7 = par<T>(p.s[7], p.sf[7]), s8 = par<T>(p.s[8], p.sf[8]);
+    const T h1 = (T)1 - (T)0.5 * s1, h2 = (T)1 - (T)0.5 * s2, h4 = (T)1 - (T)0.5 * s4;
+    const T h6 = (T)1 - (T)0.5 * s6, h7 = (T)1 - (T)0.5 * s7, h8 = (T)1 - (T)0.5 * s8;
+
+    // adjoint of the post-collision moments: M^-T xi = diag(1/|row|^2) M xi
+    T L[NQ];
+    moments9<T>(xi, L);
+    L[0] *= (T)(1.0 / 9.0); L[1] *= (T)(1.0 / 36.0); L[2] *= (T)(1.0 / 36.0);
+    L[3] *= (T)(1.0 / 6.0); L[4] *= (T)(1.0 / 12.0); L[5] *= (T)(1.0 / 6.0);
+    L[6] *= (T)(1.0 / 12.0); L[7] *= (T)0.25; L[8] *= (T)0.25;
+
+    // parameter partials (before L is consumed)
+    const T e_eq = (T)-2 * rs + (T)3 * u2r;
+    g[1] = L[1] * (-(m[1] - e_eq) - (T)3 * uG);
+    g[2] = L[7] * (-(m[7] - W1) - W2);
+    g[3] = L[8] * (-(m[8] - W3) - (T)0.5 * W4);
+
+    // back through the relaxation (Eq. 17 in closed form)
+    T lm[NQ];   // adjoint of the pre-collision moments
+    lm[1] = ((T)1 - s1) * L[1];
+    lm[2] = ((T)1 - s2) * L[2];
+    lm[4] = ((T)1 - s4) * L[4];
+    lm[6] = ((T)1 - s6) * L[6];
+    lm[7] = ((T)1 - s7) * L[7];
+    lm[8] = ((T)1 - s8) * L[8];
+    T l_rs = L[0] - (T)2 * s1 * L[1] + s2 * L[2];
+    const T l_u2r = (T)3 * s1 * L[1] - (T)3 * s2 * L[2];
+    const T l_uG = (T)6 * h1 * L[1] - (T)6 * h2 * L[2];
+    T l_jx = L[3], l_jy = L[5];
+    T l_Gx = L[3] - h4 * L[4], l_Gy = L[5] - h6 * L[6];
+    T l_rho = -s4 * L[4] * ux - s6 * L[6] * uy;
+    T l_ux = -s4 * L[4] * rho, l_uy = -s6 * L[6] * rho;
+    const T lW1 = s7 * L[7], lW2 = (T)2 * h7 * L[7], lW3 = s8 * L[8], lW4 = h8 * L[8];
+    l_rho += lW1 * (ux * ux - uy * uy) + lW3 * ux * uy + l_u2r * (ux * ux + uy * uy);
+    l_ux += lW1 * (T)2 * rho * ux + lW2 * Gx + lW3 * rho * uy + lW4 * Gy + l_u2r * (T)2 * rho * ux + l_uG * Gx;
+    l_uy += -lW1 * (T)2 * rho * uy - lW2 * Gy + lW3 * rho * ux + lW4 * Gx + l_u2r * (T)2 * rho * uy + l_uG * Gy;
+    l_Gx += lW2 * ux + lW4 * uy + l_uG * ux;
+    l_Gy += -lW2 * uy + lW4 * ux + l_uG * uy;
+    // G = rho (g + a)
+    l_rho += l_Gx * (gx + ax) + l_Gy * (gy + ay);
+    T l_ax = rho * l_Gx + (T)0.5 * l_ux, l_ay = rho * l_Gy + (T)0.5 * l_uy;
+    T l_vx = l_ux, l_vy = l_uy;
+    if (chi) {
+        l_vx += -k * l_ax;
+        l_vy += -k * l_ay;
+        g[0] = k * k * ((vx - usx) * l_ax + (vy - usy) * l_ay);
+    }
+    // v = j / rho + g/2
+    l_jx += l_vx * inv_rho;
+    l_jy += l_vy * inv_rho;
+    l_rho += -(l_vx * jx + l_vy * jy) * (inv_rho * inv_rho);
+    l_rs += l_rho;
+    lm[0] = l_rs;
+    lm[3] = l_jx;
+    lm[5] = l_jy;
+    T out[NQ];
+    mt9<T>(lm, out);
     const T wx = par<T>(a.wx, a.wxf), wy = par<T>(a.wy, a.wyf);
+    if (chi) {   // the objective's momentum-exchange term at a solid node
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) out[q] += (T)cx_of(q) * wx + (T)cy_of(q) * wy;
+    }
+    // (b): mu_q(x) goes to the population its pull read, less the
+    // momentum-exchange own term [y in R(n)] dJ/dF_h . c of that node; a
+    // target can be solid only if the node's 3 x 3 neighbourhood meets the
+    // body's node range
+    const bool near = p.body.present && i + 1 >= a.ilo && i - 1 <= a.ihi && j + 1 >= a.jlo && j - 1 <= a.jhi;
+    auto own = [&](int q, int ti, int tj) -> T {
+        T ddx, ddy;
+        return near && chi_adj<T>(p, a, ti, tj, ddx, ddy) ? (T)cx_of(q) * wx + (T)cy_of(q) * wy : (T)0;
+    };
+    const long long ps = p.ps;
+    if (i > 0 && i < p.nx - 1 && j > 0 && j < p.ny - 1) {
+        if (near) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) lp.dst[q][b] = out[q] - own(q, i - cx_of(q), j - cy_of(q));
+        } else {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) lp.dst[q][b] = out[q];
+        }
+        return;
+    }
+    double gu = 0;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        T acc = 0;
-        // plain pull into (q, y + c_q), with periodic wrap
-        int ti = i + cx_of(q), tj = j + cy_of(q);
-        bool ok = true;
-        if (tj < 0 || tj >= ny) {
-            if (p.bc[tj < 0 ? VPLBM_SOUTH : VPLBM_NORTH] == VPLBM_BC_PERIODIC) tj = (tj + ny) % ny;
-            else ok = false;
+        int sd = -1;
+        const int kind = pull_kind(p, q, i, j, &sd);
+        if (kind == PULL_PLAIN) {
+            int ti = i - cx_of(q), tj = j - cy_of(q);
+            ti = ti < 0 ? ti + p.nx : (ti >= p.nx ? ti - p.nx : ti);
+            tj = tj < 0 ? tj + p.ny : (tj >= p.ny ? tj - p.ny : tj);
+            lam[q * ps + (long long)tj * p.nx + ti] = out[q] - own(q, ti, tj);
+        } else if (kind == PULL_WALL) {
+            const int o = opp_of(q);
+            lam[o * ps + b] = out[q] - own(o, i, j);
+            if (sd == VPLBM_WEST && cx_of(q) == 1 && grad_uin && p.bc[VPLBM_WEST] == VPLBM_BC_VELOCITY &&
+                p.wall_prof[VPLBM_WEST][0])
+                gu += (double)out[q] * 6.0 * w_of(q) * p.rho0;
+        } else {   // zero-gradient copy from (i, j - c_qy), picked up by the next reverse step
+            int tj = j - cy_of(q);
+            tj = tj < 0 ? tj + p.ny : (tj >= p.ny ? tj - p.ny : tj);
+            zg_out[zg_slot(q) * p.ny + tj] = out[q];
         }
-        if (ok && (ti < 0 || ti >= nx)) {
-            if (p.bc[ti < 0 ? VPLBM_WEST : VPLBM_EAST] == VPLBM_BC_PERIODIC) ti = (ti + nx) % nx;
-            else ok = false;
-        }
-        if (ok) {
-            int sd;
-            if (pull_kind(p, q, ti, tj, &sd) == PULL_PLAIN) acc += MU(q, ti, tj);
-        }
-        // wall pull into (opp(q), y) reads (q, y)
-        {
-            int sd;
-            if (pull_kind(p, opp_of(q), i, j, &sd) == PULL_WALL) acc += MU(opp_of(q), i, j);
-        }
-        // zero-gradient pull into (q, (i, j + c_qy)) reads (q, (i, j)) at an edge column
-        if (cx_of(q) != 0 && ((cx_of(q) == 1 && i == 0) || (cx_of(q) == -1 && i == nx - 1))) {
-            int zj = j + cy_of(q);
-            bool zok = true;
-            if (zj < 0 || zj >= ny) {
-                if (p.bc[zj < 0 ? VPLBM_SOUTH : VPLBM_NORTH] == VPLBM_BC_PERIODIC) zj = (zj + ny) % ny;
-                else zok = false;
-            }
-            if (zok) {
-                int sd;
-                if (pull_kind(p, q, i, zj, &sd) == PULL_ZEROGRAD) acc += MU(q, i, zj);
-            }
-        }
-        if (chi) acc -= (T)cx_of(q) * wx + (T)cy_of(q) * wy;
-        lam[q * ps + (long long)j * nx + i] = acc;
+        // a population that no pull reads (its opposite's pull here is a
+        // zero-gradient copy): only the own term
+        int sd2 = -1;
+        if (pull_kind(p, opp_of(q), i, j, &sd2) == PULL_ZEROGRAD) lam[q * ps + b] = -own(q, i, j);
     }
-    // inlet profile: the west velocity-wall pulls of this node
-    if (i == 0 && grad_uin && p.bc[VPLBM_WEST] == VPLBM_BC_VELOCITY && p.wall_prof[VPLBM_WEST][0]) {
-        double g = 0;
+    if (i == 0 && grad_uin && p.bc[VPLBM_WEST] == VPLBM_BC_VELOCITY && p.wall_prof[VPLBM_WEST][0]) grad_uin[j] += gu;
+}
+
+// The reverse step of one lattice step n, one node per thread: (a) mu =
+// (dC/df)^T L_{n+1} + objective term at every node, pushed (b) into L_n;
+// parameter partials into the warps' accumulators acc[warp][4]
+// (float-float in FP32, so no FP64 work and no block barrier; one writer
+// per slot and launch, hence deterministic sums); dJ/du_in at the west
+// inlet.  zg_in: the zero-gradient contributions to L_{n+1} left by the
+// previous reverse step (added as L_{n+1} is loaded); zg_out: this
+// step's, [6][ny].
+template <int P>
+__global__ void __launch_bounds__(ADJ_BLOCK, adj_minb<P>()) adj_fused(const StepParams p, const AdjStep a,
+                                                                 const LamPlanes<typename Prec<P>::T> lp,
+                                                                 const typename Prec<P>::T *zg_in,
+                                                                 typename Prec<P>::T *lam, typename Prec<P>::T *zg_out,
+                                                                 typename SumT<P>::A *acc, double *grad_uin)
+{
+    using T = typename Prec<P>::T;
+    using S = typename Prec<P>::S;
+    const int i = blockIdx.x * ADJ_BX + threadIdx.x;
+    const int j = blockIdx.y * ADJ_BY + threadIdx.y;
+    const int tid = threadIdx.y * ADJ_BX + threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    T g[4] = {0, 0, 0, 0};
+    if (i < p.nx && j < p.ny) {
+        T f[NQ];
+        pull_all<P>(p, static_cast<const S *>(p.fin), i, j, f);
+        adj_one_node<P>(p, a, lp, zg_in, lam, zg_out, grad_uin, i, j, f, g);
+    }
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            if (cx_of(q) != 1) continue;
-            int sd = -1;
-            if (pull_kind(p, q, i, j, &sd) == PULL_WALL && sd == VPLBM_WEST)
-                g += (double)MU(q, i, j) * 6.0 * w_of(q) * p.rho0;
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) g[q] += __shfl_down_sync(0xffffffffu, g[q], off);
+    }
+    if (lane == 0) {
+        using A = typename SumT<P>::A;
+        A *dst = acc + (((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (ADJ_BLOCK / 32) + warp) * 4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            A t = dst[q];
+            acc_add(t, g[q]);
+            dst[q] = t;
         }
-        grad_uin[j] += g;
     }
 }
 
+// Grid of the reverse kernel: tiles of ADJ_BX x ADJ_BY nodes.
+inline dim3 adj_grid(int nx, int ny) { return dim3((nx + ADJ_BX - 1) / ADJ_BX, (ny + ADJ_BY - 1) / ADJ_BY); }
+
 template <int P>
-cudaError_t launch_adjoint_step(const StepParams &p, const AdjStep &a, const void *lam_next, void *mu, void *lam,
-                                double *acc, double *grad_uin, cudaStream_t stream)
+cudaError_t launch_adjoint_step(const StepParams &p, const AdjStep &a, const void *lam_next, const void *zg_in, void *lam,
+                                void *zg_out, void *acc, double *grad_uin, cudaStream_t stream)
 {
     using T = typename Prec<P>::T;
-    dim3 block(256);
-    dim3 grid((p.nx + 255) / 256, p.ny);
-    adj_collide<P><<<grid, block, 0, stream>>>(p, a, static_cast<const T *>(lam_next), static_cast<T *>(mu), acc);
-    adj_stream<P><<<grid, block, 0, stream>>>(p, a, static_cast<const T *>(mu), static_cast<T *>(lam), grad_uin);
+    LamPlanes<T> lp;
+    for (int q = 0; q < NQ; ++q) {
+        lp.src[q] = static_cast<const T *>(lam_next) + q * p.ps;
+        lp.dst[q] = static_cast<T *>(lam) + q * p.ps - cx_host(q) - (long long)cy_host(q) * p.nx;
+    }
+    adj_fused<P><<<adj_grid(p.nx, p.ny), dim3(ADJ_BX, ADJ_BY), 0, stream>>>(p, a, lp, static_cast<const T *>(zg_in),
+                                                                 static_cast<T *>(lam), static_cast<T *>(zg_out),
+                                                                 static_cast<typename SumT<P>::A *>(acc), grad_uin);
     return cudaGetLastError();
 }
 
@@ -360,12 +402,15 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
     cudaStream_t st = c->stream;
     const long long step0 = c->nstep;
 
-    char *ckpt = nullptr, *store = nullptr, *work = nullptr;
-    double *dacc = nullptr;
+    char *ckpt = nullptr, *store = nullptr, *work = nullptr;   // work: lam[0], lam[1], zero-gradient rows [2][6][ny]
+    double *dacc = nullptr;   // the warps' parameter accumulators, then dJ/du_in [ny]
     void *final_f = nullptr;
     BodyState final_bs[2];
-    const dim3 grid((c->nx + 255) / 256, c->ny);
-    const size_t nacc = (size_t)grid.x * grid.y * 4;
+    // parameter partials: 4 accumulators per warp of the reverse kernel
+    // (FP32: float-float pairs, FP64: doubles), then the inlet gradient
+    const dim3 agrid = adj_grid(c->nx, c->ny);
+    const size_t nwarps = (size_t)agrid.x * agrid.y * (ADJ_BLOCK / 32);
+    const size_t acc_bytes = nwarps * 4 * (c->precision == VPLBM_F64 ? sizeof(double) : sizeof(float2));
     auto cleanup = [&]() {
         cudaFree(ckpt); cudaFree(store); cudaFree(work); cudaFree(dacc); cudaFree(final_f);
     };
@@ -379,12 +424,13 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
     } while (0)
     ATRY(cudaMalloc(&ckpt, pop * nck));
     ATRY(cudaMalloc(&store, pop * K));
-    ATRY(cudaMalloc(&work, lam_bytes * 3));
-    ATRY(cudaMalloc(&dacc, (nacc + (size_t)c->ny) * sizeof(double)));
+    const size_t zg_bytes = (size_t)6 * c->ny * es;
+    ATRY(cudaMalloc(&work, lam_bytes * 2 + 2 * zg_bytes));
+    ATRY(cudaMalloc(&dacc, acc_bytes + (size_t)c->ny * sizeof(double)));
     ATRY(cudaMalloc(&final_f, pop));
-    double *grad_uin = dacc + nacc;
-    ATRY(cudaMemsetAsync(work, 0, lam_bytes * 3, st));
-    ATRY(cudaMemsetAsync(dacc, 0, (nacc + c->ny) * sizeof(double), st));
+    double *grad_uin = reinterpret_cast<double *>(reinterpret_cast<char *>(dacc) + acc_bytes);
+    ATRY(cudaMemsetAsync(work, 0, lam_bytes * 2 + 2 * zg_bytes, st));
+    ATRY(cudaMemsetAsync(dacc, 0, acc_bytes + (size_t)c->ny * sizeof(double), st));
 
     // forward with a checkpoint every K steps
     for (long long s = 0; s < nck; ++s) {
@@ -426,7 +472,7 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
     const bool scalar = c->kernel != KERNEL_TMA;
     const int rbx = scalar ? c->bx : 256, rby = scalar ? c->by : 1;
     const int rminb = !scalar ? 5 : c->kernel == KERNEL_SCALAR_40 || c->kernel == KERNEL_FUSED2 ? 6 : c->kernel == KERNEL_SCALAR_48 ? 5 : 4;
-    int cur = 0;   // work: lam[0], lam[1], mu
+    int cur = 0;   // lam[cur] holds L_{n+1}, zero-gradient rows [cur] its pending column contributions
     for (long long s = nck - 1; s >= 0; --s) {
         const long long s0 = s * K, len = std::min(K, N - s0);
         // recompute the segment's states S_{s0} .. S_{s0+len-1}
@@ -469,26 +515,37 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
                 a.vxf = bsn.vxf; a.vyf = bsn.vyf; a.omf = bsn.omf;
                 a.wxf = (float)a.wx; a.wyf = (float)a.wy;
             }
-            void *lam_next = work + lam_bytes * cur, *lam_new = work + lam_bytes * (cur ^ 1), *mu = work + 2 * lam_bytes;
-            cudaError_t e = c->precision == VPLBM_F64
-                                ? launch_adjoint_step<VPLBM_F64>(p, a, lam_next, mu, lam_new, dacc, grad_uin, st)
-                                : launch_adjoint_step<VPLBM_F32_DEV>(p, a, lam_next, mu, lam_new, dacc, grad_uin, st);
+            void *lam_next = work + lam_bytes * cur, *lam_new = work + lam_bytes * (cur ^ 1);
+            void *zg_in = work + 2 * lam_bytes + zg_bytes * cur, *zg_out = work + 2 * lam_bytes + zg_bytes * (cur ^ 1);
+            cudaError_t e =
+                c->precision == VPLBM_F64
+                    ? launch_adjoint_step<VPLBM_F64>(p, a, lam_next, zg_in, lam_new, zg_out, dacc, grad_uin, st)
+                    : launch_adjoint_step<VPLBM_F32_DEV>(p, a, lam_next, zg_in, lam_new, zg_out, dacc, grad_uin, st);
             ATRY(e);
             cur ^= 1;
         }
     }
     // gradients
-    std::vector<double> acc(nacc + c->ny);
-    ATRY(cudaMemcpyAsync(acc.data(), dacc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    std::vector<char> accb(acc_bytes);
+    std::vector<double> guin(c->ny);
+    ATRY(cudaMemcpyAsync(accb.data(), dacc, acc_bytes, cudaMemcpyDeviceToHost, st));
+    ATRY(cudaMemcpyAsync(guin.data(), grad_uin, guin.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     // restore the state after the forward run
     ATRY(cudaMemcpyAsync(c->f[nfinal & 1], final_f, pop, cudaMemcpyDeviceToDevice, st));
     ATRY(cudaMemcpyAsync(c->bs, final_bs, sizeof final_bs, cudaMemcpyHostToDevice, st));
     ATRY(cudaStreamSynchronize(st));
     c->nstep = nfinal;
-    double g4[4] = {0, 0, 0, 0};
-    for (size_t blk = 0; blk < nacc / 4; ++blk)
-        for (int q = 0; q < 4; ++q) g4[q] += acc[blk * 4 + q];
-    for (int jj = 0; jj < c->ny; ++jj) grad[jj] = acc[nacc + jj];
+    double g4[4] = {0, 0, 0, 0};   // fixed-order sum over the warps' accumulators
+    for (size_t w = 0; w < nwarps; ++w)
+        for (int q = 0; q < 4; ++q) {
+            if (c->precision == VPLBM_F64) {
+                g4[q] += reinterpret_cast<const double *>(accb.data())[w * 4 + q];
+            } else {
+                const float2 v = reinterpret_cast<const float2 *>(accb.data())[w * 4 + q];
+                g4[q] += (double)v.x + (double)v.y;
+            }
+        }
+    for (int jj = 0; jj < c->ny; ++jj) grad[jj] = guin[jj];
     grad[c->ny] = g4[0];
     grad[c->ny + 1] = g4[2] + g4[3];
     grad[c->ny + 2] = g4[1];
