@@ -564,10 +564,10 @@ def run_batched(args, torch, stream):
     import paper_1905_05110_gb300 as vp
     from paper_1905_05110_gb300.viv import viv_response
     probs = wl.viv_sweep()
-    steps = probs[0]["steps"]
+    steps = args.sweep_steps or probs[0]["steps"]
     nodes = sum(p["nx"] * p["ny"] for p in probs)
     peak, _ = measured_peak()
-    k_cmp = 2000
+    k_cmp = min(2000, steps)
     b = vp.Batch(probs, precision="f32", history_capacity=steps + 64, stream=stream)
     b.init_from_problems()
     tuned = b.autotune(32)
@@ -612,7 +612,7 @@ def run_batched(args, torch, stream):
         s64.close()
     mlups64 = nodes * k_cmp / t64 / 1e6
     # accuracy: FP32 batched records against FP64 runs of the same members
-    acc_steps = 3000
+    acc_steps = min(3000, steps)
     order = sorted(range(len(probs)), key=lambda k: probs[k]["nx"] * probs[k]["ny"])
     acc = {}
     for label, k in (("smallest", order[0]), ("median", order[len(order) // 2]), ("largest", order[-1])):
@@ -669,6 +669,8 @@ def run_adjoint(args, torch, f64_compare):
     import paper_1905_05110_gb300 as vp
     p = wl.adjoint_disk()
     nsteps, ck = p["steps"], p["checkpoint_interval"]
+    if args.adjoint_steps and args.adjoint_steps != nsteps:   # a shorter run: checkpoints every sqrt(N)
+        nsteps, ck = args.adjoint_steps, max(1, int(round(args.adjoint_steps ** 0.5)))
     w0 = nsteps // 2
     nodes = p["nx"] * p["ny"]
     nparams = p["ny"] + 3
@@ -776,6 +778,10 @@ def main():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="", help="comma-separated subset of " + ",".join(LEGS) + " (default: all)")
+    ap.add_argument("--adjoint-steps", type=int, default=0,
+                    help="steps of the gradient leg (default: the workload's 20 000, checkpoints every 141)")
+    ap.add_argument("--sweep-steps", type=int, default=0,
+                    help="steps of the sweep leg's full run (default: the workload's 50 000)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
