@@ -411,8 +411,21 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
     const dim3 agrid = adj_grid(c->nx, c->ny);
     const size_t nwarps = (size_t)agrid.x * agrid.y * (ADJ_BLOCK / 32);
     const size_t acc_bytes = nwarps * 4 * (c->precision == VPLBM_F64 ? sizeof(double) : sizeof(float2));
+    // the reverse sweep recomputes segment s - 1 on a second stream while
+    // segment s runs its reverse steps: two segment stores, and events
+    // that order the two streams
+    cudaStream_t sr = nullptr;
+    BodyState *seg_bs = nullptr;   // [nck] body state at each segment's start
+    cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
     auto cleanup = [&]() {
-        cudaFree(ckpt); cudaFree(store); cudaFree(work); cudaFree(dacc); cudaFree(final_f);
+        if (sr) cudaStreamSynchronize(sr);
+        cudaStreamSynchronize(st);
+        for (int q = 0; q < 2; ++q) {
+            if (ev_rec[q]) cudaEventDestroy(ev_rec[q]);
+            if (ev_rev[q]) cudaEventDestroy(ev_rev[q]);
+        }
+        if (sr) cudaStreamDestroy(sr);
+        cudaFree(ckpt); cudaFree(store); cudaFree(work); cudaFree(dacc); cudaFree(final_f); cudaFree(seg_bs);
     };
 #define ATRY(expr)                                                                     \
     do {                                                                               \
@@ -423,7 +436,13 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
         }                                                                              \
     } while (0)
     ATRY(cudaMalloc(&ckpt, pop * nck));
-    ATRY(cudaMalloc(&store, pop * K));
+    ATRY(cudaMalloc(&store, pop * K * 2));
+    ATRY(cudaMalloc(&seg_bs, (size_t)nck * sizeof(BodyState)));
+    ATRY(cudaStreamCreateWithFlags(&sr, cudaStreamNonBlocking));
+    for (int q = 0; q < 2; ++q) {
+        ATRY(cudaEventCreateWithFlags(&ev_rec[q], cudaEventDisableTiming));
+        ATRY(cudaEventCreateWithFlags(&ev_rev[q], cudaEventDisableTiming));
+    }
     const size_t zg_bytes = (size_t)6 * c->ny * es;
     ATRY(cudaMalloc(&work, lam_bytes * 2 + 2 * zg_bytes));
     ATRY(cudaMalloc(&dacc, acc_bytes + (size_t)c->ny * sizeof(double)));
@@ -473,29 +492,57 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
     const int rbx = scalar ? c->bx : 256, rby = scalar ? c->by : 1;
     const int rminb = !scalar ? 5 : c->kernel == KERNEL_SCALAR_40 || c->kernel == KERNEL_FUSED2 ? 6 : c->kernel == KERNEL_SCALAR_48 ? 5 : 4;
     int cur = 0;   // lam[cur] holds L_{n+1}, zero-gradient rows [cur] its pending column contributions
+    // recompute the states S_{s0} .. S_{s0+len-1} of segment s into store
+    // slot set s & 1, on stream sr, straight from one slot to the next (the
+    // context's scalar kernel and block shape)
+    auto recompute = [&](long long s) -> cudaError_t {
+        const long long s0 = s * K, len = std::min(K, N - s0);
+        char *seg = store + pop * K * (s & 1);
+        c->nstep = step0 + s0;
+        cudaError_t e = cudaMemcpyAsync(c->bs + (c->nstep & 1), seg_bs + s, sizeof(BodyState), cudaMemcpyDeviceToDevice, sr);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(seg, ckpt + pop * s, pop, cudaMemcpyDeviceToDevice, sr);
+        for (long long k = 0; k + 1 < len && e == cudaSuccess; ++k) {
+            StepParams q = ctx_params(c, step0 + s0 + k);
+            q.fin = seg + pop * k;
+            q.fout = seg + pop * (k + 1);
+            set_planes(q, (int)es);
+            e = launch_step(c->precision, q, rbx, rby, sr, rminb);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev_rec[s & 1], sr);
+        return e;
+    };
+    // the body state at each segment's start, from the records (uploaded
+    // once: a copy from host memory per segment could stall the host)
+    {
+        std::vector<BodyState> bsv((size_t)nck);
+        for (long long q = 0; q < nck; ++q) {
+            const long long s0 = q * K;
+            BodyState &b = bsv[(size_t)q];
+            b = BodyState{};
+            b.q[0] = h[s0].x; b.q[1] = h[s0].y; b.q[2] = h[s0].theta;
+            b.v[0] = h[s0].vx; b.v[1] = h[s0].vy; b.v[2] = h[s0].omega;
+            b.step = step0 + s0;
+            derive_pose(b, c->has_body, c->has_body ? c->body_desc.radius : 0.0, c->nx, c->ny);
+        }
+        ATRY(cudaMemcpyAsync(seg_bs, bsv.data(), bsv.size() * sizeof(BodyState), cudaMemcpyHostToDevice, st));
+        ATRY(cudaStreamSynchronize(st));
+    }
+    // the first segments' slot sets are free
+    ATRY(cudaEventRecord(ev_rev[0], st));
+    ATRY(cudaEventRecord(ev_rev[1], st));
+    ATRY(cudaStreamWaitEvent(sr, ev_rev[0], 0));   // after the forward run
+    ATRY(recompute(nck - 1));
     for (long long s = nck - 1; s >= 0; --s) {
         const long long s0 = s * K, len = std::min(K, N - s0);
-        // recompute the segment's states S_{s0} .. S_{s0+len-1}
-        c->nstep = step0 + s0;
-        BodyState b{};
-        b.q[0] = h[s0].x; b.q[1] = h[s0].y; b.q[2] = h[s0].theta;
-        b.v[0] = h[s0].vx; b.v[1] = h[s0].vy; b.v[2] = h[s0].omega;
-        b.step = step0 + s0;
-        derive_pose(b, c->has_body, c->has_body ? c->body_desc.radius : 0.0, c->nx, c->ny);
-        ATRY(cudaMemcpyAsync(c->bs + (c->nstep & 1), &b, sizeof b, cudaMemcpyHostToDevice, st));
-        ATRY(cudaMemcpyAsync(store, ckpt + pop * s, pop, cudaMemcpyDeviceToDevice, st));
-        for (long long k = 0; k + 1 < len; ++k) {
-            // S_{s0+k} -> S_{s0+k+1} straight from one slot of the store to
-            // the next (the context's scalar kernel and block shape)
-            StepParams q = ctx_params(c, step0 + s0 + k);
-            q.fin = store + pop * k;
-            q.fout = store + pop * (k + 1);
-            set_planes(q, (int)es);
-            ATRY(launch_step(c->precision, q, rbx, rby, st, rminb));
+        if (s > 0) {   // segment s - 1 reuses the slots of segment s + 1, once its reverse steps are done
+            ATRY(cudaStreamWaitEvent(sr, ev_rev[(s - 1) & 1], 0));
+            ATRY(recompute(s - 1));
         }
+        ATRY(cudaStreamWaitEvent(st, ev_rec[s & 1], 0));
+        const char *seg = store + pop * K * (s & 1);
         for (long long n = s0 + len - 1; n >= s0; --n) {
             StepParams p = ctx_params(c, step0 + n);
-            p.fin = store + pop * (n - s0);
+            p.fin = seg + pop * (n - s0);
             set_planes(p, (int)es);
             AdjStep a;
             a.xg = h[n].x; a.yg = h[n].y;
@@ -524,6 +571,7 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
             ATRY(e);
             cur ^= 1;
         }
+        ATRY(cudaEventRecord(ev_rev[s & 1], st));
     }
     // gradients
     std::vector<char> accb(acc_bytes);
