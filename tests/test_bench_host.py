@@ -1,0 +1,60 @@
+"""Host logic of bench.py: the strips the CPU baseline cuts a workload
+into, the kernel a timed region is attributed to, and the config both arms
+of the comparison print."""
+import bench
+import workloads as wl
+
+
+def test_strips_cover_the_lattice_once_and_keep_the_body_once():
+    p = wl.oscillating_disk()
+    for n in (1, 3, 7, 16, 100):
+        strips = bench.strip_problems(p, n)
+        assert len(strips) == n
+        assert sum(q["ny"] for q in strips) == p["ny"]
+        assert all(q["nx"] == p["nx"] and q["ny"] >= 1 for q in strips)
+        with_body = [q for q in strips if q["body"] is not None]
+        assert len(with_body) == 1
+        # the body sits at the same place relative to its strip
+        lo = 0
+        for q in strips:
+            if q["body"] is not None:
+                assert q["body"]["y"] == p["body"]["y"] - lo
+                assert 0 <= q["body"]["y"] < q["ny"]
+                assert q["body"]["x"] == p["body"]["x"]
+            lo += q["ny"]
+        for q in strips:   # the cut edges are walls; west and east as the workload
+            assert q["bc"]["south"]["kind"] == q["bc"]["north"]["kind"] == "noslip"
+            assert q["bc"]["west"] == p["bc"]["west"] and q["bc"]["east"] == p["bc"]["east"]
+
+
+def test_dominant_kernel_follows_the_node_updates_of_the_region():
+    two = {"one_step": 0, "two_step": 10, "lookahead": 1, "tma": 0}
+    assert bench.dominant_kernel("f32", ("fused2", 256, 1), two) == "vp_mrt_step2<1, 0, 0>"
+    # 3 single steps against 2 two-step launches (4 steps): still the two-step kernel
+    mixed = {"one_step": 3, "two_step": 2, "lookahead": 1, "tma": 0}
+    assert bench.dominant_kernel("f32", ("fused2", 256, 1), mixed) == "vp_mrt_step2<1, 0, 0>"
+    single = {"one_step": 5, "two_step": 2, "lookahead": 1, "tma": 0}
+    assert bench.dominant_kernel("f32", ("fused2", 256, 1), single) == "vp_mrt_step<1, 6, 0, 0>"
+    assert bench.dominant_kernel("f64", ("scalar", 32, 4), {"one_step": 20}) == "vp_mrt_step<0, 4, 0, 0>"
+    assert bench.dominant_kernel("f16", ("pair", 32, 8), {"one_step": 20}) == "vp_mrt_step_pair<5, 0>"
+    assert bench.dominant_kernel("f32", ("tma", 256, 1), {"tma": 20}) == "vp_mrt_step_tma<1>"
+
+
+def test_both_arms_print_the_same_config():
+    p = wl.oscillating_disk()
+    a = bench.bench_config(p, "f32", 1)
+    assert a == bench.bench_config(p, "f32", 1)
+    assert a["workload"] == "oscillating_disk_2048x1024" and a["storage"] == "f32 deviation"
+    assert "151 MB" in a["l2"]   # 72 bytes per node update over 2 097 152 nodes
+
+
+def test_profiled_traffic_needs_a_matching_source_hash(tmp_path, monkeypatch):
+    k = "vp_mrt_step2<1, 0, 0>"
+    monkeypatch.setattr(bench, "PROFILE_DIR", str(tmp_path))
+    stem = "vp_mrt_step2_1_0_0_w"
+    (tmp_path / f"{stem}.md").write_text(f"dram_bytes_per_launch_full_size: 1.5e+08\n"
+                                         f"kernel_source_sha256_16: {bench.kernel_source_hash(k)}\n")
+    assert bench.profiled_traffic(k, "w") == 1.5e8
+    (tmp_path / f"{stem}.md").write_text("dram_bytes_per_launch_full_size: 1.5e+08\n"
+                                         "kernel_source_sha256_16: 0000000000000000\n")
+    assert bench.profiled_traffic(k, "w") is None
