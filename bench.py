@@ -721,6 +721,12 @@ def run_adjoint(args, torch, f64_compare):
             "grad_rel_diff_f32_vs_f64": float(np.linalg.norm(grads["f32"] - grads["f64"]) /
                                               np.linalg.norm(grads["f64"])),
             "gbs_at_216_bytes_per_node_step": gbs, "frac_of_hbm": gbs / peak,
+            # every phase of the call: the forward run with its checkpoints
+            # (72 B per node-step), the recomputation (72) and the reverse
+            # kernel (pulled state and incoming adjoint read, outgoing adjoint
+            # written: 108)
+            "gbs_all_phases_252_bytes_per_node_step": 252 * nodes * nsteps / secs["f32"] / 1e9,
+            "frac_of_hbm_all_phases": 252 * nodes * nsteps / secs["f32"] / 1e9 / peak,
             "forward_f32_seconds": t_fwd32, "forward_f64_seconds_measured": t_fwd64,
             "speedup_vs_fd_f64": 2 * nparams * t_fwd64 / secs["f32"],
             "speedup_vs_fd_f64_how": "2 x 515 FP64 forward runs at the mean CUDA-event time of the 16 FD runs "
