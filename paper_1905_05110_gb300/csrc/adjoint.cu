@@ -144,7 +144,7 @@ template <typename T> struct LamPlanes {
 // The reverse step at node (i, j) with its pulled populations f: (a) mu =
 // (dC/df)^T L_{n+1} + objective term, (b) mu pushed into L_n, the
 // parameter partials into g.
-template <int P>
+template <int P, bool EDGE>
 __device__ __forceinline__ void adj_one_node(const StepParams &p, const AdjStep &a,
                                              const LamPlanes<typename Prec<P>::T> &lp,
                                              const typename Prec<P>::T *zg_in, typename Prec<P>::T *lam,
@@ -157,7 +157,7 @@ __device__ __forceinline__ void adj_one_node(const StepParams &p, const AdjStep 
     T xi[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) xi[q] = lp.src[q][b];
-    if (i == 0 || i == p.nx - 1) {   // pending zero-gradient contributions of a column
+    if (EDGE && (i == 0 || i == p.nx - 1)) {   // pending zero-gradient contributions of a column
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
             if ((cx_of(q) == 1 && i == 0) || (cx_of(q) == -1 && i == p.nx - 1)) xi[q] += zg_in[zg_slot(q) * p.ny + j];
@@ -261,7 +261,7 @@ __device__ __forceinline__ void adj_one_node(const StepParams &p, const AdjStep 
         return near && chi_adj<T>(p, a, ti, tj, ddx, ddy) ? (T)cx_of(q) * wx + (T)cy_of(q) * wy : (T)0;
     };
     const long long ps = p.ps;
-    if (i > 0 && i < p.nx - 1 && j > 0 && j < p.ny - 1) {
+    if (!EDGE || (i > 0 && i < p.nx - 1 && j > 0 && j < p.ny - 1)) {
         if (near) {
 #pragma unroll
             for (int q = 0; q < NQ; ++q) lp.dst[q][b] = out[q] - own(q, i - cx_of(q), j - cy_of(q));
@@ -271,6 +271,7 @@ __device__ __forceinline__ void adj_one_node(const StepParams &p, const AdjStep 
         }
         return;
     }
+    if constexpr (!EDGE) return;
     double gu = 0;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -300,6 +301,54 @@ __device__ __forceinline__ void adj_one_node(const StepParams &p, const AdjStep 
     if (i == 0 && grad_uin && p.bc[VPLBM_WEST] == VPLBM_BC_VELOCITY && p.wall_prof[VPLBM_WEST][0]) grad_uin[j] += gu;
 }
 
+// Layout of the reverse kernel's grid (1-D): the interior nodes
+// [1, nx - 2] x [1, ny - 2] in tiles of ADJ_BX x ADJ_BY aligned on x = 0
+// (rows of a warp stay on 128-byte boundaries; the lanes on columns 0 and
+// nx - 1 idle), which take no boundary rule, so their warps never diverge
+// into one; the perimeter nodes, ADJ_BLOCK per block, come first (their
+// blocks take the boundary rules and run longest, and the last blocks of a
+// launch set its end; a lattice less than 3 nodes wide or high is all
+// perimeter, taken row by row).
+struct AdjLayout {
+    int itx, ity;    // interior tiles in x and y (0 when there is no interior)
+    int nper;        // perimeter nodes
+    int blocks;      // interior tiles + perimeter blocks
+};
+
+inline AdjLayout adj_layout(int nx, int ny)
+{
+    AdjLayout l;
+    if (nx >= 3 && ny >= 3) {
+        l.itx = (nx + ADJ_BX - 1) / ADJ_BX;
+        l.ity = (ny - 2 + ADJ_BY - 1) / ADJ_BY;
+        l.nper = 2 * nx + 2 * (ny - 2);
+    } else {
+        l.itx = l.ity = 0;
+        l.nper = nx * ny;
+    }
+    l.blocks = l.itx * l.ity + (l.nper + ADJ_BLOCK - 1) / ADJ_BLOCK;
+    return l;
+}
+
+// Perimeter node k of an nx x ny lattice (the layout above).
+__device__ __forceinline__ void perimeter_node(int nx, int ny, int k, int &i, int &j)
+{
+    if (nx < 3 || ny < 3) {
+        i = k % nx;
+        j = k / nx;
+    } else if (k < nx) {
+        i = k;
+        j = 0;
+    } else if (k < 2 * nx) {
+        i = k - nx;
+        j = ny - 1;
+    } else {
+        const int r = k - 2 * nx;
+        j = 1 + (r >> 1);
+        i = (r & 1) ? nx - 1 : 0;
+    }
+}
+
 // The reverse step of one lattice step n, one node per thread: (a) mu =
 // (dC/df)^T L_{n+1} + objective term at every node, pushed (b) into L_n;
 // parameter partials into the warps' accumulators acc[warp][4]
@@ -313,19 +362,33 @@ __global__ void __launch_bounds__(ADJ_BLOCK, adj_minb<P>()) adj_fused(const Step
                                                                  const LamPlanes<typename Prec<P>::T> lp,
                                                                  const typename Prec<P>::T *zg_in,
                                                                  typename Prec<P>::T *lam, typename Prec<P>::T *zg_out,
-                                                                 typename SumT<P>::A *acc, double *grad_uin)
+                                                                 typename SumT<P>::A *acc, double *grad_uin,
+                                                                 const AdjLayout lay)
 {
     using T = typename Prec<P>::T;
     using S = typename Prec<P>::S;
-    const int i = blockIdx.x * ADJ_BX + threadIdx.x;
-    const int j = blockIdx.y * ADJ_BY + threadIdx.y;
     const int tid = threadIdx.y * ADJ_BX + threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    const int nperb = (lay.nper + ADJ_BLOCK - 1) / ADJ_BLOCK;
     T g[4] = {0, 0, 0, 0};
-    if (i < p.nx && j < p.ny) {
-        T f[NQ];
-        pull_all<P>(p, static_cast<const S *>(p.fin), i, j, f);
-        adj_one_node<P>(p, a, lp, zg_in, lam, zg_out, grad_uin, i, j, f, g);
+    if ((int)blockIdx.x >= nperb) {
+        const int bi = (int)blockIdx.x - nperb;
+        const int i = (bi % lay.itx) * ADJ_BX + threadIdx.x;
+        const int j = 1 + (bi / lay.itx) * ADJ_BY + threadIdx.y;
+        if (i >= 1 && i < p.nx - 1 && j < p.ny - 1) {
+            T f[NQ];
+            pull_all<P, true>(p, static_cast<const S *>(p.fin), i, j, f);
+            adj_one_node<P, false>(p, a, lp, zg_in, lam, zg_out, grad_uin, i, j, f, g);
+        }
+    } else {
+        const int k = (int)blockIdx.x * ADJ_BLOCK + tid;
+        if (k < lay.nper) {
+            int i, j;
+            perimeter_node(p.nx, p.ny, k, i, j);
+            T f[NQ];
+            pull_all<P>(p, static_cast<const S *>(p.fin), i, j, f);
+            adj_one_node<P, true>(p, a, lp, zg_in, lam, zg_out, grad_uin, i, j, f, g);
+        }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -334,7 +397,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK, adj_minb<P>()) adj_fused(const Step
     }
     if (lane == 0) {
         using A = typename SumT<P>::A;
-        A *dst = acc + (((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (ADJ_BLOCK / 32) + warp) * 4;
+        A *dst = acc + ((size_t)blockIdx.x * (ADJ_BLOCK / 32) + warp) * 4;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             A t = dst[q];
@@ -343,9 +406,6 @@ __global__ void __launch_bounds__(ADJ_BLOCK, adj_minb<P>()) adj_fused(const Step
         }
     }
 }
-
-// Grid of the reverse kernel: tiles of ADJ_BX x ADJ_BY nodes.
-inline dim3 adj_grid(int nx, int ny) { return dim3((nx + ADJ_BX - 1) / ADJ_BX, (ny + ADJ_BY - 1) / ADJ_BY); }
 
 template <int P>
 cudaError_t launch_adjoint_step(const StepParams &p, const AdjStep &a, const void *lam_next, const void *zg_in, void *lam,
@@ -357,9 +417,10 @@ cudaError_t launch_adjoint_step(const StepParams &p, const AdjStep &a, const voi
         lp.src[q] = static_cast<const T *>(lam_next) + q * p.ps;
         lp.dst[q] = static_cast<T *>(lam) + q * p.ps - cx_host(q) - (long long)cy_host(q) * p.nx;
     }
-    adj_fused<P><<<adj_grid(p.nx, p.ny), dim3(ADJ_BX, ADJ_BY), 0, stream>>>(p, a, lp, static_cast<const T *>(zg_in),
+    const AdjLayout lay = adj_layout(p.nx, p.ny);
+    adj_fused<P><<<lay.blocks, dim3(ADJ_BX, ADJ_BY), 0, stream>>>(p, a, lp, static_cast<const T *>(zg_in),
                                                                  static_cast<T *>(lam), static_cast<T *>(zg_out),
-                                                                 static_cast<typename SumT<P>::A *>(acc), grad_uin);
+                                                                 static_cast<typename SumT<P>::A *>(acc), grad_uin, lay);
     return cudaGetLastError();
 }
 
@@ -408,8 +469,7 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
     BodyState final_bs[2];
     // parameter partials: 4 accumulators per warp of the reverse kernel
     // (FP32: float-float pairs, FP64: doubles), then the inlet gradient
-    const dim3 agrid = adj_grid(c->nx, c->ny);
-    const size_t nwarps = (size_t)agrid.x * agrid.y * (ADJ_BLOCK / 32);
+    const size_t nwarps = (size_t)adj_layout(c->nx, c->ny).blocks * (ADJ_BLOCK / 32);
     const size_t acc_bytes = nwarps * 4 * (c->precision == VPLBM_F64 ? sizeof(double) : sizeof(float2));
     // the reverse sweep recomputes segment s - 1 on a second stream while
     // segment s runs its reverse steps: two segment stores, and events
