@@ -46,6 +46,8 @@ struct vplbm_batch {
     int rows = 8;                     // tiles per block, stacked in y
     StepParams *params_dev = nullptr; // [2][n]: parameters of each member per step parity
     int *tile_start_dev = nullptr;    // [n + 1]
+    int2 *tile_map_dev = nullptr;     // [total_tiles]: (member, macro tile within the member)
+    long long tile_map_cap = 0;
     int total_tiles = 0;
     int mode = VPLBM_BATCH_BRANCHES;
     std::vector<cudaStream_t> branch;  // capture streams of the per-member graph branches
@@ -59,7 +61,9 @@ struct vplbm_batch {
 namespace {
 
 // Macro-tile prefix of the members for blocks of bx x by threads that run
-// `rows` tiles each.
+// `rows` tiles each, and the map from a block (macro tile) to its member
+// and its macro tile within the member, so that a block finds both with
+// one load.
 vplbm_status build_tiles(vplbm_batch *b)
 {
     std::vector<int> start(b->n + 1, 0);
@@ -72,9 +76,27 @@ vplbm_status build_tiles(vplbm_batch *b)
     }
     if (total > (1LL << 30)) return berr(VPLBM_EINVAL, "batch too large (%lld tiles)", total);
     start[b->n] = (int)total;
+    std::vector<int2> map;
+    try {
+        map.resize((size_t)total);
+    } catch (...) {
+        return berr(VPLBM_ENOMEM, "host allocation failed");
+    }
+    for (int k = 0; k < b->n; ++k)
+        for (int t = start[k]; t < start[k + 1]; ++t) map[(size_t)t] = make_int2(k, t - start[k]);
+    if (total > b->tile_map_cap) {
+        if (b->tile_map_dev) cudaFree(b->tile_map_dev);
+        b->tile_map_dev = nullptr;
+        b->tile_map_cap = 0;
+        if (cudaMalloc(&b->tile_map_dev, (size_t)total * sizeof(int2)) != cudaSuccess)
+            return berr(VPLBM_ENOMEM, "tile map allocation failed");
+        b->tile_map_cap = total;
+    }
     b->total_tiles = (int)total;
     cudaError_t e = cudaMemcpyAsync(b->tile_start_dev, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice,
                                     b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->tile_map_dev, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return berr(VPLBM_ECUDA, "tile table upload failed: %s", cudaGetErrorString(e));
     return VPLBM_OK;
@@ -103,7 +125,7 @@ cudaError_t launch_batch_step(const vplbm_batch *b, long long step, cudaStream_t
     }
     BatchLaunch bl;
     bl.params = b->params_dev + (size_t)(step & 1) * b->n;
-    bl.tile_start = b->tile_start_dev;
+    bl.tile_map = b->tile_map_dev;
     bl.n = b->n;
     bl.rows = b->rows;
     bl.collision = b->collision;
@@ -249,6 +271,7 @@ void vplbm_batch_destroy(vplbm_batch *b)
     if (b->capture) cudaStreamDestroy(b->capture);
     if (b->params_dev) cudaFree(b->params_dev);
     if (b->tile_start_dev) cudaFree(b->tile_start_dev);
+    if (b->tile_map_dev) cudaFree(b->tile_map_dev);
     for (vplbm_ctx *c : b->members) vplbm_destroy(c);
     delete b;
 }

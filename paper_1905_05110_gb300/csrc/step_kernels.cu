@@ -29,10 +29,11 @@ namespace {
 
 // Every member of a batch in one launch: block b runs macro tile b of the
 // concatenated macro-tile lists (bl.rows tiles of blockDim.x x blockDim.y
-// stacked in y); its member is found in the macro-tile prefix and its step
-// parameters are staged in shared memory.  The lookup and the staging read
-// only data that no step writes, so they run before the wait on the previous
-// step's grid (programmatic dependent launch).
+// stacked in y); its member and its macro tile within the member come from
+// the tile map (one load), and the member's step parameters are staged in
+// shared memory.  The lookup and the staging read only data that no step
+// writes, so they run before the wait on the previous step's grid
+// (programmatic dependent launch).
 template <int P, int COLL>
 __global__ void __launch_bounds__(256, 5) vp_mrt_step_batch(const BatchLaunch bl)
 {
@@ -42,14 +43,9 @@ __global__ void __launch_bounds__(256, 5) vp_mrt_step_batch(const BatchLaunch bl
     __shared__ __align__(16) StepParams sp;
     __shared__ int s_member, s_local;
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-        int lo = 0, hi = bl.n - 1;   // last member whose first macro tile is <= blockIdx.x
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (bl.tile_start[mid] <= (int)blockIdx.x) lo = mid;
-            else hi = mid - 1;
-        }
-        s_member = lo;
-        s_local = (int)blockIdx.x - bl.tile_start[lo];
+        const int2 ml = __ldg(bl.tile_map + blockIdx.x);
+        s_member = ml.x;
+        s_local = ml.y;
     }
     __syncthreads();
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;

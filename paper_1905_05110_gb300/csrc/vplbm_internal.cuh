@@ -254,7 +254,7 @@ cudaError_t launch_lookahead(const StepParams &p, cudaStream_t stream);
 // Batched launch of the scalar step over many lattices.
 struct BatchLaunch {
     const StepParams *params;   // one per member (device), for this step's parity
-    const int *tile_start;      // n + 1 prefix sums of the members' macro-tile counts (device)
+    const int2 *tile_map;       // per macro tile (block): its member and its macro tile within the member (device)
     int n;
     int rows;                   // tiles per macro tile (stacked in y), one macro tile per block
     int collision;              // shared by every member (host-side dispatch)
