@@ -34,11 +34,11 @@
 namespace vplbm {
 namespace {
 
-constexpr int ADJ_BX = 32, ADJ_BY = 8;   // block of the reverse kernel (a tile of nodes)
+constexpr int ADJ_BX = 32, ADJ_BY = 4;   // block of the reverse kernel (a tile of nodes)
 constexpr int ADJ_BLOCK = ADJ_BX * ADJ_BY;
-// blocks per SM the reverse kernel's register budget is sized for: 64
-// registers in FP32, 96 in FP64 (no spills)
-template <int P> constexpr int adj_minb() { return P == VPLBM_F64 ? 2 : 4; }
+// blocks of 128 threads per SM the reverse kernel's register budget is
+// sized for: 64 registers in FP32, 128 in FP64 (no spills)
+template <int P> constexpr int adj_minb() { return P == VPLBM_F64 ? 4 : 8; }
 inline int cx_host(int q) { static const int c[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1}; return c[q]; }
 inline int cy_host(int q) { static const int c[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1}; return c[q]; }
 
