@@ -292,8 +292,8 @@ vplbm_status vplbm_get_body_k(vplbm_ctx *ctx, int k, double q[3], double v[3], l
  *                          block_y) given to vplbm_set_launch (0 x 0: the
  *                          current blocks).  Its populations equal the
  *                          scalar kernel's bit for bit.
- *  VPLBM_KERNEL_PAIR       two x-adjacent nodes per thread (FP16 storage,
- *                          MRT collision, one body, even nx): a block of
+ *  VPLBM_KERNEL_PAIR       two x-adjacent nodes per thread (FP32 or FP16
+ *                          storage, MRT collision, one body, even nx): a block of
  *                          block_x x block_y threads updates a tile of
  *                          2 block_x x block_y nodes, loading the pulls of
  *                          both nodes, running the update on paired FP32
@@ -424,8 +424,8 @@ vplbm_status vplbm_batch_get_mode(vplbm_batch *batch, int *mode);
 vplbm_status vplbm_batch_set_launch(vplbm_batch *batch, int block_x, int block_y, int tiles_per_block);
 vplbm_status vplbm_batch_get_launch(vplbm_batch *batch, int *block_x, int *block_y, int *tiles_per_block,
                                    long long *launches);
-/* Time the branch mode with four member launch choices (every member set to
- * one scalar kernel and block shape) and six tile-mode launch shapes over
+/* Time the branch mode with six member launch choices (every member set to
+ * one scalar or node-pair kernel and block shape) and six tile-mode launch shapes over
  * 2 x steps_per_trial steps each (rounded up to whole 32-step graphs) and
  * keep the fastest (members keep the winning launch choice; the tile-mode
  * launch shape is the fastest tile shape whichever mode won, so that

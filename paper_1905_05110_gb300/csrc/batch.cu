@@ -425,10 +425,12 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int steps_per_trial)
     vplbm_status st = VPLBM_OK;
     // branch mode with every member on one scalar kernel and block shape
     // (mode, kernel, bx, by), then tile-mode shapes (mode, bx, by, rows)
-    const int cands[10][4] = {{VPLBM_BATCH_BRANCHES, KERNEL_SCALAR_40, 256, 1},
+    const int cands[12][4] = {{VPLBM_BATCH_BRANCHES, KERNEL_SCALAR_40, 256, 1},
                               {VPLBM_BATCH_BRANCHES, KERNEL_SCALAR_48, 256, 1},
                               {VPLBM_BATCH_BRANCHES, KERNEL_SCALAR_48, 128, 2},
                               {VPLBM_BATCH_BRANCHES, KERNEL_SCALAR_40, 64, 2},
+                              {VPLBM_BATCH_BRANCHES, KERNEL_PAIR, 32, 8},
+                              {VPLBM_BATCH_BRANCHES, KERNEL_PAIR, 64, 4},
                               {VPLBM_BATCH_TILES, 256, 1, 8}, {VPLBM_BATCH_TILES, 256, 1, 4},
                               {VPLBM_BATCH_TILES, 256, 1, 16}, {VPLBM_BATCH_TILES, 128, 2, 4},
                               {VPLBM_BATCH_TILES, 128, 1, 8}, {VPLBM_BATCH_TILES, 256, 1, 1}};

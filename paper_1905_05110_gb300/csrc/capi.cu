@@ -296,7 +296,7 @@ const char *fused2_refusal(const vplbm_ctx *c)
 // Why the node-pair kernel cannot run this context (nullptr: it can).
 const char *pair_refusal(const vplbm_ctx *c)
 {
-    if (c->precision != VPLBM_F16_DEV) return "the node-pair kernel needs FP16 storage";
+    if (c->precision == VPLBM_F64) return "the node-pair kernel needs FP32 or FP16 storage";
     if (c->collision != VPLBM_COLLISION_MRT) return "the node-pair kernel runs the MRT collision";
     if (c->nbodies > 1) return "the node-pair kernel takes one body";
     if (c->nx & 1) return "the node-pair kernel needs an even nx";

@@ -1,15 +1,14 @@
-// The node-pair step kernel for FP16-deviation storage: the one-step fused
-// update of Algorithm 1 with two x-adjacent nodes per thread.
+// The node-pair step kernel for FP32- and FP16-deviation storage: the
+// one-step fused update of Algorithm 1 with two x-adjacent nodes per thread.
 //
-// FP16 storage halves the bytes of a node update against FP32, but the
-// one-node-per-thread kernel then runs out of instruction issue before it
-// runs out of bandwidth.  Here a thread of an interior tile away from the
-// body loads the two nodes' pulls (one 32-bit load for the three
-// populations with c_ax = 0, two 16-bit loads for the others), runs the
-// MRT update once on float2 lanes with paired FP32 instructions
-// (mrt_dev_lanes<Lane2>: every lane rounds as the scalar update does, so
-// the populations are those of the one-node kernel bit for bit) and stores
-// the nine results as 32-bit pairs.  Tiles on a lattice edge or meeting the
+// The one-node-per-thread kernel runs out of instruction issue before it
+// runs out of bandwidth in FP16 storage, and comes close to it in FP32.
+// Here a thread of an interior tile away from the body loads the two
+// nodes' pulls (one aligned pair load for the three populations with
+// c_ax = 0, two single loads for the others), runs the MRT update once on
+// float2 lanes with paired FP32 instructions (mrt_dev_lanes<Lane2>: every
+// lane rounds as the scalar update does, so the populations are those of
+// the one-node kernel bit for bit) and stores the nine results as pairs.  Tiles on a lattice edge or meeting the
 // body's node range take the one-node code for each of their nodes.
 //
 // Grid: the scalar kernel's body blocks first (tiles of blockDim.x x
@@ -26,15 +25,11 @@ namespace {
 // registers; 40 and 64 measured within 2 % of it, 5 blocks per SM ahead).
 constexpr int PAIR_MINB = 5;
 
-__device__ __forceinline__ float2 ld_pair(const __half *p) { return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p))); }
-__device__ __forceinline__ float2 ld_two(const __half *p) { return make_float2(__half2float(__ldg(p)), __half2float(__ldg(p + 1))); }
-
 // Nodes (i, j), (i + 1, j) of one pair tile, i even.
-template <int SHAPE>
+template <int P, int SHAPE>
 __device__ __forceinline__ void pair_tile(const StepParams &p, int tile_x, int tile_y)
 {
-    constexpr int P = VPLBM_F16_DEV;
-    using S = __half;
+    using S = typename Prec<P>::S;
     const int w = 2 * (int)blockDim.x;
     const int bi0 = tile_x * w, bj0 = tile_y * (int)blockDim.y;
     const int i = bi0 + 2 * (int)threadIdx.x, j = bj0 + (int)threadIdx.y;
@@ -61,7 +56,7 @@ __device__ __forceinline__ void pair_tile(const StepParams &p, int tile_x, int t
 #pragma unroll
     for (int a = 0; a < NQ; ++a) {
         const S *src = static_cast<const S *>(p.src_plane[a]) + b;
-        f2[a] = cx_of(a) == 0 ? ld_pair(src) : ld_two(src);
+        f2[a] = cx_of(a) == 0 ? ld_pair_g(src) : ld_two_g(src);
     }
     const int4 range = __ldg(reinterpret_cast<const int4 *>(&bs->ilo));
     if (range.x <= range.y && tile_near_body(range, bi0, bj0, w, blockDim.y, false)) {
@@ -77,13 +72,13 @@ __device__ __forceinline__ void pair_tile(const StepParams &p, int tile_x, int t
     S *const *dp = reinterpret_cast<S *const *>(p.dst_plane);
     float ax, ay;
     mrt_dev_lanes<Lane2>(p, f2, false, 0.f, 0.f, bs,
-                         [&](int a, float2 v) { *reinterpret_cast<__half2 *>(dp[a] + b) = __floats2half2_rn(v.x, v.y); },
+                         [&](int a, float2 v) { st_pair(dp[a] + b, v); },
                          ax, ay);
 }
 
 // MINB: blocks of 256 threads per SM the register budget is sized for.
 // Programmatic dependent launch as in the one-node kernel.
-template <int MINB, int SHAPE>
+template <int P, int MINB, int SHAPE>
 __global__ void __launch_bounds__(256, MINB) vp_mrt_step_pair(const StepParams p)
 {
     __shared__ double red[8][NPART];
@@ -105,8 +100,7 @@ __global__ void __launch_bounds__(256, MINB) vp_mrt_step_pair(const StepParams p
             nrect = rw * (range.w / (int)blockDim.y - ty0 + 1);
         }
         if (b < nrect)
-            scalar_tile<VPLBM_F16_DEV, VPLBM_COLLISION_MRT, SHAPE>(p, tx0 + b % rw, ty0 + b / rw, red, rows, &s_last,
-                                                                 true);
+            scalar_tile<P, VPLBM_COLLISION_MRT, SHAPE>(p, tx0 + b % rw, ty0 + b / rw, red, rows, &s_last, true);
         if (b == 0 && nrect > p.nbody && threadIdx.x == 0 && threadIdx.y == 0) *p.err |= ERR_INTERNAL;
         if (b == 0 && threadIdx.x == 0 && threadIdx.y == 0 && prescribed_motion(p)) advance_prescribed(p);
         return;
@@ -117,10 +111,10 @@ __global__ void __launch_bounds__(256, MINB) vp_mrt_step_pair(const StepParams p
     // blocks of the launch
     const int ntx = gridDim.x, nty = gridDim.y - nbr;
     const int c = blockIdx.x, r = blockIdx.y - nbr;
-    pair_tile<SHAPE>(p, c == 0 ? 0 : (c == 1 ? ntx - 1 : c - 1), r == 0 ? 0 : (r == 1 ? nty - 1 : r - 1));
+    pair_tile<P, SHAPE>(p, c == 0 ? 0 : (c == 1 ? ntx - 1 : c - 1), r == 0 ? 0 : (r == 1 ? nty - 1 : r - 1));
 }
 
-template <int SHAPE>
+template <int P, int SHAPE>
 cudaError_t launch_pair_t(const StepParams &p0, int bx, int by, cudaStream_t stream)
 {
     StepParams p = p0;
@@ -138,7 +132,7 @@ cudaError_t launch_pair_t(const StepParams &p0, int bx, int by, cudaStream_t str
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, vp_mrt_step_pair<PAIR_MINB, SHAPE>, p);
+    return cudaLaunchKernelEx(&cfg, vp_mrt_step_pair<P, PAIR_MINB, SHAPE>, p);
 }
 
 }  // namespace
@@ -152,10 +146,17 @@ long long pair_grid_rows(int nx, int ny, double radius, int present, int bx, int
 
 cudaError_t launch_step_pair(int precision, const StepParams &p, int bx, int by, cudaStream_t stream)
 {
-    if (precision != VPLBM_F16_DEV || p.collision != VPLBM_COLLISION_MRT || p.nbodies > 1 || (p.nx & 1))
-        return cudaErrorInvalidValue;
-    if (p.body.present && p.body.shape != VPLBM_SHAPE_DISK) return launch_pair_t<SHAPE_ANY>(p, bx, by, stream);
-    return launch_pair_t<VPLBM_SHAPE_DISK>(p, bx, by, stream);
+    if (p.collision != VPLBM_COLLISION_MRT || p.nbodies > 1 || (p.nx & 1)) return cudaErrorInvalidValue;
+    const bool disk = !p.body.present || p.body.shape == VPLBM_SHAPE_DISK;
+    switch (precision) {
+    case VPLBM_F32_DEV:
+        return disk ? launch_pair_t<VPLBM_F32_DEV, VPLBM_SHAPE_DISK>(p, bx, by, stream)
+                    : launch_pair_t<VPLBM_F32_DEV, SHAPE_ANY>(p, bx, by, stream);
+    case VPLBM_F16_DEV:
+        return disk ? launch_pair_t<VPLBM_F16_DEV, VPLBM_SHAPE_DISK>(p, bx, by, stream)
+                    : launch_pair_t<VPLBM_F16_DEV, SHAPE_ANY>(p, bx, by, stream);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace vplbm

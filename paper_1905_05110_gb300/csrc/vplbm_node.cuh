@@ -25,6 +25,20 @@ __device__ __forceinline__ void stv(double *p, double x) { *p = x; }
 __device__ __forceinline__ void stv(float *p, float x) { *p = x; }
 __device__ __forceinline__ void stv(__half *p, float x) { *p = __float2half_rn(x); }
 
+// Pairs of x-adjacent populations (the node-pair paths): an aligned pair
+// from global memory or a shared-memory stage, two single values (a pair
+// that straddles the alignment), an aligned pair store.
+__device__ __forceinline__ float2 ld_pair_g(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+__device__ __forceinline__ float2 ld_pair_g(const __half *p) { return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p))); }
+__device__ __forceinline__ float2 ld_two_g(const float *p) { return make_float2(__ldg(p), __ldg(p + 1)); }
+__device__ __forceinline__ float2 ld_two_g(const __half *p) { return make_float2(__half2float(__ldg(p)), __half2float(__ldg(p + 1))); }
+__device__ __forceinline__ float2 ld_pair_s(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ float2 ld_pair_s(const __half *p) { return __half22float2(*reinterpret_cast<const __half2 *>(p)); }
+__device__ __forceinline__ float2 ld_two_s(const float *p) { return make_float2(p[0], p[1]); }
+__device__ __forceinline__ float2 ld_two_s(const __half *p) { return make_float2(__half2float(p[0]), __half2float(p[1])); }
+__device__ __forceinline__ void st_pair(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+__device__ __forceinline__ void st_pair(__half *p, float2 v) { *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(v.x, v.y); }
+
 // D2Q9 velocity set in the order of Eq. (10), weights of Eq. (13).
 __host__ __device__ constexpr int cx_of(int a) { return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0); }
 __host__ __device__ constexpr int cy_of(int a) { return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0); }
@@ -634,8 +648,8 @@ __device__ __forceinline__ bool node_collide_to(const StepParams &p, const BodyS
 {
     using T = typename Prec<P>::T;
     constexpr bool DEV = Prec<P>::DEV;
-    if constexpr (P == VPLBM_F16_DEV && COLL == VPLBM_COLLISION_MRT) {
-        // FP16 storage: the lane form, shared with the node-pair kernel
+    if constexpr (Prec<P>::DEV && COLL == VPLBM_COLLISION_MRT) {
+        // FP32 / FP16 storage: the lane form, shared with the node-pair kernels
         float ax, ay;
         cr = mrt_dev_lanes<Lane1>(p, f, chi, dxl, dyl, bs, store, ax, ay);
         cax = ax;
