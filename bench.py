@@ -55,7 +55,7 @@ def dominant_kernel(prec: str, launch, kinds: dict) -> str:
     if top == "tma":
         return f"vp_mrt_step_tma<{PREC_ID[prec]}>"
     if launch[0] == "pair":
-        return "vp_mrt_step_pair<5, 0>"
+        return f"vp_mrt_step_pair<{PREC_ID[prec]}, 5, 0>"
     # single steps of a two-step choice run the 40-register kernel
     minb = {"scalar": 4, "scalar48": 5, "scalar40": 6, "fused2": 6, "tma": 6}[launch[0]]
     return f"vp_mrt_step<{PREC_ID[prec]}, {minb}, 0, 0>"

@@ -36,7 +36,8 @@ def test_dominant_kernel_follows_the_node_updates_of_the_region():
     single = {"one_step": 5, "two_step": 2, "lookahead": 1, "tma": 0}
     assert bench.dominant_kernel("f32", ("fused2", 256, 1), single) == "vp_mrt_step<1, 6, 0, 0>"
     assert bench.dominant_kernel("f64", ("scalar", 32, 4), {"one_step": 20}) == "vp_mrt_step<0, 4, 0, 0>"
-    assert bench.dominant_kernel("f16", ("pair", 32, 8), {"one_step": 20}) == "vp_mrt_step_pair<5, 0>"
+    assert bench.dominant_kernel("f16", ("pair", 32, 8), {"one_step": 20}) == "vp_mrt_step_pair<2, 5, 0>"
+    assert bench.dominant_kernel("f32", ("pair", 32, 8), {"one_step": 20}) == "vp_mrt_step_pair<1, 5, 0>"
     assert bench.dominant_kernel("f32", ("tma", 256, 1), {"tma": 20}) == "vp_mrt_step_tma<1>"
 
 
