@@ -572,7 +572,7 @@ def run_batched(args, torch, stream):
     b.init_from_problems()
     tuned = b.autotune(32)
     modes = {}
-    for mode in ("branches", "tiles"):
+    for mode in ("branches", "tiles", "persistent"):
         b.set_mode(mode)
         b.init_from_problems()
         b.step(64)
@@ -581,8 +581,9 @@ def run_batched(args, torch, stream):
         b.sync()
         gbs = 72 * nodes * k_cmp / t / 1e9
         modes[mode] = {"mlups": nodes * k_cmp / t / 1e6, "steps": k_cmp, "gbs_algorithmic": gbs,
-                       "frac_of_hbm": gbs / peak, "launch": list(b.launch()[:3]) if mode == "tiles" else
-                       list(b.members[0].launch())}
+                       "frac_of_hbm": gbs / peak,
+                       "launch": (list(b.launch()[:3]) if mode == "tiles" else
+                                  list(b.persistent()[:5]) if mode == "persistent" else list(b.members[0].launch()))}
     b.set_mode(tuned[0])
     b.init_from_problems()
     b.sync()

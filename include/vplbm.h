@@ -386,10 +386,8 @@ vplbm_status vplbm_adjoint(vplbm_ctx *ctx, const vplbm_adjoint_desc *desc, doubl
 /* ---- batched sweep ---------------------------------------------------------
  * Many independent simulations of uneven lattice sizes (a parameter sweep:
  * stiffness, reduced velocity, ... as in the vortex-induced-vibration study
- * of Sec. 3.3) advanced together: one kernel launch per time step covers the
- * tiles of every member (the scalar step's tile code), K steps at a time
- * as CUDA graphs, each member keeping its own body, force reduction, tail
- * and history.  Members are ordinary contexts (vplbm_batch_member): every
+ * of Sec. 3.3) advanced together, each member keeping its own body, force
+ * reduction, tail and history (three ways to launch them: vplbm_batch_mode).  Members are ordinary contexts (vplbm_batch_member): every
  * per-simulation call (init, fields, history, body, checkpoints) works on
  * them; vplbm_step on a single member would take it out of step with the
  * others, which vplbm_batch_step then rejects with VPLBM_EINVAL.
@@ -404,14 +402,25 @@ void vplbm_batch_destroy(vplbm_batch *batch);   /* destroys the members too */
 vplbm_status vplbm_batch_member(vplbm_batch *batch, int k, vplbm_ctx **member);
 /* nsteps time steps of every member (asynchronous on the batch's stream). */
 vplbm_status vplbm_batch_step(vplbm_batch *batch, long long nsteps);
-/* Wait; returns the first member's latched device error, if any. */
+/* Wait; returns VPLBM_ETIMEOUT if a barrier wait of the persistent kernel
+ * gave up (reported once), else the first member's latched device error,
+ * if any. */
 vplbm_status vplbm_batch_sync(vplbm_batch *batch);
 /* How a batch steps its members.  BRANCHES (default): each member's own step
  * kernel (its launch shape is set through vplbm_batch_member +
  * vplbm_set_launch), one CUDA-graph branch per member so the members run
  * concurrently.  TILES: one launch per time step over the concatenated
- * tiles of every member, shaped by vplbm_batch_set_launch. */
-typedef enum { VPLBM_BATCH_BRANCHES = 0, VPLBM_BATCH_TILES = 1 } vplbm_batch_mode;
+ * tiles of every member, shaped by vplbm_batch_set_launch.  PERSISTENT
+ * (FP32 or FP16 storage, MRT collision; VPLBM_EUNSUPPORTED otherwise): one
+ * cooperative launch runs up to 1024 time steps of every member (a CUDA
+ * graph of that launch from an even step), its blocks resident for the
+ * whole launch, taking work items (each member's body tiles, then node-pair
+ * tiles of two x-adjacent nodes per thread, one-node tiles for an odd nx)
+ * from a queue and meeting at a grid-wide barrier after every step; shaped
+ * by vplbm_batch_set_persistent.  In every mode a member's populations,
+ * forces and trajectory are those of its own step kernel at the same
+ * block shape. */
+typedef enum { VPLBM_BATCH_BRANCHES = 0, VPLBM_BATCH_TILES = 1, VPLBM_BATCH_PERSISTENT = 2 } vplbm_batch_mode;
 vplbm_status vplbm_batch_set_mode(vplbm_batch *batch, int mode);
 vplbm_status vplbm_batch_get_mode(vplbm_batch *batch, int *mode);
 /* Launch shape of the batched kernel (TILES mode): blocks of block_x x block_y threads
@@ -424,13 +433,36 @@ vplbm_status vplbm_batch_get_mode(vplbm_batch *batch, int *mode);
 vplbm_status vplbm_batch_set_launch(vplbm_batch *batch, int block_x, int block_y, int tiles_per_block);
 vplbm_status vplbm_batch_get_launch(vplbm_batch *batch, int *block_x, int *block_y, int *tiles_per_block,
                                    long long *launches);
+/* Shape of the persistent kernel: blocks of block_x x block_y = 256 threads
+ * (block_x a multiple of 32); node-pair tiles of 2 block_x x block_y nodes,
+ * body and one-node tiles of block_x x block_y; a block takes chunk (1..16)
+ * work items from the queue at a time; params_in_shared != 0 copies a
+ * member's parameters to shared memory when a block's member changes
+ * (otherwise they are read from device memory where they are used).
+ * EINVAL for a shape outside these limits or one that needs more reduction
+ * slots than a member allocated (the previous shape is kept);
+ * VPLBM_EUNSUPPORTED for FP64 storage or BGK collision. */
+vplbm_status vplbm_batch_set_persistent(vplbm_batch *batch, int block_x, int block_y, int chunk,
+                                       int params_in_shared);
+/* The persistent shape, the grid (blocks kept resident on the device) and
+ * the number of persistent launches made so far.  Any pointer may be NULL. */
+vplbm_status vplbm_batch_get_persistent(vplbm_batch *batch, int *block_x, int *block_y, int *chunk,
+                                       int *params_in_shared, int *grid, long long *kernel_launches);
+/* Test hook for the bounded barrier waits of the persistent kernel: when
+ * enabled, every grid-wide barrier waits for one arrival more than the grid
+ * makes and gives up after 20 ms; the launch's blocks then leave, and the
+ * next vplbm_batch_sync returns VPLBM_ETIMEOUT once (the members hold the
+ * state of an unfinished step: initialise or load them again).  Disable to
+ * resume. */
+vplbm_status vplbm_batch_inject_barrier_timeout(vplbm_batch *batch, int enable);
 /* Time the branch mode with six member launch choices (every member set to
- * one scalar or node-pair kernel and block shape) and six tile-mode launch shapes over
- * 2 x steps_per_trial steps each (rounded up to whole 32-step graphs) and
- * keep the fastest (members keep the winning launch choice; the tile-mode
- * launch shape is the fastest tile shape whichever mode won, so that
- * vplbm_batch_set_mode(VPLBM_BATCH_TILES) afterwards runs at it); the trial
- * steps advance the members (they are real steps). */
+ * one scalar or node-pair kernel and block shape), six tile-mode launch
+ * shapes and (FP32/FP16, MRT) six persistent variants over 2 x
+ * steps_per_trial steps each (rounded up to whole 32-step graphs) and keep
+ * the fastest (members keep the winning launch choice; the tile-mode and
+ * persistent shapes are the fastest of their mode whichever mode won, so
+ * that vplbm_batch_set_mode afterwards runs at them); the trial steps
+ * advance the members (they are real steps). */
 vplbm_status vplbm_batch_autotune(vplbm_batch *batch, int steps_per_trial);
 
 /* ---- allocation-free stepping --------------------------------------------

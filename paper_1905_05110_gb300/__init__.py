@@ -30,7 +30,8 @@ __all__ = [
     "vplbm_step_noalloc", "BodyState", "vplbm_inject_wait_timeout", "Batch",
     "vplbm_batch_create", "vplbm_batch_destroy", "vplbm_batch_member", "vplbm_batch_step",
     "vplbm_batch_sync", "vplbm_batch_set_launch", "vplbm_batch_get_launch", "vplbm_batch_autotune",
-    "vplbm_batch_set_mode", "vplbm_batch_get_mode",
+    "vplbm_batch_set_mode", "vplbm_batch_get_mode", "vplbm_batch_set_persistent",
+    "vplbm_batch_get_persistent", "vplbm_batch_inject_barrier_timeout",
     "EXPORTED_SYMBOLS", "RECORD_FIELDS",
 ]
 
@@ -151,6 +152,9 @@ _SIGS = {
     "vplbm_batch_autotune": (C.c_int, [C.c_void_p, C.c_int]),
     "vplbm_batch_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "vplbm_batch_get_mode": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "vplbm_batch_set_persistent": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "vplbm_batch_get_persistent": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 5 + [C.POINTER(C.c_longlong)]),
+    "vplbm_batch_inject_barrier_timeout": (C.c_int, [C.c_void_p, C.c_int]),
     "vplbm_adjoint": (C.c_int, [_CTX, C.c_void_p, _D, _D]),
     "vplbm_last_error": (C.c_char_p, []),
     "vplbm_version": (C.c_char_p, []),
@@ -374,7 +378,7 @@ MAX_BODIES = 4   # VPLBM_MAX_BODIES
 
 COLLISIONS = {"mrt": 0, "bgk": 1}
 SHAPES = {"disk": 0, "ellipse": 1, "rectangle": 2}
-BATCH_MODES = {"branches": 0, "tiles": 1}
+BATCH_MODES = {"branches": 0, "tiles": 1, "persistent": 2}
 BATCH_MODE_NAMES = {v: k for k, v in BATCH_MODES.items()}
 KERNELS = {"scalar": 0, "scalar48": 1, "scalar40": 2, "tma": 3, "fused2": 4, "pair": 5}
 KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
@@ -481,6 +485,24 @@ def vplbm_batch_get_mode(batch) -> int:
 
 def vplbm_batch_autotune(batch, steps_per_trial: int = 8):
     _check(load_library().vplbm_batch_autotune(batch, int(steps_per_trial)))
+
+
+def vplbm_batch_set_persistent(batch, block_x: int = 64, block_y: int = 4, chunk: int = 2,
+                               params_in_shared: bool = False):
+    _check(load_library().vplbm_batch_set_persistent(batch, int(block_x), int(block_y), int(chunk),
+                                                     int(bool(params_in_shared))))
+
+
+def vplbm_batch_get_persistent(batch):
+    """(block_x, block_y, chunk, params_in_shared, grid, persistent launches so far)."""
+    v = [C.c_int() for _ in range(5)]
+    n = C.c_longlong()
+    _check(load_library().vplbm_batch_get_persistent(batch, *[C.byref(x) for x in v], C.byref(n)))
+    return tuple(x.value for x in v) + (int(n.value),)
+
+
+def vplbm_batch_inject_barrier_timeout(batch, enable: bool):
+    _check(load_library().vplbm_batch_inject_barrier_timeout(batch, int(bool(enable))))
 
 
 def vplbm_adjoint(ctx, ny: int, nsteps: int, window_start: int, w_cd: float = 1.0, w_cl: float = 0.0,
@@ -716,14 +738,29 @@ class Batch:
         return vplbm_batch_get_launch(self.handle)
 
     def set_mode(self, mode):
-        """"branches" (each member's own kernel, concurrent graph branches) or "tiles"."""
+        """"branches" (each member's own kernel, concurrent graph branches), "tiles" (one
+        launch per step) or "persistent" (one launch for many steps)."""
         vplbm_batch_set_mode(self.handle, BATCH_MODES[mode] if isinstance(mode, str) else int(mode))
 
     @property
     def mode(self) -> str:
         return BATCH_MODE_NAMES[vplbm_batch_get_mode(self.handle)]
 
+    def set_persistent(self, block_x: int = 64, block_y: int = 4, chunk: int = 2, params_in_shared: bool = False):
+        vplbm_batch_set_persistent(self.handle, block_x, block_y, chunk, params_in_shared)
+
+    def persistent(self):
+        """(block_x, block_y, chunk, params_in_shared, grid, persistent launches so far)."""
+        return vplbm_batch_get_persistent(self.handle)
+
+    def inject_barrier_timeout(self, enable: bool = True):
+        vplbm_batch_inject_barrier_timeout(self.handle, enable)
+
     def autotune(self, steps_per_trial: int = 8):
-        """Fastest of the branch mode and the tile-mode shapes: (mode, block_x, block_y, tiles_per_block)."""
+        """Fastest of the branch mode, the tile-mode shapes and the persistent variants:
+        (mode, block_x, block_y, tiles_per_block) or, persistent,
+        (mode, block_x, block_y, chunk, params_in_shared)."""
         vplbm_batch_autotune(self.handle, steps_per_trial)
+        if self.mode == "persistent":
+            return (self.mode,) + tuple(self.persistent()[:4])
         return (self.mode,) + tuple(self.launch()[:3])

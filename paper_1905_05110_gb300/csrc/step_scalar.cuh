@@ -39,7 +39,7 @@ __device__ __forceinline__ void scalar_tile(const StepParams &p, int tile_x, int
         if (i == p.nx - 1 && p.bc[VPLBM_EAST] == VPLBM_BC_CONVECTIVE) record_outlet<P>(p, j, f);
     }
 
-    const int4 range = __ldg(reinterpret_cast<const int4 *>(&bs->ilo));   // ilo, ihi, jlo, jhi
+    const int4 range = VPLBM_LDG(reinterpret_cast<const int4 *>(&bs->ilo));   // ilo, ihi, jlo, jhi
     const bool part_block = tile_near_body(range, bi0, bj0, blockDim.x, blockDim.y, tile_x == 0 && tile_y == 0);
     bool chi = false;
     T cr = 0, cax = 0, cay = 0;   // kept for the solid-node sums (converted there)
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256, MINB) vp_mrt_step(const StepParams p)
     bool sums = false;
     if ((int)blockIdx.y < nbr) {
         if (b >= p.nbody) return;
-        const int4 range = __ldg(reinterpret_cast<const int4 *>(&p.bs_in->ilo));
+        const int4 range = VPLBM_LDG(reinterpret_cast<const int4 *>(&p.bs_in->ilo));
         int tx0 = 0, ty0 = 0, rw = 1, nrect = 1;   // no solid node: tile (0, 0) runs the tail
         if (range.x <= range.y) {
             tx0 = range.x / (int)blockDim.x;

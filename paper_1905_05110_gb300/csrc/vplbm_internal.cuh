@@ -263,6 +263,43 @@ struct BatchLaunch {
 cudaError_t launch_step_batch(int precision, const BatchLaunch &bl, int total_tiles, int bx, int by,
                               cudaStream_t stream);
 
+// Persistent sweep (sweep.cu): one launch runs nsteps time steps of every
+// member of a batch.  Its blocks take work items from a queue (an atomic
+// counter over the launch's steps, `chunk` items at a time) and meet at a
+// grid-wide barrier after each step; the launch is cooperative, so every
+// block is resident and the barrier can complete.
+struct SweepCtl {
+    unsigned grab;      // work items handed out so far (over the launch)
+    unsigned arrive;    // barrier arrivals so far (over the launch)
+    int abort;          // set by a block whose barrier wait gave up: all leave
+    int err;            // ERR_TIMEOUT: a barrier wait gave up (kept until read)
+    unsigned pad[60];
+};
+static_assert(sizeof(SweepCtl) == 256, "SweepCtl layout");
+// Kinds of work item: a body slot (the scalar tile with the solid-node sums
+// that the member's current node range maps slot z to; slot 0 also checks
+// the slot count w and advances a prescribed body), a pair tile (2 bx x by
+// nodes at tile (z, w)), a scalar tile (bx x by nodes at (z, w), no sums).
+enum : int { SWEEP_BODY = 0, SWEEP_PAIR = 1, SWEEP_SCALAR = 2 };
+struct SweepLaunch {
+    const StepParams *params;      // [2][n]: each member's parameters by step parity (device)
+    const int4 *items;             // [items_per_step]: (member or -1, kind, z, w) (device)
+    SweepCtl *ctl;                 // grab, arrive and abort zeroed before the launch (device)
+    int n;
+    unsigned items_per_step;       // a multiple of chunk
+    unsigned chunk;                // items a block takes at a time
+    long long step0;               // step of the launch's first step (its parity picks the parameters)
+    int nsteps;
+    unsigned long long timeout_ns; // a barrier wait gives up after this long
+    unsigned extra_arrivals;       // test hook: arrivals every barrier waits for in vain (0)
+};
+// 1 if the persistent kernel is built for this precision and collision.
+int sweep_supported(int precision, int collision);
+// Blocks of bx x by threads the kernel variant keeps resident on the device.
+cudaError_t sweep_max_grid(int precision, bool disk, bool psmem, int bx, int by, int *grid);
+cudaError_t launch_sweep(int precision, bool disk, bool psmem, const SweepLaunch &sl, int grid, int bx, int by,
+                         cudaStream_t stream);
+
 // Launchers (step_kernels.cu).  All are asynchronous on `stream`.
 cudaError_t launch_step(int precision, const StepParams &p, int bx, int by, cudaStream_t stream, int minb = 4);
 // The same for an elliptic body (step_ellipse.cu) and a rectangular one (step_rectangle.cu).

@@ -18,9 +18,22 @@ template <> struct Prec<VPLBM_F64> { using S = double; using T = double; static 
 template <> struct Prec<VPLBM_F32_DEV> { using S = float; using T = float; static constexpr bool DEV = true; };
 template <> struct Prec<VPLBM_F16_DEV> { using S = __half; using T = float; static constexpr bool DEV = true; };
 
-__device__ __forceinline__ double ldv(const double *p) { return __ldg(p); }
-__device__ __forceinline__ float ldv(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float ldv(const __half *p) { return __half2float(__ldg(p)); }
+// Loads of the populations and the pose written by the previous time step.
+// A kernel launched once per step reads them through the read-only path
+// (ld.global.nc: they do not change while it runs).  A kernel that runs
+// several steps in one launch reads data it wrote itself after a grid-wide
+// barrier, which the non-coherent path may serve stale: its translation unit
+// defines VPLBM_COHERENT_LOADS before including this header, and its loads
+// go to L2 (ld.global.cg).
+#ifdef VPLBM_COHERENT_LOADS
+#define VPLBM_LDG(ptr) __ldcg(ptr)
+#else
+#define VPLBM_LDG(ptr) __ldg(ptr)
+#endif
+
+__device__ __forceinline__ double ldv(const double *p) { return VPLBM_LDG(p); }
+__device__ __forceinline__ float ldv(const float *p) { return VPLBM_LDG(p); }
+__device__ __forceinline__ float ldv(const __half *p) { return __half2float(VPLBM_LDG(p)); }
 __device__ __forceinline__ void stv(double *p, double x) { *p = x; }
 __device__ __forceinline__ void stv(float *p, float x) { *p = x; }
 __device__ __forceinline__ void stv(__half *p, float x) { *p = __float2half_rn(x); }
@@ -28,10 +41,10 @@ __device__ __forceinline__ void stv(__half *p, float x) { *p = __float2half_rn(x
 // Pairs of x-adjacent populations (the node-pair paths): an aligned pair
 // from global memory or a shared-memory stage, two single values (a pair
 // that straddles the alignment), an aligned pair store.
-__device__ __forceinline__ float2 ld_pair_g(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
-__device__ __forceinline__ float2 ld_pair_g(const __half *p) { return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p))); }
-__device__ __forceinline__ float2 ld_two_g(const float *p) { return make_float2(__ldg(p), __ldg(p + 1)); }
-__device__ __forceinline__ float2 ld_two_g(const __half *p) { return make_float2(__half2float(__ldg(p)), __half2float(__ldg(p + 1))); }
+__device__ __forceinline__ float2 ld_pair_g(const float *p) { return VPLBM_LDG(reinterpret_cast<const float2 *>(p)); }
+__device__ __forceinline__ float2 ld_pair_g(const __half *p) { return __half22float2(VPLBM_LDG(reinterpret_cast<const __half2 *>(p))); }
+__device__ __forceinline__ float2 ld_two_g(const float *p) { return make_float2(VPLBM_LDG(p), VPLBM_LDG(p + 1)); }
+__device__ __forceinline__ float2 ld_two_g(const __half *p) { return make_float2(__half2float(VPLBM_LDG(p)), __half2float(VPLBM_LDG(p + 1))); }
 __device__ __forceinline__ float2 ld_pair_s(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 __device__ __forceinline__ float2 ld_pair_s(const __half *p) { return __half22float2(*reinterpret_cast<const __half2 *>(p)); }
 __device__ __forceinline__ float2 ld_two_s(const float *p) { return make_float2(p[0], p[1]); }
@@ -415,8 +428,8 @@ __device__ __forceinline__ void solid_terms_from(const BodyState *bs, const type
         dx = (double)i - bs->q[0];
         dy = (double)j - bs->q[1];
     } else {
-        const int2 xy = __ldg(reinterpret_cast<const int2 *>(&bs->xi));
-        const float2 fr = __ldg(reinterpret_cast<const float2 *>(&bs->xf));
+        const int2 xy = VPLBM_LDG(reinterpret_cast<const int2 *>(&bs->xi));
+        const float2 fr = VPLBM_LDG(reinterpret_cast<const float2 *>(&bs->xf));
         dx = (float)(i - xy.x) - fr.x;
         dy = (float)(j - xy.y) - fr.y;
     }
@@ -466,15 +479,15 @@ __device__ __forceinline__ bool body_chi(const DevBody &body, float r2f, const B
     constexpr bool DEV = Prec<P>::DEV;
     bool chi = false;
     if constexpr (DEV) {
-        const int2 xy = __ldg(reinterpret_cast<const int2 *>(&bs->xi));
-        const float2 fr = __ldg(reinterpret_cast<const float2 *>(&bs->xf));
+        const int2 xy = VPLBM_LDG(reinterpret_cast<const int2 *>(&bs->xi));
+        const float2 fr = VPLBM_LDG(reinterpret_cast<const float2 *>(&bs->xf));
         const float dxf = (float)(i - xy.x) - fr.x;
         const float dyf = (float)(j - xy.y) - fr.y;
         const int shape = SHAPE == SHAPE_ANY ? body.shape : SHAPE;
         if (shape == VPLBM_SHAPE_RECTANGLE) {
             // |u| <= a and |v| <= b in the body frame, in FP32, exact
             // FP64 re-test where either is within the band of its edge
-            const float2 cs = __ldg(reinterpret_cast<const float2 *>(&bs->cthf));
+            const float2 cs = VPLBM_LDG(reinterpret_cast<const float2 *>(&bs->cthf));
             const float uf = fabsf(dxf * cs.x + dyf * cs.y);
             const float vf = fabsf(dyf * cs.x - dxf * cs.y);
             const float band = body.bandr;
@@ -485,7 +498,7 @@ __device__ __forceinline__ bool body_chi(const DevBody &body, float r2f, const B
         } else if (shape == VPLBM_SHAPE_ELLIPSE) {
             // b^2 u^2 + a^2 v^2 <= a^2 b^2 in the body frame, in FP32,
             // exact FP64 re-test inside the band
-            const float2 cs = __ldg(reinterpret_cast<const float2 *>(&bs->cthf));
+            const float2 cs = VPLBM_LDG(reinterpret_cast<const float2 *>(&bs->cthf));
             const float uf = dxf * cs.x + dyf * cs.y;
             const float vf = dyf * cs.x - dxf * cs.y;
             const float lhs = body.b2f * (uf * uf) + body.a2f * (vf * vf);
@@ -500,7 +513,7 @@ __device__ __forceinline__ bool body_chi(const DevBody &body, float r2f, const B
         }
         dxl = dxf; dyl = dyf;
     } else {
-        const double xg = __ldg(&bs->q[0]), yg = __ldg(&bs->q[1]);
+        const double xg = VPLBM_LDG(&bs->q[0]), yg = VPLBM_LDG(&bs->q[1]);
         const int shape = SHAPE == SHAPE_ANY ? body.shape : SHAPE;
         chi = shape == VPLBM_SHAPE_ELLIPSE   ? chi_exact_ellipse(i, j, bs, body)
               : shape == VPLBM_SHAPE_RECTANGLE ? chi_exact_rect(i, j, bs, body)
@@ -580,7 +593,7 @@ __device__ __forceinline__ typename Ln::L mrt_dev_lanes(const StepParams &p, con
     ay_out = 0.f;
     if constexpr (Ln::SCALAR) {
         if (chi) {   // Eq. (22), eta-stable form: a = (u_s - v) / (eta + 1/2), u = v + a / 2
-            const float4 vv = __ldg(reinterpret_cast<const float4 *>(&bs->vxf));
+            const float4 vv = VPLBM_LDG(reinterpret_cast<const float4 *>(&bs->vxf));
             const float usx = __fmaf_rn(-vv.z, dyl, vv.x), usy = __fmaf_rn(vv.z, dxl, vv.y);
             const float ax = __fmul_rn(__fsub_rn(usx, ux), p.pen_kf), ay = __fmul_rn(__fsub_rn(usy, uy), p.pen_kf);
             Gx = __fmul_rn(rho, __fadd_rn(p.gxf, ax));
@@ -682,7 +695,7 @@ __device__ __forceinline__ bool node_collide_to(const StepParams &p, const BodyS
     if (chi) {
         T usx, usy;
         if constexpr (DEV) {
-            const float4 vv = __ldg(reinterpret_cast<const float4 *>(&bs->vxf));
+            const float4 vv = VPLBM_LDG(reinterpret_cast<const float4 *>(&bs->vxf));
             usx = vv.x - vv.z * dyl; usy = vv.y + vv.z * dxl;
         } else {
             usx = bs->v[0] - bs->v[2] * dyl; usy = bs->v[1] + bs->v[2] * dxl;
