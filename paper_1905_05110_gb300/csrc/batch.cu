@@ -200,10 +200,10 @@ vplbm_status build_items(vplbm_batch *b)
 }
 
 // Steps one persistent launch may run: the queue counter runs over all of
-// them and must stay below 2^32.
+// them (and two chunks per block beyond) and must stay below 2^32.
 long long persist_max_steps(const vplbm_batch *b)
 {
-    const unsigned long long room = 0xffffffffull - (unsigned long long)b->pgrid * b->pchunk;
+    const unsigned long long room = 0xffffffffull - 3ull * b->pgrid * b->pchunk;
     const long long m = (long long)(room / b->items_per_step) - 1;
     return m < PERSIST_STEPS ? m : PERSIST_STEPS;
 }
@@ -648,9 +648,9 @@ vplbm_status vplbm_batch_autotune(vplbm_batch *b, int steps_per_trial)
                               {VPLBM_BATCH_TILES, 256, 1, 8, 0}, {VPLBM_BATCH_TILES, 256, 1, 4, 0},
                               {VPLBM_BATCH_TILES, 256, 1, 16, 0}, {VPLBM_BATCH_TILES, 128, 2, 4, 0},
                               {VPLBM_BATCH_TILES, 128, 1, 8, 0}, {VPLBM_BATCH_TILES, 256, 1, 1, 0},
-                              {VPLBM_BATCH_PERSISTENT, 32, 8, 2, 0}, {VPLBM_BATCH_PERSISTENT, 32, 8, 2, 1},
-                              {VPLBM_BATCH_PERSISTENT, 32, 8, 4, 1}, {VPLBM_BATCH_PERSISTENT, 64, 4, 2, 1},
-                              {VPLBM_BATCH_PERSISTENT, 64, 4, 4, 1}, {VPLBM_BATCH_PERSISTENT, 128, 2, 2, 1}};
+                              {VPLBM_BATCH_PERSISTENT, 32, 8, 4, 1}, {VPLBM_BATCH_PERSISTENT, 32, 8, 4, 0},
+                              {VPLBM_BATCH_PERSISTENT, 32, 8, 2, 1}, {VPLBM_BATCH_PERSISTENT, 32, 8, 8, 1},
+                              {VPLBM_BATCH_PERSISTENT, 64, 4, 4, 1}, {VPLBM_BATCH_PERSISTENT, 128, 2, 4, 1}};
     for (const auto &cb : cands) {
         if (cb[0] == VPLBM_BATCH_BRANCHES) {
             bool ok = true;

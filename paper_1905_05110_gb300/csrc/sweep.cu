@@ -134,41 +134,63 @@ __device__ __forceinline__ void sweep_item(const StepParams &p, const int4 it, d
 // Blocks take the items of a step from a queue: one atomic counter that
 // runs over all steps of the launch hands out `chunk` consecutive items at
 // a time (a block that draws a chunk of the next step keeps it for after
-// the barrier).  Thread 0 draws the next chunk when the current one starts,
-// so the counter's latency is hidden behind the chunk's work; the list
-// starts with the body slots, so the members' tails run early in the step.
+// the barrier).  The queue is pipelined so that neither the counter nor the
+// item list is waited for: while a block runs chunk c, its thread 0 draws
+// the start of chunk c + 2 and the first `chunk` threads copy the items of
+// chunk c + 1 into shared memory (cp.async), both complete by the block
+// barrier that ends chunk c.  The list starts with the body slots, so the
+// members' tails run early in the step.
 //
 // PSMEM: the item's member parameters are copied to shared memory when
 // the member (or the step parity) changes; otherwise they are read from
 // global memory where they are used.
+constexpr int SWEEP_MAX_CHUNK = 16;
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <int P, int COLL, int SHAPE, bool PSMEM>
 __global__ void __launch_bounds__(256, SWEEP_MINB) vp_mrt_sweep(const SweepLaunch sl)
 {
     __shared__ double red[8][NPART];
     __shared__ float rows[NPART - 1][256];
     __shared__ int s_last, s_go, s_key;
-    __shared__ unsigned s_next[2];
+    __shared__ unsigned s_g[3];                               // chunk starts, chunk c in slot c % 3
+    __shared__ __align__(16) int4 s_items[2][SWEEP_MAX_CHUNK]; // items of chunk c in slot c % 2
     __shared__ __align__(16) StepParams s_p;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthreads = blockDim.x * blockDim.y;
     const unsigned V = sl.items_per_step, CH = sl.chunk;
     if (tid == 0) {
-        s_next[0] = atomicAdd(&sl.ctl->grab, CH);
+        s_g[0] = atomicAdd(&sl.ctl->grab, CH);
+        s_g[1] = atomicAdd(&sl.ctl->grab, CH);
         s_key = -1;
     }
     __syncthreads();
-    unsigned g = s_next[0];
-    int flip = 1;
+    if (tid < (int)CH) {
+        cp_async16(&s_items[0][tid], sl.items + s_g[0] % V + tid);
+        cp_async_wait_all();
+    }
+    __syncthreads();
+    int c3 = 0, c2 = 0;   // chunk c's slots in s_g and s_items
     for (int k = 0; k < sl.nsteps; ++k) {
         const int par = (int)((sl.step0 + k) & 1);
         const StepParams *pp = sl.params + (size_t)par * sl.n;
-        const unsigned v0 = (unsigned)k * V, v1 = v0 + V;
-        while (g < v1) {
-            // draw the next chunk now; its index is needed only after this one
-            unsigned nxt = 0;
-            if (tid == 0) nxt = atomicAdd(&sl.ctl->grab, CH);
+        const unsigned v1 = (unsigned)(k + 1) * V;
+        while (s_g[c3] < v1) {   // uniform: written before the last block barrier
+            const int n3 = c3 == 2 ? 0 : c3 + 1, nn3 = n3 == 2 ? 0 : n3 + 1;
+            // chunk c + 1's items into the other slot (its readers, chunk
+            // c - 1, are past the last barrier), chunk c + 2's start
+            if (tid < (int)CH) cp_async16(&s_items[c2 ^ 1][tid], sl.items + s_g[n3] % V + tid);
+            unsigned g2 = 0;
+            if (tid == 0) g2 = atomicAdd(&sl.ctl->grab, CH);
             for (unsigned c = 0; c < CH; ++c) {
-                const int4 it = __ldg(sl.items + (g - v0) + c);
+                const int4 it = s_items[c2][c];
                 if (it.x < 0) continue;   // padding (uniform over the block)
                 if constexpr (PSMEM) {
                     const int key = par * sl.n + it.x;
@@ -185,12 +207,12 @@ __global__ void __launch_bounds__(256, SWEEP_MINB) vp_mrt_sweep(const SweepLaunc
                     sweep_item<P, COLL, SHAPE>(pp[it.x], it, red, rows, &s_last);
                 }
             }
-            // double-buffered: s_next[flip] is written again only after the
-            // next chunk's barrier, when every thread has read it
-            if (tid == 0) s_next[flip] = nxt;
+            if (tid < (int)CH) cp_async_wait_all();
+            // slot nn3 last held chunk c - 1's start, read before the last barrier
+            if (tid == 0) s_g[nn3] = g2;
             __syncthreads();
-            g = s_next[flip];
-            flip ^= 1;
+            c3 = n3;
+            c2 ^= 1;
         }
         if (k + 1 < sl.nsteps && !sweep_barrier(sl, (unsigned)(k + 1) * gridDim.x + sl.extra_arrivals, &s_go)) return;
     }
