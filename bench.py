@@ -105,7 +105,8 @@ KERNEL_SOURCES = {
     "vp_mrt_step<": ("vplbm_internal.cuh", "vplbm_node.cuh", "step_scalar.cuh", "step_kernels.cu"),
     "vp_mrt_step2<": ("vplbm_internal.cuh", "vplbm_node.cuh", "step_fused2.cu"),
     "vp_mrt_step_tma<": ("vplbm_internal.cuh", "vplbm_node.cuh", "step_tma.cu"),
-    "vp_mrt_step_pair<": ("vplbm_internal.cuh", "vplbm_node.cuh", "step_scalar.cuh", "step_pair.cu"),
+    "vp_mrt_step_pair<": ("vplbm_internal.cuh", "vplbm_node.cuh", "step_scalar.cuh", "step_pair.cuh", "step_pair.cu"),
+    "vp_mrt_sweep<": ("vplbm_internal.cuh", "vplbm_node.cuh", "step_scalar.cuh", "step_pair.cuh", "sweep.cu"),
 }
 
 
