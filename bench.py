@@ -556,8 +556,8 @@ def run_sharded_sweep(args, torch, stream, rank, world, dev):
 
 def run_batched(args, torch, stream):
     """The 64-member spring-mounted sweep (uneven lattices, reduced velocity
-    in [3, 12], m/(rho pi R^2) = 10): both batch modes timed over the same
-    2 000 steps, the full 50 000-step run on the autotuned mode with the
+    in [3, 12], m/(rho pi R^2) = 10; --sweep-members N keeps its N smallest,
+    for profiling): the three batch modes timed over the same 2 000 steps, the full 50 000-step run on the autotuned mode with the
     response of every member (A*, omega*, k*_eff of Sec. 3.3 over the second
     half), the FP64 plain path (one member after another) over 2 000 steps,
     and the FP32 records of the smallest, a median and the largest member
@@ -565,6 +565,8 @@ def run_batched(args, torch, stream):
     import paper_1905_05110_gb300 as vp
     from paper_1905_05110_gb300.viv import viv_response
     probs = wl.viv_sweep()
+    if args.sweep_members:
+        probs = sorted(probs, key=lambda q: q["nx"] * q["ny"])[:args.sweep_members]
     steps = args.sweep_steps or probs[0]["steps"]
     nodes = sum(p["nx"] * p["ny"] for p in probs)
     peak, _ = measured_peak()
@@ -790,6 +792,8 @@ def main():
                     help="steps of the gradient leg (default: the workload's 20 000, checkpoints every 141)")
     ap.add_argument("--sweep-steps", type=int, default=0,
                     help="steps of the sweep leg's full run (default: the workload's 50 000)")
+    ap.add_argument("--sweep-members", type=int, default=0,
+                    help="the sweep leg on its N smallest members only (default: all 64; for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
