@@ -59,3 +59,14 @@ def test_profiled_traffic_needs_a_matching_source_hash(tmp_path, monkeypatch):
     (tmp_path / f"{stem}.md").write_text("dram_bytes_per_launch_full_size: 1.5e+08\n"
                                          "kernel_source_sha256_16: 0000000000000000\n")
     assert bench.profiled_traffic(k, "w") is None
+
+
+def test_reference_band_keeps_the_body_and_walls_the_cut_edges():
+    p = bench.workload("oscillating_2048x1024")
+    q = bench.row_band(p, 64)
+    assert q["nx"] == p["nx"] and q["ny"] == 64
+    assert q["bc"]["west"] == p["bc"]["west"] and q["bc"]["east"] == p["bc"]["east"]
+    assert q["bc"]["south"]["kind"] == "noslip" and q["bc"]["north"]["kind"] == "noslip"
+    assert q["body"] is not None and 0 <= q["body"]["y"] < 64
+    assert abs(q["body"]["y"] - 32) <= 1 and q["body"]["x"] == p["body"]["x"]
+    assert bench.row_band(p, p["ny"])["body"]["y"] == p["body"]["y"]
