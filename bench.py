@@ -435,7 +435,7 @@ def run_ours(args, rank, world, local_rank):
             s2 = vp.Simulation(p, precision=other, history_capacity=4096, stream=stream)
             s2.init_from_problem()
             if not args.no_autotune:
-                s2.autotune(8)
+                s2.autotune(20)
             s2.step(50)
             s2.sync()
             k = max(200, min(args.steps, 2000 if other == "f64" else args.steps))
