@@ -222,7 +222,10 @@ void vplbm_destroy(vplbm_ctx *ctx);
 
 /* State := equilibrium (Eq. 11) of the host fields rho, ux, uy ([ny][nx]);
  * a NULL field means rho0 (for rho) or 0 (for a velocity).  Resets the
- * step counter, the history and the body to its initial pose. */
+ * step counter, the history and the body to its initial pose.  A
+ * page-locked (pinned, device-mapped) field is read in place by the
+ * initialisation kernel over the CPU-GPU link; a pageable one is copied to
+ * device memory first. */
 vplbm_status vplbm_init_equilibrium(vplbm_ctx *ctx, const double *rho, const double *ux,
                                     const double *uy);
 
@@ -240,7 +243,10 @@ vplbm_status vplbm_sync(vplbm_ctx *ctx);
 vplbm_status vplbm_get_populations(vplbm_ctx *ctx, double *f);
 
 /* rho, u_x, u_y of the current step (Eqs. 19-22, with chi of the current
- * pose), host arrays [ny][nx]; any pointer may be NULL. */
+ * pose), host arrays [ny][nx]; any pointer may be NULL.  If every given
+ * array is page-locked (pinned, device-mapped) the fields kernel writes
+ * them in place over the CPU-GPU link; otherwise they are staged through
+ * device memory.  Returns when the arrays hold the fields. */
 vplbm_status vplbm_get_fields(vplbm_ctx *ctx, double *rho, double *ux, double *uy);
 
 /* Same into device arrays (asynchronous, on the context's stream). */

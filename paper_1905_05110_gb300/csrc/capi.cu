@@ -866,18 +866,36 @@ void vplbm_destroy(vplbm_ctx *c)
     delete c;
 }
 
+// Device address of a page-locked, device-mapped host buffer (the kernels
+// then read or write it in place over the CPU-GPU link); null for pageable
+// memory, which is staged through device memory instead.
+void *mapped_host(const void *host)
+{
+    if (!host) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();   // an unknown pointer: pageable
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 vplbm_status vplbm_init_equilibrium(vplbm_ctx *c, const double *rho, const double *ux, const double *uy)
 {
     if (!c) return fail(VPLBM_EINVAL, "context is NULL");
     const size_t n = (size_t)c->nx * c->ny;
     double *tmp = nullptr;
-    const int nf = (rho ? 1 : 0) + (ux ? 1 : 0) + (uy ? 1 : 0);
-    if (nf) CUDA_TRY(cudaMallocAsync((void **)&tmp, nf * n * sizeof(double), c->stream));
     double *d[3] = {nullptr, nullptr, nullptr};
     const double *h[3] = {rho, ux, uy};
+    int nf = 0;
+    for (int m = 0; m < 3; ++m) {
+        d[m] = static_cast<double *>(mapped_host(h[m]));
+        if (h[m] && !d[m]) ++nf;
+    }
+    if (nf) CUDA_TRY(cudaMallocAsync((void **)&tmp, nf * n * sizeof(double), c->stream));
     int k = 0;
     for (int m = 0; m < 3; ++m)
-        if (h[m]) {
+        if (h[m] && !d[m]) {
             d[m] = tmp + k++ * n;
             CUDA_TRY(cudaMemcpyAsync(d[m], h[m], n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         }
@@ -941,6 +959,20 @@ vplbm_status vplbm_get_fields(vplbm_ctx *c, double *rho, double *ux, double *uy)
 {
     if (!c) return fail(VPLBM_EINVAL, "context is NULL");
     const size_t n = (size_t)c->nx * c->ny;
+    {   // page-locked outputs: the fields kernel writes them in place
+        double *h[3] = {rho, ux, uy}, *m[3];
+        bool all = true;
+        for (int q = 0; q < 3; ++q) {
+            m[q] = static_cast<double *>(mapped_host(h[q]));
+            all = all && (!h[q] || m[q]);
+        }
+        if (all) {
+            vplbm_status st = vplbm_get_fields_dev(c, m[0], m[1], m[2]);
+            if (st != VPLBM_OK) return st;
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            return read_error(c);
+        }
+    }
     double *tmp = nullptr;
     CUDA_TRY(cudaMallocAsync((void **)&tmp, 3 * n * sizeof(double), c->stream));
     vplbm_status st = vplbm_get_fields_dev(c, tmp, tmp + n, tmp + 2 * n);
