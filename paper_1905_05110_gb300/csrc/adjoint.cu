@@ -35,6 +35,9 @@ namespace vplbm {
 namespace {
 
 constexpr int ADJ_BX = 32, ADJ_BY = 4;   // block of the reverse kernel (a tile of nodes)
+// an interior thread takes ADJ_ROWS nodes of its column, ADJ_BY rows apart
+// (at 1024 x 512 the interior then fits in one wave of resident blocks)
+constexpr int ADJ_ROWS = 4;
 constexpr int ADJ_BLOCK = ADJ_BX * ADJ_BY;
 // blocks of 128 threads per SM the reverse kernel's register budget is
 // sized for: 64 registers in FP32, 128 in FP64 (no spills)
@@ -302,7 +305,7 @@ __device__ __forceinline__ void adj_one_node(const StepParams &p, const AdjStep 
 }
 
 // Layout of the reverse kernel's grid (1-D): the interior nodes
-// [1, nx - 2] x [1, ny - 2] in tiles of ADJ_BX x ADJ_BY aligned on x = 0
+// [1, nx - 2] x [1, ny - 2] in tiles of ADJ_BX x (ADJ_BY * ADJ_ROWS) aligned on x = 0
 // (rows of a warp stay on 128-byte boundaries; the lanes on columns 0 and
 // nx - 1 idle), which take no boundary rule, so their warps never diverge
 // into one; the perimeter nodes, ADJ_BLOCK per block, come first (their
@@ -320,7 +323,7 @@ inline AdjLayout adj_layout(int nx, int ny)
     AdjLayout l;
     if (nx >= 3 && ny >= 3) {
         l.itx = (nx + ADJ_BX - 1) / ADJ_BX;
-        l.ity = (ny - 2 + ADJ_BY - 1) / ADJ_BY;
+        l.ity = (ny - 2 + ADJ_BY * ADJ_ROWS - 1) / (ADJ_BY * ADJ_ROWS);
         l.nper = 2 * nx + 2 * (ny - 2);
     } else {
         l.itx = l.ity = 0;
@@ -349,14 +352,17 @@ __device__ __forceinline__ void perimeter_node(int nx, int ny, int k, int &i, in
     }
 }
 
-// The reverse step of one lattice step n, one node per thread: (a) mu =
+// The reverse step of one lattice step n (ADJ_ROWS interior nodes or one
+// perimeter node per thread): (a) mu =
 // (dC/df)^T L_{n+1} + objective term at every node, pushed (b) into L_n;
 // parameter partials into the warps' accumulators acc[warp][4]
 // (float-float in FP32, so no FP64 work and no block barrier; one writer
 // per slot and launch, hence deterministic sums); dJ/du_in at the west
 // inlet.  zg_in: the zero-gradient contributions to L_{n+1} left by the
 // previous reverse step (added as L_{n+1} is loaded); zg_out: this
-// step's, [6][ny].
+// step's, [6][ny].  Launched with programmatic dependent launch: a block
+// reads its first pulled state before it waits for the previous reverse
+// step to complete, so those loads overlap that step's last blocks.
 template <int P>
 __global__ void __launch_bounds__(ADJ_BLOCK, adj_minb<P>()) adj_fused(const StepParams p, const AdjStep a,
                                                                  const LamPlanes<typename Prec<P>::T> lp,
@@ -371,22 +377,39 @@ __global__ void __launch_bounds__(ADJ_BLOCK, adj_minb<P>()) adj_fused(const Step
     const int lane = tid & 31, warp = tid >> 5;
     const int nperb = (lay.nper + ADJ_BLOCK - 1) / ADJ_BLOCK;
     T g[4] = {0, 0, 0, 0};
+    const S *fin = static_cast<const S *>(p.fin);
     if ((int)blockIdx.x >= nperb) {
         const int bi = (int)blockIdx.x - nperb;
         const int i = (bi % lay.itx) * ADJ_BX + threadIdx.x;
-        const int j = 1 + (bi / lay.itx) * ADJ_BY + threadIdx.y;
-        if (i >= 1 && i < p.nx - 1 && j < p.ny - 1) {
+        const int j0 = 1 + (bi / lay.itx) * ADJ_BY * ADJ_ROWS + threadIdx.y;
+        const bool col = i >= 1 && i < p.nx - 1;
+#pragma unroll 1
+        for (int r = 0; r < ADJ_ROWS; ++r) {
+            const int j = j0 + r * ADJ_BY;
+            const bool in = col && j < p.ny - 1;
             T f[NQ];
-            pull_all<P, true>(p, static_cast<const S *>(p.fin), i, j, f);
-            adj_one_node<P, false>(p, a, lp, zg_in, lam, zg_out, grad_uin, i, j, f, g);
+            if (in) pull_all<P, true>(p, fin, i, j, f);
+            if (r == 0) {   // the first row's pulled state S_n is read before waiting on the
+                            // previous reverse step: no reverse step writes the segment store
+                asm volatile("griddepcontrol.wait;" ::: "memory");
+                asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+            }
+            if (in) {
+                T gn[4] = {0, 0, 0, 0};   // the node's partials (adj_one_node assigns them)
+                adj_one_node<P, false>(p, a, lp, zg_in, lam, zg_out, grad_uin, i, j, f, gn);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) g[q] += gn[q];
+            }
         }
     } else {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         const int k = (int)blockIdx.x * ADJ_BLOCK + tid;
         if (k < lay.nper) {
             int i, j;
             perimeter_node(p.nx, p.ny, k, i, j);
             T f[NQ];
-            pull_all<P>(p, static_cast<const S *>(p.fin), i, j, f);
+            pull_all<P>(p, fin, i, j, f);
             adj_one_node<P, true>(p, a, lp, zg_in, lam, zg_out, grad_uin, i, j, f, g);
         }
     }
@@ -409,7 +432,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK, adj_minb<P>()) adj_fused(const Step
 
 template <int P>
 cudaError_t launch_adjoint_step(const StepParams &p, const AdjStep &a, const void *lam_next, const void *zg_in, void *lam,
-                                void *zg_out, void *acc, double *grad_uin, cudaStream_t stream)
+                                void *zg_out, void *acc, double *grad_uin, cudaStream_t stream, bool pdl)
 {
     using T = typename Prec<P>::T;
     LamPlanes<T> lp;
@@ -418,10 +441,17 @@ cudaError_t launch_adjoint_step(const StepParams &p, const AdjStep &a, const voi
         lp.dst[q] = static_cast<T *>(lam) + q * p.ps - cx_host(q) - (long long)cy_host(q) * p.nx;
     }
     const AdjLayout lay = adj_layout(p.nx, p.ny);
-    adj_fused<P><<<lay.blocks, dim3(ADJ_BX, ADJ_BY), 0, stream>>>(p, a, lp, static_cast<const T *>(zg_in),
-                                                                 static_cast<T *>(lam), static_cast<T *>(zg_out),
-                                                                 static_cast<typename SumT<P>::A *>(acc), grad_uin, lay);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(lay.blocks);
+    cfg.blockDim = dim3(ADJ_BX, ADJ_BY);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, adj_fused<P>, p, a, lp, static_cast<const T *>(zg_in), static_cast<T *>(lam),
+                              static_cast<T *>(zg_out), static_cast<typename SumT<P>::A *>(acc), grad_uin, lay);
 }
 
 vplbm_status aerr(vplbm_status st, const char *fmt, ...)
@@ -622,12 +652,16 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
                 a.vxf = bsn.vxf; a.vyf = bsn.vyf; a.omf = bsn.omf;
                 a.wxf = (float)a.wx; a.wyf = (float)a.wy;
             }
+            // programmatic dependent launch between the reverse steps of a
+            // segment; the first one follows the wait on the recomputation
+            // (a full dependency)
+            const bool pdl = n < s0 + len - 1;
             void *lam_next = work + lam_bytes * cur, *lam_new = work + lam_bytes * (cur ^ 1);
             void *zg_in = work + 2 * lam_bytes + zg_bytes * cur, *zg_out = work + 2 * lam_bytes + zg_bytes * (cur ^ 1);
             cudaError_t e =
                 c->precision == VPLBM_F64
-                    ? launch_adjoint_step<VPLBM_F64>(p, a, lam_next, zg_in, lam_new, zg_out, dacc, grad_uin, st)
-                    : launch_adjoint_step<VPLBM_F32_DEV>(p, a, lam_next, zg_in, lam_new, zg_out, dacc, grad_uin, st);
+                    ? launch_adjoint_step<VPLBM_F64>(p, a, lam_next, zg_in, lam_new, zg_out, dacc, grad_uin, st, pdl)
+                    : launch_adjoint_step<VPLBM_F32_DEV>(p, a, lam_next, zg_in, lam_new, zg_out, dacc, grad_uin, st, pdl);
             ATRY(e);
             cur ^= 1;
         }
