@@ -15,6 +15,7 @@ path has no exchange step): value = node updates of all ranks / max time.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import hashlib
 import json
 import math
@@ -715,20 +716,25 @@ def run_adjoint(args, torch, f64_compare):
         sim.init_from_problem()
         if prec == "f32":
             launch = sim.autotune(8)   # the forward and recomputed steps use the tuned step kernel
-        # FP32: one untimed call, then the median of three (the FP64 call,
-        # about 10 s, once)
+        # FP32: one untimed call, then the median of three, each from the
+        # initial state (a call leaves the context at the state after its
+        # forward run); the FP64 call, about 10 s, once
         reps = 3 if prec == "f32" else 1
         if prec == "f32":
             sim.adjoint(nsteps, w0, 1.0, 1.0, checkpoint_interval=ck)
         tt = []
-        for _ in range(reps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            grads[prec], js[prec] = sim.adjoint(nsteps, w0, 1.0, 1.0, checkpoint_interval=ck)
-            tt.append(time.perf_counter() - t0)
+        with (ClockSampler(torch.cuda.current_device()) if prec == "f32" else contextlib.nullcontext()) as cs:
+            for _ in range(reps):
+                if prec == "f32":
+                    sim.init_from_problem()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                grads[prec], js[prec] = sim.adjoint(nsteps, w0, 1.0, 1.0, checkpoint_interval=ck)
+                tt.append(time.perf_counter() - t0)
         secs[prec] = float(np.median(tt))
         if prec == "f32":
             secs_f32_all = [round(t, 4) for t in tt]
+            clocks_f32 = cs.summary()
             sim.init_from_problem()
             t_fwd32 = time_device(sim, nsteps, stream, torch)
         sim.close()
@@ -758,7 +764,8 @@ def run_adjoint(args, torch, f64_compare):
     gbs = 216 * nodes * nsteps / secs["f32"] / 1e9
     return {"lattice": f"{p['nx']}x{p['ny']}", "steps": nsteps, "window": [w0, nsteps], "checkpoint_interval": ck,
             "params": nparams, "launch": list(launch),
-            "seconds": secs["f32"], "seconds_f32_repeats": secs_f32_all, "seconds_f64_adjoint": secs["f64"], "J": js["f32"], "J_f64": js["f64"],
+            "seconds": secs["f32"], "seconds_f32_repeats": secs_f32_all, "clocks_f32": clocks_f32,
+            "seconds_f64_adjoint": secs["f64"], "J": js["f32"], "J_f64": js["f64"],
             "grad_norm": float(np.linalg.norm(grads["f32"])),
             "grad_rel_diff_f32_vs_f64": float(np.linalg.norm(grads["f32"] - grads["f64"]) /
                                               np.linalg.norm(grads["f64"])),

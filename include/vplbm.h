@@ -379,7 +379,11 @@ vplbm_status vplbm_load(vplbm_ctx *ctx, const char *path);
  * FP64 storage: FP64 adjoint; FP32 deviation storage: FP32 adjoint with
  * FP64 parameter sums.  history_capacity must be >= nsteps.
  * grad (host, ny + 3 values): dJ/du_in(j) for j < ny, then dJ/deta,
- * dJ/ds_nu, dJ/ds_e.  j_out (host, 2 values, may be NULL): J1, J2. */
+ * dJ/ds_nu, dJ/ds_e.  j_out (host, 2 values, may be NULL): J1, J2.
+ * Device memory: the first call allocates a workspace of about
+ * (ceil(nsteps / K) + 2 K + 3) population buffers (K the checkpoint
+ * interval) and the context keeps it for later calls (a call that needs
+ * more replaces it) until vplbm_destroy. */
 typedef struct {
     long long nsteps;
     long long window_start;

@@ -515,7 +515,6 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
             if (ev_rev[q]) cudaEventDestroy(ev_rev[q]);
         }
         if (sr) cudaStreamDestroy(sr);
-        cudaFree(ckpt); cudaFree(store); cudaFree(work); cudaFree(dacc); cudaFree(final_f); cudaFree(seg_bs);
     };
 #define ATRY(expr)                                                                     \
     do {                                                                               \
@@ -525,18 +524,40 @@ extern "C" vplbm_status vplbm_adjoint(vplbm_ctx *c, const vplbm_adjoint_desc *d,
             return aerr(VPLBM_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));  \
         }                                                                              \
     } while (0)
-    ATRY(cudaMalloc(&ckpt, pop * nck));
-    ATRY(cudaMalloc(&store, pop * K * 2));
-    ATRY(cudaMalloc(&seg_bs, (size_t)nck * sizeof(BodyState)));
+    // the device workspace, kept in the context between calls: checkpoints
+    // [nck], two segment stores [2][K], segment-start body states [nck],
+    // work, accumulators and inlet gradient, the final state
+    const size_t zg_bytes = (size_t)6 * c->ny * es;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t o_store = al(pop * nck), o_segbs = o_store + al(pop * K * 2);
+    const size_t o_work = o_segbs + al((size_t)nck * sizeof(BodyState));
+    const size_t o_dacc = o_work + al(lam_bytes * 2 + 2 * zg_bytes);
+    const size_t o_final = o_dacc + al(acc_bytes + (size_t)c->ny * sizeof(double));
+    const size_t ws_bytes = o_final + al(pop);
+    if (c->adj_ws_bytes < ws_bytes) {
+        if (c->adj_ws) {
+            cudaStreamSynchronize(st);
+            cudaFree(c->adj_ws);
+            c->adj_ws = nullptr;
+            c->adj_ws_bytes = 0;
+        }
+        ATRY(cudaMalloc(&c->adj_ws, ws_bytes));
+        c->adj_ws_bytes = ws_bytes;
+    }
+    {
+        char *ws = static_cast<char *>(c->adj_ws);
+        ckpt = ws;
+        store = ws + o_store;
+        seg_bs = reinterpret_cast<BodyState *>(ws + o_segbs);
+        work = ws + o_work;
+        dacc = reinterpret_cast<double *>(ws + o_dacc);
+        final_f = ws + o_final;
+    }
     ATRY(cudaStreamCreateWithFlags(&sr, cudaStreamNonBlocking));
     for (int q = 0; q < 2; ++q) {
         ATRY(cudaEventCreateWithFlags(&ev_rec[q], cudaEventDisableTiming));
         ATRY(cudaEventCreateWithFlags(&ev_rev[q], cudaEventDisableTiming));
     }
-    const size_t zg_bytes = (size_t)6 * c->ny * es;
-    ATRY(cudaMalloc(&work, lam_bytes * 2 + 2 * zg_bytes));
-    ATRY(cudaMalloc(&dacc, acc_bytes + (size_t)c->ny * sizeof(double)));
-    ATRY(cudaMalloc(&final_f, pop));
     double *grad_uin = reinterpret_cast<double *>(reinterpret_cast<char *>(dacc) + acc_bytes);
     ATRY(cudaMemsetAsync(work, 0, lam_bytes * 2 + 2 * zg_bytes, st));
     ATRY(cudaMemsetAsync(dacc, 0, acc_bytes + (size_t)c->ny * sizeof(double), st));

@@ -863,6 +863,7 @@ void vplbm_destroy(vplbm_ctx *c)
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->capture) cudaStreamDestroy(c->capture);
     if (c->owned) cudaFree(c->owned);
+    if (c->adj_ws) cudaFree(c->adj_ws);
     delete c;
 }
 

@@ -44,6 +44,11 @@ struct vplbm_ctx {
     bool tma_ok = false;
     CUtensorMap tmap[2];
     int tma_grid = 0;
+    // device workspace of vplbm_adjoint (checkpoints, segment stores,
+    // adjoint fields, accumulators), kept between calls; grown when a call
+    // needs more, freed by vplbm_destroy
+    void *adj_ws = nullptr;
+    size_t adj_ws_bytes = 0;
 };
 
 namespace vplbm {

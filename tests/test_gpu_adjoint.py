@@ -93,6 +93,32 @@ def test_fp32_adjoint_multi_tile_close_to_oracle(nx, weights):
     assert np.array_equal(gg, gg2)
 
 
+def test_adjoint_workspace_kept_between_calls():
+    """The context keeps the adjoint's device workspace: a repeated call, a
+    call that needs a larger workspace (more checkpoints and a longer
+    segment) and a smaller call after it give, bit for bit, what a fresh
+    context gives."""
+    import paper_1905_05110_gb300 as vp
+    p = wl.adjoint_channel(nx=72, ny=40, radius=6.0)
+
+    def run(sim, n, k):
+        sim.init_from_problem()
+        return sim.adjoint(n, n // 2, 1.0, 1.0, checkpoint_interval=k)
+
+    g = vp.Simulation(p, precision="f32", history_capacity=128)
+    a1, ja1 = run(g, 30, 7)
+    a2, ja2 = run(g, 30, 7)
+    assert np.array_equal(a1, a2) and np.array_equal(ja1, ja2)
+    b1, jb1 = run(g, 60, 5)   # 12 checkpoints and 2 x 5 store slots: the workspace grows
+    c1, _ = run(g, 30, 7)     # fits the grown workspace
+    assert np.array_equal(c1, a1)
+    fresh = vp.Simulation(p, precision="f32", history_capacity=128)
+    b2, jb2 = run(fresh, 60, 5)
+    assert np.array_equal(b1, b2) and np.array_equal(jb1, jb2)
+    g.close()
+    fresh.close()
+
+
 def test_adjoint_rejects_free_bodies():
     import paper_1905_05110_gb300 as vp
     p = wl.sedimenting_disk(nx=64, ny=128, diameter=8)
