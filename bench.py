@@ -455,10 +455,12 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_compare and world > 1 and "batched" in legs:
         compare["batched_sharded"] = run_sharded_sweep(args, torch, stream, rank, world, dev)
     if not args.no_compare and rank == 0:
-        if "batched" in legs:
-            compare["batched"] = run_batched(args, torch, stream)
+        # the gradient before the sweep: the sweep's 50 000 steps keep the
+        # GPU at high power for about half a minute
         if "adjoint" in legs:
             compare["adjoint"] = run_adjoint(args, torch, compare.get("f64"))
+        if "batched" in legs:
+            compare["batched"] = run_batched(args, torch, stream)
         if "sedimenting" in legs:
             compare["sedimenting_disk"] = run_other_workload("sedimenting_1024x4096", 200_000, torch, stream)
         if "paper" in legs:

@@ -664,7 +664,11 @@ class Simulation:
 
     def adjoint(self, nsteps: int, window_start: int, w_cd: float = 1.0, w_cl: float = 0.0,
                 checkpoint_interval: int = 0):
-        """Gradient of w_cd mean C_D + w_cl RMS C_L over [window_start, nsteps)."""
+        """Gradient of w_cd mean C_D + w_cl RMS C_L over [window_start, nsteps)
+        of a run of nsteps steps from the current state, with respect to the
+        west inlet profile (ny values), eta, s_nu and s_e; returns (grad, (J1, J2)).
+        The context ends at the state after the forward run, and keeps the
+        adjoint's device workspace for later calls until close()."""
         return vplbm_adjoint(self.ctx, self.ny, nsteps, window_start, w_cd, w_cl, checkpoint_interval)
 
     def save(self, path):
