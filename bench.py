@@ -38,7 +38,7 @@ METRIC = "D2Q9 VP-MRT MLUPS & % HBM roofline; FP32/batched/adjoint vs FP64 plain
 UNIT = "MLUPS"
 BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36}   # 9 loads + 9 stores of one population
 PREC_ID = {"f64": 0, "f32": 1, "f16": 2}
-LEGS = ("f64", "f16", "batched", "adjoint", "sedimenting", "paper", "several")   # comparison legs after the headline
+LEGS = ("f64", "f16", "adjoint", "batched", "sedimenting", "paper", "several")   # comparison legs after the headline
 FALLBACK_HBM_GBS = 6800.0
 REPEATS = 5   # timed regions of K steps; the line reports the median
 PROFILE_DIR = os.path.join(ROOT, "profiles")
