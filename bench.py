@@ -111,16 +111,21 @@ KERNEL_SOURCES = {
 }
 
 
+_C_COMMENT = re.compile(rb"//[^\n]*|/\*.*?\*/", re.S)
+_SPACE = re.compile(rb"\s+")
+
+
 def kernel_source_hash(kernel: str = "vp_mrt_step<") -> str:
-    """Hash of the sources of one step kernel (any change to them invalidates
-    its counters)."""
+    """Hash of the code of one step kernel's sources, comments left out and
+    white space collapsed: a change to the code invalidates the kernel's
+    counters, a change to a comment or to the layout does not."""
     files = next(v for k, v in KERNEL_SOURCES.items() if kernel.startswith(k))
     h = hashlib.sha256()
     paths = [os.path.join(ROOT, "include", "vplbm.h")] + [os.path.join(CSRC, f) for f in files]
     for path in paths:
         with open(path, "rb") as fh:
             h.update(os.path.basename(path).encode())
-            h.update(fh.read())
+            h.update(_SPACE.sub(b" ", _C_COMMENT.sub(b" ", fh.read())).strip())
     return h.hexdigest()[:16]
 
 

@@ -52,7 +52,7 @@ typedef enum {
     VPLBM_ECUDA = 3,         /* a CUDA runtime call failed */
     VPLBM_ENONFINITE = 4,    /* a density became non-positive or non-finite */
     VPLBM_ETIMEOUT = 5,      /* a bounded device wait gave up */
-    VPLBM_EUNSUPPORTED = 6,  /* valid request this build does not provide */
+    VPLBM_EUNSUPPORTED = 6,  /* valid request the library does not support */
     VPLBM_ERANGE = 7,        /* history record no longer (or not yet) stored */
     VPLBM_EIO = 8            /* file read or write failed */
 } vplbm_status;

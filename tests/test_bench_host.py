@@ -1,6 +1,8 @@
 """Host logic of bench.py: the strips the CPU baseline cuts a workload
 into, the kernel a timed region is attributed to, and the config both arms
 of the comparison print."""
+import os
+
 import bench
 import workloads as wl
 
@@ -59,6 +61,26 @@ def test_profiled_traffic_needs_a_matching_source_hash(tmp_path, monkeypatch):
     (tmp_path / f"{stem}.md").write_text("dram_bytes_per_launch_full_size: 1.5e+08\n"
                                          "kernel_source_sha256_16: 0000000000000000\n")
     assert bench.profiled_traffic(k, "w") is None
+
+
+def test_source_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    import shutil
+    k = "vp_mrt_step2<"
+    (tmp_path / "include").mkdir()
+    csrc = tmp_path / "csrc"
+    csrc.mkdir()
+    shutil.copy(os.path.join(bench.ROOT, "include", "vplbm.h"), tmp_path / "include" / "vplbm.h")
+    for f in bench.KERNEL_SOURCES[k]:
+        shutil.copy(os.path.join(bench.CSRC, f), csrc / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "CSRC", str(csrc))
+    h0 = bench.kernel_source_hash(k)
+    src = csrc / "step_fused2.cu"
+    text = src.read_text()
+    src.write_text(text + "\n// a comment\n/* and a block\n   comment */\n")
+    assert bench.kernel_source_hash(k) == h0
+    src.write_text(text + "\nstatic int extra_symbol = 1;\n")
+    assert bench.kernel_source_hash(k) != h0
 
 
 def test_reference_band_keeps_the_body_and_walls_the_cut_edges():
