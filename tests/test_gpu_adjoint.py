@@ -93,6 +93,23 @@ def test_fp32_adjoint_multi_tile_close_to_oracle(nx, weights):
     assert np.array_equal(gg, gg2)
 
 
+@pytest.mark.parametrize("ckpt", [0, 13])
+def test_fp64_adjoint_long_run_matches_oracle(ckpt):
+    """A 64 x 32 channel over 200 steps (several checkpoint segments, the
+    oscillating disk crossing nodes many times) against the FP64 oracle
+    adjoint."""
+    p = wl.adjoint_channel(nx=64, ny=32, radius=5.0, steps=200)
+    N, w0 = 200, 100
+    g, o = _init_both(p, "f64", hist=N + 8)
+    gg, gj = g.adjoint(N, w0, 1.0, 1.0, checkpoint_interval=ckpt)
+    og, oj = o.adjoint(N, w0, 1.0, 1.0)
+    assert np.allclose(gj, oj, rtol=1e-11)
+    scale_u = np.max(np.abs(og[:-3]))
+    assert np.max(np.abs(gg[:-3] - og[:-3])) < 1e-9 * scale_u
+    for k in (-3, -2, -1):
+        assert abs(gg[k] - og[k]) < 1e-9 * abs(og[k]), k
+
+
 def test_adjoint_workspace_kept_between_calls():
     """The context keeps the adjoint's device workspace: a repeated call, a
     call that needs a larger workspace (more checkpoints and a longer
