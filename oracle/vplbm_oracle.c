@@ -830,7 +830,7 @@ static void collide_adjoint(const double f[Q], const double s[Q], int chi, doubl
     for (int r = 0; r < Q; ++r) {
         lam_m[r] = (1.0 - s[r]) * lam_ms[r];
         lam_meq[r] = s[r] * lam_ms[r];
-        lam_MF[r] = (1.0 - 0.5 * s[r]) * lam_ms[r];
+        lam_MF[r] = (PLANT(10) ? 1.0 - s[r] : 1.0 - 0.5 * s[r]) * lam_ms[r];
         d_s[r] += lam_ms[r] * (-(m[r] - meq[r]) - 0.5 * MF[r]);
     }
     for (int a = 0; a < Q; ++a) { lam_F[a] = 0; for (int r = 0; r < Q; ++r) lam_F[a] += M[r][a] * lam_MF[r]; }
@@ -954,9 +954,9 @@ int orc_adjoint(orc_sim *s, const orc_adjoint_desc *d, double *grad, double out_
                     const double g = mu[((size_t)a * ny + j) * nx + i];
                     nlam[((size_t)b * ny + sj) * nx + si] += g;
                     if (wall == ORC_WEST && s->prof_ux[ORC_WEST])
-                        grad[j] += g * 6.0 * W[a] * s->lat.rho0 * C[a][0];
+                        grad[j] += (PLANT(11) ? -g : g) * 6.0 * W[a] * s->lat.rho0 * C[a][0];
                 }
-                if (owner_at(s, i, j) >= 0)
+                if (!PLANT(9) && owner_at(s, i, j) >= 0)
                     for (int a = 0; a < Q; ++a) nlam[((size_t)a * ny + j) * nx + i] -= wx * C[a][0] + wy * C[a][1];
             }
         double *t = lam; lam = nlam; nlam = t;

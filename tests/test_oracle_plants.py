@@ -19,6 +19,9 @@ PLANTS = {
     6: "the sign of the momentum-exchange torque (Eq. 27)",
     7: "the sign of the moving-wall term of the bounce-back",
     8: "the outlet's source row j instead of j - c_ay (zero-gradient and convective rules)",
+    9: "the adjoint: a solid node's own momentum-exchange term (Eqs. 25-27) dropped from L_n",
+    10: "the adjoint: the forcing factor (1 - s_r/2) of Eq. 17 taken as (1 - s_r)",
+    11: "the adjoint: the sign of the inlet-profile gradient",
 }
 
 
