@@ -227,12 +227,12 @@ static int chi_body(const orc_sim *s, int k, int i, int j)
         double a2 = b->radius * b->radius, b2 = b->radius_b * b->radius_b;
         double u = dx * c + dy * sn;
         double v = dy * c - dx * sn;
-        return b2 * (u * u) + a2 * (v * v) <= a2 * b2;
+        return PLANT(14) ? a2 * (u * u) + b2 * (v * v) <= a2 * b2 : b2 * (u * u) + a2 * (v * v) <= a2 * b2;
     }
     if (b->shape == ORC_RECT) {
         double c = cos(s->q[k][2]), sn = sin(s->q[k][2]);
-        double u = dx * c + dy * sn;
-        double v = dy * c - dx * sn;
+        double u = PLANT(15) ? dx * c - dy * sn : dx * c + dy * sn;
+        double v = PLANT(15) ? dy * c + dx * sn : dy * c - dx * sn;
         return fabs(u) <= b->radius && fabs(v) <= b->radius_b;
     }
     double d2 = dx * dx + dy * dy;
@@ -344,7 +344,7 @@ static void collide_bgk(const double f[Q], double omega, double rho,
     equilibrium(rho, ux, uy, feq);
     guo_forcing(ux, uy, Gx, Gy, F);
     for (int a = 0; a < Q; ++a)
-        ft[a] = f[a] - omega * (f[a] - feq[a]) + (1.0 - 0.5 * omega) * F[a];
+        ft[a] = f[a] - omega * (f[a] - feq[a]) + (PLANT(12) ? 1.0 : 1.0 - 0.5 * omega) * F[a];
 }
 
 /* ---- streaming with boundary rules (Eq. 18) ------------------------- */
@@ -368,7 +368,7 @@ static double pulled(const orc_sim *s, int a, int i, int j)
              * the node's own mirrored population is taken */
             int mi = i - C[a][0];
             if (mi < 0 || mi >= nx) mi = s->lat.bc_kind[ORC_WEST] == ORC_PERIODIC ? (mi + nx) % nx : i;
-            return FT(MIRY[a], mi, j);
+            return FT(PLANT(13) ? OPP[a] : MIRY[a], mi, j);
         } else {
             /* half-way bounce-back at y = -1/2 or y = ny - 1/2 */
             double val = FT(OPP[a], i, j);

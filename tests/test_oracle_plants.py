@@ -22,6 +22,10 @@ PLANTS = {
     9: "the adjoint: a solid node's own momentum-exchange term (Eqs. 25-27) dropped from L_n",
     10: "the adjoint: the forcing factor (1 - s_r/2) of Eq. 17 taken as (1 - s_r)",
     11: "the adjoint: the sign of the inlet-profile gradient",
+    12: "the BGK forcing prefactor (1 - 1/(2 tau)) of Eq. 12 dropped",
+    13: "a symmetry wall that bounces populations back instead of mirroring them",
+    14: "the ellipse's semi-axes swapped in its predicate",
+    15: "the rectangle's body frame turned by -theta instead of theta",
 }
 
 
