@@ -619,7 +619,7 @@ static void one_step(orc_sim *s)
             if (ns.chi) {
                 const int k = ns.owner;
                 /* reaction of the penalization force on the body */
-                double px = -ns.rho * ns.ax, py = -ns.rho * ns.ay;
+                double px = (PLANT(16) ? 1.0 : -1.0) * ns.rho * ns.ax, py = (PLANT(16) ? 1.0 : -1.0) * ns.rho * ns.ay;
                 fpen[k][0] += px;
                 fpen[k][1] += py;
                 fpen[k][2] += ns.dx * py - ns.dy * px;
@@ -630,7 +630,7 @@ static void one_step(orc_sim *s)
                     ox += C[a][0] * own;
                     oy += C[a][1] * own;
                 }
-                double ex = ns.jx - ox, ey = ns.jy - oy;
+                double ex = PLANT(17) ? ns.jx : ns.jx - ox, ey = PLANT(17) ? ns.jy : ns.jy - oy;
                 fh[k][0] += ex;
                 fh[k][1] += ey;
                 fh[k][2] += PLANT(6) ? ns.dy * ex - ns.dx * ey : ns.dx * ey - ns.dy * ex;   /* Eq. (27) */

@@ -26,6 +26,8 @@ PLANTS = {
     13: "a symmetry wall that bounces populations back instead of mirroring them",
     14: "the ellipse's semi-axes swapped in its predicate",
     15: "the rectangle's body frame turned by -theta instead of theta",
+    16: "the sign of the penalization reaction on the body",
+    17: "the momentum exchange without the node's own streamed-in momentum (Eq. 25)",
 }
 
 
