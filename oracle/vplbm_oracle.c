@@ -392,6 +392,7 @@ static double pulled(const orc_sim *s, int a, int i, int j)
              * and its inner neighbour (whose pulled value is the
              * zero-gradient one): f(N, n+1) = (f(N, n) + U f(N-1, n+1)) / (1 + U) */
             const double U = s->lat.bc_u[side][0];
+            if (PLANT(18)) return (U * s->conv_prev[(size_t)a * ny + j] + FT(a, i, sj)) / (1.0 + U);
             return (s->conv_prev[(size_t)a * ny + j] + U * FT(a, i, PLANT(8) ? j : sj)) / (1.0 + U);
         } else {
             double val = FT(OPP[a], i, j);
@@ -459,7 +460,7 @@ static void body_advance(const orc_body *b, long long step, double q_center,
         double t1 = (double)(step + 1);
         double ph = 2.0 * pi * b->freq * t1 + b->phase;
         q[b->axis] = q_center + b->amp * sin(ph);
-        v[b->axis] = 2.0 * pi * b->freq * b->amp * cos(ph);
+        v[b->axis] = 2.0 * pi * b->freq * b->amp * (PLANT(19) ? sin(ph) : cos(ph));
         return;
     }
     /* classic fourth-order Runge-Kutta on (q, v) for the free DOFs */

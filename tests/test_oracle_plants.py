@@ -28,6 +28,8 @@ PLANTS = {
     15: "the rectangle's body frame turned by -theta instead of theta",
     16: "the sign of the penalization reaction on the body",
     17: "the momentum exchange without the node's own streamed-in momentum (Eq. 25)",
+    18: "the convective outlet's two weights swapped (f_prev and the upwind value)",
+    19: "the imposed motion's velocity taken as the sine instead of the cosine",
 }
 
 
