@@ -231,33 +231,41 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+def cut_rows(p: dict, lo: int, hi: int) -> dict:
+    """Rows [lo, hi) of the workload as a lattice of their own: no-slip walls
+    at the cut edges, the west and east walls' per-row velocity profiles cut
+    to the same rows, and the bodies whose centre lies in the rows kept at
+    the same place relative to them (the others left out)."""
+    bc = dict(p["bc"], south={"kind": "noslip", "u": (0.0, 0.0)}, north={"kind": "noslip", "u": (0.0, 0.0)})
+    for side in ("west", "east"):
+        d = dict(bc[side])
+        for key in ("ux_profile", "uy_profile"):
+            if d.get(key) is not None:
+                d[key] = np.asarray(d[key], dtype=np.float64)[lo:hi].copy()
+        bc[side] = d
+    q = dict(p, ny=hi - lo, bc=bc)
+    b = p.get("body")
+    q["body"] = dict(b, y=b["y"] - lo) if b is not None and lo <= b["y"] < hi else None
+    if p.get("bodies"):
+        q["bodies"] = [dict(c, y=c["y"] - lo) for c in p["bodies"] if lo <= c["y"] < hi]
+    return q
+
+
 def strip_problems(p: dict, n: int) -> list:
     """The workload cut into n disjoint full-width strips of rows, each an
-    independent lattice (no-slip walls at its cut edges); the body stays in
-    the strip that holds its centre, at the same place relative to it."""
+    independent lattice (`cut_rows`)."""
     ny = p["ny"]
     bounds = [round(k * ny / n) for k in range(n + 1)]
-    out = []
-    for k in range(n):
-        lo, hi = bounds[k], bounds[k + 1]
-        q = dict(p, ny=hi - lo, bc=dict(p["bc"], south={"kind": "noslip", "u": (0.0, 0.0)},
-                                        north={"kind": "noslip", "u": (0.0, 0.0)}))
-        b = p.get("body")
-        q["body"] = dict(b, y=b["y"] - lo) if b is not None and lo <= b["y"] < hi else None
-        out.append(q)
-    return out
+    return [cut_rows(p, bounds[k], bounds[k + 1]) for k in range(n)]
 
 
 def row_band(p: dict, rows: int) -> dict:
     """`rows` full-width rows of the workload centred on its body (the
-    middle rows without one), no-slip walls at the cut edges."""
+    middle rows without one), as a lattice of their own (`cut_rows`)."""
     b = p.get("body")
     yc = b["y"] if b is not None else p["ny"] / 2
     lo = int(min(max(0, round(yc - rows / 2)), p["ny"] - rows))
-    q = dict(p, ny=rows, bc=dict(p["bc"], south={"kind": "noslip", "u": (0.0, 0.0)},
-                                  north={"kind": "noslip", "u": (0.0, 0.0)}))
-    q["body"] = dict(b, y=b["y"] - lo) if b is not None and lo <= b["y"] < lo + rows else None
-    return q
+    return cut_rows(p, lo, lo + rows)
 
 
 def _oracle_strip(args):

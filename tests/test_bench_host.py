@@ -3,6 +3,8 @@ into, the kernel a timed region is attributed to, and the config both arms
 of the comparison print."""
 import os
 
+import numpy as np
+
 import bench
 import workloads as wl
 
@@ -27,6 +29,47 @@ def test_strips_cover_the_lattice_once_and_keep_the_body_once():
         for q in strips:   # the cut edges are walls; west and east as the workload
             assert q["bc"]["south"]["kind"] == q["bc"]["north"]["kind"] == "noslip"
             assert q["bc"]["west"] == p["bc"]["west"] and q["bc"]["east"] == p["bc"]["east"]
+
+
+def test_strips_cut_wall_profiles_and_keep_every_body_once():
+    # a per-row inlet profile is cut with the rows; several bodies each stay
+    # in the one strip that holds its centre
+    p = wl.channel_fixed_disk()
+    prof = p["bc"]["west"]["ux_profile"]
+    for n in (1, 5, 16):
+        strips = bench.strip_problems(p, n)
+        assert all(len(q["bc"]["west"]["ux_profile"]) == q["ny"] for q in strips)
+        assert np.array_equal(np.concatenate([q["bc"]["west"]["ux_profile"] for q in strips]), prof)
+    band = bench.row_band(p, 40)
+    assert band["ny"] == 40 and len(band["bc"]["west"]["ux_profile"]) == 40
+    lo = int(round(p["body"]["y"] - 20))
+    assert np.array_equal(band["bc"]["west"]["ux_profile"], prof[lo:lo + 40])
+    m = wl.several_bodies()
+    strips = bench.strip_problems(m, 16)
+    kept = sorted((c["x"], c["y"] + sum(q["ny"] for q in strips[:k]))
+                  for k, q in enumerate(strips) for c in q.get("bodies") or [])
+    assert kept == sorted((c["x"], c["y"]) for c in m["bodies"])
+    for q in strips:
+        assert all(0 <= c["y"] < q["ny"] for c in q.get("bodies") or [])
+
+
+def test_reference_arm_prints_the_contract_line_on_the_host():
+    # the reference arm (the oracle on the host cores) on a small workload:
+    # one JSON line with the keys the comparison reads
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3",
+                        "--workload", "channel_256x128"], cwd=bench.ROOT, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["unit"] == "MLUPS" and d["value"] > 0
+    assert d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["config"]["workload"] == "channel_fixed_disk_256x128"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
 def test_dominant_kernel_follows_the_node_updates_of_the_region():
