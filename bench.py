@@ -233,10 +233,19 @@ def host_cores() -> int:
 
 def cut_rows(p: dict, lo: int, hi: int) -> dict:
     """Rows [lo, hi) of the workload as a lattice of their own: no-slip walls
-    at the cut edges, the west and east walls' per-row velocity profiles cut
-    to the same rows, and the bodies whose centre lies in the rows kept at
-    the same place relative to them (the others left out)."""
-    bc = dict(p["bc"], south={"kind": "noslip", "u": (0.0, 0.0)}, north={"kind": "noslip", "u": (0.0, 0.0)})
+    at the cut edges (a south or north wall of the workload stays where the
+    rows reach it, unless it is periodic), the west and east walls' per-row
+    velocity profiles cut to the same rows, and the bodies whose centre lies
+    in the rows kept at the same place relative to them (the others left
+    out)."""
+    wall = {"kind": "noslip", "u": (0.0, 0.0)}
+    whole = lo == 0 and hi == p["ny"]
+
+    def edge(side, reached):
+        keep = whole or (reached and p["bc"][side]["kind"] != "periodic")
+        return p["bc"][side] if keep else wall
+
+    bc = dict(p["bc"], south=edge("south", lo == 0), north=edge("north", hi == p["ny"]))
     for side in ("west", "east"):
         d = dict(bc[side])
         for key in ("ux_profile", "uy_profile"):

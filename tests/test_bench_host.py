@@ -31,6 +31,21 @@ def test_strips_cover_the_lattice_once_and_keep_the_body_once():
             assert q["bc"]["west"] == p["bc"]["west"] and q["bc"]["east"] == p["bc"]["east"]
 
 
+def test_strips_keep_the_outer_walls_where_they_reach_them():
+    # the paper's cylinder has symmetry walls south and north: the first
+    # strip keeps the south one, the last the north one, the cuts are no-slip;
+    # a periodic edge becomes a wall unless the strip is the whole lattice
+    p = wl.paper_oscillating_cylinder()
+    strips = bench.strip_problems(p, 4)
+    kinds = [(q["bc"]["south"]["kind"], q["bc"]["north"]["kind"]) for q in strips]
+    assert kinds[0] == (p["bc"]["south"]["kind"], "noslip") and kinds[-1] == ("noslip", p["bc"]["north"]["kind"])
+    assert all(k == ("noslip", "noslip") for k in kinds[1:-1])
+    assert bench.strip_problems(p, 1)[0]["bc"] == p["bc"]
+    box = wl.periodic_box(40, 30)
+    assert [q["bc"]["south"]["kind"] for q in bench.strip_problems(box, 3)] == ["noslip"] * 3
+    assert bench.strip_problems(box, 1)[0]["bc"]["south"]["kind"] == "periodic"
+
+
 def test_strips_cut_wall_profiles_and_keep_every_body_once():
     # a per-row inlet profile is cut with the rows; several bodies each stay
     # in the one strip that holds its centre
