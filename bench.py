@@ -334,7 +334,7 @@ def cpu_baseline(problem: dict, budget_s: float = 10.0):
             "sample": f"all cores: {strip_steps} FP64 time steps of the full {problem['nx']}x{problem['ny']} lattice "
                       f"cut into {cores} full-width strips, one single-threaded oracle process per core, "
                       f"after 1 untimed step (node updates of all strips over the slowest strip's time); "
-                      f"one core: {steps} steps of the whole lattice after 1 untimed"}
+                      f"one core: {steps} step{'s' if steps != 1 else ''} of the whole lattice after 1 untimed"}
 
 
 def run_reference(args, rank, world):
