@@ -579,6 +579,7 @@ class Simulation:
                                              self.stream.cuda_stream, bufs)
 
     def close(self):
+        """Destroy the context (device memory it owns, graphs, the adjoint workspace)."""
         if getattr(self, "ctx", None):
             vplbm_destroy(self.ctx)
             self.ctx = None
@@ -591,6 +592,8 @@ class Simulation:
 
     # state -------------------------------------------------------------------------
     def init_equilibrium(self, rho=None, ux=None, uy=None):
+        """Equilibrium populations (Eq. 11) of host fields rho, ux, uy ([ny, nx],
+        FP64; None: rho0 and 0); resets the step counter and the body."""
         shape = (self.ny, self.nx)
         arrs = [None if a is None else _f64(np.broadcast_to(a, shape)) for a in (rho, ux, uy)]
         vplbm_init_equilibrium(self.ctx, *arrs)
@@ -602,20 +605,25 @@ class Simulation:
         self.init_equilibrium(init.get("rho", None), u[0], u[1])
 
     def set_populations(self, f):
+        """Set the full populations f[9, ny, nx] (FP64, host); stored in the context's precision."""
         vplbm_set_populations(self.ctx, _f64(f, (Q, self.ny, self.nx)))
 
     def step(self, n: int = 1):
+        """Advance n time steps (asynchronous on the simulation's stream)."""
         vplbm_step(self.ctx, n)
 
     def sync(self):
+        """Wait for the stream; raises VplbmError on a latched device error (non-finite density, a timed-out wait)."""
         vplbm_sync(self.ctx)
 
     def populations(self) -> np.ndarray:
+        """The full populations f[9, ny, nx] in FP64 (deviation storage has w rho0 added back)."""
         out = np.empty((Q, self.ny, self.nx))
         vplbm_get_populations(self.ctx, out)
         return out
 
     def fields(self):
+        """rho, ux, uy [ny, nx] in FP64 at the current step."""
         rho = np.empty((self.ny, self.nx))
         ux = np.empty_like(rho)
         uy = np.empty_like(rho)
@@ -631,11 +639,13 @@ class Simulation:
         return arr.reshape(count, len(RECORD_FIELDS)).copy()
 
     def body_state(self, body: int = 0):
+        """Pose (x_G, y_G, theta) and velocity (vx, vy, omega) of body `body` at the current step."""
         q, v, _ = vplbm_get_body_k(self.ctx, body)
         return q, v
 
     @property
     def nstep(self) -> int:
+        """Time steps taken since the last initialisation."""
         return vplbm_get_body(self.ctx)[2]
 
     def set_launch(self, kernel, bx=0, by=0):
@@ -651,11 +661,13 @@ class Simulation:
         return KERNEL_NAMES[k], bx, by
 
     def autotune(self, steps_per_trial: int = 20):
+        """Time the step kernels and launch shapes over short trials, keep the fastest; returns it as launch()."""
         vplbm_autotune(self.ctx, steps_per_trial)
         return self.launch()
 
     @property
     def launches(self) -> int:
+        """Kernel launches made by step() since creation."""
         return vplbm_get_launch_count(self.ctx)
 
     def kernel_launches(self) -> dict:
@@ -672,9 +684,11 @@ class Simulation:
         return vplbm_adjoint(self.ctx, self.ny, nsteps, window_start, w_cd, w_cl, checkpoint_interval)
 
     def save(self, path):
+        """Write a checkpoint (populations, body state, step counter, history ring) to path."""
         vplbm_save(self.ctx, path)
 
     def load(self, path):
+        """Read a checkpoint written by save() on a context of the same size, precision and history capacity."""
         vplbm_load(self.ctx, path)
 
 
@@ -698,7 +712,9 @@ class _Member:
 
 
 class Batch:
-    """Many simulations of uneven sizes stepped together (one launch per step)."""
+    """Many simulations of uneven sizes stepped together: concurrent graph
+    branches (one per member), one launch per step over all members' tiles,
+    or one persistent launch for many steps (set_mode, autotune)."""
 
     def __init__(self, problems, precision: str = "f32", history_capacity: int = 1 << 12, stream=None):
         import torch
@@ -714,6 +730,7 @@ class Batch:
         self.members = [_Member(vplbm_batch_member(self.handle, k), p) for k, p in enumerate(self.problems)]
 
     def close(self):
+        """Destroy the batch and every member's context."""
         if getattr(self, "handle", None):
             vplbm_batch_destroy(self.handle)
             self.handle = None
@@ -725,16 +742,21 @@ class Batch:
             pass
 
     def init_from_problems(self):
+        """Every member at the equilibrium of its problem's uniform initial state."""
         for m in self.members:
             m.init_from_problem()
 
     def step(self, n: int = 1):
+        """Advance every member n time steps (asynchronous on the batch's stream)."""
         vplbm_batch_step(self.handle, n)
 
     def sync(self):
+        """Wait for the stream; raises VplbmError on a latched device error of any member
+        (a persistent launch's timed-out grid barrier included)."""
         vplbm_batch_sync(self.handle)
 
     def set_launch(self, block_x: int, block_y: int = 1, tiles_per_block: int = 1):
+        """Block shape and tiles per block of the one-launch-per-step (tile) mode."""
         vplbm_batch_set_launch(self.handle, block_x, block_y, tiles_per_block)
 
     def launch(self):
@@ -748,9 +770,11 @@ class Batch:
 
     @property
     def mode(self) -> str:
+        """The current mode: "branches", "tiles" or "persistent"."""
         return BATCH_MODE_NAMES[vplbm_batch_get_mode(self.handle)]
 
     def set_persistent(self, block_x: int = 64, block_y: int = 4, chunk: int = 2, params_in_shared: bool = False):
+        """Block shape, work items per queue draw and parameter staging of the persistent mode."""
         vplbm_batch_set_persistent(self.handle, block_x, block_y, chunk, params_in_shared)
 
     def persistent(self):
@@ -758,6 +782,8 @@ class Batch:
         return vplbm_batch_get_persistent(self.handle)
 
     def inject_barrier_timeout(self, enable: bool = True):
+        """Test hook: the persistent launch's grid barriers wait for one arrival more than
+        the grid makes, so they give up after a short bounded wait (ETIMEOUT at sync)."""
         vplbm_batch_inject_barrier_timeout(self.handle, enable)
 
     def autotune(self, steps_per_trial: int = 8):
